@@ -1,0 +1,38 @@
+"""FP64 CPU oracle for the simulation and pre-processing hot path (test infrastructure).
+
+This package is the slow, plain, obviously-correct restatement of what the GPU
+library computes.  It exists only to check the GPU path: the only code allowed
+to import it is ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg
+of ``bench.py``.  The product path (the ``paper_2407_19048_gb300`` package and
+its CUDA library) never imports, calls or links anything here, and this package
+imports nothing from the product.
+
+The method (Sec. 3, "Simulations on Accelerated Hardware") generates training
+data on the fly: draw parameters from the prior (Table 1), evaluate
+frequency-domain compact-binary waveforms (Sec. 3.1), project them onto the
+detectors, inject them into background strain, estimate the background power
+spectrum and whiten the batch (Sec. 3.2).  The plain likelihood used by the
+paper's nested-sampling comparison (Sec. 6, Fig. 5 caption: "the standard GW
+likelihood") is the sixth piece.
+
+Modules, in pipeline order:
+
+* ``philox``     -- Philox4x32-10 counter-based generator (Salmon et al. 2011).
+* ``prior``      -- parameter draws for one batch (Table 1 / configured ranges).
+* ``taylorf2``   -- TaylorF2 3.5PN frequency-domain inspiral (Sec. 3.1).
+* ``detector``   -- detector geometry, antenna patterns, delays, projection.
+* ``noise``      -- analytic aLIGO PSD and coloured Gaussian background.
+* ``spectral``   -- Welch PSD, PSD interpolation, injection, whitening.
+* ``likelihood`` -- noise-weighted inner product, log-likelihood, mismatch.
+* ``pipeline``   -- the whole per-batch pass, step by step, unfused.
+
+Everything is float64 / uint32-uint64 numpy.  ``numpy.fft`` is used as the
+FFT primitive; the pins in ``tests/test_oracle_*.py`` tie every function to
+closed forms, textbook special cases, library routines (``scipy.signal``) or
+brute force.
+
+Parity status: every function is pinned except the spin-dependent TaylorF2
+terms beyond 1.5PN spin-orbit, which the oracle does not include (no
+published table for them is available here), and IMRPhenomD, which is not
+implemented (its fitted coefficient tables are not available).
+"""
