@@ -1,0 +1,236 @@
+/*
+ * gwx.h -- C ABI of libgwx: on-the-fly simulation and pre-processing of
+ * compact-binary gravitational-wave training data on one NVIDIA GB300 (sm_103a).
+ *
+ * The paper (Sec. 3, "Simulations on Accelerated Hardware") generates every
+ * training batch on the GPU: prior draws (Table 1), frequency-domain waveforms
+ * (Sec. 3.1), projection onto the detectors, injection into background
+ * windows cropped from a device-resident chunk, a power spectrum fitted to the
+ * chunk, and whitening (Sec. 3.2).  Its parameter-estimation comparison uses
+ * the standard Gaussian-noise likelihood (Sec. 6, Fig. 5 caption).  Each of
+ * those steps is one entry point below, plus one fused entry point that runs
+ * the whole per-batch pass.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Return value: GWX_OK (0) or a negative GWX_E* status.  On failure
+ *   gwx_last_error() returns a message for the calling thread.  Arguments are
+ *   validated before anything is launched; a failed validation launches nothing.
+ * - Array arguments are DEVICE pointers owned by the caller unless a comment
+ *   says "host".  The library never frees, keeps or reallocates them.
+ * - Arrays are C-contiguous.  "complex" arrays are interleaved float pairs
+ *   (re, im): a [B][F] complex array holds 2*B*F floats.
+ * - Every call is asynchronous on `stream` (a cudaStream_t, NULL = legacy
+ *   default stream) and performs no device allocation and no host
+ *   synchronisation.  Calls that need scratch memory take a caller-owned
+ *   device workspace and its size; the matching *_workspace() query returns
+ *   the required size in bytes.  A workspace may be reused by later calls on
+ *   the same stream; calls that overlap in time on the GPU must not share one.
+ * - gwx_init() prepares per-device constant tables (FFT twiddles, powers of
+ *   the bin index).  Every entry point calls it implicitly for the current
+ *   device on first use; because that set-up copies to device memory
+ *   synchronously, the first call on a device must not happen inside CUDA
+ *   stream capture (call gwx_init() beforehand).
+ * - Frequency grid of a window of N samples at rate fs: f_k = k df,
+ *   df = fs / N, k = 0 .. N/2 (F = N/2 + 1 bins).  Supported window lengths
+ *   are powers of two 256 <= N <= 16384; Welch segment lengths are powers of
+ *   two 16 <= seg_len <= 16384; background lengths are powers of two
+ *   1024 <= L <= 2^24.  Up to GWX_MAX_DET detectors.
+ */
+#ifndef GWX_H
+#define GWX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define GWX_OK            0
+#define GWX_EINVAL       -1   /* bad pointer or scalar argument            */
+#define GWX_ESHAPE       -2   /* unsupported or inconsistent sizes         */
+#define GWX_ECUDA        -3   /* a CUDA runtime call failed                */
+#define GWX_ENOMEM       -4   /* workspace smaller than *_workspace()      */
+#define GWX_ETIMEOUT     -5   /* reserved: bounded device wait expired     */
+#define GWX_EUNSUPPORTED -6   /* valid request this build does not offer   */
+
+/* ---- waveform models ---------------------------------------------------- */
+#define GWX_TAYLORF2    0     /* TaylorF2 3.5PN inspiral (Sec. 3.1)         */
+#define GWX_IMRPHENOMD  1     /* IMRPhenomD (Sec. 3.1): returns GWX_EUNSUPPORTED */
+
+/* ---- detectors ------------------------------------------------------- */
+#define GWX_H1 0              /* LIGO Hanford                               */
+#define GWX_L1 1              /* LIGO Livingston                            */
+#define GWX_V1 2              /* Virgo                                      */
+#define GWX_MAX_DET 4
+
+/* ---- parameter layout: theta is double[GWX_NPARAM][B] (row p = parameter p) */
+enum {
+  GWX_M1 = 0,      /* primary mass, detector frame [M_sun]                  */
+  GWX_M2,          /* secondary mass [M_sun]                                */
+  GWX_CHI1,        /* aligned spin of body 1                                */
+  GWX_CHI2,        /* aligned spin of body 2                                */
+  GWX_DIST,        /* luminosity distance [Mpc]                             */
+  GWX_TC,          /* geocentre merger time from the window start [s]       */
+  GWX_PHIC,        /* coalescence phase [rad]                               */
+  GWX_THETAJN,     /* inclination theta_JN [rad]                            */
+  GWX_PSI,         /* polarisation angle [rad]                              */
+  GWX_RA,          /* right ascension [rad]                                 */
+  GWX_DEC,         /* declination [rad]                                     */
+  GWX_NPARAM
+};
+
+/* Prior box for gwx_sample_prior / gwx_simulate_batch (Table 1 shapes for the
+ * angles; uniform ranges for masses, spins, distance, merger time, phase and
+ * polarisation). */
+typedef struct gwx_prior {
+  double m_lo, m_hi;       /* m1, m2 ~ U[m_lo, m_hi]                          */
+  double chi_lo, chi_hi;   /* chi1, chi2 ~ U[chi_lo, chi_hi]                  */
+  double d_lo, d_hi;       /* distance ~ U[d_lo, d_hi] Mpc                    */
+  double tc_lo, tc_hi;     /* tc ~ U[tc_lo, tc_hi] s                          */
+  double phi_lo, phi_hi;   /* phic ~ U[phi_lo, phi_hi]                        */
+  double psi_lo, psi_hi;   /* psi ~ U[psi_lo, psi_hi]                         */
+} gwx_prior;
+
+/* ---- library ---------------------------------------------------------- */
+int         gwx_version(void);                  /* 10000*major + 100*minor + patch */
+const char* gwx_status_string(int status);      /* static string                  */
+const char* gwx_last_error(void);               /* thread-local message           */
+int         gwx_init(void);                     /* tables for the current device  */
+
+/* Host query: detector tensor D (row-major 3x3, D = (x x^T - y y^T)/2 from the
+ * arm unit vectors) and vertex position [m] (Earth-fixed, WGS-84) of detector
+ * `det`.  Both outputs are HOST arrays.  Pure host code, no CUDA call. */
+int gwx_detector_geometry(int det, double* tensor9, double* position3);
+
+/* ---- A1: prior draws --------------------------------------------------
+ * Sec. 3.2 "We generate N points from our parameter prior"; Table 1 shapes.
+ * Draw b uses Philox4x32-10 (Salmon et al., SC'11) with counter
+ * (b, j, 1, step), key (seed low word, seed high word), j = 0..5.  Block j
+ * yields uniforms u_{2j}, u_{2j+1} from word pairs (0,1), (2,3) as
+ * u = (x + 1/2) 2^-52, x the top 52 bits of the pair; block 5 words (0,1) give
+ * u_10 and word 2 gives the crop offset floor(w (L-N+1) / 2^32).  Transforms:
+ * m1,m2,chi1,chi2,distance,tc,phic,psi linear in u_0..u_6,u_8;
+ * theta_jn = acos(1 - 2u_7), ra = 2 pi u_9, dec = asin(2 u_10 - 1).
+ *   prior   HOST pointer to the prior box.
+ *   theta   out, double[GWX_NPARAM][B].     offsets  out, int64[B] in [0, L-N].
+ * B = 0 is valid and launches nothing. */
+int gwx_sample_prior(const gwx_prior* prior, uint64_t seed, uint32_t step,
+                     int64_t B, int64_t L, int64_t N,
+                     double* theta, int64_t* offsets, void* stream);
+
+/* ---- A2: waveforms ------------------------------------------------------
+ * Sec. 3.1: TaylorF2 3.5PN inspiral.  h(f) = A f^-7/6 exp(-i Psi(f)) with the
+ * non-spinning phase coefficients of Buonanno et al. 2009 (eq. 3.18) plus the
+ * 1.5PN aligned-spin spin-orbit term, leading-order amplitude, merger at the
+ * time origin (tc is applied by gwx_project); h_plus = A (1+cos^2 i)/2 e^{-i Psi},
+ * h_cross = -i A cos i e^{-i Psi}.  Bins k with ceil(f_lo/df) <= k <=
+ * floor(f_isco/df), f_isco = 1/(6^1.5 pi M), are non-zero; all others are zero.
+ *   theta  in, double[GWX_NPARAM][B] (masses, spins, distance, phic, theta_jn used).
+ *   hp, hc out, complex[B][F] (strain per Hz).
+ * approximant GWX_IMRPHENOMD returns GWX_EUNSUPPORTED. */
+int gwx_generate_waveforms(int approximant, const double* theta, int64_t B,
+                           double f_lo, double df, int64_t F,
+                           float* hp, float* hc, void* stream);
+
+/* ---- A3: projection and time shift -------------------------------------
+ * Sec. 6: signal projection onto the detectors on the fly on the GPU.
+ * h_det[b][d][k] = (F+_d hp[b][k] + Fx_d hc[b][k]) exp(-2 pi i f_k (tc_b + dt_d)),
+ * F+ = X.D.X - Y.D.Y, Fx = X.D.Y + Y.D.X with the polarisation basis
+ * X = cos(psi) e_theta + sin(psi) e_phi, Y = sin(psi) e_theta - cos(psi) e_phi of
+ * the source direction (theta = pi/2 - dec, phi = ra - gmst), and
+ * dt_d = -(r_d . n)/c.
+ *   det_ids HOST int32[D] of GWX_H1/L1/V1.  h_det out, complex[B][D][F]. */
+int gwx_project(const float* hp, const float* hc, const double* theta, int64_t B,
+                const int32_t* det_ids, int D, double gmst, double df, int64_t F,
+                float* h_det, void* stream);
+
+/* ---- A4: coloured Gaussian background ------------------------------------
+ * Synthetic stand-in for the paper's real background chunk (Sec. 3.2).
+ * Per detector d: X_0 = 0, X_k = sqrt(L fs S(f_k)/4)(g_re + i g_im) for
+ * 0 < k < L/2, X_{L/2} = sqrt(L fs S/2) g_re, noise[d] = irfft(X) (1/L
+ * normalisation), with S(f) the analytic aLIGO fit evaluated at max(f, f_lo).
+ * g from Box-Muller on Philox counter (k/2, d, 2, step): bin 2j takes words
+ * (0,1), bin 2j+1 words (2,3), u = ((w >> 8) + 1/2) 2^-24.
+ *   noise out, float[D][L].  L a power of two, 1024 <= L <= 2^24. */
+size_t gwx_colored_noise_workspace(int D, int64_t L);
+int gwx_colored_noise(uint64_t seed, uint32_t step, int D, int64_t L, double fs, double f_lo,
+                      float* noise, void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---- A5: Welch PSD --------------------------------------------------------
+ * Sec. 3.2 "The power spectra is fit to this background chunk".  One-sided
+ * density, periodic Hann window, mean of K = (L - seg_len)/stride + 1
+ * periodograms, no detrending: P_k = c_k/(fs sum w^2) (1/K) sum_s |rfft(w x_s)_k|^2,
+ * c_k = 1 at DC and Nyquist, 2 elsewhere.  FP32 FFTs, FP64 squares and sums.
+ *   x in float[D][L].  psd out, double[D][seg_len/2+1]. */
+size_t gwx_welch_psd_workspace(int D, int64_t L, int64_t seg_len, int64_t stride);
+int gwx_welch_psd(const float* x, int D, int64_t L, double fs, int64_t seg_len, int64_t stride,
+                  double* psd, void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---- A6: crop and inject ---------------------------------------------------
+ * Sec. 3.2: N background windows are cropped from the chunk and the signals are
+ * injected.  d[b][dd] = noise[dd][off_b : off_b + N] + irfft(fs h_det[b][dd])
+ * (circular window; the crop offset is shared by the detectors of a draw).
+ *   noise in float[D][L]; offsets in int64[B], 0 <= off <= L-N;
+ *   h_det in complex[B][D][N/2+1]; d out float[B][D][N]. */
+int gwx_inject(const float* noise, int D, int64_t L, const int64_t* offsets,
+               const float* h_det, int64_t B, int64_t N, double fs,
+               float* d, void* stream);
+
+/* ---- A7: whitening -----------------------------------------------------------
+ * Sec. 3.2 "We whiten the batch using the estimated power spectra".
+ * y = irfft(rfft(d) M_k / sqrt(S~_k fs/2)), M_k = 1 for ceil(f_lo/df) <= k < N/2,
+ * S~ = psd (grid fs/seg_len) linearly interpolated to f_k.
+ *   d in float[B][D][N]; psd in double[D][seg_len/2+1]; y out float[B][D][N]
+ *   (y may alias d). */
+size_t gwx_whiten_workspace(int D, int64_t N);
+int gwx_whiten(const float* d, const double* psd, int64_t seg_len, double fs, double f_lo,
+               int64_t B, int D, int64_t N, float* y,
+               void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---- A1-A3, A6, A7 fused: one whitened batch --------------------------------
+ * The whole per-batch pass of Sec. 3.2 in one call: prior draws (as
+ * gwx_sample_prior with `seed`, `step`), TaylorF2 waveforms, projection and
+ * shift, crop + injection into `noise`, whitening with `psd`.  Injection is
+ * linear, so each window is transformed once: y = irfft((rfft(crop) + fs h_det) W).
+ * Results equal gwx_whiten(gwx_inject(...)) up to rounding.
+ *   noise in float[D][L]; psd in double[D][seg_len/2+1];
+ *   y out float[B][D][N]; theta out double[GWX_NPARAM][B]; offsets out int64[B]. */
+size_t gwx_simulate_batch_workspace(int D, int64_t B, int64_t N);
+int gwx_simulate_batch(const gwx_prior* prior, uint64_t seed, uint32_t step,
+                       const float* noise, int64_t L, const double* psd, int64_t seg_len,
+                       double fs, double f_lo, const int32_t* det_ids, int D, double gmst,
+                       int64_t B, int64_t N, float* y, double* theta, int64_t* offsets,
+                       void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---- A8: log-likelihood -------------------------------------------------------
+ * Sec. 6 (Fig. 5 caption): the standard GW likelihood.  For sample s of event e
+ * (event_offsets[e] <= s < event_offsets[e+1]):
+ *   ln L_s = -(1/N) sum_d sum_{ceil(f_lo/df) <= k < N/2} |Y_e,d,k - fs h_d(theta_s, f_k) W_d,k|^2,
+ * Y = rfft(y_data) of the whitened data, W = 1/sqrt(S~ fs/2), h_d the TaylorF2
+ * projection of theta_s.  Equal to -<d-h, d-h>/2 with the noise-weighted inner
+ * product.  FP32 products, FP64 sums.
+ *   y_data in float[E][D][N]; theta in double[GWX_NPARAM][S];
+ *   event_offsets in int64[E+1] (device, ragged, event_offsets[E] == S);
+ *   lnl out double[S]. */
+size_t gwx_log_likelihood_workspace(int64_t E, int D, int64_t N, int64_t S);
+int gwx_log_likelihood(int approximant, const float* y_data, int64_t E, int D, int64_t N,
+                       const double* psd, int64_t seg_len, double fs, double f_lo,
+                       const int32_t* det_ids, double gmst,
+                       const double* theta, const int64_t* event_offsets, int64_t S,
+                       double* lnl, void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---- transforms (the FFT kernels of the steps above, exposed for checking) ----
+ * gwx_rfft:  X[r] = rfft(x[r]) for R rows of N real samples (numpy convention,
+ *            X_k = sum_n x_n e^{-2 pi i k n/N}); X complex[R][N/2+1].
+ * gwx_irfft: x[r] = irfft(X[r]) with 1/N normalisation; imaginary parts of the
+ *            DC and Nyquist bins are ignored. */
+int gwx_rfft(const float* x, int64_t R, int64_t N, float* X, void* stream);
+int gwx_irfft(const float* X, int64_t R, int64_t N, float* x, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GWX_H */

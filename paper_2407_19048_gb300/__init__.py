@@ -1,0 +1,253 @@
+"""GB300-native on-the-fly simulation and pre-processing of gravitational-wave training data.
+
+Python binding of the libgwx C ABI (``include/gwx.h``).  Each function below
+has the name of a C entry point without its ``gwx_`` prefix and only marshals
+arguments: it checks tensor devices, dtypes and shapes, allocates outputs and
+workspaces with PyTorch on the current CUDA device, and calls the library on
+PyTorch's current stream.  All computation happens in the library's CUDA
+kernels; nothing here has a CPU path.
+
+The steps follow Sec. 3 of the paper: prior draws (Table 1), TaylorF2
+waveforms (Sec. 3.1), detector projection, background crops and injection,
+Welch PSD and whitening (Sec. 3.2), plus the standard Gaussian-noise
+log-likelihood used by its nested-sampling comparison (Sec. 6).
+"""
+import ctypes
+
+from . import _lib
+
+TAYLORF2 = 0
+IMRPHENOMD = 1
+DETECTORS = {"H1": 0, "L1": 1, "V1": 2}
+M1, M2, CHI1, CHI2, DIST, TC, PHIC, THETAJN, PSI, RA, DEC = range(11)
+NPARAM = 11
+
+__all__ = ["GwxError", "version", "init", "detector_geometry", "sample_prior", "generate_waveforms", "project",
+           "colored_noise", "welch_psd", "inject", "whiten", "simulate_batch", "log_likelihood", "rfft", "irfft",
+           "workspace_bytes", "TAYLORF2", "IMRPHENOMD", "DETECTORS"]
+
+
+class GwxError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("libgwx status %d: %s" % (status, message))
+        self.status = status
+
+
+def _check(status):
+    if status != 0:
+        lib = _lib.load()
+        raise GwxError(status, lib.gwx_last_error().decode(errors="replace"))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream():
+    torch = _torch()
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else ctypes.c_void_p(0)
+
+
+def _dev(t, dtype, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch.Tensor" % name)
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor (libgwx has no CPU path)" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return t
+
+
+def _workspace(nbytes, device):
+    torch = _torch()
+    if nbytes == 0:
+        return None, 0
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+    off = (-ws.data_ptr()) % 256
+    return ws[off:off + nbytes], nbytes
+
+
+def _det_ids(dets):
+    ids = [DETECTORS[d] if isinstance(d, str) else int(d) for d in dets]
+    return (ctypes.c_int32 * len(ids))(*ids), len(ids)
+
+
+def _prior(p):
+    if isinstance(p, _lib.GwxPrior):
+        return p
+    return _lib.GwxPrior(*[float(p[k]) for k in (
+        "m_lo", "m_hi", "chi_lo", "chi_hi", "d_lo", "d_hi", "tc_lo", "tc_hi", "phi_lo", "phi_hi", "psi_lo", "psi_hi")])
+
+
+def version():
+    return _lib.load().gwx_version()
+
+
+def init():
+    """Prepare the per-device tables on the current device (outside stream capture)."""
+    _check(_lib.load().gwx_init())
+
+
+def detector_geometry(det):
+    """(tensor [3][3], position [3] m) of a detector, computed on the host."""
+    lib = _lib.load()
+    T = (ctypes.c_double * 9)()
+    r = (ctypes.c_double * 3)()
+    _check(lib.gwx_detector_geometry(DETECTORS[det] if isinstance(det, str) else int(det), T, r))
+    return [list(T[3 * i:3 * i + 3]) for i in range(3)], list(r)
+
+
+def workspace_bytes(call, *args):
+    """Workspace size of an entry point, e.g. workspace_bytes("whiten", D, N)."""
+    return int(getattr(_lib.load(), "gwx_%s_workspace" % call)(*args))
+
+
+def sample_prior(prior, seed, step, B, L, N, theta=None, offsets=None):
+    torch = _torch()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    theta = torch.empty((NPARAM, B), dtype=torch.float64, device=dev) if theta is None else \
+        _dev(theta, torch.float64, "theta")
+    offsets = torch.empty(B, dtype=torch.int64, device=dev) if offsets is None else _dev(offsets, torch.int64, "offsets")
+    p = _prior(prior)
+    _check(_lib.load().gwx_sample_prior(ctypes.byref(p), seed, step, B, L, N, _ptr(theta), _ptr(offsets), _stream()))
+    return theta, offsets
+
+
+def generate_waveforms(theta, f_lo, df, F, approximant=TAYLORF2, hp=None, hc=None):
+    torch = _torch()
+    _dev(theta, torch.float64, "theta")
+    B = theta.shape[1]
+    hp = torch.empty((B, F), dtype=torch.complex64, device=theta.device) if hp is None else hp
+    hc = torch.empty((B, F), dtype=torch.complex64, device=theta.device) if hc is None else hc
+    _check(_lib.load().gwx_generate_waveforms(approximant, _ptr(theta), B, f_lo, df, F, _ptr(hp), _ptr(hc), _stream()))
+    return hp, hc
+
+
+def project(hp, hc, theta, dets, gmst, df, out=None):
+    torch = _torch()
+    _dev(hp, torch.complex64, "hp")
+    _dev(hc, torch.complex64, "hc")
+    _dev(theta, torch.float64, "theta")
+    B, F = hp.shape
+    ids, D = _det_ids(dets)
+    out = torch.empty((B, D, F), dtype=torch.complex64, device=hp.device) if out is None else out
+    _check(_lib.load().gwx_project(_ptr(hp), _ptr(hc), _ptr(theta), B, ids, D, gmst, df, F, _ptr(out), _stream()))
+    return out
+
+
+def colored_noise(seed, step, D, L, fs, f_lo, out=None):
+    torch = _torch()
+    lib = _lib.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = torch.empty((D, L), dtype=torch.float32, device=dev) if out is None else out
+    ws, nb = _workspace(lib.gwx_colored_noise_workspace(D, L), dev)
+    _check(lib.gwx_colored_noise(seed, step, D, L, fs, f_lo, _ptr(out), _ptr(ws), nb, _stream()))
+    return out
+
+
+def welch_psd(x, fs, seg_len, stride, out=None):
+    torch = _torch()
+    lib = _lib.load()
+    _dev(x, torch.float32, "x")
+    D, L = x.shape
+    out = torch.empty((D, seg_len // 2 + 1), dtype=torch.float64, device=x.device) if out is None else out
+    ws, nb = _workspace(lib.gwx_welch_psd_workspace(D, L, seg_len, stride), x.device)
+    _check(lib.gwx_welch_psd(_ptr(x), D, L, fs, seg_len, stride, _ptr(out), _ptr(ws), nb, _stream()))
+    return out
+
+
+def inject(noise, offsets, h_det, N, fs, out=None):
+    torch = _torch()
+    _dev(noise, torch.float32, "noise")
+    _dev(offsets, torch.int64, "offsets")
+    _dev(h_det, torch.complex64, "h_det")
+    D, L = noise.shape
+    B = h_det.shape[0]
+    out = torch.empty((B, D, N), dtype=torch.float32, device=noise.device) if out is None else out
+    _check(_lib.load().gwx_inject(_ptr(noise), D, L, _ptr(offsets), _ptr(h_det), B, N, fs, _ptr(out), _stream()))
+    return out
+
+
+def whiten(d, psd, seg_len, fs, f_lo, out=None):
+    torch = _torch()
+    lib = _lib.load()
+    _dev(d, torch.float32, "d")
+    _dev(psd, torch.float64, "psd")
+    B, D, N = d.shape
+    out = torch.empty_like(d) if out is None else out
+    ws, nb = _workspace(lib.gwx_whiten_workspace(D, N), d.device)
+    _check(lib.gwx_whiten(_ptr(d), _ptr(psd), seg_len, fs, f_lo, B, D, N, _ptr(out), _ptr(ws), nb, _stream()))
+    return out
+
+
+class SimulateBuffers:
+    """Preallocated outputs and workspace for repeated simulate_batch calls."""
+
+    def __init__(self, B, D, N, device=None):
+        torch = _torch()
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        self.y = torch.empty((B, D, N), dtype=torch.float32, device=dev)
+        self.theta = torch.empty((NPARAM, B), dtype=torch.float64, device=dev)
+        self.offsets = torch.empty(B, dtype=torch.int64, device=dev)
+        self.ws, self.ws_bytes = _workspace(_lib.load().gwx_simulate_batch_workspace(D, B, N), dev)
+
+
+def simulate_batch(prior, seed, step, noise, psd, seg_len, fs, f_lo, dets, gmst, B, N, buffers=None):
+    """One whitened batch (Sec. 3.2): returns (y [B][D][N], theta [11][B], offsets [B])."""
+    torch = _torch()
+    _dev(noise, torch.float32, "noise")
+    _dev(psd, torch.float64, "psd")
+    D, L = noise.shape
+    ids, nd = _det_ids(dets)
+    bufs = buffers or SimulateBuffers(B, nd, N, noise.device)
+    p = _prior(prior)
+    _check(_lib.load().gwx_simulate_batch(ctypes.byref(p), seed, step, _ptr(noise), L, _ptr(psd), seg_len, fs, f_lo,
+                                          ids, nd, gmst, B, N, _ptr(bufs.y), _ptr(bufs.theta), _ptr(bufs.offsets),
+                                          _ptr(bufs.ws), bufs.ws_bytes, _stream()))
+    return bufs.y, bufs.theta, bufs.offsets
+
+
+def log_likelihood(y_data, psd, seg_len, fs, f_lo, dets, gmst, theta, event_offsets, approximant=TAYLORF2,
+                   out=None):
+    """ln L [S] of samples theta [11][S] against whitened events y_data [E][D][N]."""
+    torch = _torch()
+    lib = _lib.load()
+    _dev(y_data, torch.float32, "y_data")
+    _dev(psd, torch.float64, "psd")
+    _dev(theta, torch.float64, "theta")
+    _dev(event_offsets, torch.int64, "event_offsets")
+    E, D, N = y_data.shape
+    S = theta.shape[1]
+    ids, nd = _det_ids(dets)
+    out = torch.empty(S, dtype=torch.float64, device=y_data.device) if out is None else out
+    ws, nb = _workspace(lib.gwx_log_likelihood_workspace(E, D, N, S), y_data.device)
+    _check(lib.gwx_log_likelihood(approximant, _ptr(y_data), E, D, N, _ptr(psd), seg_len, fs, f_lo, ids, gmst,
+                                  _ptr(theta), _ptr(event_offsets), S, _ptr(out), _ptr(ws), nb, _stream()))
+    return out
+
+
+def rfft(x, out=None):
+    torch = _torch()
+    _dev(x, torch.float32, "x")
+    N = x.shape[-1]
+    R = x.numel() // N
+    out = torch.empty(x.shape[:-1] + (N // 2 + 1,), dtype=torch.complex64, device=x.device) if out is None else out
+    _check(_lib.load().gwx_rfft(_ptr(x), R, N, _ptr(out), _stream()))
+    return out
+
+
+def irfft(X, N, out=None):
+    torch = _torch()
+    _dev(X, torch.complex64, "X")
+    R = X.numel() // X.shape[-1]
+    out = torch.empty(X.shape[:-1] + (N,), dtype=torch.float32, device=X.device) if out is None else out
+    _check(_lib.load().gwx_irfft(_ptr(X), R, N, _ptr(out), _stream()))
+    return out

@@ -1,0 +1,74 @@
+"""ctypes declarations of the libgwx C ABI (``include/gwx.h``).
+
+Loading fails loudly when the shared library has not been built: there is no
+fallback implementation of any entry point.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgwx.so")
+
+c_i64 = ctypes.c_int64
+c_u64 = ctypes.c_uint64
+c_u32 = ctypes.c_uint32
+c_int = ctypes.c_int
+c_dbl = ctypes.c_double
+c_size = ctypes.c_size_t
+c_vp = ctypes.c_void_p
+c_i32p = ctypes.POINTER(ctypes.c_int32)
+c_dblp = ctypes.POINTER(ctypes.c_double)
+
+
+class GwxPrior(ctypes.Structure):
+    _fields_ = [(name, c_dbl) for name in (
+        "m_lo", "m_hi", "chi_lo", "chi_hi", "d_lo", "d_hi",
+        "tc_lo", "tc_hi", "phi_lo", "phi_hi", "psi_lo", "psi_hi")]
+
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "gwx_version": (c_int, []),
+    "gwx_status_string": (ctypes.c_char_p, [c_int]),
+    "gwx_last_error": (ctypes.c_char_p, []),
+    "gwx_init": (c_int, []),
+    "gwx_detector_geometry": (c_int, [c_int, c_dblp, c_dblp]),
+    "gwx_sample_prior": (c_int, [ctypes.POINTER(GwxPrior), c_u64, c_u32, c_i64, c_i64, c_i64, c_vp, c_vp, c_vp]),
+    "gwx_generate_waveforms": (c_int, [c_int, c_vp, c_i64, c_dbl, c_dbl, c_i64, c_vp, c_vp, c_vp]),
+    "gwx_project": (c_int, [c_vp, c_vp, c_vp, c_i64, c_i32p, c_int, c_dbl, c_dbl, c_i64, c_vp, c_vp]),
+    "gwx_colored_noise_workspace": (c_size, [c_int, c_i64]),
+    "gwx_colored_noise": (c_int, [c_u64, c_u32, c_int, c_i64, c_dbl, c_dbl, c_vp, c_vp, c_size, c_vp]),
+    "gwx_welch_psd_workspace": (c_size, [c_int, c_i64, c_i64, c_i64]),
+    "gwx_welch_psd": (c_int, [c_vp, c_int, c_i64, c_dbl, c_i64, c_i64, c_vp, c_vp, c_size, c_vp]),
+    "gwx_inject": (c_int, [c_vp, c_int, c_i64, c_vp, c_vp, c_i64, c_i64, c_dbl, c_vp, c_vp]),
+    "gwx_whiten_workspace": (c_size, [c_int, c_i64]),
+    "gwx_whiten": (c_int, [c_vp, c_vp, c_i64, c_dbl, c_dbl, c_i64, c_int, c_i64, c_vp, c_vp, c_size, c_vp]),
+    "gwx_simulate_batch_workspace": (c_size, [c_int, c_i64, c_i64]),
+    "gwx_simulate_batch": (c_int, [ctypes.POINTER(GwxPrior), c_u64, c_u32, c_vp, c_i64, c_vp, c_i64, c_dbl, c_dbl,
+                                   c_i32p, c_int, c_dbl, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_size, c_vp]),
+    "gwx_log_likelihood_workspace": (c_size, [c_i64, c_int, c_i64, c_i64]),
+    "gwx_log_likelihood": (c_int, [c_int, c_vp, c_i64, c_int, c_i64, c_vp, c_i64, c_dbl, c_dbl, c_i32p, c_dbl,
+                                   c_vp, c_vp, c_i64, c_vp, c_vp, c_size, c_vp]),
+    "gwx_rfft": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp]),
+    "gwx_irfft": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp]),
+}
+
+_lib = None
+
+
+def load():
+    """Return the loaded libgwx (raises RuntimeError if it is missing or incomplete)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            "libgwx.so is not built (%s). Run `python -m paper_2407_19048_gb300.build` or "
+            "`__graft_entry__.build()`; there is no CPU fallback." % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)          # AttributeError if the library lacks a symbol
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib

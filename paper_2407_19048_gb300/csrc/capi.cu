@@ -1,0 +1,392 @@
+// capi.cu -- the extern "C" entry points of libgwx: argument validation, the
+// detector site table, per-device table set-up, workspace layout and dispatch to
+// the kernel launchers.  Nothing here allocates device memory.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "gwx_internal.h"
+
+using namespace gwx;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int status, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return status;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(GWX_ECUDA, "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// ---------------------------------------------------------------- detector sites
+// Vertex geodetic latitude and longitude [deg], elevation [m], x- and y-arm
+// azimuths [deg clockwise from North] (approximate published values for the LIGO
+// Hanford, LIGO Livingston and Virgo vertices; arm tilts neglected).
+struct Site { double lat, lon, h, xaz, yaz; };
+const Site kSites[3] = {
+    {46.455147, -119.407657, 142.554, 324.0000, 234.0000},  // H1
+    {30.562894, -90.774240, -6.574, 252.2835, 162.2835},    // L1
+    {43.631415, 10.504497, 51.884, 19.4326, 289.4326},      // V1
+};
+
+void site_geometry(int det, double* T, double* r) {
+  const double deg = 3.141592653589793238462643383279502884 / 180.0;
+  const Site& s = kSites[det];
+  const double phi = s.lat * deg, lam = s.lon * deg;
+  const double north[3] = {-sin(phi) * cos(lam), -sin(phi) * sin(lam), cos(phi)};
+  const double east[3] = {-sin(lam), cos(lam), 0.0};
+  double x[3], y[3];
+  for (int i = 0; i < 3; ++i) {
+    x[i] = cos(s.xaz * deg) * north[i] + sin(s.xaz * deg) * east[i];
+    y[i] = cos(s.yaz * deg) * north[i] + sin(s.yaz * deg) * east[i];
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) T[3 * i + j] = 0.5 * (x[i] * x[j] - y[i] * y[j]);
+  const double a = 6378137.0, f = 1.0 / 298.257223563, e2 = f * (2.0 - f);
+  const double Nphi = a / sqrt(1.0 - e2 * sin(phi) * sin(phi));
+  r[0] = (Nphi + s.h) * cos(phi) * cos(lam);
+  r[1] = (Nphi + s.h) * cos(phi) * sin(lam);
+  r[2] = (Nphi * (1.0 - e2) + s.h) * sin(phi);
+}
+
+int make_detparams(const int32_t* det_ids, int D, DetParams& dp) {
+  if (D < 1 || D > GWX_MAX_DET) return fail(GWX_ESHAPE, "D=%d outside [1, %d]", D, GWX_MAX_DET);
+  if (!det_ids) return fail(GWX_EINVAL, "det_ids is NULL");
+  memset(&dp, 0, sizeof(dp));
+  dp.D = D;
+  for (int d = 0; d < D; ++d) {
+    if (det_ids[d] < 0 || det_ids[d] > 2) return fail(GWX_EINVAL, "unknown detector id %d", det_ids[d]);
+    site_geometry(det_ids[d], dp.tensor[d], dp.pos[d]);
+  }
+  return GWX_OK;
+}
+
+// ---------------------------------------------------------------- per-device set-up
+std::mutex g_init_mu;
+bool g_init_done[256] = {false};
+
+int ensure_init() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 256) return fail(GWX_EUNSUPPORTED, "device ordinal %d", dev);
+  std::lock_guard<std::mutex> lk(g_init_mu);
+  if (g_init_done[dev]) return GWX_OK;
+  if ((e = init_tables_random()) != cudaSuccess) return cuda_fail(e, "table set-up");
+  if ((e = init_tables_spectral()) != cudaSuccess) return cuda_fail(e, "table set-up");
+  if ((e = init_tables_waveform()) != cudaSuccess) return cuda_fail(e, "table set-up");
+  if ((e = init_tables_fused()) != cudaSuccess) return cuda_fail(e, "table set-up");
+  g_init_done[dev] = true;
+  return GWX_OK;
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int launched(cudaError_t e, const char* what) { return e == cudaSuccess ? GWX_OK : cuda_fail(e, what); }
+
+// ---------------------------------------------------------------- validation helpers
+int check_window(int64_t N) {
+  if (!is_pow2(N) || N < 256 || N > 16384)
+    return fail(GWX_ESHAPE, "window length N=%lld must be a power of two in [256, 16384]", (long long)N);
+  return GWX_OK;
+}
+
+int band_start(double f_lo, double df, int64_t limit, int* k_lo) {
+  if (!(f_lo > 0.0) || !(df > 0.0) || !isfinite(f_lo) || !isfinite(df))
+    return fail(GWX_EINVAL, "f_lo=%g and df=%g must be positive", f_lo, df);
+  const double k = ceil(f_lo / df);
+  if (k >= (double)limit) return fail(GWX_ESHAPE, "f_lo=%g is above the last usable bin", f_lo);
+  *k_lo = (int)k;
+  return GWX_OK;
+}
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+size_t whiten_ws_bytes(int D, int64_t N) { return align_up((size_t)D * (size_t)(N / 2 + 1) * sizeof(float)); }
+size_t coef_bytes(int64_t B) { return align_up((size_t)B * sizeof(DrawCoef)); }
+
+int check_ws(void* ws, size_t have, size_t need) {
+  if (need == 0) return GWX_OK;
+  if (!ws) return fail(GWX_EINVAL, "workspace is NULL (need %zu bytes)", need);
+  if (have < need) return fail(GWX_ENOMEM, "workspace of %zu bytes is smaller than the %zu required", have, need);
+  if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(GWX_EINVAL, "workspace must be %zu-byte aligned", kAlign);
+  return GWX_OK;
+}
+
+#define GWX_TRY(expr)          \
+  do {                         \
+    int _st = (expr);          \
+    if (_st != GWX_OK) return _st; \
+  } while (0)
+
+}  // namespace
+
+extern "C" {
+
+int gwx_version(void) { return 100; }
+
+const char* gwx_status_string(int status) {
+  switch (status) {
+    case GWX_OK: return "ok";
+    case GWX_EINVAL: return "invalid argument";
+    case GWX_ESHAPE: return "unsupported or inconsistent sizes";
+    case GWX_ECUDA: return "CUDA runtime error";
+    case GWX_ENOMEM: return "workspace too small";
+    case GWX_ETIMEOUT: return "device wait timed out";
+    case GWX_EUNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+const char* gwx_last_error(void) { return g_err; }
+
+int gwx_init(void) { return ensure_init(); }
+
+int gwx_detector_geometry(int det, double* tensor9, double* position3) {
+  if (det < 0 || det > 2) return fail(GWX_EINVAL, "unknown detector id %d", det);
+  if (!tensor9 || !position3) return fail(GWX_EINVAL, "NULL output");
+  site_geometry(det, tensor9, position3);
+  return GWX_OK;
+}
+
+int gwx_sample_prior(const gwx_prior* prior, uint64_t seed, uint32_t step, int64_t B, int64_t L, int64_t N,
+                     double* theta, int64_t* offsets, void* stream) {
+  if (!prior) return fail(GWX_EINVAL, "prior is NULL");
+  if (B < 0 || B > 0x7fffffffLL) return fail(GWX_ESHAPE, "B=%lld", (long long)B);
+  if (N < 1 || L < N || L - N + 1 > 0xffffffffLL) return fail(GWX_ESHAPE, "need 1 <= N <= L, L-N < 2^32");
+  if (B == 0) return GWX_OK;
+  if (!theta || !offsets) return fail(GWX_EINVAL, "NULL output");
+  GWX_TRY(ensure_init());
+  return launched(launch_sample_prior(*prior, seed, step, B, L, N, theta, offsets, as_stream(stream)),
+                  "sample_prior");
+}
+
+int gwx_generate_waveforms(int approximant, const double* theta, int64_t B, double f_lo, double df, int64_t F,
+                           float* hp, float* hc, void* stream) {
+  if (approximant == GWX_IMRPHENOMD)
+    return fail(GWX_EUNSUPPORTED, "IMRPhenomD is not available: its fitted coefficient tables are not in this build");
+  if (approximant != GWX_TAYLORF2) return fail(GWX_EINVAL, "unknown approximant %d", approximant);
+  if (B < 0 || B > 0x7fffffffLL) return fail(GWX_ESHAPE, "B=%lld", (long long)B);
+  if (F < 2 || F - 1 > 16384) return fail(GWX_ESHAPE, "F=%lld outside [2, 16385]", (long long)F);
+  int k_lo = 0;
+  GWX_TRY(band_start(f_lo, df, F, &k_lo));
+  if (B == 0) return GWX_OK;
+  if (!theta || !hp || !hc) return fail(GWX_EINVAL, "NULL array");
+  GWX_TRY(ensure_init());
+  return launched(launch_generate_waveforms(theta, B, k_lo, df, F, reinterpret_cast<float2*>(hp),
+                                            reinterpret_cast<float2*>(hc), as_stream(stream)),
+                  "generate_waveforms");
+}
+
+int gwx_project(const float* hp, const float* hc, const double* theta, int64_t B, const int32_t* det_ids, int D,
+                double gmst, double df, int64_t F, float* h_det, void* stream) {
+  DetParams dp;
+  GWX_TRY(make_detparams(det_ids, D, dp));
+  if (B < 0 || B > 0x7fffffffLL) return fail(GWX_ESHAPE, "B=%lld", (long long)B);
+  if (F < 1 || !(df > 0.0) || !isfinite(gmst)) return fail(GWX_EINVAL, "bad F, df or gmst");
+  if (B == 0) return GWX_OK;
+  if (!hp || !hc || !theta || !h_det) return fail(GWX_EINVAL, "NULL array");
+  GWX_TRY(ensure_init());
+  return launched(launch_project(reinterpret_cast<const float2*>(hp), reinterpret_cast<const float2*>(hc), theta, B,
+                                 dp, gmst, df, F, reinterpret_cast<float2*>(h_det), as_stream(stream)),
+                  "project");
+}
+
+size_t gwx_colored_noise_workspace(int D, int64_t L) {
+  if (D < 1 || L < 2) return 0;
+  return align_up(colored_noise_ws(D, L));
+}
+
+int gwx_colored_noise(uint64_t seed, uint32_t step, int D, int64_t L, double fs, double f_lo, float* noise,
+                      void* workspace, size_t workspace_bytes, void* stream) {
+  if (D < 1 || D > GWX_MAX_DET) return fail(GWX_ESHAPE, "D=%d", D);
+  if (!is_pow2(L) || L < 1024 || L > ((int64_t)1 << 24))
+    return fail(GWX_ESHAPE, "L=%lld must be a power of two in [1024, 2^24]", (long long)L);
+  if (!(fs > 0.0) || !(f_lo > 0.0)) return fail(GWX_EINVAL, "fs and f_lo must be positive");
+  if (!noise) return fail(GWX_EINVAL, "noise is NULL");
+  GWX_TRY(check_ws(workspace, workspace_bytes, gwx_colored_noise_workspace(D, L)));
+  GWX_TRY(ensure_init());
+  return launched(launch_colored_noise(seed, step, D, L, fs, f_lo, noise, workspace, as_stream(stream)),
+                  "colored_noise");
+}
+
+size_t gwx_welch_psd_workspace(int D, int64_t L, int64_t seg_len, int64_t stride) {
+  if (D < 1 || seg_len < 2 || stride < 1 || L < seg_len) return 0;
+  return align_up(welch_ws(D, L, seg_len, stride));
+}
+
+int gwx_welch_psd(const float* x, int D, int64_t L, double fs, int64_t seg_len, int64_t stride, double* psd,
+                  void* workspace, size_t workspace_bytes, void* stream) {
+  if (D < 1 || D > GWX_MAX_DET) return fail(GWX_ESHAPE, "D=%d", D);
+  if (!is_pow2(seg_len) || seg_len < 16 || seg_len > 16384)
+    return fail(GWX_ESHAPE, "seg_len=%lld must be a power of two in [16, 16384]", (long long)seg_len);
+  if (stride < 1 || stride > seg_len || L < seg_len) return fail(GWX_ESHAPE, "need 1 <= stride <= seg_len <= L");
+  if ((L - seg_len) / stride + 1 > 0x7fffffffLL) return fail(GWX_ESHAPE, "too many segments");
+  if (!(fs > 0.0)) return fail(GWX_EINVAL, "fs must be positive");
+  if (!x || !psd) return fail(GWX_EINVAL, "NULL array");
+  GWX_TRY(check_ws(workspace, workspace_bytes, gwx_welch_psd_workspace(D, L, seg_len, stride)));
+  GWX_TRY(ensure_init());
+  return launched(launch_welch(x, D, L, fs, seg_len, stride, psd, workspace, as_stream(stream)), "welch_psd");
+}
+
+int gwx_inject(const float* noise, int D, int64_t L, const int64_t* offsets, const float* h_det, int64_t B, int64_t N,
+               double fs, float* d, void* stream) {
+  GWX_TRY(check_window(N));
+  if (D < 1 || D > GWX_MAX_DET) return fail(GWX_ESHAPE, "D=%d", D);
+  if (L < N) return fail(GWX_ESHAPE, "L < N");
+  if (B < 0 || B * D > 0x7fffffffLL) return fail(GWX_ESHAPE, "B=%lld", (long long)B);
+  if (!(fs > 0.0)) return fail(GWX_EINVAL, "fs must be positive");
+  if (B == 0) return GWX_OK;
+  if (!noise || !offsets || !h_det || !d) return fail(GWX_EINVAL, "NULL array");
+  GWX_TRY(ensure_init());
+  return launched(launch_inject_rows(noise, D, L, offsets, reinterpret_cast<const float2*>(h_det), B, N, fs, d,
+                                     as_stream(stream)),
+                  "inject");
+}
+
+size_t gwx_whiten_workspace(int D, int64_t N) {
+  if (D < 1 || N < 2) return 0;
+  return whiten_ws_bytes(D, N);
+}
+
+static int check_psd_args(int64_t seg_len, int64_t N) {
+  if (!is_pow2(seg_len) || seg_len < 16 || seg_len > 16384)
+    return fail(GWX_ESHAPE, "seg_len=%lld must be a power of two in [16, 16384]", (long long)seg_len);
+  (void)N;
+  return GWX_OK;
+}
+
+int gwx_whiten(const float* d, const double* psd, int64_t seg_len, double fs, double f_lo, int64_t B, int D,
+               int64_t N, float* y, void* workspace, size_t workspace_bytes, void* stream) {
+  GWX_TRY(check_window(N));
+  GWX_TRY(check_psd_args(seg_len, N));
+  if (D < 1 || D > GWX_MAX_DET) return fail(GWX_ESHAPE, "D=%d", D);
+  if (B < 0 || B * D > 0x7fffffffLL) return fail(GWX_ESHAPE, "B=%lld", (long long)B);
+  if (!(fs > 0.0)) return fail(GWX_EINVAL, "fs must be positive");
+  int k_lo = 0;
+  GWX_TRY(band_start(f_lo, fs / (double)N, N / 2, &k_lo));
+  if (B == 0) return GWX_OK;
+  if (!d || !psd || !y) return fail(GWX_EINVAL, "NULL array");
+  GWX_TRY(check_ws(workspace, workspace_bytes, gwx_whiten_workspace(D, N)));
+  GWX_TRY(ensure_init());
+  float* W = reinterpret_cast<float*>(workspace);
+  cudaStream_t s = as_stream(stream);
+  GWX_TRY(launched(launch_whiten_filter(psd, D, seg_len, fs, k_lo, N, W, s), "whiten filter"));
+  return launched(launch_whiten_rows(d, W, B * D, D, N, y, s), "whiten");
+}
+
+size_t gwx_simulate_batch_workspace(int D, int64_t B, int64_t N) {
+  if (D < 1 || B < 0 || N < 2) return 0;
+  return whiten_ws_bytes(D, N) + coef_bytes(B);
+}
+
+int gwx_simulate_batch(const gwx_prior* prior, uint64_t seed, uint32_t step, const float* noise, int64_t L,
+                       const double* psd, int64_t seg_len, double fs, double f_lo, const int32_t* det_ids, int D,
+                       double gmst, int64_t B, int64_t N, float* y, double* theta, int64_t* offsets, void* workspace,
+                       size_t workspace_bytes, void* stream) {
+  if (!prior) return fail(GWX_EINVAL, "prior is NULL");
+  GWX_TRY(check_window(N));
+  GWX_TRY(check_psd_args(seg_len, N));
+  DetParams dp;
+  GWX_TRY(make_detparams(det_ids, D, dp));
+  if ((size_t)D * (size_t)(N / 2) * sizeof(float2) > 200 * 1024)
+    return fail(GWX_EUNSUPPORTED, "D=%d windows of N=%lld do not fit in shared memory", D, (long long)N);
+  if (L < N || L - N + 1 > 0xffffffffLL) return fail(GWX_ESHAPE, "need N <= L, L-N < 2^32");
+  if (B < 0 || B > 0x7fffffffLL) return fail(GWX_ESHAPE, "B=%lld", (long long)B);
+  if (!(fs > 0.0) || !isfinite(gmst)) return fail(GWX_EINVAL, "bad fs or gmst");
+  const double df = fs / (double)N;
+  int k_lo = 0;
+  GWX_TRY(band_start(f_lo, df, N / 2, &k_lo));
+  if (B == 0) return GWX_OK;
+  if (!noise || !psd || !y || !theta || !offsets) return fail(GWX_EINVAL, "NULL array");
+  GWX_TRY(check_ws(workspace, workspace_bytes, gwx_simulate_batch_workspace(D, B, N)));
+  GWX_TRY(ensure_init());
+  cudaStream_t s = as_stream(stream);
+  float* W = reinterpret_cast<float*>(workspace);
+  DrawCoef* coef = reinterpret_cast<DrawCoef*>(reinterpret_cast<char*>(workspace) + whiten_ws_bytes(D, N));
+  GWX_TRY(launched(launch_sample_prior(*prior, seed, step, B, L, N, theta, offsets, s), "sample_prior"));
+  GWX_TRY(launched(launch_whiten_filter(psd, D, seg_len, fs, k_lo, N, W, s), "whiten filter"));
+  GWX_TRY(launched(launch_draw_setup(theta, B, k_lo, df, fs, N / 2 + 1, dp, gmst, coef, s), "draw set-up"));
+  return launched(launch_simulate_fused(coef, noise, L, offsets, W, k_lo, D, B, N, fs, y, s), "simulate");
+}
+
+static size_t loglike_base_bytes(int64_t E, int D, int64_t N) {
+  // per-event spectra, whitening filter, per-event norms
+  return align_up((size_t)E * D * (size_t)(N / 2 + 1) * sizeof(float2)) + whiten_ws_bytes(D, N) +
+         align_up((size_t)E * sizeof(double));
+}
+
+size_t gwx_log_likelihood_workspace(int64_t E, int D, int64_t N, int64_t S) {
+  if (E < 0 || D < 1 || N < 2 || S < 0) return 0;
+  return loglike_base_bytes(E, D, N) + coef_bytes(S);
+}
+
+int gwx_log_likelihood(int approximant, const float* y_data, int64_t E, int D, int64_t N, const double* psd,
+                       int64_t seg_len, double fs, double f_lo, const int32_t* det_ids, double gmst,
+                       const double* theta, const int64_t* event_offsets, int64_t S, double* lnl, void* workspace,
+                       size_t workspace_bytes, void* stream) {
+  if (approximant == GWX_IMRPHENOMD)
+    return fail(GWX_EUNSUPPORTED, "IMRPhenomD is not available: its fitted coefficient tables are not in this build");
+  if (approximant != GWX_TAYLORF2) return fail(GWX_EINVAL, "unknown approximant %d", approximant);
+  GWX_TRY(check_window(N));
+  GWX_TRY(check_psd_args(seg_len, N));
+  DetParams dp;
+  GWX_TRY(make_detparams(det_ids, D, dp));
+  if (E < 0 || S < 0 || S > 0x7fffffffLL * 8 || E * D > 0x7fffffffLL) return fail(GWX_ESHAPE, "bad E or S");
+  if (S > 0 && E == 0) return fail(GWX_ESHAPE, "samples without events");
+  if (!(fs > 0.0) || !isfinite(gmst)) return fail(GWX_EINVAL, "bad fs or gmst");
+  const double df = fs / (double)N;
+  int k_lo = 0;
+  GWX_TRY(band_start(f_lo, df, N / 2, &k_lo));
+  if (S == 0) return GWX_OK;
+  if (!y_data || !psd || !theta || !event_offsets || !lnl) return fail(GWX_EINVAL, "NULL array");
+  GWX_TRY(check_ws(workspace, workspace_bytes, gwx_log_likelihood_workspace(E, D, N, S)));
+  GWX_TRY(ensure_init());
+  cudaStream_t s = as_stream(stream);
+  char* w = reinterpret_cast<char*>(workspace);
+  float2* Y = reinterpret_cast<float2*>(w);
+  w += align_up((size_t)E * D * (size_t)(N / 2 + 1) * sizeof(float2));
+  float* W = reinterpret_cast<float*>(w);
+  w += whiten_ws_bytes(D, N);
+  double* yy = reinterpret_cast<double*>(w);
+  w += align_up((size_t)E * sizeof(double));
+  DrawCoef* coef = reinterpret_cast<DrawCoef*>(w);
+  GWX_TRY(launched(launch_rfft_rows(y_data, E * D, N, Y, s), "rfft of the data"));
+  GWX_TRY(launched(launch_whiten_filter(psd, D, seg_len, fs, k_lo, N, W, s), "whiten filter"));
+  GWX_TRY(launched(launch_draw_setup(theta, S, k_lo, df, fs, N / 2 + 1, dp, gmst, coef, s), "sample set-up"));
+  return launched(launch_loglike_full(y_data, Y, W, coef, event_offsets, yy, E, D, N, k_lo, S, lnl, s),
+                  "log_likelihood");
+}
+
+int gwx_rfft(const float* x, int64_t R, int64_t N, float* X, void* stream) {
+  GWX_TRY(check_window(N));
+  if (R < 0 || R > 0x7fffffffLL) return fail(GWX_ESHAPE, "R=%lld", (long long)R);
+  if (R == 0) return GWX_OK;
+  if (!x || !X) return fail(GWX_EINVAL, "NULL array");
+  GWX_TRY(ensure_init());
+  return launched(launch_rfft_rows(x, R, N, reinterpret_cast<float2*>(X), as_stream(stream)), "rfft");
+}
+
+int gwx_irfft(const float* X, int64_t R, int64_t N, float* x, void* stream) {
+  GWX_TRY(check_window(N));
+  if (R < 0 || R > 0x7fffffffLL) return fail(GWX_ESHAPE, "R=%lld", (long long)R);
+  if (R == 0) return GWX_OK;
+  if (!x || !X) return fail(GWX_EINVAL, "NULL array");
+  GWX_TRY(ensure_init());
+  return launched(launch_irfft_rows(reinterpret_cast<const float2*>(X), R, N, x, as_stream(stream)), "irfft");
+}
+
+}  // extern "C"

@@ -1,0 +1,76 @@
+// gwx_internal.h -- structures and launcher declarations shared by the
+// libgwx translation units (not part of the public C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gwx.h"
+
+namespace gwx {
+
+// Detector table passed by value to kernels: tensor D (row-major) and vertex
+// position r [m] for each selected detector, in FP64.
+struct DetParams {
+  int D;
+  double tensor[GWX_MAX_DET][9];
+  double pos[GWX_MAX_DET][3];
+};
+
+// Per-draw waveform and projection coefficients (written by the set-up stage,
+// read per frequency bin).  Phase in turns (cycles):
+//   Psi(k)/2pi = c0 k^-5/3 + c2 k^-1 + c3 k^-2/3 + c4 k^-1/3 + d5 ln k
+//                + (c6 + d6 ln k) k^1/3 + c7 k^2/3 + cph
+// with c0, c2, c3, d5 as double-float pairs (hi, lo); amplitude of bin k is
+// amp * k^-7/6.  The detector-d strain of bin k (times the sample rate) is
+// g[d] * k^-7/6 * e^{-2 pi i (Psi(k)/2pi + k nu[d] 2^-64)}, with g[d] the complex
+// double-float constant fs amp (F+_d qp - i Fx_d qc_im) as (re hi, re lo, im hi, im lo).
+struct __align__(16) DrawCoef {
+  float2 c0, c2, c3, d5;
+  float c4, c6, d6, c7;
+  float cph, amp, qp, qc_im;        // amp = A(df) (strain/Hz); h_plus factor qp = (1 + cos^2 i)/2,
+                                    // h_cross factor -i qc_im with qc_im = cos i
+  int kcut, pad0, pad1, pad2;       // last non-zero bin (inclusive), may be < k_lo
+  float4 g[GWX_MAX_DET];            // fs amp (F+_d qp - i Fx_d qc_im), double-float
+  unsigned long long nu[GWX_MAX_DET];
+};
+
+// ---- launchers (return cudaGetLastError() of the launch) ----
+cudaError_t launch_sample_prior(const gwx_prior& p, uint64_t seed, uint32_t step, int64_t B, int64_t L,
+                                int64_t N, double* theta, int64_t* offsets, cudaStream_t s);
+cudaError_t launch_generate_waveforms(const double* theta, int64_t B, int k_lo, double df, int64_t F,
+                                      float2* hp, float2* hc, cudaStream_t s);
+cudaError_t launch_project(const float2* hp, const float2* hc, const double* theta, int64_t B,
+                           const DetParams& dp, double gmst, double df, int64_t F, float2* hdet,
+                           cudaStream_t s);
+cudaError_t launch_draw_setup(const double* theta, int64_t B, int k_lo, double df, double fs, int64_t F,
+                              const DetParams& dp, double gmst, DrawCoef* coef, cudaStream_t s);
+cudaError_t launch_colored_noise(uint64_t seed, uint32_t step, int D, int64_t L, double fs, double f_lo,
+                                 float* noise, void* ws, cudaStream_t s);
+size_t colored_noise_ws(int D, int64_t L);
+cudaError_t launch_welch(const float* x, int D, int64_t L, double fs, int64_t M, int64_t stride, double* psd,
+                         void* ws, cudaStream_t s);
+size_t welch_ws(int D, int64_t L, int64_t M, int64_t stride);
+cudaError_t launch_whiten_filter(const double* psd, int D, int64_t M, double fs, int k_lo, int64_t N, float* W,
+                                 cudaStream_t s);
+cudaError_t launch_whiten_rows(const float* d, const float* W, int64_t rows, int D, int64_t N, float* y,
+                               cudaStream_t s);
+cudaError_t launch_inject_rows(const float* noise, int D, int64_t L, const int64_t* offsets, const float2* hdet,
+                               int64_t B, int64_t N, double fs, float* d, cudaStream_t s);
+cudaError_t launch_rfft_rows(const float* x, int64_t R, int64_t N, float2* X, cudaStream_t s);
+cudaError_t launch_irfft_rows(const float2* X, int64_t R, int64_t N, float* x, cudaStream_t s);
+cudaError_t launch_simulate_fused(const DrawCoef* coef, const float* noise, int64_t L, const int64_t* offsets,
+                                  const float* W, int k_lo, int D, int64_t B, int64_t N, double fs, float* y,
+                                  cudaStream_t s);
+// yy: E doubles of scratch for the per-event sum of |Y|^2 over the band.
+cudaError_t launch_loglike_full(const float* ydata, const float2* Ydata, const float* W, const DrawCoef* coef,
+                                const int64_t* ev_off, double* yy, int64_t E, int D, int64_t N, int k_lo, int64_t S,
+                                double* lnl, cudaStream_t s);
+
+// per-translation-unit table set-up on the current device
+cudaError_t init_tables_random();
+cudaError_t init_tables_spectral();
+cudaError_t init_tables_waveform();
+cudaError_t init_tables_fused();
+
+}  // namespace gwx

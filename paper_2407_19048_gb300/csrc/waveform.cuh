@@ -1,0 +1,169 @@
+// waveform.cuh -- TaylorF2 per-draw set-up (FP64) and per-bin evaluation (FP32 +
+// double-float), shared by the waveform, fused-simulation and likelihood kernels.
+//
+// Model (Sec. 3.1; Buonanno et al. 2009 eq. 3.18 for the non-spinning phase,
+// 1.5PN aligned-spin spin-orbit term 4 beta):
+//   h(f) = A(f) e^{-i Psi(f)},  A(f) = sqrt(5/24) pi^{-2/3} Mc^{5/6} f^{-7/6} / D,
+//   Psi(f) = -phic - pi/4 + 3/(128 eta v^5) sum_j (a_j + l_j ln v) v^j,  v = (pi M f)^{1/3}
+// with the merger at the time origin.  On the grid f = k df, v = V k^{1/3} with
+// V = (pi M df)^{1/3}, so Psi/(2 pi) is a short sum of per-draw coefficients
+// times fixed powers of k (see DrawCoef).  The large terms (up to ~10^3 rad at
+// 20 Hz for the lightest systems) are double-float products reduced modulo one
+// turn before they are added, which keeps the phase error near 1e-6 rad while
+// using only FP32 arithmetic per bin.  The linear phase 2 pi f (tc + dt) of the
+// projection is exact: (tc + dt) df modulo one is held as a 64-bit fixed-point
+// fraction and multiplied by the integer k.
+#pragma once
+
+#include "common.cuh"
+
+namespace gwx {
+
+constexpr double MTSUN_S = 4.925490947641267e-6;
+constexpr double MPC_M = 3.085677581491367e22;
+constexpr double C_MS = 299792458.0;
+constexpr double EULER_GAMMA = 0.5772156649015329;
+constexpr double PI_D = 3.141592653589793238462643383279502884;
+
+__device__ __forceinline__ float2 split_df(double x) {
+  float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+
+__device__ __forceinline__ double th_at(const double* th, int64_t B, int64_t b, int p) { return th[(int64_t)p * B + b]; }
+
+// A(df) = sqrt(5/24) pi^{-2/3} Mc^{5/6} df^{-7/6} / D in FP64 (strain per Hz), so that
+// the amplitude of bin k is A(df) k^{-7/6}.
+__device__ inline double waveform_amp(const double* th, int64_t B, int64_t b, double df) {
+  const double m1 = th_at(th, B, b, GWX_M1), m2 = th_at(th, B, b, GWX_M2);
+  const double mt = m1 + m2;
+  const double M = mt * MTSUN_S;
+  const double eta = m1 * m2 / (mt * mt);
+  const double Mc = M * pow(eta, 0.6);
+  const double D = th_at(th, B, b, GWX_DIST) * MPC_M / C_MS;
+  return sqrt(5.0 / 24.0) * pow(PI_D, -2.0 / 3.0) * pow(Mc, 5.0 / 6.0) / D * pow(df, -7.0 / 6.0);
+}
+
+// Waveform part of the set-up: PN phase coefficients in turns, amplitude and cut-off.
+__device__ inline void draw_waveform_coef(const double* th, int64_t B, int64_t b, double df, int64_t F,
+                                          DrawCoef& c) {
+  const double m1 = th_at(th, B, b, GWX_M1), m2 = th_at(th, B, b, GWX_M2);
+  const double chi1 = th_at(th, B, b, GWX_CHI1), chi2 = th_at(th, B, b, GWX_CHI2);
+  const double phic = th_at(th, B, b, GWX_PHIC);
+  const double iota = th_at(th, B, b, GWX_THETAJN);
+  const double mt = m1 + m2;
+  const double M = mt * MTSUN_S;
+  const double eta = m1 * m2 / (mt * mt);
+  const double delta = (m1 - m2) / mt;
+  const double chis = 0.5 * (chi1 + chi2), chia = 0.5 * (chi1 - chi2);
+  const double pi = PI_D, pi2 = PI_D * PI_D;
+  const double a2 = 3715.0 / 756.0 + 55.0 * eta / 9.0;
+  const double a3 = -16.0 * pi + (113.0 / 3.0) * delta * chia + (113.0 / 3.0 - 76.0 * eta / 3.0) * chis;
+  const double a4 = 15293365.0 / 508032.0 + 27145.0 * eta / 504.0 + 3085.0 * eta * eta / 72.0;
+  const double a5 = pi * (38645.0 / 756.0 - 65.0 * eta / 9.0);
+  const double l5 = 3.0 * a5;
+  const double a6 = 11583231236531.0 / 4694215680.0 - 640.0 * pi2 / 3.0 - 6848.0 * EULER_GAMMA / 21.0 -
+                    6848.0 * log(4.0) / 21.0 + (-15737765635.0 / 3048192.0 + 2255.0 * pi2 / 12.0) * eta +
+                    76055.0 * eta * eta / 1728.0 - 127825.0 * eta * eta * eta / 1296.0;
+  const double l6 = -6848.0 / 21.0;
+  const double a7 = pi * (77096675.0 / 254016.0 + 378515.0 * eta / 1512.0 - 74045.0 * eta * eta / 756.0);
+  const double V = cbrt(pi * M * df);
+  const double lnV = log(V);
+  const double pref = 3.0 / (256.0 * pi * eta);   // 3/(128 eta) in turns
+  const double Vi = 1.0 / V;
+  const double Vi2 = Vi * Vi, Vi3 = Vi2 * Vi, Vi5 = Vi3 * Vi2;
+  c.c0 = split_df(pref * Vi5);
+  c.c2 = split_df(pref * Vi3 * a2);
+  c.c3 = split_df(pref * Vi2 * a3);
+  c.c4 = (float)(pref * Vi * a4);
+  c.d5 = split_df(pref * l5 / 3.0);
+  c.c6 = (float)(pref * V * (a6 + l6 * lnV));
+  c.d6 = (float)(pref * V * l6 / 3.0);
+  c.c7 = (float)(pref * V * V * a7);
+  double cph = -(phic + 0.25 * pi) / (2.0 * pi) + pref * (a5 + l5 * lnV);
+  cph -= rint(cph);
+  c.cph = (float)cph;
+  c.amp = (float)waveform_amp(th, B, b, df);
+  const double f_isco = 1.0 / (pow(6.0, 1.5) * pi * M);
+  double kc = floor(f_isco / df);
+  c.kcut = kc > (double)(F - 1) ? (int)(F - 1) : (int)kc;
+  const double ci = cos(iota);
+  c.qp = (float)(0.5 * (1.0 + ci * ci));
+  c.qc_im = (float)ci;
+  c.pad0 = c.pad1 = c.pad2 = 0;
+}
+
+// Projection part: scale * (F+ qp - i Fx qc) per detector as a complex double-float,
+// and the per-detector linear phase (tc + dt_d) df modulo one as a 2^-64 fixed point.
+__device__ inline void draw_detector_coef(const double* th, int64_t B, int64_t b, double df, const DetParams& dp,
+                                          double gmst, double qp, double qc, double scale, DrawCoef& c) {
+  const double tc = th_at(th, B, b, GWX_TC), psi = th_at(th, B, b, GWX_PSI);
+  const double ra = th_at(th, B, b, GWX_RA), dec = th_at(th, B, b, GWX_DEC);
+  double sd, cd, sp, cp, spsi, cpsi;
+  sincos(dec, &sd, &cd);
+  sincos(ra - gmst, &sp, &cp);
+  sincos(psi, &spsi, &cpsi);
+  const double n[3] = {cd * cp, cd * sp, sd};
+  const double eth[3] = {sd * cp, sd * sp, -cd};
+  const double eph[3] = {-sp, cp, 0.0};
+  double X[3], Y[3];
+  for (int i = 0; i < 3; ++i) {
+    X[i] = cpsi * eth[i] + spsi * eph[i];
+    Y[i] = spsi * eth[i] - cpsi * eph[i];
+  }
+  for (int d = 0; d < dp.D; ++d) {
+    const double* T = dp.tensor[d];
+    double DX[3], DY[3];
+    for (int i = 0; i < 3; ++i) {
+      DX[i] = T[3 * i] * X[0] + T[3 * i + 1] * X[1] + T[3 * i + 2] * X[2];
+      DY[i] = T[3 * i] * Y[0] + T[3 * i + 1] * Y[1] + T[3 * i + 2] * Y[2];
+    }
+    const double fp = X[0] * DX[0] + X[1] * DX[1] + X[2] * DX[2] - (Y[0] * DY[0] + Y[1] * DY[1] + Y[2] * DY[2]);
+    const double fc = X[0] * DY[0] + X[1] * DY[1] + X[2] * DY[2] + (Y[0] * DX[0] + Y[1] * DX[1] + Y[2] * DX[2]);
+    const double dt = -(dp.pos[d][0] * n[0] + dp.pos[d][1] * n[1] + dp.pos[d][2] * n[2]) / C_MS;
+    // scale (F+ qp + Fx (-i qc))
+    const float2 re = split_df(scale * fp * qp), im = split_df(-scale * fc * qc);
+    c.g[d] = make_float4(re.x, re.y, im.x, im.y);
+    double x = (tc + dt) * df;
+    x -= floor(x);
+    double fx = ldexp(x, 64);
+    c.nu[d] = fx >= 18446744073709551615.0 ? 0ull : (unsigned long long)fx;
+  }
+  for (int d = dp.D; d < GWX_MAX_DET; ++d) {
+    c.g[d] = make_float4(0.f, 0.f, 0.f, 0.f);
+    c.nu[d] = 0ull;
+  }
+}
+
+// Fractional turns of k * nu * 2^-64, in [-1/2, 1/2).
+__device__ __forceinline__ float lin_turns(unsigned long long nu, int k) {
+  unsigned long long p = nu * (unsigned long long)(unsigned)k;
+  return (float)(int)(p >> 32) * 0x1p-32f;
+}
+
+// Phase Psi(k)/(2 pi) reduced to [-1/2, 1/2] and the factor k^{-7/6}, for 1 <= k <= KMAX.
+__device__ __forceinline__ float waveform_turns(const DrawCoef& c, int k, float& k76) {
+  const float4 p = __ldg(&g_kp53[k]);
+  const float4 q = __ldg(&g_kq[k]);
+  const float kf = (float)k;
+  const float rh = __frcp_rn(kf);
+  const float rl = fmaf(-rh, kf, 1.0f) * rh;
+  const float t = df_frac(df_mul(c.c0.x, c.c0.y, p.x, p.y)) + df_frac(df_mul(c.c2.x, c.c2.y, rh, rl)) +
+                  df_frac(df_mul(c.c3.x, c.c3.y, p.z, p.w)) + df_frac(df_mul(c.d5.x, c.d5.y, q.y, q.z));
+  const float k13 = kf * p.z;   // k^{1/3}
+  const float k23 = kf * q.x;   // k^{2/3}
+  const float small = fmaf(c.c4, q.x, fmaf(fmaf(c.d6, q.y, c.c6), k13, fmaf(c.c7, k23, c.cph)));
+  float tt = t + small;
+  tt -= rintf(tt);
+  k76 = p.x * sqrtf(kf);   // k^{-5/3} k^{1/2}: two correctly rounded operations
+  return tt;
+}
+
+// e^{-2 pi i turns}
+__device__ __forceinline__ float2 expm2pi(float turns) {
+  float s, c;
+  sincospif(2.0f * turns, &s, &c);
+  return make_float2(c, -s);
+}
+
+}  // namespace gwx

@@ -1,0 +1,84 @@
+"""Host-side checks of the C ABI (CPU only): the library builds, loads, exports
+every entry point the header declares, and its pure-host functions agree with
+the oracle.  No call here launches device work."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gwx.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2407_19048_gb300 import build, _lib
+    build.build()
+    return _lib.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gwx_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("gwx_generate_waveforms", "gwx_project", "gwx_inject", "gwx_welch_psd", "gwx_whiten",
+                     "gwx_log_likelihood", "gwx_sample_prior", "gwx_colored_noise", "gwx_simulate_batch"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2407_19048_gb300 import _lib
+    out = subprocess.run(["nm", "-D", "--defined-only", _lib.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (gwx_\w+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    assert set(_lib.SIGNATURES) <= exported
+
+
+def test_version_and_status_strings(lib):
+    assert lib.gwx_version() == 100
+    assert lib.gwx_status_string(0) == b"ok"
+    assert lib.gwx_status_string(-6) == b"unsupported"
+
+
+def test_detector_geometry_matches_oracle(lib):
+    import paper_2407_19048_gb300 as gwx
+    from oracle import detector
+    for name in ("H1", "L1", "V1"):
+        T, r = gwx.detector_geometry(name)
+        D_ref, r_ref = detector.geometry(name)
+        np.testing.assert_allclose(np.array(T), D_ref, atol=1e-15)
+        np.testing.assert_allclose(np.array(r), r_ref, rtol=1e-15)
+
+
+def test_workspace_sizes(lib):
+    import paper_2407_19048_gb300 as gwx
+    assert gwx.workspace_bytes("whiten", 3, 8192) == ((3 * 4097 * 4 + 255) // 256) * 256
+    K = (131072 - 4096) // 2048 + 1
+    assert gwx.workspace_bytes("welch_psd", 3, 131072, 4096, 2048) >= 3 * K * 2049 * 8
+    assert gwx.workspace_bytes("colored_noise", 3, 131072) >= 2 * 3 * 65536 * 8
+    assert gwx.workspace_bytes("simulate_batch", 3, 2048, 8192) > 2048 * 144
+    assert gwx.workspace_bytes("log_likelihood", 4, 3, 8192, 100) > 0
+
+
+def test_validation_fails_before_any_launch(lib):
+    """Bad sizes are rejected on the host, with a message, without touching a device."""
+    import paper_2407_19048_gb300 as gwx
+    from paper_2407_19048_gb300 import _lib
+    st = lib.gwx_generate_waveforms(1, None, 4, 20.0, 0.25, 4097, None, None, None)
+    assert st == -6 and b"IMRPhenomD" in lib.gwx_last_error()
+    st = lib.gwx_inject(None, 2, 1000, None, None, 4, 1000, 1024.0, None, None)   # N not a power of two
+    assert st == -2 and b"power of two" in lib.gwx_last_error()
+    st = lib.gwx_welch_psd(None, 9, 4096, 1024.0, 1024, 512, None, None, 0, None)
+    assert st == -2
+    p = _lib.GwxPrior(*([0.0] * 12))
+    st = lib.gwx_sample_prior(p, 1, 0, 16, 100, 200, None, None, None)         # L < N
+    assert st == -2
+    with pytest.raises(KeyError):
+        gwx.detector_geometry("K1")

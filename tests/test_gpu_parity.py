@@ -1,0 +1,359 @@
+"""Parity of every libgwx entry point with the FP64 oracle (needs a GPU).
+
+Each test feeds the same seeded inputs to the CUDA path (through the C ABI via
+the Python binding) and to the oracle, and compares element by element.
+Tolerances (from the precision targets of the method):
+  * waveforms: mismatch <= 1e-6 (analytic PSD, not maximised) and per-bin error
+    <= 2e-5 of the draw's peak amplitude;
+  * whitened strain: max-abs error <= 1e-4 of the oracle RMS;
+  * log-likelihood: |Delta ln L| <= 1e-3;
+  * Welch: relative error <= 1e-4 per bin; projection and injection: <= 2e-5
+    of the peak; prior draws: offsets bit-exact, doubles within 4 ulp.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import detector, likelihood, noise, pipeline, prior, spectral, taylorf2
+from oracle import constants as C
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gwx():
+    import paper_2407_19048_gb300 as m
+    from paper_2407_19048_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "the gpu tests need a CUDA device"
+    m.init()
+    return m
+
+
+def cuda(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rms(x):
+    return float(np.sqrt(np.mean(np.abs(x) ** 2)))
+
+
+# ------------------------------------------------------------------ FFT
+@pytest.mark.parametrize("N,R", [(256, 3), (2048, 5), (8192, 3), (16384, 2)])
+def test_rfft_irfft_match_numpy(gwx, N, R):
+    x = workloads.random_strain(N + R, (R, N), 1.0)
+    X = host(gwx.rfft(cuda(x, torch.float32)))
+    ref = np.fft.rfft(x.astype(np.float32).astype(np.float64), axis=-1)
+    assert np.abs(X - ref).max() <= 2e-6 * rms(ref) * math.log2(N)
+    back = host(gwx.irfft(cuda(ref.astype(np.complex64)), N))
+    ref_back = np.fft.irfft(ref.astype(np.complex64).astype(np.complex128), n=N, axis=-1)
+    assert np.abs(back - ref_back).max() <= 2e-6 * rms(ref_back) * math.log2(N)
+
+
+def test_rfft_matches_brute_force_dft(gwx):
+    N = 256
+    x = workloads.random_strain(3, N, 1.0).astype(np.float32)
+    k = np.arange(N)
+    X_brute = (np.exp(-2j * math.pi * np.outer(k, k) / N) @ x.astype(np.float64))[: N // 2 + 1]
+    X = host(gwx.rfft(cuda(x[None])))[0]
+    assert np.abs(X - X_brute).max() < 1e-5 * rms(X_brute)
+
+
+# ------------------------------------------------------------------ A1 prior
+@pytest.mark.parametrize("name,step", [("small", 0), ("hl3", 7)])
+def test_sample_prior_matches_oracle(gwx, name, step):
+    wl = workloads.workload(name)
+    th_ref, off_ref = prior.sample_prior(wl["prior"], wl["param_seed"], step, wl["B"], wl["L"], wl["N"])
+    th, off = gwx.sample_prior(wl["prior"], wl["param_seed"], step, wl["B"], wl["L"], wl["N"])
+    np.testing.assert_array_equal(host(off), off_ref)
+    np.testing.assert_allclose(host(th), th_ref, rtol=4 * 2.0 ** -52, atol=4 * 2.0 ** -52)
+
+
+def test_sample_prior_edge_sizes(gwx):
+    wl = workloads.workload("small")
+    th, off = gwx.sample_prior(wl["prior"], 3, 1, 0, wl["L"], wl["N"])
+    assert th.shape == (11, 0) and off.shape == (0,)
+    th, off = gwx.sample_prior(wl["prior"], 3, 1, 1, wl["N"], wl["N"])     # L == N: offset 0
+    assert int(host(off)[0]) == 0
+
+
+# ------------------------------------------------------------------ A2 waveforms
+def _mismatch_per_draw(h_gpu, h_ref, df, k_lo):
+    h_gpu = h_gpu.astype(np.complex128)      # |h|^2 ~ 1e-46 would underflow in float32
+    F = h_ref.shape[-1]
+    S = noise.aligo_psd(np.maximum(np.arange(F) * df, 1.0))
+    out = []
+    for b in range(h_ref.shape[0]):
+        if np.abs(h_ref[b]).max() == 0:
+            assert np.abs(h_gpu[b]).max() == 0
+            out.append(0.0)
+            continue
+        out.append(float(likelihood.mismatch(h_gpu[b], h_ref[b], S, df, k_lo, F)))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("name", ["small", "hl3"])
+def test_generate_waveforms_matches_oracle(gwx, name):
+    wl = workloads.workload(name)
+    N, fs = wl["N"], wl["fs"]
+    df, F = fs / N, N // 2 + 1
+    th = workloads.random_theta(21, wl["B"], wl["prior"])
+    hp_ref, hc_ref = taylorf2.generate_waveforms(th, wl["f_lo"], df, F)
+    hp, hc = gwx.generate_waveforms(cuda(th), wl["f_lo"], df, F)
+    hp, hc = host(hp), host(hc)
+    k_lo = math.ceil(wl["f_lo"] / df)
+    for got, ref in ((hp, hp_ref), (hc, hc_ref)):
+        peak = np.abs(ref).max(axis=1, keepdims=True)
+        np.testing.assert_array_equal(got == 0, ref == 0)
+        assert np.max(np.abs(got - ref) / np.where(peak > 0, peak, 1)) <= 2e-5
+    mm = _mismatch_per_draw(hp, hp_ref, df, k_lo)
+    assert mm.max() <= 1e-6, mm.max()
+
+
+def test_generate_waveforms_lightest_system_phase(gwx):
+    """5+5 Msun from 20 Hz on 0.25 Hz bins: ~1400 rad of PN phase at the band edge."""
+    th = np.zeros((11, 2))
+    th[C.M1], th[C.M2], th[C.DIST] = 5.0, 5.0, 100.0
+    th[C.CHI1], th[C.CHI2] = 0.99, -0.99
+    th[:, 1] = th[:, 0]
+    th[C.CHI1, 1], th[C.CHI2, 1] = 0.99, 0.99
+    hp_ref, _ = taylorf2.generate_waveforms(th, 20.0, 0.25, 4097)
+    hp, _ = gwx.generate_waveforms(cuda(th), 20.0, 0.25, 4097)
+    hp = host(hp)
+    on = hp_ref != 0
+    dphi = np.angle(hp[on] / hp_ref[on])
+    assert np.abs(dphi).max() < 2e-5
+    assert _mismatch_per_draw(hp, hp_ref, 0.25, 80).max() <= 1e-6
+
+
+def test_generate_waveforms_rejects_phenomd_and_bad_sizes(gwx):
+    th = cuda(np.ones((11, 2)))
+    with pytest.raises(gwx.GwxError) as e:
+        gwx.generate_waveforms(th, 20.0, 0.25, 4097, approximant=gwx.IMRPHENOMD)
+    assert e.value.status == -6
+    with pytest.raises(gwx.GwxError):
+        gwx.generate_waveforms(th, 20.0, 0.25, 40000)
+    with pytest.raises(gwx.GwxError):
+        gwx.generate_waveforms(th, -1.0, 0.25, 4097)
+
+
+# ------------------------------------------------------------------ A3 projection
+@pytest.mark.parametrize("name", ["small", "hl3"])
+def test_project_matches_oracle(gwx, name):
+    wl = workloads.workload(name)
+    N, fs = wl["N"], wl["fs"]
+    df, F = fs / N, N // 2 + 1
+    B = min(wl["B"], 256)
+    th = workloads.random_theta(22, B, wl["prior"])
+    hp_ref, hc_ref = taylorf2.generate_waveforms(th, wl["f_lo"], df, F)
+    hp32, hc32 = hp_ref.astype(np.complex64), hc_ref.astype(np.complex64)
+    ref = detector.project(hp32.astype(np.complex128), hc32.astype(np.complex128), th, wl["dets"], 0.3, df)
+    got = host(gwx.project(cuda(hp32), cuda(hc32), cuda(th), wl["dets"], 0.3, df))
+    peak = np.abs(ref).max(axis=-1, keepdims=True)
+    assert np.max(np.abs(got - ref) / np.where(peak > 0, peak, 1)) <= 2e-5
+
+
+# ------------------------------------------------------------------ A4 noise
+@pytest.mark.parametrize("name", ["small", "hl3"])
+def test_colored_noise_matches_oracle(gwx, name):
+    wl = workloads.workload(name)
+    D = len(wl["dets"])
+    ref = noise.colored_noise(wl["noise_seed"], 3, D, wl["L"], wl["fs"], wl["f_lo"])
+    got = host(gwx.colored_noise(wl["noise_seed"], 3, D, wl["L"], wl["fs"], wl["f_lo"]))
+    r = rms(ref)
+    assert np.abs(got - ref).max() <= 1e-4 * r
+    assert rms(got - ref) <= 1e-5 * r
+
+
+# ------------------------------------------------------------------ A5 Welch
+@pytest.mark.parametrize("name", ["small", "hl3"])
+def test_welch_matches_oracle(gwx, name):
+    wl = workloads.workload(name)
+    D = len(wl["dets"])
+    x = noise.colored_noise(wl["noise_seed"], 4, D, wl["L"], wl["fs"], wl["f_lo"]).astype(np.float32)
+    ref = spectral.welch_psd(x.astype(np.float64), wl["fs"], wl["seg_len"], wl["seg_stride"])
+    got = host(gwx.welch_psd(cuda(x), wl["fs"], wl["seg_len"], wl["seg_stride"]))
+    assert np.max(np.abs(got / ref - 1)) <= 1e-4
+
+
+def test_welch_ragged_segments(gwx):
+    x = workloads.random_strain(5, (2, 5000), 1e-21).astype(np.float32)
+    ref = spectral.welch_psd(x.astype(np.float64), 1024.0, 512, 300)
+    got = host(gwx.welch_psd(cuda(x), 1024.0, 512, 300))
+    assert np.max(np.abs(got / ref - 1)) <= 1e-4
+
+
+# ------------------------------------------------------------------ A6 injection
+@pytest.mark.parametrize("name", ["small", "hl3"])
+def test_inject_matches_oracle(gwx, name):
+    wl = workloads.workload(name)
+    N, fs, L = wl["N"], wl["fs"], wl["L"]
+    df, F = fs / N, N // 2 + 1
+    B = 37
+    th = workloads.random_theta(23, B, wl["prior"])
+    hp, hc = taylorf2.generate_waveforms(th, wl["f_lo"], df, F)
+    h = detector.project(hp, hc, th, wl["dets"], 0.0, df).astype(np.complex64)
+    bg = noise.colored_noise(wl["noise_seed"], 0, len(wl["dets"]), L, fs, wl["f_lo"]).astype(np.float32)
+    off = workloads.random_offsets(24, B, L, N)
+    off[0], off[-1] = 0, L - N
+    ref = spectral.inject(bg.astype(np.float64), off, h.astype(np.complex128), N, fs)
+    got = host(gwx.inject(cuda(bg), cuda(off), cuda(h), N, fs))
+    assert np.abs(got - ref).max() <= 2e-5 * np.abs(ref).max()
+
+
+# ------------------------------------------------------------------ A7 whitening
+@pytest.mark.parametrize("name", ["small", "hl3"])
+def test_whiten_matches_oracle(gwx, name):
+    wl = workloads.workload(name)
+    N, fs, L = wl["N"], wl["fs"], wl["L"]
+    D = len(wl["dets"])
+    bg = noise.colored_noise(wl["noise_seed"], 0, D, L, fs, wl["f_lo"])
+    psd = spectral.welch_psd(bg, fs, wl["seg_len"], wl["seg_stride"])
+    B = 29
+    off = workloads.random_offsets(25, B, L, N)
+    d = spectral.crop(bg, off, N).astype(np.float32)
+    ref = spectral.whiten(d.astype(np.float64), psd, wl["seg_len"], fs, wl["f_lo"])
+    got = host(gwx.whiten(cuda(d), cuda(psd), wl["seg_len"], fs, wl["f_lo"]))
+    assert np.abs(got - ref).max() <= 1e-4 * rms(ref)
+
+
+def test_whiten_in_place(gwx):
+    wl = workloads.workload("small")
+    d = workloads.random_strain(26, (3, 2, wl["N"]), 1e-21).astype(np.float32)
+    psd = np.full((2, wl["seg_len"] // 2 + 1), 1e-42)
+    t = cuda(d)
+    ref = host(gwx.whiten(t, cuda(psd), wl["seg_len"], wl["fs"], wl["f_lo"]))
+    got = host(gwx.whiten(t, cuda(psd), wl["seg_len"], wl["fs"], wl["f_lo"], out=t))
+    np.testing.assert_array_equal(got, ref)
+
+
+# ------------------------------------------------------------------ fused pass
+def _gpu_background(gwx, wl, step):
+    D = len(wl["dets"])
+    n = gwx.colored_noise(wl["noise_seed"], step, D, wl["L"], wl["fs"], wl["f_lo"])
+    S = gwx.welch_psd(n, wl["fs"], wl["seg_len"], wl["seg_stride"])
+    return n, S
+
+
+def test_simulate_batch_small_matches_oracle(gwx):
+    wl = workloads.workload("small")
+    step = 0
+    n, S = _gpu_background(gwx, wl, step)
+    y, th, off = gwx.simulate_batch(wl["prior"], wl["param_seed"], step, n, S, wl["seg_len"], wl["fs"], wl["f_lo"],
+                                    wl["dets"], 0.0, wl["B"], wl["N"])
+    ref = pipeline.simulate_batch(wl, step)
+    np.testing.assert_array_equal(host(off), ref["offsets"])
+    np.testing.assert_allclose(host(th), ref["theta"], rtol=4 * 2.0 ** -52, atol=4 * 2.0 ** -52)
+    yr = ref["y"]
+    assert np.abs(host(y) - yr).max() <= 1e-4 * rms(yr)
+
+
+def test_simulate_batch_full_size_sampled(gwx):
+    """Three-detector 4 s windows, 2048 draws, in the launch configuration the
+    benchmark times; the oracle checks a sample of draws including the first
+    and the last."""
+    wl = workloads.workload("hl3")
+    step = 5
+    n, S = _gpu_background(gwx, wl, step)
+    y, th, off = gwx.simulate_batch(wl["prior"], wl["param_seed"], step, n, S, wl["seg_len"], wl["fs"], wl["f_lo"],
+                                    wl["dets"], 0.0, wl["B"], wl["N"])
+    draws = np.unique(np.concatenate([[0, wl["B"] - 1], np.random.default_rng(27).integers(0, wl["B"], 14)]))
+    ref = pipeline.simulate_batch(wl, step, draws=draws)
+    np.testing.assert_array_equal(host(off), ref["offsets"])
+    yr = ref["y"]
+    assert np.abs(host(y)[draws] - yr).max() <= 1e-4 * rms(yr)
+
+
+def test_simulate_equals_whiten_of_inject(gwx):
+    """The fused pass equals the unfused inject -> whiten chain on the same inputs."""
+    wl = workloads.workload("small")
+    n, S = _gpu_background(gwx, wl, 2)
+    y, th, off = gwx.simulate_batch(wl["prior"], 9, 2, n, S, wl["seg_len"], wl["fs"], wl["f_lo"], wl["dets"], 0.0,
+                                    wl["B"], wl["N"])
+    df, F = wl["fs"] / wl["N"], wl["N"] // 2 + 1
+    hp, hc = gwx.generate_waveforms(th, wl["f_lo"], df, F)
+    h = gwx.project(hp, hc, th, wl["dets"], 0.0, df)
+    d = gwx.inject(n, off, h, wl["N"], wl["fs"])
+    y2 = gwx.whiten(d, S, wl["seg_len"], wl["fs"], wl["f_lo"])
+    a, b = host(y), host(y2)
+    assert np.abs(a - b).max() <= 1e-4 * rms(b)
+
+
+@pytest.mark.parametrize("B", [0, 1, 3, 1000])
+def test_simulate_batch_ragged_sizes(gwx, B):
+    wl = workloads.workload("small")
+    n, S = _gpu_background(gwx, wl, 1)
+    y, th, off = gwx.simulate_batch(wl["prior"], 4, 1, n, S, wl["seg_len"], wl["fs"], wl["f_lo"], wl["dets"], 0.0,
+                                    B, wl["N"])
+    if B == 0:
+        return
+    draws = np.unique([0, B - 1, B // 2])
+    ref = pipeline.simulate_batch(dict(wl, B=B, param_seed=4), 1, draws=draws)
+    assert np.abs(host(y)[draws] - ref["y"]).max() <= 1e-4 * rms(ref["y"])
+
+
+def test_simulate_batch_longest_window(gwx):
+    """8 s windows at 2048 Hz (N = 16384, the largest supported) with three detectors."""
+    wl = workloads.workload("sweep", B=24)
+    n, S = _gpu_background(gwx, wl, 0)
+    y, th, off = gwx.simulate_batch(wl["prior"], wl["param_seed"], 0, n, S, wl["seg_len"], wl["fs"], wl["f_lo"],
+                                    wl["dets"], 0.0, wl["B"], wl["N"])
+    draws = np.array([0, 11, 23])
+    ref = pipeline.simulate_batch(wl, 0, draws=draws)
+    assert np.abs(host(y)[draws] - ref["y"]).max() <= 1e-4 * rms(ref["y"])
+
+
+# ------------------------------------------------------------------ A8 log-likelihood
+def _events(wl, E, seed):
+    N, fs = wl["N"], wl["fs"]
+    df = fs / N
+    D = len(wl["dets"])
+    th = workloads.random_theta(seed, E, wl["prior"])
+    hp, hc = taylorf2.generate_waveforms(th, wl["f_lo"], df, N // 2 + 1)
+    h = detector.project(hp, hc, th, wl["dets"], 0.0, df)
+    bg = noise.colored_noise(seed, 0, D, wl["L"], fs, wl["f_lo"])
+    psd = spectral.welch_psd(bg, fs, wl["seg_len"], wl["seg_stride"])
+    off = workloads.random_offsets(seed, E, wl["L"], N)
+    d = spectral.inject(bg, off, h, N, fs)
+    y = spectral.whiten(d, psd, wl["seg_len"], fs, wl["f_lo"]).astype(np.float32)
+    return th, y, psd
+
+
+@pytest.mark.parametrize("name", ["small", "hl3"])
+def test_log_likelihood_matches_oracle(gwx, name):
+    wl = workloads.workload(name)
+    E = 6
+    th_true, y, psd = _events(wl, E, 31)
+    counts = workloads.ragged_counts(32, E, 3, 40, zeros=1)
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    S = int(offs[-1])
+    samples = workloads.random_theta(33, S, wl["prior"])
+    for e in range(1, E):            # the first sample of every non-empty event is the truth
+        samples[:, offs[e]] = th_true[:, e]
+    ref = likelihood.log_likelihood(y.astype(np.float64), psd, wl["seg_len"], wl["fs"], wl["f_lo"], samples, offs,
+                                    wl["dets"])
+    got = host(gwx.log_likelihood(cuda(y), cuda(psd), wl["seg_len"], wl["fs"], wl["f_lo"], wl["dets"], 0.0,
+                                  cuda(samples), cuda(offs)))
+    assert np.abs(got - ref).max() <= 1e-3, np.abs(got - ref).max()
+
+
+def test_log_likelihood_empty_and_errors(gwx):
+    wl = workloads.workload("small")
+    th_true, y, psd = _events(wl, 2, 34)
+    out = gwx.log_likelihood(cuda(y), cuda(psd), wl["seg_len"], wl["fs"], wl["f_lo"], wl["dets"], 0.0,
+                             cuda(np.zeros((11, 0))), cuda(np.array([0, 0, 0])))
+    assert out.shape == (0,)
+    with pytest.raises(gwx.GwxError):
+        gwx.log_likelihood(cuda(y), cuda(psd), wl["seg_len"], wl["fs"], wl["f_lo"], wl["dets"], 0.0,
+                           cuda(th_true), cuda(np.array([0, 1, 2])), approximant=gwx.IMRPHENOMD)
