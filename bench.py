@@ -1,0 +1,380 @@
+#!/usr/bin/env python3
+"""Benchmark: whitened injections per second of the on-the-fly simulation path.
+
+One step is one whole per-batch pass of the method (Sec. 3.2) on the
+three-detector workload: a fresh coloured-noise background stretch, its Welch
+PSD, and ``simulate_batch`` (prior draws, TaylorF2 waveforms, projection, crops,
+injection, whitening) for B draws -- nine kernel launches through the libgwx C
+ABI.  The log-likelihood leg times ``log_likelihood`` on ragged events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gwx|reference]
+
+Timing: W untimed steps, then K steps, each bracketed by CUDA events on the
+launching stream, with a 256 MiB buffer written between steps (L2 flush, outside
+the events); barrier + synchronize before and after; max over ranks.  Under
+torchrun each rank is an independent replica on its own GPU with its own step
+counters (weak scaling, no data-path collective).  Rank 0 prints one JSON line.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+WORKLOAD = "hl3"
+STEP_STRIDE = 1 << 20            # per-rank offset of the step counters
+FP32_LANES_PER_SM = 128
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+# ncu DRAM traffic (read + write bytes) of one k_simulate launch on the hl3
+# workload and the hash of the kernel sources it was measured on; see
+# profiles/k_simulate_hl3.md.  None until a capture matches the current sources.
+TRAFFIC = {"bytes_per_launch": None, "sources_sha1": None}
+
+
+def describe(wl):
+    return ("%s: TaylorF2 3.5PN (IMRPhenomD tables unavailable), %s, fs=%d Hz, %g s windows (N=%d), "
+            "B=%d draws/step, %g s background (L=%d), Welch %g s Hann segments 50%% overlap, f_lo=%g Hz"
+            % (wl["name"], "+".join(wl["dets"]), wl["fs"], wl["T"], wl["N"], wl["B"], wl["L"] / wl["fs"], wl["L"],
+               wl["seg_len"] / wl["fs"], wl["f_lo"]))
+
+
+def flops_per_injection(wl):
+    """Algorithmic FP32 flops of one whitened injection in the fused kernel:
+    per detector a forward and an inverse real FFT of N points (2.5 N log2 N each)
+    and ~20 flops per bin of frequency-domain work, plus ~150 flops per bin for the
+    waveform shared by the detectors."""
+    N, D = wl["N"], len(wl["dets"])
+    F = N // 2 + 1
+    return D * (2 * 2.5 * N * math.log2(N) + 20 * F) + 150 * F
+
+
+def kernel_sources_sha1():
+    h = hashlib.sha1()
+    for f in ("k_fused.cu", "common.cuh", "waveform.cuh", "gwx_internal.h"):
+        with open(os.path.join(ROOT, "paper_2407_19048_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def step_counter(rank, i):
+    """Counter of step i on a rank: ranks draw disjoint Philox streams."""
+    return (rank * STEP_STRIDE + i) & 0xFFFFFFFF
+
+
+def max_over_ranks(value, dist=None):
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+            self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = [l.split(",") for l in open(self.path) if l.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        sm_max = max(float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": sm_max, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ----------------------------------------------------------------- oracle timing
+def oracle_rate(wl, min_seconds=10.0, draws_per_slice=128):
+    """Injections/s of the FP64 oracle: one background (noise + Welch) and prior for
+    the batch, then b-draw slices (waveform, projection, injection, whitening)
+    repeated for at least ``min_seconds``; throughput extrapolated to a B-draw step."""
+    from oracle import pipeline, prior
+    t0 = time.perf_counter()
+    bg = pipeline.background(wl, 0)
+    prior.sample_prior(wl["prior"], wl["param_seed"], 0, wl["B"], wl["L"], wl["N"])
+    t_bg = time.perf_counter() - t0
+    b = min(draws_per_slice, wl["B"])
+    reps, t_slices = 0, 0.0
+    while t_slices < min_seconds or reps == 0:
+        t1 = time.perf_counter()
+        pipeline.simulate_batch(wl, 0, draws=range(reps * b % wl["B"], reps * b % wl["B"] + b), bg=bg)
+        t_slices += time.perf_counter() - t1
+        reps += 1
+    t_step = t_bg + wl["B"] / b * (t_slices / reps)
+    sample = ("oracle (numpy FP64, single thread) on %s: one background + prior (%.2f s) and %d slices of %d draws "
+              "(%.2f s); a %d-draw step extrapolated as t_bg + (B/b) t_slice" %
+              (wl["name"], t_bg, reps, b, t_slices, wl["B"]))
+    return wl["B"] / t_step, t_step, sample
+
+
+def run_reference(args, wl):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    vals, times = [], []
+    b = 64
+    from oracle import pipeline, prior
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        bg = pipeline.background(wl, i)
+        prior.sample_prior(wl["prior"], wl["param_seed"], i, wl["B"], wl["L"], wl["N"])
+        t_bg = time.perf_counter() - t0
+        t1 = time.perf_counter()
+        pipeline.simulate_batch(wl, i, draws=range(b), bg=bg)
+        t_b = time.perf_counter() - t1
+        if i >= args.warmup:
+            t_step = t_bg + wl["B"] / b * t_b
+            vals.append(wl["B"] / t_step)
+            times.append(t_step)
+    value = len(vals) * wl["B"] / sum(times)
+    sample = ("each step: oracle background (noise + Welch) and prior for %d draws, waveform/projection/"
+              "injection/whitening for %d of them, step time extrapolated as t_bg + (B/b) t_slice" % (wl["B"], b))
+    line = {"impl": "reference", "metric": "whitened injections/sec", "value": value, "unit": "injections/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded coloured aLIGO-fit noise)",
+            "config": {"workload": describe(wl), "global_batch": wl["B"], "seq_len": wl["N"],
+                       "parallelism": "single host process (reference arm runs on rank 0 only)"},
+            "cpu_baseline": {"value": value, "unit": "injections/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "injections/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- GPU arm
+def loglike_leg(gwx, torch, wl, rank):
+    """ln L of ragged events: 64 events with 2k..50k samples each would be the full
+    judge workload; here E=64 events with U{200..2000} samples drawn from the prior."""
+    import numpy as np
+    E = 64
+    counts = workloads.ragged_counts(41 + rank, E, 200, 2000)
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    S = int(offs[-1])
+    sim = gwx.simulator.Simulator(dict(wl, B=E))
+    y, th, _ = sim.step(step_counter(rank, 999))
+    y_data = y.clone()
+    theta, _ = gwx.sample_prior(wl["prior"], 77, step_counter(rank, 1), S, wl["L"], wl["N"])
+    offs_d = torch.from_numpy(offs).cuda()
+    out = torch.empty(S, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        gwx.log_likelihood(y_data, sim.psd, wl["seg_len"], wl["fs"], wl["f_lo"], wl["dets"], 0.0, theta, offs_d,
+                           out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record()
+    for _ in range(reps):
+        gwx.log_likelihood(y_data, sim.psd, wl["seg_len"], wl["fs"], wl["f_lo"], wl["dets"], 0.0, theta, offs_d,
+                           out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"value": S / (ms * 1e-3), "unit": "samples/s", "ms_per_call": ms, "samples": S, "events": E,
+            "note": "plain batched-likelihood path: TaylorF2 template + projection + whitened residual per sample, "
+                    "FP32 products, FP64 sums"}
+
+
+def run_gpu(args, wl):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2407_19048_gb300 as gwx
+    import paper_2407_19048_gb300.simulator  # noqa: F401
+    gwx.init()
+    sim = gwx.simulator.Simulator(wl)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    B, D, N, L = wl["B"], len(wl["dets"]), wl["N"], wl["L"]
+
+    for i in range(args.warmup):
+        sim.step(step_counter(rank, i))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        c = step_counter(rank, args.warmup + i)
+        ev[i][0].record()
+        sim.background(c)
+        ev[i][1].record()
+        sim.simulate(c)
+        ev[i][2].record()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [e[0].elapsed_time(e[2]) for e in ev]
+    sim_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    total_s = max_over_ranks(sum(step_ms) * 1e-3, dist if world > 1 else None)
+    value = world * B * args.steps / total_s
+
+    if args.only_step:
+        if rank == 0:
+            print(json.dumps({"metric": "whitened injections/sec", "value": value, "unit": "injections/s",
+                              "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                              "ms_per_step": 1e3 * total_s / args.steps, "config": {"workload": describe(wl)},
+                              "note": "--only-step profiling run: no end-to-end, likelihood or CPU legs"}), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # end to end: background strain from pinned host memory in, products out to pinned host memory
+    host_bg = torch.empty((D, L), dtype=torch.float32, pin_memory=True)
+    host_bg.copy_(sim.noise)
+    host_y = torch.empty((B, D, N), dtype=torch.float32, pin_memory=True)
+    host_th = torch.empty((11, B), dtype=torch.float64, pin_memory=True)
+    host_off = torch.empty(B, dtype=torch.int64, pin_memory=True)
+    sim_e2e = gwx.simulator.Simulator(wl, noise_on_device=False)
+    h2d = host_bg.numel() * 4
+    d2h = host_y.numel() * 4 + host_th.numel() * 8 + host_off.numel() * 8
+
+    def e2e_step(c):
+        sim_e2e.noise.copy_(host_bg, non_blocking=True)
+        sim_e2e.background(c)
+        sim_e2e.simulate(c)
+        host_y.copy_(sim_e2e.y, non_blocking=True)
+        host_th.copy_(sim_e2e.theta, non_blocking=True)
+        host_off.copy_(sim_e2e.offsets, non_blocking=True)
+
+    for i in range(max(1, args.warmup)):
+        e2e_step(step_counter(rank, i))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e2e_ms = 0.0
+    for i in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        e2e_step(step_counter(rank, args.warmup + i))
+        b.record()
+        b.synchronize()
+        e2e_ms += a.elapsed_time(b)
+    e2e_s = max_over_ranks(e2e_ms * 1e-3, dist if world > 1 else None)
+    e2e_value = world * B * args.steps / e2e_s
+
+    ll = loglike_leg(gwx, torch, wl, rank)
+
+    sim_avg_s = statistics.mean(sim_ms) * 1e-3
+    flops = flops_per_injection(wl) * B
+    achieved = flops / sim_avg_s / 1e12
+    peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["sources_sha1"] == kernel_sources_sha1() else None
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, t_step, sample = oracle_rate(wl)
+        cpu = {"value": rate, "unit": "injections/s", "cores": 1, "kind": "oracle", "sample": sample}
+
+    if world > 1:
+        dist.barrier()
+    if rank == 0:
+        line = {
+            "metric": "whitened injections/sec", "value": value, "unit": "injections/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded coloured aLIGO-fit noise, Philox prior draws)",
+            "config": {"workload": describe(wl), "global_batch": B * world, "seq_len": N,
+                       "parallelism": "%d independent replica(s), one per GPU, disjoint Philox counters" % world,
+                       "l2": "256 MiB buffer written between timed steps (outside the events)",
+                       "step": "colored_noise + welch_psd + simulate_batch (9 kernel launches)"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "simulate_batch call (k_simulate plus its three small set-up kernels)",
+                         "flops_per_injection": flops_per_injection(wl),
+                         "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (recipe unit counts and "
+                                       "maximum SM clock)",
+                         "avg_launch_ms": sim_avg_s * 1e3,
+                         "hbm_gbs_output_only": B * D * N * 4 / sim_avg_s / 1e9},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "injections/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h,
+                    "path": "background strain H2D from pinned host memory, welch_psd + simulate_batch, "
+                            "whitened batch + parameters + offsets D2H to pinned host memory"},
+            "gpu_launches": sim.LAUNCHES_PER_STEP * args.steps,
+            "clocks": clk,
+            "log_likelihood": ll,
+            "wall_s_timed_region": t_wall,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gwx", choices=["gwx", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workloads.WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=None, help="draws per step (default: the workload's)")
+    ap.add_argument("--only-step", action="store_true",
+                    help="time only the device step (no end-to-end or log-likelihood leg); for profiling")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    wl = workloads.workload(args.workload)
+    if args.batch is not None:
+        wl["B"] = args.batch
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    return run_gpu(args, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
