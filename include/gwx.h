@@ -190,6 +190,27 @@ int gwx_whiten(const float* d, const double* psd, int64_t seg_len, double fs, do
                int64_t B, int D, int64_t N, float* y,
                void* workspace, size_t workspace_bytes, void* stream);
 
+/* ---- whitening without caller scratch -------------------------------------------
+ * Same result as gwx_whiten, for callers that cannot allocate device memory and
+ * so cannot pass a workspace: for example a plug-in whose host application owns
+ * every device allocation, a serving loop that must run inside a fixed,
+ * pre-reserved memory budget with no allocation or pool growth, or a binding that
+ * can only pass its data pointers.  The paper has no counterpart to this entry
+ * point; it exists for those callers only.
+ *
+ * The whitening filter is kept in a file-scope device array of the library that
+ * holds at most GWX_MAX_DET x 8193 floats (128 KiB), so D x (N/2 + 1) must not
+ * exceed 4 x 8193; larger requests return GWX_ESHAPE.  Every GPU that loads the
+ * library holds that array until the process exits.  The call allocates nothing.
+ * The first call on a device looks up the array's device address on that device
+ * (and prepares the library's tables as gwx_init does), so that first call should
+ * happen before any stream capture.  All calls share the one array, and each call
+ * overwrites it completely before reading it: calls that overlap in time on the
+ * GPU (different streams, or different host threads) race on it and must be
+ * serialised by the caller.  Arguments and errors as gwx_whiten. */
+int gwx_whiten_static(const float* d, const double* psd, int64_t seg_len, double fs, double f_lo,
+                      int64_t B, int D, int64_t N, float* y, void* stream);
+
 /* ---- A1-A3, A6, A7 fused: one whitened batch --------------------------------
  * The whole per-batch pass of Sec. 3.2 in one call: prior draws (as
  * gwx_sample_prior with `seed`, `step`), TaylorF2 waveforms, projection and

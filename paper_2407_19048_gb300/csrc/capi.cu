@@ -134,6 +134,8 @@ int check_ws(void* ws, size_t have, size_t need) {
 
 }  // namespace
 
+int gwx::set_last_error(int status, const char* msg) { return fail(status, "%s", msg); }
+
 extern "C" {
 
 int gwx_version(void) { return 100; }

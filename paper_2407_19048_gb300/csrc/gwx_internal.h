@@ -67,6 +67,9 @@ cudaError_t launch_loglike_full(const float* ydata, const float2* Ydata, const f
                                 const int64_t* ev_off, double* yy, int64_t E, int D, int64_t N, int k_lo, int64_t S,
                                 double* lnl, cudaStream_t s);
 
+// Record msg as the calling thread's gwx_last_error() message; returns status.
+int set_last_error(int status, const char* msg);
+
 // per-translation-unit table set-up on the current device
 cudaError_t init_tables_random();
 cudaError_t init_tables_spectral();
