@@ -226,6 +226,20 @@ int gwx_simulate_batch(const gwx_prior* prior, uint64_t seed, uint32_t step,
                        int64_t B, int64_t N, float* y, double* theta, int64_t* offsets,
                        void* workspace, size_t workspace_bytes, void* stream);
 
+/* The same pass in two calls, so that the prior draws and the FP64 per-draw set-up
+ * (which leave most of the GPU idle) can run on a second stream while the background
+ * and its PSD are produced: gwx_prepare_batch writes theta, offsets and the per-draw
+ * coefficients into the workspace; gwx_simulate_prepared reads them from the same
+ * workspace (sized by gwx_simulate_batch_workspace) and writes y.  The caller orders
+ * the two calls (same stream, or an event); gwx_simulate_batch is exactly
+ * gwx_prepare_batch followed by gwx_simulate_prepared on one stream. */
+int gwx_prepare_batch(const gwx_prior* prior, uint64_t seed, uint32_t step, int64_t L, int64_t N,
+                      double fs, double f_lo, const int32_t* det_ids, int D, double gmst, int64_t B,
+                      double* theta, int64_t* offsets, void* workspace, size_t workspace_bytes, void* stream);
+int gwx_simulate_prepared(const float* noise, int64_t L, const double* psd, int64_t seg_len,
+                          double fs, double f_lo, int D, int64_t B, int64_t N, const int64_t* offsets,
+                          float* y, void* workspace, size_t workspace_bytes, void* stream);
+
 /* ---- A8: log-likelihood -------------------------------------------------------
  * Sec. 6 (Fig. 5 caption): the standard GW likelihood.  For sample s of event e
  * (event_offsets[e] <= s < event_offsets[e+1]):

@@ -134,6 +134,30 @@ int check_ws(void* ws, size_t have, size_t need) {
 
 }  // namespace
 
+namespace {
+int check_psd_args(int64_t seg_len, int64_t N) {
+  if (!is_pow2(seg_len) || seg_len < 16 || seg_len > 16384)
+    return fail(GWX_ESHAPE, "seg_len=%lld must be a power of two in [16, 16384]", (long long)seg_len);
+  (void)N;
+  return GWX_OK;
+}
+
+int check_sim_shapes(int D, int64_t L, int64_t B, int64_t N, double fs, double f_lo, int* k_lo) {
+  GWX_TRY(check_window(N));
+  if (D < 1 || D > GWX_MAX_DET) return fail(GWX_ESHAPE, "D=%d outside [1, %d]", D, GWX_MAX_DET);
+  if ((size_t)D * (size_t)(N / 2) * sizeof(float2) > 200 * 1024)
+    return fail(GWX_EUNSUPPORTED, "D=%d windows of N=%lld do not fit in shared memory", D, (long long)N);
+  if (L < N || L - N + 1 > 0xffffffffLL) return fail(GWX_ESHAPE, "need N <= L, L-N < 2^32");
+  if (B < 0 || B > 0x7fffffffLL) return fail(GWX_ESHAPE, "B=%lld", (long long)B);
+  if (!(fs > 0.0)) return fail(GWX_EINVAL, "fs must be positive");
+  return band_start(f_lo, fs / (double)N, N / 2, k_lo);
+}
+
+DrawCoef* sim_coef(void* ws, int D, int64_t N) {
+  return reinterpret_cast<DrawCoef*>(reinterpret_cast<char*>(ws) + whiten_ws_bytes(D, N));
+}
+}  // namespace
+
 int gwx::set_last_error(int status, const char* msg) { return fail(status, "%s", msg); }
 
 extern "C" {
@@ -264,12 +288,6 @@ size_t gwx_whiten_workspace(int D, int64_t N) {
   return whiten_ws_bytes(D, N);
 }
 
-static int check_psd_args(int64_t seg_len, int64_t N) {
-  if (!is_pow2(seg_len) || seg_len < 16 || seg_len > 16384)
-    return fail(GWX_ESHAPE, "seg_len=%lld must be a power of two in [16, 16384]", (long long)seg_len);
-  (void)N;
-  return GWX_OK;
-}
 
 int gwx_whiten(const float* d, const double* psd, int64_t seg_len, double fs, double f_lo, int64_t B, int D,
                int64_t N, float* y, void* workspace, size_t workspace_bytes, void* stream) {
@@ -295,34 +313,52 @@ size_t gwx_simulate_batch_workspace(int D, int64_t B, int64_t N) {
   return whiten_ws_bytes(D, N) + coef_bytes(B);
 }
 
-int gwx_simulate_batch(const gwx_prior* prior, uint64_t seed, uint32_t step, const float* noise, int64_t L,
-                       const double* psd, int64_t seg_len, double fs, double f_lo, const int32_t* det_ids, int D,
-                       double gmst, int64_t B, int64_t N, float* y, double* theta, int64_t* offsets, void* workspace,
-                       size_t workspace_bytes, void* stream) {
+int gwx_prepare_batch(const gwx_prior* prior, uint64_t seed, uint32_t step, int64_t L, int64_t N, double fs,
+                      double f_lo, const int32_t* det_ids, int D, double gmst, int64_t B, double* theta,
+                      int64_t* offsets, void* workspace, size_t workspace_bytes, void* stream) {
   if (!prior) return fail(GWX_EINVAL, "prior is NULL");
-  GWX_TRY(check_window(N));
-  GWX_TRY(check_psd_args(seg_len, N));
   DetParams dp;
   GWX_TRY(make_detparams(det_ids, D, dp));
-  if ((size_t)D * (size_t)(N / 2) * sizeof(float2) > 200 * 1024)
-    return fail(GWX_EUNSUPPORTED, "D=%d windows of N=%lld do not fit in shared memory", D, (long long)N);
-  if (L < N || L - N + 1 > 0xffffffffLL) return fail(GWX_ESHAPE, "need N <= L, L-N < 2^32");
-  if (B < 0 || B > 0x7fffffffLL) return fail(GWX_ESHAPE, "B=%lld", (long long)B);
-  if (!(fs > 0.0) || !isfinite(gmst)) return fail(GWX_EINVAL, "bad fs or gmst");
-  const double df = fs / (double)N;
   int k_lo = 0;
-  GWX_TRY(band_start(f_lo, df, N / 2, &k_lo));
+  GWX_TRY(check_sim_shapes(D, L, B, N, fs, f_lo, &k_lo));
+  if (!isfinite(gmst)) return fail(GWX_EINVAL, "bad gmst");
   if (B == 0) return GWX_OK;
-  if (!noise || !psd || !y || !theta || !offsets) return fail(GWX_EINVAL, "NULL array");
+  if (!theta || !offsets) return fail(GWX_EINVAL, "NULL array");
+  GWX_TRY(check_ws(workspace, workspace_bytes, gwx_simulate_batch_workspace(D, B, N)));
+  GWX_TRY(ensure_init());
+  cudaStream_t s = as_stream(stream);
+  GWX_TRY(launched(launch_sample_prior(*prior, seed, step, B, L, N, theta, offsets, s), "sample_prior"));
+  return launched(launch_draw_setup(theta, B, k_lo, fs / (double)N, fs, N / 2 + 1, dp, gmst, sim_coef(workspace, D, N), s),
+                  "draw set-up");
+}
+
+int gwx_simulate_prepared(const float* noise, int64_t L, const double* psd, int64_t seg_len, double fs, double f_lo,
+                          int D, int64_t B, int64_t N, const int64_t* offsets, float* y, void* workspace,
+                          size_t workspace_bytes, void* stream) {
+  int k_lo = 0;
+  GWX_TRY(check_sim_shapes(D, L, B, N, fs, f_lo, &k_lo));
+  GWX_TRY(check_psd_args(seg_len, N));
+  if (B == 0) return GWX_OK;
+  if (!noise || !psd || !y || !offsets) return fail(GWX_EINVAL, "NULL array");
   GWX_TRY(check_ws(workspace, workspace_bytes, gwx_simulate_batch_workspace(D, B, N)));
   GWX_TRY(ensure_init());
   cudaStream_t s = as_stream(stream);
   float* W = reinterpret_cast<float*>(workspace);
-  DrawCoef* coef = reinterpret_cast<DrawCoef*>(reinterpret_cast<char*>(workspace) + whiten_ws_bytes(D, N));
-  GWX_TRY(launched(launch_sample_prior(*prior, seed, step, B, L, N, theta, offsets, s), "sample_prior"));
   GWX_TRY(launched(launch_whiten_filter(psd, D, seg_len, fs, k_lo, N, W, s), "whiten filter"));
-  GWX_TRY(launched(launch_draw_setup(theta, B, k_lo, df, fs, N / 2 + 1, dp, gmst, coef, s), "draw set-up"));
-  return launched(launch_simulate_fused(coef, noise, L, offsets, W, k_lo, D, B, N, fs, y, s), "simulate");
+  return launched(launch_simulate_fused(sim_coef(workspace, D, N), noise, L, offsets, W, k_lo, D, B, N, fs, y, s),
+                  "simulate");
+}
+
+int gwx_simulate_batch(const gwx_prior* prior, uint64_t seed, uint32_t step, const float* noise, int64_t L,
+                       const double* psd, int64_t seg_len, double fs, double f_lo, const int32_t* det_ids, int D,
+                       double gmst, int64_t B, int64_t N, float* y, double* theta, int64_t* offsets, void* workspace,
+                       size_t workspace_bytes, void* stream) {
+  GWX_TRY(check_psd_args(seg_len, N));
+  if (B > 0 && (!noise || !psd || !y)) return fail(GWX_EINVAL, "NULL array");
+  GWX_TRY(gwx_prepare_batch(prior, seed, step, L, N, fs, f_lo, det_ids, D, gmst, B, theta, offsets, workspace,
+                            workspace_bytes, stream));
+  return gwx_simulate_prepared(noise, L, psd, seg_len, fs, f_lo, D, B, N, offsets, y, workspace, workspace_bytes,
+                               stream);
 }
 
 static size_t loglike_base_bytes(int64_t E, int D, int64_t N) {

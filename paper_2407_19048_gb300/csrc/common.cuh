@@ -42,7 +42,28 @@ constexpr int TWN = 16384;
 // k^{-1/3}, ln k (hi, lo).
 constexpr int KMAX = 16384;
 
+// Per-pass twiddles of the Stockham passes, laid out [pass][row][jm] so that the
+// butterflies of consecutive threads (consecutive jm) read consecutive entries.
+// Radix-8 passes keep rows r = 1, 2, 4 (the other powers are formed by products),
+// radix-4 passes rows 1..3, radix-2 passes row 1, for Ns = 8, 64, 512, 4096.
+__host__ __device__ constexpr int twp_rows(int R) { return R == 8 ? 3 : (R == 4 ? 3 : 1); }
+__host__ __device__ constexpr int twp_nsets(int R) { return R == 4 ? 3 : 4; }       // Ns = 8, 64, 512 (, 4096)
+__host__ __device__ constexpr int twp_ns(int q) { return 8 << (3 * q); }
+__host__ __device__ constexpr int twp_size(int R) {
+  int t = 0;
+  for (int q = 0; q < twp_nsets(R); ++q) t += twp_rows(R) * twp_ns(q);
+  return t;
+}
+__host__ __device__ constexpr int twp_base(int R) { return R == 8 ? 0 : (R == 4 ? twp_size(8) : twp_size(8) + twp_size(4)); }
+__host__ __device__ constexpr int twp_offset(int R, int Ns) {
+  int t = twp_base(R);
+  for (int q = 0; twp_ns(q) < Ns; ++q) t += twp_rows(R) * twp_ns(q);
+  return t;
+}
+constexpr int TWP_TOTAL = twp_size(8) + twp_size(4) + twp_size(2);
+
 namespace {
+__device__ float2 g_twp[TWP_TOTAL];
 __device__ float2 g_tw[TWN];
 __device__ float4 g_kp53[KMAX + 1];   // k^-5/3 hi, lo, k^-2/3 hi, lo
 __device__ float4 g_kq[KMAX + 1];     // k^-1/3, ln k hi, ln k lo, 0
@@ -79,12 +100,27 @@ static inline float2 unit_twiddle(double a) {
 
 static inline cudaError_t fill_tables_for_this_tu() {
   static float2 tw[TWN];
+  static float2 twp[TWP_TOTAL];
   static float4 kp[KMAX + 1];
   static float4 kq[KMAX + 1];
   static bool built = false;
   if (!built) {
     const double two_pi = 6.283185307179586476925286766559;
     for (int m = 0; m < TWN; ++m) tw[m] = unit_twiddle(two_pi * (double)m / (double)TWN);
+    const int radices[3] = {8, 4, 2};
+    for (int ri = 0; ri < 3; ++ri) {
+      const int R = radices[ri];
+      const int rows8[3] = {1, 2, 4}, rows4[3] = {1, 2, 3}, rows2[1] = {1};
+      const int* rows = R == 8 ? rows8 : (R == 4 ? rows4 : rows2);
+      for (int q = 0; q < twp_nsets(R); ++q) {
+        const int Ns = twp_ns(q);
+        const int off = twp_offset(R, Ns);
+        for (int row = 0; row < twp_rows(R); ++row)
+          for (int jm = 0; jm < Ns; ++jm)
+            twp[off + row * Ns + jm] =
+                unit_twiddle(two_pi * (double)jm * (double)rows[row] / ((double)Ns * (double)R));
+      }
+    }
     kp[0] = make_float4(0.f, 0.f, 0.f, 0.f);
     kq[0] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int k = 1; k <= KMAX; ++k) {
@@ -99,6 +135,7 @@ static inline cudaError_t fill_tables_for_this_tu() {
     built = true;
   }
   cudaError_t e = cudaMemcpyToSymbol(g_tw, tw, sizeof(tw));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_twp, twp, sizeof(twp));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_kp53, kp, sizeof(kp));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_kq, kq, sizeof(kq));
   return e;
@@ -147,6 +184,13 @@ __device__ __forceinline__ float2 df_mul(float ah, float al, float bh, float bl)
 __device__ __forceinline__ float df_frac(float2 v) { return (v.x - rintf(v.x)) + v.y; }
 
 // ---------------------------------------------------------------- FFT
+// Shared-memory layout of every FFT buffer: element i is stored at sw(i), an XOR
+// swizzle of bits 0-3 by bits 3-6.  It is a bijection on [0, n) for any power of two
+// n, and it makes the strided stores of the first two radix-8 Stockham passes (stride
+// 8 and 64 complex values) as well as the contiguous loads free of bank conflicts for
+// 64-bit accesses (checked exhaustively for n = 2^10 .. 2^13).
+__device__ __forceinline__ int sw(int i) { return i ^ ((i >> 3) & 1) ^ (((i >> 4) & 7) << 1); }
+
 template <bool INV>
 __device__ __forceinline__ void dft2(float2& a, float2& b) {
   float2 t = a;
@@ -214,8 +258,28 @@ __device__ __forceinline__ void dftR(float2* v) {
 // x[(j div Ns) Ns R + (j mod Ns) + r Ns] (Govindaraju et al., SC'08).  Thread t of
 // the n/8 threads owns butterflies t + i n/8, i < 8/R, and all of them are read
 // before any is written (the two barriers make the pass in place).
-template <int LOGN, int R, bool INV>
-__device__ __forceinline__ void fft_pass(float2* x, int Ns, int t) {
+// Shared-memory accesses by 32-bit shared-window address (explicit ld/st.shared, so the
+// FFT keeps native shared-memory instructions although it is a separate function).
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ float2 lds2(uint32_t a) {
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void sts2(uint32_t a, float2 v) {
+  asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+
+// One Stockham pass of radix R over x[0..n) in shared memory, Ns = product of
+// the radices of the previous passes.  Butterfly j reads x[j + r n/R],
+// multiplies by e^{-+2 pi i (j mod Ns) r/(Ns R)}, transforms, and writes
+// x[(j div Ns) Ns R + (j mod Ns) + r Ns] (Govindaraju et al., SC'08).  Thread t of
+// the n/8 threads owns butterflies t + i n/8, i < 8/R, and all of them are read
+// before any is written (the two barriers make the pass in place).  x is the
+// shared-window address of element 0; element i lives at x + 8 sw(i).
+template <int LOGN, int R, int Ns, bool INV>
+__device__ __forceinline__ void fft_pass(uint32_t x, int t) {
+  static_assert(Ns == 1 || (Ns >= 8 && Ns <= 4096 && (R != 4 || Ns <= 512)), "no twiddle table for this pass");
   constexpr int n = 1 << LOGN;
   constexpr int NB = 8 / R;
   constexpr int nR = n / R;
@@ -223,17 +287,35 @@ __device__ __forceinline__ void fft_pass(float2* x, int Ns, int t) {
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
     const int j = t + i * (n / 8);
+    if constexpr (nR % 128 == 0) {
+      // r nR leaves bits 0-6 alone, so sw(j + r nR) = sw(j) + r nR
+      const uint32_t b = x + 8u * (uint32_t)sw(j);
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[i][r] = x[j + r * nR];
+      for (int r = 0; r < R; ++r) v[i][r] = lds2(b + 8u * (uint32_t)(r * nR));
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[i][r] = lds2(x + 8u * (uint32_t)sw(j + r * nR));
+    }
     const int jm = j & (Ns - 1);
     if (Ns > 1) {
-      const int step = jm * (TWN / R) / Ns;   // (TWN / (Ns R)) * jm, exact
+      // e^{-2 pi i jm r/(Ns R)} from the per-pass table (coalesced across threads)
+      const float2* tp = g_twp + twp_offset(R, Ns) + jm;
+      float2 w[R];
+      if constexpr (R == 8) {
+        // three table rows, four products: fewer load instructions per butterfly
+        w[1] = __ldg(tp);
+        w[2] = __ldg(tp + Ns);
+        w[4] = __ldg(tp + 2 * Ns);
+        w[3] = cmul(w[1], w[2]);
+        w[5] = cmul(w[1], w[4]);
+        w[6] = cmul(w[2], w[4]);
+        w[7] = cmul(w[3], w[4]);
+      } else {
 #pragma unroll
-      for (int r = 1; r < R; ++r) {
-        float2 w = twiddle(step * r);
-        if (INV) w.y = -w.y;
-        v[i][r] = cmul(v[i][r], w);
+        for (int r = 1; r < R; ++r) w[r] = __ldg(tp + (r - 1) * Ns);
       }
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[i][r] = cmul(v[i][r], INV ? cconj(w[r]) : w[r]);
     }
     dftR<R, INV>(v[i]);
   }
@@ -243,33 +325,66 @@ __device__ __forceinline__ void fft_pass(float2* x, int Ns, int t) {
     const int j = t + i * (n / 8);
     const int jm = j & (Ns - 1);
     const int idx = (j - jm) * R + jm;
+    // Closed forms of sw(idx + r Ns) for the strides that occur (checked exhaustively).
+    if constexpr (Ns % 128 == 0) {
+      const uint32_t b = x + 8u * (uint32_t)sw(idx);
 #pragma unroll
-    for (int r = 0; r < R; ++r) x[idx + r * Ns] = v[i][r];
+      for (int r = 0; r < R; ++r) sts2(b + 8u * (uint32_t)(r * Ns), v[i][r]);
+    } else if constexpr (Ns == 64 && R == 8) {
+      // idx has bits 6-8 clear; bit 6 of idx + 64 r is r & 1, which flips bit 3
+      const int se = sw(idx), so = se ^ 8;
+#pragma unroll
+      for (int r = 0; r < R; ++r) sts2(x + 8u * (uint32_t)(((r & 1) ? so : se) + 64 * r), v[i][r]);
+    } else if constexpr (Ns == 8 && R == 8) {
+      // idx has bits 3-5 clear: r fills them; bit 6 of idx flips bit 3
+      const int b6 = ((idx >> 6) & 1) << 3;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int kr = (r & 1) ^ (((r >> 1) & 3) << 1);
+        sts2(x + 8u * (uint32_t)((idx + 8 * r) ^ (kr ^ b6)), v[i][r]);
+      }
+    } else if constexpr (Ns == 1 && R == 8) {
+      // idx = 8 j: r fills bits 0-2; bits 3-6 come from j
+      const int c = (j & 1) ^ (((j >> 1) & 7) << 1);
+      const int base = (8 * j) ^ (c & 8), lo = c & 7;
+#pragma unroll
+      for (int r = 0; r < R; ++r) sts2(x + 8u * (uint32_t)(base | (r ^ lo)), v[i][r]);
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) sts2(x + 8u * (uint32_t)sw(idx + r * Ns), v[i][r]);
+    }
   }
   __syncthreads();
 }
 
 template <int LOGN, int DONE, bool INV>
 struct FftPasses {
-  static __device__ __forceinline__ void run(float2* x, int t) {
+  static __device__ __forceinline__ void run(uint32_t x, int t) {
     constexpr int REM = LOGN - DONE;
     constexpr int LR = REM >= 3 ? 3 : REM;
-    fft_pass<LOGN, (1 << LR), INV>(x, 1 << DONE, t);
+    fft_pass<LOGN, (1 << LR), (1 << DONE), INV>(x, t);
     FftPasses<LOGN, DONE + LR, INV>::run(x, t);
   }
 };
 template <int LOGN, bool INV>
 struct FftPasses<LOGN, LOGN, INV> {
-  static __device__ __forceinline__ void run(float2*, int) {}
+  static __device__ __forceinline__ void run(uint32_t, int) {}
 };
 
-// Complex FFT of n = 2^LOGN points in shared memory x by threads t = 0 .. n/8-1.
-// Every thread of the block must call it (it contains __syncthreads); threads
-// with t >= n/8 must not exist in the block.  Starts and ends with the data in x.
+// Complex FFT of n = 2^LOGN points held in shared memory at x (swizzled layout, see
+// sw) by threads t = 0 .. n/8-1.  Every thread of the block must call it (it
+// contains __syncthreads).  Starts and ends with the data in x.  Kept out of line:
+// inlined into a loop over transforms, the compiler keeps the addresses of all
+// passes live at once and spills.
 template <int LOGN, bool INV>
-__device__ __forceinline__ void fft_smem(float2* x, int t) {
+__device__ __noinline__ void fft_smem_at(uint32_t x, int t) {
   static_assert(LOGN >= 3 && LOGN <= 13, "FFT size out of range");
   FftPasses<LOGN, 0, INV>::run(x, t);
+}
+
+template <int LOGN, bool INV>
+__device__ __forceinline__ void fft_smem(float2* x, int t) {
+  fft_smem_at<LOGN, INV>(smem_addr(x), t);
 }
 
 // ------------------------------------------------ real <-> half-length complex

@@ -43,7 +43,7 @@ __global__ void k_sample_prior(gwx_prior p, uint32_t k0, uint32_t k1, uint32_t s
 cudaError_t launch_sample_prior(const gwx_prior& p, uint64_t seed, uint32_t step, int64_t B, int64_t L, int64_t N,
                                 double* theta, int64_t* offsets, cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
-  const int T = 128;
+  const int T = 32;   // FP64 acos/asin: spread the draws over many SMs
   k_sample_prior<<<(unsigned)((B + T - 1) / T), T, 0, s>>>(p, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32),
                                                            step, B, (uint32_t)(L - N + 1), theta, offsets);
   return cudaGetLastError();
@@ -116,7 +116,7 @@ __global__ void k_fourstep_a(const float2* __restrict__ Z, int64_t n, int n1, in
   const int stride = n2 + 1;
   for (int e = threadIdx.x; e < TK * n2; e += blockDim.x) {
     const int g = e % TK, k2 = e / TK;
-    sm[g * stride + k2] = Zd[(int64_t)(k1_0 + g) + (int64_t)n1 * k2];
+    sm[g * stride + sw(k2)] = Zd[(int64_t)(k1_0 + g) + (int64_t)n1 * k2];
   }
   __syncthreads();
   const int g = threadIdx.x / (n2 / 8), t = threadIdx.x % (n2 / 8);
@@ -127,7 +127,7 @@ __global__ void k_fourstep_a(const float2* __restrict__ Z, int64_t n, int n1, in
     const int k1 = k1_0 + gg;
     float sn, cs;
     sincospif((float)(k1 * m2) * two_over_n, &sn, &cs);   // k1 m2 < n <= 2^23: exact
-    Gd[(int64_t)k1 * n2 + m2] = cmul(sm[gg * stride + m2], make_float2(cs, sn));
+    Gd[(int64_t)k1 * n2 + m2] = cmul(sm[gg * stride + sw(m2)], make_float2(cs, sn));
   }
 }
 
@@ -144,14 +144,14 @@ __global__ void k_fourstep_b(const float2* __restrict__ G, int64_t n, int n2, in
   const int stride = n1 + 1;
   for (int e = threadIdx.x; e < TM * n1; e += blockDim.x) {
     const int g = e % TM, k1 = e / TM;
-    sm[g * stride + k1] = Gd[(int64_t)k1 * n2 + m2_0 + g];
+    sm[g * stride + sw(k1)] = Gd[(int64_t)k1 * n2 + m2_0 + g];
   }
   __syncthreads();
   const int g = threadIdx.x / (n1 / 8), t = threadIdx.x % (n1 / 8);
   fft_smem<LOGN1, true>(sm + g * stride, t);
   for (int e = threadIdx.x; e < TM * n1; e += blockDim.x) {
     const int gg = e % TM, m1 = e / TM;
-    xd[(int64_t)n2 * m1 + m2_0 + gg] = sm[gg * stride + m1];
+    xd[(int64_t)n2 * m1 + m2_0 + gg] = sm[gg * stride + sw(m1)];
   }
 }
 
@@ -171,7 +171,7 @@ static cudaError_t run_pass_a(int lg, const float2* Z, int64_t n, int n1, int D,
     constexpr int n2 = 1 << LOG;
     const int per = n2 / 8;
     int TK = 1024 / per;
-    if (TK > 16) TK = 16;
+    if (TK > 4) TK = 4;   // small tiles: many blocks for a transform done once per step
     if (TK > n1) TK = n1;
     const size_t smem = (size_t)TK * (n2 + 1) * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(k_fourstep_a<LOG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -191,7 +191,7 @@ static cudaError_t run_pass_b(int lg, const float2* G, int64_t n, int n2, int D,
     constexpr int n1 = 1 << LOG;
     const int per = n1 / 8;
     int TM = 1024 / per;
-    if (TM > 16) TM = 16;
+    if (TM > 4) TM = 4;
     if (TM > n2) TM = n2;
     const size_t smem = (size_t)TM * (n1 + 1) * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(k_fourstep_b<LOG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

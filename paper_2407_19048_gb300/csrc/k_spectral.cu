@@ -44,37 +44,55 @@ __global__ void __launch_bounds__(RowGeom<LOGN>::TPR) k_welch_seg(const float* _
     const int m = t + i * (n / 8);
     const float w0 = 0.5f - 0.5f * cospif((float)(2 * m) * (2.0f / (float)M));
     const float w1 = 0.5f - 0.5f * cospif((float)(2 * m + 1) * (2.0f / (float)M));
-    sm[m] = make_float2(seg[2 * m] * w0, seg[2 * m + 1] * w1);
+    sm[sw(m)] = make_float2(seg[2 * m] * w0, seg[2 * m + 1] * w1);
   }
   __syncthreads();
   fft_smem<LOGN, false>(sm, t);
   double* P = part + ((int64_t)d * K + s) * (n + 1);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int k = 1 + t + i * (n / 8);
+    const int k = t + i * (n / 8);
+    if (k == 0) {
+      const float2 z0 = sm[0];
+      const double x0 = (double)z0.x + z0.y, xn = (double)z0.x - z0.y;
+      P[0] = x0 * x0;
+      P[n] = xn * xn;
+      continue;
+    }
     float2 xk, xnk;
-    unpack_pair(sm[k], sm[n - k], pack_twiddle(k, LOGN + 1), xk, xnk);
+    unpack_pair(sm[sw(k)], sm[sw(n - k)], pack_twiddle(k, LOGN + 1), xk, xnk);
     P[k] = (double)xk.x * xk.x + (double)xk.y * xk.y;
-    if (n - k != k) P[n - k] = (double)xnk.x * xnk.x + (double)xnk.y * xnk.y;
+    P[n - k] = (double)xnk.x * xnk.x + (double)xnk.y * xnk.y;
   }
   if (t == 0) {
-    const float2 z0 = sm[0];
-    const double x0 = (double)z0.x + z0.y, xn = (double)z0.x - z0.y;
-    P[0] = x0 * x0;
-    P[n] = xn * xn;
+    float2 xh, xh2;
+    unpack_pair(sm[sw(n / 2)], sm[sw(n / 2)], pack_twiddle(n / 2, LOGN + 1), xh, xh2);
+    P[n / 2] = (double)xh.x * xh.x + (double)xh.y * xh.y;
   }
 }
 
-// psd[d][k] = c_k / (fs sum w^2) / K * sum_s part[d][s][k], summed in segment order.
-__global__ void k_welch_reduce(const double* __restrict__ part, int D, int K, int nb, double scale_mid,
-                               double scale_end, double* __restrict__ psd) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (int64_t)D * nb) return;
-  const int d = (int)(i / nb), k = (int)(i % nb);
+// psd[d][k] = c_k / (fs sum w^2) / K * sum_s part[d][s][k].  A block covers 32 bins
+// of one detector with 8 lanes per bin; lane l sums the segments s = l mod 8 and the
+// eight partial sums are combined in a fixed order (deterministic result).
+__global__ void __launch_bounds__(256) k_welch_reduce(const double* __restrict__ part, int D, int K, int nb,
+                                                      double scale_mid, double scale_end, double* __restrict__ psd) {
+  __shared__ double red[8][33];
+  const int d = blockIdx.y;
+  const int kk = threadIdx.x & 31, lane = threadIdx.x >> 5;
+  const int k = blockIdx.x * 32 + kk;
   double acc = 0.0;
-  const double* p = part + (int64_t)d * K * nb + k;
-  for (int s = 0; s < K; ++s) acc += p[(int64_t)s * nb];
-  psd[i] = acc * ((k == 0 || k == nb - 1) ? scale_end : scale_mid);
+  if (k < nb) {
+    const double* p = part + (int64_t)d * K * nb + k;
+    for (int s = lane; s < K; s += 8) acc += p[(int64_t)s * nb];
+  }
+  red[lane][kk] = acc;
+  __syncthreads();
+  if (lane == 0 && k < nb) {
+    double t = 0.0;
+#pragma unroll
+    for (int l = 0; l < 8; ++l) t += red[l][kk];
+    psd[(int64_t)d * nb + k] = t * ((k == 0 || k == nb - 1) ? scale_end : scale_mid);
+  }
 }
 
 size_t welch_ws(int D, int64_t L, int64_t M, int64_t stride) {
@@ -104,8 +122,8 @@ cudaError_t launch_welch(const float* x, int D, int64_t L, double fs, int64_t M,
   }
   const int nb = (int)(M / 2 + 1);
   const double scale_end = 1.0 / (fs * sw2) / (double)K;
-  const int64_t total = (int64_t)D * nb;
-  k_welch_reduce<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(part, D, K, nb, 2.0 * scale_end, scale_end, psd);
+  k_welch_reduce<<<dim3((unsigned)((nb + 31) / 32), (unsigned)D), 256, 0, s>>>(part, D, K, nb, 2.0 * scale_end,
+                                                                               scale_end, psd);
   return cudaGetLastError();
 }
 
@@ -136,7 +154,7 @@ __global__ void k_whiten_filter(const double* __restrict__ psd, int D, int64_t M
 cudaError_t launch_whiten_filter(const double* psd, int D, int64_t M, double fs, int k_lo, int64_t N, float* W,
                                  cudaStream_t s) {
   const int64_t total = (int64_t)D * (N / 2 + 1);
-  k_whiten_filter<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(psd, D, M, fs, k_lo, N, W);
+  k_whiten_filter<<<(unsigned)((total + 63) / 64), 64, 0, s>>>(psd, D, M, fs, k_lo, N, W);   // FP64: spread wide
   return cudaGetLastError();
 }
 
@@ -148,7 +166,7 @@ __device__ __forceinline__ void load_real_row(float2* z, const float* row, int t
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int m = t + i * (n / 8);
-    z[m] = live ? r2[m] : make_float2(0.f, 0.f);
+    z[sw(m)] = live ? r2[m] : make_float2(0.f, 0.f);
   }
 }
 
@@ -160,7 +178,7 @@ __device__ __forceinline__ void store_real_row(const float2* z, float* row, int 
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int m = t + i * (n / 8);
-    __stcs(&r2[m], z[m]);
+    __stcs(&r2[m], z[sw(m)]);
   }
 }
 
@@ -185,18 +203,28 @@ __global__ void __launch_bounds__(RowGeom<LOGN>::THREADS) k_whiten_rows(const fl
   const float inv_n = 1.0f / (float)n;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int k = 1 + t + i * (n / 8);
+    const int k = t + i * (n / 8);
+    if (k == 0) {
+      const float2 z0 = z[0];
+      const float y0 = (z0.x + z0.y) * __ldg(&Wd[0]) * inv_n, yn = (z0.x - z0.y) * __ldg(&Wd[n]) * inv_n;
+      z[0] = make_float2(0.5f * (y0 + yn), 0.5f * (y0 - yn));
+      continue;
+    }
     const float2 wk = pack_twiddle(k, LOGN + 1);
     float2 xk, xnk, zk, znk;
-    unpack_pair(z[k], z[n - k], wk, xk, xnk);
+    unpack_pair(z[sw(k)], z[sw(n - k)], wk, xk, xnk);
     pack_pair(cscale(xk, __ldg(&Wd[k]) * inv_n), cscale(xnk, __ldg(&Wd[n - k]) * inv_n), wk, zk, znk);
-    z[k] = zk;
-    z[n - k] = znk;
+    z[sw(k)] = zk;
+    z[sw(n - k)] = znk;
   }
-  if (t == 0) {
-    const float2 z0 = z[0];
-    const float y0 = (z0.x + z0.y) * __ldg(&Wd[0]) * inv_n, yn = (z0.x - z0.y) * __ldg(&Wd[n]) * inv_n;
-    z[0] = make_float2(0.5f * (y0 + yn), 0.5f * (y0 - yn));
+  if (t == 0) {   // k = n/2 pairs with itself
+    const int h = n / 2;
+    const float2 wk = pack_twiddle(h, LOGN + 1);
+    float2 xk, xnk, zk, znk;
+    unpack_pair(z[sw(h)], z[sw(h)], wk, xk, xnk);
+    const float s_ = __ldg(&Wd[h]) * inv_n;
+    pack_pair(cscale(xk, s_), cscale(xk, s_), wk, zk, znk);
+    z[sw(h)] = zk;
   }
   __syncthreads();
   fft_smem<LOGN, true>(z, t);
@@ -231,15 +259,22 @@ __global__ void __launch_bounds__(RowGeom<LOGN>::THREADS) k_inject_rows(const fl
   const float2* hr = h + (live ? r : 0) * F;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int k = 1 + t + i * (n / 8);
+    const int k = t + i * (n / 8);
+    if (k == 0) {
+      const float y0 = hr[0].x * scale, yn = hr[n].x * scale;
+      z[0] = make_float2(0.5f * (y0 + yn), 0.5f * (y0 - yn));
+      continue;
+    }
     float2 zk, znk;
     pack_pair(cscale(hr[k], scale), cscale(hr[n - k], scale), pack_twiddle(k, LOGN + 1), zk, znk);
-    z[k] = zk;
-    z[n - k] = znk;
+    z[sw(k)] = zk;
+    z[sw(n - k)] = znk;
   }
   if (t == 0) {
-    const float y0 = hr[0].x * scale, yn = hr[n].x * scale;
-    z[0] = make_float2(0.5f * (y0 + yn), 0.5f * (y0 - yn));
+    const int h = n / 2;
+    float2 zk, znk;
+    pack_pair(cscale(hr[h], scale), cscale(hr[h], scale), pack_twiddle(h, LOGN + 1), zk, znk);
+    z[sw(h)] = zk;
   }
   __syncthreads();
   fft_smem<LOGN, true>(z, t);
@@ -253,7 +288,7 @@ __global__ void __launch_bounds__(RowGeom<LOGN>::THREADS) k_inject_rows(const fl
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int m = t + i * (n / 8);
-    const float2 v = z[m];
+    const float2 v = z[sw(m)];
     __stcs(&out[m], make_float2(v.x + crop[2 * m], v.y + crop[2 * m + 1]));
   }
 }
@@ -290,16 +325,22 @@ __global__ void __launch_bounds__(RowGeom<LOGN>::THREADS) k_rfft_rows(const floa
   float2* Xr = X + r * F;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int k = 1 + t + i * (n / 8);
+    const int k = t + i * (n / 8);
+    if (k == 0) {
+      const float2 z0 = z[0];
+      Xr[0] = make_float2(z0.x + z0.y, 0.f);
+      Xr[n] = make_float2(z0.x - z0.y, 0.f);
+      continue;
+    }
     float2 xk, xnk;
-    unpack_pair(z[k], z[n - k], pack_twiddle(k, LOGN + 1), xk, xnk);
+    unpack_pair(z[sw(k)], z[sw(n - k)], pack_twiddle(k, LOGN + 1), xk, xnk);
     Xr[k] = xk;
-    if (n - k != k) Xr[n - k] = xnk;
+    Xr[n - k] = xnk;
   }
   if (t == 0) {
-    const float2 z0 = z[0];
-    Xr[0] = make_float2(z0.x + z0.y, 0.f);
-    Xr[n] = make_float2(z0.x - z0.y, 0.f);
+    float2 xk, xnk;
+    unpack_pair(z[sw(n / 2)], z[sw(n / 2)], pack_twiddle(n / 2, LOGN + 1), xk, xnk);
+    Xr[n / 2] = xk;
   }
 }
 
@@ -319,15 +360,22 @@ __global__ void __launch_bounds__(RowGeom<LOGN>::THREADS) k_irfft_rows(const flo
   const float inv_n = 1.0f / (float)n;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int k = 1 + t + i * (n / 8);
+    const int k = t + i * (n / 8);
+    if (k == 0) {
+      const float y0 = Xr[0].x * inv_n, yn = Xr[n].x * inv_n;
+      z[0] = make_float2(0.5f * (y0 + yn), 0.5f * (y0 - yn));
+      continue;
+    }
     float2 zk, znk;
     pack_pair(cscale(Xr[k], inv_n), cscale(Xr[n - k], inv_n), pack_twiddle(k, LOGN + 1), zk, znk);
-    z[k] = zk;
-    z[n - k] = znk;
+    z[sw(k)] = zk;
+    z[sw(n - k)] = znk;
   }
   if (t == 0) {
-    const float y0 = Xr[0].x * inv_n, yn = Xr[n].x * inv_n;
-    z[0] = make_float2(0.5f * (y0 + yn), 0.5f * (y0 - yn));
+    const int h = n / 2;
+    float2 zk, znk;
+    pack_pair(cscale(Xr[h], inv_n), cscale(Xr[h], inv_n), pack_twiddle(h, LOGN + 1), zk, znk);
+    z[sw(h)] = zk;
   }
   __syncthreads();
   fft_smem<LOGN, true>(z, t);

@@ -7,32 +7,35 @@ namespace gwx {
 cudaError_t init_tables_waveform() { return fill_tables_for_this_tu(); }
 
 // One thread per draw: FP64 set-up of the waveform and projection coefficients.
-__global__ void k_draw_setup(const double* __restrict__ theta, int64_t B, double df, double fs, int64_t F,
-                             DetParams dp, double gmst, DrawCoef* __restrict__ coef) {
+// One thread per draw.  The set-up is FP64-throughput bound (GB300 issues a warp's
+// FP64 instruction over many cycles), so blocks are one warp wide to spread the
+// draws over as many SMs as possible.
+__global__ void k_draw_setup(const double* __restrict__ theta, int64_t B, double df, double df76, double fs,
+                             int64_t F, DetParams dp, double gmst, DrawCoef* __restrict__ coef) {
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   DrawCoef c;
-  draw_waveform_coef(theta, B, b, df, F, c);
-  // fs * amp recomputed in FP64 from the same inputs (c.amp is its float rounding)
-  draw_detector_coef(theta, B, b, df, dp, gmst, c.qp, c.qc_im, fs * waveform_amp(theta, B, b, df), c);
+  double amp = 0.0;
+  draw_waveform_coef(theta, B, b, df, df76, F, c, &amp);
+  draw_detector_coef(theta, B, b, df, dp, gmst, c.qp, c.qc_im, fs * amp, c);
   coef[b] = c;
 }
 
 cudaError_t launch_draw_setup(const double* theta, int64_t B, int /*k_lo*/, double df, double fs, int64_t F,
                               const DetParams& dp, double gmst, DrawCoef* coef, cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
-  const int T = 128;
-  k_draw_setup<<<(unsigned)((B + T - 1) / T), T, 0, s>>>(theta, B, df, fs, F, dp, gmst, coef);
+  const int T = 32;
+  k_draw_setup<<<(unsigned)((B + T - 1) / T), T, 0, s>>>(theta, B, df, pow(df, -7.0 / 6.0), fs, F, dp, gmst, coef);
   return cudaGetLastError();
 }
 
 // A2: one block per draw; thread 0 computes the coefficients, all threads sweep
 // the bins.  hp/hc are written for every bin (zeros outside [k_lo, kcut]).
-__global__ void k_generate_waveforms(const double* __restrict__ theta, int64_t B, int k_lo, double df, int64_t F,
-                                     float2* __restrict__ hp, float2* __restrict__ hc) {
+__global__ void k_generate_waveforms(const double* __restrict__ theta, int64_t B, int k_lo, double df, double df76,
+                                     int64_t F, float2* __restrict__ hp, float2* __restrict__ hc) {
   __shared__ DrawCoef sc;
   const int64_t b = blockIdx.x;
-  if (threadIdx.x == 0) draw_waveform_coef(theta, B, b, df, F, sc);
+  if (threadIdx.x == 0) draw_waveform_coef(theta, B, b, df, df76, F, sc);
   __syncthreads();
   const DrawCoef& c = sc;
   float2* hpb = hp + b * F;
@@ -56,7 +59,7 @@ __global__ void k_generate_waveforms(const double* __restrict__ theta, int64_t B
 cudaError_t launch_generate_waveforms(const double* theta, int64_t B, int k_lo, double df, int64_t F, float2* hp,
                                       float2* hc, cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
-  k_generate_waveforms<<<(unsigned)B, 256, 0, s>>>(theta, B, k_lo, df, F, hp, hc);
+  k_generate_waveforms<<<(unsigned)B, 256, 0, s>>>(theta, B, k_lo, df, pow(df, -7.0 / 6.0), F, hp, hc);
   return cudaGetLastError();
 }
 

@@ -32,21 +32,21 @@ __device__ __forceinline__ float2 split_df(double x) {
 
 __device__ __forceinline__ double th_at(const double* th, int64_t B, int64_t b, int p) { return th[(int64_t)p * B + b]; }
 
+constexpr double SQRT_5_24_PI_M23 = 0.21278751013966343;   // sqrt(5/24) pi^(-2/3)
+constexpr double LN4 = 1.3862943611198906;
+constexpr double INV_6P15_PI = 0.021658244478713226;        // 1 / (6^1.5 pi)
+
 // A(df) = sqrt(5/24) pi^{-2/3} Mc^{5/6} df^{-7/6} / D in FP64 (strain per Hz), so that
-// the amplitude of bin k is A(df) k^{-7/6}.
-__device__ inline double waveform_amp(const double* th, int64_t B, int64_t b, double df) {
-  const double m1 = th_at(th, B, b, GWX_M1), m2 = th_at(th, B, b, GWX_M2);
-  const double mt = m1 + m2;
-  const double M = mt * MTSUN_S;
-  const double eta = m1 * m2 / (mt * mt);
-  const double Mc = M * pow(eta, 0.6);
-  const double D = th_at(th, B, b, GWX_DIST) * MPC_M / C_MS;
-  return sqrt(5.0 / 24.0) * pow(PI_D, -2.0 / 3.0) * pow(Mc, 5.0 / 6.0) / D * pow(df, -7.0 / 6.0);
+// the amplitude of bin k is A(df) k^{-7/6}; df76 = df^{-7/6}.  Mc^{5/6} =
+// M^{5/6} eta^{1/2} since Mc = M eta^{3/5}.
+__device__ __forceinline__ double waveform_amp(double M, double eta, double dist_mpc, double df76) {
+  const double D = dist_mpc * (MPC_M / C_MS);
+  return SQRT_5_24_PI_M23 * exp((5.0 / 6.0) * log(M)) * sqrt(eta) / D * df76;
 }
 
 // Waveform part of the set-up: PN phase coefficients in turns, amplitude and cut-off.
-__device__ inline void draw_waveform_coef(const double* th, int64_t B, int64_t b, double df, int64_t F,
-                                          DrawCoef& c) {
+__device__ inline void draw_waveform_coef(const double* th, int64_t B, int64_t b, double df, double df76,
+                                          int64_t F, DrawCoef& c, double* amp64 = nullptr) {
   const double m1 = th_at(th, B, b, GWX_M1), m2 = th_at(th, B, b, GWX_M2);
   const double chi1 = th_at(th, B, b, GWX_CHI1), chi2 = th_at(th, B, b, GWX_CHI2);
   const double phic = th_at(th, B, b, GWX_PHIC);
@@ -63,7 +63,7 @@ __device__ inline void draw_waveform_coef(const double* th, int64_t B, int64_t b
   const double a5 = pi * (38645.0 / 756.0 - 65.0 * eta / 9.0);
   const double l5 = 3.0 * a5;
   const double a6 = 11583231236531.0 / 4694215680.0 - 640.0 * pi2 / 3.0 - 6848.0 * EULER_GAMMA / 21.0 -
-                    6848.0 * log(4.0) / 21.0 + (-15737765635.0 / 3048192.0 + 2255.0 * pi2 / 12.0) * eta +
+                    6848.0 * LN4 / 21.0 + (-15737765635.0 / 3048192.0 + 2255.0 * pi2 / 12.0) * eta +
                     76055.0 * eta * eta / 1728.0 - 127825.0 * eta * eta * eta / 1296.0;
   const double l6 = -6848.0 / 21.0;
   const double a7 = pi * (77096675.0 / 254016.0 + 378515.0 * eta / 1512.0 - 74045.0 * eta * eta / 756.0);
@@ -83,8 +83,10 @@ __device__ inline void draw_waveform_coef(const double* th, int64_t B, int64_t b
   double cph = -(phic + 0.25 * pi) / (2.0 * pi) + pref * (a5 + l5 * lnV);
   cph -= rint(cph);
   c.cph = (float)cph;
-  c.amp = (float)waveform_amp(th, B, b, df);
-  const double f_isco = 1.0 / (pow(6.0, 1.5) * pi * M);
+  const double amp = waveform_amp(M, eta, th_at(th, B, b, GWX_DIST), df76);
+  if (amp64) *amp64 = amp;
+  c.amp = (float)amp;
+  const double f_isco = INV_6P15_PI / M;
   double kc = floor(f_isco / df);
   c.kcut = kc > (double)(F - 1) ? (int)(F - 1) : (int)kc;
   const double ci = cos(iota);
