@@ -117,6 +117,7 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 size_t whiten_ws_bytes(int D, int64_t N) { return align_up((size_t)D * (size_t)(N / 2 + 1) * sizeof(float)); }
 size_t coef_bytes(int64_t B) { return align_up((size_t)B * sizeof(DrawCoef)); }
+size_t packed_ws_bytes(int D, int64_t N) { return align_up((size_t)D * (size_t)(N / 2) * sizeof(float2)); }
 
 int check_ws(void* ws, size_t have, size_t need) {
   if (need == 0) return GWX_OK;
@@ -153,8 +154,12 @@ int check_sim_shapes(int D, int64_t L, int64_t B, int64_t N, double fs, double f
   return band_start(f_lo, fs / (double)N, N / 2, k_lo);
 }
 
+// simulate workspace: [W: D x (N/2+1) floats | Wp: D x N/2 float2 | per-draw coefficients]
+float2* sim_packed(void* ws, int D, int64_t N) {
+  return reinterpret_cast<float2*>(reinterpret_cast<char*>(ws) + whiten_ws_bytes(D, N));
+}
 DrawCoef* sim_coef(void* ws, int D, int64_t N) {
-  return reinterpret_cast<DrawCoef*>(reinterpret_cast<char*>(ws) + whiten_ws_bytes(D, N));
+  return reinterpret_cast<DrawCoef*>(reinterpret_cast<char*>(ws) + whiten_ws_bytes(D, N) + packed_ws_bytes(D, N));
 }
 }  // namespace
 
@@ -310,7 +315,7 @@ int gwx_whiten(const float* d, const double* psd, int64_t seg_len, double fs, do
 
 size_t gwx_simulate_batch_workspace(int D, int64_t B, int64_t N) {
   if (D < 1 || B < 0 || N < 2) return 0;
-  return whiten_ws_bytes(D, N) + coef_bytes(B);
+  return whiten_ws_bytes(D, N) + packed_ws_bytes(D, N) + coef_bytes(B);
 }
 
 int gwx_prepare_batch(const gwx_prior* prior, uint64_t seed, uint32_t step, int64_t L, int64_t N, double fs,
@@ -344,8 +349,10 @@ int gwx_simulate_prepared(const float* noise, int64_t L, const double* psd, int6
   GWX_TRY(ensure_init());
   cudaStream_t s = as_stream(stream);
   float* W = reinterpret_cast<float*>(workspace);
+  float2* Wp = sim_packed(workspace, D, N);
   GWX_TRY(launched(launch_whiten_filter(psd, D, seg_len, fs, k_lo, N, W, s), "whiten filter"));
-  return launched(launch_simulate_fused(sim_coef(workspace, D, N), noise, L, offsets, W, k_lo, D, B, N, fs, y, s),
+  GWX_TRY(launched(launch_packed_filter(W, D, N, Wp, s), "packed filter"));
+  return launched(launch_simulate_fused(sim_coef(workspace, D, N), noise, L, offsets, W, Wp, k_lo, D, B, N, fs, y, s),
                   "simulate");
 }
 

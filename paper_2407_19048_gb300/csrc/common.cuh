@@ -45,21 +45,14 @@ constexpr int KMAX = 16384;
 // Per-pass twiddles of the Stockham passes, laid out [pass][row][jm] so that the
 // butterflies of consecutive threads (consecutive jm) read consecutive entries.
 // Radix-8 passes keep rows r = 1, 2, 4 (the other powers are formed by products),
-// radix-4 passes rows 1..3, radix-2 passes row 1, for Ns = 8, 64, 512, 4096.
-__host__ __device__ constexpr int twp_rows(int R) { return R == 8 ? 3 : (R == 4 ? 3 : 1); }
-__host__ __device__ constexpr int twp_nsets(int R) { return R == 4 ? 3 : 4; }       // Ns = 8, 64, 512 (, 4096)
-__host__ __device__ constexpr int twp_ns(int q) { return 8 << (3 * q); }
-__host__ __device__ constexpr int twp_size(int R) {
-  int t = 0;
-  for (int q = 0; q < twp_nsets(R); ++q) t += twp_rows(R) * twp_ns(q);
-  return t;
-}
+// radix-4 passes rows 1..3, radix-2 passes row 1; one set for every stride
+// Ns = 2, 4, ..., 4096 of each radix.
+__host__ __device__ constexpr int twp_rows(int R) { return R == 2 ? 1 : 3; }
+constexpr int TWP_NSETS = 12;                                    // Ns = 2 .. 4096
+__host__ __device__ constexpr int twp_ns(int q) { return 2 << q; }
+__host__ __device__ constexpr int twp_size(int R) { return twp_rows(R) * ((2 << TWP_NSETS) - 2); }
 __host__ __device__ constexpr int twp_base(int R) { return R == 8 ? 0 : (R == 4 ? twp_size(8) : twp_size(8) + twp_size(4)); }
-__host__ __device__ constexpr int twp_offset(int R, int Ns) {
-  int t = twp_base(R);
-  for (int q = 0; twp_ns(q) < Ns; ++q) t += twp_rows(R) * twp_ns(q);
-  return t;
-}
+__host__ __device__ constexpr int twp_offset(int R, int Ns) { return twp_base(R) + twp_rows(R) * (Ns - 2); }
 constexpr int TWP_TOTAL = twp_size(8) + twp_size(4) + twp_size(2);
 
 namespace {
@@ -112,7 +105,7 @@ static inline cudaError_t fill_tables_for_this_tu() {
       const int R = radices[ri];
       const int rows8[3] = {1, 2, 4}, rows4[3] = {1, 2, 3}, rows2[1] = {1};
       const int* rows = R == 8 ? rows8 : (R == 4 ? rows4 : rows2);
-      for (int q = 0; q < twp_nsets(R); ++q) {
+      for (int q = 0; q < TWP_NSETS; ++q) {
         const int Ns = twp_ns(q);
         const int off = twp_offset(R, Ns);
         for (int row = 0; row < twp_rows(R); ++row)
@@ -279,7 +272,7 @@ __device__ __forceinline__ void sts2(uint32_t a, float2 v) {
 // shared-window address of element 0; element i lives at x + 8 sw(i).
 template <int LOGN, int R, int Ns, bool INV>
 __device__ __forceinline__ void fft_pass(uint32_t x, int t) {
-  static_assert(Ns == 1 || (Ns >= 8 && Ns <= 4096 && (R != 4 || Ns <= 512)), "no twiddle table for this pass");
+  static_assert(Ns == 1 || (Ns >= 2 && Ns <= 4096), "no twiddle table for this pass");
   constexpr int n = 1 << LOGN;
   constexpr int NB = 8 / R;
   constexpr int nR = n / R;

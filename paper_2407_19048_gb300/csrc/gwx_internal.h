@@ -53,6 +53,8 @@ cudaError_t launch_welch(const float* x, int D, int64_t L, double fs, int64_t M,
 size_t welch_ws(int D, int64_t L, int64_t M, int64_t stride);
 cudaError_t launch_whiten_filter(const double* psd, int D, int64_t M, double fs, int k_lo, int64_t N, float* W,
                                  cudaStream_t s);
+// Packed-domain whitening coefficients (alpha, beta) [D][N/2] from W [D][N/2+1].
+cudaError_t launch_packed_filter(const float* W, int D, int64_t N, float2* Wp, cudaStream_t s);
 cudaError_t launch_whiten_rows(const float* d, const float* W, int64_t rows, int D, int64_t N, float* y,
                                cudaStream_t s);
 cudaError_t launch_inject_rows(const float* noise, int D, int64_t L, const int64_t* offsets, const float2* hdet,
@@ -60,8 +62,8 @@ cudaError_t launch_inject_rows(const float* noise, int D, int64_t L, const int64
 cudaError_t launch_rfft_rows(const float* x, int64_t R, int64_t N, float2* X, cudaStream_t s);
 cudaError_t launch_irfft_rows(const float2* X, int64_t R, int64_t N, float* x, cudaStream_t s);
 cudaError_t launch_simulate_fused(const DrawCoef* coef, const float* noise, int64_t L, const int64_t* offsets,
-                                  const float* W, int k_lo, int D, int64_t B, int64_t N, double fs, float* y,
-                                  cudaStream_t s);
+                                  const float* W, const float2* Wp, int k_lo, int D, int64_t B, int64_t N, double fs,
+                                  float* y, cudaStream_t s);
 // yy: E doubles of scratch for the per-event sum of |Y|^2 over the band.
 cudaError_t launch_loglike_full(const float* ydata, const float2* Ydata, const float* W, const DrawCoef* coef,
                                 const int64_t* ev_off, double* yy, int64_t E, int D, int64_t N, int k_lo, int64_t S,

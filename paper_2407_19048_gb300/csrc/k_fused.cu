@@ -6,122 +6,243 @@
 // complex points each; the waveform of a bin is evaluated once and projected onto
 // all D detectors, so the frequency-domain stage costs one phase/amplitude
 // evaluation per bin plus one complex exponential per detector.
+#include "fft16.cuh"
 #include "waveform.cuh"
 
 namespace gwx {
 
 cudaError_t init_tables_fused() { return fill_tables_for_this_tu(); }
 
-// Frequency-domain step of one bin pair (k, n-k), 0 < k < n/2, for every detector:
-// unpack the real spectra, add the projected waveform, whiten, repack.
-__device__ __forceinline__ void fd_pair(float2* sm, int n, int D, int k, const DrawCoef& c, int k_lo,
-                                        const float* __restrict__ W, int64_t F, float inv_n, int logN) {
+// Frequency-domain step of one real-FFT bin pair (k, nk = n - k), 0 < k < n, k != n/2,
+// done on the half-length transform Z directly.  Whitening (s = W/n) in that domain is
+//   Z'_k = alpha_k Z_k + i beta_k conj(Z_nk)   (packed filter table Wp = (alpha, beta));
+// the injected strain H (continuous FT times fs) adds
+//   Z'_k += p s_k H_k + q s_nk conj(H_nk),  p = (1 + i conj w)/2, q = (1 - i conj w)/2,
+// w = e^{-2 pi i k/N}, and the mirrored terms with w_nk = -conj(w) for Z'_nk.
+// (tk, ak), (tnk, ank): waveform phase in turns and amplitude factor k^-7/6 of the two
+// bins (ak = 0 outside the support).
+template <int LOGN>
+__device__ __forceinline__ void fd_pair(float2& zk, float2& znk, int k, float tk, float ak, float tnk, float ank,
+                                        float2 gd, unsigned long long nu, const float* __restrict__ Wd,
+                                        const float2* __restrict__ Wpd, float inv_n) {
+  constexpr int n = 1 << LOGN;
   const int nk = n - k;
-  const float2 wk = pack_twiddle(k, logN);
-  float ak = 0.f, tk = 0.f, ank = 0.f, tnk = 0.f;
-  if (k >= k_lo && k <= c.kcut) tk = waveform_turns(c, k, ak);
-  if (nk != k && nk >= k_lo && nk <= c.kcut) tnk = waveform_turns(c, nk, ank);
-  for (int d = 0; d < D; ++d) {
-    float2* z = sm + d * n;
-    float2 xk, xnk;
-    unpack_pair(z[sw(k)], z[sw(nk)], wk, xk, xnk);
-    const float2 gd = make_float2(c.g[d].x, c.g[d].z);
-    if (ak != 0.f) xk = cadd(xk, cscale(cmul(gd, expm2pi(tk + lin_turns(c.nu[d], k))), ak));
-    if (ank != 0.f) xnk = cadd(xnk, cscale(cmul(gd, expm2pi(tnk + lin_turns(c.nu[d], nk))), ank));
-    const float* Wd = W + (int64_t)d * F;
-    float2 zk, znk;
-    pack_pair(cscale(xk, __ldg(&Wd[k]) * inv_n), cscale(xnk, __ldg(&Wd[nk]) * inv_n), wk, zk, znk);
-    z[sw(k)] = zk;
-    if (nk != k) z[sw(nk)] = znk;
+  const float2 fk = __ldg(&Wpd[k]), fnk = __ldg(&Wpd[nk]);
+  const float2 a = zk, b = znk;
+  zk = make_float2(fmaf(fk.x, a.x, fk.y * b.y), fmaf(fk.x, a.y, fk.y * b.x));
+  znk = make_float2(fmaf(fnk.x, b.x, fnk.y * a.y), fmaf(fnk.x, b.y, fnk.y * a.x));
+  if (ak != 0.f || ank != 0.f) {
+    float2 hk = make_float2(0.f, 0.f), hnk = hk;
+    if (ak != 0.f) hk = cscale(cmul(gd, expm2pi(tk + lin_turns(nu, k))), ak * __ldg(&Wd[k]) * inv_n);
+    if (ank != 0.f) hnk = cscale(cmul(gd, expm2pi(tnk + lin_turns(nu, nk))), ank * __ldg(&Wd[nk]) * inv_n);
+    // hk, hnk now carry s_k and s_nk
+    const float2 w = pack_twiddle(k, LOGN + 1);
+    const float pr = 0.5f * (1.0f + w.y), qr = 0.5f * (1.0f - w.y), wi = 0.5f * w.x;
+    // Z'_k += p hk + q conj(hnk), p = (pr, wi), q = (qr, -wi)
+    zk.x += pr * hk.x - wi * hk.y + qr * hnk.x - wi * hnk.y;
+    zk.y += pr * hk.y + wi * hk.x - qr * hnk.y - wi * hnk.x;
+    // Z'_nk += p' hnk + q' conj(hk), p' = (pr, -wi), q' = (qr, wi)
+    znk.x += pr * hnk.x + wi * hnk.y + qr * hk.x + wi * hk.y;
+    znk.y += pr * hnk.y - wi * hnk.x - qr * hk.y + wi * hk.x;
   }
 }
 
+// The bin k = n/2, which pairs with itself (w = -i, so p = 0 and q = 1).
 template <int LOGN>
-__global__ void __launch_bounds__((1 << LOGN) / 8, LOGN >= 13 ? 1 : 2)
+__device__ __forceinline__ void fd_half(float2& z, float t, float a, float2 gd, unsigned long long nu,
+                                        const float* __restrict__ Wd, const float2* __restrict__ Wpd, float inv_n) {
+  constexpr int h = (1 << LOGN) / 2;
+  const float2 f = __ldg(&Wpd[h]);
+  const float2 v = z;
+  z = make_float2(fmaf(f.x, v.x, f.y * v.y), fmaf(f.x, v.y, f.y * v.x));
+  if (a != 0.f) {
+    const float2 hh = cscale(cmul(gd, expm2pi(t + lin_turns(nu, h))), a * __ldg(&Wd[h]) * inv_n);
+    z.x += hh.x;
+    z.y -= hh.y;
+  }
+}
+
+// DC and Nyquist (carried together in element 0); the waveform is zero there.
+__device__ __forceinline__ void fd_dc(float2& z0, const float2* __restrict__ Wpd) {
+  const float2 f = __ldg(&Wpd[0]);
+  const float2 v = z0;
+  z0 = make_float2(fmaf(f.x, v.x, f.y * v.y), fmaf(f.y, v.x, f.x * v.y));
+}
+
+// Waveform phase (turns) and amplitude factor of bin k; amplitude 0 outside the support.
+__device__ __forceinline__ void wave_bin(const DrawCoef& c, int k, int k_lo, float& t, float& a) {
+  t = 0.f;
+  a = 0.f;
+  if (k >= k_lo && k <= c.kcut) t = waveform_turns(c, k, a);
+}
+
+// One block per draw (persistent over draws), n/16 threads.  The D windows go
+// through one n-point shared buffer in turn; the waveform values of the bins a
+// thread owns are computed once per draw and shared by the detectors.
+template <int LOGN>
+__global__ void __launch_bounds__((1 << LOGN) / 16, LOGN >= 13 ? 1 : 2)
     k_simulate(const DrawCoef* __restrict__ coef, const float* __restrict__ noise, int64_t L,
-               const int64_t* __restrict__ offsets, const float* __restrict__ W, int k_lo, int D, int64_t B,
-               float* __restrict__ y) {
-  constexpr int n = 1 << LOGN;
+               const int64_t* __restrict__ offsets, const float* __restrict__ W, const float2* __restrict__ Wp,
+               int k_lo, int D, int64_t B, float* __restrict__ y) {
+  using PL = Plan16<LOGN>;
+  constexpr int n = PL::n, T = PL::T, RL = PL::RL, NB = PL::NB, SLOTS = PL::SLOTS, P = PL::P;
   constexpr int64_t N = 2 * n;
   constexpr int64_t F = n + 1;
-  constexpr int NT = n / 8;
   extern __shared__ float2 sm[];
   __shared__ DrawCoef sc;
+  float2 (*wv)[T] = reinterpret_cast<float2 (*)[T]>(sm + n);   // 16 x T waveform values
+#define WIDX(s, h, r) (((s) * 2 + (h)) * RL + (r))
   const int t = threadIdx.x;
+  const int lane = t & 31;
+  const uint32_t x = smem_addr(sm);
   const float inv_n = 1.0f / (float)n;
   for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
-    if (t < (int)(sizeof(DrawCoef) / 16))
-      reinterpret_cast<int4*>(&sc)[t] = __ldg(reinterpret_cast<const int4*>(coef + b) + t);
+    for (int i = t; i < (int)(sizeof(DrawCoef) / 16); i += T)
+      reinterpret_cast<int4*>(&sc)[i] = __ldg(reinterpret_cast<const int4*>(coef + b) + i);
     int64_t off = __ldg(&offsets[b]);
     off = off < 0 ? 0 : (off > L - N ? L - N : off);   // keep a bad offset inside the stretch
-    // Crop: aligned float2 loads of (x[a + 2m], x[a + 2m + 1]) with a = off rounded
-    // down to even; for an odd offset each value pair is (own .y, next lane's .x).
-    const int64_t a = off & ~(int64_t)1;
+    const int64_t a0 = off & ~(int64_t)1;
     const bool odd = (off & 1) != 0;
-    const int lane = t & 31;
-    for (int d = 0; d < D; ++d) {
-      const float* row = noise + (int64_t)d * L + a;
-      const float2* row2 = reinterpret_cast<const float2*>(row);
-      float2* z = sm + d * n;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int m = t + i * NT;
-        const float2 p = __ldg(&row2[m]);
-        float2 v = p;
-        if (odd) {
-          float nx;
-          if constexpr (NT >= 32) {   // full warps: the next pair comes from lane + 1
-            nx = __shfl_down_sync(0xffffffffu, p.x, 1);
-            if (lane == 31) nx = __ldg(&row[2 * m + 2]);
-          } else {
-            nx = __ldg(&row[2 * m + 2]);
-          }
-          v = make_float2(p.y, nx);
-        }
-        z[sw(m)] = v;
-      }
-    }
     __syncthreads();
-    for (int d = 0; d < D; ++d) fft_smem<LOGN, false>(sm + d * n, t);
     const DrawCoef& c = sc;
-#pragma unroll 1
-    for (int i = 0; i < 4; ++i) {
-      const int k = t + i * NT;
-      if (k == 0) {   // DC and Nyquist: real parts, both outside the whitening band in practice
-        for (int d = 0; d < D; ++d) {
-          const float2 z0 = sm[d * n];
-          const float* Wd = W + (int64_t)d * F;
-          const float y0 = (z0.x + z0.y) * __ldg(&Wd[0]) * inv_n, yn = (z0.x - z0.y) * __ldg(&Wd[n]) * inv_n;
-          sm[d * n] = make_float2(0.5f * (y0 + yn), 0.5f * (y0 - yn));
-        }
-      } else {
-        fd_pair(sm, n, D, k, c, k_lo, W, F, inv_n, LOGN + 1);
-      }
-    }
-    if (t == 0) fd_pair(sm, n, D, n / 2, c, k_lo, W, F, inv_n, LOGN + 1);
-    __syncthreads();
-    for (int d = 0; d < D; ++d) fft_smem<LOGN, true>(sm + d * n, t);
-    for (int d = 0; d < D; ++d) {
-      float2* out = reinterpret_cast<float2*>(y + (b * D + d) * N);
-      const float2* z = sm + d * n;
+
+    // waveform values (turns, amplitude factor) of the 16 bins this thread owns in the
+    // short-radix pass, kept in shared memory as wv[v][t] for the D detectors
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int m = t + i * NT;
-        __stcs(&out[m], z[sw(m)]);
+    for (int s = 0; s < SLOTS; ++s) {
+      const int p = t + s * T;
+      const int jA = p, jB = p ? NB - p : NB / 2;
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        float tt, aa;
+        wave_bin(c, jA + NB * r, k_lo, tt, aa);
+        wv[WIDX(s, 0, r)][t] = make_float2(tt, aa);
+        wave_bin(c, jB + NB * r, k_lo, tt, aa);
+        wv[WIDX(s, 1, r)][t] = make_float2(tt, aa);
       }
     }
-    __syncthreads();
+
+    for (int d = 0; d < D; ++d) {
+      // forward pass 1 (radix 8, Ns = 1), input straight from the background crop
+      {
+        const float* row = noise + (int64_t)d * L + a0;
+        const float2* row2 = reinterpret_cast<const float2*>(row);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          const int j = t + i * T;
+          float2 v[8];
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            const int m = j + r * (n / 8);
+            const float2 q = __ldg(&row2[m]);
+            v[r] = q;
+            if (odd) {   // the window starts at an odd sample: pair (own .y, next pair's .x)
+              float nx;
+              if constexpr (T >= 32) {
+                nx = __shfl_down_sync(0xffffffffu, q.x, 1);
+                if (lane == 31) nx = __ldg(&row[2 * m + 2]);
+              } else {
+                nx = __ldg(&row[2 * m + 2]);
+              }
+              v[r] = make_float2(q.y, nx);
+            }
+          }
+          dft8<false>(v);
+          store_pass<8, 1>(x, j, v);
+        }
+      }
+      __syncthreads();
+      FwdMiddle<LOGN, 1, P - 2>::run(x, t);
+
+      // last forward pass (radix RL, Ns = NB) on butterfly pairs, frequency-domain
+      // step and first inverse pass, all in registers
+      const float2 gd = make_float2(c.g[d].x, c.g[d].z);
+      const unsigned long long nu = c.nu[d];
+      const float* Wd = W + (int64_t)d * F;
+      const float2* Wpd = Wp + (int64_t)d * n;
+      float2 vA[SLOTS][RL], vB[SLOTS][RL];
+#pragma unroll
+      for (int s = 0; s < SLOTS; ++s) {
+        const int p = t + s * T;
+        const int jA = p, jB = p ? NB - p : NB / 2;
+        load_strided<RL, NB>(x, jA, vA[s]);
+        load_strided<RL, NB>(x, jB, vB[s]);
+        if constexpr (NB > 1) {
+          float2 w[RL];
+          pass_twiddles<RL, NB, false>(jA, w);
+#pragma unroll
+          for (int r = 1; r < RL; ++r) vA[s][r] = cmul(vA[s][r], w[r]);
+          pass_twiddles<RL, NB, false>(jB, w);
+#pragma unroll
+          for (int r = 1; r < RL; ++r) vB[s][r] = cmul(vB[s][r], w[r]);
+        }
+        dftR<RL, false>(vA[s]);
+        dftR<RL, false>(vB[s]);
+        // now vA[s][r] = Z[jA + NB r], vB[s][r] = Z[jB + NB r]
+        if (p != 0) {
+#pragma unroll
+          for (int r = 0; r < RL; ++r) {
+            const float2 ea = wv[WIDX(s, 0, r)][t], eb = wv[WIDX(s, 1, RL - 1 - r)][t];
+            fd_pair<LOGN>(vA[s][r], vB[s][RL - 1 - r], jA + NB * r, ea.x, ea.y, eb.x, eb.y, gd, nu, Wd, Wpd, inv_n);
+          }
+        } else {
+          fd_dc(vA[s][0], Wpd);
+          const float2 eh = wv[WIDX(s, 0, RL / 2)][t];
+          fd_half<LOGN>(vA[s][RL / 2], eh.x, eh.y, gd, nu, Wd, Wpd, inv_n);
+#pragma unroll
+          for (int r = 1; r < RL / 2; ++r) {
+            const float2 ea = wv[WIDX(s, 0, r)][t], eb = wv[WIDX(s, 0, RL - r)][t];
+            fd_pair<LOGN>(vA[s][r], vA[s][RL - r], NB * r, ea.x, ea.y, eb.x, eb.y, gd, nu, Wd, Wpd, inv_n);
+          }
+#pragma unroll
+          for (int r = 0; r < RL / 2; ++r) {
+            const float2 ea = wv[WIDX(s, 1, r)][t], eb = wv[WIDX(s, 1, RL - 1 - r)][t];
+            fd_pair<LOGN>(vB[s][r], vB[s][RL - 1 - r], NB / 2 + NB * r, ea.x, ea.y, eb.x, eb.y, gd, nu, Wd, Wpd, inv_n);
+          }
+        }
+        dftR<RL, true>(vA[s]);
+        dftR<RL, true>(vB[s]);
+      }
+      __syncthreads();   // every read of the last forward pass precedes the writes below
+#pragma unroll
+      for (int s = 0; s < SLOTS; ++s) {
+        const int p = t + s * T;
+        store_pass<RL, 1>(x, p, vA[s]);
+        store_pass<RL, 1>(x, p ? NB - p : NB / 2, vB[s]);
+      }
+      __syncthreads();
+      InvMiddle<LOGN, 1, P - 2, RL>::run(x, t);
+
+      // last inverse pass (radix 8, Ns = n/8), output straight to the whitened batch
+      float2* out = reinterpret_cast<float2*>(y + (b * D + d) * N);
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int j = t + i * T;
+        float2 v[8];
+        load_strided<8, n / 8>(x, j, v);
+        float2 w[8];
+        pass_twiddles<8, n / 8, true>(j, w);
+#pragma unroll
+        for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], w[r]);
+        dft8<true>(v);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) __stcs(&out[j + r * (n / 8)], v[r]);
+      }
+      __syncthreads();
+    }
   }
+#undef WIDX
 }
 
 cudaError_t launch_simulate_fused(const DrawCoef* coef, const float* noise, int64_t L, const int64_t* offsets,
-                                  const float* W, int k_lo, int D, int64_t B, int64_t N, double fs, float* y,
-                                  cudaStream_t s) {
+                                  const float* W, const float2* Wp, int k_lo, int D, int64_t B, int64_t N, double fs,
+                                  float* y, cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
-  return dispatch_log<4, 13>(ilog2_exact(N / 2), [&](auto cst) {
+  return dispatch_log<7, 13>(ilog2_exact(N / 2), [&](auto cst) {
     constexpr int LG = decltype(cst)::value;
-    constexpr int NT = (1 << LG) / 8;
-    const size_t smem = (size_t)D * (1 << LG) * sizeof(float2);
+    constexpr int NT = Plan16<LG>::T;
+    // one window at a time plus 16 waveform values per thread
+    const size_t smem = (size_t)(1 << LG) * sizeof(float2) + (size_t)16 * NT * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(k_simulate<LG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
@@ -132,7 +253,7 @@ cudaError_t launch_simulate_fused(const DrawCoef* coef, const float* noise, int6
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int64_t grid = (int64_t)sms * per_sm;
     if (grid > B) grid = B;
-    k_simulate<LG><<<(unsigned)grid, NT, smem, s>>>(coef, noise, L, offsets, W, k_lo, D, B, y);
+    k_simulate<LG><<<(unsigned)grid, NT, smem, s>>>(coef, noise, L, offsets, W, Wp, k_lo, D, B, y);
     return cudaGetLastError();
   });
 }

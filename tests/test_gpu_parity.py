@@ -290,6 +290,22 @@ def test_simulate_equals_whiten_of_inject(gwx):
     assert np.abs(a - b).max() <= 1e-4 * rms(b)
 
 
+def test_split_prepare_and_simulate_on_two_streams(gwx):
+    """prepare_batch on a side stream + simulate_prepared (the Simulator's step) gives
+    the same batch as the single simulate_batch call."""
+    import paper_2407_19048_gb300.simulator as S
+    wl = workloads.workload("small", B=96)
+    sim = S.Simulator(wl)
+    y1, th1, off1 = [t.clone() for t in sim.step(11)]
+    sim2 = S.Simulator(wl)
+    sim2.background(11)
+    sim2.simulate(11)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(host(off1), host(sim2.offsets))
+    np.testing.assert_array_equal(host(th1), host(sim2.theta))
+    np.testing.assert_array_equal(host(y1), host(sim2.y))
+
+
 @pytest.mark.parametrize("B", [0, 1, 3, 1000])
 def test_simulate_batch_ragged_sizes(gwx, B):
     wl = workloads.workload("small")
