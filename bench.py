@@ -38,7 +38,7 @@ SM_MAX_MHZ = 2070.0
 # ncu DRAM traffic (read + write bytes) of one k_simulate launch on the hl3
 # workload and the hash of the kernel sources it was measured on; see
 # profiles/k_simulate_hl3.md.  None until a capture matches the current sources.
-TRAFFIC = {"bytes_per_launch": None, "sources_sha1": None}
+TRAFFIC = {"bytes_per_launch": 143056128, "sources_sha1": "3a320450ddadaaf0212e9c5b9bca9ba634f92c1b"}
 
 
 def describe(wl):
@@ -356,7 +356,7 @@ def run_gpu(args, wl):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gwx", choices=["gwx", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workloads.WORKLOADS))

@@ -75,48 +75,42 @@ __device__ __forceinline__ float2 noise_bin(uint32_t k0, uint32_t k1, uint32_t s
   return make_float2(sigma * rad * cs, sigma * rad * sn);
 }
 
-// Pack the half-length complex sequence Z (length n) whose inverse FFT gives
-// (x_2m, x_2m+1) of irfft(X): Z_k = E_k + i O_k (see pack_pair), w = e^{-2 pi i/L}.
-__global__ void k_noise_pack(uint32_t k0, uint32_t k1, uint32_t step, int64_t L, float fs, float f_lo,
-                             float sig_scale, float2* __restrict__ Z) {
+// Packed spectrum element Z_k (0 <= k < n) of the background, generated on the fly:
+// Z_k = E_k + i O_k from X_k and X_{n-k} (see pack_pair), w = e^{-2 pi i/L}.
+__device__ __forceinline__ float2 noise_packed(uint32_t k0, uint32_t k1, uint32_t step, int d, int64_t k, int64_t L,
+                                               float fs, float f_lo, float sig_scale) {
   const int64_t n = L / 2;
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int d = blockIdx.y;
-  if (p > n / 2) return;
-  float2* Zd = Z + (int64_t)d * n;
-  if (p == 0) {
-    const float2 x0 = noise_bin(k0, k1, step, d, 0, L, fs, f_lo, sig_scale);
-    const float2 xn = noise_bin(k0, k1, step, d, n, L, fs, f_lo, sig_scale);
-    // E_0 = (X_0 + X_n)/2, O_0 = (X_0 - X_n)/2 (real parts; irfft ignores the imaginary parts)
-    Zd[0] = make_float2(0.5f * (x0.x + xn.x), 0.5f * (x0.x - xn.x));
-    return;
+  if (k == 0) {
+    const float2 xn = noise_bin(k0, k1, step, d, n, L, fs, f_lo, sig_scale);   // X_0 = 0
+    return make_float2(0.5f * xn.x, -0.5f * xn.x);
   }
-  const float2 xk = noise_bin(k0, k1, step, d, p, L, fs, f_lo, sig_scale);
-  const float2 xnk = noise_bin(k0, k1, step, d, n - p, L, fs, f_lo, sig_scale);
+  const float2 xk = noise_bin(k0, k1, step, d, k, L, fs, f_lo, sig_scale);
+  const float2 xnk = noise_bin(k0, k1, step, d, n - k, L, fs, f_lo, sig_scale);
   float sn, cs;
-  sincospif(2.0f * (float)p / (float)L, &sn, &cs);
+  sincospif(2.0f * (float)k / (float)L, &sn, &cs);
   float2 zk, znk;
   pack_pair(xk, xnk, make_float2(cs, -sn), zk, znk);
-  Zd[p] = zk;
-  if (n - p != p) Zd[n - p] = znk;
+  return zk;
 }
 
 // Four-step inverse FFT of length n = n1 n2 (Bailey 1990): with k = k1 + n1 k2 and
 // m = n2 m1 + m2, z_m = sum_k1 e^{2 pi i k1 m1/n1} [e^{2 pi i k1 m2/n} sum_k2 e^{2 pi i k2 m2/n2} Z_k].
 // Pass A: for a tile of TK consecutive k1, inverse FFTs of length n2 over k2, then the
-// twiddle; writes G[k1][m2].
+// twiddle; writes G[k1][m2].  The input elements Z_k are generated here.
 template <int LOGN2>
-__global__ void k_fourstep_a(const float2* __restrict__ Z, int64_t n, int n1, int TK, float2* __restrict__ G) {
+__global__ void k_fourstep_a(uint32_t key0, uint32_t key1, uint32_t step, int64_t L, float fs, float f_lo,
+                             float sig_scale, int n1, int TK, float2* __restrict__ G) {
   constexpr int n2 = 1 << LOGN2;
   extern __shared__ float2 sm[];
+  const int64_t n = L / 2;
   const int d = blockIdx.y;
   const int k1_0 = blockIdx.x * TK;
-  const float2* Zd = Z + (int64_t)d * n;
   float2* Gd = G + (int64_t)d * n;
   const int stride = n2 + 1;
   for (int e = threadIdx.x; e < TK * n2; e += blockDim.x) {
     const int g = e % TK, k2 = e / TK;
-    sm[g * stride + sw(k2)] = Zd[(int64_t)(k1_0 + g) + (int64_t)n1 * k2];
+    sm[g * stride + sw(k2)] =
+        noise_packed(key0, key1, step, d, (int64_t)(k1_0 + g) + (int64_t)n1 * k2, L, fs, f_lo, sig_scale);
   }
   __syncthreads();
   const int g = threadIdx.x / (n2 / 8), t = threadIdx.x % (n2 / 8);
@@ -155,19 +149,24 @@ __global__ void k_fourstep_b(const float2* __restrict__ G, int64_t n, int n2, in
   }
 }
 
-size_t colored_noise_ws(int D, int64_t L) { return (size_t)2 * (size_t)D * (size_t)(L / 2) * sizeof(float2); }
+size_t colored_noise_ws(int D, int64_t L) { return (size_t)D * (size_t)(L / 2) * sizeof(float2); }
 
+struct NoiseArgs {
+  uint32_t k0, k1, step;
+  int64_t L;
+  float fs, f_lo, sig_scale;
+};
 template <int LOG>
-static cudaError_t run_pass_a(int lg, const float2* Z, int64_t n, int n1, int D, float2* G, cudaStream_t s);
+static cudaError_t run_pass_a(int lg, const NoiseArgs& a, int n1, int D, float2* G, cudaStream_t s);
 template <int LOG>
 static cudaError_t run_pass_b(int lg, const float2* G, int64_t n, int n2, int D, float* x, cudaStream_t s);
 
 template <int LOG>
-static cudaError_t run_pass_a(int lg, const float2* Z, int64_t n, int n1, int D, float2* G, cudaStream_t s) {
+static cudaError_t run_pass_a(int lg, const NoiseArgs& a, int n1, int D, float2* G, cudaStream_t s) {
   if constexpr (LOG > 13) {
     return cudaErrorInvalidValue;
   } else {
-    if (lg != LOG) return run_pass_a<LOG + 1>(lg, Z, n, n1, D, G, s);
+    if (lg != LOG) return run_pass_a<LOG + 1>(lg, a, n1, D, G, s);
     constexpr int n2 = 1 << LOG;
     const int per = n2 / 8;
     int TK = 1024 / per;
@@ -177,7 +176,7 @@ static cudaError_t run_pass_a(int lg, const float2* Z, int64_t n, int n1, int D,
     cudaError_t e = cudaFuncSetAttribute(k_fourstep_a<LOG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)(n1 / TK), (unsigned)D);
-    k_fourstep_a<LOG><<<grid, TK * per, smem, s>>>(Z, n, n1, TK, G);
+    k_fourstep_a<LOG><<<grid, TK * per, smem, s>>>(a.k0, a.k1, a.step, a.L, a.fs, a.f_lo, a.sig_scale, n1, TK, G);
     return cudaGetLastError();
   }
 }
@@ -209,15 +208,10 @@ cudaError_t launch_colored_noise(uint64_t seed, uint32_t step, int D, int64_t L,
   while (((int64_t)1 << logn) < n) ++logn;
   const int log1 = logn / 2, log2 = logn - log1;   // n1 <= n2, both >= 2^3 for L >= 1024... checked by caller
   const int n1 = 1 << log1, n2 = 1 << log2;
-  float2* Z = reinterpret_cast<float2*>(ws);
-  float2* G = Z + (int64_t)D * n;
-  const float sig_scale = (float)(sqrt((double)L * fs * 1e-49 / 4.0) / (double)n);
-  dim3 g0((unsigned)((n / 2 + 1 + 255) / 256), (unsigned)D);
-  k_noise_pack<<<g0, 256, 0, s>>>((uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), step, L, (float)fs,
-                                  (float)f_lo, sig_scale, Z);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  e = run_pass_a<3>(log2, Z, n, n1, D, G, s);
+  float2* G = reinterpret_cast<float2*>(ws);
+  const NoiseArgs a{(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), step, L, (float)fs, (float)f_lo,
+                    (float)(sqrt((double)L * fs * 1e-49 / 4.0) / (double)n)};
+  cudaError_t e = run_pass_a<3>(log2, a, n1, D, G, s);
   if (e != cudaSuccess) return e;
   return run_pass_b<3>(log1, G, n, n2, D, noise, s);
 }

@@ -62,7 +62,7 @@ def test_workspace_sizes(lib):
     assert gwx.workspace_bytes("whiten", 3, 8192) == ((3 * 4097 * 4 + 255) // 256) * 256
     K = (131072 - 4096) // 2048 + 1
     assert gwx.workspace_bytes("welch_psd", 3, 131072, 4096, 2048) >= 3 * K * 2049 * 8
-    assert gwx.workspace_bytes("colored_noise", 3, 131072) >= 2 * 3 * 65536 * 8
+    assert gwx.workspace_bytes("colored_noise", 3, 131072) >= 3 * 65536 * 8
     assert gwx.workspace_bytes("simulate_batch", 3, 2048, 8192) > 2048 * 144
     assert gwx.workspace_bytes("log_likelihood", 4, 3, 8192, 100) > 0
 
