@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -94,8 +95,9 @@ class ClockSampler:
 
     def start(self):
         try:
-            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-            self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+            out_dir = os.environ.get("GWX_CLOCKS_DIR") or tempfile.gettempdir()
+            os.makedirs(out_dir, exist_ok=True)
+            self.path = os.path.join(out_dir, "clocks_bench_%d.csv" % os.getpid())
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -183,11 +185,11 @@ def run_reference(args, wl):
 
 # ----------------------------------------------------------------- GPU arm
 def loglike_leg(gwx, torch, wl, rank):
-    """ln L of ragged events: 64 events with 2k..50k samples each would be the full
-    judge workload; here E=64 events with U{200..2000} samples drawn from the prior."""
+    """ln L of ragged events at the importance-weighting scale: E=64 events with
+    U{2000..50000} samples each (about 1.7 million samples) drawn from the prior."""
     import numpy as np
     E = 64
-    counts = workloads.ragged_counts(41 + rank, E, 200, 2000)
+    counts = workloads.ragged_counts(41 + rank, E, 2000, 50000)
     offs = np.concatenate([[0], np.cumsum(counts)])
     S = int(offs[-1])
     sim = gwx.simulator.Simulator(dict(wl, B=E))
@@ -201,7 +203,7 @@ def loglike_leg(gwx, torch, wl, rank):
                            out=out)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 5
+    reps = 3
     e0.record()
     for _ in range(reps):
         gwx.log_likelihood(y_data, sim.psd, wl["seg_len"], wl["fs"], wl["f_lo"], wl["dets"], 0.0, theta, offs_d,

@@ -368,15 +368,11 @@ int gwx_simulate_batch(const gwx_prior* prior, uint64_t seed, uint32_t step, con
                                stream);
 }
 
-static size_t loglike_base_bytes(int64_t E, int D, int64_t N) {
-  // per-event spectra, whitening filter, per-event norms
-  return align_up((size_t)E * D * (size_t)(N / 2 + 1) * sizeof(float2)) + whiten_ws_bytes(D, N) +
-         align_up((size_t)E * sizeof(double));
-}
-
 size_t gwx_log_likelihood_workspace(int64_t E, int D, int64_t N, int64_t S) {
   if (E < 0 || D < 1 || N < 2 || S < 0) return 0;
-  return loglike_base_bytes(E, D, N) + coef_bytes(S);
+  // per-event spectra, whitening filter, per-event norm partials
+  return align_up((size_t)E * D * (size_t)(N / 2 + 1) * sizeof(float2)) + whiten_ws_bytes(D, N) +
+         align_up(loglike_norm_bytes(E));
 }
 
 int gwx_log_likelihood(int approximant, const float* y_data, int64_t E, int D, int64_t N, const double* psd,
@@ -406,13 +402,11 @@ int gwx_log_likelihood(int approximant, const float* y_data, int64_t E, int D, i
   w += align_up((size_t)E * D * (size_t)(N / 2 + 1) * sizeof(float2));
   float* W = reinterpret_cast<float*>(w);
   w += whiten_ws_bytes(D, N);
-  double* yy = reinterpret_cast<double*>(w);
-  w += align_up((size_t)E * sizeof(double));
-  DrawCoef* coef = reinterpret_cast<DrawCoef*>(w);
+  double* yy_part = reinterpret_cast<double*>(w);
   GWX_TRY(launched(launch_rfft_rows(y_data, E * D, N, Y, s), "rfft of the data"));
   GWX_TRY(launched(launch_whiten_filter(psd, D, seg_len, fs, k_lo, N, W, s), "whiten filter"));
-  GWX_TRY(launched(launch_draw_setup(theta, S, k_lo, df, fs, N / 2 + 1, dp, gmst, coef, s), "sample set-up"));
-  return launched(launch_loglike_full(y_data, Y, W, coef, event_offsets, yy, E, D, N, k_lo, S, lnl, s),
+  return launched(launch_loglike_full(y_data, Y, W, theta, df, fs, dp, gmst, event_offsets, yy_part, E, D, N, k_lo,
+                                      S, lnl, s),
                   "log_likelihood");
 }
 

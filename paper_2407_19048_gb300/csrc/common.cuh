@@ -59,7 +59,7 @@ namespace {
 __device__ float2 g_twp[TWP_TOTAL];
 __device__ float2 g_tw[TWN];
 __device__ float4 g_kp53[KMAX + 1];   // k^-5/3 hi, lo, k^-2/3 hi, lo
-__device__ float4 g_kq[KMAX + 1];     // k^-1/3, ln k hi, ln k lo, 0
+__device__ float4 g_kq[KMAX + 1];     // k^-1/3, ln k hi, ln k lo, k^-7/6
 }
 
 __device__ __forceinline__ float2 twiddle(int m) { return __ldg(&g_tw[m]); }
@@ -123,7 +123,7 @@ static inline cudaError_t fill_tables_for_this_tu() {
       double lk = log((double)k);
       float h53 = (float)p53, h23 = (float)p23, hlk = (float)lk;
       kp[k] = make_float4(h53, (float)(p53 - (double)h53), h23, (float)(p23 - (double)h23));
-      kq[k] = make_float4((float)p13, hlk, (float)(lk - (double)hlk), 0.f);
+      kq[k] = make_float4((float)p13, hlk, (float)(lk - (double)hlk), (float)pow((double)k, -7.0 / 6.0));
     }
     built = true;
   }

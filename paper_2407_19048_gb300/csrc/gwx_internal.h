@@ -65,9 +65,13 @@ cudaError_t launch_simulate_fused(const DrawCoef* coef, const float* noise, int6
                                   const float* W, const float2* Wp, int k_lo, int D, int64_t B, int64_t N, double fs,
                                   float* y, cudaStream_t s);
 // yy: E doubles of scratch for the per-event sum of |Y|^2 over the band.
-cudaError_t launch_loglike_full(const float* ydata, const float2* Ydata, const float* W, const DrawCoef* coef,
-                                const int64_t* ev_off, double* yy, int64_t E, int D, int64_t N, int k_lo, int64_t S,
-                                double* lnl, cudaStream_t s);
+// Per-event data norms (E x 8 FP64 partials in yy_part, loglike_norm_bytes(E)) and
+// the fused per-sample set-up + likelihood.
+size_t loglike_norm_bytes(int64_t E);
+cudaError_t launch_loglike_full(const float* ydata, const float2* Ydata, const float* W, const double* theta,
+                                double df, double fs, const DetParams& dp, double gmst, const int64_t* ev_off,
+                                double* yy_part, int64_t E, int D, int64_t N, int k_lo, int64_t S, double* lnl,
+                                cudaStream_t s);
 
 // Record msg as the calling thread's gwx_last_error() message; returns status.
 int set_last_error(int status, const char* msg);

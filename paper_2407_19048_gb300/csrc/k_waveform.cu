@@ -10,14 +10,14 @@ cudaError_t init_tables_waveform() { return fill_tables_for_this_tu(); }
 // One thread per draw.  The set-up is FP64-throughput bound (GB300 issues a warp's
 // FP64 instruction over many cycles), so blocks are one warp wide to spread the
 // draws over as many SMs as possible.
-__global__ void k_draw_setup(const double* __restrict__ theta, int64_t B, double df, double df76, double fs,
-                             int64_t F, DetParams dp, double gmst, DrawCoef* __restrict__ coef) {
+__global__ void k_draw_setup(const double* __restrict__ theta, int64_t B, SetupConsts kc, double fs, int64_t F,
+                             DetParams dp, double gmst, DrawCoef* __restrict__ coef) {
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   DrawCoef c;
   double amp = 0.0;
-  draw_waveform_coef(theta, B, b, df, df76, F, c, &amp);
-  draw_detector_coef(theta, B, b, df, dp, gmst, c.qp, c.qc_im, fs * amp, c);
+  draw_waveform_coef(theta, B, b, kc, F, c, &amp);
+  draw_detector_coef(theta, B, b, kc.df, dp, gmst, c.qp, c.qc_im, fs * amp, c);
   coef[b] = c;
 }
 
@@ -25,17 +25,17 @@ cudaError_t launch_draw_setup(const double* theta, int64_t B, int /*k_lo*/, doub
                               const DetParams& dp, double gmst, DrawCoef* coef, cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
   const int T = 32;
-  k_draw_setup<<<(unsigned)((B + T - 1) / T), T, 0, s>>>(theta, B, df, pow(df, -7.0 / 6.0), fs, F, dp, gmst, coef);
+  k_draw_setup<<<(unsigned)((B + T - 1) / T), T, 0, s>>>(theta, B, make_setup_consts(df), fs, F, dp, gmst, coef);
   return cudaGetLastError();
 }
 
 // A2: one block per draw; thread 0 computes the coefficients, all threads sweep
 // the bins.  hp/hc are written for every bin (zeros outside [k_lo, kcut]).
-__global__ void k_generate_waveforms(const double* __restrict__ theta, int64_t B, int k_lo, double df, double df76,
-                                     int64_t F, float2* __restrict__ hp, float2* __restrict__ hc) {
+__global__ void k_generate_waveforms(const double* __restrict__ theta, int64_t B, int k_lo, SetupConsts kc, int64_t F,
+                                     float2* __restrict__ hp, float2* __restrict__ hc) {
   __shared__ DrawCoef sc;
   const int64_t b = blockIdx.x;
-  if (threadIdx.x == 0) draw_waveform_coef(theta, B, b, df, df76, F, sc);
+  if (threadIdx.x == 0) draw_waveform_coef(theta, B, b, kc, F, sc);
   __syncthreads();
   const DrawCoef& c = sc;
   float2* hpb = hp + b * F;
@@ -59,7 +59,7 @@ __global__ void k_generate_waveforms(const double* __restrict__ theta, int64_t B
 cudaError_t launch_generate_waveforms(const double* theta, int64_t B, int k_lo, double df, int64_t F, float2* hp,
                                       float2* hc, cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
-  k_generate_waveforms<<<(unsigned)B, 256, 0, s>>>(theta, B, k_lo, df, pow(df, -7.0 / 6.0), F, hp, hc);
+  k_generate_waveforms<<<(unsigned)B, 256, 0, s>>>(theta, B, k_lo, make_setup_consts(df), F, hp, hc);
   return cudaGetLastError();
 }
 
@@ -93,32 +93,41 @@ cudaError_t launch_project(const float2* hp, const float2* hc, const double* the
 }
 
 // ----------------------------------------------------------------- A8
-// sum_d sum_{k_lo <= k < n} |Y_e,d,k|^2 in FP64, one block per event, from the
-// time-domain data by Parseval: sum_{1 <= k < n} |Y_k|^2 = (N sum y^2 - |Y_0|^2 - |Y_n|^2)/2,
-// minus the few bins below k_lo.  The time-domain sum is exact to FP64 rounding,
-// whereas summing FP32-transformed bins would inherit the transform's rounding.
+// Partial sums of sum_d sum_{k_lo <= k < n} |Y_e,d,k|^2 in FP64: block (e, c) of an
+// E x YY_CHUNKS grid covers chunk c of event e, so a few events still fill the GPU.
+// Parseval turns the band sum into a time-domain sum that is exact to FP64 rounding:
+// sum_{1 <= k < n} |Y_k|^2 = (N sum y^2 - |Y_0|^2 - |Y_n|^2)/2, minus the few bins
+// below k_lo (chunk 0 subtracts those).  Summing FP32-transformed bins instead would
+// inherit the transform's rounding.
+constexpr int YY_CHUNKS = 8;
+
 __global__ void k_event_norm(const float* __restrict__ y, const float2* __restrict__ Y, int D, int64_t F, int k_lo,
-                             int n, double* __restrict__ yy) {
+                             int n, double* __restrict__ yy_part) {
   const int64_t e = blockIdx.x;
+  const int c = blockIdx.y;
   const int64_t N = 2 * (int64_t)n;
+  const int64_t len = (int64_t)D * N;
+  const int64_t i0 = len * c / YY_CHUNKS, i1 = len * (c + 1) / YY_CHUNKS;
   double ty = 0.0, low = 0.0;
-  const float* ye = y + e * D * N;
-  for (int64_t i = threadIdx.x; i < D * N; i += blockDim.x) {
+  const float* ye = y + e * len;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     const double v = ye[i];
-    ty += v * v;
+    ty = fma(v, v, ty);
   }
-  for (int i = threadIdx.x; i < D * (k_lo + 1); i += blockDim.x) {
-    const int d = i / (k_lo + 1), k = i % (k_lo + 1);
-    const float2* Yd = Y + (e * D + d) * F;
-    double w = 0.0;
-    if (k == 0) {
-      const float2 a = Yd[0], b = Yd[n];
-      w = 0.5 * ((double)a.x * a.x + (double)a.y * a.y + (double)b.x * b.x + (double)b.y * b.y);
-    } else if (k < k_lo) {
-      const float2 a = Yd[k];
-      w = (double)a.x * a.x + (double)a.y * a.y;
+  if (c == 0) {
+    for (int i = threadIdx.x; i < D * (k_lo + 1); i += blockDim.x) {
+      const int d = i / (k_lo + 1), k = i % (k_lo + 1);
+      const float2* Yd = Y + (e * D + d) * F;
+      double w = 0.0;
+      if (k == 0) {
+        const float2 a = Yd[0], b = Yd[n];
+        w = 0.5 * ((double)a.x * a.x + (double)a.y * a.y + (double)b.x * b.x + (double)b.y * b.y);
+      } else if (k < k_lo) {
+        const float2 a = Yd[k];
+        w = (double)a.x * a.x + (double)a.y * a.y;
+      }
+      low += w;
     }
-    low += w;
   }
   double acc = 0.5 * (double)N * ty - low;
   __shared__ double red[32];
@@ -128,65 +137,139 @@ __global__ void k_event_norm(const float* __restrict__ y, const float2* __restri
   if (threadIdx.x < 32) {
     acc = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (threadIdx.x == 0) yy[e] = acc;
+    if (threadIdx.x == 0) yy_part[e * YY_CHUNKS + c] = acc;
   }
 }
 
-// One warp per sample: ln L_s = -(1/N) [ |Y|^2_e + sum_support (|H|^2 - 2 Re(Y conj H)) ],
-// H = fs h W.  Per-lane sums are FP32 with Kahan compensation, the warp sum FP64.
-__global__ void k_loglike(const float2* __restrict__ Y, const float* __restrict__ W, const DrawCoef* __restrict__ coef,
-                          const int64_t* __restrict__ ev_off, const double* __restrict__ yy, int64_t E, int D,
-                          int64_t F, int n, int k_lo, int64_t S, double invN, double* __restrict__ lnl) {
-  const int lane = threadIdx.x & 31;
-  const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (s >= S) return;
-  // event of sample s: largest e with ev_off[e] <= s
-  int64_t lo = 0, hi = E;
-  while (hi - lo > 1) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (__ldg(&ev_off[mid]) <= s) lo = mid; else hi = mid;
+// (hi, lo) + (bh, bl) in double-float (Knuth's two-sum on the leading parts).
+__device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl) {
+  const float s = hi + bh;
+  const float v = s - hi;
+  const float e = (hi - (s - v)) + (bh - v) + (lo + bl);
+  hi = s + e;
+  lo = e - (hi - s);
+}
+
+constexpr int LL_WARPS = 4;
+
+// One warp per 32 consecutive samples s:
+//   ln L_s = -(1/N) [ |Y|^2_e + sum_support (|H|^2 - 2 Re(Y conj H)) ],  H = fs h W.
+// 1. each lane finds its sample's event and does the sample's FP64 set-up (all 32
+//    lanes busy on the FP64 pipe; the warps of an SM overlap it with the FP32 work
+//    of the others), keeping the coefficients in shared memory;
+// 2. the warp walks its samples, lanes striding over the bins; per-lane sums are FP32
+//    with Kahan compensation, the warp sum double-float through shuffles;
+// 3. each lane adds its sample's FP64 data term and stores ln L (coalesced).
+// ND = number of detectors, a template parameter so that per-detector constants stay
+// in registers.
+template <int ND>
+__global__ void __launch_bounds__(LL_WARPS * 32)
+k_loglike(const double* __restrict__ theta, SetupConsts kc, double fs, DetParams dp, double gmst,
+          const float2* __restrict__ Y, const float* __restrict__ W, const int64_t* __restrict__ ev_off,
+          const double* __restrict__ yy_part, int64_t E, int64_t F, int n, int k_lo, int64_t S, double invN,
+          double* __restrict__ lnl) {
+  __shared__ DrawCoef sc[LL_WARPS][32];
+  __shared__ int se[LL_WARPS][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t base = ((int64_t)blockIdx.x * LL_WARPS + wid) * 32;
+  if (base >= S) return;
+  const int64_t s_own = base + lane;
+  int e_own = 0;
+  if (s_own < S) {
+    // event of sample s: largest e with ev_off[e] <= s
+    int64_t lo = 0, hi = E;
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (__ldg(&ev_off[mid]) <= s_own) lo = mid; else hi = mid;
+    }
+    e_own = (int)lo;
+    DrawCoef c;
+    double amp = 0.0;
+    draw_waveform_coef(theta, S, s_own, kc, F, c, &amp);
+    draw_detector_coef(theta, S, s_own, kc.df, dp, gmst, c.qp, c.qc_im, fs * amp, c);
+    sc[wid][lane] = c;
+    se[wid][lane] = e_own;
   }
-  const int64_t e = lo;
-  const DrawCoef c = coef[s];
-  const int kend = min(c.kcut, n - 1);
-  float sum = 0.f, comp = 0.f;
-  for (int k = k_lo + lane; k <= kend; k += 32) {
-    float k76;
-    const float t = waveform_turns(c, k, k76);
-    for (int d = 0; d < D; ++d) {
-      const float x = k76 * __ldg(&W[(int64_t)d * F + k]);
-      const float4 g = c.g[d];
-      const float2 ph = expm2pi(t + lin_turns(c.nu[d], k));
-      // per-draw constant applied with one rounding so it carries no systematic error
-      const float2 H = cmul(make_float2(df_scale(g.x, g.y, x), df_scale(g.z, g.w, x)), ph);
-      const float2 y = __ldg(&Y[(e * D + d) * F + k]);
-      const float term = fmaf(H.x, H.x - 2.f * y.x, H.y * (H.y - 2.f * y.y));
-      const float yk = term - comp;
-      const float tk = sum + yk;
-      comp = (tk - sum) - yk;
-      sum = tk;
+  __syncwarp();
+  const int cnt = S - base < 32 ? (int)(S - base) : 32;
+  float own_hi = 0.f, own_lo = 0.f;
+  for (int j = 0; j < cnt; ++j) {
+    const DrawCoef c = sc[wid][j];
+    const int64_t e = se[wid][j];
+    const int kend = min(c.kcut, n - 1);
+    // one Kahan pair per detector, so that the detectors' additions do not form one chain
+    float sum[ND], comp[ND];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) sum[d] = comp[d] = 0.f;
+    for (int k = k_lo + lane; k <= kend; k += 32) {
+      float k76;
+      const float t = waveform_turns(c, k, k76);
+#pragma unroll
+      for (int d = 0; d < ND; ++d) {
+        const float x = k76 * __ldg(&W[(int64_t)d * F + k]);
+        const float4 g = c.g[d];
+        const float2 ph = expm2pi(t + lin_turns(c.nu[d], k));
+        // per-draw constant applied with one rounding so it carries no systematic error
+        const float2 H = cmul(make_float2(df_scale(g.x, g.y, x), df_scale(g.z, g.w, x)), ph);
+        const float2 yv = __ldg(&Y[(e * ND + d) * F + k]);
+        const float term = fmaf(H.x, H.x - 2.f * yv.x, H.y * (H.y - 2.f * yv.y));
+        const float yk = term - comp[d];
+        const float tk = sum[d] + yk;
+        comp[d] = (tk - sum[d]) - yk;
+        sum[d] = tk;
+      }
+    }
+    float hi = sum[0], lo = -comp[0];
+#pragma unroll
+    for (int d = 1; d < ND; ++d) df_add(hi, lo, sum[d], -comp[d]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float bh = __shfl_xor_sync(0xffffffffu, hi, o);
+      const float bl = __shfl_xor_sync(0xffffffffu, lo, o);
+      df_add(hi, lo, bh, bl);
+    }
+    if (lane == j) {
+      own_hi = hi;
+      own_lo = lo;
     }
   }
-  double acc = (double)sum - (double)comp;
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if (lane == 0) lnl[s] = -(yy[e] + acc) * invN;
+  if (s_own < S) {
+    double yy = 0.0;
+#pragma unroll
+    for (int c = 0; c < YY_CHUNKS; ++c) yy += yy_part[(int64_t)e_own * YY_CHUNKS + c];
+    lnl[s_own] = -(yy + ((double)own_hi + (double)own_lo)) * invN;
+  }
 }
 
-cudaError_t launch_loglike_full(const float* ydata, const float2* Ydata, const float* W, const DrawCoef* coef,
-                                const int64_t* ev_off, double* yy, int64_t E, int D, int64_t N, int k_lo, int64_t S,
-                                double* lnl, cudaStream_t s) {
+size_t loglike_norm_bytes(int64_t E) { return (size_t)E * YY_CHUNKS * sizeof(double); }
+
+cudaError_t launch_loglike_full(const float* ydata, const float2* Ydata, const float* W, const double* theta,
+                                double df, double fs, const DetParams& dp, double gmst, const int64_t* ev_off,
+                                double* yy_part, int64_t E, int D, int64_t N, int k_lo, int64_t S, double* lnl,
+                                cudaStream_t s) {
   const int64_t F = N / 2 + 1;
   const int n = (int)(N / 2);
   if (E > 0) {
-    k_event_norm<<<(unsigned)E, 256, 0, s>>>(ydata, Ydata, D, F, k_lo, n, yy);
+    k_event_norm<<<dim3((unsigned)E, YY_CHUNKS), 256, 0, s>>>(ydata, Ydata, D, F, k_lo, n, yy_part);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
   }
   if (S <= 0) return cudaSuccess;
-  const int T = 256;
-  const int64_t warps_per_block = T / 32;
-  k_loglike<<<(unsigned)((S + warps_per_block - 1) / warps_per_block), T, 0, s>>>(
-      Ydata, W, coef, ev_off, yy, E, D, F, n, k_lo, S, 1.0 / (double)N, lnl);
+  const int64_t per_block = LL_WARPS * 32;
+  const unsigned grid = (unsigned)((S + per_block - 1) / per_block);
+  const double invN = 1.0 / (double)N;
+  const SetupConsts kc = make_setup_consts(df);
+  const int T = LL_WARPS * 32;
+#define GWX_LL(ND_)                                                                                                \
+  k_loglike<ND_><<<grid, T, 0, s>>>(theta, kc, fs, dp, gmst, Ydata, W, ev_off, yy_part, E, F, n, k_lo, S, invN, lnl)
+  switch (D) {
+    case 1: GWX_LL(1); break;
+    case 2: GWX_LL(2); break;
+    case 3: GWX_LL(3); break;
+    case 4: GWX_LL(4); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef GWX_LL
   return cudaGetLastError();
 }
 

@@ -35,59 +35,72 @@ __device__ __forceinline__ double th_at(const double* th, int64_t B, int64_t b, 
 constexpr double SQRT_5_24_PI_M23 = 0.21278751013966343;   // sqrt(5/24) pi^(-2/3)
 constexpr double LN4 = 1.3862943611198906;
 constexpr double INV_6P15_PI = 0.021658244478713226;        // 1 / (6^1.5 pi)
+constexpr double INV_C = 1.0 / C_MS;
 
-// A(df) = sqrt(5/24) pi^{-2/3} Mc^{5/6} df^{-7/6} / D in FP64 (strain per Hz), so that
-// the amplitude of bin k is A(df) k^{-7/6}; df76 = df^{-7/6}.  Mc^{5/6} =
-// M^{5/6} eta^{1/2} since Mc = M eta^{3/5}.
-__device__ __forceinline__ double waveform_amp(double M, double eta, double dist_mpc, double df76) {
-  const double D = dist_mpc * (MPC_M / C_MS);
-  return SQRT_5_24_PI_M23 * exp((5.0 / 6.0) * log(M)) * sqrt(eta) / D * df76;
+// Per-call constants of the set-up, computed once on the host.
+struct SetupConsts {
+  double df;         // frequency resolution
+  double ln_pi_df;   // ln(pi df)
+  double amp_k;      // sqrt(5/24) pi^{-2/3} (pi df)^{-5/6} df^{-7/6} c / (1 Mpc): A(df) = amp_k V^{5/2} eta^{1/2} / D[Mpc]
+  double isco_bins;  // 1 / (6^1.5 pi MTSUN_S df): floor(isco_bins / (m1 + m2)) is the last bin below f_isco
+};
+
+static inline SetupConsts make_setup_consts(double df) {
+  return {df, log(PI_D * df), SQRT_5_24_PI_M23 * pow(PI_D * df, -5.0 / 6.0) * pow(df, -7.0 / 6.0) * (C_MS / MPC_M),
+          INV_6P15_PI / (MTSUN_S * df)};
 }
 
 // Waveform part of the set-up: PN phase coefficients in turns, amplitude and cut-off.
-__device__ inline void draw_waveform_coef(const double* th, int64_t B, int64_t b, double df, double df76,
-                                          int64_t F, DrawCoef& c, double* amp64 = nullptr) {
+// Written for the GPU's scarce FP64 throughput: constant ratios are folded at compile
+// time, one logarithm serves both ln V and M^(5/6), and the remaining divisions are
+// the few reciprocals that depend on the draw.
+__device__ inline void draw_waveform_coef(const double* th, int64_t B, int64_t b, const SetupConsts& k, int64_t F,
+                                          DrawCoef& c, double* amp64 = nullptr) {
   const double m1 = th_at(th, B, b, GWX_M1), m2 = th_at(th, B, b, GWX_M2);
   const double chi1 = th_at(th, B, b, GWX_CHI1), chi2 = th_at(th, B, b, GWX_CHI2);
   const double phic = th_at(th, B, b, GWX_PHIC);
   const double iota = th_at(th, B, b, GWX_THETAJN);
   const double mt = m1 + m2;
+  const double inv_mt = 1.0 / mt;
   const double M = mt * MTSUN_S;
-  const double eta = m1 * m2 / (mt * mt);
-  const double delta = (m1 - m2) / mt;
+  const double eta = m1 * m2 * inv_mt * inv_mt;
+  const double eta2 = eta * eta;
+  const double delta = (m1 - m2) * inv_mt;
   const double chis = 0.5 * (chi1 + chi2), chia = 0.5 * (chi1 - chi2);
-  const double pi = PI_D, pi2 = PI_D * PI_D;
-  const double a2 = 3715.0 / 756.0 + 55.0 * eta / 9.0;
-  const double a3 = -16.0 * pi + (113.0 / 3.0) * delta * chia + (113.0 / 3.0 - 76.0 * eta / 3.0) * chis;
-  const double a4 = 15293365.0 / 508032.0 + 27145.0 * eta / 504.0 + 3085.0 * eta * eta / 72.0;
-  const double a5 = pi * (38645.0 / 756.0 - 65.0 * eta / 9.0);
+  const double pi = PI_D;
+  const double a2 = 3715.0 / 756.0 + (55.0 / 9.0) * eta;
+  const double a3 = -16.0 * pi + (113.0 / 3.0) * delta * chia + (113.0 / 3.0 - (76.0 / 3.0) * eta) * chis;
+  const double a4 = 15293365.0 / 508032.0 + (27145.0 / 504.0) * eta + (3085.0 / 72.0) * eta2;
+  const double a5 = pi * (38645.0 / 756.0 - (65.0 / 9.0) * eta);
   const double l5 = 3.0 * a5;
-  const double a6 = 11583231236531.0 / 4694215680.0 - 640.0 * pi2 / 3.0 - 6848.0 * EULER_GAMMA / 21.0 -
-                    6848.0 * LN4 / 21.0 + (-15737765635.0 / 3048192.0 + 2255.0 * pi2 / 12.0) * eta +
-                    76055.0 * eta * eta / 1728.0 - 127825.0 * eta * eta * eta / 1296.0;
+  constexpr double a6_0 = 11583231236531.0 / 4694215680.0 - 640.0 * (PI_D * PI_D) / 3.0 -
+                          6848.0 * EULER_GAMMA / 21.0 - 6848.0 * LN4 / 21.0;
+  constexpr double a6_1 = -15737765635.0 / 3048192.0 + 2255.0 * (PI_D * PI_D) / 12.0;
+  const double a6 = a6_0 + a6_1 * eta + (76055.0 / 1728.0) * eta2 - (127825.0 / 1296.0) * eta2 * eta;
   const double l6 = -6848.0 / 21.0;
-  const double a7 = pi * (77096675.0 / 254016.0 + 378515.0 * eta / 1512.0 - 74045.0 * eta * eta / 756.0);
-  const double V = cbrt(pi * M * df);
-  const double lnV = log(V);
-  const double pref = 3.0 / (256.0 * pi * eta);   // 3/(128 eta) in turns
+  const double a7 = pi * (77096675.0 / 254016.0 + (378515.0 / 1512.0) * eta - (74045.0 / 756.0) * eta2);
+  const double lnV = (1.0 / 3.0) * (k.ln_pi_df + log(M));   // V = (pi M df)^(1/3)
+  const double V = exp(lnV);
   const double Vi = 1.0 / V;
+  const double pref = (3.0 / (256.0 * PI_D)) / eta;   // 3/(128 eta) in turns
   const double Vi2 = Vi * Vi, Vi3 = Vi2 * Vi, Vi5 = Vi3 * Vi2;
   c.c0 = split_df(pref * Vi5);
   c.c2 = split_df(pref * Vi3 * a2);
   c.c3 = split_df(pref * Vi2 * a3);
   c.c4 = (float)(pref * Vi * a4);
-  c.d5 = split_df(pref * l5 / 3.0);
+  c.d5 = split_df(pref * a5);   // pref l5 / 3
   c.c6 = (float)(pref * V * (a6 + l6 * lnV));
-  c.d6 = (float)(pref * V * l6 / 3.0);
+  c.d6 = (float)(pref * V * (l6 / 3.0));
   c.c7 = (float)(pref * V * V * a7);
-  double cph = -(phic + 0.25 * pi) / (2.0 * pi) + pref * (a5 + l5 * lnV);
+  double cph = -(phic + 0.25 * PI_D) * (1.0 / (2.0 * PI_D)) + pref * (a5 + l5 * lnV);
   cph -= rint(cph);
   c.cph = (float)cph;
-  const double amp = waveform_amp(M, eta, th_at(th, B, b, GWX_DIST), df76);
+  // A(df) = sqrt(5/24) pi^{-2/3} Mc^{5/6} df^{-7/6} / D with Mc^{5/6} = M^{5/6} eta^{1/2}
+  // = V^2 (V eta)^{1/2} (pi df)^{-5/6}; k.amp_k folds the constants and df^{-7/6}.
+  const double amp = k.amp_k * (V * V) * sqrt(V * eta) / th_at(th, B, b, GWX_DIST);
   if (amp64) *amp64 = amp;
   c.amp = (float)amp;
-  const double f_isco = INV_6P15_PI / M;
-  double kc = floor(f_isco / df);
+  const double kc = floor(k.isco_bins * inv_mt);
   c.kcut = kc > (double)(F - 1) ? (int)(F - 1) : (int)kc;
   const double ci = cos(iota);
   c.qp = (float)(0.5 * (1.0 + ci * ci));
@@ -109,20 +122,29 @@ __device__ inline void draw_detector_coef(const double* th, int64_t B, int64_t b
   const double eth[3] = {sd * cp, sd * sp, -cd};
   const double eph[3] = {-sp, cp, 0.0};
   double X[3], Y[3];
+#pragma unroll
   for (int i = 0; i < 3; ++i) {
     X[i] = cpsi * eth[i] + spsi * eph[i];
     Y[i] = spsi * eth[i] - cpsi * eph[i];
   }
-  for (int d = 0; d < dp.D; ++d) {
+  // unrolled over the detector slots so that DetParams stays in the parameter bank
+#pragma unroll
+  for (int d = 0; d < GWX_MAX_DET; ++d) {
+    if (d >= dp.D) {
+      c.g[d] = make_float4(0.f, 0.f, 0.f, 0.f);
+      c.nu[d] = 0ull;
+      continue;
+    }
     const double* T = dp.tensor[d];
     double DX[3], DY[3];
+#pragma unroll
     for (int i = 0; i < 3; ++i) {
       DX[i] = T[3 * i] * X[0] + T[3 * i + 1] * X[1] + T[3 * i + 2] * X[2];
       DY[i] = T[3 * i] * Y[0] + T[3 * i + 1] * Y[1] + T[3 * i + 2] * Y[2];
     }
     const double fp = X[0] * DX[0] + X[1] * DX[1] + X[2] * DX[2] - (Y[0] * DY[0] + Y[1] * DY[1] + Y[2] * DY[2]);
     const double fc = X[0] * DY[0] + X[1] * DY[1] + X[2] * DY[2] + (Y[0] * DX[0] + Y[1] * DX[1] + Y[2] * DX[2]);
-    const double dt = -(dp.pos[d][0] * n[0] + dp.pos[d][1] * n[1] + dp.pos[d][2] * n[2]) / C_MS;
+    const double dt = -(dp.pos[d][0] * n[0] + dp.pos[d][1] * n[1] + dp.pos[d][2] * n[2]) * INV_C;
     // scale (F+ qp + Fx (-i qc))
     const float2 re = split_df(scale * fp * qp), im = split_df(-scale * fc * qc);
     c.g[d] = make_float4(re.x, re.y, im.x, im.y);
@@ -130,10 +152,6 @@ __device__ inline void draw_detector_coef(const double* th, int64_t B, int64_t b
     x -= floor(x);
     double fx = ldexp(x, 64);
     c.nu[d] = fx >= 18446744073709551615.0 ? 0ull : (unsigned long long)fx;
-  }
-  for (int d = dp.D; d < GWX_MAX_DET; ++d) {
-    c.g[d] = make_float4(0.f, 0.f, 0.f, 0.f);
-    c.nu[d] = 0ull;
   }
 }
 
@@ -144,11 +162,14 @@ __device__ __forceinline__ float lin_turns(unsigned long long nu, int k) {
 }
 
 // Phase Psi(k)/(2 pi) reduced to [-1/2, 1/2] and the factor k^{-7/6}, for 1 <= k <= KMAX.
+// 1/k enters as a double-float: the hardware reciprocal estimate rh is within a few
+// ulp of 1/k, and the exact residual 1 - rh k (one FMA) times rh supplies the low part.
 __device__ __forceinline__ float waveform_turns(const DrawCoef& c, int k, float& k76) {
   const float4 p = __ldg(&g_kp53[k]);
   const float4 q = __ldg(&g_kq[k]);
   const float kf = (float)k;
-  const float rh = __frcp_rn(kf);
+  float rh;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rh) : "f"(kf));
   const float rl = fmaf(-rh, kf, 1.0f) * rh;
   const float t = df_frac(df_mul(c.c0.x, c.c0.y, p.x, p.y)) + df_frac(df_mul(c.c2.x, c.c2.y, rh, rl)) +
                   df_frac(df_mul(c.c3.x, c.c3.y, p.z, p.w)) + df_frac(df_mul(c.d5.x, c.d5.y, q.y, q.z));
@@ -157,7 +178,7 @@ __device__ __forceinline__ float waveform_turns(const DrawCoef& c, int k, float&
   const float small = fmaf(c.c4, q.x, fmaf(fmaf(c.d6, q.y, c.c6), k13, fmaf(c.c7, k23, c.cph)));
   float tt = t + small;
   tt -= rintf(tt);
-  k76 = p.x * sqrtf(kf);   // k^{-5/3} k^{1/2}: two correctly rounded operations
+  k76 = q.w;   // k^{-7/6}, correctly rounded from FP64
   return tt;
 }
 

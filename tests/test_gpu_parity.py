@@ -382,9 +382,9 @@ def test_log_likelihood_matches_oracle(gwx, name):
     assert np.abs(got - ref).max() <= 1e-3, np.abs(got - ref).max()
 
 
-def test_log_likelihood_judge_scale_sampled(gwx):
+def test_log_likelihood_importance_weighting_scale_sampled(gwx):
     """64 events with 2k..50k samples each (about 1.7 million samples, three
-    detectors, 4 s windows): the importance-sampling judge's scale.  The oracle
+    detectors, 4 s windows): the scale of importance-weighting a flow's samples.  The oracle
     recomputes a sample of 40 samples spread over the events."""
     wl = workloads.workload("hl3")
     E = 64
