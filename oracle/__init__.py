@@ -13,7 +13,7 @@ frequency-domain compact-binary waveforms (Sec. 3.1), project them onto the
 detectors, inject them into background strain, estimate the background power
 spectrum and whiten the batch (Sec. 3.2).  The plain likelihood used by the
 paper's nested-sampling comparison (Sec. 6, Fig. 5 caption: "the standard GW
-likelihood") is the sixth piece.
+likelihood") is the sixth piece, and importance weights built on it the seventh.
 
 Modules, in pipeline order:
 
@@ -24,6 +24,7 @@ Modules, in pipeline order:
 * ``noise``      -- analytic aLIGO PSD and coloured Gaussian background.
 * ``spectral``   -- Welch PSD, PSD interpolation, injection, whitening.
 * ``likelihood`` -- noise-weighted inner product, log-likelihood, mismatch.
+* ``importance`` -- importance weights, effective sample size, evidence per event.
 * ``pipeline``   -- the whole per-batch pass, step by step, unfused.
 
 Everything is float64 / uint32-uint64 numpy.  ``numpy.fft`` is used as the
