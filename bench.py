@@ -39,7 +39,7 @@ SM_MAX_MHZ = 2070.0
 # ncu DRAM traffic (read + write bytes) of one k_simulate launch on the hl3
 # workload and the hash of the kernel sources it was measured on; see
 # profiles/k_simulate_hl3.md.  None until a capture matches the current sources.
-TRAFFIC = {"bytes_per_launch": 143056128, "sources_sha1": "3a320450ddadaaf0212e9c5b9bca9ba634f92c1b"}
+TRAFFIC = {"bytes_per_launch": 142819840, "sources_sha1": "9111b41493d24cb23459a100afe8161facd524ea"}
 
 
 def describe(wl):
@@ -61,7 +61,7 @@ def flops_per_injection(wl):
 
 def kernel_sources_sha1():
     h = hashlib.sha1()
-    for f in ("k_fused.cu", "common.cuh", "waveform.cuh", "gwx_internal.h"):
+    for f in ("k_fused.cu", "fft16.cuh", "common.cuh", "waveform.cuh", "gwx_internal.h"):
         with open(os.path.join(ROOT, "paper_2407_19048_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -211,9 +211,77 @@ def loglike_leg(gwx, torch, wl, rank):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
+
+    # the plain importance-sampling path: prior samples scored, then weighted per event
+    def chain():
+        gwx.log_likelihood(y_data, sim.psd, wl["seg_len"], wl["fs"], wl["f_lo"], wl["dets"], 0.0, theta, offs_d,
+                           out=out)
+        return gwx.importance_weights(out, offs_d)
+
+    chain()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        w, ess, eff, lnz = chain()
+    e1.record()
+    torch.cuda.synchronize()
+    chain_ms = e0.elapsed_time(e1) / reps
+    ess_total = float(ess.sum().item())
     return {"value": S / (ms * 1e-3), "unit": "samples/s", "ms_per_call": ms, "samples": S, "events": E,
             "note": "plain batched-likelihood path: TaylorF2 template + projection + whitened residual per sample, "
-                    "FP32 products, FP64 sums"}
+                    "FP32 products, FP64 sums",
+            "importance": {"metric": "importance-weighted posterior samples/sec (prior as proposal)",
+                           "value": ess_total / (chain_ms * 1e-3), "unit": "effective samples/s",
+                           "ms_per_chain": chain_ms, "ess_total": ess_total,
+                           "median_efficiency": float(eff.median().item()),
+                           "chain": "log_likelihood + importance_weights over all events"}}
+
+
+def cufft_leg(gwx, torch, sim, wl, fused_ms):
+    """The shared-memory FFT kernels against cuFFT (called through torch.fft) on the
+    batch's shape, B x D rows of N real samples.  cuFFT is a timing baseline here only:
+    nothing on the product path calls it."""
+    B, D, N = sim.y.shape
+    F = N // 2 + 1
+    x = sim.y.clone()
+    X = torch.empty((B, D, F), dtype=torch.complex64, device=x.device)
+    Xc = torch.empty_like(X)
+    yo = torch.empty_like(x)
+    Wt = torch.rand((D, F), dtype=torch.float32, device=x.device)
+    lib = gwx._lib.load()
+    ws, nb = gwx._workspace(lib.gwx_whiten_workspace(D, N), x.device)
+
+    def ours_whiten():
+        gwx._check(lib.gwx_whiten(gwx._ptr(x), gwx._ptr(sim.psd), wl["seg_len"], wl["fs"], wl["f_lo"], B, D, N,
+                                  gwx._ptr(yo), gwx._ptr(ws), nb, gwx._stream()))
+
+    def cufft_whiten():
+        torch.fft.rfft(x, dim=-1, out=Xc)
+        Xc.mul_(Wt)
+        torch.fft.irfft(Xc, n=N, dim=-1, out=yo)
+
+    def timed(fn, reps=20):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    res = {"rows": B * D, "N": N,
+           "gwx_rfft_ms": timed(lambda: gwx.rfft(x, out=X)),
+           "cufft_rfft_ms": timed(lambda: torch.fft.rfft(x, dim=-1, out=Xc)),
+           "gwx_irfft_ms": timed(lambda: gwx.irfft(X, N, out=yo)),
+           "cufft_irfft_ms": timed(lambda: torch.fft.irfft(Xc, n=N, dim=-1, out=yo)),
+           "gwx_whiten_ms": timed(ours_whiten),
+           "cufft_whiten_ms": timed(cufft_whiten),
+           "gwx_fused_simulate_ms": fused_ms,
+           "note": "inputs (201 MB) exceed L2; the fused pass also crops, evaluates and injects the waveforms"}
+    return res
 
 
 def run_gpu(args, wl):
@@ -305,6 +373,7 @@ def run_gpu(args, wl):
     e2e_value = world * B * args.steps / e2e_s
 
     ll = loglike_leg(gwx, torch, wl, rank)
+    fft_cmp = cufft_leg(gwx, torch, sim, wl, statistics.mean(sim_ms))
 
     sim_avg_s = statistics.mean(sim_ms) * 1e-3
     flops = flops_per_injection(wl) * B
@@ -347,6 +416,7 @@ def run_gpu(args, wl):
             "gpu_launches": sim.LAUNCHES_PER_STEP * args.steps,
             "clocks": clk,
             "log_likelihood": ll,
+            "fft_vs_cufft": fft_cmp,
             "wall_s_timed_region": t_wall,
         }
         print(json.dumps(line), flush=True)

@@ -257,6 +257,24 @@ int gwx_log_likelihood(int approximant, const float* y_data, int64_t E, int D, i
                        const double* theta, const int64_t* event_offsets, int64_t S,
                        double* lnl, void* workspace, size_t workspace_bytes, void* stream);
 
+/* ---- importance weights of scored samples ------------------------------------
+ * Samples theta_s ~ q of event e, scored by gwx_log_likelihood, become posterior
+ * samples by importance sampling with the standard GW likelihood (Sec. 6):
+ *   ln w_s = lnl_s + log_ratio_s   (log_ratio = ln prior - ln q; NULL = zeros, q = prior),
+ *   weights_s = w_s / sum_{s in e} w_s,
+ *   ess_e = (sum w)^2 / sum w^2 (Kish),  efficiency_e = ess_e / S_e,
+ *   ln_evidence_e = ln((1/S_e) sum w_s).
+ * An event without samples, or whose every ln w is -inf, gets ess = efficiency = 0,
+ * ln_evidence = -inf and zero weights.  exp is evaluated in FP32 on the FP64 value
+ * ln w - max split into two floats (relative error ~2e-7); sums are FP64.
+ *   lnl, log_ratio in double[S]; event_offsets int64[E+1] (device, ragged; entries are
+ *   clamped to [0, S]); weights out double[S]; ess, efficiency, ln_evidence out
+ *   double[E]; any output may be NULL.  Workspace: gwx_importance_weights_workspace(E). */
+size_t gwx_importance_weights_workspace(int64_t E);
+int gwx_importance_weights(const double* lnl, const double* log_ratio, const int64_t* event_offsets,
+                           int64_t E, int64_t S, double* weights, double* ess, double* efficiency,
+                           double* ln_evidence, void* workspace, size_t workspace_bytes, void* stream);
+
 /* ---- transforms (the FFT kernels of the steps above, exposed for checking) ----
  * gwx_rfft:  X[r] = rfft(x[r]) for R rows of N real samples (numpy convention,
  *            X_k = sum_n x_n e^{-2 pi i k n/N}); X complex[R][N/2+1].

@@ -23,7 +23,8 @@ M1, M2, CHI1, CHI2, DIST, TC, PHIC, THETAJN, PSI, RA, DEC = range(11)
 NPARAM = 11
 
 __all__ = ["GwxError", "version", "init", "detector_geometry", "sample_prior", "generate_waveforms", "project",
-           "colored_noise", "welch_psd", "inject", "whiten", "simulate_batch", "log_likelihood", "rfft", "irfft",
+           "colored_noise", "welch_psd", "inject", "whiten", "simulate_batch", "log_likelihood",
+           "importance_weights", "rfft", "irfft",
            "workspace_bytes", "TAYLORF2", "IMRPHENOMD", "DETECTORS"]
 
 
@@ -232,6 +233,27 @@ def log_likelihood(y_data, psd, seg_len, fs, f_lo, dets, gmst, theta, event_offs
     _check(lib.gwx_log_likelihood(approximant, _ptr(y_data), E, D, N, _ptr(psd), seg_len, fs, f_lo, ids, gmst,
                                   _ptr(theta), _ptr(event_offsets), S, _ptr(out), _ptr(ws), nb, _stream()))
     return out
+
+
+def importance_weights(lnl, event_offsets, log_ratio=None):
+    """Per-event importance weights of scored samples: returns (weights [S], ess [E],
+    efficiency [E], ln_evidence [E]) as device float64 tensors (see gwx.h)."""
+    torch = _torch()
+    lib = _lib.load()
+    _dev(lnl, torch.float64, "lnl")
+    _dev(event_offsets, torch.int64, "event_offsets")
+    if log_ratio is not None:
+        _dev(log_ratio, torch.float64, "log_ratio")
+    S = lnl.shape[0]
+    E = event_offsets.shape[0] - 1
+    dev = lnl.device
+    w = torch.empty(S, dtype=torch.float64, device=dev)
+    ess, eff, lnz = (torch.empty(max(E, 0), dtype=torch.float64, device=dev) for _ in range(3))
+    ws, nb = _workspace(lib.gwx_importance_weights_workspace(E), dev)
+    _check(lib.gwx_importance_weights(_ptr(lnl), _ptr(log_ratio) if log_ratio is not None else None,
+                                      _ptr(event_offsets), E, S, _ptr(w), _ptr(ess), _ptr(eff), _ptr(lnz),
+                                      _ptr(ws), nb, _stream()))
+    return w, ess, eff, lnz
 
 
 def rfft(x, out=None):

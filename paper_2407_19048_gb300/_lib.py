@@ -54,6 +54,8 @@ SIGNATURES = {
     "gwx_log_likelihood_workspace": (c_size, [c_i64, c_int, c_i64, c_i64]),
     "gwx_log_likelihood": (c_int, [c_int, c_vp, c_i64, c_int, c_i64, c_vp, c_i64, c_dbl, c_dbl, c_i32p, c_dbl,
                                    c_vp, c_vp, c_i64, c_vp, c_vp, c_size, c_vp]),
+    "gwx_importance_weights_workspace": (c_size, [c_i64]),
+    "gwx_importance_weights": (c_int, [c_vp, c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_size, c_vp]),
     "gwx_rfft": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp]),
     "gwx_irfft": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp]),
 }

@@ -410,6 +410,25 @@ int gwx_log_likelihood(int approximant, const float* y_data, int64_t E, int D, i
                   "log_likelihood");
 }
 
+size_t gwx_importance_weights_workspace(int64_t E) {
+  if (E < 0) return 0;
+  return align_up(iw_workspace_bytes(E));
+}
+
+int gwx_importance_weights(const double* lnl, const double* log_ratio, const int64_t* event_offsets, int64_t E,
+                           int64_t S, double* weights, double* ess, double* efficiency, double* ln_evidence,
+                           void* workspace, size_t workspace_bytes, void* stream) {
+  if (E < 0 || S < 0 || E > 0x7fffffffLL) return fail(GWX_ESHAPE, "bad E=%lld or S=%lld", (long long)E, (long long)S);
+  if (S > 0 && E == 0) return fail(GWX_ESHAPE, "samples without events");
+  if (E == 0) return GWX_OK;
+  if (!event_offsets || (S > 0 && !lnl)) return fail(GWX_EINVAL, "NULL array");
+  GWX_TRY(check_ws(workspace, workspace_bytes, gwx_importance_weights_workspace(E)));
+  GWX_TRY(ensure_init());
+  return launched(launch_importance_weights(lnl, log_ratio, event_offsets, E, S, weights, ess, efficiency,
+                                            ln_evidence, workspace, as_stream(stream)),
+                  "importance_weights");
+}
+
 int gwx_rfft(const float* x, int64_t R, int64_t N, float* X, void* stream) {
   GWX_TRY(check_window(N));
   if (R < 0 || R > 0x7fffffffLL) return fail(GWX_ESHAPE, "R=%lld", (long long)R);

@@ -73,6 +73,12 @@ cudaError_t launch_loglike_full(const float* ydata, const float2* Ydata, const f
                                 double* yy_part, int64_t E, int D, int64_t N, int k_lo, int64_t S, double* lnl,
                                 cudaStream_t s);
 
+// Importance weights: E x iw_chunks(E) partials in ws (iw_workspace_bytes(E)).
+size_t iw_workspace_bytes(int64_t E);
+cudaError_t launch_importance_weights(const double* lnl, const double* ratio, const int64_t* off, int64_t E,
+                                      int64_t S, double* weights, double* ess, double* eff, double* lnz, void* ws,
+                                      cudaStream_t s);
+
 // Record msg as the calling thread's gwx_last_error() message; returns status.
 int set_last_error(int status, const char* msg);
 

@@ -65,6 +65,8 @@ def test_workspace_sizes(lib):
     assert gwx.workspace_bytes("colored_noise", 3, 131072) >= 3 * 65536 * 8
     assert gwx.workspace_bytes("simulate_batch", 3, 2048, 8192) > 2048 * 144
     assert gwx.workspace_bytes("log_likelihood", 4, 3, 8192, 100) > 0
+    assert gwx.workspace_bytes("importance_weights", 64) >= 64 * 16 * 24
+    assert gwx.workspace_bytes("importance_weights", 0) == 0
 
 
 def test_validation_fails_before_any_launch(lib):
@@ -79,6 +81,10 @@ def test_validation_fails_before_any_launch(lib):
     assert st == -2
     p = _lib.GwxPrior(*([0.0] * 12))
     st = lib.gwx_sample_prior(p, 1, 0, 16, 100, 200, None, None, None)         # L < N
+    assert st == -2
+    st = lib.gwx_importance_weights(None, None, None, 0, 5, None, None, None, None, None, 0, None)
+    assert st == -2 and b"without events" in lib.gwx_last_error()
+    st = lib.gwx_importance_weights(None, None, None, -1, 0, None, None, None, None, None, 0, None)
     assert st == -2
     with pytest.raises(KeyError):
         gwx.detector_geometry("K1")
