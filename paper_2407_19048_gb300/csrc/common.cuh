@@ -47,7 +47,7 @@ constexpr int KMAX = 16384;
 // Radix-8 passes keep rows r = 1, 2, 4 (the other powers are formed by products),
 // radix-4 passes rows 1..3, radix-2 passes row 1; one set for every stride
 // Ns = 2, 4, ..., 4096 of each radix.
-__host__ __device__ constexpr int twp_rows(int R) { return R == 2 ? 1 : 3; }
+__host__ __device__ constexpr int twp_rows(int R) { return R - 1; }   // rows r = 1 .. R-1
 constexpr int TWP_NSETS = 12;                                    // Ns = 2 .. 4096
 __host__ __device__ constexpr int twp_ns(int q) { return 2 << q; }
 __host__ __device__ constexpr int twp_size(int R) { return twp_rows(R) * ((2 << TWP_NSETS) - 2); }
@@ -103,15 +103,13 @@ static inline cudaError_t fill_tables_for_this_tu() {
     const int radices[3] = {8, 4, 2};
     for (int ri = 0; ri < 3; ++ri) {
       const int R = radices[ri];
-      const int rows8[3] = {1, 2, 4}, rows4[3] = {1, 2, 3}, rows2[1] = {1};
-      const int* rows = R == 8 ? rows8 : (R == 4 ? rows4 : rows2);
       for (int q = 0; q < TWP_NSETS; ++q) {
         const int Ns = twp_ns(q);
         const int off = twp_offset(R, Ns);
         for (int row = 0; row < twp_rows(R); ++row)
           for (int jm = 0; jm < Ns; ++jm)
             twp[off + row * Ns + jm] =
-                unit_twiddle(two_pi * (double)jm * (double)rows[row] / ((double)Ns * (double)R));
+                unit_twiddle(two_pi * (double)jm * (double)(row + 1) / ((double)Ns * (double)R));
       }
     }
     kp[0] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -219,28 +217,43 @@ __device__ __forceinline__ float df_scale(float hi, float lo, float x) {
   return p + fmaf(lo, x, fmaf(hi, x, -p));
 }
 
-template <bool INV>
+// Radix-8 butterfly.  EXACT: the products by sqrt(1/2) are rounded once from their
+// exact values (mul_rsqrt2), which removes the ~6e-8 energy loss per transform that the
+// nearest-float constant leaves (it would bias a likelihood built on the transform by
+// ~1e-3); otherwise the constant product is fused into the final additions.
+template <bool INV, bool EXACT = true>
 __device__ __forceinline__ void dft8(float2* v) {
   // even/odd split: E = DFT4(v0, v2, v4, v6), O = DFT4(v1, v3, v5, v7)
   dft4<INV>(v[0], v[2], v[4], v[6]);
   dft4<INV>(v[1], v[3], v[5], v[7]);
   // O_k *= w8^{-+k}, w8 = e^{2 pi i/8}
   const float2 p = v[3], q = v[7];
-  float2 o1 = INV ? make_float2(mul_rsqrt2(p.x - p.y), mul_rsqrt2(p.x + p.y))
-                  : make_float2(mul_rsqrt2(p.x + p.y), mul_rsqrt2(p.y - p.x));
-  float2 o2 = mul_mi<INV>(v[5]);
-  float2 o3 = INV ? make_float2(-mul_rsqrt2(q.x + q.y), mul_rsqrt2(q.x - q.y))
-                  : make_float2(mul_rsqrt2(q.y - q.x), -mul_rsqrt2(q.x + q.y));
-  float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
+  const float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
+  const float2 o2 = mul_mi<INV>(v[5]);
   v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
-  v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
   v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
-  v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
+  if constexpr (EXACT) {
+    const float2 o1 = INV ? make_float2(mul_rsqrt2(p.x - p.y), mul_rsqrt2(p.x + p.y))
+                          : make_float2(mul_rsqrt2(p.x + p.y), mul_rsqrt2(p.y - p.x));
+    const float2 o3 = INV ? make_float2(-mul_rsqrt2(q.x + q.y), mul_rsqrt2(q.x - q.y))
+                          : make_float2(mul_rsqrt2(q.y - q.x), -mul_rsqrt2(q.x + q.y));
+    v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
+    v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
+  } else {
+    constexpr float c = 0.707106769084930419921875f;   // nearest float to sqrt(1/2)
+    // o1 = c (a1x, a1y), o3 = c (a3x, a3y)
+    const float a1x = INV ? p.x - p.y : p.x + p.y, a1y = INV ? p.x + p.y : p.y - p.x;
+    const float a3x = INV ? -(q.x + q.y) : q.y - q.x, a3y = INV ? q.x - q.y : -(q.x + q.y);
+    v[1] = make_float2(fmaf(c, a1x, e1.x), fmaf(c, a1y, e1.y));
+    v[5] = make_float2(fmaf(-c, a1x, e1.x), fmaf(-c, a1y, e1.y));
+    v[3] = make_float2(fmaf(c, a3x, e3.x), fmaf(c, a3y, e3.y));
+    v[7] = make_float2(fmaf(-c, a3x, e3.x), fmaf(-c, a3y, e3.y));
+  }
 }
 
-template <int R, bool INV>
+template <int R, bool INV, bool EXACT = true>
 __device__ __forceinline__ void dftR(float2* v) {
-  if constexpr (R == 8) dft8<INV>(v);
+  if constexpr (R == 8) dft8<INV, EXACT>(v);
   else if constexpr (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
   else dft2<INV>(v[0], v[1]);
 }
@@ -294,19 +307,8 @@ __device__ __forceinline__ void fft_pass(uint32_t x, int t) {
       // e^{-2 pi i jm r/(Ns R)} from the per-pass table (coalesced across threads)
       const float2* tp = g_twp + twp_offset(R, Ns) + jm;
       float2 w[R];
-      if constexpr (R == 8) {
-        // three table rows, four products: fewer load instructions per butterfly
-        w[1] = __ldg(tp);
-        w[2] = __ldg(tp + Ns);
-        w[4] = __ldg(tp + 2 * Ns);
-        w[3] = cmul(w[1], w[2]);
-        w[5] = cmul(w[1], w[4]);
-        w[6] = cmul(w[2], w[4]);
-        w[7] = cmul(w[3], w[4]);
-      } else {
 #pragma unroll
-        for (int r = 1; r < R; ++r) w[r] = __ldg(tp + (r - 1) * Ns);
-      }
+      for (int r = 1; r < R; ++r) w[r] = __ldg(tp + (r - 1) * Ns);
 #pragma unroll
       for (int r = 1; r < R; ++r) v[i][r] = cmul(v[i][r], INV ? cconj(w[r]) : w[r]);
     }

@@ -29,18 +29,8 @@ struct Plan16 {
 template <int R, int Ns, bool INV>
 __device__ __forceinline__ void pass_twiddles(int jm, float2* w) {
   const float2* tp = g_twp + twp_offset(R, Ns) + jm;
-  if constexpr (R == 8) {
-    w[1] = __ldg(tp);
-    w[2] = __ldg(tp + Ns);
-    w[4] = __ldg(tp + 2 * Ns);
-    w[3] = cmul(w[1], w[2]);
-    w[5] = cmul(w[1], w[4]);
-    w[6] = cmul(w[2], w[4]);
-    w[7] = cmul(w[3], w[4]);
-  } else {
 #pragma unroll
-    for (int r = 1; r < R; ++r) w[r] = __ldg(tp + (r - 1) * Ns);
-  }
+  for (int r = 1; r < R; ++r) w[r] = __ldg(tp + (r - 1) * Ns);
   if (INV) {
 #pragma unroll
     for (int r = 1; r < R; ++r) w[r] = cconj(w[r]);
@@ -109,7 +99,7 @@ __device__ __forceinline__ void pass16(uint32_t x, int t) {
 #pragma unroll
       for (int r = 1; r < R; ++r) v[i][r] = cmul(v[i][r], w[r]);
     }
-    dftR<R, INV>(v[i]);
+    dftR<R, INV, false>(v[i]);
   }
   __syncthreads();
 #pragma unroll

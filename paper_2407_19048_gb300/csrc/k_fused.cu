@@ -147,7 +147,7 @@ __global__ void __launch_bounds__((1 << LOGN) / 16, LOGN >= 13 ? 1 : 2)
               v[r] = make_float2(q.y, nx);
             }
           }
-          dft8<false>(v);
+          dft8<false, false>(v);
           store_pass<8, 1>(x, j, v);
         }
       }
@@ -176,8 +176,8 @@ __global__ void __launch_bounds__((1 << LOGN) / 16, LOGN >= 13 ? 1 : 2)
 #pragma unroll
           for (int r = 1; r < RL; ++r) vB[s][r] = cmul(vB[s][r], w[r]);
         }
-        dftR<RL, false>(vA[s]);
-        dftR<RL, false>(vB[s]);
+        dftR<RL, false, false>(vA[s]);
+        dftR<RL, false, false>(vB[s]);
         // now vA[s][r] = Z[jA + NB r], vB[s][r] = Z[jB + NB r]
         if (p != 0) {
 #pragma unroll
@@ -200,8 +200,8 @@ __global__ void __launch_bounds__((1 << LOGN) / 16, LOGN >= 13 ? 1 : 2)
             fd_pair<LOGN>(vB[s][r], vB[s][RL - 1 - r], NB / 2 + NB * r, ea.x, ea.y, eb.x, eb.y, gd, nu, Wd, Wpd, inv_n);
           }
         }
-        dftR<RL, true>(vA[s]);
-        dftR<RL, true>(vB[s]);
+        dftR<RL, true, false>(vA[s]);
+        dftR<RL, true, false>(vB[s]);
       }
       __syncthreads();   // every read of the last forward pass precedes the writes below
 #pragma unroll
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__((1 << LOGN) / 16, LOGN >= 13 ? 1 : 2)
         pass_twiddles<8, n / 8, true>(j, w);
 #pragma unroll
         for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], w[r]);
-        dft8<true>(v);
+        dft8<true, false>(v);
 #pragma unroll
         for (int r = 0; r < 8; ++r) __stcs(&out[j + r * (n / 8)], v[r]);
       }
