@@ -20,6 +20,10 @@
  *   says "host".  The library never frees, keeps or reallocates them.
  * - Arrays are C-contiguous.  "complex" arrays are interleaved float pairs
  *   (re, im): a [B][F] complex array holds 2*B*F floats.
+ * - Every array pointer must be 8-byte aligned (cudaMalloc and PyTorch
+ *   allocations are), except the background strain `noise` of gwx_inject and
+ *   of the simulate calls, which may start at any float; a misaligned pointer
+ *   returns GWX_EINVAL.
  * - Every call is asynchronous on `stream` (a cudaStream_t, NULL = legacy
  *   default stream) and performs no device allocation and no host
  *   synchronisation.  Calls that need scratch memory take a caller-owned

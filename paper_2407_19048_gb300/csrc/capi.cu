@@ -133,6 +133,14 @@ int check_ws(void* ws, size_t have, size_t need) {
     if (_st != GWX_OK) return _st; \
   } while (0)
 
+// Arrays the kernels read or write with 64-bit accesses (complex values, pairs of
+// floats, doubles, int64) must be 8-byte aligned; a misaligned pointer is rejected here
+// instead of faulting on the device.
+#define GWX_ALIGN8(p)                                                                     \
+  do {                                                                                    \
+    if (((uintptr_t)(const void*)(p)) & 7u) return fail(GWX_EINVAL, "%s is not 8-byte aligned", #p); \
+  } while (0)
+
 }  // namespace
 
 namespace {
@@ -200,6 +208,8 @@ int gwx_sample_prior(const gwx_prior* prior, uint64_t seed, uint32_t step, int64
   if (N < 1 || L < N || L - N + 1 > 0xffffffffLL) return fail(GWX_ESHAPE, "need 1 <= N <= L, L-N < 2^32");
   if (B == 0) return GWX_OK;
   if (!theta || !offsets) return fail(GWX_EINVAL, "NULL output");
+  GWX_ALIGN8(theta);
+  GWX_ALIGN8(offsets);
   GWX_TRY(ensure_init());
   return launched(launch_sample_prior(*prior, seed, step, B, L, N, theta, offsets, as_stream(stream)),
                   "sample_prior");
@@ -216,6 +226,9 @@ int gwx_generate_waveforms(int approximant, const double* theta, int64_t B, doub
   GWX_TRY(band_start(f_lo, df, F, &k_lo));
   if (B == 0) return GWX_OK;
   if (!theta || !hp || !hc) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN8(theta);
+  GWX_ALIGN8(hp);
+  GWX_ALIGN8(hc);
   GWX_TRY(ensure_init());
   return launched(launch_generate_waveforms(theta, B, k_lo, df, F, reinterpret_cast<float2*>(hp),
                                             reinterpret_cast<float2*>(hc), as_stream(stream)),
@@ -230,6 +243,10 @@ int gwx_project(const float* hp, const float* hc, const double* theta, int64_t B
   if (F < 1 || !(df > 0.0) || !isfinite(gmst)) return fail(GWX_EINVAL, "bad F, df or gmst");
   if (B == 0) return GWX_OK;
   if (!hp || !hc || !theta || !h_det) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN8(hp);
+  GWX_ALIGN8(hc);
+  GWX_ALIGN8(theta);
+  GWX_ALIGN8(h_det);
   GWX_TRY(ensure_init());
   return launched(launch_project(reinterpret_cast<const float2*>(hp), reinterpret_cast<const float2*>(hc), theta, B,
                                  dp, gmst, df, F, reinterpret_cast<float2*>(h_det), as_stream(stream)),
@@ -248,6 +265,7 @@ int gwx_colored_noise(uint64_t seed, uint32_t step, int D, int64_t L, double fs,
     return fail(GWX_ESHAPE, "L=%lld must be a power of two in [1024, 2^24]", (long long)L);
   if (!(fs > 0.0) || !(f_lo > 0.0)) return fail(GWX_EINVAL, "fs and f_lo must be positive");
   if (!noise) return fail(GWX_EINVAL, "noise is NULL");
+  GWX_ALIGN8(noise);
   GWX_TRY(check_ws(workspace, workspace_bytes, gwx_colored_noise_workspace(D, L)));
   GWX_TRY(ensure_init());
   return launched(launch_colored_noise(seed, step, D, L, fs, f_lo, noise, workspace, as_stream(stream)),
@@ -268,6 +286,7 @@ int gwx_welch_psd(const float* x, int D, int64_t L, double fs, int64_t seg_len, 
   if ((L - seg_len) / stride + 1 > 0x7fffffffLL) return fail(GWX_ESHAPE, "too many segments");
   if (!(fs > 0.0)) return fail(GWX_EINVAL, "fs must be positive");
   if (!x || !psd) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN8(psd);
   GWX_TRY(check_ws(workspace, workspace_bytes, gwx_welch_psd_workspace(D, L, seg_len, stride)));
   GWX_TRY(ensure_init());
   return launched(launch_welch(x, D, L, fs, seg_len, stride, psd, workspace, as_stream(stream)), "welch_psd");
@@ -282,6 +301,9 @@ int gwx_inject(const float* noise, int D, int64_t L, const int64_t* offsets, con
   if (!(fs > 0.0)) return fail(GWX_EINVAL, "fs must be positive");
   if (B == 0) return GWX_OK;
   if (!noise || !offsets || !h_det || !d) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN8(offsets);
+  GWX_ALIGN8(h_det);
+  GWX_ALIGN8(d);
   GWX_TRY(ensure_init());
   return launched(launch_inject_rows(noise, D, L, offsets, reinterpret_cast<const float2*>(h_det), B, N, fs, d,
                                      as_stream(stream)),
@@ -305,6 +327,9 @@ int gwx_whiten(const float* d, const double* psd, int64_t seg_len, double fs, do
   GWX_TRY(band_start(f_lo, fs / (double)N, N / 2, &k_lo));
   if (B == 0) return GWX_OK;
   if (!d || !psd || !y) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN8(d);
+  GWX_ALIGN8(psd);
+  GWX_ALIGN8(y);
   GWX_TRY(check_ws(workspace, workspace_bytes, gwx_whiten_workspace(D, N)));
   GWX_TRY(ensure_init());
   float* W = reinterpret_cast<float*>(workspace);
@@ -329,6 +354,8 @@ int gwx_prepare_batch(const gwx_prior* prior, uint64_t seed, uint32_t step, int6
   if (!isfinite(gmst)) return fail(GWX_EINVAL, "bad gmst");
   if (B == 0) return GWX_OK;
   if (!theta || !offsets) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN8(theta);
+  GWX_ALIGN8(offsets);
   GWX_TRY(check_ws(workspace, workspace_bytes, gwx_simulate_batch_workspace(D, B, N)));
   GWX_TRY(ensure_init());
   cudaStream_t s = as_stream(stream);
@@ -345,6 +372,9 @@ int gwx_simulate_prepared(const float* noise, int64_t L, const double* psd, int6
   GWX_TRY(check_psd_args(seg_len, N));
   if (B == 0) return GWX_OK;
   if (!noise || !psd || !y || !offsets) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN8(psd);
+  GWX_ALIGN8(y);
+  GWX_ALIGN8(offsets);
   GWX_TRY(check_ws(workspace, workspace_bytes, gwx_simulate_batch_workspace(D, B, N)));
   GWX_TRY(ensure_init());
   cudaStream_t s = as_stream(stream);
@@ -394,6 +424,11 @@ int gwx_log_likelihood(int approximant, const float* y_data, int64_t E, int D, i
   GWX_TRY(band_start(f_lo, df, N / 2, &k_lo));
   if (S == 0) return GWX_OK;
   if (!y_data || !psd || !theta || !event_offsets || !lnl) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN8(y_data);
+  GWX_ALIGN8(psd);
+  GWX_ALIGN8(theta);
+  GWX_ALIGN8(event_offsets);
+  GWX_ALIGN8(lnl);
   GWX_TRY(check_ws(workspace, workspace_bytes, gwx_log_likelihood_workspace(E, D, N, S)));
   GWX_TRY(ensure_init());
   cudaStream_t s = as_stream(stream);
@@ -422,6 +457,13 @@ int gwx_importance_weights(const double* lnl, const double* log_ratio, const int
   if (S > 0 && E == 0) return fail(GWX_ESHAPE, "samples without events");
   if (E == 0) return GWX_OK;
   if (!event_offsets || (S > 0 && !lnl)) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN8(lnl);
+  GWX_ALIGN8(log_ratio);
+  GWX_ALIGN8(event_offsets);
+  GWX_ALIGN8(weights);
+  GWX_ALIGN8(ess);
+  GWX_ALIGN8(efficiency);
+  GWX_ALIGN8(ln_evidence);
   GWX_TRY(check_ws(workspace, workspace_bytes, gwx_importance_weights_workspace(E)));
   GWX_TRY(ensure_init());
   return launched(launch_importance_weights(lnl, log_ratio, event_offsets, E, S, weights, ess, efficiency,
@@ -434,6 +476,8 @@ int gwx_rfft(const float* x, int64_t R, int64_t N, float* X, void* stream) {
   if (R < 0 || R > 0x7fffffffLL) return fail(GWX_ESHAPE, "R=%lld", (long long)R);
   if (R == 0) return GWX_OK;
   if (!x || !X) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN8(x);
+  GWX_ALIGN8(X);
   GWX_TRY(ensure_init());
   return launched(launch_rfft_rows(x, R, N, reinterpret_cast<float2*>(X), as_stream(stream)), "rfft");
 }
@@ -443,6 +487,8 @@ int gwx_irfft(const float* X, int64_t R, int64_t N, float* x, void* stream) {
   if (R < 0 || R > 0x7fffffffLL) return fail(GWX_ESHAPE, "R=%lld", (long long)R);
   if (R == 0) return GWX_OK;
   if (!x || !X) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN8(x);
+  GWX_ALIGN8(X);
   GWX_TRY(ensure_init());
   return launched(launch_irfft_rows(reinterpret_cast<const float2*>(X), R, N, x, as_stream(stream)), "irfft");
 }

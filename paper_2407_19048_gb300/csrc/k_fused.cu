@@ -79,7 +79,9 @@ __device__ __forceinline__ void wave_bin(const DrawCoef& c, int k, int k_lo, flo
 // One block per draw (persistent over draws), n/16 threads.  The D windows go
 // through one n-point shared buffer in turn; the waveform values of the bins a
 // thread owns are computed once per draw and shared by the detectors.
-template <int LOGN>
+// VEC: the background rows are 8-byte aligned (aligned base, even L), so the crop is
+// read as float pairs; otherwise it is read one float at a time.
+template <int LOGN, bool VEC>
 __global__ void __launch_bounds__((1 << LOGN) / 16, LOGN >= 13 ? 1 : 2)
     k_simulate(const DrawCoef* __restrict__ coef, const float* __restrict__ noise, int64_t L,
                const int64_t* __restrict__ offsets, const float* __restrict__ W, const float2* __restrict__ Wp,
@@ -134,17 +136,22 @@ __global__ void __launch_bounds__((1 << LOGN) / 16, LOGN >= 13 ? 1 : 2)
 #pragma unroll
           for (int r = 0; r < 8; ++r) {
             const int m = j + r * (n / 8);
-            const float2 q = __ldg(&row2[m]);
-            v[r] = q;
-            if (odd) {   // the window starts at an odd sample: pair (own .y, next pair's .x)
-              float nx;
-              if constexpr (T >= 32) {
-                nx = __shfl_down_sync(0xffffffffu, q.x, 1);
-                if (lane == 31) nx = __ldg(&row[2 * m + 2]);
-              } else {
-                nx = __ldg(&row[2 * m + 2]);
+            if constexpr (!VEC) {
+              const int o = odd ? 1 : 0;
+              v[r] = make_float2(__ldg(&row[o + 2 * m]), __ldg(&row[o + 2 * m + 1]));
+            } else {
+              const float2 q = __ldg(&row2[m]);
+              v[r] = q;
+              if (odd) {   // the window starts at an odd sample: pair (own .y, next pair's .x)
+                float nx;
+                if constexpr (T >= 32) {
+                  nx = __shfl_down_sync(0xffffffffu, q.x, 1);
+                  if (lane == 31) nx = __ldg(&row[2 * m + 2]);
+                } else {
+                  nx = __ldg(&row[2 * m + 2]);
+                }
+                v[r] = make_float2(q.y, nx);
               }
-              v[r] = make_float2(q.y, nx);
             }
           }
           dft8<false, false>(v);
@@ -234,27 +241,36 @@ __global__ void __launch_bounds__((1 << LOGN) / 16, LOGN >= 13 ? 1 : 2)
 #undef WIDX
 }
 
+template <int LG, bool VEC>
+static cudaError_t launch_simulate_lg(const DrawCoef* coef, const float* noise, int64_t L, const int64_t* offsets,
+                                      const float* W, const float2* Wp, int k_lo, int D, int64_t B, float* y,
+                                      cudaStream_t s) {
+  constexpr int NT = Plan16<LG>::T;
+  // one window at a time plus 16 waveform values per thread
+  const size_t smem = (size_t)(1 << LG) * sizeof(float2) + (size_t)16 * NT * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(k_simulate<LG, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_simulate<LG, VEC>, NT, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int64_t grid = (int64_t)sms * per_sm;
+  if (grid > B) grid = B;
+  k_simulate<LG, VEC><<<(unsigned)grid, NT, smem, s>>>(coef, noise, L, offsets, W, Wp, k_lo, D, B, y);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_simulate_fused(const DrawCoef* coef, const float* noise, int64_t L, const int64_t* offsets,
                                   const float* W, const float2* Wp, int k_lo, int D, int64_t B, int64_t N, double fs,
                                   float* y, cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
+  const bool vec = ((uintptr_t)noise % 8 == 0) && (L % 2 == 0);
   return dispatch_log<7, 13>(ilog2_exact(N / 2), [&](auto cst) {
     constexpr int LG = decltype(cst)::value;
-    constexpr int NT = Plan16<LG>::T;
-    // one window at a time plus 16 waveform values per thread
-    const size_t smem = (size_t)(1 << LG) * sizeof(float2) + (size_t)16 * NT * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(k_simulate<LG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_simulate<LG>, NT, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    int64_t grid = (int64_t)sms * per_sm;
-    if (grid > B) grid = B;
-    k_simulate<LG><<<(unsigned)grid, NT, smem, s>>>(coef, noise, L, offsets, W, Wp, k_lo, D, B, y);
-    return cudaGetLastError();
+    return vec ? launch_simulate_lg<LG, true>(coef, noise, L, offsets, W, Wp, k_lo, D, B, y, s)
+               : launch_simulate_lg<LG, false>(coef, noise, L, offsets, W, Wp, k_lo, D, B, y, s);
   });
 }
 

@@ -70,6 +70,8 @@ int gwx_whiten_static(const float* d, const double* psd, int64_t seg_len, double
   if (k >= (double)(N / 2)) return fail(GWX_ESHAPE, "gwx_whiten_static: f_lo is above the last usable bin");
   if (B == 0) return GWX_OK;
   if (!d || !psd || !y) return fail(GWX_EINVAL, "gwx_whiten_static: NULL array");
+  if ((((uintptr_t)d) | ((uintptr_t)psd) | ((uintptr_t)y)) & 7u)
+    return fail(GWX_EINVAL, "gwx_whiten_static: d, psd and y must be 8-byte aligned");
   int st = gwx_init();
   if (st != GWX_OK) return fail(st, "gwx_whiten_static: device set-up failed");
   float* W = nullptr;

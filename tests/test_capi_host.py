@@ -82,6 +82,9 @@ def test_validation_fails_before_any_launch(lib):
     p = _lib.GwxPrior(*([0.0] * 12))
     st = lib.gwx_sample_prior(p, 1, 0, 16, 100, 200, None, None, None)         # L < N
     assert st == -2
+    import ctypes
+    st = lib.gwx_rfft(ctypes.c_void_p(0x1004), 1, 256, ctypes.c_void_p(0x2000), None)
+    assert st == -1 and b"not 8-byte aligned" in lib.gwx_last_error()
     st = lib.gwx_importance_weights(None, None, None, 0, 5, None, None, None, None, None, 0, None)
     assert st == -2 and b"without events" in lib.gwx_last_error()
     st = lib.gwx_importance_weights(None, None, None, -1, 0, None, None, None, None, None, 0, None)

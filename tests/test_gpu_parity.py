@@ -259,6 +259,25 @@ def test_simulate_batch_small_matches_oracle(gwx):
     assert np.abs(host(y) - yr).max() <= 1e-4 * rms(yr)
 
 
+def test_simulate_batch_unaligned_background(gwx):
+    """A background that starts at an odd float (not 8-byte aligned) takes the scalar
+    crop-load path; same results."""
+    wl = workloads.workload("small")
+    step = 0
+    n, S = _gpu_background(gwx, wl, step)
+    D, L = n.shape
+    buf = torch.empty(D * L + 1, dtype=torch.float32, device=n.device)
+    buf[1:].copy_(n.reshape(-1))
+    n_mis = buf[1:].view(D, L)
+    assert n_mis.data_ptr() % 16 != 0
+    y, th, off = gwx.simulate_batch(wl["prior"], wl["param_seed"], step, n_mis, S, wl["seg_len"], wl["fs"],
+                                    wl["f_lo"], wl["dets"], 0.0, wl["B"], wl["N"])
+    ref = pipeline.simulate_batch(wl, step)
+    np.testing.assert_array_equal(host(off), ref["offsets"])
+    yr = ref["y"]
+    assert np.abs(host(y) - yr).max() <= 1e-4 * rms(yr)
+
+
 def test_simulate_batch_full_size_sampled(gwx):
     """Three-detector 4 s windows, 2048 draws, in the launch configuration the
     benchmark times; the oracle checks a sample of draws including the first
