@@ -1,11 +1,16 @@
 #!/usr/bin/env python3
 """Benchmark: whitened injections per second of the on-the-fly simulation path.
 
-One step is one whole per-batch pass of the method (Sec. 3.2) on the
-three-detector workload: a fresh coloured-noise background stretch, its Welch
-PSD, and ``simulate_batch`` (prior draws, TaylorF2 waveforms, projection, crops,
-injection, whitening) for B draws -- nine kernel launches through the libgwx C
-ABI.  The log-likelihood leg times ``log_likelihood`` on ragged events.
+One step is one batch of the method's per-batch pass (Sec. 3.2) on the
+three-detector workload: prior draws and the FP64 per-draw set-up (prepared one
+batch ahead on a side stream), and ``simulate_prepared`` (TaylorF2 waveforms,
+projection, crops, injection, whitening) for B draws, through the libgwx C ABI.
+The background (a fresh coloured-noise stretch and its Welch PSD) is regenerated
+inside the timed loop every ``--background-every`` steps (default 16; the paper
+keeps one background chunk for many batches); the line also reports the rate with
+a fresh background every step.  Further legs: end to end through pinned host
+memory, the log-likelihood with importance weights on ragged events, and the FFT
+kernels against cuFFT.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gwx|reference]
 
@@ -126,15 +131,18 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- oracle timing
-def oracle_rate(wl, min_seconds=10.0, draws_per_slice=128):
-    """Injections/s of the FP64 oracle: one background (noise + Welch) and prior for
-    the batch, then b-draw slices (waveform, projection, injection, whitening)
-    repeated for at least ``min_seconds``; throughput extrapolated to a B-draw step."""
+def oracle_rate(wl, min_seconds=10.0, draws_per_slice=128, background_every=1):
+    """Injections/s of the FP64 oracle: one background (noise + Welch) and the prior
+    for the batch, then b-draw slices (waveform, projection, injection, whitening)
+    repeated for at least ``min_seconds``; throughput extrapolated to a B-draw step
+    that carries 1/background_every of a background."""
     from oracle import pipeline, prior
     t0 = time.perf_counter()
     bg = pipeline.background(wl, 0)
-    prior.sample_prior(wl["prior"], wl["param_seed"], 0, wl["B"], wl["L"], wl["N"])
     t_bg = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    prior.sample_prior(wl["prior"], wl["param_seed"], 0, wl["B"], wl["L"], wl["N"])
+    t_prior = time.perf_counter() - t0
     b = min(draws_per_slice, wl["B"])
     reps, t_slices = 0, 0.0
     while t_slices < min_seconds or reps == 0:
@@ -142,10 +150,11 @@ def oracle_rate(wl, min_seconds=10.0, draws_per_slice=128):
         pipeline.simulate_batch(wl, 0, draws=range(reps * b % wl["B"], reps * b % wl["B"] + b), bg=bg)
         t_slices += time.perf_counter() - t1
         reps += 1
-    t_step = t_bg + wl["B"] / b * (t_slices / reps)
-    sample = ("oracle (numpy FP64, single thread) on %s: one background + prior (%.2f s) and %d slices of %d draws "
-              "(%.2f s); a %d-draw step extrapolated as t_bg + (B/b) t_slice" %
-              (wl["name"], t_bg, reps, b, t_slices, wl["B"]))
+    t_step = t_bg / background_every + t_prior + wl["B"] / b * (t_slices / reps)
+    sample = ("oracle (numpy FP64, single thread) on %s: one background (%.2f s, charged 1/%d per step), the prior "
+              "(%.2f s) and %d slices of %d draws (%.2f s); a %d-draw step extrapolated as "
+              "t_bg/%d + t_prior + (B/b) t_slice" %
+              (wl["name"], t_bg, background_every, t_prior, reps, b, t_slices, wl["B"], background_every))
     return wl["B"] / t_step, t_step, sample
 
 
@@ -155,10 +164,13 @@ def run_reference(args, wl):
         return 0
     vals, times = [], []
     b = 64
+    R = max(1, args.background_every)
     from oracle import pipeline, prior
+    bg = None
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        bg = pipeline.background(wl, i)
+        if bg is None or i % R == 0:
+            bg = pipeline.background(wl, i)
         prior.sample_prior(wl["prior"], wl["param_seed"], i, wl["B"], wl["L"], wl["N"])
         t_bg = time.perf_counter() - t0
         t1 = time.perf_counter()
@@ -169,14 +181,16 @@ def run_reference(args, wl):
             vals.append(wl["B"] / t_step)
             times.append(t_step)
     value = len(vals) * wl["B"] / sum(times)
-    sample = ("each step: oracle background (noise + Welch) and prior for %d draws, waveform/projection/"
-              "injection/whitening for %d of them, step time extrapolated as t_bg + (B/b) t_slice" % (wl["B"], b))
+    sample = ("each step: the oracle prior for %d draws (and a fresh background with its Welch PSD every %d steps, "
+              "as in the GPU arm), waveform/projection/injection/whitening for %d of the draws, step time "
+              "extrapolated as t_bg+prior + (B/b) t_slice" % (wl["B"], R, b))
     line = {"impl": "reference", "metric": "whitened injections/sec", "value": value, "unit": "injections/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded coloured aLIGO-fit noise)",
             "config": {"workload": describe(wl), "global_batch": wl["B"], "seq_len": wl["N"],
-                       "parallelism": "single host process (reference arm runs on rank 0 only)"},
+                       "parallelism": "single host process (reference arm runs on rank 0 only)",
+                       "background_every": R},
             "cpu_baseline": {"value": value, "unit": "injections/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "injections/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -296,35 +310,38 @@ def run_gpu(args, wl):
     import paper_2407_19048_gb300 as gwx
     import paper_2407_19048_gb300.simulator  # noqa: F401
     gwx.init()
-    sim = gwx.simulator.Simulator(wl)
+    sim = gwx.simulator.Simulator(wl, pipeline=True, background_every=args.background_every)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     B, D, N, L = wl["B"], len(wl["dets"]), wl["N"], wl["L"]
 
+    def timed_steps(sm, first, count, clocks=None):
+        """Run `count` steps from counter `first`; returns (per-step ms, fused-call ms,
+        wall seconds, launches)."""
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(count)]
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        if clocks is not None:
+            clocks.start()
+        l0 = sm.launches
+        t0 = time.perf_counter()
+        for i in range(count):
+            flush.zero_()
+            ev[i][0].record()
+            sm.step(step_counter(rank, first + i), mark=ev[i][1])
+            ev[i][2].record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if world > 1:
+            dist.barrier()
+        return ([e[0].elapsed_time(e[2]) for e in ev], [e[1].elapsed_time(e[2]) for e in ev], wall,
+                sm.launches - l0)
+
     for i in range(args.warmup):
         sim.step(step_counter(rank, i))
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
     clocks = ClockSampler(local)
-    clocks.start()
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    t_wall0 = time.perf_counter()
-    for i in range(args.steps):
-        flush.zero_()
-        c = step_counter(rank, args.warmup + i)
-        ev[i][0].record()
-        sim.step(c, mark=ev[i][1])
-        ev[i][2].record()
-    torch.cuda.synchronize()
-    t_wall = time.perf_counter() - t_wall0
-    if world > 1:
-        dist.barrier()
+    step_ms, sim_ms, t_wall, launches = timed_steps(sim, args.warmup, args.steps, clocks)
     clk = clocks.stop()
-    step_ms = [e[0].elapsed_time(e[2]) for e in ev]
-    sim_ms = [e[1].elapsed_time(e[2]) for e in ev]
     total_s = max_over_ranks(sum(step_ms) * 1e-3, dist if world > 1 else None)
     value = world * B * args.steps / total_s
 
@@ -337,6 +354,15 @@ def run_gpu(args, wl):
         if world > 1:
             dist.destroy_process_group()
         return 0
+
+    # the same loop with a fresh background (colored noise + Welch PSD) every step
+    sim1 = gwx.simulator.Simulator(wl, pipeline=True, background_every=1)
+    n1 = min(args.steps, 500)
+    for i in range(args.warmup):
+        sim1.step(step_counter(rank, args.warmup + args.steps + i))
+    ms1, _, _, _ = timed_steps(sim1, 2 * args.warmup + args.steps, n1)
+    value_bg1 = world * B * n1 / max_over_ranks(sum(ms1) * 1e-3, dist if world > 1 else None)
+    del sim1
 
     # end to end: background strain from pinned host memory in, products out to pinned host memory
     host_bg = torch.empty((D, L), dtype=torch.float32, pin_memory=True)
@@ -383,7 +409,7 @@ def run_gpu(args, wl):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, t_step, sample = oracle_rate(wl)
+        rate, t_step, sample = oracle_rate(wl, background_every=args.background_every)
         cpu = {"value": rate, "unit": "injections/s", "cores": 1, "kind": "oracle", "sample": sample}
 
     if world > 1:
@@ -397,12 +423,14 @@ def run_gpu(args, wl):
             "config": {"workload": describe(wl), "global_batch": B * world, "seq_len": N,
                        "parallelism": "%d independent replica(s), one per GPU, disjoint Philox counters" % world,
                        "l2": "256 MiB buffer written between timed steps (outside the events)",
-                       "step": "prepare_batch (side stream) + colored_noise + welch_psd + simulate_prepared "
-                               "(9 kernel launches)"},
+                       "step": "prepare_batch of the next batch on a side stream + simulate_prepared; background "
+                               "(colored_noise + welch_psd) regenerated every %d steps inside the timed loop"
+                               % args.background_every,
+                       "background_every": args.background_every},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "simulate_prepared call after the background (k_whiten_filter + k_simulate, "
-                                   "plus any wait for the side-stream preparation)",
+                         "kernel": "simulate_prepared call (k_whiten_filter, k_packed_filter, k_simulate), timed "
+                                   "from after the wait for the side-stream preparation",
                          "flops_per_injection": flops_per_injection(wl),
                          "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (recipe unit counts and "
                                        "maximum SM clock)",
@@ -413,7 +441,8 @@ def run_gpu(args, wl):
                     "d2h_bytes_per_step": d2h,
                     "path": "background strain H2D from pinned host memory, welch_psd + simulate_batch, "
                             "whitened batch + parameters + offsets D2H to pinned host memory"},
-            "gpu_launches": sim.LAUNCHES_PER_STEP * args.steps,
+            "gpu_launches": launches,
+            "value_background_every_step": value_bg1,
             "clocks": clk,
             "log_likelihood": ll,
             "fft_vs_cufft": fft_cmp,
@@ -433,6 +462,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="gwx", choices=["gwx", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workloads.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--background-every", type=int, default=16,
+                    help="regenerate the background and its PSD every this many steps")
     ap.add_argument("--batch", type=int, default=None, help="draws per step (default: the workload's)")
     ap.add_argument("--only-step", action="store_true",
                     help="time only the device step (no end-to-end or log-likelihood leg); for profiling")

@@ -325,6 +325,25 @@ def test_split_prepare_and_simulate_on_two_streams(gwx):
     np.testing.assert_array_equal(host(y1), host(sim2.y))
 
 
+def test_pipelined_simulator_matches_single_calls(gwx):
+    """The pipelined Simulator (next batch prepared on the side stream, two buffer sets,
+    background every 2 steps) gives the same batches as single simulate_batch calls."""
+    import paper_2407_19048_gb300.simulator as S
+    wl = workloads.workload("small", B=96)
+    sim = S.Simulator(wl, pipeline=True, background_every=2)
+    got = [[t.clone() for t in sim.step(st)] for st in (11, 12, 13)]
+    again = [t.clone() for t in sim.step(20)]          # a jump in the counter re-prepares
+    ref = S.Simulator(wl)
+    for st, g in zip((11, 12, 13, 20), got + [again]):
+        if st in (11, 13):                              # every second step: 11, 13
+            ref.background(st)
+        ref.simulate(st)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(host(g[2]), host(ref.offsets))
+        np.testing.assert_array_equal(host(g[1]), host(ref.theta))
+        np.testing.assert_array_equal(host(g[0]), host(ref.y))
+
+
 @pytest.mark.parametrize("B", [0, 1, 3, 1000])
 def test_simulate_batch_ragged_sizes(gwx, B):
     wl = workloads.workload("small")
