@@ -329,6 +329,9 @@ def run_gpu(args, wl):
             flush.zero_()
             ev[i][0].record()
             sm.step(step_counter(rank, first + i), mark=ev[i][1])
+            # the step ends when its fused pass and the next batch's preparation (side
+            # stream) are both done, so no work of the step runs during the L2 flush
+            torch.cuda.current_stream().wait_stream(sm.side)
             ev[i][2].record()
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0

@@ -16,7 +16,9 @@ draws, their waveforms, N background crops, injection and whitening.  One
 2 and 3 run every ``background_every`` batches (the paper keeps one background
 for many batches).  With ``pipeline=True`` the side stream prepares batch i + 1
 while batch i's fused pass runs (two buffer sets, used alternately), so the
-latency-bound FP64 set-up overlaps the previous pass instead of delaying the next.
+latency-bound FP64 set-up overlaps the previous pass instead of delaying the next;
+the passes then run on a high-priority stream so the preparation fills the SMs the
+fused pass leaves idle rather than taking them first.
 All buffers and workspaces are allocated once: a step performs no allocation and
 no host synchronisation.
 """
@@ -59,7 +61,11 @@ class Simulator:
         self._ws_sim = [_workspace(lib.gwx_simulate_batch_workspace(self.D, self.B, self.N), self.dev)
                         for _ in range(nbuf)]
         self.side = torch.cuda.Stream(device=self.dev)
+        # pipelined passes run on a high-priority stream, so that when both are pending
+        # the block scheduler dispatches the fused pass before the next batch's preparation
+        self.work = torch.cuda.Stream(device=self.dev, priority=-1) if self.pipeline else None
         self.ev_start = torch.cuda.Event()
+        self.ev_done = torch.cuda.Event()
         self._ev_prep = [torch.cuda.Event() for _ in range(nbuf)]
         self._slot = 0
         self._ready = None        # step counter already prepared in the current slot (pipeline)
@@ -140,22 +146,29 @@ class Simulator:
         background, the PSD and the wait for the preparation, just before the fused
         pass."""
         import torch
-        main = torch.cuda.current_stream(self.dev)
-        self.ev_start.record(main)
+        caller = torch.cuda.current_stream(self.dev)
+        self.ev_start.record(caller)
         self.side.wait_event(self.ev_start)
+        main = self.work if self.pipeline else caller
+        if main is not caller:
+            main.wait_event(self.ev_start)
         slot = self._slot
         if not self.pipeline or self._ready != step:
             with torch.cuda.stream(self.side):
                 self.prepare(step, slot)
                 self._ev_prep[slot].record(self.side)
-        if self._since_bg is None or self._since_bg >= self.background_every:
-            self.background(step)
-            self._since_bg = 0
-        self._since_bg += 1
-        main.wait_event(self._ev_prep[slot])
-        if mark is not None:
-            mark.record(main)
-        self.simulate_prepared(slot)
+        with torch.cuda.stream(main):
+            if self._since_bg is None or self._since_bg >= self.background_every:
+                self.background(step)
+                self._since_bg = 0
+            self._since_bg += 1
+            main.wait_event(self._ev_prep[slot])
+            if mark is not None:
+                mark.record(main)
+            self.simulate_prepared(slot)
+        if main is not caller:
+            self.ev_done.record(main)
+            caller.wait_event(self.ev_done)
         out = (self._y[slot], self._theta[slot], self._offsets[slot])
         if self.pipeline:
             nxt = 1 - slot
