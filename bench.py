@@ -44,7 +44,7 @@ SM_MAX_MHZ = 2070.0
 # ncu DRAM traffic (read + write bytes) of one k_simulate launch on the hl3
 # workload and the hash of the kernel sources it was measured on; see
 # profiles/k_simulate_hl3.md.  None until a capture matches the current sources.
-TRAFFIC = {"bytes_per_launch": 142819840, "sources_sha1": "9111b41493d24cb23459a100afe8161facd524ea"}
+TRAFFIC = {"bytes_per_launch": 143167488, "sources_sha1": "669042c740ab3146ca2e4ddc908e06f44498345a"}
 
 
 def describe(wl):
@@ -198,12 +198,13 @@ def run_reference(args, wl):
 
 
 # ----------------------------------------------------------------- GPU arm
-def loglike_leg(gwx, torch, wl, rank):
+def loglike_leg(gwx, torch, wl, rank, lo=2000, hi=50000):
     """ln L of ragged events at the importance-weighting scale: E=64 events with
-    U{2000..50000} samples each (about 1.7 million samples) drawn from the prior."""
+    U{lo..hi} samples each (by default 2000..50000, about 1.7 million samples) drawn
+    from the prior."""
     import numpy as np
     E = 64
-    counts = workloads.ragged_counts(41 + rank, E, 2000, 50000)
+    counts = workloads.ragged_counts(41 + rank, E, lo, hi)
     offs = np.concatenate([[0], np.cumsum(counts)])
     S = int(offs[-1])
     sim = gwx.simulator.Simulator(dict(wl, B=E))
@@ -249,6 +250,52 @@ def loglike_leg(gwx, torch, wl, rank):
                            "ms_per_chain": chain_ms, "ess_total": ess_total,
                            "median_efficiency": float(eff.median().item()),
                            "chain": "log_likelihood + importance_weights over all events"}}
+
+
+def serving_leg(gwx, torch, rank, n_events=1000):
+    """Streaming loop of the plain importance-sampling path on the 8 s, three-detector
+    geometry (N = 16384): 1000 events with U{2000..50000} samples each arrive one at a
+    time; per event the samples are drawn from the prior, scored by log_likelihood and
+    weighted by importance_weights, and the event's effective sample size is read back
+    to the host.  Latency is host time from the start of the event to that read."""
+    import numpy as np
+    wl = workloads.workload("sweep", B=n_events)
+    counts = workloads.ragged_counts(5 + rank, n_events, 2000, 50000)
+    sim = gwx.simulator.Simulator(wl)
+    y, _, _ = sim.step(step_counter(rank, 5000))
+    psd = sim.psd
+    smax = int(counts.max())
+    theta_flat = torch.empty(11 * smax, dtype=torch.float64, device="cuda")
+    lnl = torch.empty(smax, dtype=torch.float64, device="cuda")
+    offs = torch.zeros(2, dtype=torch.int64, device="cuda")
+
+    def event(e):
+        S = int(counts[e])
+        theta = theta_flat[:11 * S].view(11, S)
+        gwx.sample_prior(wl["prior"], 55, step_counter(rank, e), S, wl["L"], wl["N"], theta=theta)
+        offs[1] = S
+        out = gwx.log_likelihood(y[e:e + 1], psd, wl["seg_len"], wl["fs"], wl["f_lo"], wl["dets"], 0.0, theta, offs,
+                                 out=lnl[:S])
+        _, ess, _, _ = gwx.importance_weights(out, offs)
+        return float(ess[0].item())
+
+    for e in range(5):
+        event(e)
+    torch.cuda.synchronize()
+    lat = []
+    t0 = time.perf_counter()
+    for e in range(n_events):
+        a = time.perf_counter()
+        event(e)
+        lat.append(time.perf_counter() - a)
+    wall = time.perf_counter() - t0
+    lat_ms = np.array(lat) * 1e3
+    del sim, y
+    return {"events": n_events, "samples": int(counts.sum()), "events_per_s": n_events / wall,
+            "samples_per_s": float(counts.sum()) / wall, "latency_ms_p50": float(np.percentile(lat_ms, 50)),
+            "latency_ms_p99": float(np.percentile(lat_ms, 99)), "latency_ms_max": float(lat_ms.max()),
+            "workload": "8 s windows at 2048 Hz (N = 16384), H1+L1+V1, U{2000..50000} prior samples per event",
+            "per_event": "sample_prior + log_likelihood + importance_weights + host read of the ESS"}
 
 
 def cufft_leg(gwx, torch, sim, wl, fused_ms):
@@ -403,6 +450,7 @@ def run_gpu(args, wl):
 
     ll = loglike_leg(gwx, torch, wl, rank)
     fft_cmp = cufft_leg(gwx, torch, sim, wl, statistics.mean(sim_ms))
+    serve = serving_leg(gwx, torch, rank)
 
     sim_avg_s = statistics.mean(sim_ms) * 1e-3
     flops = flops_per_injection(wl) * B
@@ -449,6 +497,7 @@ def run_gpu(args, wl):
             "clocks": clk,
             "log_likelihood": ll,
             "fft_vs_cufft": fft_cmp,
+            "serving": serve,
             "wall_s_timed_region": t_wall,
         }
         print(json.dumps(line), flush=True)
@@ -470,6 +519,8 @@ def main(argv=None):
     ap.add_argument("--batch", type=int, default=None, help="draws per step (default: the workload's)")
     ap.add_argument("--only-step", action="store_true",
                     help="time only the device step (no end-to-end or log-likelihood leg); for profiling")
+    ap.add_argument("--only-loglike", default=None, metavar="LO,HI",
+                    help="run only the log-likelihood leg with U{LO..HI} samples per event; for profiling")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -478,6 +529,14 @@ def main(argv=None):
         wl["B"] = args.batch
     if args.impl == "reference":
         return run_reference(args, wl)
+    if args.only_loglike:
+        import torch
+        import paper_2407_19048_gb300 as gwx
+        import paper_2407_19048_gb300.simulator  # noqa: F401
+        lo, hi = (int(v) for v in args.only_loglike.split(","))
+        gwx.init()
+        print(json.dumps({"log_likelihood": loglike_leg(gwx, torch, wl, 0, lo, hi)}), flush=True)
+        return 0
     return run_gpu(args, wl)
 
 
