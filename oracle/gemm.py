@@ -1,0 +1,39 @@
+"""Dense products for the learned part (oracle; test infrastructure).
+
+The network that the simulated batches train (the embedding network of Sec. 4 and the
+normalizing flow of Sec. 5) is a stack of dense contractions; its GPU kernels take
+bfloat16 operands and accumulate in FP32.  The oracle states the product in FP64 on
+the exact values of the bfloat16 operands:
+
+    C[m][n] = sum_k A[m][k] B[n][k]        (A is M x K, B is N x K, both row-major),
+
+and the bfloat16 format itself: 1 sign bit, 8 exponent bits (bias 127) and 7 stored
+mantissa bits, i.e. the upper half of an IEEE binary32 word.
+"""
+import numpy as np
+
+
+def bf16_to_f64(bits):
+    """Decode bfloat16 bit patterns (uint16 array) exactly: the pattern is the upper
+    16 bits of a binary32 value."""
+    b = np.asarray(bits, dtype=np.uint16).astype(np.uint32) << 16
+    return b.view(np.float32).astype(np.float64)
+
+
+def f64_to_bf16(x):
+    """Round to the nearest bfloat16, ties to even (finite inputs), as bit patterns."""
+    f = np.asarray(x, dtype=np.float64).astype(np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    r = (u + 0x7FFF + lsb) >> 16
+    return r.astype(np.uint16)
+
+
+def gemm_nt(a_bits, b_bits):
+    """C = A B^T in FP64 from bfloat16 operands A [M][K], B [N][K]."""
+    return bf16_to_f64(a_bits) @ bf16_to_f64(b_bits).T
+
+
+def abs_product_sum(a_bits, b_bits):
+    """sum_k |A[m][k]| |B[n][k]|: the scale of the rounding error of the FP32 sum."""
+    return np.abs(bf16_to_f64(a_bits)) @ np.abs(bf16_to_f64(b_bits)).T

@@ -92,3 +92,13 @@ def ragged_counts(seed, E, lo, hi, zeros=0):
     c = np.random.default_rng(seed).integers(lo, hi + 1, E).astype(np.int64)
     c[:zeros] = 0
     return c
+
+
+def random_bf16_bits(seed, shape, exp_lo=-8, exp_hi=1):
+    """Random bfloat16 values as their 16-bit patterns (uint16): random sign, exponent
+    in [exp_lo, exp_hi] and mantissa bits.  Both sides decode the same bits."""
+    rng = np.random.default_rng(seed)
+    sign = rng.integers(0, 2, shape).astype(np.uint16) << 15
+    exp = (rng.integers(exp_lo, exp_hi + 1, shape) + 127).astype(np.uint16) << 7
+    man = rng.integers(0, 128, shape).astype(np.uint16)
+    return (sign | exp | man).astype(np.uint16)
