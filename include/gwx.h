@@ -57,7 +57,7 @@ extern "C" {
 #define GWX_ESHAPE       -2   /* unsupported or inconsistent sizes         */
 #define GWX_ECUDA        -3   /* a CUDA runtime call failed                */
 #define GWX_ENOMEM       -4   /* workspace smaller than *_workspace()      */
-#define GWX_ETIMEOUT     -5   /* reserved: bounded device wait expired     */
+#define GWX_ETIMEOUT     -5   /* a bounded device wait expired             */
 #define GWX_EUNSUPPORTED -6   /* valid request this build does not offer   */
 
 /* ---- waveform models ---------------------------------------------------- */
@@ -278,6 +278,26 @@ size_t gwx_importance_weights_workspace(int64_t E);
 int gwx_importance_weights(const double* lnl, const double* log_ratio, const int64_t* event_offsets,
                            int64_t E, int64_t S, double* weights, double* ess, double* efficiency,
                            double* ln_evidence, void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---- learned part: dense products -----------------------------------------------
+ * C = A B^T, the contraction of the dense layers of the embedding network (Sec. 4) and
+ * the normalizing flow (Sec. 5) that train on the simulated batches:
+ *   C[m][n] = sum_k A[m][k] B[n][k],
+ * A bfloat16 [M][K] and B bfloat16 [N][K] row-major (K contiguous), C [M][N] row-major
+ * in FP32 (c_dtype GWX_F32) or bfloat16 rounded to nearest even (GWX_BF16).  The
+ * products accumulate in FP32 in tensor memory (tcgen05.mma), operands arrive by TMA.
+ * Sizes: 1 <= M <= 2^23, 1 <= N, 8 <= K < 2^31 with K % 8 == 0; A, B and C 16-byte
+ * aligned.  Rows and columns past M, N and the K tail are handled (zero fill, masked
+ * stores).  A kernel whose bounded wait for its own copies expires skips its stores
+ * and records it for gwx_device_status. */
+#define GWX_F32  0
+#define GWX_BF16 1
+int gwx_gemm_bf16(const void* A, const void* B, void* C, int64_t M, int64_t N, int64_t K, int c_dtype,
+                  void* stream);
+
+/* Synchronises the current device; returns GWX_ETIMEOUT (and clears the record) if a
+ * kernel gave up a bounded wait since the last call, else GWX_OK. */
+int gwx_device_status(void);
 
 /* ---- transforms (the FFT kernels of the steps above, exposed for checking) ----
  * gwx_rfft:  X[r] = rfft(x[r]) for R rows of N real samples (numpy convention,

@@ -24,7 +24,7 @@ NPARAM = 11
 
 __all__ = ["GwxError", "version", "init", "detector_geometry", "sample_prior", "generate_waveforms", "project",
            "colored_noise", "welch_psd", "inject", "whiten", "simulate_batch", "log_likelihood",
-           "importance_weights", "rfft", "irfft",
+           "importance_weights", "gemm_bf16", "device_status", "rfft", "irfft",
            "workspace_bytes", "TAYLORF2", "IMRPHENOMD", "DETECTORS"]
 
 
@@ -254,6 +254,29 @@ def importance_weights(lnl, event_offsets, log_ratio=None):
                                       _ptr(event_offsets), E, S, _ptr(w), _ptr(ess), _ptr(eff), _ptr(lnz),
                                       _ptr(ws), nb, _stream()))
     return w, ess, eff, lnz
+
+
+def gemm_bf16(A, B, out=None, out_dtype=None):
+    """C = A B^T on the tensor cores: A bfloat16 [M][K], B bfloat16 [N][K], C float32
+    (default) or bfloat16 [M][N]."""
+    torch = _torch()
+    _dev(A, torch.bfloat16, "A")
+    _dev(B, torch.bfloat16, "B")
+    M, K = A.shape
+    N = B.shape[0]
+    if B.shape[1] != K:
+        raise ValueError("A is [M][K] and B is [N][K]")
+    if out is None:
+        out = torch.empty((M, N), dtype=out_dtype or torch.float32, device=A.device)
+    code = {torch.float32: 0, torch.bfloat16: 1}[out.dtype]
+    _check(_lib.load().gwx_gemm_bf16(_ptr(A), _ptr(B), _ptr(out), M, N, K, code, _stream()))
+    return out
+
+
+def device_status():
+    """Raise GwxError(GWX_ETIMEOUT) if a kernel gave up a bounded wait since the last
+    call (synchronises the device)."""
+    _check(_lib.load().gwx_device_status())
 
 
 def rfft(x, out=None):

@@ -471,6 +471,27 @@ int gwx_importance_weights(const double* lnl, const double* log_ratio, const int
                   "importance_weights");
 }
 
+int gwx_gemm_bf16(const void* A, const void* B, void* C, int64_t M, int64_t N, int64_t K, int c_dtype,
+                  void* stream) {
+  if (M < 1 || M > ((int64_t)1 << 23) || N < 1 || N > 0x7fffffffLL || K < 8 || K > 0x7fffffffLL || K % 8 != 0)
+    return fail(GWX_ESHAPE, "gemm sizes M=%lld N=%lld K=%lld (need K %% 8 == 0)", (long long)M, (long long)N,
+                (long long)K);
+  if (c_dtype != GWX_F32 && c_dtype != GWX_BF16) return fail(GWX_EINVAL, "c_dtype %d", c_dtype);
+  if (!A || !B || !C) return fail(GWX_EINVAL, "NULL array");
+  if ((((uintptr_t)A) | ((uintptr_t)B) | ((uintptr_t)C)) & 15u)
+    return fail(GWX_EINVAL, "A, B and C must be 16-byte aligned");
+  GWX_TRY(ensure_init());
+  return launched(launch_gemm_bf16(A, B, C, M, N, K, c_dtype == GWX_BF16, as_stream(stream)), "gemm_bf16");
+}
+
+int gwx_device_status(void) {
+  GWX_TRY(ensure_init());
+  int st = 0;
+  GWX_TRY(launched(gemm_status(&st), "device status"));
+  if (st != 0) return fail(GWX_ETIMEOUT, "a kernel gave up waiting for its own copies; its output is incomplete");
+  return GWX_OK;
+}
+
 int gwx_rfft(const float* x, int64_t R, int64_t N, float* X, void* stream) {
   GWX_TRY(check_window(N));
   if (R < 0 || R > 0x7fffffffLL) return fail(GWX_ESHAPE, "R=%lld", (long long)R);

@@ -1,0 +1,283 @@
+// k_gemm.cu -- C = A B^T with bfloat16 operands and FP32 accumulation on the fifth-
+// generation tensor cores: the dense layers of the learned part (the embedding network
+// of Sec. 4 and the normalizing flow of Sec. 5) are products of this form.
+//
+// One CTA computes a 128 x 256 tile of C with four warps:
+// - thread 0 streams 128 x 64 (A) and 256 x 64 (B) bfloat16 tiles into shared memory with
+//   TMA (cp.async.bulk.tensor, 128-byte swizzle), four stages deep, each stage completing
+//   on a "full" mbarrier;
+// - thread 32 issues tcgen05.mma (M 128, N 256, K 16; four per stage) into a 128 x 256
+//   FP32 accumulator in tensor memory and commits each stage to an "empty" mbarrier that
+//   hands the stage back to the producer, and the last one to a "done" mbarrier;
+// - all four warps then read the accumulator with tcgen05.ld (warp w owns rows 32 w ..
+//   32 w + 31) and store C.
+// Every mbarrier wait is bounded: on expiry the CTA records a status, skips its stores,
+// frees its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include "gwx_internal.h"
+
+namespace gwx {
+
+namespace {
+
+constexpr int GM = 128, GN = 256, GK = 64, STAGES = 4;
+constexpr uint32_t A_BYTES = GM * GK * 2;               // 16 KiB
+constexpr uint32_t B_BYTES = GN * GK * 2;               // 32 KiB
+constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr uint32_t TMEM_COLS = GN;                      // FP32 accumulator columns
+constexpr uint32_t WAIT_POLLS = 1u << 22;
+constexpr size_t GEMM_SMEM = (size_t)STAGES * STAGE_BYTES + 1024;   // + alignment slack
+
+// Instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1), A and B
+// bfloat16 (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits
+// 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GN >> 3) << 17) |
+                           ((uint32_t)(GM >> 4) << 24);
+
+__device__ int g_gemm_status;
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// Poll phase `parity` of a barrier at most `limit` times; false on expiry.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major bfloat16 tile written by TMA with the
+// 128-byte swizzle: rows of 64 elements (128 B), 8-row groups 1024 B apart (stride byte
+// offset), descriptor version 1 (bits 46-47), swizzle mode 2 = 128 B (bits 61-63).  The
+// leading byte offset is not used by swizzled K-major layouts (set to 16 B).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's accumulator row.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <bool OUT_BF16>
+__global__ void __launch_bounds__(128, 1)
+    k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, void* __restrict__ C,
+                int M, int N, int K) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t base = (su32(smem_raw) + 1023u) & ~1023u;   // 1024-byte aligned stages
+  const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
+  const int KB = (K + GK - 1) / GK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(su32(&full[s]), 1);
+      mbar_init(su32(&empty[s]), 1);
+    }
+    mbar_init(su32(&done), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  if (threadIdx.x == 0) {
+    // producer: stage kb % STAGES is free again once the MMAs of kb - STAGES completed
+    for (int kb = 0; kb < KB; ++kb) {
+      const int s = kb % STAGES;
+      if (kb >= STAGES && !mbar_wait(su32(&empty[s]), (uint32_t)((kb / STAGES) - 1) & 1u, WAIT_POLLS)) {
+        atomicExch(&abort_flag, 1);
+        break;
+      }
+      const uint32_t sa = base + (uint32_t)s * STAGE_BYTES, sb = sa + A_BYTES;
+      mbar_expect_tx(su32(&full[s]), STAGE_BYTES);
+      tma_load_2d(sa, &ta, kb * GK, m0, su32(&full[s]));
+      tma_load_2d(sb, &tb, kb * GK, n0, su32(&full[s]));
+    }
+  } else if (threadIdx.x == 32) {
+    // MMA issuer
+    bool ok = true;
+    for (int kb = 0; kb < KB; ++kb) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(su32(&full[s]), (uint32_t)(kb / STAGES) & 1u, WAIT_POLLS)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = base + (uint32_t)s * STAGE_BYTES, sb = sa + A_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < GK / 16; ++kk)   // 16 bfloat16 = 32 bytes along K per instruction
+        mma_bf16(tmem, sw128_desc(sa + 32u * kk), sw128_desc(sb + 32u * kk), (kb | kk) != 0);
+      mma_commit(su32(&empty[s]));
+    }
+    if (!ok) atomicExch(&abort_flag, 1);
+    mma_commit(su32(&done));   // arrives once every issued MMA has completed
+  }
+  __syncwarp();
+
+  // epilogue: row 32 warp + lane of the tile, 32 columns per tensor-memory load
+  const bool have = mbar_wait(su32(&done), 0u, WAIT_POLLS);
+  __syncthreads();   // orders the issuers' abort_flag writes before the reads below
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int row = m0 + 32 * warp + lane;
+  // warp-uniform: tcgen05.ld is executed by whole warps
+  const bool stop = __any_sync(0xffffffffu, !have || abort_flag != 0);
+  if (!stop) {
+#pragma unroll 1
+    for (int c = 0; c < GN / 32; ++c) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * c), v);
+      const int col0 = n0 + 32 * c;
+      if (row >= M || col0 >= N) continue;
+      if constexpr (OUT_BF16) {
+        __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(C) + (int64_t)row * N + col0;
+        if (col0 + 32 <= N && (N % 8) == 0) {
+#pragma unroll
+          for (int i = 0; i < 32; i += 8) {
+            uint4 pk;
+            __nv_bfloat162 h0 = __floats2bfloat162_rn(v[i], v[i + 1]), h1 = __floats2bfloat162_rn(v[i + 2], v[i + 3]);
+            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[i + 4], v[i + 5]), h3 = __floats2bfloat162_rn(v[i + 6], v[i + 7]);
+            pk.x = *reinterpret_cast<uint32_t*>(&h0);
+            pk.y = *reinterpret_cast<uint32_t*>(&h1);
+            pk.z = *reinterpret_cast<uint32_t*>(&h2);
+            pk.w = *reinterpret_cast<uint32_t*>(&h3);
+            *reinterpret_cast<uint4*>(out + i) = pk;
+          }
+        } else {
+          for (int i = 0; i < 32 && col0 + i < N; ++i) out[i] = __float2bfloat16_rn(v[i]);
+        }
+      } else {
+        float* out = reinterpret_cast<float*>(C) + (int64_t)row * N + col0;
+        if (col0 + 32 <= N && (N % 4) == 0) {
+#pragma unroll
+          for (int i = 0; i < 32; i += 4)
+            *reinterpret_cast<float4*>(out + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+        } else {
+          for (int i = 0; i < 32 && col0 + i < N; ++i) out[i] = v[i];
+        }
+      }
+    }
+  } else if (threadIdx.x == 0) {
+    atomicExch(&g_gemm_status, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// Row-major bfloat16 [rows][K] as a 2-D tensor map with boxes of box_rows x 64.
+bool make_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t K, uint32_t box_rows) {
+  auto enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+  cuuint32_t box[2] = {(cuuint32_t)GK, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+cudaError_t launch_gemm_bf16(const void* A, const void* B, void* C, int64_t M, int64_t N, int64_t K, bool out_bf16,
+                             cudaStream_t s) {
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, A, M, K, GM) || !make_map(&tb, B, N, K, GN)) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)((N + GN - 1) / GN), (unsigned)((M + GM - 1) / GM));
+  cudaError_t e;
+  if (out_bf16) {
+    e = cudaFuncSetAttribute(k_gemm_bf16<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
+    if (e != cudaSuccess) return e;
+    k_gemm_bf16<true><<<grid, 128, GEMM_SMEM, s>>>(ta, tb, C, (int)M, (int)N, (int)K);
+  } else {
+    e = cudaFuncSetAttribute(k_gemm_bf16<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
+    if (e != cudaSuccess) return e;
+    k_gemm_bf16<false><<<grid, 128, GEMM_SMEM, s>>>(ta, tb, C, (int)M, (int)N, (int)K);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t gemm_status(int* status) {
+  int zero = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpyFromSymbol(status, g_gemm_status, sizeof(int));
+  if (e == cudaSuccess && *status != 0) e = cudaMemcpyToSymbol(g_gemm_status, &zero, sizeof(int));
+  return e;
+}
+
+}  // namespace gwx

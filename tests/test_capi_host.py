@@ -85,6 +85,11 @@ def test_validation_fails_before_any_launch(lib):
     import ctypes
     st = lib.gwx_rfft(ctypes.c_void_p(0x1004), 1, 256, ctypes.c_void_p(0x2000), None)
     assert st == -1 and b"not 8-byte aligned" in lib.gwx_last_error()
+    st = lib.gwx_gemm_bf16(None, None, None, 128, 256, 12, 0, None)
+    assert st == -2 and b"K % 8" in lib.gwx_last_error()
+    st = lib.gwx_gemm_bf16(ctypes.c_void_p(0x1008), ctypes.c_void_p(0x2000), ctypes.c_void_p(0x3000), 8, 8, 8, 0,
+                           None)
+    assert st == -1 and b"16-byte aligned" in lib.gwx_last_error()
     st = lib.gwx_importance_weights(None, None, None, 0, 5, None, None, None, None, None, 0, None)
     assert st == -2 and b"without events" in lib.gwx_last_error()
     st = lib.gwx_importance_weights(None, None, None, -1, 0, None, None, None, None, None, 0, None)

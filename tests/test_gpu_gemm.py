@@ -1,0 +1,79 @@
+"""Parity of gwx_gemm_bf16 (tcgen05 tensor cores) with oracle.gemm (needs a GPU).
+
+Both sides take the same bfloat16 bit patterns.  The kernel forms exact products and
+sums them in FP32, so |C - C_oracle| <= 2 K 2^-24 sum_k |A_mk| |B_nk| (a bound on
+recursive FP32 summation of K terms); a bfloat16 output adds the rounding to 8
+significant bits, at most 2^-8 |C|.
+"""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import gemm
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gwx():
+    import paper_2407_19048_gb300 as m
+    from paper_2407_19048_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "the gpu tests need a CUDA device"
+    m.init()
+    return m
+
+
+def _bf16(bits):
+    return torch.from_numpy(bits.view(np.int16)).cuda().view(torch.bfloat16)
+
+
+def _check(gwx, M, N, K, seed, out_dtype=torch.float32):
+    a = workloads.random_bf16_bits(seed, (M, K))
+    b = workloads.random_bf16_bits(seed + 1, (N, K))
+    C = gwx.gemm_bf16(_bf16(a), _bf16(b), out_dtype=out_dtype)
+    gwx.device_status()
+    got = C.float().cpu().numpy().astype(np.float64)
+    ref = gemm.gemm_nt(a, b)
+    tol = 2.0 * K * 2.0 ** -24 * gemm.abs_product_sum(a, b)
+    if out_dtype == torch.bfloat16:
+        tol = tol * (1.0 + 2.0 ** -8) + 2.0 ** -8 * np.abs(ref)
+    err = np.abs(got - ref)
+    assert np.all(err <= tol + 1e-30), (float(err.max()), float((err / (tol + 1e-30)).max()))
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (256, 512, 256), (384, 768, 1024), (128, 256, 8)])
+def test_gemm_full_tiles(gwx, M, N, K):
+    _check(gwx, M, N, K, 60 + K)
+
+
+@pytest.mark.parametrize("M,N,K", [(1, 1, 8), (200, 300, 72), (1000, 700, 520), (129, 257, 136)])
+def test_gemm_ragged(gwx, M, N, K):
+    """Rows, columns and the K tail past the 128 x 256 x 64 tiles."""
+    _check(gwx, M, N, K, 70 + M)
+
+
+@pytest.mark.parametrize("M,N,K", [(256, 512, 192), (130, 300, 64)])
+def test_gemm_bf16_output(gwx, M, N, K):
+    _check(gwx, M, N, K, 80 + N, out_dtype=torch.bfloat16)
+
+
+def test_gemm_large(gwx):
+    """A 2048 x 4096 x 4096 product (many tiles, 64 k-blocks: the stage ring wraps)."""
+    M, N, K = 2048, 4096, 4096
+    a = workloads.random_bf16_bits(90, (M, K))
+    b = workloads.random_bf16_bits(91, (N, K))
+    C = gwx.gemm_bf16(_bf16(a), _bf16(b))
+    gwx.device_status()
+    rows = np.array([0, 1, 127, 128, 1000, 2047])
+    got = C[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64)
+    ref = gemm.gemm_nt(a[rows], b)
+    tol = 2.0 * K * 2.0 ** -24 * gemm.abs_product_sum(a[rows], b)
+    assert np.all(np.abs(got - ref) <= tol)
+
+
+def test_gemm_rejects_bad_arguments(gwx):
+    a = torch.zeros((16, 12), dtype=torch.bfloat16, device="cuda")
+    with pytest.raises(gwx.GwxError):
+        gwx.gemm_bf16(a, a)          # K = 12 is not a multiple of 8
