@@ -47,6 +47,17 @@ SM_MAX_MHZ = 2070.0
 TRAFFIC = {"bytes_per_launch": 143167488, "sources_sha1": "669042c740ab3146ca2e4ddc908e06f44498345a"}
 
 
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+MEASURED_PEAKS = _measured_peaks()
+
+
 def describe(wl):
     return ("%s: TaylorF2 3.5PN (IMRPhenomD tables unavailable), %s, fs=%d Hz, %g s windows (N=%d), "
             "B=%d draws/step, %g s background (L=%d), Welch %g s Hann segments 50%% overlap, f_lo=%g Hz"
@@ -298,6 +309,42 @@ def serving_leg(gwx, torch, rank, n_events=1000):
             "per_event": "sample_prior + log_likelihood + importance_weights + host read of the ESS"}
 
 
+def gemm_leg(gwx, torch, shape=(8192, 8192, 8192)):
+    """The learned part's dense product C = A B^T (bfloat16 in, FP32 accumulation,
+    bfloat16 out) on the tensor cores, against cuBLAS (torch.matmul) on the same GPU."""
+    M, N, K = shape
+    g = torch.Generator(device="cuda")
+    g.manual_seed(7)
+    A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+    B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+    C = torch.empty(M, N, device="cuda", dtype=torch.bfloat16)
+
+    def timed(fn, reps=20):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    ms = timed(lambda: gwx.gemm_bf16(A, B, out=C))
+    gwx.device_status()
+    ms_cublas = timed(lambda: torch.matmul(A, B.t(), out=C))
+    flops = 2.0 * M * N * K
+    peak = MEASURED_PEAKS.get("bf16_tflops")
+    achieved = flops / ms / 1e9
+    del A, B, C
+    return {"shape": [M, N, K], "ms": ms, "tflops": achieved, "cublas_ms": ms_cublas,
+            "cublas_tflops": flops / ms_cublas / 1e9,
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak if peak else None,
+                         "peak_basis": "measured bf16 burst (MEASURED_PEAKS.json)"}}
+
+
 def cufft_leg(gwx, torch, sim, wl, fused_ms):
     """The shared-memory FFT kernels against cuFFT (called through torch.fft) on the
     batch's shape, B x D rows of N real samples.  cuFFT is a timing baseline here only:
@@ -451,6 +498,7 @@ def run_gpu(args, wl):
     ll = loglike_leg(gwx, torch, wl, rank)
     fft_cmp = cufft_leg(gwx, torch, sim, wl, statistics.mean(sim_ms))
     serve = serving_leg(gwx, torch, rank)
+    gemm = gemm_leg(gwx, torch)
 
     sim_avg_s = statistics.mean(sim_ms) * 1e-3
     flops = flops_per_injection(wl) * B
@@ -498,6 +546,7 @@ def run_gpu(args, wl):
             "log_likelihood": ll,
             "fft_vs_cufft": fft_cmp,
             "serving": serve,
+            "gemm_bf16": gemm,
             "wall_s_timed_region": t_wall,
         }
         print(json.dumps(line), flush=True)

@@ -2,16 +2,17 @@
 // generation tensor cores: the dense layers of the learned part (the embedding network
 // of Sec. 4 and the normalizing flow of Sec. 5) are products of this form.
 //
-// One CTA computes a 128 x 256 tile of C with four warps:
-// - thread 0 streams 128 x 64 (A) and 256 x 64 (B) bfloat16 tiles into shared memory with
+// Persistent CTAs (one per SM) walk the 128 x 256 tiles of C; per CTA:
+// - warp 0 streams 128 x 64 (A) and 256 x 64 (B) bfloat16 tiles into shared memory with
 //   TMA (cp.async.bulk.tensor, 128-byte swizzle), four stages deep, each stage completing
 //   on a "full" mbarrier;
-// - thread 32 issues tcgen05.mma (M 128, N 256, K 16; four per stage) into a 128 x 256
-//   FP32 accumulator in tensor memory and commits each stage to an "empty" mbarrier that
-//   hands the stage back to the producer, and the last one to a "done" mbarrier;
-// - all four warps then read the accumulator with tcgen05.ld (warp w owns rows 32 w ..
-//   32 w + 31) and store C.
-// Every mbarrier wait is bounded: on expiry the CTA records a status, skips its stores,
+// - warp 1 allocates 512 tensor-memory columns and issues tcgen05.mma (M 128, N 256,
+//   K 16; four per stage) into one of two 256-column FP32 accumulators, committing each
+//   stage to an "empty" mbarrier (the stage goes back to the producer) and each tile to a
+//   "tfull" mbarrier;
+// - warps 2-5 drain the accumulator of the previous tile with tcgen05.ld (lane quarter
+//   warp % 4 = rows 32 q .. 32 q + 31) and store C, while the next tile accumulates.
+// Every mbarrier wait is bounded: on expiry the CTA records a status, stops storing,
 // frees its tensor memory and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -109,31 +110,55 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Tile t of a persistent CTA -> (tm, tn): bands of GROUP tile-rows, columns fastest
+// within a band, so the CTAs working at the same time share a few A and B panels in L2.
+constexpr int GROUP = 16;
+__device__ __forceinline__ void tile_coords(int t, int TM, int TN, int& tm, int& tn) {
+  const int band = t / (GROUP * TN);
+  const int r = t - band * GROUP * TN;
+  const int rows = min(GROUP, TM - band * GROUP);
+  tm = band * GROUP + r % rows;
+  tn = r / rows;
+}
+
+// Persistent, warp-specialised: warp 0 lane 0 produces (TMA), warp 1 allocates tensor
+// memory and its lane 0 issues the MMAs, warps 2-5 drain accumulators.  Two 256-column
+// accumulators alternate between tiles, so a tile's epilogue overlaps the next tile's
+// main loop; "tfull" (MMA commit) and "tempty" (one arrival per epilogue warp) hand them
+// over.
 template <bool OUT_BF16>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(192, 1)
     k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, void* __restrict__ C,
                 int M, int N, int K) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t base = (su32(smem_raw) + 1023u) & ~1023u;   // 1024-byte aligned stages
-  const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
   const int KB = (K + GK - 1) / GK;
+  const int TM = (M + GM - 1) / GM, TN = (N + GN - 1) / GN;
+  const int tiles = TM * TN;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(su32(&full[s]), 1);
       mbar_init(su32(&empty[s]), 1);
     }
-    mbar_init(su32(&done), 1);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(su32(&tfull[a]), 1);
+      mbar_init(su32(&tempty[a]), 4);
+    }
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_slot)),
-                 "r"(TMEM_COLS)
+                 "r"(2 * TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -142,89 +167,118 @@ __global__ void __launch_bounds__(128, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
 
-  if (threadIdx.x == 0) {
-    // producer: stage kb % STAGES is free again once the MMAs of kb - STAGES completed
-    for (int kb = 0; kb < KB; ++kb) {
-      const int s = kb % STAGES;
-      if (kb >= STAGES && !mbar_wait(su32(&empty[s]), (uint32_t)((kb / STAGES) - 1) & 1u, WAIT_POLLS)) {
-        atomicExch(&abort_flag, 1);
-        break;
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t it = 0;
+      for (int t = blockIdx.x; t < tiles && !*(volatile int*)&abort_flag; t += gridDim.x) {
+        int tm, tn;
+        tile_coords(t, TM, TN, tm, tn);
+        for (int kb = 0; kb < KB; ++kb, ++it) {
+          const uint32_t s = it % STAGES;
+          if (it >= STAGES && !mbar_wait(su32(&empty[s]), ((it / STAGES) - 1) & 1u, WAIT_POLLS)) {
+            atomicExch(&abort_flag, 1);
+            break;
+          }
+          const uint32_t sa = base + s * STAGE_BYTES, sb = sa + A_BYTES;
+          mbar_expect_tx(su32(&full[s]), STAGE_BYTES);
+          tma_load_2d(sa, &ta, kb * GK, tm * GM, su32(&full[s]));
+          tma_load_2d(sb, &tb, kb * GK, tn * GN, su32(&full[s]));
+        }
       }
-      const uint32_t sa = base + (uint32_t)s * STAGE_BYTES, sb = sa + A_BYTES;
-      mbar_expect_tx(su32(&full[s]), STAGE_BYTES);
-      tma_load_2d(sa, &ta, kb * GK, m0, su32(&full[s]));
-      tma_load_2d(sb, &tb, kb * GK, n0, su32(&full[s]));
     }
-  } else if (threadIdx.x == 32) {
-    // MMA issuer
-    bool ok = true;
-    for (int kb = 0; kb < KB; ++kb) {
-      const int s = kb % STAGES;
-      if (!mbar_wait(su32(&full[s]), (uint32_t)(kb / STAGES) & 1u, WAIT_POLLS)) {
-        ok = false;
-        break;
+  } else if (warp == 1) {
+    if (lane == 0) {
+      uint32_t it = 0, tl = 0;
+      for (int t = blockIdx.x; t < tiles && !*(volatile int*)&abort_flag; t += gridDim.x, ++tl) {
+        const uint32_t acc = tl & 1u;
+        if (tl >= 2 && !mbar_wait(su32(&tempty[acc]), ((tl >> 1) - 1) & 1u, WAIT_POLLS)) {
+          atomicExch(&abort_flag, 1);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + acc * TMEM_COLS;
+        bool ok = true;
+        for (int kb = 0; kb < KB; ++kb, ++it) {
+          const uint32_t s = it % STAGES;
+          if (!mbar_wait(su32(&full[s]), (it / STAGES) & 1u, WAIT_POLLS)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sa = base + s * STAGE_BYTES, sb = sa + A_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < GK / 16; ++kk)   // 16 bfloat16 = 32 bytes along K per instruction
+            mma_bf16(d, sw128_desc(sa + 32u * kk), sw128_desc(sb + 32u * kk), (kb | kk) != 0);
+          mma_commit(su32(&empty[s]));
+        }
+        if (!ok) atomicExch(&abort_flag, 1);
+        mma_commit(su32(&tfull[acc]));   // arrives once the tile's MMAs have completed
+        if (!ok) break;
       }
+    }
+  } else {
+    // epilogue warps 2-5; tensor-memory lane quarter (warp % 4) = tile rows 32 q .. 32 q + 31
+    const int q = warp & 3;
+    uint32_t tl = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++tl) {
+      int tm, tn;
+      tile_coords(t, TM, TN, tm, tn);
+      const uint32_t acc = tl & 1u;
+      const bool have = mbar_wait(su32(&tfull[acc]), (tl >> 1) & 1u, WAIT_POLLS);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t sa = base + (uint32_t)s * STAGE_BYTES, sb = sa + A_BYTES;
-#pragma unroll
-      for (int kk = 0; kk < GK / 16; ++kk)   // 16 bfloat16 = 32 bytes along K per instruction
-        mma_bf16(tmem, sw128_desc(sa + 32u * kk), sw128_desc(sb + 32u * kk), (kb | kk) != 0);
-      mma_commit(su32(&empty[s]));
-    }
-    if (!ok) atomicExch(&abort_flag, 1);
-    mma_commit(su32(&done));   // arrives once every issued MMA has completed
-  }
-  __syncwarp();
-
-  // epilogue: row 32 warp + lane of the tile, 32 columns per tensor-memory load
-  const bool have = mbar_wait(su32(&done), 0u, WAIT_POLLS);
-  __syncthreads();   // orders the issuers' abort_flag writes before the reads below
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const int row = m0 + 32 * warp + lane;
-  // warp-uniform: tcgen05.ld is executed by whole warps
-  const bool stop = __any_sync(0xffffffffu, !have || abort_flag != 0);
-  if (!stop) {
+      if (__any_sync(0xffffffffu, !have || *(volatile int*)&abort_flag != 0)) {
+        if (lane == 0) atomicExch(&abort_flag, 1);
+        break;
+      }
+      const int row = tm * GM + 32 * q + lane;
 #pragma unroll 1
-    for (int c = 0; c < GN / 32; ++c) {
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * c), v);
-      const int col0 = n0 + 32 * c;
-      if (row >= M || col0 >= N) continue;
-      if constexpr (OUT_BF16) {
-        __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(C) + (int64_t)row * N + col0;
-        if (col0 + 32 <= N && (N % 8) == 0) {
+      for (int c = 0; c < GN / 32; ++c) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + acc * TMEM_COLS + (uint32_t)(32 * c), v);
+        const int col0 = tn * GN + 32 * c;
+        if (row >= M || col0 >= N) continue;
+        if constexpr (OUT_BF16) {
+          __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(C) + (int64_t)row * N + col0;
+          if (col0 + 32 <= N && (N % 8) == 0) {
 #pragma unroll
-          for (int i = 0; i < 32; i += 8) {
-            uint4 pk;
-            __nv_bfloat162 h0 = __floats2bfloat162_rn(v[i], v[i + 1]), h1 = __floats2bfloat162_rn(v[i + 2], v[i + 3]);
-            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[i + 4], v[i + 5]), h3 = __floats2bfloat162_rn(v[i + 6], v[i + 7]);
-            pk.x = *reinterpret_cast<uint32_t*>(&h0);
-            pk.y = *reinterpret_cast<uint32_t*>(&h1);
-            pk.z = *reinterpret_cast<uint32_t*>(&h2);
-            pk.w = *reinterpret_cast<uint32_t*>(&h3);
-            *reinterpret_cast<uint4*>(out + i) = pk;
+            for (int i = 0; i < 32; i += 8) {
+              uint4 pk;
+              __nv_bfloat162 h0 = __floats2bfloat162_rn(v[i], v[i + 1]);
+              __nv_bfloat162 h1 = __floats2bfloat162_rn(v[i + 2], v[i + 3]);
+              __nv_bfloat162 h2 = __floats2bfloat162_rn(v[i + 4], v[i + 5]);
+              __nv_bfloat162 h3 = __floats2bfloat162_rn(v[i + 6], v[i + 7]);
+              pk.x = *reinterpret_cast<uint32_t*>(&h0);
+              pk.y = *reinterpret_cast<uint32_t*>(&h1);
+              pk.z = *reinterpret_cast<uint32_t*>(&h2);
+              pk.w = *reinterpret_cast<uint32_t*>(&h3);
+              *reinterpret_cast<uint4*>(out + i) = pk;
+            }
+          } else {
+            for (int i = 0; i < 32 && col0 + i < N; ++i) out[i] = __float2bfloat16_rn(v[i]);
           }
         } else {
-          for (int i = 0; i < 32 && col0 + i < N; ++i) out[i] = __float2bfloat16_rn(v[i]);
-        }
-      } else {
-        float* out = reinterpret_cast<float*>(C) + (int64_t)row * N + col0;
-        if (col0 + 32 <= N && (N % 4) == 0) {
+          float* out = reinterpret_cast<float*>(C) + (int64_t)row * N + col0;
+          if (col0 + 32 <= N && (N % 4) == 0) {
 #pragma unroll
-          for (int i = 0; i < 32; i += 4)
-            *reinterpret_cast<float4*>(out + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-        } else {
-          for (int i = 0; i < 32 && col0 + i < N; ++i) out[i] = v[i];
+            for (int i = 0; i < 32; i += 4)
+              *reinterpret_cast<float4*>(out + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+          } else {
+            for (int i = 0; i < 32 && col0 + i < N; ++i) out[i] = v[i];
+          }
         }
       }
+      // the accumulator is drained: hand it back to the MMA issuer
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(su32(&tempty[acc]));
     }
-  } else if (threadIdx.x == 0) {
-    atomicExch(&g_gemm_status, 1);
   }
+  __syncwarp();
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  if (threadIdx.x == 0 && *(volatile int*)&abort_flag) atomicExch(&g_gemm_status, 1);
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TMEM_COLS) : "memory");
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -258,16 +312,20 @@ cudaError_t launch_gemm_bf16(const void* A, const void* B, void* C, int64_t M, i
                              cudaStream_t s) {
   CUtensorMap ta, tb;
   if (!make_map(&ta, A, M, K, GM) || !make_map(&tb, B, N, K, GN)) return cudaErrorInvalidValue;
-  const dim3 grid((unsigned)((N + GN - 1) / GN), (unsigned)((M + GM - 1) / GM));
-  cudaError_t e;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int64_t tiles = ((M + GM - 1) / GM) * ((N + GN - 1) / GN);
+  const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);   // persistent: one CTA per SM
   if (out_bf16) {
     e = cudaFuncSetAttribute(k_gemm_bf16<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
     if (e != cudaSuccess) return e;
-    k_gemm_bf16<true><<<grid, 128, GEMM_SMEM, s>>>(ta, tb, C, (int)M, (int)N, (int)K);
+    k_gemm_bf16<true><<<grid, 192, GEMM_SMEM, s>>>(ta, tb, C, (int)M, (int)N, (int)K);
   } else {
     e = cudaFuncSetAttribute(k_gemm_bf16<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
     if (e != cudaSuccess) return e;
-    k_gemm_bf16<false><<<grid, 128, GEMM_SMEM, s>>>(ta, tb, C, (int)M, (int)N, (int)K);
+    k_gemm_bf16<false><<<grid, 192, GEMM_SMEM, s>>>(ta, tb, C, (int)M, (int)N, (int)K);
   }
   return cudaGetLastError();
 }
