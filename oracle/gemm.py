@@ -37,3 +37,22 @@ def gemm_nt(a_bits, b_bits):
 def abs_product_sum(a_bits, b_bits):
     """sum_k |A[m][k]| |B[n][k]|: the scale of the rounding error of the FP32 sum."""
     return np.abs(bf16_to_f64(a_bits)) @ np.abs(bf16_to_f64(b_bits)).T
+
+
+RELU, GELU = 1, 2
+
+
+def dense(x_bits, w_bits, bias=None, act=0):
+    """A dense layer Y = act(X W^T + b) in FP64: X bfloat16 [M][K], W bfloat16 [N][K],
+    b [N] (FP64 values of the FP32 bias), act 0 = identity, 1 = ReLU max(0, z),
+    2 = GELU z Phi(z) with Phi the standard normal CDF, (1 + erf(z / sqrt 2)) / 2."""
+    import math
+    z = gemm_nt(x_bits, w_bits)
+    if bias is not None:
+        z = z + np.asarray(bias, dtype=np.float64)[None, :]
+    if act == RELU:
+        return np.maximum(z, 0.0)
+    if act == GELU:
+        erf = np.vectorize(math.erf)
+        return z * 0.5 * (1.0 + erf(z / math.sqrt(2.0)))
+    return z

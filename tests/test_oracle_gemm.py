@@ -50,3 +50,21 @@ def test_product_closed_forms():
     np.testing.assert_array_equal(gemm.gemm_nt(x, eye), gemm.bf16_to_f64(x))    # X I^T = X
     np.testing.assert_array_equal(gemm.gemm_nt(eye, x), gemm.bf16_to_f64(x).T)  # I X^T = X^T
     np.testing.assert_array_equal(gemm.abs_product_sum(one, one), np.full((3, 3), 9.0))
+
+
+def test_dense_activations():
+    import math
+    x = gemm.f64_to_bf16(np.array([[1.0, -2.0], [0.5, 0.25]]))
+    w = gemm.f64_to_bf16(np.array([[1.0, 1.0], [2.0, -1.0], [0.0, 0.0]]))
+    b = np.array([0.5, -1.0, 3.0])
+    z = np.array([[1.0 - 2.0 + 0.5, 2.0 + 2.0 - 1.0, 3.0], [0.75 + 0.5, 1.0 - 0.25 - 1.0, 3.0]])
+    np.testing.assert_array_equal(gemm.dense(x, w, b), z)
+    np.testing.assert_array_equal(gemm.dense(x, w, b, gemm.RELU), np.maximum(z, 0))
+    g = gemm.dense(x, w, b, gemm.GELU)
+    # GELU(0) = 0, GELU(z) - GELU(-z) = z, GELU(z) -> z for large z
+    for (i, j), v in np.ndenumerate(z):
+        assert abs(g[i, j] - v * 0.5 * math.erfc(-v / math.sqrt(2.0))) < 1e-15
+    big = gemm.dense(gemm.f64_to_bf16(np.array([[8.0]])), gemm.f64_to_bf16(np.array([[1.0]])), None, gemm.GELU)
+    assert abs(big[0, 0] - 8.0) < 1e-12
+    p = gemm.dense(x, w, None, gemm.GELU) - gemm.dense(gemm.f64_to_bf16(-gemm.bf16_to_f64(x)), w, None, gemm.GELU)
+    np.testing.assert_allclose(p, gemm.gemm_nt(x, w), rtol=1e-14, atol=1e-14)
