@@ -332,13 +332,16 @@ def gemm_leg(gwx, torch, shape=(8192, 8192, 8192)):
         return a.elapsed_time(b) / reps
 
     ms = timed(lambda: gwx.gemm_bf16(A, B, out=C))
+    bias = torch.zeros(N, device="cuda", dtype=torch.float32)
+    ms_dense = timed(lambda: gwx.dense_bf16(A, B, bias, act=gwx.ACT_GELU, out=C))
     gwx.device_status()
     ms_cublas = timed(lambda: torch.matmul(A, B.t(), out=C))
     flops = 2.0 * M * N * K
     peak = MEASURED_PEAKS.get("bf16_tflops")
     achieved = flops / ms / 1e9
     del A, B, C
-    return {"shape": [M, N, K], "ms": ms, "tflops": achieved, "cublas_ms": ms_cublas,
+    return {"shape": [M, N, K], "ms": ms, "tflops": achieved, "dense_bias_gelu_ms": ms_dense,
+            "cublas_ms": ms_cublas,
             "cublas_tflops": flops / ms_cublas / 1e9,
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak if peak else None,

@@ -295,6 +295,18 @@ int gwx_importance_weights(const double* lnl, const double* log_ratio, const int
 int gwx_gemm_bf16(const void* A, const void* B, void* C, int64_t M, int64_t N, int64_t K, int c_dtype,
                   void* stream);
 
+/* A dense layer with its epilogue fused into the product above:
+ *   Y[m][n] = act( sum_k X[m][k] W[n][k] + bias[n] ),
+ * X bfloat16 [M][K] (activations), W bfloat16 [N][K] (weights, one row per output),
+ * bias FP32 [N] or NULL, act GWX_ACT_NONE, GWX_ACT_RELU (max(0, z)) or GWX_ACT_GELU
+ * (z Phi(z), Phi the standard normal CDF), Y FP32 or bfloat16 [M][N].  Same sizes and
+ * alignment as gwx_gemm_bf16; bias 4-byte aligned. */
+#define GWX_ACT_NONE 0
+#define GWX_ACT_RELU 1
+#define GWX_ACT_GELU 2
+int gwx_dense_bf16(const void* X, const void* W, const float* bias, void* Y, int64_t M, int64_t N, int64_t K,
+                   int act, int y_dtype, void* stream);
+
 /* Synchronises the current device; returns GWX_ETIMEOUT (and clears the record) if a
  * kernel gave up a bounded wait since the last call, else GWX_OK. */
 int gwx_device_status(void);

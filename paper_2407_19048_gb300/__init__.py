@@ -24,7 +24,7 @@ NPARAM = 11
 
 __all__ = ["GwxError", "version", "init", "detector_geometry", "sample_prior", "generate_waveforms", "project",
            "colored_noise", "welch_psd", "inject", "whiten", "simulate_batch", "log_likelihood",
-           "importance_weights", "gemm_bf16", "device_status", "rfft", "irfft",
+           "importance_weights", "gemm_bf16", "dense_bf16", "device_status", "rfft", "irfft",
            "workspace_bytes", "TAYLORF2", "IMRPHENOMD", "DETECTORS"]
 
 
@@ -270,6 +270,28 @@ def gemm_bf16(A, B, out=None, out_dtype=None):
         out = torch.empty((M, N), dtype=out_dtype or torch.float32, device=A.device)
     code = {torch.float32: 0, torch.bfloat16: 1}[out.dtype]
     _check(_lib.load().gwx_gemm_bf16(_ptr(A), _ptr(B), _ptr(out), M, N, K, code, _stream()))
+    return out
+
+
+ACT_NONE, ACT_RELU, ACT_GELU = 0, 1, 2
+
+
+def dense_bf16(X, W, bias=None, act=ACT_NONE, out=None, out_dtype=None):
+    """Y = act(X W^T + bias) on the tensor cores: X bfloat16 [M][K], W bfloat16 [N][K],
+    bias float32 [N] or None, Y float32 (default) or bfloat16 [M][N]."""
+    torch = _torch()
+    _dev(X, torch.bfloat16, "X")
+    _dev(W, torch.bfloat16, "W")
+    if bias is not None:
+        _dev(bias, torch.float32, "bias")
+    M, K = X.shape
+    N = W.shape[0]
+    if W.shape[1] != K or (bias is not None and bias.numel() != N):
+        raise ValueError("X is [M][K], W is [N][K], bias is [N]")
+    if out is None:
+        out = torch.empty((M, N), dtype=out_dtype or torch.float32, device=X.device)
+    code = {torch.float32: 0, torch.bfloat16: 1}[out.dtype]
+    _check(_lib.load().gwx_dense_bf16(_ptr(X), _ptr(W), _ptr(bias), _ptr(out), M, N, K, act, code, _stream()))
     return out
 
 

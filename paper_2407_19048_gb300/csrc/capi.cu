@@ -471,17 +471,29 @@ int gwx_importance_weights(const double* lnl, const double* log_ratio, const int
                   "importance_weights");
 }
 
-int gwx_gemm_bf16(const void* A, const void* B, void* C, int64_t M, int64_t N, int64_t K, int c_dtype,
-                  void* stream) {
+static int dense_common(const void* A, const void* B, const float* bias, void* C, int64_t M, int64_t N, int64_t K,
+                        int act, int c_dtype, void* stream) {
   if (M < 1 || M > ((int64_t)1 << 23) || N < 1 || N > 0x7fffffffLL || K < 8 || K > 0x7fffffffLL || K % 8 != 0)
     return fail(GWX_ESHAPE, "gemm sizes M=%lld N=%lld K=%lld (need K %% 8 == 0)", (long long)M, (long long)N,
                 (long long)K);
   if (c_dtype != GWX_F32 && c_dtype != GWX_BF16) return fail(GWX_EINVAL, "c_dtype %d", c_dtype);
+  if (act != GWX_ACT_NONE && act != GWX_ACT_RELU && act != GWX_ACT_GELU) return fail(GWX_EINVAL, "act %d", act);
   if (!A || !B || !C) return fail(GWX_EINVAL, "NULL array");
   if ((((uintptr_t)A) | ((uintptr_t)B) | ((uintptr_t)C)) & 15u)
     return fail(GWX_EINVAL, "A, B and C must be 16-byte aligned");
+  if (((uintptr_t)bias) & 3u) return fail(GWX_EINVAL, "bias must be 4-byte aligned");
   GWX_TRY(ensure_init());
-  return launched(launch_gemm_bf16(A, B, C, M, N, K, c_dtype == GWX_BF16, as_stream(stream)), "gemm_bf16");
+  return launched(launch_gemm_bf16(A, B, C, M, N, K, c_dtype == GWX_BF16, bias, act, as_stream(stream)), "gemm_bf16");
+}
+
+int gwx_gemm_bf16(const void* A, const void* B, void* C, int64_t M, int64_t N, int64_t K, int c_dtype,
+                  void* stream) {
+  return dense_common(A, B, nullptr, C, M, N, K, GWX_ACT_NONE, c_dtype, stream);
+}
+
+int gwx_dense_bf16(const void* X, const void* W, const float* bias, void* Y, int64_t M, int64_t N, int64_t K,
+                   int act, int y_dtype, void* stream) {
+  return dense_common(X, W, bias, Y, M, N, K, act, y_dtype, stream);
 }
 
 int gwx_device_status(void) {

@@ -114,6 +114,22 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+// Fused epilogue of a dense layer on 32 accumulator columns starting at col0:
+// z = acc + bias[col], then the activation (0 identity, 1 ReLU, 2 GELU z Phi(z)).
+__device__ __forceinline__ void epilogue_ops(float* v, const float* __restrict__ bias, int act, int col0, int N) {
+  if (bias) {
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] += (col0 + i < N) ? __ldg(&bias[col0 + i]) : 0.f;
+  }
+  if (act == 1) {
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i], 0.f);
+  } else if (act == 2) {
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = 0.5f * v[i] * erfcf(-0.70710678118654752f * v[i]);
+  }
+}
+
 // Tile t of a persistent CTA -> (tm, tn): bands of GROUP tile-rows, columns fastest
 // within a band, so the CTAs working at the same time share a few A and B panels in L2.
 constexpr int GROUP = 16;
@@ -133,7 +149,7 @@ __device__ __forceinline__ void tile_coords(int t, int TM, int TN, int& tm, int&
 template <bool OUT_BF16>
 __global__ void __launch_bounds__(192, 1)
     k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, void* __restrict__ C,
-                int M, int N, int K) {
+                const float* __restrict__ bias, int act, int M, int N, int K) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2];
   __shared__ uint32_t tmem_slot;
@@ -237,6 +253,7 @@ __global__ void __launch_bounds__(192, 1)
         tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + acc * TMEM_COLS + (uint32_t)(32 * c), v);
         const int col0 = tn * GN + 32 * c;
         if (row >= M || col0 >= N) continue;
+        epilogue_ops(v, bias, act, col0, N);
         if constexpr (OUT_BF16) {
           __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(C) + (int64_t)row * N + col0;
           if (col0 + 32 <= N && (N % 8) == 0) {
@@ -309,7 +326,7 @@ bool make_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t K, uint32
 }  // namespace
 
 cudaError_t launch_gemm_bf16(const void* A, const void* B, void* C, int64_t M, int64_t N, int64_t K, bool out_bf16,
-                             cudaStream_t s) {
+                             const float* bias, int act, cudaStream_t s) {
   CUtensorMap ta, tb;
   if (!make_map(&ta, A, M, K, GM) || !make_map(&tb, B, N, K, GN)) return cudaErrorInvalidValue;
   int dev = 0, sms = 0;
@@ -321,11 +338,11 @@ cudaError_t launch_gemm_bf16(const void* A, const void* B, void* C, int64_t M, i
   if (out_bf16) {
     e = cudaFuncSetAttribute(k_gemm_bf16<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
     if (e != cudaSuccess) return e;
-    k_gemm_bf16<true><<<grid, 192, GEMM_SMEM, s>>>(ta, tb, C, (int)M, (int)N, (int)K);
+    k_gemm_bf16<true><<<grid, 192, GEMM_SMEM, s>>>(ta, tb, C, bias, act, (int)M, (int)N, (int)K);
   } else {
     e = cudaFuncSetAttribute(k_gemm_bf16<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
     if (e != cudaSuccess) return e;
-    k_gemm_bf16<false><<<grid, 192, GEMM_SMEM, s>>>(ta, tb, C, (int)M, (int)N, (int)K);
+    k_gemm_bf16<false><<<grid, 192, GEMM_SMEM, s>>>(ta, tb, C, bias, act, (int)M, (int)N, (int)K);
   }
   return cudaGetLastError();
 }

@@ -77,3 +77,26 @@ def test_gemm_rejects_bad_arguments(gwx):
     a = torch.zeros((16, 12), dtype=torch.bfloat16, device="cuda")
     with pytest.raises(gwx.GwxError):
         gwx.gemm_bf16(a, a)          # K = 12 is not a multiple of 8
+
+
+@pytest.mark.parametrize("act", [0, 1, 2])
+@pytest.mark.parametrize("M,N,K,out_dtype", [(256, 512, 128, torch.float32), (300, 260, 72, torch.float32),
+                                             (128, 512, 256, torch.bfloat16)])
+def test_dense_layer(gwx, act, M, N, K, out_dtype):
+    """Y = act(X W^T + b): the sum's bound plus one FP32 rounding of the bias add; ReLU is
+    1-Lipschitz, GELU's slope is below 1.13 and erfc adds a few FP32 ulps; a bfloat16
+    output adds 2^-8 |Y|."""
+    x = workloads.random_bf16_bits(100 + act, (M, K))
+    w = workloads.random_bf16_bits(110 + act, (N, K))
+    b = np.random.default_rng(120 + act).normal(0.0, 0.5, N).astype(np.float32)
+    Y = gwx.dense_bf16(_bf16(x), _bf16(w), torch.from_numpy(b).cuda(), act=act, out_dtype=out_dtype)
+    gwx.device_status()
+    got = Y.float().cpu().numpy().astype(np.float64)
+    ref = gemm.dense(x, w, b.astype(np.float64), act)
+    z = gemm.dense(x, w, b.astype(np.float64), 0)
+    tol_z = 2.0 * K * 2.0 ** -24 * gemm.abs_product_sum(x, w) + 2.0 ** -23 * np.abs(z)
+    tol = tol_z * (1.13 if act == 2 else 1.0) + (8 * 2.0 ** -24 * np.abs(ref) + 1e-37 if act == 2 else 0.0)
+    if out_dtype == torch.bfloat16:
+        tol = tol * (1.0 + 2.0 ** -8) + 2.0 ** -8 * np.abs(ref)
+    err = np.abs(got - ref)
+    assert np.all(err <= tol + 1e-30), (float(err.max()), float((err / (tol + 1e-30)).max()))
