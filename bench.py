@@ -331,6 +331,7 @@ def gemm_leg(gwx, torch, shape=(8192, 8192, 8192)):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / reps
 
+    group = gwx.gemm_autotune(A, B, C)
     ms = timed(lambda: gwx.gemm_bf16(A, B, out=C))
     bias = torch.zeros(N, device="cuda", dtype=torch.float32)
     ms_dense = timed(lambda: gwx.dense_bf16(A, B, bias, act=gwx.ACT_GELU, out=C))
@@ -340,7 +341,8 @@ def gemm_leg(gwx, torch, shape=(8192, 8192, 8192)):
     peak = MEASURED_PEAKS.get("bf16_tflops")
     achieved = flops / ms / 1e9
     del A, B, C
-    return {"shape": [M, N, K], "ms": ms, "tflops": achieved, "dense_bias_gelu_ms": ms_dense,
+    return {"shape": [M, N, K], "ms": ms, "tflops": achieved, "autotuned_band": group,
+            "dense_bias_gelu_ms": ms_dense,
             "cublas_ms": ms_cublas,
             "cublas_tflops": flops / ms_cublas / 1e9,
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -573,6 +575,8 @@ def main(argv=None):
                     help="time only the device step (no end-to-end or log-likelihood leg); for profiling")
     ap.add_argument("--only-loglike", default=None, metavar="LO,HI",
                     help="run only the log-likelihood leg with U{LO..HI} samples per event; for profiling")
+    ap.add_argument("--only-gemm", default=None, metavar="M,N,K",
+                    help="run only the bfloat16 product leg at this shape; for profiling")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -581,6 +585,13 @@ def main(argv=None):
         wl["B"] = args.batch
     if args.impl == "reference":
         return run_reference(args, wl)
+    if args.only_gemm:
+        import torch
+        import paper_2407_19048_gb300 as gwx
+        gwx.init()
+        shape = tuple(int(v) for v in args.only_gemm.split(","))
+        print(json.dumps({"gemm_bf16": gemm_leg(gwx, torch, shape)}), flush=True)
+        return 0
     if args.only_loglike:
         import torch
         import paper_2407_19048_gb300 as gwx

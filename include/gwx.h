@@ -307,6 +307,15 @@ int gwx_gemm_bf16(const void* A, const void* B, void* C, int64_t M, int64_t N, i
 int gwx_dense_bf16(const void* X, const void* W, const float* bias, void* Y, int64_t M, int64_t N, int64_t K,
                    int act, int y_dtype, void* stream);
 
+/* Autotuner of the product's tile raster (a set-up call, not a hot call: it launches the
+ * product several times on the caller's buffers and synchronises `stream`).  For the
+ * shape (M, N, K, c_dtype) it times each candidate band height of the persistent tile
+ * walk (1 .. 64 tile-rows), keeps the fastest for later gwx_gemm_bf16 / gwx_dense_bf16
+ * calls of that shape in this process, and returns it in *group (if not NULL).
+ * C is overwritten. */
+int gwx_gemm_autotune(const void* A, const void* B, void* C, int64_t M, int64_t N, int64_t K, int c_dtype,
+                      int* group, void* stream);
+
 /* Synchronises the current device; returns GWX_ETIMEOUT (and clears the record) if a
  * kernel gave up a bounded wait since the last call, else GWX_OK. */
 int gwx_device_status(void);

@@ -24,7 +24,7 @@ NPARAM = 11
 
 __all__ = ["GwxError", "version", "init", "detector_geometry", "sample_prior", "generate_waveforms", "project",
            "colored_noise", "welch_psd", "inject", "whiten", "simulate_batch", "log_likelihood",
-           "importance_weights", "gemm_bf16", "dense_bf16", "device_status", "rfft", "irfft",
+           "importance_weights", "gemm_bf16", "dense_bf16", "gemm_autotune", "device_status", "rfft", "irfft",
            "workspace_bytes", "TAYLORF2", "IMRPHENOMD", "DETECTORS"]
 
 
@@ -293,6 +293,21 @@ def dense_bf16(X, W, bias=None, act=ACT_NONE, out=None, out_dtype=None):
     code = {torch.float32: 0, torch.bfloat16: 1}[out.dtype]
     _check(_lib.load().gwx_dense_bf16(_ptr(X), _ptr(W), _ptr(bias), _ptr(out), M, N, K, act, code, _stream()))
     return out
+
+
+def gemm_autotune(A, B, out):
+    """Tune the product's tile raster for this shape on these buffers (out is
+    overwritten); later gemm_bf16 / dense_bf16 calls of the shape use it.  Returns the
+    chosen band height."""
+    torch = _torch()
+    _dev(A, torch.bfloat16, "A")
+    _dev(B, torch.bfloat16, "B")
+    M, K = A.shape
+    N = B.shape[0]
+    code = {torch.float32: 0, torch.bfloat16: 1}[out.dtype]
+    g = ctypes.c_int(0)
+    _check(_lib.load().gwx_gemm_autotune(_ptr(A), _ptr(B), _ptr(out), M, N, K, code, ctypes.byref(g), _stream()))
+    return g.value
 
 
 def device_status():

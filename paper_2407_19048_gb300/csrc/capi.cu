@@ -6,7 +6,9 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "gwx_internal.h"
 
@@ -471,8 +473,21 @@ int gwx_importance_weights(const double* lnl, const double* log_ratio, const int
                   "importance_weights");
 }
 
-static int dense_common(const void* A, const void* B, const float* bias, void* C, int64_t M, int64_t N, int64_t K,
-                        int act, int c_dtype, void* stream) {
+// Tuned raster bands of the product, per (M, N, K, output type); filled by
+// gwx_gemm_autotune, read (without synchronising) by every product call.
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int64_t, int64_t, int64_t, int>, int> g_tune;
+
+int tuned_group(int64_t M, int64_t N, int64_t K, int c_dtype) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(std::make_tuple(M, N, K, c_dtype));
+  return it == g_tune.end() ? 0 : it->second;
+}
+}  // namespace
+
+static int check_dense(const void* A, const void* B, const float* bias, const void* C, int64_t M, int64_t N, int64_t K,
+                       int act, int c_dtype) {
   if (M < 1 || M > ((int64_t)1 << 23) || N < 1 || N > 0x7fffffffLL || K < 8 || K > 0x7fffffffLL || K % 8 != 0)
     return fail(GWX_ESHAPE, "gemm sizes M=%lld N=%lld K=%lld (need K %% 8 == 0)", (long long)M, (long long)N,
                 (long long)K);
@@ -482,8 +497,58 @@ static int dense_common(const void* A, const void* B, const float* bias, void* C
   if ((((uintptr_t)A) | ((uintptr_t)B) | ((uintptr_t)C)) & 15u)
     return fail(GWX_EINVAL, "A, B and C must be 16-byte aligned");
   if (((uintptr_t)bias) & 3u) return fail(GWX_EINVAL, "bias must be 4-byte aligned");
+  return GWX_OK;
+}
+
+static int dense_common(const void* A, const void* B, const float* bias, void* C, int64_t M, int64_t N, int64_t K,
+                        int act, int c_dtype, void* stream) {
+  GWX_TRY(check_dense(A, B, bias, C, M, N, K, act, c_dtype));
   GWX_TRY(ensure_init());
-  return launched(launch_gemm_bf16(A, B, C, M, N, K, c_dtype == GWX_BF16, bias, act, as_stream(stream)), "gemm_bf16");
+  return launched(launch_gemm_bf16(A, B, C, M, N, K, c_dtype == GWX_BF16, bias, act, tuned_group(M, N, K, c_dtype),
+                                   as_stream(stream)),
+                  "gemm_bf16");
+}
+
+int gwx_gemm_autotune(const void* A, const void* B, void* C, int64_t M, int64_t N, int64_t K, int c_dtype,
+                      int* group_out, void* stream) {
+  GWX_TRY(check_dense(A, B, nullptr, C, M, N, K, GWX_ACT_NONE, c_dtype));
+  GWX_TRY(ensure_init());
+  cudaStream_t s = as_stream(stream);
+  const int candidates[] = {1, 2, 4, 8, 16, 32, 64};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(cudaGetLastError(), "autotune event");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(cudaGetLastError(), "autotune event");
+  }
+  int best = 0;
+  float best_ms = 0.f;
+  cudaError_t err = cudaSuccess;
+  for (int g : candidates) {
+    for (int rep = 0; rep < 2 && err == cudaSuccess; ++rep)   // warm-up
+      err = launch_gemm_bf16(A, B, C, M, N, K, c_dtype == GWX_BF16, nullptr, GWX_ACT_NONE, g, s);
+    if (err == cudaSuccess) err = cudaEventRecord(e0, s);
+    for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep)
+      err = launch_gemm_bf16(A, B, C, M, N, K, c_dtype == GWX_BF16, nullptr, GWX_ACT_NONE, g, s);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    if (err != cudaSuccess) break;
+    if (best == 0 || ms < best_ms) {
+      best = g;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return cuda_fail(err, "autotune");
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[std::make_tuple(M, N, K, c_dtype)] = best;
+  }
+  if (group_out) *group_out = best;
+  return GWX_OK;
 }
 
 int gwx_gemm_bf16(const void* A, const void* B, void* C, int64_t M, int64_t N, int64_t K, int c_dtype,

@@ -81,8 +81,9 @@ cudaError_t launch_importance_weights(const double* lnl, const double* ratio, co
 
 // C = act(A B^T + bias), bfloat16 operands [M][K], [N][K], FP32 accumulation on the
 // tensor cores; C FP32 or bfloat16 [M][N]; bias FP32 [N] or NULL; act 0/1/2.  gemm_status reads and clears the timed-out-wait record.
+// group: tile-rows per raster band (0 = the default).
 cudaError_t launch_gemm_bf16(const void* A, const void* B, void* C, int64_t M, int64_t N, int64_t K, bool out_bf16,
-                             const float* bias, int act, cudaStream_t s);
+                             const float* bias, int act, int group, cudaStream_t s);
 cudaError_t gemm_status(int* status);
 
 // Record msg as the calling thread's gwx_last_error() message; returns status.

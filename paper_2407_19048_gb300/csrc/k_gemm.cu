@@ -130,14 +130,14 @@ __device__ __forceinline__ void epilogue_ops(float* v, const float* __restrict__
   }
 }
 
-// Tile t of a persistent CTA -> (tm, tn): bands of GROUP tile-rows, columns fastest
+// Tile t of a persistent CTA -> (tm, tn): bands of `group` tile-rows, columns fastest
 // within a band, so the CTAs working at the same time share a few A and B panels in L2.
-constexpr int GROUP = 16;
-__device__ __forceinline__ void tile_coords(int t, int TM, int TN, int& tm, int& tn) {
-  const int band = t / (GROUP * TN);
-  const int r = t - band * GROUP * TN;
-  const int rows = min(GROUP, TM - band * GROUP);
-  tm = band * GROUP + r % rows;
+constexpr int DEFAULT_GROUP = 16;
+__device__ __forceinline__ void tile_coords(int t, int TM, int TN, int group, int& tm, int& tn) {
+  const int band = t / (group * TN);
+  const int r = t - band * group * TN;
+  const int rows = min(group, TM - band * group);
+  tm = band * group + r % rows;
   tn = r / rows;
 }
 
@@ -149,7 +149,7 @@ __device__ __forceinline__ void tile_coords(int t, int TM, int TN, int& tm, int&
 template <bool OUT_BF16>
 __global__ void __launch_bounds__(192, 1)
     k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, void* __restrict__ C,
-                const float* __restrict__ bias, int act, int M, int N, int K) {
+                const float* __restrict__ bias, int act, int group, int M, int N, int K) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2];
   __shared__ uint32_t tmem_slot;
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(192, 1)
       uint32_t it = 0;
       for (int t = blockIdx.x; t < tiles && !*(volatile int*)&abort_flag; t += gridDim.x) {
         int tm, tn;
-        tile_coords(t, TM, TN, tm, tn);
+        tile_coords(t, TM, TN, group, tm, tn);
         for (int kb = 0; kb < KB; ++kb, ++it) {
           const uint32_t s = it % STAGES;
           if (it >= STAGES && !mbar_wait(su32(&empty[s]), ((it / STAGES) - 1) & 1u, WAIT_POLLS)) {
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(192, 1)
     uint32_t tl = 0;
     for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++tl) {
       int tm, tn;
-      tile_coords(t, TM, TN, tm, tn);
+      tile_coords(t, TM, TN, group, tm, tn);
       const uint32_t acc = tl & 1u;
       const bool have = mbar_wait(su32(&tfull[acc]), (tl >> 1) & 1u, WAIT_POLLS);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -326,7 +326,8 @@ bool make_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t K, uint32
 }  // namespace
 
 cudaError_t launch_gemm_bf16(const void* A, const void* B, void* C, int64_t M, int64_t N, int64_t K, bool out_bf16,
-                             const float* bias, int act, cudaStream_t s) {
+                             const float* bias, int act, int group, cudaStream_t s) {
+  if (group < 1) group = DEFAULT_GROUP;
   CUtensorMap ta, tb;
   if (!make_map(&ta, A, M, K, GM) || !make_map(&tb, B, N, K, GN)) return cudaErrorInvalidValue;
   int dev = 0, sms = 0;
@@ -338,11 +339,11 @@ cudaError_t launch_gemm_bf16(const void* A, const void* B, void* C, int64_t M, i
   if (out_bf16) {
     e = cudaFuncSetAttribute(k_gemm_bf16<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
     if (e != cudaSuccess) return e;
-    k_gemm_bf16<true><<<grid, 192, GEMM_SMEM, s>>>(ta, tb, C, bias, act, (int)M, (int)N, (int)K);
+    k_gemm_bf16<true><<<grid, 192, GEMM_SMEM, s>>>(ta, tb, C, bias, act, group, (int)M, (int)N, (int)K);
   } else {
     e = cudaFuncSetAttribute(k_gemm_bf16<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
     if (e != cudaSuccess) return e;
-    k_gemm_bf16<false><<<grid, 192, GEMM_SMEM, s>>>(ta, tb, C, bias, act, (int)M, (int)N, (int)K);
+    k_gemm_bf16<false><<<grid, 192, GEMM_SMEM, s>>>(ta, tb, C, bias, act, group, (int)M, (int)N, (int)K);
   }
   return cudaGetLastError();
 }

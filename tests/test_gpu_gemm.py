@@ -100,3 +100,20 @@ def test_dense_layer(gwx, act, M, N, K, out_dtype):
         tol = tol * (1.0 + 2.0 ** -8) + 2.0 ** -8 * np.abs(ref)
     err = np.abs(got - ref)
     assert np.all(err <= tol + 1e-30), (float(err.max()), float((err / (tol + 1e-30)).max()))
+
+
+def test_gemm_autotune_keeps_results(gwx):
+    """The autotuner picks a raster band among its candidates; the tuned product of that
+    shape still matches the oracle."""
+    M, N, K = 1024, 2048, 512
+    a = workloads.random_bf16_bits(130, (M, K))
+    b = workloads.random_bf16_bits(131, (N, K))
+    A, B = _bf16(a), _bf16(b)
+    out = torch.empty((M, N), dtype=torch.float32, device="cuda")
+    g = gwx.gemm_autotune(A, B, out)
+    assert g in (1, 2, 4, 8, 16, 32, 64)
+    C = gwx.gemm_bf16(A, B)
+    gwx.device_status()
+    ref = gemm.gemm_nt(a, b)
+    tol = 2.0 * K * 2.0 ** -24 * gemm.abs_product_sum(a, b)
+    assert np.all(np.abs(C.cpu().numpy().astype(np.float64) - ref) <= tol)
