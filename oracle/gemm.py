@@ -56,3 +56,28 @@ def dense(x_bits, w_bits, bias=None, act=0):
         erf = np.vectorize(math.erf)
         return z * 0.5 * (1.0 + erf(z / math.sqrt(2.0)))
     return z
+
+
+def act_grad(z, act):
+    """d act / dz: ReLU 1 for z > 0 else 0; GELU Phi(z) + z phi(z) (phi the standard
+    normal density)."""
+    import math
+    z = np.asarray(z, dtype=np.float64)
+    if act == RELU:
+        return (z > 0).astype(np.float64)
+    if act == GELU:
+        erf = np.vectorize(math.erf)
+        return 0.5 * (1.0 + erf(z / math.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
+    return np.ones_like(z)
+
+
+def dense_backward(x_bits, w_bits, bias, act, dy):
+    """Gradients of L with dL/dY = dy for Y = act(X W^T + b), by the chain rule in FP64:
+    dZ = dy * act'(Z), dX = dZ W, dW = dZ^T X, db = sum over rows of dZ.
+    Returns (dX [M][K], dW [N][K], db [N], dZ [M][N])."""
+    X, W = bf16_to_f64(x_bits), bf16_to_f64(w_bits)
+    z = X @ W.T
+    if bias is not None:
+        z = z + np.asarray(bias, dtype=np.float64)[None, :]
+    dz = np.asarray(dy, dtype=np.float64) * act_grad(z, act)
+    return dz @ W, dz.T @ X, dz.sum(axis=0), dz

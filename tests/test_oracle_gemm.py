@@ -68,3 +68,54 @@ def test_dense_activations():
     assert abs(big[0, 0] - 8.0) < 1e-12
     p = gemm.dense(x, w, None, gemm.GELU) - gemm.dense(gemm.f64_to_bf16(-gemm.bf16_to_f64(x)), w, None, gemm.GELU)
     np.testing.assert_allclose(p, gemm.gemm_nt(x, w), rtol=1e-14, atol=1e-14)
+
+
+def _loss(x_bits, w_bits, b, act, g):
+    """L = sum(g * Y) with X, W given as FP64 values (no bfloat16 rounding)."""
+    return float(np.sum(g * gemm.dense(x_bits, w_bits, b, act)))
+
+
+def test_dense_backward_matches_finite_differences():
+    """Central differences of L = sum(G * act(X W^T + b)) in FP64, perturbing the decoded
+    inputs (the oracle differentiates the exact-value function)."""
+    rng = np.random.default_rng(5)
+    M, N, K = 3, 4, 5
+    x = workloads.random_bf16_bits(6, (M, K), exp_lo=-2, exp_hi=0)
+    w = workloads.random_bf16_bits(7, (N, K), exp_lo=-2, exp_hi=0)
+    b = rng.normal(0.0, 0.3, N)
+    g = rng.normal(0.0, 1.0, (M, N))
+    X, W = gemm.bf16_to_f64(x), gemm.bf16_to_f64(w)
+    for act in (0, gemm.RELU, gemm.GELU):
+        dX, dW, db, _ = gemm.dense_backward(x, w, b, act, g)
+
+        def L(Xv, Wv, bv):
+            z = Xv @ Wv.T + bv[None, :]
+            if act == gemm.RELU:
+                y = np.maximum(z, 0)
+            elif act == gemm.GELU:
+                import math
+                y = z * 0.5 * (1 + np.vectorize(math.erf)(z / math.sqrt(2)))
+            else:
+                y = z
+            return float(np.sum(g * y))
+        h = 1e-6
+        for (i, j) in [(0, 0), (2, 4), (1, 2)]:
+            e = np.zeros_like(X); e[i, j] = h
+            assert abs((L(X + e, W, b) - L(X - e, W, b)) / (2 * h) - dX[i, j]) < 1e-6
+        for (i, j) in [(0, 0), (3, 4), (2, 1)]:
+            e = np.zeros_like(W); e[i, j] = h
+            assert abs((L(X, W + e, b) - L(X, W - e, b)) / (2 * h) - dW[i, j]) < 1e-6
+        for j in range(N):
+            e = np.zeros(N); e[j] = h
+            assert abs((L(X, W, b + e) - L(X, W, b - e)) / (2 * h) - db[j]) < 1e-6
+
+
+def test_act_grad_closed_forms():
+    import math
+    z = np.array([-2.0, -0.5, 0.0, 0.5, 3.0])
+    np.testing.assert_array_equal(gemm.act_grad(z, gemm.RELU), [0, 0, 0, 1, 1])
+    gz = gemm.act_grad(z, gemm.GELU)
+    assert gz[2] == 0.5                                   # GELU'(0) = 1/2
+    for v, d in zip(z, gz):                               # GELU'(z) + GELU'(-z) = 1
+        assert abs(d + gemm.act_grad(np.array([-v]), gemm.GELU)[0] - 1.0) < 1e-15
+    np.testing.assert_array_equal(gemm.act_grad(z, 0), np.ones(5))
