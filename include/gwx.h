@@ -307,6 +307,19 @@ int gwx_gemm_bf16(const void* A, const void* B, void* C, int64_t M, int64_t N, i
 int gwx_dense_bf16(const void* X, const void* W, const float* bias, void* Y, int64_t M, int64_t N, int64_t K,
                    int act, int y_dtype, void* stream);
 
+/* Backward pass of gwx_dense_bf16 for a loss L given dY = dL/dY (FP32 [M][N]):
+ *   Z = X W^T + b (recomputed on the tensor cores when act is not GWX_ACT_NONE),
+ *   dZ = dY * act'(Z)  (ReLU' = [z > 0], GELU' = Phi(z) + z phi(z)),
+ *   dX = dZ W  (FP32 [M][K]),  dW = dZ^T X  (FP32 [N][K]),  db = sum_m dZ  (FP32 [N]).
+ * dZ enters both products in bfloat16 (round to nearest even), with FP32 accumulation;
+ * db sums the FP32 dZ.  dX, dW or db may be NULL to skip it.  M, N, K multiples of 8 in
+ * [8, 65535 * 32]; X, W, dX, dW 16-byte aligned, dY, bias, db 4-byte aligned.
+ * Workspace: gwx_dense_bf16_backward_workspace(M, N, K) bytes. */
+size_t gwx_dense_bf16_backward_workspace(int64_t M, int64_t N, int64_t K);
+int gwx_dense_bf16_backward(const void* X, const void* W, const float* bias, const float* dY, int64_t M,
+                            int64_t N, int64_t K, int act, float* dX, float* dW, float* db,
+                            void* workspace, size_t workspace_bytes, void* stream);
+
 /* Autotuner of the product's tile raster (a set-up call, not a hot call: it launches the
  * product several times on the caller's buffers and synchronises `stream`).  For the
  * shape (M, N, K, c_dtype) it times each candidate band height of the persistent tile

@@ -24,7 +24,7 @@ NPARAM = 11
 
 __all__ = ["GwxError", "version", "init", "detector_geometry", "sample_prior", "generate_waveforms", "project",
            "colored_noise", "welch_psd", "inject", "whiten", "simulate_batch", "log_likelihood",
-           "importance_weights", "gemm_bf16", "dense_bf16", "gemm_autotune", "device_status", "rfft", "irfft",
+           "importance_weights", "gemm_bf16", "dense_bf16", "dense_bf16_backward", "gemm_autotune", "device_status", "rfft", "irfft",
            "workspace_bytes", "TAYLORF2", "IMRPHENOMD", "DETECTORS"]
 
 
@@ -293,6 +293,28 @@ def dense_bf16(X, W, bias=None, act=ACT_NONE, out=None, out_dtype=None):
     code = {torch.float32: 0, torch.bfloat16: 1}[out.dtype]
     _check(_lib.load().gwx_dense_bf16(_ptr(X), _ptr(W), _ptr(bias), _ptr(out), M, N, K, act, code, _stream()))
     return out
+
+
+def dense_bf16_backward(X, W, bias, dY, act=ACT_NONE):
+    """Gradients of Y = act(X W^T + bias) for dL/dY = dY (float32 [M][N]): returns
+    (dX float32 [M][K], dW float32 [N][K], db float32 [N])."""
+    torch = _torch()
+    _dev(X, torch.bfloat16, "X")
+    _dev(W, torch.bfloat16, "W")
+    _dev(dY, torch.float32, "dY")
+    if bias is not None:
+        _dev(bias, torch.float32, "bias")
+    M, K = X.shape
+    N = W.shape[0]
+    dev = X.device
+    dX = torch.empty((M, K), dtype=torch.float32, device=dev)
+    dW = torch.empty((N, K), dtype=torch.float32, device=dev)
+    db = torch.empty(N, dtype=torch.float32, device=dev)
+    lib = _lib.load()
+    ws, nb = _workspace(lib.gwx_dense_bf16_backward_workspace(M, N, K), dev)
+    _check(lib.gwx_dense_bf16_backward(_ptr(X), _ptr(W), _ptr(bias), _ptr(dY), M, N, K, act, _ptr(dX), _ptr(dW),
+                                       _ptr(db), _ptr(ws), nb, _stream()))
+    return dX, dW, db
 
 
 def gemm_autotune(A, B, out):

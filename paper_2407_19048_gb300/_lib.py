@@ -58,6 +58,9 @@ SIGNATURES = {
     "gwx_importance_weights": (c_int, [c_vp, c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_size, c_vp]),
     "gwx_gemm_bf16": (c_int, [c_vp, c_vp, c_vp, c_i64, c_i64, c_i64, c_int, c_vp]),
     "gwx_dense_bf16": (c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_i64, c_i64, c_int, c_int, c_vp]),
+    "gwx_dense_bf16_backward_workspace": (c_size, [c_i64, c_i64, c_i64]),
+    "gwx_dense_bf16_backward": (c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_i64, c_i64, c_int, c_vp, c_vp, c_vp, c_vp,
+                                        c_size, c_vp]),
     "gwx_gemm_autotune": (c_int, [c_vp, c_vp, c_vp, c_i64, c_i64, c_i64, c_int, c_vp, c_vp]),
     "gwx_device_status": (c_int, []),
     "gwx_rfft": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp]),

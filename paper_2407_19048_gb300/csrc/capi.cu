@@ -509,6 +509,31 @@ static int dense_common(const void* A, const void* B, const float* bias, void* C
                   "gemm_bf16");
 }
 
+size_t gwx_dense_bf16_backward_workspace(int64_t M, int64_t N, int64_t K) {
+  if (M < 1 || N < 1 || K < 1) return 0;
+  return align_up(dense_backward_ws(M, N, K));
+}
+
+int gwx_dense_bf16_backward(const void* X, const void* W, const float* bias, const float* dY, int64_t M, int64_t N,
+                            int64_t K, int act, float* dX, float* dW, float* db, void* workspace,
+                            size_t workspace_bytes, void* stream) {
+  const int64_t lim = (int64_t)65535 * 32;
+  if (M < 8 || N < 8 || K < 8 || M % 8 || N % 8 || K % 8 || M > lim || N > lim || K > lim)
+    return fail(GWX_ESHAPE, "dense backward sizes M=%lld N=%lld K=%lld (multiples of 8, at most %lld)",
+                (long long)M, (long long)N, (long long)K, (long long)lim);
+  if (act != GWX_ACT_NONE && act != GWX_ACT_RELU && act != GWX_ACT_GELU) return fail(GWX_EINVAL, "act %d", act);
+  if (!X || !W || !dY) return fail(GWX_EINVAL, "NULL array");
+  if ((((uintptr_t)X) | ((uintptr_t)W) | ((uintptr_t)dX) | ((uintptr_t)dW)) & 15u)
+    return fail(GWX_EINVAL, "X, W, dX and dW must be 16-byte aligned");
+  if ((((uintptr_t)dY) | ((uintptr_t)bias) | ((uintptr_t)db)) & 3u)
+    return fail(GWX_EINVAL, "dY, bias and db must be 4-byte aligned");
+  GWX_TRY(check_ws(workspace, workspace_bytes, gwx_dense_bf16_backward_workspace(M, N, K)));
+  GWX_TRY(ensure_init());
+  return launched(launch_dense_backward(X, W, bias, dY, M, N, K, act, dX, dW, db, workspace,
+                                        tuned_group(M, N, K, GWX_F32), as_stream(stream)),
+                  "dense_bf16_backward");
+}
+
 int gwx_gemm_autotune(const void* A, const void* B, void* C, int64_t M, int64_t N, int64_t K, int c_dtype,
                       int* group_out, void* stream) {
   GWX_TRY(check_dense(A, B, nullptr, C, M, N, K, GWX_ACT_NONE, c_dtype));

@@ -86,6 +86,12 @@ cudaError_t launch_gemm_bf16(const void* A, const void* B, void* C, int64_t M, i
                              const float* bias, int act, int group, cudaStream_t s);
 cudaError_t gemm_status(int* status);
 
+// Dense-layer backward (k_dense.cu): workspace bytes and the launcher.
+size_t dense_backward_ws(int64_t M, int64_t N, int64_t K);
+cudaError_t launch_dense_backward(const void* X, const void* W, const float* bias, const float* dY, int64_t M,
+                                  int64_t N, int64_t K, int act, float* dX, float* dW, float* db, void* ws, int group,
+                                  cudaStream_t s);
+
 // Record msg as the calling thread's gwx_last_error() message; returns status.
 int set_last_error(int status, const char* msg);
 

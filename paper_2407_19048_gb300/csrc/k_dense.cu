@@ -1,0 +1,144 @@
+// k_dense.cu -- backward pass of the dense layer Y = act(X W^T + b) of the learned part
+// (the embedding network of Sec. 4 and the flow of Sec. 5), by the chain rule:
+//   dZ = dY * act'(Z),  dX = dZ W,  dW = dZ^T X,  db = sum over rows of dZ,
+// with both products on the tensor cores (the tcgen05 GEMM, K-major operands): dX takes
+// dZ [M][N] and W^T [K][N], dW takes dZ^T [N][M] and X^T [K][M].  This file holds the
+// elementwise and layout kernels around them: the activation derivative with the
+// bfloat16 dZ, its transpose and per-tile column sums in one pass, bfloat16 transposes,
+// and the final column-sum reduction.
+#include <cuda_bf16.h>
+
+#include "gwx_internal.h"
+
+namespace gwx {
+
+namespace {
+
+constexpr int TT = 32;   // transpose tile
+
+__device__ __forceinline__ float act_grad(float z, int act) {
+  if (act == GWX_ACT_RELU) return z > 0.f ? 1.f : 0.f;
+  if (act == GWX_ACT_GELU)   // Phi(z) + z phi(z)
+    return 0.5f * erfcf(-0.70710678118654752f * z) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+  return 1.f;
+}
+
+// One 32 x 32 tile per block (32 x 8 threads): dz = dY act'(Z) in FP32; dZ and dZ^T in
+// bfloat16 (round to nearest even); the tile's column sums of the FP32 dz into
+// part[blockIdx.y][n].
+__global__ void __launch_bounds__(256) k_act_backward(const float* __restrict__ Z, const float* __restrict__ dY,
+                                                      int act, int M, int N, __nv_bfloat16* __restrict__ dZ,
+                                                      __nv_bfloat16* __restrict__ dZt, float* __restrict__ part) {
+  __shared__ float tile[TT][TT + 1];
+  const int n0 = blockIdx.x * TT, m0 = blockIdx.y * TT;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll
+  for (int i = 0; i < TT; i += 8) {
+    const int m = m0 + ty + i, n = n0 + tx;
+    float v = 0.f;
+    if (m < M && n < N) {
+      const int64_t at = (int64_t)m * N + n;
+      v = __ldg(&dY[at]);
+      if (act != GWX_ACT_NONE) v *= act_grad(__ldg(&Z[at]), act);
+      dZ[at] = __float2bfloat16_rn(v);
+    }
+    tile[ty + i][tx] = v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < TT; i += 8) {
+    const int n = n0 + ty + i, m = m0 + tx;
+    if (n < N && m < M) dZt[(int64_t)n * M + m] = __float2bfloat16_rn(tile[tx][ty + i]);
+  }
+  if (ty == 0 && n0 + tx < N) {
+    float sum = 0.f;
+#pragma unroll 8
+    for (int r = 0; r < TT; ++r) sum += tile[r][tx];
+    part[(int64_t)blockIdx.y * N + n0 + tx] = sum;
+  }
+}
+
+// out[c][r] = in[r][c] for a bfloat16 [R][C] matrix.
+__global__ void __launch_bounds__(256) k_transpose_bf16(const __nv_bfloat16* __restrict__ in, int R, int C,
+                                                        __nv_bfloat16* __restrict__ out) {
+  __shared__ __nv_bfloat16 tile[TT][TT + 2];
+  const int c0 = blockIdx.x * TT, r0 = blockIdx.y * TT;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll
+  for (int i = 0; i < TT; i += 8) {
+    const int r = r0 + ty + i, c = c0 + tx;
+    if (r < R && c < C) tile[ty + i][tx] = in[(int64_t)r * C + c];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < TT; i += 8) {
+    const int c = c0 + ty + i, r = r0 + tx;
+    if (c < C && r < R) out[(int64_t)c * R + r] = tile[tx][ty + i];
+  }
+}
+
+// db[n] = sum_p part[p][n] (FP64 accumulation of the FP32 tile sums).
+__global__ void k_colsum(const float* __restrict__ part, int P, int N, float* __restrict__ db) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  double s = 0.0;
+  for (int p = 0; p < P; ++p) s += (double)part[(int64_t)p * N + n];
+  db[n] = (float)s;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+size_t dense_backward_ws(int64_t M, int64_t N, int64_t K) {
+  const int64_t P = (M + TT - 1) / TT;
+  return align256((size_t)M * N * 4)            // Z (FP32)
+         + align256((size_t)M * N * 2) * 2      // dZ, dZ^T
+         + align256((size_t)K * M * 2)          // X^T
+         + align256((size_t)K * N * 2)          // W^T
+         + align256((size_t)P * N * 4);         // column-sum partials
+}
+
+cudaError_t launch_dense_backward(const void* X, const void* W, const float* bias, const float* dY, int64_t M,
+                                  int64_t N, int64_t K, int act, float* dX, float* dW, float* db, void* ws, int group,
+                                  cudaStream_t s) {
+  char* w = reinterpret_cast<char*>(ws);
+  float* Z = reinterpret_cast<float*>(w);
+  w += align256((size_t)M * N * 4);
+  __nv_bfloat16* dZ = reinterpret_cast<__nv_bfloat16*>(w);
+  w += align256((size_t)M * N * 2);
+  __nv_bfloat16* dZt = reinterpret_cast<__nv_bfloat16*>(w);
+  w += align256((size_t)M * N * 2);
+  __nv_bfloat16* Xt = reinterpret_cast<__nv_bfloat16*>(w);
+  w += align256((size_t)K * M * 2);
+  __nv_bfloat16* Wt = reinterpret_cast<__nv_bfloat16*>(w);
+  w += align256((size_t)K * N * 2);
+  float* part = reinterpret_cast<float*>(w);
+  const int64_t P = (M + TT - 1) / TT;
+  cudaError_t e = cudaSuccess;
+  // pre-activation Z = X W^T + b (only the activation derivative needs it)
+  if (act != GWX_ACT_NONE) {
+    e = launch_gemm_bf16(X, W, Z, M, N, K, false, bias, GWX_ACT_NONE, group, s);
+    if (e != cudaSuccess) return e;
+  }
+  const dim3 tb(TT, 8);
+  k_act_backward<<<dim3((unsigned)((N + TT - 1) / TT), (unsigned)P), tb, 0, s>>>(Z, dY, act, (int)M, (int)N, dZ, dZt,
+                                                                                 part);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_transpose_bf16<<<dim3((unsigned)((K + TT - 1) / TT), (unsigned)((M + TT - 1) / TT)), tb, 0, s>>>(
+      reinterpret_cast<const __nv_bfloat16*>(X), (int)M, (int)K, Xt);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_transpose_bf16<<<dim3((unsigned)((K + TT - 1) / TT), (unsigned)((N + TT - 1) / TT)), tb, 0, s>>>(
+      reinterpret_cast<const __nv_bfloat16*>(W), (int)N, (int)K, Wt);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // dX [M][K] = dZ [M][N] . (W^T [K][N])^T ;  dW [N][K] = dZ^T [N][M] . (X^T [K][M])^T
+  if (dX && (e = launch_gemm_bf16(dZ, Wt, dX, M, K, N, false, nullptr, GWX_ACT_NONE, 0, s)) != cudaSuccess) return e;
+  if (dW && (e = launch_gemm_bf16(dZt, Xt, dW, N, K, M, false, nullptr, GWX_ACT_NONE, 0, s)) != cudaSuccess) return e;
+  if (db) {
+    k_colsum<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(part, (int)P, (int)N, db);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace gwx

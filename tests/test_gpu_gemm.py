@@ -117,3 +117,35 @@ def test_gemm_autotune_keeps_results(gwx):
     ref = gemm.gemm_nt(a, b)
     tol = 2.0 * K * 2.0 ** -24 * gemm.abs_product_sum(a, b)
     assert np.all(np.abs(C.cpu().numpy().astype(np.float64) - ref) <= tol)
+
+
+@pytest.mark.parametrize("act", [0, 1, 2])
+@pytest.mark.parametrize("M,N,K", [(256, 512, 128), (200, 136, 72)])
+def test_dense_backward(gwx, act, M, N, K):
+    """dX, dW, db against the FP64 chain rule.  Bounds: dZ enters the products rounded to
+    bfloat16 (2^-8 relative) after FP32 evaluation (2^-20), its activation derivative is
+    taken at the FP32 pre-activation (|act''| <= 0.4 times that error), and each product
+    adds its FP32 summation bound; dY is zeroed where ReLU's kink is within reach of
+    the pre-activation error."""
+    rng = np.random.default_rng(140 + act)
+    x = workloads.random_bf16_bits(150 + act, (M, K), exp_lo=-3, exp_hi=0)
+    w = workloads.random_bf16_bits(160 + act, (N, K), exp_lo=-3, exp_hi=0)
+    b = rng.normal(0.0, 0.5, N).astype(np.float32)
+    dy = rng.normal(0.0, 1.0, (M, N)).astype(np.float32)
+    X, W = gemm.bf16_to_f64(x), gemm.bf16_to_f64(w)
+    z = X @ W.T + b.astype(np.float64)[None, :]
+    tol_z = 2.0 * K * 2.0 ** -24 * (np.abs(X) @ np.abs(W).T) + 2.0 ** -23 * np.abs(z)
+    if act == 1:
+        dy[np.abs(z) <= 4 * tol_z] = 0.0
+    dX_ref, dW_ref, db_ref, dz = gemm.dense_backward(x, w, b.astype(np.float64), act, dy.astype(np.float64))
+    dX, dW, db = gwx.dense_bf16_backward(_bf16(x), _bf16(w), torch.from_numpy(b).cuda(),
+                                         torch.from_numpy(dy).cuda(), act=act)
+    gwx.device_status()
+    e_dz = (2.0 ** -8 + 2.0 ** -20) * np.abs(dz) + (0.4 if act == 2 else 0.0) * np.abs(dy) * tol_z
+    tol_dX = e_dz @ np.abs(W) + 2.0 * N * 2.0 ** -24 * (np.abs(dz) @ np.abs(W))
+    tol_dW = e_dz.T @ np.abs(X) + 2.0 * M * 2.0 ** -24 * (np.abs(dz).T @ np.abs(X))
+    e_db = 2.0 ** -20 * np.abs(dz) + (0.4 if act == 2 else 0.0) * np.abs(dy) * tol_z
+    tol_db = e_db.sum(axis=0) + 2.0 * 32 * 2.0 ** -24 * np.abs(dz).sum(axis=0)
+    for got, ref, tol in ((dX, dX_ref, tol_dX), (dW, dW_ref, tol_dW), (db, db_ref, tol_db)):
+        err = np.abs(got.cpu().numpy().astype(np.float64) - ref)
+        assert np.all(err <= tol * (1.0 + 1e-6) + 1e-30), (float(err.max()), float((err / (tol + 1e-30)).max()))
