@@ -194,6 +194,13 @@ int gwx_whiten(const float* d, const double* psd, int64_t seg_len, double fs, do
                int64_t B, int D, int64_t N, float* y,
                void* workspace, size_t workspace_bytes, void* stream);
 
+/* Inverse of gwx_whiten on the band, for checks: d = irfft(rfft(y) M_k sqrt(S~_k fs/2)),
+ * so unwhiten(whiten(x)) is x restricted to the band (bins ceil(f_lo/df) <= k < N/2).
+ * Arguments, layouts and workspace as gwx_whiten (y in, d out; d may alias y). */
+int gwx_unwhiten(const float* y, const double* psd, int64_t seg_len, double fs, double f_lo,
+                 int64_t B, int D, int64_t N, float* d,
+                 void* workspace, size_t workspace_bytes, void* stream);
+
 /* ---- whitening without caller scratch -------------------------------------------
  * Same result as gwx_whiten, for callers that cannot allocate device memory and
  * so cannot pass a workspace: for example a plug-in whose host application owns

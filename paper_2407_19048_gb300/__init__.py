@@ -23,7 +23,7 @@ M1, M2, CHI1, CHI2, DIST, TC, PHIC, THETAJN, PSI, RA, DEC = range(11)
 NPARAM = 11
 
 __all__ = ["GwxError", "version", "init", "detector_geometry", "sample_prior", "generate_waveforms", "project",
-           "colored_noise", "welch_psd", "inject", "whiten", "simulate_batch", "log_likelihood",
+           "colored_noise", "welch_psd", "inject", "whiten", "unwhiten", "simulate_batch", "log_likelihood",
            "importance_weights", "gemm_bf16", "dense_bf16", "dense_bf16_backward", "gemm_autotune", "device_status", "rfft", "irfft",
            "workspace_bytes", "TAYLORF2", "IMRPHENOMD", "DETECTORS"]
 
@@ -186,6 +186,19 @@ def whiten(d, psd, seg_len, fs, f_lo, out=None):
     out = torch.empty_like(d) if out is None else out
     ws, nb = _workspace(lib.gwx_whiten_workspace(D, N), d.device)
     _check(lib.gwx_whiten(_ptr(d), _ptr(psd), seg_len, fs, f_lo, B, D, N, _ptr(out), _ptr(ws), nb, _stream()))
+    return out
+
+
+def unwhiten(y, psd, seg_len, fs, f_lo, out=None):
+    """Inverse of whiten on the band (for checks): d [B][D][N] from y."""
+    torch = _torch()
+    lib = _lib.load()
+    _dev(y, torch.float32, "y")
+    _dev(psd, torch.float64, "psd")
+    B, D, N = y.shape
+    out = torch.empty_like(y) if out is None else out
+    ws, nb = _workspace(lib.gwx_whiten_workspace(D, N), y.device)
+    _check(lib.gwx_unwhiten(_ptr(y), _ptr(psd), seg_len, fs, f_lo, B, D, N, _ptr(out), _ptr(ws), nb, _stream()))
     return out
 
 

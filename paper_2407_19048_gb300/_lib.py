@@ -43,6 +43,7 @@ SIGNATURES = {
     "gwx_inject": (c_int, [c_vp, c_int, c_i64, c_vp, c_vp, c_i64, c_i64, c_dbl, c_vp, c_vp]),
     "gwx_whiten_workspace": (c_size, [c_int, c_i64]),
     "gwx_whiten": (c_int, [c_vp, c_vp, c_i64, c_dbl, c_dbl, c_i64, c_int, c_i64, c_vp, c_vp, c_size, c_vp]),
+    "gwx_unwhiten": (c_int, [c_vp, c_vp, c_i64, c_dbl, c_dbl, c_i64, c_int, c_i64, c_vp, c_vp, c_size, c_vp]),
     "gwx_whiten_static": (c_int, [c_vp, c_vp, c_i64, c_dbl, c_dbl, c_i64, c_int, c_i64, c_vp, c_vp]),
     "gwx_simulate_batch_workspace": (c_size, [c_int, c_i64, c_i64]),
     "gwx_simulate_batch": (c_int, [ctypes.POINTER(GwxPrior), c_u64, c_u32, c_vp, c_i64, c_vp, c_i64, c_dbl, c_dbl,

@@ -318,7 +318,7 @@ size_t gwx_whiten_workspace(int D, int64_t N) {
 }
 
 
-int gwx_whiten(const float* d, const double* psd, int64_t seg_len, double fs, double f_lo, int64_t B, int D,
+static int whiten_common(bool inverse, const float* d, const double* psd, int64_t seg_len, double fs, double f_lo, int64_t B, int D,
                int64_t N, float* y, void* workspace, size_t workspace_bytes, void* stream) {
   GWX_TRY(check_window(N));
   GWX_TRY(check_psd_args(seg_len, N));
@@ -336,8 +336,18 @@ int gwx_whiten(const float* d, const double* psd, int64_t seg_len, double fs, do
   GWX_TRY(ensure_init());
   float* W = reinterpret_cast<float*>(workspace);
   cudaStream_t s = as_stream(stream);
-  GWX_TRY(launched(launch_whiten_filter(psd, D, seg_len, fs, k_lo, N, W, s), "whiten filter"));
+  GWX_TRY(launched(launch_whiten_filter(psd, D, seg_len, fs, k_lo, N, W, s, inverse), "whiten filter"));
   return launched(launch_whiten_rows(d, W, B * D, D, N, y, s), "whiten");
+}
+
+int gwx_whiten(const float* d, const double* psd, int64_t seg_len, double fs, double f_lo, int64_t B, int D,
+               int64_t N, float* y, void* workspace, size_t workspace_bytes, void* stream) {
+  return whiten_common(false, d, psd, seg_len, fs, f_lo, B, D, N, y, workspace, workspace_bytes, stream);
+}
+
+int gwx_unwhiten(const float* y, const double* psd, int64_t seg_len, double fs, double f_lo, int64_t B, int D,
+                 int64_t N, float* d, void* workspace, size_t workspace_bytes, void* stream) {
+  return whiten_common(true, y, psd, seg_len, fs, f_lo, B, D, N, d, workspace, workspace_bytes, stream);
 }
 
 size_t gwx_simulate_batch_workspace(int D, int64_t B, int64_t N) {

@@ -52,7 +52,7 @@ cudaError_t launch_welch(const float* x, int D, int64_t L, double fs, int64_t M,
                          void* ws, cudaStream_t s);
 size_t welch_ws(int D, int64_t L, int64_t M, int64_t stride);
 cudaError_t launch_whiten_filter(const double* psd, int D, int64_t M, double fs, int k_lo, int64_t N, float* W,
-                                 cudaStream_t s);
+                                 cudaStream_t s, bool inverse = false);
 // Packed-domain whitening coefficients (alpha, beta) [D][N/2] from W [D][N/2+1].
 cudaError_t launch_packed_filter(const float* W, int D, int64_t N, float2* Wp, cudaStream_t s);
 cudaError_t launch_whiten_rows(const float* d, const float* W, int64_t rows, int D, int64_t N, float* y,

@@ -130,8 +130,10 @@ cudaError_t launch_welch(const float* x, int D, int64_t L, double fs, int64_t M,
 // ----------------------------------------------------------------- whitening filter
 // W[d][k] = M_k / sqrt(S~_k fs / 2), S~ the PSD linearly interpolated from the grid
 // fs/M to fs/N at the exact rational position k M / N.
+// W_k = M_k / sqrt(S~_k fs/2) (whitening), or M_k sqrt(S~_k fs/2) with `inverse` (the
+// unwhitening filter: its inverse on the band).
 __global__ void k_whiten_filter(const double* __restrict__ psd, int D, int64_t M, double fs, int k_lo, int64_t N,
-                                float* __restrict__ W) {
+                                bool inverse, float* __restrict__ W) {
   const int64_t F = N / 2 + 1;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (int64_t)D * F) return;
@@ -146,15 +148,15 @@ __global__ void k_whiten_filter(const double* __restrict__ psd, int D, int64_t M
     const double frac = (double)(num % N) / (double)N;
     const double* p = psd + (int64_t)d * nb;
     const double S = p[j0] + (p[j1] - p[j0]) * frac;
-    w = (float)(1.0 / sqrt(S * fs * 0.5));
+    w = inverse ? (float)sqrt(S * fs * 0.5) : (float)(1.0 / sqrt(S * fs * 0.5));
   }
   W[i] = w;
 }
 
 cudaError_t launch_whiten_filter(const double* psd, int D, int64_t M, double fs, int k_lo, int64_t N, float* W,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, bool inverse) {
   const int64_t total = (int64_t)D * (N / 2 + 1);
-  k_whiten_filter<<<(unsigned)((total + 63) / 64), 64, 0, s>>>(psd, D, M, fs, k_lo, N, W);   // FP64: spread wide
+  k_whiten_filter<<<(unsigned)((total + 63) / 64), 64, 0, s>>>(psd, D, M, fs, k_lo, N, inverse, W);   // FP64: spread wide
   return cudaGetLastError();
 }
 

@@ -228,6 +228,27 @@ def test_whiten_matches_oracle(gwx, name):
     assert np.abs(got - ref).max() <= 1e-4 * rms(ref)
 
 
+@pytest.mark.parametrize("name", ["small", "hl3"])
+def test_unwhiten_matches_oracle_and_inverts_whiten(gwx, name):
+    """unwhiten against the oracle (max-abs 1e-4 of the RMS), and unwhiten(whiten(x)) =
+    x restricted to the band within 1e-5 of its RMS in FP32."""
+    wl = workloads.workload(name)
+    D, N = len(wl["dets"]), wl["N"]
+    bg = noise.colored_noise(3, 0, D, wl["L"], wl["fs"], wl["f_lo"])
+    psd = spectral.welch_psd(bg, wl["fs"], wl["seg_len"], wl["seg_stride"])
+    y = workloads.random_strain(41, (5, D, N), 1.0)
+    ref = spectral.unwhiten(y, psd, wl["seg_len"], wl["fs"], wl["f_lo"])
+    got = host(gwx.unwhiten(cuda(y, torch.float32), cuda(psd), wl["seg_len"], wl["fs"], wl["f_lo"]))
+    assert np.abs(got - ref).max() <= 1e-4 * rms(ref)
+    x = workloads.random_strain(42, (5, D, N), 1e-21)
+    band = spectral.band_mask(N, wl["fs"], wl["f_lo"])
+    x_band = np.fft.irfft(np.fft.rfft(x.astype(np.float32).astype(np.float64), axis=-1) * band, n=N, axis=-1)
+    xc = cuda(x, torch.float32)
+    back = host(gwx.unwhiten(gwx.whiten(xc, cuda(psd), wl["seg_len"], wl["fs"], wl["f_lo"]), cuda(psd),
+                             wl["seg_len"], wl["fs"], wl["f_lo"]))
+    assert np.abs(back - x_band).max() <= 1e-5 * rms(x_band)
+
+
 def test_whiten_in_place(gwx):
     wl = workloads.workload("small")
     d = workloads.random_strain(26, (3, 2, wl["N"]), 1e-21).astype(np.float32)
