@@ -25,6 +25,8 @@ Modules, in pipeline order:
 * ``spectral``   -- Welch PSD, PSD interpolation, injection, whitening.
 * ``likelihood`` -- noise-weighted inner product, log-likelihood, mismatch.
 * ``importance`` -- importance weights, effective sample size, evidence per event.
+* ``gemm``       -- bfloat16 dense products and the dense layer, forward and backward.
+* ``learn``      -- the learned Gaussian proposal: features, loss, AdamW, proposal density.
 * ``pipeline``   -- the whole per-batch pass, step by step, unfused.
 
 Everything is float64 / uint32-uint64 numpy.  ``numpy.fft`` is used as the

@@ -1,0 +1,107 @@
+"""Pins of oracle.learn: brute-force DFT, closed forms, finite differences."""
+import math
+
+import numpy as np
+
+import workloads
+from oracle import learn
+
+
+def test_features_brute_force_dft():
+    rng = np.random.default_rng(1)
+    B, D, N, k_lo, G, F = 2, 2, 64, 3, 4, 32
+    y = rng.normal(0.0, 1.0, (B, D, N))
+    f = learn.features(y, k_lo, G, F)
+    n = np.arange(N)
+    ng = (N // 2 - k_lo) // G
+    for b in range(B):
+        for d in range(D):
+            for g in range(ng):
+                p = []
+                for k in range(k_lo + g * G, k_lo + g * G + G):
+                    X = sum(y[b, d, j] * complex(math.cos(2 * math.pi * k * j / N), -math.sin(2 * math.pi * k * j / N))
+                            for j in n)
+                    p.append(abs(X) ** 2 / N)
+                assert abs(f[b, d * ng + g] - math.log(sum(p) / G)) < 1e-10
+    assert np.all(f[:, D * ng:] == 0.0)
+
+
+def test_features_of_white_noise_are_near_log_variance():
+    rng = np.random.default_rng(2)
+    y = rng.normal(0.0, 3.0, (64, 1, 4096))
+    f = learn.features(y, 40, 64, 64)[:, :(2048 - 40) // 64]
+    assert abs(np.mean(np.exp(f)) - 9.0) < 0.1     # E |Y_k|^2 / N = sigma^2
+
+
+def test_chirp_mass_and_targets():
+    assert abs(learn.chirp_mass(10.0, 10.0) - 10.0 * 2.0 ** -0.2) < 1e-12
+    th = np.zeros((11, 2))
+    th[0] = [10.0, 30.0]
+    th[1] = [10.0, 20.0]
+    th[4] = [500.0, 1500.0]
+    t = learn.targets(th, [1.0, 2.0, 3.0], [2.0, 4.0, 5.0])
+    np.testing.assert_allclose(t[:, 1], [(20.0 - 2.0) / 4.0, (50.0 - 2.0) / 4.0])
+    np.testing.assert_allclose(t[:, 2], [(500.0 - 3.0) / 5.0, (1500.0 - 3.0) / 5.0])
+    np.testing.assert_allclose(t[1, 0], ((600.0 ** 0.6 / 50.0 ** 0.2) - 1.0) / 2.0)
+
+
+def test_gauss_nll_value_and_gradient():
+    rng = np.random.default_rng(3)
+    B, P = 5, 3
+    out = rng.normal(0.0, 0.5, (B, 8))
+    t = rng.normal(0.0, 1.0, (B, P))
+    loss, mean, g = learn.gauss_nll(out, t)
+    assert abs(mean - loss.mean()) < 1e-15
+    z = out.copy()
+    z[:, :P] = t
+    z[:, P:2 * P] = 0.0
+    assert np.all(learn.gauss_nll(z, t)[0] == 0.0)            # mu = t, sigma = 1
+    h = 1e-6
+    for (i, j) in [(0, 0), (2, 1), (4, 3), (1, 5), (3, 7)]:
+        e = np.zeros_like(out)
+        e[i, j] = h
+        fd = (learn.gauss_nll(out + e, t)[1] - learn.gauss_nll(out - e, t)[1]) / (2 * h)
+        assert abs(fd - g[i, j]) < 1e-8
+
+
+def test_adamw_first_step_closed_form():
+    p = np.array([1.0, -2.0, 0.5])
+    g = np.array([0.3, -0.1, 0.0])
+    z = np.zeros(3)
+    p1, m1, v1 = learn.adamw(p, g, z, z, lr=0.1, beta1=0.9, beta2=0.999, eps=1e-8, wd=0.01, step=1)
+    np.testing.assert_allclose(m1, 0.1 * g)
+    np.testing.assert_allclose(v1, 0.001 * g * g)
+    want = p - 0.1 * (g / (np.abs(g) + 1e-8) + 0.01 * p)
+    np.testing.assert_allclose(p1, want, rtol=1e-15)
+
+
+def test_mass_jacobian_by_finite_differences():
+    for m1, m2 in [(30.0, 12.0), (11.0, 45.0), (25.0, 24.0)]:
+        h = 1e-6
+        def f(a, b):
+            return np.array([learn.chirp_mass(a, b), a + b])
+        J = np.column_stack([(f(m1 + h, m2) - f(m1 - h, m2)) / (2 * h), (f(m1, m2 + h) - f(m1, m2 - h)) / (2 * h)])
+        Mc = learn.chirp_mass(m1, m2)
+        assert abs(abs(np.linalg.det(J)) - 0.6 * Mc * abs(m1 - m2) / (m1 * m2)) < 1e-7
+
+
+def test_proposal_round_trip_and_support():
+    prior = workloads.workload("small")["prior"]
+    mean, scale = [20.0, 60.0, 1100.0], [5.0, 15.0, 500.0]
+    rng = np.random.default_rng(4)
+    n = 200
+    mu = rng.normal(0.0, 0.3, (n, 3))
+    s = rng.normal(-1.0, 0.2, (n, 3))
+    z = rng.normal(0.0, 1.0, (n, 3))
+    u = rng.uniform(0.0, 1.0, n)
+    m1, m2, D, lr = learn.proposal(mu, s, mean, scale, z, u, prior)
+    x = np.asarray(mean) + np.asarray(scale) * (mu + np.exp(s) * z)
+    ok = np.isfinite(m1)
+    np.testing.assert_allclose(learn.chirp_mass(m1[ok], m2[ok]), x[ok, 0], rtol=1e-12)
+    np.testing.assert_allclose((m1 + m2)[ok], x[ok, 1], rtol=1e-12)
+    fin = np.isfinite(lr)
+    assert fin.sum() > 50
+    assert np.all((m1[fin] >= prior["m_lo"]) & (m1[fin] <= prior["m_hi"]) & (D[fin] >= prior["d_lo"]))
+    # the order of the masses follows u
+    both = ok & (m1 != m2)
+    assert np.all((m1[both] < m2[both]) == (u[both] < 0.5))
