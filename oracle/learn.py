@@ -116,3 +116,63 @@ def proposal(mu, s, mean, scale, z, u, prior):
         jac = 0.6 * Mc[i] * abs(a - b) / (a * b)
         lr[i] = log_box - (log_qx + math.log(jac) - math.log(2.0))
     return m1, m2, D, lr
+
+
+TAG_PROPOSAL = 3
+
+
+def proposal_uniforms(seed, counter, idx):
+    """Ten uniforms per sample from Philox4x32-10: block j (0..4) of sample s has counter
+    (s, j, TAG_PROPOSAL, counter) and gives uniform52(w0, w1), uniform52(w2, w3)."""
+    from .philox import key_of, philox4x32_10, uniform52
+    k0, k1 = key_of(seed)
+    idx = np.asarray(idx, dtype=np.uint64)
+    out = np.zeros((len(idx), 10))
+    for j in range(5):
+        w = philox4x32_10((idx & np.uint64(0xFFFFFFFF)).astype(np.uint32), np.uint32(j), np.uint32(TAG_PROPOSAL),
+                          np.uint32(counter & 0xFFFFFFFF), k0, k1)
+        out[:, 2 * j] = uniform52(w[0], w[1])
+        out[:, 2 * j + 1] = uniform52(w[2], w[3])
+    return out
+
+
+def sample_proposal(net_out, mean, scale, prior, truth, offsets, seed, counter):
+    """Samples for importance sampling, event e owning rows offsets[e] .. offsets[e+1]-1.
+
+    Uniforms u[0..9] of sample s (proposal_uniforms): normals z0, z1 = r (cos, sin)(2 pi u1)
+    with r = sqrt(-2 ln u0), z2 = sqrt(-2 ln u2) cos(2 pi u3); u4 orders the masses; phic,
+    psi, RA = lo + (hi - lo) u5, u6, 2 pi u8 (psi, phic ranges from the prior, RA in
+    [0, 2 pi)); theta_JN = acos(2 u7 - 1); dec = asin(2 u9 - 1); spins and t_c are the
+    event's own (truth [11][E]).  With net_out (rows per event: mu in columns 0..2, s in
+    3..5) the masses and distance come from proposal() with log ratio ln pi - ln q;
+    without it (the prior as proposal) m1 = lo + (hi - lo) u0, m2 likewise with u2,
+    D = d_lo + (d_hi - d_lo) u1, log ratio 0.  Returns (theta [11][S], log_ratio [S])."""
+    offsets = np.asarray(offsets, dtype=np.int64)
+    S = int(offsets[-1])
+    E = len(offsets) - 1
+    ev = np.searchsorted(offsets, np.arange(S), side="right") - 1
+    ev = np.minimum(np.maximum(ev, 0), E - 1)
+    u = proposal_uniforms(seed, counter, np.arange(S))
+    truth = np.asarray(truth, dtype=np.float64)
+    th = np.zeros((11, S))
+    th[2], th[3], th[5] = truth[2][ev], truth[3][ev], truth[5][ev]
+    th[6] = prior["phi_lo"] + (prior["phi_hi"] - prior["phi_lo"]) * u[:, 5]
+    th[8] = prior["psi_lo"] + (prior["psi_hi"] - prior["psi_lo"]) * u[:, 6]
+    th[7] = np.arccos(2.0 * u[:, 7] - 1.0)
+    th[9] = 2.0 * math.pi * u[:, 8]
+    th[10] = np.arcsin(2.0 * u[:, 9] - 1.0)
+    if net_out is None:
+        th[0] = prior["m_lo"] + (prior["m_hi"] - prior["m_lo"]) * u[:, 0]
+        th[1] = prior["m_lo"] + (prior["m_hi"] - prior["m_lo"]) * u[:, 2]
+        th[4] = prior["d_lo"] + (prior["d_hi"] - prior["d_lo"]) * u[:, 1]
+        return th, np.zeros(S)
+    r01 = np.sqrt(-2.0 * np.log(u[:, 0]))
+    z = np.stack([r01 * np.cos(2.0 * math.pi * u[:, 1]), r01 * np.sin(2.0 * math.pi * u[:, 1]),
+                  np.sqrt(-2.0 * np.log(u[:, 2])) * np.cos(2.0 * math.pi * u[:, 3])], axis=1)
+    out = np.asarray(net_out, dtype=np.float64)[ev]
+    m1, m2, D, lr = proposal(out[:, 0:3], out[:, 3:6], mean, scale, z, u[:, 4], prior)
+    bad = ~np.isfinite(m1)
+    th[0] = np.where(bad, prior["m_lo"], m1)
+    th[1] = np.where(bad, prior["m_lo"], m2)
+    th[4] = np.where(np.isfinite(D), D, prior["d_lo"])
+    return th, lr

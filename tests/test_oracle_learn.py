@@ -105,3 +105,31 @@ def test_proposal_round_trip_and_support():
     # the order of the masses follows u
     both = ok & (m1 != m2)
     assert np.all((m1[both] < m2[both]) == (u[both] < 0.5))
+
+
+def test_sample_proposal_prior_mode_and_angles():
+    prior = workloads.workload("small")["prior"]
+    truth = np.zeros((11, 2))
+    truth[2], truth[3], truth[5] = [0.1, -0.2], [0.3, 0.0], [1.2, 1.4]
+    offs = [0, 3000, 5000]
+    th, lr = learn.sample_proposal(None, None, None, prior, truth, offs, seed=9, counter=1)
+    assert np.all(lr == 0.0)
+    assert np.all((th[0] >= prior["m_lo"]) & (th[0] <= prior["m_hi"]))
+    np.testing.assert_array_equal(th[5][:3000], 1.2)
+    np.testing.assert_array_equal(th[2][3000:], -0.2)
+    # isotropic orientation and sky: cos(theta_JN) and sin(dec) uniform on [-1, 1]
+    assert abs(np.mean(np.cos(th[7]))) < 0.05 and abs(np.mean(np.sin(th[10]))) < 0.05
+    assert abs(np.var(np.cos(th[7])) - 1.0 / 3.0) < 0.03
+    # the same (seed, counter) reproduces the draws
+    th2, _ = learn.sample_proposal(None, None, None, prior, truth, offs, seed=9, counter=1)
+    np.testing.assert_array_equal(th, th2)
+
+
+def test_sample_proposal_normals():
+    """Box-Muller normals of the proposal have mean 0 and variance 1."""
+    u = learn.proposal_uniforms(3, 0, np.arange(20000))
+    r = np.sqrt(-2.0 * np.log(u[:, 0]))
+    z0, z1 = r * np.cos(2 * math.pi * u[:, 1]), r * np.sin(2 * math.pi * u[:, 1])
+    for z in (z0, z1):
+        assert abs(z.mean()) < 0.03 and abs(z.var() - 1.0) < 0.04
+    assert abs(np.mean(z0 * z1)) < 0.03
