@@ -327,6 +327,47 @@ int gwx_dense_bf16_backward(const void* X, const void* W, const float* bias, con
                             int64_t N, int64_t K, int act, float* dX, float* dW, float* db,
                             void* workspace, size_t workspace_bytes, void* stream);
 
+/* ---- learned proposal: the pieces around the dense layers ---------------------------
+ * The network trained on the simulated batches (Sec. 4, 5; AdamW) starts as the simplest
+ * conditional flow: a Gaussian over chirp mass Mc = (m1 m2)^{3/5} / M^{1/5}, total mass M
+ * and distance D whose mean mu and log-scale s (standardised units) a stack of
+ * gwx_dense_bf16 layers computes from spectral features of the whitened strain.
+ *
+ * gwx_spectral_features: out[b][d ng + g] = ln( sum_{k in group g} |Y_b,d,k|^2 / (N G) )
+ *   for the groups of G bins from k_lo = ceil(f_lo N / fs) (ng = (N/2 - k_lo) / G), Y the
+ *   rfft of y [B][D][N] (FP32); columns from D ng to F_pad - 1 are 0; bfloat16 [B][F_pad],
+ *   F_pad a multiple of 8.  Workspace gwx_spectral_features_workspace(B, D, N).
+ * gwx_proposal_targets: t[b] = ((Mc, M, D) - mean) / scale, FP32 [B][3], from theta
+ *   [GWX_NPARAM][B]; mean3 and scale3 are HOST arrays of 3 doubles.
+ * gwx_gauss_nll: for network outputs out [B][ldo] (mu in columns 0..P-1, s in P..2P-1)
+ *   and targets [B][P]: loss_rows[b] = sum_p (t - mu)^2 e^{-2s} / 2 + s (FP32), *loss_mean
+ *   their mean (FP64, one device double), grad [B][ldo] = d(mean)/d(out) (0 elsewhere).
+ * gwx_adamw: one AdamW step (Loshchilov & Hutter) on n FP32 parameters with moments m, v;
+ *   step counts from 1; param_bf16 (optional) receives the bfloat16 copy the layers use.
+ * gwx_sample_proposal: S samples for importance sampling, event e owning rows
+ *   event_offsets[e] .. event_offsets[e+1] - 1.  Uniforms from Philox4x32-10 with counter
+ *   (s, block 0..4, tag 3, counter) and key seed; spins and t_c are the event's own (truth
+ *   [GWX_NPARAM][E]); phic, psi uniform in the prior ranges, RA uniform in [0, 2 pi),
+ *   theta_JN and dec isotropic.  With net_out (rows [E][ldn], ldn >= 6: mu, s of Mc, M, D
+ *   in standardised units, mean3/scale3 as for the targets) (Mc, M, D) are drawn from the
+ *   Gaussian and (m1, m2) solved (order by a fair coin); log_ratio = ln prior - ln q
+ *   (uniform prior in m1, m2, D; -inf outside it).  With net_out NULL the prior is the
+ *   proposal (m1, m2, D uniform; log_ratio 0).  theta out [GWX_NPARAM][S], log_ratio [S]:
+ *   pass both to gwx_log_likelihood and gwx_importance_weights. */
+size_t gwx_spectral_features_workspace(int64_t B, int D, int64_t N);
+int gwx_spectral_features(const float* y, int64_t B, int D, int64_t N, double fs, double f_lo, int group,
+                          int F_pad, void* features, void* workspace, size_t workspace_bytes, void* stream);
+int gwx_proposal_targets(const double* theta, int64_t B, const double* mean3, const double* scale3,
+                         float* targets, void* stream);
+int gwx_gauss_nll(const float* out, int ldo, const float* targets, int P, int64_t B, float* loss_rows,
+                  double* loss_mean, float* grad, void* stream);
+int gwx_adamw(float* param, const float* grad, float* m, float* v, int64_t n, double lr, double beta1,
+              double beta2, double eps, double weight_decay, int64_t step, void* param_bf16, void* stream);
+int gwx_sample_proposal(const float* net_out, int ldn, const double* mean3, const double* scale3,
+                        const gwx_prior* prior, const double* truth, int64_t E, const int64_t* event_offsets,
+                        int64_t S, uint64_t seed, uint32_t counter, double* theta, double* log_ratio,
+                        void* stream);
+
 /* Autotuner of the product's tile raster (a set-up call, not a hot call: it launches the
  * product several times on the caller's buffers and synchronises `stream`).  For the
  * shape (M, N, K, c_dtype) it times each candidate band height of the persistent tile

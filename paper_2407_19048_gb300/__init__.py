@@ -24,7 +24,8 @@ NPARAM = 11
 
 __all__ = ["GwxError", "version", "init", "detector_geometry", "sample_prior", "generate_waveforms", "project",
            "colored_noise", "welch_psd", "inject", "whiten", "unwhiten", "simulate_batch", "log_likelihood",
-           "importance_weights", "gemm_bf16", "dense_bf16", "dense_bf16_backward", "gemm_autotune", "device_status", "rfft", "irfft",
+           "importance_weights", "gemm_bf16", "dense_bf16", "dense_bf16_backward", "gemm_autotune", "spectral_features", "proposal_targets",
+           "gauss_nll", "adamw", "sample_proposal", "device_status", "rfft", "irfft",
            "workspace_bytes", "TAYLORF2", "IMRPHENOMD", "DETECTORS"]
 
 
@@ -328,6 +329,76 @@ def dense_bf16_backward(X, W, bias, dY, act=ACT_NONE):
     _check(lib.gwx_dense_bf16_backward(_ptr(X), _ptr(W), _ptr(bias), _ptr(dY), M, N, K, act, _ptr(dX), _ptr(dW),
                                        _ptr(db), _ptr(ws), nb, _stream()))
     return dX, dW, db
+
+
+def _host3(v):
+    return (ctypes.c_double * 3)(*[float(x) for x in v]) if v is not None else None
+
+
+def spectral_features(y, fs, f_lo, group, F_pad, out=None):
+    """bfloat16 [B][F_pad] log group powers of whitened windows y [B][D][N] (see gwx.h)."""
+    torch = _torch()
+    lib = _lib.load()
+    _dev(y, torch.float32, "y")
+    B, D, N = y.shape
+    out = torch.empty((B, F_pad), dtype=torch.bfloat16, device=y.device) if out is None else out
+    ws, nb = _workspace(lib.gwx_spectral_features_workspace(B, D, N), y.device)
+    _check(lib.gwx_spectral_features(_ptr(y), B, D, N, fs, f_lo, group, F_pad, _ptr(out), _ptr(ws), nb, _stream()))
+    return out
+
+
+def proposal_targets(theta, mean, scale, out=None):
+    """float32 [B][3] standardised (Mc, M, D) of draws theta [11][B]."""
+    torch = _torch()
+    _dev(theta, torch.float64, "theta")
+    B = theta.shape[1]
+    out = torch.empty((B, 3), dtype=torch.float32, device=theta.device) if out is None else out
+    _check(_lib.load().gwx_proposal_targets(_ptr(theta), B, _host3(mean), _host3(scale), _ptr(out), _stream()))
+    return out
+
+
+def gauss_nll(out, targets, grad=None, loss_rows=None, loss_mean=None):
+    """Gaussian NLL of targets [B][P] under network outputs out [B][ldo]: returns
+    (loss_rows [B], loss_mean [1] float64 on the device, grad [B][ldo])."""
+    torch = _torch()
+    _dev(out, torch.float32, "out")
+    _dev(targets, torch.float32, "targets")
+    B, ldo = out.shape
+    P = targets.shape[1]
+    dev = out.device
+    grad = torch.empty_like(out) if grad is None else grad
+    loss_rows = torch.empty(B, dtype=torch.float32, device=dev) if loss_rows is None else loss_rows
+    loss_mean = torch.empty(1, dtype=torch.float64, device=dev) if loss_mean is None else loss_mean
+    _check(_lib.load().gwx_gauss_nll(_ptr(out), ldo, _ptr(targets), P, B, _ptr(loss_rows), _ptr(loss_mean),
+                                     _ptr(grad), _stream()))
+    return loss_rows, loss_mean, grad
+
+
+def adamw(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, param_bf16=None):
+    """One AdamW step in place on float32 param, m, v (step counts from 1)."""
+    _check(_lib.load().gwx_adamw(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(), lr, beta1, beta2, eps,
+                                 weight_decay, step, _ptr(param_bf16), _stream()))
+
+
+def sample_proposal(prior, truth, event_offsets, seed, counter, net_out=None, mean=None, scale=None):
+    """Importance-sampling draws: returns (theta [11][S] float64, log_ratio [S] float64)."""
+    torch = _torch()
+    _dev(truth, torch.float64, "truth")
+    _dev(event_offsets, torch.int64, "event_offsets")
+    E = event_offsets.shape[0] - 1
+    S = int(event_offsets[-1].item())
+    dev = truth.device
+    theta = torch.empty((NPARAM, S), dtype=torch.float64, device=dev)
+    lr = torch.empty(S, dtype=torch.float64, device=dev)
+    ldn = 0
+    if net_out is not None:
+        _dev(net_out, torch.float32, "net_out")
+        ldn = net_out.shape[1]
+    p = _prior(prior)
+    _check(_lib.load().gwx_sample_proposal(_ptr(net_out), ldn, _host3(mean), _host3(scale), ctypes.byref(p),
+                                           _ptr(truth), E, _ptr(event_offsets), S, seed, counter, _ptr(theta),
+                                           _ptr(lr), _stream()))
+    return theta, lr
 
 
 def gemm_autotune(A, B, out):

@@ -62,6 +62,14 @@ SIGNATURES = {
     "gwx_dense_bf16_backward_workspace": (c_size, [c_i64, c_i64, c_i64]),
     "gwx_dense_bf16_backward": (c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_i64, c_i64, c_int, c_vp, c_vp, c_vp, c_vp,
                                         c_size, c_vp]),
+    "gwx_spectral_features_workspace": (c_size, [c_i64, c_int, c_i64]),
+    "gwx_spectral_features": (c_int, [c_vp, c_i64, c_int, c_i64, c_dbl, c_dbl, c_int, c_int, c_vp, c_vp, c_size,
+                                      c_vp]),
+    "gwx_proposal_targets": (c_int, [c_vp, c_i64, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl), c_vp, c_vp]),
+    "gwx_gauss_nll": (c_int, [c_vp, c_int, c_vp, c_int, c_i64, c_vp, c_vp, c_vp, c_vp]),
+    "gwx_adamw": (c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl, c_i64, c_vp, c_vp]),
+    "gwx_sample_proposal": (c_int, [c_vp, c_int, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl),
+                                    ctypes.POINTER(GwxPrior), c_vp, c_i64, c_vp, c_i64, c_u64, c_u32, c_vp, c_vp, c_vp]),
     "gwx_gemm_autotune": (c_int, [c_vp, c_vp, c_vp, c_i64, c_i64, c_i64, c_int, c_vp, c_vp]),
     "gwx_device_status": (c_int, []),
     "gwx_rfft": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp]),

@@ -604,6 +604,91 @@ int gwx_device_status(void) {
   return GWX_OK;
 }
 
+size_t gwx_spectral_features_workspace(int64_t B, int D, int64_t N) {
+  if (B < 1 || D < 1 || N < 2) return 0;
+  return align_up((size_t)B * D * (size_t)(N / 2 + 1) * sizeof(float2));
+}
+
+int gwx_spectral_features(const float* y, int64_t B, int D, int64_t N, double fs, double f_lo, int group, int F_pad,
+                          void* features, void* workspace, size_t workspace_bytes, void* stream) {
+  GWX_TRY(check_window(N));
+  if (D < 1 || D > GWX_MAX_DET) return fail(GWX_ESHAPE, "D=%d", D);
+  if (B < 0 || B * D > 0x7fffffffLL) return fail(GWX_ESHAPE, "B=%lld", (long long)B);
+  if (!(fs > 0.0)) return fail(GWX_EINVAL, "fs must be positive");
+  int k_lo = 0;
+  GWX_TRY(band_start(f_lo, fs / (double)N, N / 2, &k_lo));
+  if (group < 1 || group > N / 2) return fail(GWX_EINVAL, "group %d", group);
+  const int64_t ng = (N / 2 - k_lo) / group;
+  if (F_pad < D * ng || F_pad % 8 != 0)
+    return fail(GWX_ESHAPE, "F_pad=%d must be a multiple of 8 and at least D x groups = %lld", F_pad,
+                (long long)(D * ng));
+  if (B == 0) return GWX_OK;
+  if (!y || !features) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN8(y);
+  GWX_ALIGN8(features);
+  GWX_TRY(check_ws(workspace, workspace_bytes, gwx_spectral_features_workspace(B, D, N)));
+  GWX_TRY(ensure_init());
+  return launched(launch_features(y, B, D, N, k_lo, group, F_pad, workspace, features, as_stream(stream)),
+                  "spectral_features");
+}
+
+int gwx_proposal_targets(const double* theta, int64_t B, const double* mean3, const double* scale3, float* targets,
+                         void* stream) {
+  if (B < 0) return fail(GWX_ESHAPE, "B=%lld", (long long)B);
+  if (!mean3 || !scale3) return fail(GWX_EINVAL, "mean and scale (host, 3 values each) are required");
+  for (int i = 0; i < 3; ++i)
+    if (!(scale3[i] > 0.0) || !isfinite(mean3[i])) return fail(GWX_EINVAL, "bad mean or scale %d", i);
+  if (B == 0) return GWX_OK;
+  if (!theta || !targets) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN8(theta);
+  GWX_TRY(ensure_init());
+  return launched(launch_targets(theta, B, mean3, scale3, targets, as_stream(stream)), "proposal_targets");
+}
+
+int gwx_gauss_nll(const float* out, int ldo, const float* targets, int P, int64_t B, float* loss_rows,
+                  double* loss_mean, float* grad, void* stream) {
+  if (P < 1 || ldo < 2 * P || B < 1 || B > 0x7fffffffLL) return fail(GWX_ESHAPE, "gauss_nll sizes");
+  if (!out || !targets || !loss_rows || !loss_mean || !grad) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN8(loss_mean);
+  GWX_TRY(ensure_init());
+  return launched(launch_gauss_nll(out, ldo, targets, P, (int)B, loss_rows, loss_mean, grad, as_stream(stream)),
+                  "gauss_nll");
+}
+
+int gwx_adamw(float* param, const float* grad, float* m, float* v, int64_t n, double lr, double beta1, double beta2,
+              double eps, double weight_decay, int64_t step, void* param_bf16, void* stream) {
+  if (n < 0) return fail(GWX_ESHAPE, "n=%lld", (long long)n);
+  if (step < 1 || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0) || !(lr >= 0.0))
+    return fail(GWX_EINVAL, "AdamW hyper-parameters (step counts from 1)");
+  if (n == 0) return GWX_OK;
+  if (!param || !grad || !m || !v) return fail(GWX_EINVAL, "NULL array");
+  GWX_TRY(ensure_init());
+  return launched(launch_adamw(param, grad, m, v, n, lr, beta1, beta2, eps, weight_decay, step, param_bf16,
+                               as_stream(stream)),
+                  "adamw");
+}
+
+int gwx_sample_proposal(const float* net_out, int ldn, const double* mean3, const double* scale3,
+                        const gwx_prior* prior, const double* truth, int64_t E, const int64_t* event_offsets,
+                        int64_t S, uint64_t seed, uint32_t counter, double* theta, double* log_ratio, void* stream) {
+  if (!prior) return fail(GWX_EINVAL, "prior is NULL");
+  if (E < 0 || S < 0 || (S > 0 && E == 0) || S > 0x7fffffffLL * 64) return fail(GWX_ESHAPE, "bad E or S");
+  if (net_out && (ldn < 6 || !mean3 || !scale3)) return fail(GWX_EINVAL, "net_out needs ldn >= 6, mean and scale");
+  if (net_out)
+    for (int i = 0; i < 3; ++i)
+      if (!(scale3[i] > 0.0) || !isfinite(mean3[i])) return fail(GWX_EINVAL, "bad mean or scale %d", i);
+  if (S == 0) return GWX_OK;
+  if (!truth || !event_offsets || !theta || !log_ratio) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN8(truth);
+  GWX_ALIGN8(event_offsets);
+  GWX_ALIGN8(theta);
+  GWX_ALIGN8(log_ratio);
+  GWX_TRY(ensure_init());
+  return launched(launch_proposal(net_out, ldn, mean3, scale3, *prior, truth, E, event_offsets, S, seed, counter,
+                                  theta, log_ratio, as_stream(stream)),
+                  "sample_proposal");
+}
+
 int gwx_rfft(const float* x, int64_t R, int64_t N, float* X, void* stream) {
   GWX_TRY(check_window(N));
   if (R < 0 || R > 0x7fffffffLL) return fail(GWX_ESHAPE, "R=%lld", (long long)R);

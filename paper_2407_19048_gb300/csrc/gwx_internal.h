@@ -92,6 +92,19 @@ cudaError_t launch_dense_backward(const void* X, const void* W, const float* bia
                                   int64_t N, int64_t K, int act, float* dX, float* dW, float* db, void* ws, int group,
                                   cudaStream_t s);
 
+// Learned proposal (k_learn.cu).
+cudaError_t launch_features(const float* y, int64_t B, int D, int64_t N, int k_lo, int G, int F_pad, void* ws,
+                            void* out, cudaStream_t s);
+cudaError_t launch_targets(const double* theta, int64_t B, const double* mean, const double* scale, float* t,
+                           cudaStream_t s);
+cudaError_t launch_gauss_nll(const float* out, int ldo, const float* t, int P, int B, float* loss, double* mean,
+                             float* grad, cudaStream_t s);
+cudaError_t launch_adamw(float* p, const float* g, float* m, float* v, int64_t n, double lr, double b1, double b2,
+                         double eps, double wd, int64_t step, void* p16, cudaStream_t s);
+cudaError_t launch_proposal(const float* net, int ldn, const double* mean, const double* scale, const gwx_prior& pr,
+                            const double* truth, int64_t E, const int64_t* off, int64_t S, uint64_t seed,
+                            uint32_t counter, double* theta, double* lratio, cudaStream_t s);
+
 // Record msg as the calling thread's gwx_last_error() message; returns status.
 int set_last_error(int status, const char* msg);
 
