@@ -350,6 +350,59 @@ def gemm_leg(gwx, torch, shape=(8192, 8192, 8192)):
                          "peak_basis": "measured bf16 burst (MEASURED_PEAKS.json)"}}
 
 
+def learned_leg(gwx, torch, rank, steps=2000, events=32, per_event=4000):
+    """The first learned proposal: a dense network (tcgen05 layers) trained with AdamW on
+    512-draw batches of the two-detector workload, mapping spectral features to a
+    Gaussian over chirp mass, total mass and distance; then importance sampling of 32
+    events with 4000 samples each, against the prior as proposal (spins and merger time
+    known; with and without the angles known)."""
+    import numpy as np
+    import paper_2407_19048_gb300.simulator  # noqa: F401
+    from paper_2407_19048_gb300.proposal import LearnedProposal
+    wl = workloads.workload("small", B=512)
+    sim = gwx.simulator.Simulator(wl, pipeline=True, background_every=16)
+    net = LearnedProposal(wl)
+    losses = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(steps):
+        y, th, _ = sim.step(step_counter(rank, 20000 + i))
+        loss = net.train_step(y, th)
+        if i in (0, steps // 4, steps // 2, steps - 1):
+            losses.append((i, loss))
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    losses = [(i, float(l.item())) for i, l in losses]
+    wl_ev = dict(workloads.workload("small", B=events), param_seed=777)
+    sim_ev = gwx.simulator.Simulator(wl_ev)
+    y_ev, th_ev, _ = sim_ev.step(step_counter(rank, 0))
+    y_ev, th_ev = y_ev.clone(), th_ev.clone()
+    offs = torch.arange(events + 1, dtype=torch.int64, device="cuda") * per_event
+    res = {}
+    for fix in (False, True):
+        for learned in (False, True):
+            best = None
+            for rep in range(3):
+                torch.cuda.synchronize()
+                a = time.perf_counter()
+                theta, lrat = net.proposal_samples(y_ev, th_ev, offs, seed=5, counter=rep, learned=learned,
+                                                   fix_angles=fix)
+                lnl = gwx.log_likelihood(y_ev, sim_ev.psd, wl_ev["seg_len"], wl_ev["fs"], wl_ev["f_lo"],
+                                         wl_ev["dets"], 0.0, theta, offs)
+                _, ess, eff, _ = gwx.importance_weights(lnl, offs, lrat)
+                e = float(ess.sum().item())
+                dt = time.perf_counter() - a
+                best = dt if best is None else min(best, dt)
+            key = ("learned" if learned else "prior") + ("_angles_known" if fix else "")
+            res[key] = {"ess_total": e, "ess_median": float(ess.median().item()),
+                        "efficiency_median": float(eff.median().item()), "ess_per_s": e / best}
+    del sim, sim_ev
+    return {"train_steps": steps, "batch": 512, "train_s": train_s, "loss": losses, "events": events,
+            "samples_per_event": per_event, "importance_sampling": res,
+            "note": "Gaussian over (Mc, M, D) from log spectral powers, two GELU layers of 512; spins and "
+                    "merger time known in both proposals"}
+
+
 def cufft_leg(gwx, torch, sim, wl, fused_ms):
     """The shared-memory FFT kernels against cuFFT (called through torch.fft) on the
     batch's shape, B x D rows of N real samples.  cuFFT is a timing baseline here only:
@@ -516,6 +569,7 @@ def run_gpu(args, wl):
     fft_cmp = cufft_leg(gwx, torch, sim, wl, statistics.mean(sim_ms))
     serve = serving_leg(gwx, torch, rank)
     gemm = gemm_leg(gwx, torch)
+    learned = learned_leg(gwx, torch, rank)
 
     sim_avg_s = statistics.mean(sim_ms) * 1e-3
     flops = flops_per_injection(wl) * B
@@ -566,6 +620,7 @@ def run_gpu(args, wl):
             "fft_vs_cufft": fft_cmp,
             "serving": serve,
             "gemm_bf16": gemm,
+            "learned_proposal": learned,
             "wall_s_timed_region": t_wall,
         }
         print(json.dumps(line), flush=True)

@@ -352,8 +352,11 @@ int gwx_dense_bf16_backward(const void* X, const void* W, const float* bias, con
  *   in standardised units, mean3/scale3 as for the targets) (Mc, M, D) are drawn from the
  *   Gaussian and (m1, m2) solved (order by a fair coin); log_ratio = ln prior - ln q
  *   (uniform prior in m1, m2, D; -inf outside it).  With net_out NULL the prior is the
- *   proposal (m1, m2, D uniform; log_ratio 0).  theta out [GWX_NPARAM][S], log_ratio [S]:
- *   pass both to gwx_log_likelihood and gwx_importance_weights. */
+ *   proposal (m1, m2, D uniform; log_ratio 0).  flags GWX_PROPOSAL_FIX_ANGLES takes phic,
+ *   theta_JN, psi, RA and dec from the event too, so that the proposal covers m1, m2, D
+ *   only.  theta out [GWX_NPARAM][S], log_ratio [S]: pass both to gwx_log_likelihood and
+ *   gwx_importance_weights. */
+#define GWX_PROPOSAL_FIX_ANGLES 1
 size_t gwx_spectral_features_workspace(int64_t B, int D, int64_t N);
 int gwx_spectral_features(const float* y, int64_t B, int D, int64_t N, double fs, double f_lo, int group,
                           int F_pad, void* features, void* workspace, size_t workspace_bytes, void* stream);
@@ -365,8 +368,8 @@ int gwx_adamw(float* param, const float* grad, float* m, float* v, int64_t n, do
               double beta2, double eps, double weight_decay, int64_t step, void* param_bf16, void* stream);
 int gwx_sample_proposal(const float* net_out, int ldn, const double* mean3, const double* scale3,
                         const gwx_prior* prior, const double* truth, int64_t E, const int64_t* event_offsets,
-                        int64_t S, uint64_t seed, uint32_t counter, double* theta, double* log_ratio,
-                        void* stream);
+                        int64_t S, uint64_t seed, uint32_t counter, int flags, double* theta,
+                        double* log_ratio, void* stream);
 
 /* Autotuner of the product's tile raster (a set-up call, not a hot call: it launches the
  * product several times on the caller's buffers and synchronises `stream`).  For the

@@ -136,14 +136,15 @@ def proposal_uniforms(seed, counter, idx):
     return out
 
 
-def sample_proposal(net_out, mean, scale, prior, truth, offsets, seed, counter):
+def sample_proposal(net_out, mean, scale, prior, truth, offsets, seed, counter, fix_angles=False):
     """Samples for importance sampling, event e owning rows offsets[e] .. offsets[e+1]-1.
 
     Uniforms u[0..9] of sample s (proposal_uniforms): normals z0, z1 = r (cos, sin)(2 pi u1)
     with r = sqrt(-2 ln u0), z2 = sqrt(-2 ln u2) cos(2 pi u3); u4 orders the masses; phic,
     psi, RA = lo + (hi - lo) u5, u6, 2 pi u8 (psi, phic ranges from the prior, RA in
     [0, 2 pi)); theta_JN = acos(2 u7 - 1); dec = asin(2 u9 - 1); spins and t_c are the
-    event's own (truth [11][E]).  With net_out (rows per event: mu in columns 0..2, s in
+    event's own (truth [11][E]); with fix_angles so are phic, theta_JN, psi, RA and dec
+    (the proposal then covers m1, m2, D only).  With net_out (rows per event: mu in columns 0..2, s in
     3..5) the masses and distance come from proposal() with log ratio ln pi - ln q;
     without it (the prior as proposal) m1 = lo + (hi - lo) u0, m2 likewise with u2,
     D = d_lo + (d_hi - d_lo) u1, log ratio 0.  Returns (theta [11][S], log_ratio [S])."""
@@ -161,6 +162,9 @@ def sample_proposal(net_out, mean, scale, prior, truth, offsets, seed, counter):
     th[7] = np.arccos(2.0 * u[:, 7] - 1.0)
     th[9] = 2.0 * math.pi * u[:, 8]
     th[10] = np.arcsin(2.0 * u[:, 9] - 1.0)
+    if fix_angles:
+        for r in (6, 7, 8, 9, 10):
+            th[r] = truth[r][ev]
     if net_out is None:
         th[0] = prior["m_lo"] + (prior["m_hi"] - prior["m_lo"]) * u[:, 0]
         th[1] = prior["m_lo"] + (prior["m_hi"] - prior["m_lo"]) * u[:, 2]

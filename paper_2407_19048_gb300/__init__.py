@@ -380,7 +380,8 @@ def adamw(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, weight_
                                  weight_decay, step, _ptr(param_bf16), _stream()))
 
 
-def sample_proposal(prior, truth, event_offsets, seed, counter, net_out=None, mean=None, scale=None):
+def sample_proposal(prior, truth, event_offsets, seed, counter, net_out=None, mean=None, scale=None,
+                    fix_angles=False):
     """Importance-sampling draws: returns (theta [11][S] float64, log_ratio [S] float64)."""
     torch = _torch()
     _dev(truth, torch.float64, "truth")
@@ -396,8 +397,8 @@ def sample_proposal(prior, truth, event_offsets, seed, counter, net_out=None, me
         ldn = net_out.shape[1]
     p = _prior(prior)
     _check(_lib.load().gwx_sample_proposal(_ptr(net_out), ldn, _host3(mean), _host3(scale), ctypes.byref(p),
-                                           _ptr(truth), E, _ptr(event_offsets), S, seed, counter, _ptr(theta),
-                                           _ptr(lr), _stream()))
+                                           _ptr(truth), E, _ptr(event_offsets), S, seed, counter,
+                                           1 if fix_angles else 0, _ptr(theta), _ptr(lr), _stream()))
     return theta, lr
 
 

@@ -69,7 +69,8 @@ SIGNATURES = {
     "gwx_gauss_nll": (c_int, [c_vp, c_int, c_vp, c_int, c_i64, c_vp, c_vp, c_vp, c_vp]),
     "gwx_adamw": (c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl, c_i64, c_vp, c_vp]),
     "gwx_sample_proposal": (c_int, [c_vp, c_int, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl),
-                                    ctypes.POINTER(GwxPrior), c_vp, c_i64, c_vp, c_i64, c_u64, c_u32, c_vp, c_vp, c_vp]),
+                                    ctypes.POINTER(GwxPrior), c_vp, c_i64, c_vp, c_i64, c_u64, c_u32, c_int, c_vp, c_vp,
+                                    c_vp]),
     "gwx_gemm_autotune": (c_int, [c_vp, c_vp, c_vp, c_i64, c_i64, c_i64, c_int, c_vp, c_vp]),
     "gwx_device_status": (c_int, []),
     "gwx_rfft": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp]),

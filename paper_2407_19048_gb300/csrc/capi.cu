@@ -670,8 +670,10 @@ int gwx_adamw(float* param, const float* grad, float* m, float* v, int64_t n, do
 
 int gwx_sample_proposal(const float* net_out, int ldn, const double* mean3, const double* scale3,
                         const gwx_prior* prior, const double* truth, int64_t E, const int64_t* event_offsets,
-                        int64_t S, uint64_t seed, uint32_t counter, double* theta, double* log_ratio, void* stream) {
+                        int64_t S, uint64_t seed, uint32_t counter, int flags, double* theta, double* log_ratio,
+                        void* stream) {
   if (!prior) return fail(GWX_EINVAL, "prior is NULL");
+  if (flags & ~GWX_PROPOSAL_FIX_ANGLES) return fail(GWX_EINVAL, "flags 0x%x", flags);
   if (E < 0 || S < 0 || (S > 0 && E == 0) || S > 0x7fffffffLL * 64) return fail(GWX_ESHAPE, "bad E or S");
   if (net_out && (ldn < 6 || !mean3 || !scale3)) return fail(GWX_EINVAL, "net_out needs ldn >= 6, mean and scale");
   if (net_out)
@@ -685,7 +687,7 @@ int gwx_sample_proposal(const float* net_out, int ldn, const double* mean3, cons
   GWX_ALIGN8(log_ratio);
   GWX_TRY(ensure_init());
   return launched(launch_proposal(net_out, ldn, mean3, scale3, *prior, truth, E, event_offsets, S, seed, counter,
-                                  theta, log_ratio, as_stream(stream)),
+                                  (flags & GWX_PROPOSAL_FIX_ANGLES) ? 1 : 0, theta, log_ratio, as_stream(stream)),
                   "sample_proposal");
 }
 

@@ -103,7 +103,7 @@ cudaError_t launch_adamw(float* p, const float* g, float* m, float* v, int64_t n
                          double eps, double wd, int64_t step, void* p16, cudaStream_t s);
 cudaError_t launch_proposal(const float* net, int ldn, const double* mean, const double* scale, const gwx_prior& pr,
                             const double* truth, int64_t E, const int64_t* off, int64_t S, uint64_t seed,
-                            uint32_t counter, double* theta, double* lratio, cudaStream_t s);
+                            uint32_t counter, int fix_angles, double* theta, double* lratio, cudaStream_t s);
 
 // Record msg as the calling thread's gwx_last_error() message; returns status.
 int set_last_error(int status, const char* msg);

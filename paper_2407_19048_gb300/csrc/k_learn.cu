@@ -100,7 +100,7 @@ __global__ void k_adamw(float* __restrict__ p, const float* __restrict__ g, floa
 
 __global__ void k_proposal(const float* __restrict__ net, int ldn, Std3 st, gwx_prior pr,
                            const double* __restrict__ truth, int64_t E, const int64_t* __restrict__ off, int64_t S,
-                           uint32_t k0, uint32_t k1, uint32_t counter, double* __restrict__ theta,
+                           uint32_t k0, uint32_t k1, uint32_t counter, int fix_angles, double* __restrict__ theta,
                            double* __restrict__ lratio) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= S) return;
@@ -126,6 +126,8 @@ __global__ void k_proposal(const float* __restrict__ net, int ldn, Std3 st, gwx_
   th[7 * S + s] = acos(2.0 * u[7] - 1.0);
   th[9 * S + s] = 2.0 * PI_L * u[8];
   th[10 * S + s] = asin(2.0 * u[9] - 1.0);
+  if (fix_angles)
+    for (int r = 6; r <= 10; ++r) th[(int64_t)r * S + s] = truth[(int64_t)r * E + e];
   if (!net) {   // the prior as proposal
     th[s] = pr.m_lo + (pr.m_hi - pr.m_lo) * u[0];
     th[S + s] = pr.m_lo + (pr.m_hi - pr.m_lo) * u[2];
@@ -216,7 +218,7 @@ cudaError_t launch_adamw(float* p, const float* g, float* m, float* v, int64_t n
 
 cudaError_t launch_proposal(const float* net, int ldn, const double* mean, const double* scale, const gwx_prior& pr,
                             const double* truth, int64_t E, const int64_t* off, int64_t S, uint64_t seed,
-                            uint32_t counter, double* theta, double* lratio, cudaStream_t s) {
+                            uint32_t counter, int fix_angles, double* theta, double* lratio, cudaStream_t s) {
   Std3 st;
   for (int i = 0; i < 3; ++i) {
     st.mean[i] = mean ? mean[i] : 0.0;
@@ -224,7 +226,7 @@ cudaError_t launch_proposal(const float* net, int ldn, const double* mean, const
   }
   k_proposal<<<(unsigned)((S + 127) / 128), 128, 0, s>>>(net, ldn, st, pr, truth, E, off, S,
                                                          (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32),
-                                                         counter, theta, lratio);
+                                                         counter, fix_angles, theta, lratio);
   return cudaGetLastError();
 }
 

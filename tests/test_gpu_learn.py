@@ -75,8 +75,8 @@ def test_adamw_three_steps(gwx):
     np.testing.assert_allclose(host(P16.float()), pr, rtol=2.0 ** -8, atol=1e-6)
 
 
-@pytest.mark.parametrize("learned", [False, True])
-def test_sample_proposal(gwx, learned):
+@pytest.mark.parametrize("learned,fix", [(False, False), (True, False), (True, True)])
+def test_sample_proposal(gwx, learned, fix):
     wl = workloads.workload("small")
     prior = wl["prior"]
     E = 7
@@ -87,8 +87,8 @@ def test_sample_proposal(gwx, learned):
     if learned:
         net[:, 3:6] -= 1.0
     th, lr = gwx.sample_proposal(prior, cuda(truth), cuda(offs), seed=11, counter=5,
-                                 net_out=cuda(net) if learned else None, mean=MEAN, scale=SCALE)
-    th_ref, lr_ref = learn.sample_proposal(net, MEAN, SCALE, prior, truth, offs, seed=11, counter=5)
+                                 net_out=cuda(net) if learned else None, mean=MEAN, scale=SCALE, fix_angles=fix)
+    th_ref, lr_ref = learn.sample_proposal(net, MEAN, SCALE, prior, truth, offs, seed=11, counter=5, fix_angles=fix)
     np.testing.assert_allclose(host(th), th_ref, rtol=1e-12, atol=1e-12)
     got = host(lr)
     fin = np.isfinite(lr_ref)
@@ -96,3 +96,23 @@ def test_sample_proposal(gwx, learned):
     np.testing.assert_allclose(got[fin], lr_ref[fin], rtol=0, atol=1e-9)
     if learned:
         assert fin.sum() > 0.3 * len(fin)
+
+
+def test_training_lowers_the_loss(gwx):
+    """300 AdamW steps of the learned proposal on simulated batches (512 draws of the
+    two-detector workload) lower the batch Gaussian loss from its start."""
+    import paper_2407_19048_gb300.simulator as S
+    from paper_2407_19048_gb300.proposal import LearnedProposal
+    wl = workloads.workload("small", B=512)
+    sim = S.Simulator(wl, pipeline=True, background_every=16)
+    net = LearnedProposal(wl, hidden=256)
+    first, last = [], []
+    for i in range(300):
+        y, th, _ = sim.step(i)
+        loss = net.train_step(y, th)
+        if i < 10:
+            first.append(float(loss.item()))
+        if i >= 290:
+            last.append(float(loss.item()))
+    gwx.device_status()
+    assert np.mean(last) < np.mean(first) - 0.5, (np.mean(first), np.mean(last))
