@@ -182,10 +182,30 @@ __device__ __forceinline__ float waveform_turns(const DrawCoef& c, int k, float&
   return tt;
 }
 
-// e^{-2 pi i turns}
+// e^{-2 pi i turns} for |turns| < 2^21.  turns = q/4 + r with q = rint(4 turns) and
+// |r| <= 1/8 (r exact); sin(2 pi r) and cos(2 pi r) from their Taylor series through
+// r^9 and r^10 (the first omitted terms are below 2e-9 and 1e-10 for |2 pi r| <= pi/4),
+// with the leading coefficients 2 pi and -(2 pi)^2/2 as double-float pairs: rounding
+// them to one float would scale the result by ~3e-8 and bias |H|^2 systematically.  The
+// quarter turns q then rotate (cos, sin) by multiples of 90 degrees.
 __device__ __forceinline__ float2 expm2pi(float turns) {
-  float s, c;
-  sincospif(2.0f * turns, &s, &c);
+  const float q = rintf(4.0f * turns);
+  const float r = fmaf(q, -0.25f, turns);
+  const float z = r * r;
+  // coefficients (-1)^k (2 pi)^n / n! of r^n; the n = 1 and n = 2 terms as hi + lo
+  const float ps = fmaf(z, fmaf(z, fmaf(z, fmaf(z, 42.058693944897655f, -76.70585975306139f), 81.60524927607506f),
+                                -41.34170224039976f),
+                        -1.7484555314695172e-07f);
+  const float sn = fmaf(r, 6.2831854820251465f, r * ps);
+  const float pc = fmaf(z, fmaf(z, fmaf(z, fmaf(z, -26.4262567833744f, 60.24464137187666f), -85.45681720669373f),
+                                64.9393940226683f),
+                        -5.807431762150372e-07f);
+  const float cs = fmaf(z, -19.739208221435547f, fmaf(z, pc, 1.0f));
+  const int qi = (int)q;
+  // angle 2 pi (q/4 + r): quadrant qi & 3 rotates (cos, sin) by qi * 90 degrees
+  const float c1 = (qi & 1) ? sn : cs, s1 = (qi & 1) ? cs : sn;
+  const float c = ((qi + 1) & 2) ? -c1 : c1;
+  const float s = (qi & 2) ? -s1 : s1;
   return make_float2(c, -s);
 }
 
