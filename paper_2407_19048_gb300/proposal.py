@@ -103,4 +103,44 @@ class LearnedProposal:
                                         mean=self.mean, scale=self.scale, fix_angles=fix_angles)
 
 
+    # ---------------------------------------------------------------- checkpoints
+    _MAGIC = b"GWXPROP1"
+
+    def save(self, path, next_step=None):
+        """Write weights, AdamW moments, step count, standardisation and the caller's
+        next data-stream counter to a flat binary file: magic, a little-endian int64
+        header (layers, hidden, features, steps, next_step), 6 float64 (mean, scale),
+        then per layer the FP32 arrays W, b, m_W, v_W, m_b, v_b in C order."""
+        import numpy as np
+        with open(path, "wb") as fh:
+            fh.write(self._MAGIC)
+            np.array([len(self.W), self.H, self.F, self.steps, -1 if next_step is None else next_step],
+                     dtype="<i8").tofile(fh)
+            np.array(self.mean + self.scale, dtype="<f8").tofile(fh)
+            for i in range(len(self.W)):
+                for t in (self.W[i], self.b[i], self.mW[i], self.vW[i], self.mb[i], self.vb[i]):
+                    t.detach().cpu().numpy().astype("<f4").tofile(fh)
+
+    def load(self, path):
+        """Restore a checkpoint written by save() into this object (same shapes); returns
+        the stored next data-stream counter (None if none was stored)."""
+        import numpy as np
+        import torch
+        with open(path, "rb") as fh:
+            if fh.read(len(self._MAGIC)) != self._MAGIC:
+                raise ValueError("not a learned-proposal checkpoint: %s" % path)
+            layers, H, F, steps, nxt = (int(v) for v in np.fromfile(fh, dtype="<i8", count=5))
+            if (layers, H, F) != (len(self.W), self.H, self.F):
+                raise ValueError("checkpoint shapes (%d, %d, %d) differ from this network" % (layers, H, F))
+            ms = np.fromfile(fh, dtype="<f8", count=6)
+            self.mean, self.scale = [float(v) for v in ms[:3]], [float(v) for v in ms[3:]]
+            for i in range(layers):
+                for t in (self.W[i], self.b[i], self.mW[i], self.vW[i], self.mb[i], self.vb[i]):
+                    a = np.fromfile(fh, dtype="<f4", count=t.numel()).reshape(tuple(t.shape))
+                    t.copy_(torch.from_numpy(a))
+                self.W16[i].copy_(self.W[i].to(torch.bfloat16))
+            self.steps = steps
+        return None if nxt < 0 else nxt
+
+
 __all__ = ["LearnedProposal"]

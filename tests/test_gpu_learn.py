@@ -116,3 +116,32 @@ def test_training_lowers_the_loss(gwx):
             last.append(float(loss.item()))
     gwx.device_status()
     assert np.mean(last) < np.mean(first) - 0.5, (np.mean(first), np.mean(last))
+
+
+def test_checkpoint_resume_is_bit_exact(gwx, tmp_path):
+    """Training resumed from a checkpoint (weights, AdamW moments, step count, data-stream
+    counter) follows the uninterrupted run bit for bit: the batches come from Philox
+    counters, so the data stream resumes exactly too."""
+    import paper_2407_19048_gb300.simulator as S
+    from paper_2407_19048_gb300.proposal import LearnedProposal
+    wl = workloads.workload("small", B=128)
+
+    def run(net, sim, first, n):
+        for i in range(first, first + n):
+            y, th, _ = sim.step(i)
+            net.train_step(y, th)
+
+    a = LearnedProposal(wl, hidden=128, seed=3)
+    sim_a = S.Simulator(wl)
+    run(a, sim_a, 0, 15)
+    path = str(tmp_path / "prop.ckpt")
+    a.save(path, next_step=15)
+    run(a, sim_a, 15, 10)
+    b = LearnedProposal(wl, hidden=128, seed=99)      # different initial weights
+    nxt = b.load(path)
+    assert nxt == 15 and b.steps == 15
+    run(b, S.Simulator(wl), nxt, 10)
+    torch.cuda.synchronize()
+    for i in range(3):
+        np.testing.assert_array_equal(host(a.W[i]), host(b.W[i]))
+        np.testing.assert_array_equal(host(a.vb[i]), host(b.vb[i]))
