@@ -247,9 +247,13 @@ int gwx_simulate_batch(const gwx_prior* prior, uint64_t seed, uint32_t step,
 int gwx_prepare_batch(const gwx_prior* prior, uint64_t seed, uint32_t step, int64_t L, int64_t N,
                       double fs, double f_lo, const int32_t* det_ids, int D, double gmst, int64_t B,
                       double* theta, int64_t* offsets, void* workspace, size_t workspace_bytes, void* stream);
+/* flags GWX_SIM_FILTERS_READY: the whitening filter this call would compute from psd is
+ * already in the workspace (an earlier gwx_simulate_prepared or gwx_simulate_batch on the
+ * same workspace with the same psd, seg_len, fs, f_lo, D and N), so it is not rebuilt. */
+#define GWX_SIM_FILTERS_READY 1
 int gwx_simulate_prepared(const float* noise, int64_t L, const double* psd, int64_t seg_len,
                           double fs, double f_lo, int D, int64_t B, int64_t N, const int64_t* offsets,
-                          float* y, void* workspace, size_t workspace_bytes, void* stream);
+                          float* y, int flags, void* workspace, size_t workspace_bytes, void* stream);
 
 /* ---- A8: log-likelihood -------------------------------------------------------
  * Sec. 6 (Fig. 5 caption): the standard GW likelihood.  For sample s of event e

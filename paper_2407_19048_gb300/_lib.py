@@ -50,8 +50,8 @@ SIGNATURES = {
                                    c_i32p, c_int, c_dbl, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_size, c_vp]),
     "gwx_prepare_batch": (c_int, [ctypes.POINTER(GwxPrior), c_u64, c_u32, c_i64, c_i64, c_dbl, c_dbl, c_i32p, c_int,
                                   c_dbl, c_i64, c_vp, c_vp, c_vp, c_size, c_vp]),
-    "gwx_simulate_prepared": (c_int, [c_vp, c_i64, c_vp, c_i64, c_dbl, c_dbl, c_int, c_i64, c_i64, c_vp, c_vp, c_vp,
-                                      c_size, c_vp]),
+    "gwx_simulate_prepared": (c_int, [c_vp, c_i64, c_vp, c_i64, c_dbl, c_dbl, c_int, c_i64, c_i64, c_vp, c_vp,
+                                      c_int, c_vp, c_size, c_vp]),
     "gwx_log_likelihood_workspace": (c_size, [c_i64, c_int, c_i64, c_i64]),
     "gwx_log_likelihood": (c_int, [c_int, c_vp, c_i64, c_int, c_i64, c_vp, c_i64, c_dbl, c_dbl, c_i32p, c_dbl,
                                    c_vp, c_vp, c_i64, c_vp, c_vp, c_size, c_vp]),

@@ -377,8 +377,9 @@ int gwx_prepare_batch(const gwx_prior* prior, uint64_t seed, uint32_t step, int6
 }
 
 int gwx_simulate_prepared(const float* noise, int64_t L, const double* psd, int64_t seg_len, double fs, double f_lo,
-                          int D, int64_t B, int64_t N, const int64_t* offsets, float* y, void* workspace,
+                          int D, int64_t B, int64_t N, const int64_t* offsets, float* y, int flags, void* workspace,
                           size_t workspace_bytes, void* stream) {
+  if (flags & ~GWX_SIM_FILTERS_READY) return fail(GWX_EINVAL, "flags 0x%x", flags);
   int k_lo = 0;
   GWX_TRY(check_sim_shapes(D, L, B, N, fs, f_lo, &k_lo));
   GWX_TRY(check_psd_args(seg_len, N));
@@ -392,8 +393,10 @@ int gwx_simulate_prepared(const float* noise, int64_t L, const double* psd, int6
   cudaStream_t s = as_stream(stream);
   float* W = reinterpret_cast<float*>(workspace);
   float2* Wp = sim_packed(workspace, D, N);
-  GWX_TRY(launched(launch_whiten_filter(psd, D, seg_len, fs, k_lo, N, W, s), "whiten filter"));
-  GWX_TRY(launched(launch_packed_filter(W, D, N, Wp, s), "packed filter"));
+  if (!(flags & GWX_SIM_FILTERS_READY)) {
+    GWX_TRY(launched(launch_whiten_filter(psd, D, seg_len, fs, k_lo, N, W, s), "whiten filter"));
+    GWX_TRY(launched(launch_packed_filter(W, D, N, Wp, s), "packed filter"));
+  }
   return launched(launch_simulate_fused(sim_coef(workspace, D, N), noise, L, offsets, W, Wp, k_lo, D, B, N, fs, y, s),
                   "simulate");
 }
@@ -406,7 +409,7 @@ int gwx_simulate_batch(const gwx_prior* prior, uint64_t seed, uint32_t step, con
   if (B > 0 && (!noise || !psd || !y)) return fail(GWX_EINVAL, "NULL array");
   GWX_TRY(gwx_prepare_batch(prior, seed, step, L, N, fs, f_lo, det_ids, D, gmst, B, theta, offsets, workspace,
                             workspace_bytes, stream));
-  return gwx_simulate_prepared(noise, L, psd, seg_len, fs, f_lo, D, B, N, offsets, y, workspace, workspace_bytes,
+  return gwx_simulate_prepared(noise, L, psd, seg_len, fs, f_lo, D, B, N, offsets, y, 0, workspace, workspace_bytes,
                                stream);
 }
 

@@ -29,8 +29,9 @@ from . import DETECTORS, NPARAM, _det_ids, _prior, _ptr, _stream, _workspace, _c
 
 
 class Simulator:
-    # kernels per call: prepare 2, colored noise 2, Welch 2, simulate_prepared 3
-    LAUNCHES = {"prepare": 2, "colored_noise": 2, "welch": 2, "simulate": 3}
+    # kernels per call: prepare 2, colored noise 2, Welch 2, simulate_prepared 3 (1 when the
+    # whitening filter of its workspace is still current)
+    LAUNCHES = {"prepare": 2, "colored_noise": 2, "welch": 2, "simulate": 3, "simulate_reuse": 1}
 
     def __init__(self, workload, device=None, noise_on_device=True, pipeline=False, background_every=1):
         import torch
@@ -68,6 +69,8 @@ class Simulator:
         self.ev_done = torch.cuda.Event()
         self._ev_prep = [torch.cuda.Event() for _ in range(nbuf)]
         self._slot = 0
+        self._psd_version = 0     # incremented whenever the PSD is recomputed
+        self._filter_version = [-1] * nbuf   # PSD version each workspace's whitening filter was built from
         self._ready = None        # step counter already prepared in the current slot (pipeline)
         self._since_bg = None     # batches since the last background
         self.launches = 0         # kernels launched so far (all calls of this object)
@@ -107,6 +110,7 @@ class Simulator:
         _check(lib.gwx_welch_psd(_ptr(self.noise), self.D, self.L, self.fs, self.M, self.stride, _ptr(self.psd),
                                  _ptr(ws), nb, s))
         self.launches += self.LAUNCHES["welch"]
+        self._psd_version += 1
 
     def prepare(self, step, slot=None):
         slot = self._slot if slot is None else slot
@@ -120,10 +124,12 @@ class Simulator:
     def simulate_prepared(self, slot=None):
         slot = self._slot if slot is None else slot
         ws, nb = self._ws_sim[slot]
+        ready = self._filter_version[slot] == self._psd_version
         _check(self.lib.gwx_simulate_prepared(_ptr(self.noise), self.L, _ptr(self.psd), self.M, self.fs, self.f_lo,
                                               self.D, self.B, self.N, _ptr(self._offsets[slot]),
-                                              _ptr(self._y[slot]), _ptr(ws), nb, _stream()))
-        self.launches += self.LAUNCHES["simulate"]
+                                              _ptr(self._y[slot]), 1 if ready else 0, _ptr(ws), nb, _stream()))
+        self._filter_version[slot] = self._psd_version
+        self.launches += self.LAUNCHES["simulate_reuse" if ready else "simulate"]
 
     def simulate(self, step):
         """prepare + simulate_prepared on the current stream (the single-call gwx_simulate_batch)."""
@@ -132,6 +138,7 @@ class Simulator:
                                            _ptr(self.noise), self.L, _ptr(self.psd), self.M, self.fs, self.f_lo,
                                            self.ids, self.D, self.gmst, self.B, self.N, _ptr(self.y),
                                            _ptr(self.theta), _ptr(self.offsets), _ptr(ws), nb, _stream()))
+        self._filter_version[self._slot] = self._psd_version
         self.launches += self.LAUNCHES["prepare"] + self.LAUNCHES["simulate"]
 
     def step(self, step, mark=None):
