@@ -176,6 +176,17 @@ def test_colored_noise_matches_oracle(gwx, name):
     assert rms(got - ref) <= 1e-5 * r
 
 
+def test_colored_noise_longest_background(gwx):
+    """The largest background the call accepts, L = 2^24 samples (2.3 h at 2048 Hz), one
+    detector: the four-step transform's largest factorisation and 64-bit indexing."""
+    L = 1 << 24
+    ref = noise.colored_noise(2, 9, 1, L, 2048.0, 20.0)
+    got = host(gwx.colored_noise(2, 9, 1, L, 2048.0, 20.0))
+    r = rms(ref)
+    assert np.abs(got - ref).max() <= 1e-4 * r
+    assert rms(got - ref) <= 1e-5 * r
+
+
 # ------------------------------------------------------------------ A5 Welch
 @pytest.mark.parametrize("name", ["small", "hl3"])
 def test_welch_matches_oracle(gwx, name):
@@ -423,7 +434,7 @@ def _events(wl, E, seed):
     return th, y, psd
 
 
-@pytest.mark.parametrize("name", ["small", "hl3"])
+@pytest.mark.parametrize("name", ["small", "hl3", "sweep"])
 def test_log_likelihood_matches_oracle(gwx, name):
     wl = workloads.workload(name)
     E = 6
