@@ -44,7 +44,7 @@ SM_MAX_MHZ = 2070.0
 # ncu DRAM traffic (read + write bytes) of one k_simulate launch on the hl3
 # workload and the hash of the kernel sources it was measured on; see
 # profiles/k_simulate_hl3.md.  None until a capture matches the current sources.
-TRAFFIC = {"bytes_per_launch": 143167488, "sources_sha1": "669042c740ab3146ca2e4ddc908e06f44498345a"}
+TRAFFIC = {"bytes_per_launch": 143846656, "sources_sha1": "bc9f3a78295835e84c4888ea28b61541460c5abc"}
 
 
 def _measured_peaks():
@@ -396,9 +396,26 @@ def learned_leg(gwx, torch, rank, steps=2000, events=32, per_event=4000):
             key = ("learned" if learned else "prior") + ("_angles_known" if fix else "")
             res[key] = {"ess_total": e, "ess_median": float(ess.median().item()),
                         "efficiency_median": float(eff.median().item()), "ess_per_s": e / best}
-    del sim, sim_ev
+    # calibration: the truth's CDF under each event's Gaussian (PP test) on 512 fresh draws
+    wl_pp = dict(workloads.workload("small", B=512), param_seed=778)
+    sim_pp = gwx.simulator.Simulator(wl_pp)
+    y_pp, th_pp, _ = sim_pp.step(step_counter(rank, 1))
+    out = net.net_out(y_pp).cpu().numpy().astype(np.float64)
+    t = gwx.proposal_targets(th_pp, net.mean, net.scale).cpu().numpy().astype(np.float64)
+    z = (t - out[:, :3]) / np.exp(out[:, 3:6])
+    import math
+    cdf = 0.5 * (1.0 + np.vectorize(math.erf)(z / math.sqrt(2.0)))
+    ks = []
+    for p in range(3):
+        u = np.sort(cdf[:, p])
+        n = len(u)
+        ks.append(float(max(np.max(np.arange(1, n + 1) / n - u), np.max(u - np.arange(n) / n))))
+    del sim, sim_ev, sim_pp
     return {"train_steps": steps, "batch": 512, "train_s": train_s, "loss": losses, "events": events,
             "samples_per_event": per_event, "importance_sampling": res,
+            "pp_test": {"draws": 512, "z_rms": [float(v) for v in np.sqrt((z ** 2).mean(axis=0))],
+                        "ks_distance": ks, "ks_95pct_critical": 1.36 / math.sqrt(512),
+                        "params": ["chirp mass", "total mass", "distance"]},
             "note": "Gaussian over (Mc, M, D) from log spectral powers, two GELU layers of 512; spins and "
                     "merger time known in both proposals"}
 
