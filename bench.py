@@ -266,47 +266,35 @@ def loglike_leg(gwx, torch, wl, rank, lo=2000, hi=50000):
 def serving_leg(gwx, torch, rank, n_events=1000):
     """Streaming loop of the plain importance-sampling path on the 8 s, three-detector
     geometry (N = 16384): 1000 events with U{2000..50000} samples each arrive one at a
-    time; per event the samples are drawn from the prior, scored by log_likelihood and
-    weighted by importance_weights, and the event's effective sample size is read back
-    to the host.  Latency is host time from the start of the event to that read."""
+    time; per event the samples are drawn from the prior, scored by the likelihood and
+    weighted (`scorer.Scorer`: preallocated buffers, C-ABI calls on one stream), and the
+    event's effective sample size is read back to the host.  Latency is host time from
+    the start of the event to that read."""
     import numpy as np
+    from paper_2407_19048_gb300.scorer import Scorer
     wl = workloads.workload("sweep", B=n_events)
     counts = workloads.ragged_counts(5 + rank, n_events, 2000, 50000)
     sim = gwx.simulator.Simulator(wl)
     y, _, _ = sim.step(step_counter(rank, 5000))
-    psd = sim.psd
-    smax = int(counts.max())
-    theta_flat = torch.empty(11 * smax, dtype=torch.float64, device="cuda")
-    lnl = torch.empty(smax, dtype=torch.float64, device="cuda")
-    offs = torch.zeros(2, dtype=torch.int64, device="cuda")
-
-    def event(e):
-        S = int(counts[e])
-        theta = theta_flat[:11 * S].view(11, S)
-        gwx.sample_prior(wl["prior"], 55, step_counter(rank, e), S, wl["L"], wl["N"], theta=theta)
-        offs[1] = S
-        out = gwx.log_likelihood(y[e:e + 1], psd, wl["seg_len"], wl["fs"], wl["f_lo"], wl["dets"], 0.0, theta, offs,
-                                 out=lnl[:S])
-        _, ess, _, _ = gwx.importance_weights(out, offs)
-        return float(ess[0].item())
-
+    scorer = Scorer(wl, int(counts.max()), sim.psd)
     for e in range(5):
-        event(e)
+        scorer.score(y[e], int(counts[e]), step_counter(rank, e))
     torch.cuda.synchronize()
     lat = []
     t0 = time.perf_counter()
     for e in range(n_events):
         a = time.perf_counter()
-        event(e)
+        scorer.score(y[e], int(counts[e]), step_counter(rank, e))
         lat.append(time.perf_counter() - a)
     wall = time.perf_counter() - t0
     lat_ms = np.array(lat) * 1e3
-    del sim, y
+    del sim, y, scorer
     return {"events": n_events, "samples": int(counts.sum()), "events_per_s": n_events / wall,
             "samples_per_s": float(counts.sum()) / wall, "latency_ms_p50": float(np.percentile(lat_ms, 50)),
             "latency_ms_p99": float(np.percentile(lat_ms, 99)), "latency_ms_max": float(lat_ms.max()),
             "workload": "8 s windows at 2048 Hz (N = 16384), H1+L1+V1, U{2000..50000} prior samples per event",
-            "per_event": "sample_prior + log_likelihood + importance_weights + host read of the ESS"}
+            "per_event": "sample_prior + log_likelihood + importance_weights + host read of ESS, efficiency, ln Z "
+                         "(preallocated, one stream)"}
 
 
 def gemm_leg(gwx, torch, shape=(8192, 8192, 8192)):

@@ -101,3 +101,22 @@ def test_importance_weights_after_log_likelihood(gwx):
                              cuda(samples), cuda(offs))
     got = gwx.importance_weights(lnl, cuda(offs))
     _compare(got, importance.importance_weights(lnl_ref, offs), rtol=5e-3, z_atol=2e-3)
+
+
+def test_scorer_matches_the_separate_calls(gwx):
+    """The serving Scorer (preallocated, one stream) gives the same ESS, efficiency and
+    evidence as sample_prior + log_likelihood + importance_weights called separately."""
+    import paper_2407_19048_gb300.simulator as S
+    from paper_2407_19048_gb300.scorer import Scorer
+    wl = workloads.workload("small", B=3)
+    sim = S.Simulator(wl)
+    y, _, _ = sim.step(4)
+    sc = Scorer(wl, 3000, sim.psd)
+    for e, n in enumerate((3000, 1234, 57)):
+        ess, eff, lnz = sc.score(y[e], n, 40 + e)
+        th, _ = gwx.sample_prior(wl["prior"], 55, 40 + e, n, wl["L"], wl["N"])
+        offs = cuda(np.array([0, n]))
+        lnl = gwx.log_likelihood(y[e:e + 1].contiguous(), sim.psd, wl["seg_len"], wl["fs"], wl["f_lo"], wl["dets"],
+                                 0.0, th, offs)
+        _, ess2, eff2, lnz2 = gwx.importance_weights(lnl, offs)
+        assert ess == host(ess2)[0] and eff == host(eff2)[0] and lnz == host(lnz2)[0]
