@@ -27,6 +27,8 @@ Modules, in pipeline order:
 * ``importance`` -- importance weights, effective sample size, evidence per event.
 * ``gemm``       -- bfloat16 dense products and the dense layer, forward and backward.
 * ``learn``      -- the learned Gaussian proposal: features, loss, AdamW, proposal density.
+* ``flow``       -- the conditional coupling flow: embedding, coupling layers, loss and its
+  gradient, base draws, the proposal map to theta and the prior-to-proposal ratio.
 * ``pipeline``   -- the whole per-batch pass, step by step, unfused.
 
 Everything is float64 / uint32-uint64 numpy.  ``numpy.fft`` is used as the

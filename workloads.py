@@ -102,3 +102,39 @@ def random_bf16_bits(seed, shape, exp_lo=-8, exp_hi=1):
     exp = (rng.integers(exp_lo, exp_hi + 1, shape) + 127).astype(np.uint16) << 7
     man = rng.integers(0, 128, shape).astype(np.uint16)
     return (sign | exp | man).astype(np.uint16)
+
+
+def flow_shape(features=64, group=8, embed_hidden=64, context=32, layers=4, hidden=64):
+    """Sizes of the conditional flow: spectral-feature columns F, bins per feature group G,
+    embedding hidden width H_e, context width C, coupling layers K, conditioner width H."""
+    return {"features": features, "group": group, "embed_hidden": embed_hidden, "context": context,
+            "layers": layers, "hidden": hidden}
+
+
+def flow_tensor_shapes(shape):
+    """The flow's parameter tensors in storage order: the embedding's three dense layers
+    (weight [out][in], bias [out]), then per coupling layer its conditioner's three."""
+    F, He, C = shape["features"], shape["embed_hidden"], shape["context"]
+    H, K = shape["hidden"], shape["layers"]
+    out = [(He, F), (He,), (He, He), (He,), (C, He), (C,)]
+    for _ in range(K):
+        out += [(H, 8 + C), (H,), (H, H), (H,), (8, H), (8,)]
+    return out
+
+
+def random_flow_params(seed, shape, gain=1.0, last_gain=0.5):
+    """Random flow parameters as float32 arrays whose weights are exactly representable in
+    bfloat16 (low 16 bits cleared): weights N(0, gain^2 / fan_in), the last layer of every
+    conditioner scaled by last_gain, biases N(0, 0.1^2) (not rounded)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    shapes = flow_tensor_shapes(shape)
+    for i, s in enumerate(shapes):
+        if len(s) == 2:
+            g = gain * (last_gain if (i >= 6 and i % 6 == 4) else 1.0)
+            w = (rng.normal(0.0, g / math.sqrt(s[1]), s)).astype(np.float32)
+            w = (w.view(np.uint32) & np.uint32(0xFFFF0000)).view(np.float32)
+            out.append(w)
+        else:
+            out.append(rng.normal(0.0, 0.1, s).astype(np.float32))
+    return out
