@@ -375,6 +375,133 @@ int gwx_sample_proposal(const float* net_out, int ldn, const double* mean3, cons
                         int64_t S, uint64_t seed, uint32_t counter, int flags, double* theta,
                         double* log_ratio, void* stream);
 
+/* ---- learned part: the conditional coupling flow ------------------------------------
+ * The posterior estimator q(theta | d) of Sec. 5: a standard normal over eight
+ * coordinates pushed through K affine coupling layers (Dinh, Sohl-Dickstein and Bengio
+ * 2017) whose shifts and log-scales small dense networks compute from a context vector
+ * c, the data summary of Sec. 4 computed from the spectral features of the whitened
+ * strain (gwx_spectral_features).  The paper's transforms are inverse-autoregressive;
+ * coupling transforms take one pass in both directions (training needs the density of
+ * simulated parameters, importance sampling needs draws).
+ *
+ * Coordinates r = (Mc, q, D_L, cos theta_JN, alpha, sin delta, psi, phi_c), chirp mass
+ * Mc = (m1 m2)^{3/5} / (m1 + m2)^{1/5}, q = min(m1, m2) / max(m1, m2); the flow works in
+ * x = (r - mean) / scale, mean8 and scale8 HOST arrays of 8 doubles (scale > 0).
+ *
+ * Shape: F feature columns (groups of G bins), embedding width H_e, context width C, K
+ * coupling layers (1..64), conditioner width H; F, H_e, C, H multiples of 8 in
+ * [8, 65535 * 32].
+ * Parameters: one flat FP32 array `params` and its bfloat16 copy `params_bf16` with the
+ * same element offsets (gwx_adamw with param_bf16 keeps them in step); weights are read
+ * from the bfloat16 copy, biases from the FP32 array.  Tensor t starts at element
+ * offsets[t] (a multiple of 64; gwx_flow_layout), in the order
+ *   embedding        W1 [H_e][F], b1 [H_e], W2 [H_e][H_e], b2 [H_e], W3 [C][H_e], b3 [C];
+ *   layer l = 0..K-1 V1 [H][8 + C], e1 [H], V2 [H][H], e2 [H], V3 [8][H], e3 [8].
+ * Embedding:  c = W3 h2 + b3, h2 = gelu(W2 h1 + b2), h1 = gelu(W1 f + b1), f the features
+ *             (f, h1, h2, c held in bfloat16).
+ * Layer l:    split (a, b) = SPLITS[l % 4], SPLITS = {(0 1 2 3 | 4 5 6 7), (4 5 6 7 | 0 1 2 3),
+ *             (0 2 4 6 | 1 3 5 7), (1 3 5 7 | 0 2 4 6)}; conditioner input row
+ *             X = [bf16(v_a), 0, 0, 0, 0, c] (bfloat16 [8 + C]); o = V3 g2 + e3 (FP32 [8]),
+ *             g2 = gelu(V2 g1 + e2), g1 = gelu(V1 X + e1) (bfloat16); shift mu_j = o_j,
+ *             log-scale s_j = 3 tanh(o_{4+j} / 3) on coordinate b_j.  Sampling direction
+ *             v_b <- v_b e^s + mu; density direction v_b <- (v_b - mu) e^{-s}.
+ * Sampling applies layers 0 .. K-1 to z ~ N(0, I_8), the density K-1 .. 0 to x;
+ * ln q_x(x) = ln N(z; 0, I_8) - sum over layers and j of s_j, and in r-coordinates
+ * ln q_r = ln q_x - sum_p ln scale_p.  Training minimises the batch mean of -ln q_x.
+ *
+ * gwx_flow_layout: *n_params = flat array length; offsets (6 + 6K entries) if not NULL. */
+typedef struct gwx_flow_shape {
+  int features;      /* F   */
+  int group;         /* G   */
+  int embed_hidden;  /* H_e */
+  int context;       /* C   */
+  int layers;        /* K   */
+  int hidden;        /* H   */
+} gwx_flow_shape;
+int gwx_flow_layout(const gwx_flow_shape* shape, int64_t* n_params, int64_t* offsets);
+
+/* Stages (one kernel each; the calls further down chain them).  Arrays are device
+ * arrays, row-major, 16-byte aligned (8-byte for doubles and int64).
+ * gwx_flow_targets: x [B][8] FP32 = (r(theta) - mean) / scale for theta [GWX_NPARAM][B].
+ * gwx_flow_conditioner_input: X bfloat16 [B][8 + C] of layer l from v [B][8] FP32 and
+ *   the context ctx bfloat16: [B][C] row by row when event_offsets is NULL, else [E][C]
+ *   with row r taking the context of the event owning global row row0 + r.
+ * gwx_flow_coupling: step of layer l, direction +1 (sampling) or -1 (density):
+ *   v_out [B][8] (may be v_in) from v_in and o [B][8] FP32;
+ *   sum_s[b] = (init ? 0 : sum_s[b]) + sum_j s_j.
+ * gwx_flow_nll: loss_rows[b] = |z_b|^2 / 2 + 4 ln(2 pi) + sum_s[b] (FP32), *loss_mean their
+ *   FP64 mean (device double), grad [B][8] = z / B.
+ * gwx_flow_coupling_backward: for a density step of layer l with output w [B][8] and
+ *   conditioner output o, given g = dL/dw: d_o [B][8] = dL/do including the term
+ *   row_weight x sum_j s_j of the loss, and g_u [B][8] = dL/dv_in except the
+ *   conditioner's share.
+ * gwx_flow_input_backward: adds dX[b][j] (j = 0..3; dX = dL/dX FP32 [B][8 + C]) into
+ *   g_u[b][a_j] and sets (init) or adds dX[b][8 ..] into d_ctx [B][C].
+ * gwx_flow_base: base draws z [n][8] FP32 of global draws row0 .. row0 + n - 1: Philox4x32-10
+ *   counters (s, j, 4, counter), key seed, block j = 0..3 giving u_{2j} = uniform52(w0, w1),
+ *   u_{2j+1} = uniform52(w2, w3) and the Box-Muller pair z_{2j}, z_{2j+1} =
+ *   sqrt(-2 ln u_{2j}) (cos, sin)(2 pi u_{2j+1}).
+ * gwx_flow_proposal: for flow draws x [S][8] with base z and sum_s: theta [GWX_NPARAM][S],
+ *   log_q [S] = ln q_r and log_ratio [S] = ln prior_r - ln q_r (-inf outside the prior's
+ *   support).  Inside it m_big = Mc (1 + q)^{1/5} q^{-3/5}, m_small = q m_big, swapped
+ *   into (m1, m2) when the coin u_8 (block 4 of the draw's counter, words 0 and 1) is
+ *   below 1/2; theta_JN = acos, dec = asin of their coordinates; spins and t_c are those
+ *   of the owning event in truth [GWX_NPARAM][E].  The prior (uniform in m1, m2, D, cos
+ *   theta_JN, RA, sin dec, psi, phic) has ln prior_r = ln 2 + 2 ln m_big - ln Mc
+ *   - ln((m_hi - m_lo)^2 (d_hi - d_lo) 8 pi (psi_hi - psi_lo) (phi_hi - phi_lo)).
+ *   Outside the support theta holds m_lo, d_lo and clipped angles. */
+int gwx_flow_targets(const double* theta, int64_t B, const double* mean8, const double* scale8, float* x,
+                     void* stream);
+int gwx_flow_conditioner_input(int layer, const float* v, const void* ctx, int C, const int64_t* event_offsets,
+                               int64_t E, int64_t row0, int64_t B, void* X, void* stream);
+int gwx_flow_coupling(int layer, int direction, const float* v_in, const float* o, int64_t B, float* v_out,
+                      float* sum_s, int init, void* stream);
+int gwx_flow_nll(const float* z, const float* sum_s, int64_t B, float* loss_rows, double* loss_mean, float* grad,
+                 void* stream);
+int gwx_flow_coupling_backward(int layer, const float* w, const float* o, const float* g, int64_t B,
+                               float row_weight, float* d_o, float* g_u, void* stream);
+int gwx_flow_input_backward(int layer, const float* dX, int C, int64_t B, float* g_u, float* d_ctx, int init,
+                            void* stream);
+int gwx_flow_base(uint64_t seed, uint32_t counter, int64_t row0, int64_t n, float* z, void* stream);
+int gwx_flow_proposal(const float* x, const float* z, const float* sum_s, int64_t S, const double* mean8,
+                      const double* scale8, const gwx_prior* prior, const double* truth, int64_t E,
+                      const int64_t* event_offsets, uint64_t seed, uint32_t counter, double* theta, double* log_q,
+                      double* log_ratio, void* stream);
+
+/* One training step on a simulated batch: whitened strain y [B][D][N] (FP32) and its
+ * parameters theta [GWX_NPARAM][B]: features, embedding, density pass, loss, backward
+ * into grads (flat, same layout as params; the whole array is rewritten), then (step >= 1)
+ * gwx_adamw over the flat array with step counter `step`; step 0 computes the loss and
+ * gradients only.  *loss_mean (device double) = batch mean of -ln q_x.  B a multiple of 8
+ * in [8, 65535 * 32].  Workspace gwx_flow_train_workspace(shape, B, D, N). */
+size_t gwx_flow_train_workspace(const gwx_flow_shape* shape, int64_t B, int D, int64_t N);
+int gwx_flow_train_step(const gwx_flow_shape* shape, float* params, void* params_bf16, float* grads, float* m,
+                        float* v, int64_t step, double lr, double beta1, double beta2, double eps,
+                        double weight_decay, const double* mean8, const double* scale8, const float* y,
+                        const double* theta, int64_t B, int D, int64_t N, double fs, double f_lo,
+                        double* loss_mean, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Density ln q_r(r(theta_b) | y_b) (FP64 [B]) of B parameter vectors, each with its own
+ * whitened window y [B][D][N].  Workspace gwx_flow_log_prob_workspace(shape, B, D, N). */
+size_t gwx_flow_log_prob_workspace(const gwx_flow_shape* shape, int64_t B, int D, int64_t N);
+int gwx_flow_log_prob(const gwx_flow_shape* shape, const float* params, const void* params_bf16,
+                      const double* mean8, const double* scale8, const float* y, const double* theta, int64_t B,
+                      int D, int64_t N, double fs, double f_lo, double* log_q, void* workspace,
+                      size_t workspace_bytes, void* stream);
+
+/* Posterior samples (Sec. 5: draws from q(theta | d) for new data; Sec. 6 judges them):
+ * event e of y [E][D][N] owns rows event_offsets[e] .. event_offsets[e+1] - 1 of the S
+ * outputs (event_offsets device int64 [E + 1], non-decreasing from 0 to S).  Per event
+ * the context is computed once; each draw runs the base normals, the K coupling layers
+ * in the sampling direction and gwx_flow_proposal (theta, log_q = ln q_r, log_ratio), in
+ * chunks of at most 2^17 draws.  Workspace gwx_sample_posterior_workspace(shape, E, D, N, S). */
+size_t gwx_sample_posterior_workspace(const gwx_flow_shape* shape, int64_t E, int D, int64_t N, int64_t S);
+int gwx_sample_posterior(const gwx_flow_shape* shape, const float* params, const void* params_bf16,
+                         const double* mean8, const double* scale8, const gwx_prior* prior, const float* y,
+                         int64_t E, int D, int64_t N, double fs, double f_lo, const double* truth,
+                         const int64_t* event_offsets, int64_t S, uint64_t seed, uint32_t counter, double* theta,
+                         double* log_q, double* log_ratio, void* workspace, size_t workspace_bytes, void* stream);
+
 /* Autotuner of the product's tile raster (a set-up call, not a hot call: it launches the
  * product several times on the caller's buffers and synchronises `stream`).  For the
  * shape (M, N, K, c_dtype) it times each candidate band height of the persistent tile

@@ -237,6 +237,33 @@ def _dense_back(X, W, b, dy, act_gelu, rnd_dz):
     return dzp @ W, dzp.T @ X, dz.sum(axis=0)
 
 
+def coupling_backward(l, w, o, G, row_weight):
+    """Chain rule through one density step of layer l with output w and conditioner
+    output o, given G = dL/dw and the weight of sum_s in the loss: returns
+    (dL/do [B][8], dL/dv_in [B][8] without the conditioner's share)."""
+    a, b = (list(t) for t in SPLITS[l % 4])
+    _, s = shift_logscale(o)
+    e = np.exp(-s)
+    G = np.asarray(G, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    Gb = G[:, b]
+    dmu = -Gb * e
+    ds = -Gb * w[:, b] + row_weight
+    do = np.concatenate([dmu, ds * (1.0 - (s / S_MAX) ** 2)], axis=1)
+    Gu = G.copy()
+    Gu[:, b] = Gb * e
+    return do, Gu
+
+
+def input_backward(l, dX, Gu, dc):
+    """Adds the conditioner input's gradient dX [B][8 + C] into the conditioning half of
+    Gu and into the context gradient dc (both returned as new arrays)."""
+    a, _ = SPLITS[l % 4]
+    Gu = np.array(Gu, dtype=np.float64)
+    Gu[:, list(a)] += dX[:, 0:4]
+    return Gu, np.asarray(dc, dtype=np.float64) + dX[:, 8:]
+
+
 def loss_and_grads(feat, x, params, K, rnd=round_bf16):
     """Mean training loss over rows (feat [B][F], x [B][8] standardised targets) and its
     gradient with respect to every parameter tensor (storage order)."""
@@ -250,22 +277,12 @@ def loss_and_grads(feat, x, params, K, rnd=round_bf16):
     layer_grads = [None] * K
     for l in range(K):              # the density pass applied K-1 .. 0, so 0 is undone first
         X, g1, g2, o, w = tape[l]
-        a, b = (list(t) for t in SPLITS[l % 4])
-        _, s = shift_logscale(o)
-        e = np.exp(-s)
-        Gb = G[:, b]
-        dmu = -Gb * e
-        ds = -Gb * w[:, b] + 1.0 / B
-        do = np.concatenate([dmu, ds * (1.0 - (s / S_MAX) ** 2)], axis=1)
+        do, Gu = coupling_backward(l, w, o, G, 1.0 / B)
         V1, e1, V2, e2, V3, e3 = layers[l]
         dg2, dV3, de3 = _dense_back(g2, V3, e3, do, False, rnd)
         dg1, dV2, de2 = _dense_back(g1, V2, e2, dg2, True, rnd)
         dX, dV1, de1 = _dense_back(X, V1, e1, dg1, True, rnd)
-        Gu = G.copy()
-        Gu[:, b] = Gb * e
-        Gu[:, a] += dX[:, 0:4]
-        dc += dX[:, 8:]
-        G = Gu
+        G, dc = input_backward(l, dX, Gu, dc)
         layer_grads[l] = [dV1, de1, dV2, de2, dV3, de3]
     W1, b1, W2, b2, W3, b3 = emb
     dh2, dW3, db3 = _dense_back(h2, W3, b3, dc, False, rnd)

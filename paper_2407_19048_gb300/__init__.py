@@ -440,3 +440,193 @@ def irfft(X, N, out=None):
     out = torch.empty(X.shape[:-1] + (N,), dtype=torch.float32, device=X.device) if out is None else out
     _check(_lib.load().gwx_irfft(_ptr(X), R, N, _ptr(out), _stream()))
     return out
+
+
+# ---------------------------------------------------------------- conditional coupling flow
+
+def flow_shape(features, group, embed_hidden, context, layers, hidden):
+    return _lib.GwxFlowShape(int(features), int(group), int(embed_hidden), int(context), int(layers), int(hidden))
+
+
+def _shape(shape):
+    if isinstance(shape, _lib.GwxFlowShape):
+        return shape
+    return flow_shape(shape["features"], shape["group"], shape["embed_hidden"], shape["context"], shape["layers"],
+                      shape["hidden"])
+
+
+def _host8(v):
+    return (ctypes.c_double * 8)(*[float(x) for x in v])
+
+
+def flow_layout(shape):
+    """(number of flat parameters, [offset of each tensor]) of a flow shape (see gwx.h)."""
+    sh = _shape(shape)
+    n = ctypes.c_int64(0)
+    off = (ctypes.c_int64 * (6 + 6 * sh.layers))()
+    _check(_lib.load().gwx_flow_layout(ctypes.byref(sh), ctypes.byref(n), off))
+    return n.value, list(off)
+
+
+def flow_targets(theta, mean8, scale8, out=None):
+    """float32 [B][8] standardised flow coordinates of theta [11][B]."""
+    torch = _torch()
+    _dev(theta, torch.float64, "theta")
+    B = theta.shape[1]
+    out = torch.empty((B, 8), dtype=torch.float32, device=theta.device) if out is None else out
+    _check(_lib.load().gwx_flow_targets(_ptr(theta), B, _host8(mean8), _host8(scale8), _ptr(out), _stream()))
+    return out
+
+
+def flow_conditioner_input(layer, v, ctx, event_offsets=None, row0=0, out=None):
+    """bfloat16 [B][8 + C] conditioner input rows of layer `layer`."""
+    torch = _torch()
+    _dev(v, torch.float32, "v")
+    _dev(ctx, torch.bfloat16, "ctx")
+    B = v.shape[0]
+    C = ctx.shape[1]
+    E = 0
+    if event_offsets is not None:
+        _dev(event_offsets, torch.int64, "event_offsets")
+        E = event_offsets.shape[0] - 1
+    out = torch.empty((B, 8 + C), dtype=torch.bfloat16, device=v.device) if out is None else out
+    _check(_lib.load().gwx_flow_conditioner_input(layer, _ptr(v), _ptr(ctx), C, _ptr(event_offsets), E, row0, B,
+                                                  _ptr(out), _stream()))
+    return out
+
+
+def flow_coupling(layer, direction, v_in, o, sum_s, init, v_out=None):
+    """One coupling step (direction +1 sampling, -1 density); returns v_out [B][8]."""
+    torch = _torch()
+    _dev(v_in, torch.float32, "v_in")
+    _dev(o, torch.float32, "o")
+    _dev(sum_s, torch.float32, "sum_s")
+    v_out = torch.empty_like(v_in) if v_out is None else v_out
+    _check(_lib.load().gwx_flow_coupling(layer, direction, _ptr(v_in), _ptr(o), v_in.shape[0], _ptr(v_out),
+                                         _ptr(sum_s), 1 if init else 0, _stream()))
+    return v_out
+
+
+def flow_nll(z, sum_s):
+    """(loss_rows [B] float32, loss_mean [1] float64, grad [B][8] = z / B)."""
+    torch = _torch()
+    _dev(z, torch.float32, "z")
+    _dev(sum_s, torch.float32, "sum_s")
+    B = z.shape[0]
+    rows = torch.empty(B, dtype=torch.float32, device=z.device)
+    mean = torch.empty(1, dtype=torch.float64, device=z.device)
+    grad = torch.empty_like(z)
+    _check(_lib.load().gwx_flow_nll(_ptr(z), _ptr(sum_s), B, _ptr(rows), _ptr(mean), _ptr(grad), _stream()))
+    return rows, mean, grad
+
+
+def flow_coupling_backward(layer, w, o, g, row_weight):
+    """(d_o [B][8], g_u [B][8]) of a density step (see gwx.h)."""
+    torch = _torch()
+    for t, n in ((w, "w"), (o, "o"), (g, "g")):
+        _dev(t, torch.float32, n)
+    d_o, g_u = torch.empty_like(o), torch.empty_like(g)
+    _check(_lib.load().gwx_flow_coupling_backward(layer, _ptr(w), _ptr(o), _ptr(g), w.shape[0], float(row_weight),
+                                                  _ptr(d_o), _ptr(g_u), _stream()))
+    return d_o, g_u
+
+
+def flow_input_backward(layer, dX, g_u, d_ctx, init):
+    """In place: g_u[:, a] += dX[:, 0:4]; d_ctx (=, or += unless init) dX[:, 8:]."""
+    torch = _torch()
+    for t, n in ((dX, "dX"), (g_u, "g_u"), (d_ctx, "d_ctx")):
+        _dev(t, torch.float32, n)
+    _check(_lib.load().gwx_flow_input_backward(layer, _ptr(dX), d_ctx.shape[1], dX.shape[0], _ptr(g_u), _ptr(d_ctx),
+                                               1 if init else 0, _stream()))
+
+
+def flow_base(seed, counter, row0, n):
+    """float32 [n][8] base normals of global draws row0 .. row0 + n - 1."""
+    torch = _torch()
+    z = torch.empty((n, 8), dtype=torch.float32, device=torch.device("cuda", torch.cuda.current_device()))
+    _check(_lib.load().gwx_flow_base(seed, counter, row0, n, _ptr(z), _stream()))
+    return z
+
+
+def flow_proposal(x, z, sum_s, mean8, scale8, prior, truth, event_offsets, seed, counter):
+    """(theta [11][S], log_q [S], log_ratio [S]) of flow draws x with base z and sum_s."""
+    torch = _torch()
+    _dev(x, torch.float32, "x")
+    _dev(z, torch.float32, "z")
+    _dev(sum_s, torch.float32, "sum_s")
+    _dev(truth, torch.float64, "truth")
+    _dev(event_offsets, torch.int64, "event_offsets")
+    S = x.shape[0]
+    E = event_offsets.shape[0] - 1
+    dev = x.device
+    theta = torch.empty((NPARAM, S), dtype=torch.float64, device=dev)
+    log_q, lr = (torch.empty(S, dtype=torch.float64, device=dev) for _ in range(2))
+    p = _prior(prior)
+    _check(_lib.load().gwx_flow_proposal(_ptr(x), _ptr(z), _ptr(sum_s), S, _host8(mean8), _host8(scale8),
+                                         ctypes.byref(p), _ptr(truth), E, _ptr(event_offsets), seed, counter,
+                                         _ptr(theta), _ptr(log_q), _ptr(lr), _stream()))
+    return theta, log_q, lr
+
+
+def flow_train_step(shape, params, params_bf16, grads, m, v, step, lr, mean8, scale8, y, theta, fs, f_lo,
+                    beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, loss_mean=None, workspace=None):
+    """One training step (step 0: loss and gradients only).  Returns loss_mean (device
+    float64 [1]).  `workspace` may be a preallocated (tensor, bytes) pair."""
+    torch = _torch()
+    sh = _shape(shape)
+    _dev(y, torch.float32, "y")
+    _dev(theta, torch.float64, "theta")
+    B, D, N = y.shape
+    lib = _lib.load()
+    loss_mean = torch.empty(1, dtype=torch.float64, device=y.device) if loss_mean is None else loss_mean
+    ws, nb = workspace if workspace is not None else _workspace(
+        lib.gwx_flow_train_workspace(ctypes.byref(sh), B, D, N), y.device)
+    _check(lib.gwx_flow_train_step(ctypes.byref(sh), _ptr(params), _ptr(params_bf16), _ptr(grads), _ptr(m), _ptr(v),
+                                   step, lr, beta1, beta2, eps, weight_decay, _host8(mean8), _host8(scale8), _ptr(y),
+                                   _ptr(theta), B, D, N, fs, f_lo, _ptr(loss_mean), _ptr(ws), nb, _stream()))
+    return loss_mean
+
+
+def flow_log_prob(shape, params, params_bf16, mean8, scale8, y, theta, fs, f_lo):
+    """float64 [B] ln q_r(r(theta_b) | y_b)."""
+    torch = _torch()
+    sh = _shape(shape)
+    _dev(y, torch.float32, "y")
+    _dev(theta, torch.float64, "theta")
+    B, D, N = y.shape
+    lib = _lib.load()
+    out = torch.empty(B, dtype=torch.float64, device=y.device)
+    ws, nb = _workspace(lib.gwx_flow_log_prob_workspace(ctypes.byref(sh), B, D, N), y.device)
+    _check(lib.gwx_flow_log_prob(ctypes.byref(sh), _ptr(params), _ptr(params_bf16), _host8(mean8), _host8(scale8),
+                                 _ptr(y), _ptr(theta), B, D, N, fs, f_lo, _ptr(out), _ptr(ws), nb, _stream()))
+    return out
+
+
+def sample_posterior(shape, params, params_bf16, mean8, scale8, prior, y, fs, f_lo, truth, event_offsets, seed,
+                     counter, out=None, workspace=None):
+    """Posterior draws for events y [E][D][N]: (theta [11][S], log_q [S], log_ratio [S])."""
+    torch = _torch()
+    sh = _shape(shape)
+    _dev(y, torch.float32, "y")
+    _dev(truth, torch.float64, "truth")
+    _dev(event_offsets, torch.int64, "event_offsets")
+    E, D, N = y.shape
+    S = int(event_offsets[-1].item())
+    dev = y.device
+    lib = _lib.load()
+    if out is None:
+        out = (torch.empty((NPARAM, S), dtype=torch.float64, device=dev),
+               torch.empty(S, dtype=torch.float64, device=dev), torch.empty(S, dtype=torch.float64, device=dev))
+    theta, log_q, lr = out
+    ws, nb = workspace if workspace is not None else _workspace(
+        lib.gwx_sample_posterior_workspace(ctypes.byref(sh), E, D, N, S), dev)
+    p = _prior(prior)
+    _check(lib.gwx_sample_posterior(ctypes.byref(sh), _ptr(params), _ptr(params_bf16), _host8(mean8), _host8(scale8),
+                                    ctypes.byref(p), _ptr(y), E, D, N, fs, f_lo, _ptr(truth), _ptr(event_offsets), S,
+                                    seed, counter, _ptr(theta), _ptr(log_q), _ptr(lr), _ptr(ws), nb, _stream()))
+    return theta, log_q, lr
+
+
+__all__ += ["flow_shape", "flow_layout", "flow_targets", "flow_conditioner_input", "flow_coupling", "flow_nll",
+            "flow_coupling_backward", "flow_input_backward", "flow_base", "flow_proposal", "flow_train_step",
+            "flow_log_prob", "sample_posterior"]

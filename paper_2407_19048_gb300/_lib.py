@@ -26,6 +26,15 @@ class GwxPrior(ctypes.Structure):
         "tc_lo", "tc_hi", "phi_lo", "phi_hi", "psi_lo", "psi_hi")]
 
 
+class GwxFlowShape(ctypes.Structure):
+    _fields_ = [(name, c_int) for name in ("features", "group", "embed_hidden", "context", "layers", "hidden")]
+
+
+c_shp = ctypes.POINTER(GwxFlowShape)
+c_d8 = ctypes.POINTER(c_dbl)
+c_pri = ctypes.POINTER(GwxPrior)
+c_f32 = ctypes.c_float
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "gwx_version": (c_int, []),
@@ -75,6 +84,26 @@ SIGNATURES = {
     "gwx_device_status": (c_int, []),
     "gwx_rfft": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp]),
     "gwx_irfft": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp]),
+    "gwx_flow_layout": (c_int, [c_shp, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),
+    "gwx_flow_targets": (c_int, [c_vp, c_i64, c_d8, c_d8, c_vp, c_vp]),
+    "gwx_flow_conditioner_input": (c_int, [c_int, c_vp, c_vp, c_int, c_vp, c_i64, c_i64, c_i64, c_vp, c_vp]),
+    "gwx_flow_coupling": (c_int, [c_int, c_int, c_vp, c_vp, c_i64, c_vp, c_vp, c_int, c_vp]),
+    "gwx_flow_nll": (c_int, [c_vp, c_vp, c_i64, c_vp, c_vp, c_vp, c_vp]),
+    "gwx_flow_coupling_backward": (c_int, [c_int, c_vp, c_vp, c_vp, c_i64, c_f32, c_vp, c_vp, c_vp]),
+    "gwx_flow_input_backward": (c_int, [c_int, c_vp, c_int, c_i64, c_vp, c_vp, c_int, c_vp]),
+    "gwx_flow_base": (c_int, [c_u64, c_u32, c_i64, c_i64, c_vp, c_vp]),
+    "gwx_flow_proposal": (c_int, [c_vp, c_vp, c_vp, c_i64, c_d8, c_d8, c_pri, c_vp, c_i64, c_vp, c_u64, c_u32, c_vp,
+                                  c_vp, c_vp, c_vp]),
+    "gwx_flow_train_workspace": (c_size, [c_shp, c_i64, c_int, c_i64]),
+    "gwx_flow_train_step": (c_int, [c_shp, c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl,
+                                    c_d8, c_d8, c_vp, c_vp, c_i64, c_int, c_i64, c_dbl, c_dbl, c_vp, c_vp, c_size,
+                                    c_vp]),
+    "gwx_flow_log_prob_workspace": (c_size, [c_shp, c_i64, c_int, c_i64]),
+    "gwx_flow_log_prob": (c_int, [c_shp, c_vp, c_vp, c_d8, c_d8, c_vp, c_vp, c_i64, c_int, c_i64, c_dbl, c_dbl, c_vp,
+                                  c_vp, c_size, c_vp]),
+    "gwx_sample_posterior_workspace": (c_size, [c_shp, c_i64, c_int, c_i64, c_i64]),
+    "gwx_sample_posterior": (c_int, [c_shp, c_vp, c_vp, c_d8, c_d8, c_pri, c_vp, c_i64, c_int, c_i64, c_dbl, c_dbl,
+                                     c_vp, c_vp, c_i64, c_u64, c_u32, c_vp, c_vp, c_vp, c_vp, c_size, c_vp]),
 }
 
 _lib = None

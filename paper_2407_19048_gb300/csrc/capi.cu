@@ -717,3 +717,280 @@ int gwx_irfft(const float* X, int64_t R, int64_t N, float* x, void* stream) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- conditional coupling flow
+namespace {
+
+#define GWX_ALIGN16(p)                                                                     \
+  do {                                                                                     \
+    if (((uintptr_t)(const void*)(p)) & 15u) return fail(GWX_EINVAL, "%s is not 16-byte aligned", #p); \
+  } while (0)
+
+int check_flow_shape(const gwx_flow_shape* sh) {
+  if (!sh) return fail(GWX_EINVAL, "flow shape is NULL");
+  const int64_t lim = (int64_t)65535 * 32;
+  const int w[4] = {sh->features, sh->embed_hidden, sh->context, sh->hidden};
+  for (int v : w)
+    if (v < 8 || v % 8 != 0 || v > lim)
+      return fail(GWX_ESHAPE, "flow widths F=%d H_e=%d C=%d H=%d must be multiples of 8 in [8, %lld]", sh->features,
+                  sh->embed_hidden, sh->context, sh->hidden, (long long)lim);
+  if (8 + (int64_t)sh->context > lim) return fail(GWX_ESHAPE, "context width %d", sh->context);
+  if (sh->layers < 1 || sh->layers > 64) return fail(GWX_ESHAPE, "layers=%d outside [1, 64]", sh->layers);
+  if (sh->group < 1) return fail(GWX_EINVAL, "group=%d", sh->group);
+  return GWX_OK;
+}
+
+int check_std8(const double* mean8, const double* scale8) {
+  if (!mean8 || !scale8) return fail(GWX_EINVAL, "mean and scale (host, 8 values each) are required");
+  for (int i = 0; i < 8; ++i)
+    if (!(scale8[i] > 0.0) || !isfinite(scale8[i]) || !isfinite(mean8[i]))
+      return fail(GWX_EINVAL, "bad mean or scale %d", i);
+  return GWX_OK;
+}
+
+int check_prior_box(const gwx_prior* p) {
+  if (!p) return fail(GWX_EINVAL, "prior is NULL");
+  if (!(p->m_lo > 0.0 && p->m_hi > p->m_lo && p->d_hi > p->d_lo && p->psi_hi > p->psi_lo && p->phi_hi > p->phi_lo))
+    return fail(GWX_EINVAL, "prior ranges must be non-empty with m_lo > 0");
+  return GWX_OK;
+}
+
+// Features of the flow's windows: band start and the number of groups must fit F.
+int check_flow_windows(const gwx_flow_shape* sh, int D, int64_t N, double fs, double f_lo, int* k_lo) {
+  GWX_TRY(check_window(N));
+  if (D < 1 || D > GWX_MAX_DET) return fail(GWX_ESHAPE, "D=%d", D);
+  if (!(fs > 0.0)) return fail(GWX_EINVAL, "fs must be positive");
+  GWX_TRY(band_start(f_lo, fs / (double)N, N / 2, k_lo));
+  if (sh->group > N / 2) return fail(GWX_EINVAL, "group %d", sh->group);
+  const int64_t ng = (N / 2 - *k_lo) / sh->group;
+  if (sh->features < D * ng)
+    return fail(GWX_ESHAPE, "F=%d is below D x groups = %lld", sh->features, (long long)(D * ng));
+  return GWX_OK;
+}
+
+int check_flow_params(const gwx_flow_shape* sh, const float* params, const void* params_bf16) {
+  if (!params || !params_bf16) return fail(GWX_EINVAL, "params and params_bf16 are required");
+  GWX_ALIGN16(params);
+  GWX_ALIGN16(params_bf16);
+  (void)sh;
+  return GWX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gwx_flow_layout(const gwx_flow_shape* shape, int64_t* n_params, int64_t* offsets) {
+  GWX_TRY(check_flow_shape(shape));
+  const int64_t n = flow_layout(*shape, offsets);
+  if (n_params) *n_params = n;
+  return GWX_OK;
+}
+
+int gwx_flow_targets(const double* theta, int64_t B, const double* mean8, const double* scale8, float* x,
+                     void* stream) {
+  if (B < 0 || B > ((int64_t)1 << 31)) return fail(GWX_ESHAPE, "B=%lld", (long long)B);
+  GWX_TRY(check_std8(mean8, scale8));
+  if (B == 0) return GWX_OK;
+  if (!theta || !x) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN8(theta);
+  GWX_ALIGN16(x);
+  GWX_TRY(ensure_init());
+  return launched(launch_flow_targets(theta, B, mean8, scale8, x, as_stream(stream)), "flow_targets");
+}
+
+int gwx_flow_conditioner_input(int layer, const float* v, const void* ctx, int C, const int64_t* event_offsets,
+                               int64_t E, int64_t row0, int64_t B, void* X, void* stream) {
+  if (layer < 0) return fail(GWX_EINVAL, "layer %d", layer);
+  if (C < 8 || C % 8 != 0) return fail(GWX_ESHAPE, "C=%d must be a positive multiple of 8", C);
+  if (B < 0 || B > ((int64_t)1 << 31) || row0 < 0 || (event_offsets && E < 1)) return fail(GWX_ESHAPE, "bad B, row0 or E");
+  if (B == 0) return GWX_OK;
+  if (!v || !ctx || !X) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN16(v);
+  GWX_ALIGN16(ctx);
+  GWX_ALIGN16(X);
+  if (event_offsets) GWX_ALIGN8(event_offsets);
+  GWX_TRY(ensure_init());
+  return launched(launch_flow_input(layer, v, ctx, C, event_offsets, E, row0, B, X, as_stream(stream)),
+                  "flow_conditioner_input");
+}
+
+int gwx_flow_coupling(int layer, int direction, const float* v_in, const float* o, int64_t B, float* v_out,
+                      float* sum_s, int init, void* stream) {
+  if (layer < 0 || (direction != 1 && direction != -1)) return fail(GWX_EINVAL, "layer %d direction %d", layer, direction);
+  if (B < 0 || B > ((int64_t)1 << 31)) return fail(GWX_ESHAPE, "B=%lld", (long long)B);
+  if (B == 0) return GWX_OK;
+  if (!v_in || !o || !v_out || !sum_s) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN16(v_in);
+  GWX_ALIGN16(o);
+  GWX_ALIGN16(v_out);
+  GWX_TRY(ensure_init());
+  return launched(launch_flow_coupling(layer, direction, v_in, o, B, v_out, sum_s, init ? 1 : 0, as_stream(stream)),
+                  "flow_coupling");
+}
+
+int gwx_flow_nll(const float* z, const float* sum_s, int64_t B, float* loss_rows, double* loss_mean, float* grad,
+                 void* stream) {
+  if (B < 1 || B > ((int64_t)1 << 31)) return fail(GWX_ESHAPE, "B=%lld", (long long)B);
+  if (!z || !sum_s || !loss_rows || !loss_mean || !grad) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN16(z);
+  GWX_ALIGN16(grad);
+  GWX_ALIGN8(loss_mean);
+  GWX_TRY(ensure_init());
+  return launched(launch_flow_nll(z, sum_s, B, loss_rows, loss_mean, grad, as_stream(stream)), "flow_nll");
+}
+
+int gwx_flow_coupling_backward(int layer, const float* w, const float* o, const float* g, int64_t B,
+                               float row_weight, float* d_o, float* g_u, void* stream) {
+  if (layer < 0) return fail(GWX_EINVAL, "layer %d", layer);
+  if (B < 0 || B > ((int64_t)1 << 31)) return fail(GWX_ESHAPE, "B=%lld", (long long)B);
+  if (B == 0) return GWX_OK;
+  if (!w || !o || !g || !d_o || !g_u) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN16(w);
+  GWX_ALIGN16(o);
+  GWX_ALIGN16(g);
+  GWX_ALIGN16(d_o);
+  GWX_ALIGN16(g_u);
+  GWX_TRY(ensure_init());
+  return launched(launch_flow_coupling_backward(layer, w, o, g, B, row_weight, d_o, g_u, as_stream(stream)),
+                  "flow_coupling_backward");
+}
+
+int gwx_flow_input_backward(int layer, const float* dX, int C, int64_t B, float* g_u, float* d_ctx, int init,
+                            void* stream) {
+  if (layer < 0) return fail(GWX_EINVAL, "layer %d", layer);
+  if (C < 8 || C % 8 != 0) return fail(GWX_ESHAPE, "C=%d must be a positive multiple of 8", C);
+  if (B < 0 || B > ((int64_t)1 << 31)) return fail(GWX_ESHAPE, "B=%lld", (long long)B);
+  if (B == 0) return GWX_OK;
+  if (!dX || !g_u || !d_ctx) return fail(GWX_EINVAL, "NULL array");
+  GWX_TRY(ensure_init());
+  return launched(launch_flow_input_backward(layer, dX, C, B, g_u, d_ctx, init ? 1 : 0, as_stream(stream)),
+                  "flow_input_backward");
+}
+
+int gwx_flow_base(uint64_t seed, uint32_t counter, int64_t row0, int64_t n, float* z, void* stream) {
+  if (n < 0 || row0 < 0 || row0 + n > ((int64_t)1 << 32)) return fail(GWX_ESHAPE, "draws outside [0, 2^32)");
+  if (n == 0) return GWX_OK;
+  if (!z) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN16(z);
+  GWX_TRY(ensure_init());
+  return launched(launch_flow_base(seed, counter, row0, n, z, as_stream(stream)), "flow_base");
+}
+
+int gwx_flow_proposal(const float* x, const float* z, const float* sum_s, int64_t S, const double* mean8,
+                      const double* scale8, const gwx_prior* prior, const double* truth, int64_t E,
+                      const int64_t* event_offsets, uint64_t seed, uint32_t counter, double* theta, double* log_q,
+                      double* log_ratio, void* stream) {
+  GWX_TRY(check_std8(mean8, scale8));
+  GWX_TRY(check_prior_box(prior));
+  if (S < 0 || S > ((int64_t)1 << 32) || E < 0 || (S > 0 && E == 0)) return fail(GWX_ESHAPE, "bad S or E");
+  if (S == 0) return GWX_OK;
+  if (!x || !z || !sum_s || !truth || !event_offsets || !theta || !log_q || !log_ratio)
+    return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN16(x);
+  GWX_ALIGN16(z);
+  GWX_ALIGN8(truth);
+  GWX_ALIGN8(event_offsets);
+  GWX_ALIGN8(theta);
+  GWX_ALIGN8(log_q);
+  GWX_ALIGN8(log_ratio);
+  GWX_TRY(ensure_init());
+  return launched(launch_flow_proposal(x, z, sum_s, S, 0, S, mean8, scale8, *prior, truth, E, event_offsets, seed,
+                                       counter, theta, log_q, log_ratio, as_stream(stream)),
+                  "flow_proposal");
+}
+
+size_t gwx_flow_train_workspace(const gwx_flow_shape* shape, int64_t B, int D, int64_t N) {
+  if (check_flow_shape(shape) != GWX_OK || B < 1 || D < 1 || N < 2) return 0;
+  return align_up(flow_train_ws(*shape, B, D, N));
+}
+
+int gwx_flow_train_step(const gwx_flow_shape* shape, float* params, void* params_bf16, float* grads, float* m,
+                        float* v, int64_t step, double lr, double beta1, double beta2, double eps,
+                        double weight_decay, const double* mean8, const double* scale8, const float* y,
+                        const double* theta, int64_t B, int D, int64_t N, double fs, double f_lo,
+                        double* loss_mean, void* workspace, size_t workspace_bytes, void* stream) {
+  GWX_TRY(check_flow_shape(shape));
+  GWX_TRY(check_std8(mean8, scale8));
+  int k_lo = 0;
+  GWX_TRY(check_flow_windows(shape, D, N, fs, f_lo, &k_lo));
+  const int64_t lim = (int64_t)65535 * 32;
+  if (B < 8 || B % 8 != 0 || B > lim) return fail(GWX_ESHAPE, "B=%lld must be a multiple of 8 in [8, %lld]",
+                                                  (long long)B, (long long)lim);
+  if (step < 0) return fail(GWX_EINVAL, "step %lld", (long long)step);
+  if (step >= 1 && (!(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0) || !(lr >= 0.0)))
+    return fail(GWX_EINVAL, "AdamW hyper-parameters");
+  GWX_TRY(check_flow_params(shape, params, params_bf16));
+  if (!grads || !y || !theta || !loss_mean || (step >= 1 && (!m || !v))) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN16(grads);
+  GWX_ALIGN8(y);
+  GWX_ALIGN8(theta);
+  GWX_ALIGN8(loss_mean);
+  GWX_TRY(check_ws(workspace, workspace_bytes, gwx_flow_train_workspace(shape, B, D, N)));
+  GWX_TRY(ensure_init());
+  return launched(flow_train_step(*shape, params, params_bf16, grads, m, v, step, lr, beta1, beta2, eps, weight_decay,
+                                  mean8, scale8, y, theta, B, D, N, k_lo, loss_mean, workspace, as_stream(stream)),
+                  "flow_train_step");
+}
+
+size_t gwx_flow_log_prob_workspace(const gwx_flow_shape* shape, int64_t B, int D, int64_t N) {
+  if (check_flow_shape(shape) != GWX_OK || B < 1 || D < 1 || N < 2) return 0;
+  return align_up(flow_log_prob_ws(*shape, B, D, N));
+}
+
+int gwx_flow_log_prob(const gwx_flow_shape* shape, const float* params, const void* params_bf16,
+                      const double* mean8, const double* scale8, const float* y, const double* theta, int64_t B,
+                      int D, int64_t N, double fs, double f_lo, double* log_q, void* workspace,
+                      size_t workspace_bytes, void* stream) {
+  GWX_TRY(check_flow_shape(shape));
+  GWX_TRY(check_std8(mean8, scale8));
+  int k_lo = 0;
+  GWX_TRY(check_flow_windows(shape, D, N, fs, f_lo, &k_lo));
+  if (B < 0 || B > ((int64_t)1 << 23)) return fail(GWX_ESHAPE, "B=%lld", (long long)B);
+  if (B == 0) return GWX_OK;
+  GWX_TRY(check_flow_params(shape, params, params_bf16));
+  if (!y || !theta || !log_q) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN8(y);
+  GWX_ALIGN8(theta);
+  GWX_ALIGN8(log_q);
+  GWX_TRY(check_ws(workspace, workspace_bytes, gwx_flow_log_prob_workspace(shape, B, D, N)));
+  GWX_TRY(ensure_init());
+  return launched(flow_log_prob(*shape, params, params_bf16, mean8, scale8, y, theta, B, D, N, k_lo, log_q, workspace,
+                                as_stream(stream)),
+                  "flow_log_prob");
+}
+
+size_t gwx_sample_posterior_workspace(const gwx_flow_shape* shape, int64_t E, int D, int64_t N, int64_t S) {
+  if (check_flow_shape(shape) != GWX_OK || E < 1 || D < 1 || N < 2 || S < 1) return 0;
+  return align_up(flow_sample_ws(*shape, E, D, N, S));
+}
+
+int gwx_sample_posterior(const gwx_flow_shape* shape, const float* params, const void* params_bf16,
+                         const double* mean8, const double* scale8, const gwx_prior* prior, const float* y,
+                         int64_t E, int D, int64_t N, double fs, double f_lo, const double* truth,
+                         const int64_t* event_offsets, int64_t S, uint64_t seed, uint32_t counter, double* theta,
+                         double* log_q, double* log_ratio, void* workspace, size_t workspace_bytes, void* stream) {
+  GWX_TRY(check_flow_shape(shape));
+  GWX_TRY(check_std8(mean8, scale8));
+  GWX_TRY(check_prior_box(prior));
+  int k_lo = 0;
+  GWX_TRY(check_flow_windows(shape, D, N, fs, f_lo, &k_lo));
+  if (E < 0 || E > ((int64_t)1 << 23) || S < 0 || S > ((int64_t)1 << 32) || (S > 0 && E == 0))
+    return fail(GWX_ESHAPE, "bad E or S");
+  if (S == 0) return GWX_OK;
+  GWX_TRY(check_flow_params(shape, params, params_bf16));
+  if (!y || !truth || !event_offsets || !theta || !log_q || !log_ratio) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN8(y);
+  GWX_ALIGN8(truth);
+  GWX_ALIGN8(event_offsets);
+  GWX_ALIGN8(theta);
+  GWX_ALIGN8(log_q);
+  GWX_ALIGN8(log_ratio);
+  GWX_TRY(check_ws(workspace, workspace_bytes, gwx_sample_posterior_workspace(shape, E, D, N, S)));
+  GWX_TRY(ensure_init());
+  return launched(flow_sample(*shape, params, params_bf16, mean8, scale8, *prior, y, E, D, N, k_lo, truth,
+                              event_offsets, S, seed, counter, theta, log_q, log_ratio, workspace, as_stream(stream)),
+                  "sample_posterior");
+}
+
+}  // extern "C"

@@ -105,6 +105,41 @@ cudaError_t launch_proposal(const float* net, int ldn, const double* mean, const
                             const double* truth, int64_t E, const int64_t* off, int64_t S, uint64_t seed,
                             uint32_t counter, int fix_angles, double* theta, double* lratio, cudaStream_t s);
 
+// Conditional coupling flow (k_flow.cu).  flow_layout returns the flat parameter count
+// and fills the 6 + 6K tensor offsets (when off is not NULL).
+int64_t flow_layout(const gwx_flow_shape& sh, int64_t* off);
+cudaError_t launch_flow_targets(const double* theta, int64_t B, const double* mean8, const double* scale8, float* x,
+                                cudaStream_t s);
+cudaError_t launch_flow_input(int l, const float* v, const void* ctx, int C, const int64_t* off, int64_t E,
+                              int64_t row0, int64_t B, void* X, cudaStream_t s);
+cudaError_t launch_flow_coupling(int l, int dir, const float* vin, const float* o, int64_t B, float* vout,
+                                 float* sum_s, int init, cudaStream_t s);
+cudaError_t launch_flow_nll(const float* z, const float* sum_s, int64_t B, float* loss, double* mean, float* grad,
+                            cudaStream_t s);
+cudaError_t launch_flow_coupling_backward(int l, const float* w, const float* o, const float* g, int64_t B,
+                                          float row_weight, float* d_o, float* g_u, cudaStream_t s);
+cudaError_t launch_flow_input_backward(int l, const float* dX, int C, int64_t B, float* g_u, float* d_ctx, int init,
+                                       cudaStream_t s);
+cudaError_t launch_flow_base(uint64_t seed, uint32_t counter, int64_t row0, int64_t n, float* z, cudaStream_t s);
+cudaError_t launch_flow_proposal(const float* x, const float* z, const float* sum_s, int64_t n, int64_t row0,
+                                 int64_t S, const double* mean8, const double* scale8, const gwx_prior& pr,
+                                 const double* truth, int64_t E, const int64_t* off, uint64_t seed, uint32_t counter,
+                                 double* theta, double* log_q, double* log_ratio, cudaStream_t s);
+size_t flow_train_ws(const gwx_flow_shape& sh, int64_t B, int D, int64_t N);
+cudaError_t flow_train_step(const gwx_flow_shape& sh, float* params, void* params_bf16, float* grads, float* m,
+                            float* v, int64_t step, double lr, double b1, double b2, double eps, double wd,
+                            const double* mean8, const double* scale8, const float* y, const double* theta, int64_t B,
+                            int D, int64_t N, int k_lo, double* loss_mean, void* ws, cudaStream_t s);
+size_t flow_log_prob_ws(const gwx_flow_shape& sh, int64_t B, int D, int64_t N);
+cudaError_t flow_log_prob(const gwx_flow_shape& sh, const float* params, const void* params_bf16, const double* mean8,
+                          const double* scale8, const float* y, const double* theta, int64_t B, int D, int64_t N,
+                          int k_lo, double* log_q, void* ws, cudaStream_t s);
+size_t flow_sample_ws(const gwx_flow_shape& sh, int64_t E, int D, int64_t N, int64_t S);
+cudaError_t flow_sample(const gwx_flow_shape& sh, const float* params, const void* params_bf16, const double* mean8,
+                        const double* scale8, const gwx_prior& pr, const float* y, int64_t E, int D, int64_t N,
+                        int k_lo, const double* truth, const int64_t* off, int64_t S, uint64_t seed, uint32_t counter,
+                        double* theta, double* log_q, double* log_ratio, void* ws, cudaStream_t s);
+
 // Record msg as the calling thread's gwx_last_error() message; returns status.
 int set_last_error(int status, const char* msg);
 

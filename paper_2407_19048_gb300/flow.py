@@ -1,0 +1,165 @@
+"""The conditional coupling flow as a trainable posterior estimator.
+
+Sec. 5 of the paper trains a normalizing flow q(theta | d) on the simulated batches by
+maximising ln q(theta_i | d_i) with AdamW, conditioned on a summary of the whitened
+strain (Sec. 4), and then draws posterior samples for new data; Sec. 6 judges those
+samples with the standard likelihood.  `FlowPosterior` holds the flow's parameters as
+one flat FP32 array with its bfloat16 copy and AdamW moments (the layout of
+`gwx_flow_layout`), and drives three library calls: `flow_train_step` (features,
+embedding, the K coupling layers in the density direction, loss, backward, AdamW: one
+C-ABI call), `sample_posterior` (draws with ln q and the prior-to-proposal log ratio
+for importance sampling) and `log_prob`.
+"""
+import math
+
+from . import _lib
+
+PARAM_ORDER = ("W1", "b1", "W2", "b2", "W3", "b3")
+
+
+class FlowPosterior:
+    def __init__(self, workload, layers=16, hidden=256, context=64, embed_hidden=512, group=4, seed=0,
+                 device=None, lr=1e-3, weight_decay=2e-3, max_batch=None):
+        import torch
+        import paper_2407_19048_gb300 as gwx
+        self.gwx = gwx
+        self.wl = dict(workload)
+        wl = self.wl
+        self.dev = device or torch.device("cuda", torch.cuda.current_device())
+        self.D, self.N, self.fs, self.f_lo = len(wl["dets"]), int(wl["N"]), float(wl["fs"]), float(wl["f_lo"])
+        k_lo = math.ceil(self.f_lo * self.N / self.fs - 1e-9)
+        ng = (self.N // 2 - k_lo) // group
+        F = ((self.D * ng + 7) // 8) * 8
+        self.shape = {"features": F, "group": group, "embed_hidden": embed_hidden, "context": context,
+                      "layers": layers, "hidden": hidden}
+        self.n_params, self.offsets = gwx.flow_layout(self.shape)
+        self.params = torch.zeros(self.n_params, dtype=torch.float32, device=self.dev)
+        self.params16 = torch.zeros(self.n_params, dtype=torch.bfloat16, device=self.dev)
+        self.grads = torch.zeros_like(self.params)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.lr, self.wd = float(lr), float(weight_decay)
+        self.steps = 0
+        self._ws = {}
+        self._loss = torch.zeros(1, dtype=torch.float64, device=self.dev)
+        self.init_random(seed)
+        # standardisation of the flow's coordinates from prior draws (computed by the library)
+        th, _ = gwx.sample_prior(wl["prior"], 12345, 0, 100000, wl["L"], self.N)
+        r = gwx.flow_targets(th, [0.0] * 8, [1.0] * 8).double()
+        self.mean = [float(x) for x in r.mean(dim=0).cpu()]
+        self.scale = [float(x) for x in r.std(dim=0).cpu()]
+
+    # ------------------------------------------------------------ parameters
+    def tensor_shapes(self):
+        sh = self.shape
+        F, He, C, H = sh["features"], sh["embed_hidden"], sh["context"], sh["hidden"]
+        out = [(He, F), (He,), (He, He), (He,), (C, He), (C,)]
+        for _ in range(sh["layers"]):
+            out += [(H, 8 + C), (H,), (H, H), (H,), (8, H), (8,)]
+        return out
+
+    def tensor(self, t, bf16=False):
+        """View of parameter tensor t (storage order) in the flat array."""
+        shape = self.tensor_shapes()[t]
+        n = 1
+        for s in shape:
+            n *= s
+        base = self.params16 if bf16 else self.params
+        return base[self.offsets[t]:self.offsets[t] + n].view(shape)
+
+    def set_tensors(self, arrays):
+        """Load parameter tensors (storage order; numpy or torch) and refresh the copy."""
+        import torch
+        for t, a in enumerate(arrays):
+            self.tensor(t).copy_(torch.as_tensor(a, dtype=torch.float32))
+        self.params16.copy_(self.params.to(torch.bfloat16))
+
+    def init_random(self, seed):
+        """Weights N(0, 1 / fan_in), the last layer of each conditioner scaled by 0.01 (the
+        flow starts near the identity), biases zero."""
+        import torch
+        g = torch.Generator(device=self.dev)
+        g.manual_seed(int(seed))
+        self.params.zero_()
+        for t, shape in enumerate(self.tensor_shapes()):
+            if len(shape) == 2:
+                gain = 0.01 if (t >= 6 and t % 6 == 4) else 1.0
+                w = torch.randn(shape, generator=g, device=self.dev) * (gain / math.sqrt(shape[1]))
+                self.tensor(t).copy_(w)
+        self.params16.copy_(self.params.to(torch.bfloat16))
+
+    def _workspace(self, key, nbytes):
+        import paper_2407_19048_gb300 as gwx
+        if key not in self._ws or self._ws[key][1] < nbytes:
+            self._ws[key] = gwx._workspace(nbytes, self.dev)
+        return self._ws[key]
+
+    # ------------------------------------------------------------ training and use
+    def train_step(self, y, theta, update=True):
+        """One AdamW step (or, with update False, the loss and gradients only) on a
+        simulated batch y [B][D][N] with parameters theta [11][B]; returns the batch-mean
+        loss as a device tensor (no host synchronisation)."""
+        import ctypes
+        gwx = self.gwx
+        B = y.shape[0]
+        sh = gwx._shape(self.shape)
+        nb = _lib.load().gwx_flow_train_workspace(ctypes.byref(sh), B, self.D, self.N)
+        ws = self._workspace(("train", B), nb)
+        step = self.steps + 1 if update else 0
+        gwx.flow_train_step(self.shape, self.params, self.params16, self.grads, self.m, self.v, step, self.lr,
+                            self.mean, self.scale, y, theta, self.fs, self.f_lo, weight_decay=self.wd,
+                            loss_mean=self._loss, workspace=ws)
+        if update:
+            self.steps += 1
+        return self._loss
+
+    def sample(self, y_events, truth, event_offsets, seed, counter):
+        """Posterior draws for events y_events [E][D][N] (spins and t_c from truth):
+        (theta [11][S], ln q_r [S], ln prior_r - ln q_r [S])."""
+        return self.gwx.sample_posterior(self.shape, self.params, self.params16, self.mean, self.scale,
+                                         self.wl["prior"], y_events, self.fs, self.f_lo, truth, event_offsets, seed,
+                                         counter)
+
+    def log_prob(self, y, theta):
+        return self.gwx.flow_log_prob(self.shape, self.params, self.params16, self.mean, self.scale, y, theta,
+                                      self.fs, self.f_lo)
+
+    # ------------------------------------------------------------ checkpoints
+    _MAGIC = b"GWXFLOW1"
+
+    def save(self, path, next_step=None):
+        """Flat binary checkpoint: magic, little-endian int64 header (6 shape fields, steps,
+        next_step, n_params), 16 float64 (mean, scale), then params, m and v as float32."""
+        import numpy as np
+        sh = self.shape
+        with open(path, "wb") as fh:
+            fh.write(self._MAGIC)
+            np.array([sh["features"], sh["group"], sh["embed_hidden"], sh["context"], sh["layers"], sh["hidden"],
+                      self.steps, -1 if next_step is None else next_step, self.n_params], dtype="<i8").tofile(fh)
+            np.array(self.mean + self.scale, dtype="<f8").tofile(fh)
+            for t in (self.params, self.m, self.v):
+                t.detach().cpu().numpy().astype("<f4").tofile(fh)
+
+    def load(self, path):
+        """Restore a checkpoint written by save() (same shape); returns the stored next
+        data-stream counter (None if none was stored)."""
+        import numpy as np
+        import torch
+        with open(path, "rb") as fh:
+            if fh.read(len(self._MAGIC)) != self._MAGIC:
+                raise ValueError("not a flow checkpoint: %s" % path)
+            hdr = [int(v) for v in np.fromfile(fh, dtype="<i8", count=9)]
+            sh = self.shape
+            want = [sh["features"], sh["group"], sh["embed_hidden"], sh["context"], sh["layers"], sh["hidden"]]
+            if hdr[:6] != want or hdr[8] != self.n_params:
+                raise ValueError("checkpoint shape %s differs from this flow %s" % (hdr[:6], want))
+            ms = np.fromfile(fh, dtype="<f8", count=16)
+            self.mean, self.scale = [float(v) for v in ms[:8]], [float(v) for v in ms[8:]]
+            for t in (self.params, self.m, self.v):
+                t.copy_(torch.from_numpy(np.fromfile(fh, dtype="<f4", count=self.n_params)))
+            self.params16.copy_(self.params.to(torch.bfloat16))
+            self.steps = hdr[6]
+        return None if hdr[7] < 0 else hdr[7]
+
+
+__all__ = ["FlowPosterior"]

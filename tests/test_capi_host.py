@@ -96,3 +96,39 @@ def test_validation_fails_before_any_launch(lib):
     assert st == -2
     with pytest.raises(KeyError):
         gwx.detector_geometry("K1")
+
+
+def test_flow_layout_and_validation(lib):
+    """The flow's flat parameter layout (host arithmetic) and its argument checks."""
+    import ctypes
+    import paper_2407_19048_gb300 as gwx
+    import workloads
+    shape = workloads.flow_shape(features=128, group=16, embed_hidden=64, context=32, layers=3, hidden=48)
+    n, off = gwx.flow_layout(shape)
+    sizes = [int(np.prod(s)) for s in workloads.flow_tensor_shapes(shape)]
+    assert len(off) == len(sizes) == 6 + 6 * 3
+    assert off[0] == 0 and all(o % 64 == 0 for o in off)
+    for t in range(len(off) - 1):
+        assert off[t + 1] - off[t] == (sizes[t] + 63) // 64 * 64
+    assert n == off[-1] + (sizes[-1] + 63) // 64 * 64
+    sh = gwx.flow_shape(128, 16, 64, 30, 3, 48)                     # context not a multiple of 8
+    assert lib.gwx_flow_layout(ctypes.byref(sh), None, None) == -2
+    sh = gwx.flow_shape(128, 16, 64, 32, 0, 48)                     # no layers
+    assert lib.gwx_flow_layout(ctypes.byref(sh), None, None) == -2
+    sh = gwx.flow_shape(128, 16, 64, 32, 3, 48)
+    assert lib.gwx_flow_train_workspace(ctypes.byref(sh), 64, 2, 2048) > 0
+    assert lib.gwx_sample_posterior_workspace(ctypes.byref(sh), 4, 2, 2048, 1000) > 0
+    m8 = (ctypes.c_double * 8)(*([0.0] * 8))
+    s8 = (ctypes.c_double * 8)(*([1.0] * 8))
+    # batch not a multiple of 8: rejected before any launch
+    st = lib.gwx_flow_train_step(ctypes.byref(sh), None, None, None, None, None, 1, 1e-3, 0.9, 0.999, 1e-8, 0.0, m8,
+                                 s8, None, None, 12, 2, 2048, 1024.0, 20.0, None, None, 0, None)
+    assert st == -2 and b"multiple of 8" in lib.gwx_last_error()
+    # too few feature columns for the band
+    sh_small = gwx.flow_shape(64, 16, 64, 32, 3, 48)
+    st = lib.gwx_flow_log_prob(ctypes.byref(sh_small), None, None, m8, s8, None, None, 8, 2, 2048, 1024.0, 20.0,
+                               None, None, 0, None)
+    assert st == -2 and b"groups" in lib.gwx_last_error()
+    bad = (ctypes.c_double * 8)(*([1.0] * 7 + [0.0]))
+    st = lib.gwx_flow_targets(None, 4, m8, bad, None, None)
+    assert st == -1 and b"scale" in lib.gwx_last_error()

@@ -1,0 +1,320 @@
+"""Parity of the conditional coupling flow (csrc/k_flow.cu, the orchestrated training
+step, density and posterior sampler) with oracle.flow (needs a GPU).
+
+Tolerances.  Stage kernels: FP32 arithmetic on the same FP32 inputs (1e-5 relative;
+the conditioner input rows are bfloat16 roundings of FP32 values, bit-exact; the
+proposal map works in FP64 from the same FP32 draws, 1e-9).  Whole-flow results: the
+oracle rounds to bfloat16 at the same points as the GPU but accumulates in FP64, so an
+activation that lies within an FP32 accumulation error of a bfloat16 rounding boundary
+can round the other way (one bfloat16 ulp, 2^-8 relative, in a handful of the ~10^5
+activations); through the remaining layers such a flip moves a shift or log-scale by
+~2^-8 / sqrt(H) of its size.  The bounds below (ln q within 2e-2 + 2e-3 |ln q|, draws
+within 1e-2 in standardised units, gradients within 5 % of each tensor's norm) sit
+above what the flips give and well below what a wrong term, sign or index gives (a
+changed split, sign of s or dropped sum_s term moves these quantities by O(1)).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import flow as fl
+from oracle import learn
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gwx():
+    import paper_2407_19048_gb300 as m
+    from paper_2407_19048_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "the gpu tests need a CUDA device"
+    m.init()
+    return m
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def bf16_bits(t):
+    return host(t.view(torch.int16)).view(np.uint16)
+
+
+WL = workloads.workload("small")
+GROUP = 16
+
+
+def _std():
+    th = workloads.random_theta(300, 5000, WL["prior"])
+    r = fl.coords(th)
+    return [float(v) for v in r.mean(axis=0)], [float(v) for v in r.std(axis=0)]
+
+
+MEAN, SCALE = _std()
+
+
+@pytest.fixture(scope="module")
+def model(gwx):
+    from paper_2407_19048_gb300.flow import FlowPosterior
+    fp = FlowPosterior(WL, layers=4, hidden=64, context=32, embed_hidden=64, group=GROUP, seed=1)
+    shape = workloads.flow_shape(features=fp.shape["features"], group=GROUP, embed_hidden=64, context=32, layers=4,
+                                 hidden=64)
+    params = workloads.random_flow_params(301, shape, gain=1.0, last_gain=0.5)
+    fp.set_tensors(params)
+    fp.mean, fp.scale = list(MEAN), list(SCALE)
+    return fp, params
+
+
+def oracle_features(y, F):
+    """bfloat16-rounded spectral features of windows y (the oracle's FP64 spectrum)."""
+    k_lo = int(math.ceil(WL["f_lo"] * WL["N"] / WL["fs"] - 1e-9))
+    return fl.round_bf16(learn.features(np.asarray(y, dtype=np.float64), k_lo, GROUP, F))
+
+
+# ---------------------------------------------------------------- stage kernels
+
+def test_layout(gwx, model):
+    fp, params = model
+    n, off = gwx.flow_layout(fp.shape)
+    assert all(o % 64 == 0 for o in off)
+    sizes = [int(np.prod(p.shape)) for p in params]
+    for t in range(len(off) - 1):
+        assert off[t] + sizes[t] <= off[t + 1]
+    assert off[-1] + sizes[-1] <= n
+
+
+def test_targets(gwx):
+    th = workloads.random_theta(302, 500, WL["prior"])
+    got = host(gwx.flow_targets(cuda(th), MEAN, SCALE)).astype(np.float64)
+    ref = fl.standardise(fl.coords(th), MEAN, SCALE)
+    np.testing.assert_allclose(got, ref, rtol=1e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("with_events", [False, True])
+def test_conditioner_input_bit_exact(gwx, with_events):
+    rng = np.random.default_rng(303)
+    B, C = 37, 32
+    v = rng.normal(0, 2, (B, 8)).astype(np.float32)
+    if with_events:
+        E = 5
+        ctx_bits = workloads.random_bf16_bits(304, (E, C))
+        offsets = np.array([0, 3, 3, 20, 30, B], dtype=np.int64)
+    else:
+        ctx_bits = workloads.random_bf16_bits(304, (B, C))
+        offsets = None
+    from oracle.gemm import bf16_to_f64, f64_to_bf16
+    c_rows = bf16_to_f64(ctx_bits)
+    if with_events:
+        c_rows = c_rows[fl.event_of(offsets, B)]
+    ctx = cuda(ctx_bits.view(np.int16)).view(torch.bfloat16)
+    for l in range(4):
+        X = gwx.flow_conditioner_input(l, cuda(v), ctx, None if offsets is None else cuda(offsets))
+        ref = f64_to_bf16(fl.conditioner_input(v.astype(np.float64), c_rows, l, fl.round_bf16))
+        assert np.array_equal(bf16_bits(X), ref)
+
+
+def test_coupling_both_directions(gwx):
+    rng = np.random.default_rng(305)
+    B = 1000
+    v = rng.normal(0, 1.5, (B, 8)).astype(np.float32)
+    o = rng.normal(0, 2.0, (B, 8)).astype(np.float32)
+    for l in range(4):
+        for direction in (+1, -1):
+            sum_s = cuda(np.full(B, 0.25, dtype=np.float32))
+            out = gwx.flow_coupling(l, direction, cuda(v), cuda(o), sum_s, init=False)
+            w_ref, ss_ref = fl.coupling(v.astype(np.float64), o.astype(np.float64), l, direction)
+            np.testing.assert_allclose(host(out), w_ref, rtol=2e-6, atol=2e-6)
+            np.testing.assert_allclose(host(sum_s), ss_ref + 0.25, rtol=1e-5, atol=1e-5)
+    # in place, init
+    vv = cuda(v)
+    sum_s = cuda(np.zeros(B, dtype=np.float32))
+    gwx.flow_coupling(2, -1, vv, cuda(o), sum_s, init=True, v_out=vv)
+    w_ref, ss_ref = fl.coupling(v.astype(np.float64), o.astype(np.float64), 2, -1)
+    np.testing.assert_allclose(host(vv), w_ref, rtol=2e-6, atol=2e-6)
+    np.testing.assert_allclose(host(sum_s), ss_ref, rtol=1e-5, atol=1e-5)
+
+
+def test_nll_and_backward_stages(gwx):
+    rng = np.random.default_rng(306)
+    B, C = 200, 16
+    z = rng.normal(0, 1, (B, 8)).astype(np.float32)
+    ss = rng.normal(0, 1, B).astype(np.float32)
+    rows, mean, grad = gwx.flow_nll(cuda(z), cuda(ss))
+    r_ref, m_ref = fl.nll(z.astype(np.float64), ss.astype(np.float64))
+    np.testing.assert_allclose(host(rows), r_ref, rtol=1e-5, atol=1e-5)
+    assert abs(host(mean)[0] - m_ref) <= 1e-6 * abs(m_ref) + 1e-6
+    np.testing.assert_allclose(host(grad), z / B, rtol=1e-6, atol=1e-9)
+    w = rng.normal(0, 1, (B, 8)).astype(np.float32)
+    o = rng.normal(0, 2, (B, 8)).astype(np.float32)
+    g = rng.normal(0, 1, (B, 8)).astype(np.float32)
+    dX = rng.normal(0, 1, (B, 8 + C)).astype(np.float32)
+    for l in range(4):
+        d_o, g_u = gwx.flow_coupling_backward(l, cuda(w), cuda(o), cuda(g), 1.0 / B)
+        do_ref, gu_ref = fl.coupling_backward(l, w.astype(np.float64), o.astype(np.float64), g.astype(np.float64),
+                                              np.float32(1.0 / B).astype(np.float64))
+        np.testing.assert_allclose(host(d_o), do_ref, rtol=1e-5, atol=1e-6)
+        np.testing.assert_allclose(host(g_u), gu_ref, rtol=1e-5, atol=1e-6)
+        dc0 = rng.normal(0, 1, (B, C)).astype(np.float32)
+        gu_t, dc_t = cuda(host(g_u).copy()), cuda(dc0)
+        gwx.flow_input_backward(l, cuda(dX), gu_t, dc_t, init=(l == 0))
+        gu2, dc2 = fl.input_backward(l, dX.astype(np.float64), host(g_u).astype(np.float64),
+                                     np.zeros((B, C)) if l == 0 else dc0.astype(np.float64))
+        np.testing.assert_allclose(host(gu_t), gu2, rtol=1e-6, atol=1e-6)
+        np.testing.assert_allclose(host(dc_t), dc2, rtol=1e-6, atol=1e-6)
+
+
+def test_base_normals(gwx):
+    z = host(gwx.flow_base(77, 5, 1000, 3000)).astype(np.float64)
+    ref, _ = fl.base_normals(77, 5, np.arange(1000, 4000))
+    np.testing.assert_allclose(z, ref, rtol=1e-6, atol=1e-6)
+
+
+def test_proposal_stage(gwx):
+    rng = np.random.default_rng(307)
+    S, E = 600, 4
+    offsets = np.array([0, 100, 100, 350, S], dtype=np.int64)
+    truth = workloads.random_theta(308, E, WL["prior"])
+    x = rng.normal(0, 1.2, (S, 8)).astype(np.float32)
+    z = rng.normal(0, 1, (S, 8)).astype(np.float32)
+    ss = rng.normal(0, 1, S).astype(np.float32)
+    th, lq, lr = gwx.flow_proposal(cuda(x), cuda(z), cuda(ss), MEAN, SCALE, WL["prior"], cuda(truth), cuda(offsets),
+                                   91, 3)
+    _, coin = fl.base_normals(91, 3, np.arange(S))
+    th_ref, lq_ref, lr_ref = fl.proposal_params(x.astype(np.float64), z.astype(np.float64), ss.astype(np.float64),
+                                                MEAN, SCALE, WL["prior"], truth, fl.event_of(offsets, S), coin)
+    th, lq, lr = host(th), host(lq), host(lr)
+    assert np.array_equal(np.isfinite(lr), np.isfinite(lr_ref))
+    assert 50 < np.isfinite(lr).sum() < S          # both branches exercised
+    np.testing.assert_allclose(th, th_ref, rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(lq, lq_ref, rtol=1e-9, atol=1e-9)
+    ok = np.isfinite(lr)
+    np.testing.assert_allclose(lr[ok], lr_ref[ok], rtol=1e-9, atol=1e-9)
+
+
+# ---------------------------------------------------------------- whole flow
+
+def _batch(seed, B):
+    y = workloads.random_strain(seed, (B, len(WL["dets"]), WL["N"]), 1.0).astype(np.float32)
+    th = workloads.random_theta(seed + 1, B, WL["prior"])
+    return y, th
+
+
+def test_log_prob(gwx, model):
+    fp, params = model
+    y, th = _batch(310, 48)
+    got = host(fp.log_prob(cuda(y), cuda(th)))
+    feat = oracle_features(y, fp.shape["features"])
+    ref = fl.log_prob(feat, th, params, 4, MEAN, SCALE)
+    assert np.all(np.abs(got - ref) <= 2e-2 + 2e-3 * np.abs(ref)), np.max(np.abs(got - ref))
+
+
+def test_train_step_loss_and_gradients(gwx, model):
+    fp, params = model
+    y, th = _batch(320, 64)
+    loss = host(fp.train_step(cuda(y), cuda(th), update=False))[0]
+    feat = oracle_features(y, fp.shape["features"])
+    x = fl.standardise(fl.coords(th), MEAN, SCALE)
+    m_ref, _, g_ref = fl.loss_and_grads(feat, x, params, 4)
+    assert abs(loss - m_ref) <= 2e-2 + 2e-3 * abs(m_ref), (loss, m_ref)
+    for t in range(len(params)):
+        g = host(fp.grads[fp.offsets[t]:fp.offsets[t] + params[t].size]).reshape(params[t].shape)
+        err = np.linalg.norm(g - g_ref[t])
+        assert err <= 0.05 * np.linalg.norm(g_ref[t]) + 1e-6, (t, err, np.linalg.norm(g_ref[t]))
+
+
+def test_sample_posterior(gwx, model):
+    fp, params = model
+    E = 4
+    y, truth = _batch(330, E)
+    offsets = np.array([0, 150, 150, 400, 700], dtype=np.int64)
+    th, lq, lr = fp.sample(cuda(y), cuda(truth), cuda(offsets), 2024, 9)
+    th, lq, lr = host(th), host(lq), host(lr)
+    feat = oracle_features(y, fp.shape["features"])
+    th_ref, lq_ref, lr_ref = fl.sample_posterior(feat, params, 4, MEAN, SCALE, WL["prior"], truth, offsets, 2024, 9)
+    both = np.isfinite(lr) & np.isfinite(lr_ref)
+    assert both.sum() >= 0.95 * min(np.isfinite(lr).sum(), np.isfinite(lr_ref).sum())
+    assert np.mean(np.isfinite(lr) != np.isfinite(lr_ref)) < 0.01
+    assert np.all(np.abs(lq - lq_ref) <= 2e-2 + 2e-3 * np.abs(lq_ref))
+    x = fl.standardise(fl.coords(th[:, both]), MEAN, SCALE)
+    x_ref = fl.standardise(fl.coords(th_ref[:, both]), MEAN, SCALE)
+    assert np.max(np.abs(x - x_ref)) < 1e-2
+    for r in (2, 3, 5):
+        assert np.array_equal(th[r], th_ref[r])
+
+
+def test_sample_then_density_round_trip(gwx, model):
+    fp, _ = model
+    E = 3
+    y, truth = _batch(340, E)
+    offsets = np.array([0, 300, 600, 900], dtype=np.int64)
+    th, lq, lr = fp.sample(cuda(y), cuda(truth), cuda(offsets), 5, 1)
+    ev = fl.event_of(offsets, 900)
+    ok = np.isfinite(host(lr))
+    lp = host(fp.log_prob(cuda(y[ev][ok]), th[:, torch.from_numpy(ok).cuda()].contiguous()))
+    assert np.all(np.abs(lp - host(lq)[ok]) <= 1e-2 + 1e-3 * np.abs(lp))
+
+
+def test_sample_posterior_across_chunks(gwx, model):
+    fp, params = model
+    E = 2
+    y, truth = _batch(350, E)
+    S = (1 << 17) + 3000
+    offsets = np.array([0, 70000, S], dtype=np.int64)
+    th, lq, lr = fp.sample(cuda(y), cuda(truth), cuda(offsets), 8, 2)
+    pick = np.r_[0:5, 69998:70003, (1 << 17) - 3:(1 << 17) + 3, S - 4:S]
+    feat = oracle_features(y, fp.shape["features"])
+    emb, layers = fl.split_params(params, 4)
+    c, _ = fl.embed(feat, emb)
+    ev = fl.event_of(offsets, S)[pick]
+    z, coin = fl.base_normals(8, 2, pick)
+    x, ss = fl.sample(z, c[ev], layers)
+    _, lq_ref, _ = fl.proposal_params(x, z, ss, MEAN, SCALE, WL["prior"], truth, ev, coin)
+    assert np.all(np.abs(host(lq)[pick] - lq_ref) <= 2e-2 + 2e-3 * np.abs(lq_ref))
+
+
+def test_training_lowers_the_loss(gwx):
+    from paper_2407_19048_gb300.flow import FlowPosterior
+    from paper_2407_19048_gb300.simulator import Simulator
+    sim = Simulator(WL)
+    fp = FlowPosterior(WL, layers=4, hidden=64, context=32, embed_hidden=64, group=GROUP, seed=3, lr=2e-3)
+    first, last = [], []
+    for step in range(300):
+        y, theta, _ = sim.step(step)
+        loss = fp.train_step(y, theta)
+        if step < 20:
+            first.append(float(host(loss)[0]))
+        if step >= 280:
+            last.append(float(host(loss)[0]))
+    assert np.mean(last) < np.mean(first) - 0.5, (np.mean(first), np.mean(last))
+
+
+def test_checkpoint_resume_is_bit_exact(gwx, tmp_path):
+    from paper_2407_19048_gb300.flow import FlowPosterior
+    from paper_2407_19048_gb300.simulator import Simulator
+    sim = Simulator(WL)
+    kw = dict(layers=2, hidden=32, context=16, embed_hidden=32, group=GROUP)
+    a = FlowPosterior(WL, seed=4, **kw)
+    for step in range(5):
+        y, theta, _ = sim.step(step)
+        a.train_step(y, theta)
+    path = str(tmp_path / "flow.ckpt")
+    a.save(path, next_step=5)
+    for step in range(5, 10):
+        y, theta, _ = sim.step(step)
+        a.train_step(y, theta)
+    b = FlowPosterior(WL, seed=99, **kw)
+    nxt = b.load(path)
+    assert nxt == 5
+    for step in range(nxt, 10):
+        y, theta, _ = sim.step(step)
+        b.train_step(y, theta)
+    assert torch.equal(a.params, b.params) and torch.equal(a.m, b.m) and b.steps == a.steps
