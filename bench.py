@@ -408,6 +408,109 @@ def learned_leg(gwx, torch, rank, steps=2000, events=32, per_event=4000):
                     "merger time known in both proposals"}
 
 
+def flow_leg(gwx, torch, rank, steps=2000, events=32, per_event=4000, pp_events=200, pp_samples=500):
+    """The conditional coupling flow (16 affine coupling layers, conditioners 72 -> 256 ->
+    256 -> 8, embedding 496 -> 512 -> 512 -> 64 on spectral features; tcgen05 dense layers)
+    trained with AdamW on 512-draw batches of the two-detector workload (one C-ABI call
+    per step); then posterior sampling (20,000 draws of one event, the paper's inference
+    size), importance sampling of 32 events x 4000 draws against the prior as proposal
+    (spins and merger time known to both), and a PP test of the flow's marginals."""
+    import math
+    import numpy as np
+    import paper_2407_19048_gb300.simulator  # noqa: F401
+    from paper_2407_19048_gb300.flow import FlowPosterior
+    wl = workloads.workload("small", B=512)
+    sim = gwx.simulator.Simulator(wl, pipeline=True, background_every=16)
+    fp = FlowPosterior(wl, layers=16, hidden=256, context=64, embed_hidden=512, group=4, seed=0, lr=1e-3,
+                       weight_decay=2e-3)
+    losses = []
+    y, th, _ = sim.step(step_counter(rank, 40000))
+    fp.train_step(y, th, update=False)          # workspace allocation outside the timing
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(steps):
+        y, th, _ = sim.step(step_counter(rank, 40001 + i))
+        loss = fp.train_step(y, th)
+        if i in (0, steps // 4, steps // 2, 3 * steps // 4, steps - 1):
+            losses.append((i, loss.clone()))
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    losses = [(i, float(l.item())) for i, l in losses]
+    # training step alone (no simulation) on one resident batch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    y1, th1 = y.clone(), th.clone()
+    fp_t = FlowPosterior(wl, layers=16, hidden=256, context=64, embed_hidden=512, group=4, seed=1)
+    for _ in range(3):
+        fp_t.train_step(y1, th1)
+    ev0.record()
+    for _ in range(50):
+        fp_t.train_step(y1, th1)
+    ev1.record()
+    torch.cuda.synchronize()
+    step_ms = ev0.elapsed_time(ev1) / 50
+    # posterior sampling latency: 20,000 draws for one event
+    wl_ev = dict(workloads.workload("small", B=events), param_seed=777)
+    sim_ev = gwx.simulator.Simulator(wl_ev)
+    y_ev, th_ev, _ = sim_ev.step(step_counter(rank, 0))
+    y_ev, th_ev = y_ev.clone(), th_ev.clone()
+    one = torch.tensor([0, 20000], dtype=torch.int64, device="cuda")
+    lat = []
+    for rep in range(23):
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        fp.sample(y_ev[:1].contiguous(), th_ev[:, :1].contiguous(), one, 11, rep)
+        torch.cuda.synchronize()
+        if rep >= 3:
+            lat.append(time.perf_counter() - a)
+    lat.sort()
+    # importance sampling: flow vs prior, same events and likelihood
+    offs = torch.arange(events + 1, dtype=torch.int64, device="cuda") * per_event
+    res = {}
+    for learned in (False, True):
+        best = None
+        for rep in range(3):
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            if learned:
+                theta, _, lrat = fp.sample(y_ev, th_ev, offs, 5, rep)
+            else:
+                theta, lrat = gwx.sample_proposal(wl_ev["prior"], th_ev, offs, 5, rep)
+            lnl = gwx.log_likelihood(y_ev, sim_ev.psd, wl_ev["seg_len"], wl_ev["fs"], wl_ev["f_lo"], wl_ev["dets"],
+                                     0.0, theta, offs)
+            _, ess, eff, _ = gwx.importance_weights(lnl, offs, lrat)
+            e = float(ess.sum().item())
+            dt = time.perf_counter() - a
+            best = dt if best is None else min(best, dt)
+        res["flow" if learned else "prior"] = {"ess_total": e, "ess_median": float(ess.median().item()),
+                                               "efficiency_median": float(eff.median().item()),
+                                               "ess_per_s": e / best, "chain_ms": best * 1e3}
+    # PP test: percentile of each truth among its event's flow draws, per flow coordinate
+    wl_pp = dict(workloads.workload("small", B=pp_events), param_seed=779)
+    sim_pp = gwx.simulator.Simulator(wl_pp)
+    y_pp, th_pp, _ = sim_pp.step(step_counter(rank, 2))
+    offs_pp = torch.arange(pp_events + 1, dtype=torch.int64, device="cuda") * pp_samples
+    theta_s, _, lr_s = fp.sample(y_pp, th_pp, offs_pp, 13, 0)
+    xs = gwx.flow_targets(theta_s, fp.mean, fp.scale).cpu().numpy().reshape(pp_events, pp_samples, 8)
+    ok = np.isfinite(lr_s.cpu().numpy()).reshape(pp_events, pp_samples)
+    xt = gwx.flow_targets(th_pp, fp.mean, fp.scale).cpu().numpy()
+    ks = []
+    for p in range(8):
+        pct = np.array([np.mean(xs[e, ok[e], p] < xt[e, p]) if ok[e].any() else 0.5 for e in range(pp_events)])
+        u = np.sort(pct)
+        n = len(u)
+        ks.append(float(max(np.max(np.arange(1, n + 1) / n - u), np.max(u - np.arange(n) / n))))
+    del sim, sim_ev, sim_pp
+    return {"shape": fp.shape, "params": fp.n_params, "train_steps": steps, "batch": 512, "train_s": train_s,
+            "simulations_per_s": steps * 512 / train_s, "train_step_ms": step_ms, "loss": losses,
+            "sample_20000_ms": {"p50": lat[len(lat) // 2] * 1e3, "min": lat[0] * 1e3, "max": lat[-1] * 1e3},
+            "events": events, "samples_per_event": per_event, "importance_sampling": res,
+            "pp_test": {"events": pp_events, "draws_per_event": pp_samples, "ks_distance": ks,
+                        "ks_95pct_critical": 1.36 / math.sqrt(pp_events),
+                        "coords": ["Mc", "q", "D_L", "cos theta_JN", "RA", "sin dec", "psi", "phic"]},
+            "note": "loss = batch mean of -ln q_x(x) in standardised coordinates; spins and merger time known to "
+                    "both proposals in the importance-sampling comparison"}
+
+
 def cufft_leg(gwx, torch, sim, wl, fused_ms):
     """The shared-memory FFT kernels against cuFFT (called through torch.fft) on the
     batch's shape, B x D rows of N real samples.  cuFFT is a timing baseline here only:
@@ -575,6 +678,7 @@ def run_gpu(args, wl):
     serve = serving_leg(gwx, torch, rank)
     gemm = gemm_leg(gwx, torch)
     learned = learned_leg(gwx, torch, rank)
+    flow = flow_leg(gwx, torch, rank)
 
     sim_avg_s = statistics.mean(sim_ms) * 1e-3
     flops = flops_per_injection(wl) * B
@@ -626,6 +730,7 @@ def run_gpu(args, wl):
             "serving": serve,
             "gemm_bf16": gemm,
             "learned_proposal": learned,
+            "flow": flow,
             "wall_s_timed_region": t_wall,
         }
         print(json.dumps(line), flush=True)
@@ -651,6 +756,8 @@ def main(argv=None):
                     help="run only the log-likelihood leg with U{LO..HI} samples per event; for profiling")
     ap.add_argument("--only-gemm", default=None, metavar="M,N,K",
                     help="run only the bfloat16 product leg at this shape; for profiling")
+    ap.add_argument("--only-flow", default=None, metavar="STEPS",
+                    help="run only the coupling-flow leg with this many training steps; for profiling")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -665,6 +772,13 @@ def main(argv=None):
         gwx.init()
         shape = tuple(int(v) for v in args.only_gemm.split(","))
         print(json.dumps({"gemm_bf16": gemm_leg(gwx, torch, shape)}), flush=True)
+        return 0
+    if args.only_flow:
+        import torch
+        import paper_2407_19048_gb300 as gwx
+        import paper_2407_19048_gb300.simulator  # noqa: F401
+        gwx.init()
+        print(json.dumps({"flow": flow_leg(gwx, torch, 0, steps=int(args.only_flow))}), flush=True)
         return 0
     if args.only_loglike:
         import torch

@@ -9,6 +9,11 @@ network of spectral features of the whitened strain.  This module states, in FP6
 
 * features  -- log of the mean power |Y_k|^2 / N of the whitened strain's rfft over
   groups of G consecutive bins from k_lo, per detector, zero-padded to F_pad columns;
+* cross_features -- per detector pair (d1 < d2) and group, the normalised cross spectrum
+  rho = sum_k Y_d1,k conj(Y_d2,k) / sqrt(sum_k |Y_d1,k|^2 sum_k |Y_d2,k|^2) (real and
+  imaginary parts): unchanged by a common time shift of all detectors (the shift's phase
+  factor cancels in the product), so it carries the inter-detector delay and amplitude
+  ratio that localise the source without the arrival time;
 * targets   -- (Mc, M, D) of each draw, standardised by given means and scales;
 * gauss_nll -- per-row negative log-density of standardised targets t under
   N(mu, exp(s)^2) (without the constant): sum_p [ (t_p - mu_p)^2 e^{-2 s_p} / 2 + s_p ],
@@ -43,6 +48,31 @@ def features(y, k_lo, G, F_pad):
         for g in range(ng):
             k = k_lo + g * G
             out[:, d * ng + g] = np.log(P[:, d, k:k + G].mean(axis=-1))
+    return out
+
+
+def detector_pairs(D):
+    return [(a, b) for a in range(D) for b in range(a + 1, D)]
+
+
+def cross_features(y, k_lo, G):
+    """[B][2 P ng] normalised cross spectra of whitened windows y [B][D][N]: for pair p
+    (detector_pairs order) and group g, column 2 p ng + g holds Re rho, (2 p + 1) ng + g
+    holds Im rho."""
+    y = np.asarray(y, dtype=np.float64)
+    B, D, N = y.shape
+    Y = np.fft.rfft(y, axis=-1)
+    ng = (N // 2 - k_lo) // G
+    pairs = detector_pairs(D)
+    out = np.zeros((B, 2 * len(pairs) * ng))
+    for p, (a, b) in enumerate(pairs):
+        for g in range(ng):
+            k = k_lo + g * G
+            ya, yb = Y[:, a, k:k + G], Y[:, b, k:k + G]
+            rho = np.sum(ya * np.conj(yb), axis=-1) / np.sqrt(np.sum(np.abs(ya) ** 2, axis=-1) *
+                                                             np.sum(np.abs(yb) ** 2, axis=-1))
+            out[:, 2 * p * ng + g] = rho.real
+            out[:, (2 * p + 1) * ng + g] = rho.imag
     return out
 
 

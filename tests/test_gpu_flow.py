@@ -8,10 +8,12 @@ oracle rounds to bfloat16 at the same points as the GPU but accumulates in FP64,
 activation that lies within an FP32 accumulation error of a bfloat16 rounding boundary
 can round the other way (one bfloat16 ulp, 2^-8 relative, in a handful of the ~10^5
 activations); through the remaining layers such a flip moves a shift or log-scale by
-~2^-8 / sqrt(H) of its size.  The bounds below (ln q within 2e-2 + 2e-3 |ln q|, draws
-within 1e-2 in standardised units, gradients within 5 % of each tensor's norm) sit
-above what the flips give and well below what a wrong term, sign or index gives (a
-changed split, sign of s or dropped sum_s term moves these quantities by O(1)).
+~2^-8 / sqrt(H) of its size.  Measured on a GB300 at these shapes: |d ln q| <= 1.2e-3
+(density), <= 6e-5 (draws), draws within 7e-5 in standardised units, gradients within
+2.5e-4 of each tensor's norm.  The bounds below (ln q within 5e-3 + 5e-4 |ln q|, draws
+within 1e-3, gradients within 1 % of each tensor's norm) leave room for other flips and
+stay far below what a wrong term, sign or index gives (a changed split, sign of s or
+dropped sum_s term moves these quantities by O(1)).
 """
 import math
 
@@ -214,7 +216,7 @@ def test_log_prob(gwx, model):
     got = host(fp.log_prob(cuda(y), cuda(th)))
     feat = oracle_features(y, fp.shape["features"])
     ref = fl.log_prob(feat, th, params, 4, MEAN, SCALE)
-    assert np.all(np.abs(got - ref) <= 2e-2 + 2e-3 * np.abs(ref)), np.max(np.abs(got - ref))
+    assert np.all(np.abs(got - ref) <= 5e-3 + 5e-4 * np.abs(ref)), np.max(np.abs(got - ref))
 
 
 def test_train_step_loss_and_gradients(gwx, model):
@@ -224,11 +226,11 @@ def test_train_step_loss_and_gradients(gwx, model):
     feat = oracle_features(y, fp.shape["features"])
     x = fl.standardise(fl.coords(th), MEAN, SCALE)
     m_ref, _, g_ref = fl.loss_and_grads(feat, x, params, 4)
-    assert abs(loss - m_ref) <= 2e-2 + 2e-3 * abs(m_ref), (loss, m_ref)
+    assert abs(loss - m_ref) <= 1e-3 + 1e-4 * abs(m_ref), (loss, m_ref)
     for t in range(len(params)):
         g = host(fp.grads[fp.offsets[t]:fp.offsets[t] + params[t].size]).reshape(params[t].shape)
         err = np.linalg.norm(g - g_ref[t])
-        assert err <= 0.05 * np.linalg.norm(g_ref[t]) + 1e-6, (t, err, np.linalg.norm(g_ref[t]))
+        assert err <= 0.01 * np.linalg.norm(g_ref[t]) + 1e-6, (t, err, np.linalg.norm(g_ref[t]))
 
 
 def test_sample_posterior(gwx, model):
@@ -243,10 +245,10 @@ def test_sample_posterior(gwx, model):
     both = np.isfinite(lr) & np.isfinite(lr_ref)
     assert both.sum() >= 0.95 * min(np.isfinite(lr).sum(), np.isfinite(lr_ref).sum())
     assert np.mean(np.isfinite(lr) != np.isfinite(lr_ref)) < 0.01
-    assert np.all(np.abs(lq - lq_ref) <= 2e-2 + 2e-3 * np.abs(lq_ref))
+    assert np.all(np.abs(lq - lq_ref) <= 5e-3 + 5e-4 * np.abs(lq_ref))
     x = fl.standardise(fl.coords(th[:, both]), MEAN, SCALE)
     x_ref = fl.standardise(fl.coords(th_ref[:, both]), MEAN, SCALE)
-    assert np.max(np.abs(x - x_ref)) < 1e-2
+    assert np.max(np.abs(x - x_ref)) < 1e-3
     for r in (2, 3, 5):
         assert np.array_equal(th[r], th_ref[r])
 
@@ -278,7 +280,7 @@ def test_sample_posterior_across_chunks(gwx, model):
     z, coin = fl.base_normals(8, 2, pick)
     x, ss = fl.sample(z, c[ev], layers)
     _, lq_ref, _ = fl.proposal_params(x, z, ss, MEAN, SCALE, WL["prior"], truth, ev, coin)
-    assert np.all(np.abs(host(lq)[pick] - lq_ref) <= 2e-2 + 2e-3 * np.abs(lq_ref))
+    assert np.all(np.abs(host(lq)[pick] - lq_ref) <= 5e-3 + 5e-4 * np.abs(lq_ref))
 
 
 def test_training_lowers_the_loss(gwx):

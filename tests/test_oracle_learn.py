@@ -133,3 +133,48 @@ def test_sample_proposal_normals():
     for z in (z0, z1):
         assert abs(z.mean()) < 0.03 and abs(z.var() - 1.0) < 0.04
     assert abs(np.mean(z0 * z1)) < 0.03
+
+
+def test_cross_features_brute_force_and_invariances():
+    rng = np.random.default_rng(61)
+    B, D, N, k_lo, G = 3, 3, 64, 3, 4
+    y = rng.normal(size=(B, D, N))
+    got = learn.cross_features(y, k_lo, G)
+    # brute-force DFT
+    n = np.arange(N)
+    Y = np.array([[[np.sum(y[b, d] * np.exp(-2j * np.pi * k * n / N)) for k in range(N // 2 + 1)]
+                   for d in range(D)] for b in range(B)])
+    ng = (N // 2 - k_lo) // G
+    pairs = learn.detector_pairs(D)
+    assert pairs == [(0, 1), (0, 2), (1, 2)]
+    for p, (a, c) in enumerate(pairs):
+        for g in range(ng):
+            ks = range(k_lo + g * G, k_lo + (g + 1) * G)
+            num = sum(Y[:, a, k] * np.conj(Y[:, c, k]) for k in ks)
+            den = np.sqrt(sum(abs(Y[:, a, k]) ** 2 for k in ks) * sum(abs(Y[:, c, k]) ** 2 for k in ks))
+            np.testing.assert_allclose(got[:, 2 * p * ng + g], (num / den).real, atol=1e-12)
+            np.testing.assert_allclose(got[:, (2 * p + 1) * ng + g], (num / den).imag, atol=1e-12)
+    # Cauchy-Schwarz
+    for p in range(len(pairs)):
+        re, im = got[:, 2 * p * ng:(2 * p + 1) * ng], got[:, (2 * p + 1) * ng:(2 * p + 2) * ng]
+        assert np.all(re * re + im * im <= 1.0 + 1e-12)
+    # a common circular shift of every detector leaves the features unchanged
+    np.testing.assert_allclose(learn.cross_features(np.roll(y, 7, axis=-1), k_lo, G), got, atol=1e-12)
+    # identical channels are fully coherent
+    same = np.repeat(y[:, :1], 2, axis=1)
+    f = learn.cross_features(same, k_lo, G)
+    np.testing.assert_allclose(f[:, :ng], 1.0, atol=1e-12)
+    np.testing.assert_allclose(f[:, ng:], 0.0, atol=1e-12)
+
+
+def test_cross_features_phase_of_a_delayed_tone():
+    N, k0, tau, k_lo, G = 256, 37, 5, 20, 4
+    n = np.arange(N)
+    x = np.cos(2 * np.pi * k0 * n / N)
+    y = np.stack([x, np.roll(x, tau)])[None]          # detector 1 lags detector 0 by tau samples
+    f = learn.cross_features(y, k_lo, G)
+    ng = (N // 2 - k_lo) // G
+    g = (k0 - k_lo) // G
+    # Y1 = Y0 e^{-2 pi i k tau / N}, so rho = e^{+2 pi i k0 tau / N}
+    assert abs(f[0, g] - np.cos(2 * np.pi * k0 * tau / N)) < 1e-9
+    assert abs(f[0, ng + g] - np.sin(2 * np.pi * k0 * tau / N)) < 1e-9
