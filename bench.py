@@ -408,21 +408,23 @@ def learned_leg(gwx, torch, rank, steps=2000, events=32, per_event=4000):
                     "merger time known in both proposals"}
 
 
-def flow_leg(gwx, torch, rank, steps=2000, events=32, per_event=4000, pp_events=200, pp_samples=500):
+def flow_leg(gwx, torch, rank, steps=6000, events=32, per_event=4000, pp_events=200, pp_samples=500, lr=3e-4,
+             cross=True):
     """The conditional coupling flow (16 affine coupling layers, conditioners 72 -> 256 ->
-    256 -> 8, embedding 496 -> 512 -> 512 -> 64 on spectral features; tcgen05 dense layers)
-    trained with AdamW on 512-draw batches of the two-detector workload (one C-ABI call
-    per step); then posterior sampling (20,000 draws of one event, the paper's inference
-    size), importance sampling of 32 events x 4000 draws against the prior as proposal
-    (spins and merger time known to both), and a PP test of the flow's marginals."""
+    256 -> 8; embedding 984 -> 512 -> 512 -> 64 on log group powers and inter-detector
+    cross spectra; tcgen05 dense layers) trained with AdamW (lr 3e-4, weight decay 2e-3)
+    on 512-draw batches of the two-detector workload (one C-ABI call per step); then
+    posterior sampling (20,000 draws of one event, the paper's inference size), importance
+    sampling of 32 events x 4000 draws against the prior as proposal (spins and merger
+    time known to both), and a PP test of the flow's marginals."""
     import math
     import numpy as np
     import paper_2407_19048_gb300.simulator  # noqa: F401
     from paper_2407_19048_gb300.flow import FlowPosterior
     wl = workloads.workload("small", B=512)
     sim = gwx.simulator.Simulator(wl, pipeline=True, background_every=16)
-    fp = FlowPosterior(wl, layers=16, hidden=256, context=64, embed_hidden=512, group=4, seed=0, lr=1e-3,
-                       weight_decay=2e-3)
+    fp = FlowPosterior(wl, layers=16, hidden=256, context=64, embed_hidden=512, group=4, seed=0, lr=lr,
+                       weight_decay=2e-3, cross=cross)
     losses = []
     y, th, _ = sim.step(step_counter(rank, 40000))
     fp.train_step(y, th, update=False)          # workspace allocation outside the timing
@@ -431,7 +433,7 @@ def flow_leg(gwx, torch, rank, steps=2000, events=32, per_event=4000, pp_events=
     for i in range(steps):
         y, th, _ = sim.step(step_counter(rank, 40001 + i))
         loss = fp.train_step(y, th)
-        if i in (0, steps // 4, steps // 2, 3 * steps // 4, steps - 1):
+        if i % max(1, steps // 12) == 0 or i == steps - 1:
             losses.append((i, loss.clone()))
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0

@@ -361,9 +361,20 @@ int gwx_dense_bf16_backward(const void* X, const void* W, const float* bias, con
  *   only.  theta out [GWX_NPARAM][S], log_ratio [S]: pass both to gwx_log_likelihood and
  *   gwx_importance_weights. */
 #define GWX_PROPOSAL_FIX_ANGLES 1
+/* gwx_cross_features: for each detector pair (a, b), a < b, in the order (0,1), (0,2),
+ *   .., (1,2), .. (pair p) and group g: rho = sum_k Y_a,k conj(Y_b,k) /
+ *   sqrt(sum_k |Y_a,k|^2 sum_k |Y_b,k|^2) over the group's bins, written as bfloat16
+ *   Re rho to column col0 + 2 p ng + g and Im rho to column col0 + (2 p + 1) ng + g of
+ *   features [B][F_pad] (other columns untouched).  A common time shift of all detectors
+ *   multiplies every Y by the same phase factor, which cancels in rho: the columns carry
+ *   the inter-detector delay and amplitude ratio without the arrival time (the nuisance
+ *   the paper's embedding is pre-trained to marginalise, Sec. 4.1).  Needs
+ *   col0 + D (D - 1) ng <= F_pad.  Workspace gwx_spectral_features_workspace(B, D, N). */
 size_t gwx_spectral_features_workspace(int64_t B, int D, int64_t N);
 int gwx_spectral_features(const float* y, int64_t B, int D, int64_t N, double fs, double f_lo, int group,
                           int F_pad, void* features, void* workspace, size_t workspace_bytes, void* stream);
+int gwx_cross_features(const float* y, int64_t B, int D, int64_t N, double fs, double f_lo, int group, int F_pad,
+                       int col0, void* features, void* workspace, size_t workspace_bytes, void* stream);
 int gwx_proposal_targets(const double* theta, int64_t B, const double* mean3, const double* scale3,
                          float* targets, void* stream);
 int gwx_gauss_nll(const float* out, int ldo, const float* targets, int P, int64_t B, float* loss_rows,
@@ -390,7 +401,9 @@ int gwx_sample_proposal(const float* net_out, int ldn, const double* mean3, cons
  *
  * Shape: F feature columns (groups of G bins), embedding width H_e, context width C, K
  * coupling layers (1..64), conditioner width H; F, H_e, C, H multiples of 8 in
- * [8, 65535 * 32].
+ * [8, 65535 * 32].  Features f: the D ng log group powers of gwx_spectral_features,
+ * then, when `cross` is 1, the D (D - 1) ng cross-spectral columns of gwx_cross_features
+ * from column D ng; F >= D ng (D ng (1 + (D - 1) cross) with the cross columns).
  * Parameters: one flat FP32 array `params` and its bfloat16 copy `params_bf16` with the
  * same element offsets (gwx_adamw with param_bf16 keeps them in step); weights are read
  * from the bfloat16 copy, biases from the FP32 array.  Tensor t starts at element
@@ -417,6 +430,7 @@ typedef struct gwx_flow_shape {
   int context;       /* C   */
   int layers;        /* K   */
   int hidden;        /* H   */
+  int cross;         /* 1: cross-spectral feature columns after the log powers */
 } gwx_flow_shape;
 int gwx_flow_layout(const gwx_flow_shape* shape, int64_t* n_params, int64_t* offsets);
 

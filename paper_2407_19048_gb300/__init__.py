@@ -24,7 +24,8 @@ NPARAM = 11
 
 __all__ = ["GwxError", "version", "init", "detector_geometry", "sample_prior", "generate_waveforms", "project",
            "colored_noise", "welch_psd", "inject", "whiten", "unwhiten", "simulate_batch", "log_likelihood",
-           "importance_weights", "gemm_bf16", "dense_bf16", "dense_bf16_backward", "gemm_autotune", "spectral_features", "proposal_targets",
+           "importance_weights", "gemm_bf16", "dense_bf16", "dense_bf16_backward", "gemm_autotune", "spectral_features",
+           "cross_features", "proposal_targets",
            "gauss_nll", "adamw", "sample_proposal", "device_status", "rfft", "irfft",
            "workspace_bytes", "TAYLORF2", "IMRPHENOMD", "DETECTORS"]
 
@@ -347,6 +348,20 @@ def spectral_features(y, fs, f_lo, group, F_pad, out=None):
     return out
 
 
+def cross_features(y, fs, f_lo, group, F_pad, col0, out):
+    """Writes the cross-spectral columns of whitened windows y [B][D][N] into out
+    (bfloat16 [B][F_pad]) from column col0 (see gwx.h); returns out."""
+    torch = _torch()
+    lib = _lib.load()
+    _dev(y, torch.float32, "y")
+    _dev(out, torch.bfloat16, "out")
+    B, D, N = y.shape
+    ws, nb = _workspace(lib.gwx_spectral_features_workspace(B, D, N), y.device)
+    _check(lib.gwx_cross_features(_ptr(y), B, D, N, fs, f_lo, group, F_pad, col0, _ptr(out), _ptr(ws), nb,
+                                  _stream()))
+    return out
+
+
 def proposal_targets(theta, mean, scale, out=None):
     """float32 [B][3] standardised (Mc, M, D) of draws theta [11][B]."""
     torch = _torch()
@@ -444,15 +459,16 @@ def irfft(X, N, out=None):
 
 # ---------------------------------------------------------------- conditional coupling flow
 
-def flow_shape(features, group, embed_hidden, context, layers, hidden):
-    return _lib.GwxFlowShape(int(features), int(group), int(embed_hidden), int(context), int(layers), int(hidden))
+def flow_shape(features, group, embed_hidden, context, layers, hidden, cross=0):
+    return _lib.GwxFlowShape(int(features), int(group), int(embed_hidden), int(context), int(layers), int(hidden),
+                             int(cross))
 
 
 def _shape(shape):
     if isinstance(shape, _lib.GwxFlowShape):
         return shape
     return flow_shape(shape["features"], shape["group"], shape["embed_hidden"], shape["context"], shape["layers"],
-                      shape["hidden"])
+                      shape["hidden"], shape.get("cross", 0))
 
 
 def _host8(v):

@@ -27,7 +27,8 @@ class GwxPrior(ctypes.Structure):
 
 
 class GwxFlowShape(ctypes.Structure):
-    _fields_ = [(name, c_int) for name in ("features", "group", "embed_hidden", "context", "layers", "hidden")]
+    _fields_ = [(name, c_int) for name in ("features", "group", "embed_hidden", "context", "layers", "hidden",
+                                              "cross")]
 
 
 c_shp = ctypes.POINTER(GwxFlowShape)
@@ -74,6 +75,8 @@ SIGNATURES = {
     "gwx_spectral_features_workspace": (c_size, [c_i64, c_int, c_i64]),
     "gwx_spectral_features": (c_int, [c_vp, c_i64, c_int, c_i64, c_dbl, c_dbl, c_int, c_int, c_vp, c_vp, c_size,
                                       c_vp]),
+    "gwx_cross_features": (c_int, [c_vp, c_i64, c_int, c_i64, c_dbl, c_dbl, c_int, c_int, c_int, c_vp, c_vp, c_size,
+                                   c_vp]),
     "gwx_proposal_targets": (c_int, [c_vp, c_i64, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl), c_vp, c_vp]),
     "gwx_gauss_nll": (c_int, [c_vp, c_int, c_vp, c_int, c_i64, c_vp, c_vp, c_vp, c_vp]),
     "gwx_adamw": (c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl, c_i64, c_vp, c_vp]),

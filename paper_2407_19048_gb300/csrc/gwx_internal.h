@@ -95,6 +95,12 @@ cudaError_t launch_dense_backward(const void* X, const void* W, const float* bia
 // Learned proposal (k_learn.cu).
 cudaError_t launch_features(const float* y, int64_t B, int D, int64_t N, int k_lo, int G, int F_pad, void* ws,
                             void* out, cudaStream_t s);
+// Cross-spectral columns (k_cross_features) from a spectrum Y complex [B][D][N/2+1] that
+// launch_features left in its workspace, or from y (rfft into ws first).
+cudaError_t launch_cross_from_spectrum(const void* Y, int64_t B, int D, int64_t N, int k_lo, int G, int F_pad,
+                                       int col0, void* out, cudaStream_t s);
+cudaError_t launch_cross_features(const float* y, int64_t B, int D, int64_t N, int k_lo, int G, int F_pad, int col0,
+                                  void* ws, void* out, cudaStream_t s);
 cudaError_t launch_targets(const double* theta, int64_t B, const double* mean, const double* scale, float* t,
                            cudaStream_t s);
 cudaError_t launch_gauss_nll(const float* out, int ldo, const float* t, int P, int B, float* loss, double* mean,

@@ -38,6 +38,39 @@ __global__ void k_features(const float2* __restrict__ Y, int D, int64_t F, int N
   out[i] = __float2bfloat16_rn(v);
 }
 
+// Normalised cross spectrum of detector pair p (pairs (a, b), a < b, in row-major
+// order) over group g: rho = sum Y_a conj(Y_b) / sqrt(sum |Y_a|^2 sum |Y_b|^2); Re rho
+// to column col0 + 2 p ng + g, Im rho to col0 + (2 p + 1) ng + g.
+__global__ void k_cross_features(const float2* __restrict__ Y, int D, int64_t F, int k_lo, int G, int ng, int F_pad,
+                                 int col0, int64_t B, __nv_bfloat16* __restrict__ out) {
+  const int P = D * (D - 1) / 2;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B * P * ng) return;
+  const int64_t b = i / (P * ng);
+  const int rem = (int)(i - b * P * ng);
+  const int p = rem / ng, g = rem % ng;
+  int a = 0, c = 1, q = p;
+  while (q >= D - 1 - a) {   // p-th pair in (0,1), (0,2), .., (1,2), .. order
+    q -= D - 1 - a;
+    ++a;
+  }
+  c = a + 1 + q;
+  const float2* ya = Y + (b * D + a) * F + k_lo + (int64_t)g * G;
+  const float2* yb = Y + (b * D + c) * F + k_lo + (int64_t)g * G;
+  float re = 0.f, im = 0.f, na = 0.f, nb = 0.f;
+  for (int k = 0; k < G; ++k) {
+    const float2 u = ya[k], v = yb[k];
+    re = fmaf(u.x, v.x, fmaf(u.y, v.y, re));
+    im = fmaf(u.y, v.x, fmaf(-u.x, v.y, im));
+    na = fmaf(u.x, u.x, fmaf(u.y, u.y, na));
+    nb = fmaf(v.x, v.x, fmaf(v.y, v.y, nb));
+  }
+  const float inv = rsqrtf(na * nb);
+  __nv_bfloat16* row = out + b * F_pad + col0;
+  row[2 * p * ng + g] = __float2bfloat16_rn(re * inv);
+  row[(2 * p + 1) * ng + g] = __float2bfloat16_rn(im * inv);
+}
+
 struct Std3 {
   double mean[3], scale[3];
 };
@@ -189,6 +222,24 @@ cudaError_t launch_features(const float* y, int64_t B, int D, int64_t N, int k_l
   k_features<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(Y, D, F, (int)N, k_lo, G, ng, F_pad, B,
                                                              reinterpret_cast<__nv_bfloat16*>(out));
   return cudaGetLastError();
+}
+
+cudaError_t launch_cross_from_spectrum(const void* Y, int64_t B, int D, int64_t N, int k_lo, int G, int F_pad,
+                                       int col0, void* out, cudaStream_t s) {
+  const int ng = (int)((N / 2 - k_lo) / G);
+  const int64_t total = B * (int64_t)(D * (D - 1) / 2) * ng;
+  if (total == 0) return cudaSuccess;
+  k_cross_features<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(reinterpret_cast<const float2*>(Y), D, N / 2 + 1,
+                                                                   k_lo, G, ng, F_pad, col0, B,
+                                                                   reinterpret_cast<__nv_bfloat16*>(out));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cross_features(const float* y, int64_t B, int D, int64_t N, int k_lo, int G, int F_pad, int col0,
+                                  void* ws, void* out, cudaStream_t s) {
+  cudaError_t e = launch_rfft_rows(y, B * D, N, reinterpret_cast<float2*>(ws), s);
+  if (e != cudaSuccess) return e;
+  return launch_cross_from_spectrum(ws, B, D, N, k_lo, G, F_pad, col0, out, s);
 }
 
 cudaError_t launch_targets(const double* theta, int64_t B, const double* mean, const double* scale, float* t,

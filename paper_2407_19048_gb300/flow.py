@@ -14,12 +14,10 @@ import math
 
 from . import _lib
 
-PARAM_ORDER = ("W1", "b1", "W2", "b2", "W3", "b3")
-
 
 class FlowPosterior:
     def __init__(self, workload, layers=16, hidden=256, context=64, embed_hidden=512, group=4, seed=0,
-                 device=None, lr=1e-3, weight_decay=2e-3, max_batch=None):
+                 device=None, lr=1e-3, weight_decay=2e-3, cross=True):
         import torch
         import paper_2407_19048_gb300 as gwx
         self.gwx = gwx
@@ -29,9 +27,11 @@ class FlowPosterior:
         self.D, self.N, self.fs, self.f_lo = len(wl["dets"]), int(wl["N"]), float(wl["fs"]), float(wl["f_lo"])
         k_lo = math.ceil(self.f_lo * self.N / self.fs - 1e-9)
         ng = (self.N // 2 - k_lo) // group
-        F = ((self.D * ng + 7) // 8) * 8
+        cross = 1 if (cross and self.D > 1) else 0
+        cols = self.D * ng * (1 + (self.D - 1) * cross)
+        F = ((cols + 7) // 8) * 8
         self.shape = {"features": F, "group": group, "embed_hidden": embed_hidden, "context": context,
-                      "layers": layers, "hidden": hidden}
+                      "layers": layers, "hidden": hidden, "cross": cross}
         self.n_params, self.offsets = gwx.flow_layout(self.shape)
         self.params = torch.zeros(self.n_params, dtype=torch.float32, device=self.dev)
         self.params16 = torch.zeros(self.n_params, dtype=torch.bfloat16, device=self.dev)
@@ -128,14 +128,15 @@ class FlowPosterior:
     _MAGIC = b"GWXFLOW1"
 
     def save(self, path, next_step=None):
-        """Flat binary checkpoint: magic, little-endian int64 header (6 shape fields, steps,
+        """Flat binary checkpoint: magic, little-endian int64 header (7 shape fields, steps,
         next_step, n_params), 16 float64 (mean, scale), then params, m and v as float32."""
         import numpy as np
         sh = self.shape
         with open(path, "wb") as fh:
             fh.write(self._MAGIC)
             np.array([sh["features"], sh["group"], sh["embed_hidden"], sh["context"], sh["layers"], sh["hidden"],
-                      self.steps, -1 if next_step is None else next_step, self.n_params], dtype="<i8").tofile(fh)
+                      sh["cross"], self.steps, -1 if next_step is None else next_step, self.n_params],
+                     dtype="<i8").tofile(fh)
             np.array(self.mean + self.scale, dtype="<f8").tofile(fh)
             for t in (self.params, self.m, self.v):
                 t.detach().cpu().numpy().astype("<f4").tofile(fh)
@@ -148,18 +149,19 @@ class FlowPosterior:
         with open(path, "rb") as fh:
             if fh.read(len(self._MAGIC)) != self._MAGIC:
                 raise ValueError("not a flow checkpoint: %s" % path)
-            hdr = [int(v) for v in np.fromfile(fh, dtype="<i8", count=9)]
+            hdr = [int(v) for v in np.fromfile(fh, dtype="<i8", count=10)]
             sh = self.shape
-            want = [sh["features"], sh["group"], sh["embed_hidden"], sh["context"], sh["layers"], sh["hidden"]]
-            if hdr[:6] != want or hdr[8] != self.n_params:
-                raise ValueError("checkpoint shape %s differs from this flow %s" % (hdr[:6], want))
+            want = [sh["features"], sh["group"], sh["embed_hidden"], sh["context"], sh["layers"], sh["hidden"],
+                    sh["cross"]]
+            if hdr[:7] != want or hdr[9] != self.n_params:
+                raise ValueError("checkpoint shape %s differs from this flow %s" % (hdr[:7], want))
             ms = np.fromfile(fh, dtype="<f8", count=16)
             self.mean, self.scale = [float(v) for v in ms[:8]], [float(v) for v in ms[8:]]
             for t in (self.params, self.m, self.v):
                 t.copy_(torch.from_numpy(np.fromfile(fh, dtype="<f4", count=self.n_params)))
             self.params16.copy_(self.params.to(torch.bfloat16))
-            self.steps = hdr[6]
-        return None if hdr[7] < 0 else hdr[7]
+            self.steps = hdr[7]
+        return None if hdr[8] < 0 else hdr[8]
 
 
 __all__ = ["FlowPosterior"]
