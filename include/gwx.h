@@ -410,12 +410,12 @@ int gwx_sample_proposal(const float* net_out, int ldn, const double* mean3, cons
  * offsets[t] (a multiple of 64; gwx_flow_layout), in the order
  *   embedding        W1 [H_e][F], b1 [H_e], W2 [H_e][H_e], b2 [H_e], W3 [C][H_e], b3 [C];
  *   layer l = 0..K-1 V1 [H][8 + C], e1 [H], V2 [H][H], e2 [H], V3 [8][H], e3 [8].
- * Embedding:  c = W3 h2 + b3, h2 = gelu(W2 h1 + b2), h1 = gelu(W1 f + b1), f the features
- *             (f, h1, h2, c held in bfloat16).
+ * Embedding:  c = W3 h2 + b3, h2 = relu(W2 h1 + b2), h1 = relu(W1 f + b1), f the features
+ *             (f, h1, h2, c held in bfloat16; relu(z) = max(z, 0)).
  * Layer l:    split (a, b) = SPLITS[l % 4], SPLITS = {(0 1 2 3 | 4 5 6 7), (4 5 6 7 | 0 1 2 3),
  *             (0 2 4 6 | 1 3 5 7), (1 3 5 7 | 0 2 4 6)}; conditioner input row
  *             X = [bf16(v_a), 0, 0, 0, 0, c] (bfloat16 [8 + C]); o = V3 g2 + e3 (FP32 [8]),
- *             g2 = gelu(V2 g1 + e2), g1 = gelu(V1 X + e1) (bfloat16); shift mu_j = o_j,
+ *             g2 = relu(V2 g1 + e2), g1 = relu(V1 X + e1) (bfloat16); shift mu_j = o_j,
  *             log-scale s_j = 3 tanh(o_{4+j} / 3) on coordinate b_j.  Sampling direction
  *             v_b <- v_b e^s + mu; density direction v_b <- (v_b - mu) e^{-s}.
  * Sampling applies layers 0 .. K-1 to z ~ N(0, I_8), the density K-1 .. 0 to x;

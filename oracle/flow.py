@@ -15,12 +15,14 @@ mass Mc = (m1 m2)^{3/5} / (m1 + m2)^{1/5} and q = min(m1, m2) / max(m1, m2) in (
 the flow works in x = (r - mean) / scale (given per coordinate).
 
 Embedding (the data summary).  From the spectral features f of the whitened strain
-(oracle.learn.features):  c = W3 h2 + b3,  h2 = gelu(W2 h1 + b2),  h1 = gelu(W1 f + b1).
+(oracle.learn.features and cross_features):  c = W3 h2 + b3,  h2 = relu(W2 h1 + b2),
+h1 = relu(W1 f + b1), relu(z) = max(z, 0) (the activation of the autoregressive
+networks in the library the paper builds its flow with, and of the ResNet it adapts).
 
 Coupling layer l (l = 0 .. K-1) uses the split SPLITS[l % 4] = (a, b) of the eight
 coordinates into four conditioning coordinates a and four transformed coordinates b.
 Its conditioner reads the row X = [v_a (4 values), 0, 0, 0, 0, c (C values)] and gives
-o = V3 g2 + e3 (8 values), g2 = gelu(V2 g1 + e2), g1 = gelu(V1 X + e1); the shift is
+o = V3 g2 + e3 (8 values), g2 = relu(V2 g1 + e2), g1 = relu(V1 X + e1); the shift is
 mu_j = o_j and the log-scale s_j = S_MAX tanh(o_{4+j} / S_MAX), j = 0..3, acting on
 coordinate b[j]:
   sampling direction  v_b <- v_b e^{s} + mu,
@@ -79,17 +81,12 @@ def exact(x):
     return np.asarray(x, dtype=np.float64)
 
 
-def _erf(x):
-    from scipy.special import erf
-    return erf(x)
+def relu(z):
+    return np.maximum(z, 0.0)
 
 
-def gelu(z):
-    return z * 0.5 * (1.0 + _erf(z / math.sqrt(2.0)))
-
-
-def gelu_grad(z):
-    return 0.5 * (1.0 + _erf(z / math.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
+def relu_grad(z):
+    return (np.asarray(z) > 0.0).astype(np.float64)
 
 
 def split_params(params, K):
@@ -148,8 +145,8 @@ def embed(feat, emb, rnd=round_bf16):
     """Context c [B][C] from features feat [B][F]; returns (c, (h1, h2))."""
     W1, b1, W2, b2, W3, b3 = emb
     f = np.asarray(feat, dtype=np.float64)
-    h1 = rnd(gelu(f @ W1.T + b1[None, :]))
-    h2 = rnd(gelu(h1 @ W2.T + b2[None, :]))
+    h1 = rnd(relu(f @ W1.T + b1[None, :]))
+    h2 = rnd(relu(h1 @ W2.T + b2[None, :]))
     c = rnd(h2 @ W3.T + b3[None, :])
     return c, (h1, h2)
 
@@ -168,8 +165,8 @@ def conditioner_input(v, c, l, rnd=round_bf16):
 def conditioner(X, layer, rnd=round_bf16):
     """o [B][8] of one conditioner; returns (o, (g1, g2))."""
     V1, e1, V2, e2, V3, e3 = layer
-    g1 = rnd(gelu(X @ V1.T + e1[None, :]))
-    g2 = rnd(gelu(g1 @ V2.T + e2[None, :]))
+    g1 = rnd(relu(X @ V1.T + e1[None, :]))
+    g2 = rnd(relu(g1 @ V2.T + e2[None, :]))
     return g2 @ V3.T + e3[None, :], (g1, g2)
 
 
@@ -229,10 +226,10 @@ def nll(z, sum_s):
     return rows, rows.mean()
 
 
-def _dense_back(X, W, b, dy, act_gelu, rnd_dz):
+def _dense_back(X, W, b, dy, act_relu, rnd_dz):
     """Chain rule of y = act(X W^T + b): (dX, dW, db).  The products take rnd_dz(dZ)."""
     z = X @ W.T + b[None, :]
-    dz = dy * (gelu_grad(z) if act_gelu else 1.0)
+    dz = dy * (relu_grad(z) if act_relu else 1.0)
     dzp = rnd_dz(dz)
     return dzp @ W, dzp.T @ X, dz.sum(axis=0)
 

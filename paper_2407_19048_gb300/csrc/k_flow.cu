@@ -6,7 +6,8 @@
 // q = min(m1, m2) / max(m1, m2); the flow works in x = (r - mean) / scale.  Coupling
 // layer l splits the eight coordinates by kSplit[l % 4] into a conditioning half a and a
 // transformed half b; its conditioner maps [x_a, 0 0 0 0, context] through three dense
-// layers (bfloat16 operands on the tensor cores, gwx::launch_gemm_bf16) to o[8]:
+// layers (ReLU between them; bfloat16 operands on the tensor cores,
+// gwx::launch_gemm_bf16) to o[8]:
 // shift mu_j = o_j, log-scale s_j = 3 tanh(o_{4+j} / 3).  Sampling moves x_b to
 // x_b e^s + mu, the density direction to (x_b - mu) e^{-s}; ln q_x(x) = ln N(z) - sum s.
 //
@@ -41,6 +42,7 @@ __constant__ int kSplit[4][8] = {{0, 1, 2, 3, 4, 5, 6, 7},
 struct Std8 {
   double mean[8], scale[8];
   double ln_scale_sum;
+  double ln_prior0;   // the constant part of ln prior_r (set by the proposal launcher)
 };
 
 __device__ __forceinline__ void load8(const float* p, float* v) {
@@ -212,11 +214,12 @@ __global__ void k_flow_base(uint32_t k0, uint32_t k1, uint32_t counter, int64_t 
   for (int i = 0; i < 4; ++i) {
     const u32x4 w = philox4x32_10(s, (uint32_t)i, TAG_FLOW, counter, k0, k1);
     const double u0 = uniform52(w.x, w.y), u1 = uniform52(w.z, w.w);
-    const double rad = sqrt(-2.0 * log(u0));
-    double sn, cs;
-    sincos(2.0 * PI_F * u1, &sn, &cs);
-    v[2 * i] = (float)(rad * cs);
-    v[2 * i + 1] = (float)(rad * sn);
+    // radius in FP64 (the logarithm near u0 -> 0 sets the tail), angle in FP32
+    const float rad = (float)sqrt(-2.0 * log(u0));
+    float sn, cs;
+    sincospif((float)(2.0 * u1), &sn, &cs);
+    v[2 * i] = rad * cs;
+    v[2 * i + 1] = rad * sn;
   }
   store8(z + r * 8, v);
 }
@@ -246,7 +249,9 @@ __global__ void k_flow_proposal(const float* __restrict__ x, const float* __rest
   const double Mc = r[0], q = r[1], D = r[2], ct = r[3], al = r[4], sd = r[5], psi = r[6], phi = r[7];
   double m1 = pr.m_lo, m2 = pr.m_lo, dist = pr.d_lo, lr = -INFINITY;
   if (Mc > 0.0 && q > 0.0 && q <= 1.0) {
-    const double big = Mc * pow(1.0 + q, 0.2) * pow(q, -0.6), small = q * big;
+    // m_big = Mc (1 + q)^{1/5} q^{-3/5}; ln prior_r = const + 2 ln m_big - ln Mc
+    const double l_q = log(q), l_1q = log1p(q);
+    const double big = Mc * exp(0.2 * l_1q - 0.6 * l_q), small = q * big;
     const bool inside = pr.m_lo <= small && big <= pr.m_hi && pr.d_lo <= D && D <= pr.d_hi && -1.0 <= ct &&
                         ct <= 1.0 && 0.0 <= al && al < 2.0 * PI_F && -1.0 <= sd && sd <= 1.0 && pr.psi_lo <= psi &&
                         psi <= pr.psi_hi && pr.phi_lo <= phi && phi <= pr.phi_hi;
@@ -254,9 +259,7 @@ __global__ void k_flow_proposal(const float* __restrict__ x, const float* __rest
       m1 = coin < 0.5 ? small : big;
       m2 = coin < 0.5 ? big : small;
       dist = D;
-      const double lp = log(2.0) + 2.0 * log(big) - log(Mc) - 2.0 * log(pr.m_hi - pr.m_lo) - log(pr.d_hi - pr.d_lo) -
-                        log(2.0) - log(2.0 * PI_F) - log(2.0) - log(pr.psi_hi - pr.psi_lo) -
-                        log(pr.phi_hi - pr.phi_lo);
+      const double lp = st.ln_prior0 + log(Mc) + 0.4 * l_1q - 1.2 * l_q;
       lr = lp - lq;
     }
   }
@@ -292,6 +295,7 @@ inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 Std8 make_std(const double* mean8, const double* scale8) {
   Std8 st;
   st.ln_scale_sum = 0.0;
+  st.ln_prior0 = 0.0;
   for (int p = 0; p < 8; ++p) {
     st.mean[p] = mean8[p];
     st.scale[p] = scale8[p];
@@ -405,7 +409,11 @@ cudaError_t launch_flow_proposal(const float* x, const float* z, const float* su
                                  int64_t S, const double* mean8, const double* scale8, const gwx_prior& pr,
                                  const double* truth, int64_t E, const int64_t* off, uint64_t seed, uint32_t counter,
                                  double* theta, double* log_q, double* log_ratio, cudaStream_t s) {
-  k_flow_proposal<<<blocks(n, 128), 128, 0, s>>>(x, z, sum_s, n, row0, S, make_std(mean8, scale8), pr, truth, E, off,
+  // ln prior_r = ln 2 + 2 ln m_big - ln Mc - ln((m_hi - m_lo)^2 (d_hi - d_lo) 8 pi (psi range) (phi range))
+  Std8 st = make_std(mean8, scale8);
+  st.ln_prior0 = log(2.0) - 2.0 * log(pr.m_hi - pr.m_lo) - log(pr.d_hi - pr.d_lo) - log(8.0 * PI_F) -
+                 log(pr.psi_hi - pr.psi_lo) - log(pr.phi_hi - pr.phi_lo);
+  k_flow_proposal<<<blocks(n, 128), 128, 0, s>>>(x, z, sum_s, n, row0, S, st, pr, truth, E, off,
                                                  (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), counter,
                                                  theta, log_q, log_ratio);
   return cudaGetLastError();
@@ -439,8 +447,8 @@ cudaError_t embed_forward(const FlowDims& d, const Params& P, const float* y, in
   if (d.cross)
     FL_TRY(launch_cross_from_spectrum(fws, R, D, N, k_lo, (int)d.G, (int)d.F, (int)(D * ((N / 2 - k_lo) / d.G)), feat,
                                       s));
-  FL_TRY(launch_gemm_bf16(feat, P.W(0), h1, R, d.He, d.F, true, P.b(1), GWX_ACT_GELU, 0, s));
-  FL_TRY(launch_gemm_bf16(h1, P.W(2), h2, R, d.He, d.He, true, P.b(3), GWX_ACT_GELU, 0, s));
+  FL_TRY(launch_gemm_bf16(feat, P.W(0), h1, R, d.He, d.F, true, P.b(1), GWX_ACT_RELU, 0, s));
+  FL_TRY(launch_gemm_bf16(h1, P.W(2), h2, R, d.He, d.He, true, P.b(3), GWX_ACT_RELU, 0, s));
   return launch_gemm_bf16(h2, P.W(4), ctx, R, d.C, d.He, true, P.b(5), GWX_ACT_NONE, 0, s);
 }
 
@@ -448,8 +456,8 @@ cudaError_t embed_forward(const FlowDims& d, const Params& P, const float* y, in
 cudaError_t conditioner_forward(const FlowDims& d, const Params& P, int l, int64_t R, const __nv_bfloat16* X,
                                 __nv_bfloat16* g1, __nv_bfloat16* g2, float* o, cudaStream_t s) {
   const int t = 6 + 6 * l;
-  FL_TRY(launch_gemm_bf16(X, P.W(t), g1, R, d.H, 8 + d.C, true, P.b(t + 1), GWX_ACT_GELU, 0, s));
-  FL_TRY(launch_gemm_bf16(g1, P.W(t + 2), g2, R, d.H, d.H, true, P.b(t + 3), GWX_ACT_GELU, 0, s));
+  FL_TRY(launch_gemm_bf16(X, P.W(t), g1, R, d.H, 8 + d.C, true, P.b(t + 1), GWX_ACT_RELU, 0, s));
+  FL_TRY(launch_gemm_bf16(g1, P.W(t + 2), g2, R, d.H, d.H, true, P.b(t + 3), GWX_ACT_RELU, 0, s));
   return launch_gemm_bf16(g2, P.W(t + 4), o, R, 8, d.H, false, P.b(t + 5), GWX_ACT_NONE, 0, s);
 }
 
@@ -552,18 +560,18 @@ cudaError_t flow_train_step(const gwx_flow_shape& sh, float* params, void* param
     FL_TRY(launch_flow_coupling_backward(l, w.xs + l * rows8, w.o + l * rows8, G, B, 1.f / (float)B, w.d_o, Gu, s));
     FL_TRY(launch_dense_backward(g2, P.W(t + 4), P.b(t + 5), w.d_o, B, 8, d.H, GWX_ACT_NONE, w.dA,
                                  grads + P.off[t + 4], grads + P.off[t + 5], w.dws, 0, s));
-    FL_TRY(launch_dense_backward(g1, P.W(t + 2), P.b(t + 3), w.dA, B, d.H, d.H, GWX_ACT_GELU, w.dB,
+    FL_TRY(launch_dense_backward(g1, P.W(t + 2), P.b(t + 3), w.dA, B, d.H, d.H, GWX_ACT_RELU, w.dB,
                                  grads + P.off[t + 2], grads + P.off[t + 3], w.dws, 0, s));
-    FL_TRY(launch_dense_backward(X, P.W(t), P.b(t + 1), w.dB, B, d.H, 8 + d.C, GWX_ACT_GELU, w.dA,
+    FL_TRY(launch_dense_backward(X, P.W(t), P.b(t + 1), w.dB, B, d.H, 8 + d.C, GWX_ACT_RELU, w.dA,
                                  grads + P.off[t], grads + P.off[t + 1], w.dws, 0, s));
     FL_TRY(launch_flow_input_backward(l, w.dA, (int)d.C, B, Gu, w.dctx, l == 0, s));
     std::swap(G, Gu);
   }
   FL_TRY(launch_dense_backward(w.h2, P.W(4), P.b(5), w.dctx, B, d.C, d.He, GWX_ACT_NONE, w.dA, grads + P.off[4],
                                grads + P.off[5], w.dws, 0, s));
-  FL_TRY(launch_dense_backward(w.h1, P.W(2), P.b(3), w.dA, B, d.He, d.He, GWX_ACT_GELU, w.dB, grads + P.off[2],
+  FL_TRY(launch_dense_backward(w.h1, P.W(2), P.b(3), w.dA, B, d.He, d.He, GWX_ACT_RELU, w.dB, grads + P.off[2],
                                grads + P.off[3], w.dws, 0, s));
-  FL_TRY(launch_dense_backward(w.feat, P.W(0), P.b(1), w.dB, B, d.He, d.F, GWX_ACT_GELU, nullptr, grads + P.off[0],
+  FL_TRY(launch_dense_backward(w.feat, P.W(0), P.b(1), w.dB, B, d.He, d.F, GWX_ACT_RELU, nullptr, grads + P.off[0],
                                grads + P.off[1], w.dws, 0, s));
   if (step >= 1) FL_TRY(launch_adamw(params, grads, m, v, n_params, lr, b1, b2, eps, wd, step, params_bf16, s));
   return cudaSuccess;

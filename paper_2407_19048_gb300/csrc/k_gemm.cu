@@ -10,8 +10,11 @@
 //   K 16; four per stage) into one of two 256-column FP32 accumulators, committing each
 //   stage to an "empty" mbarrier (the stage goes back to the producer) and each tile to a
 //   "tfull" mbarrier;
-// - warps 2-5 drain the accumulator of the previous tile with tcgen05.ld (lane quarter
-//   warp % 4 = rows 32 q .. 32 q + 31) and store C, while the next tile accumulates.
+// - warps 2-9 drain the accumulator of the previous tile with tcgen05.ld (lane quarter
+//   warp % 4 = rows 32 q .. 32 q + 31; two warps per quarter, 128 columns each) and
+//   store C, while the next tile accumulates.  Eight draining warps keep the fused
+//   epilogue (bias, activation, conversion, stores) off the critical path of products
+//   with a short K, where it, not the MMA, sets the time per tile.
 // Every mbarrier wait is bounded: on expiry the CTA records a status, stops storing,
 // frees its tensor memory and returns.
 #include <cuda.h>
@@ -25,6 +28,8 @@ namespace gwx {
 namespace {
 
 constexpr int GM = 128, GN = 256, GK = 64, STAGES = 4;
+constexpr int EPI_WARPS = 8;                            // two per tensor-memory lane quarter
+constexpr int GEMM_THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t A_BYTES = GM * GK * 2;               // 16 KiB
 constexpr uint32_t B_BYTES = GN * GK * 2;               // 32 KiB
 constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
@@ -142,12 +147,12 @@ __device__ __forceinline__ void tile_coords(int t, int TM, int TN, int group, in
 }
 
 // Persistent, warp-specialised: warp 0 lane 0 produces (TMA), warp 1 allocates tensor
-// memory and its lane 0 issues the MMAs, warps 2-5 drain accumulators.  Two 256-column
+// memory and its lane 0 issues the MMAs, warps 2-9 drain accumulators.  Two 256-column
 // accumulators alternate between tiles, so a tile's epilogue overlaps the next tile's
 // main loop; "tfull" (MMA commit) and "tempty" (one arrival per epilogue warp) hand them
 // over.
 template <bool OUT_BF16>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
     k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, void* __restrict__ C,
                 const float* __restrict__ bias, int act, int group, int M, int N, int K) {
   extern __shared__ uint8_t smem_raw[];
@@ -167,7 +172,7 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(su32(&tfull[a]), 1);
-      mbar_init(su32(&tempty[a]), 4);
+      mbar_init(su32(&tempty[a]), EPI_WARPS);
     }
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -233,8 +238,10 @@ __global__ void __launch_bounds__(192, 1)
       }
     }
   } else {
-    // epilogue warps 2-5; tensor-memory lane quarter (warp % 4) = tile rows 32 q .. 32 q + 31
+    // epilogue warps 2-9; tensor-memory lane quarter (warp % 4) = tile rows 32 q .. 32 q + 31,
+    // column half (warp - 2) / 4
     const int q = warp & 3;
+    const int c_lo = ((warp - 2) >> 2) * (GN / 64), c_hi = c_lo + GN / 64;
     uint32_t tl = 0;
     for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++tl) {
       int tm, tn;
@@ -248,7 +255,7 @@ __global__ void __launch_bounds__(192, 1)
       }
       const int row = tm * GM + 32 * q + lane;
 #pragma unroll 1
-      for (int c = 0; c < GN / 32; ++c) {
+      for (int c = c_lo; c < c_hi; ++c) {
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + acc * TMEM_COLS + (uint32_t)(32 * c), v);
         const int col0 = tn * GN + 32 * c;
@@ -339,11 +346,11 @@ cudaError_t launch_gemm_bf16(const void* A, const void* B, void* C, int64_t M, i
   if (out_bf16) {
     e = cudaFuncSetAttribute(k_gemm_bf16<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
     if (e != cudaSuccess) return e;
-    k_gemm_bf16<true><<<grid, 192, GEMM_SMEM, s>>>(ta, tb, C, bias, act, group, (int)M, (int)N, (int)K);
+    k_gemm_bf16<true><<<grid, GEMM_THREADS, GEMM_SMEM, s>>>(ta, tb, C, bias, act, group, (int)M, (int)N, (int)K);
   } else {
     e = cudaFuncSetAttribute(k_gemm_bf16<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
     if (e != cudaSuccess) return e;
-    k_gemm_bf16<false><<<grid, 192, GEMM_SMEM, s>>>(ta, tb, C, bias, act, group, (int)M, (int)N, (int)K);
+    k_gemm_bf16<false><<<grid, GEMM_THREADS, GEMM_SMEM, s>>>(ta, tb, C, bias, act, group, (int)M, (int)N, (int)K);
   }
   return cudaGetLastError();
 }
