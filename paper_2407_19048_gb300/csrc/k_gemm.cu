@@ -35,7 +35,8 @@ constexpr uint32_t B_BYTES = GN * GK * 2;               // 32 KiB
 constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr uint32_t TMEM_COLS = GN;                      // FP32 accumulator columns
 constexpr uint32_t WAIT_POLLS = 1u << 22;
-constexpr size_t GEMM_SMEM = (size_t)STAGES * STAGE_BYTES + 1024;   // + alignment slack
+constexpr uint32_t EPI_BUF_BYTES = 32 * 32 * 4;         // per epilogue warp: a 32 x 32 FP32 transpose tile
+constexpr size_t GEMM_SMEM = (size_t)STAGES * STAGE_BYTES + (size_t)EPI_WARPS * EPI_BUF_BYTES + 1024;
 
 // Instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1), A and B
 // bfloat16 (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits
@@ -242,6 +243,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     // column half (warp - 2) / 4
     const int q = warp & 3;
     const int c_lo = ((warp - 2) >> 2) * (GN / 64), c_hi = c_lo + GN / 64;
+    float* ebuf = reinterpret_cast<float*>(smem_raw + (base - su32(smem_raw)) + STAGES * STAGE_BYTES +
+                                           (warp - 2) * EPI_BUF_BYTES);
     uint32_t tl = 0;
     for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++tl) {
       int tm, tn;
@@ -253,43 +256,48 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         if (lane == 0) atomicExch(&abort_flag, 1);
         break;
       }
-      const int row = tm * GM + 32 * q + lane;
+      // Each warp stages its 32 rows x 32 columns through a swizzled shared tile (word j of
+      // row r at r * 32 + (j ^ r): conflict-free both ways), then stores whole row segments:
+      // FP32 one 128-byte row per instruction, bfloat16 two 64-byte rows per instruction.
+      const int row0 = tm * GM + 32 * q;
 #pragma unroll 1
       for (int c = c_lo; c < c_hi; ++c) {
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + acc * TMEM_COLS + (uint32_t)(32 * c), v);
         const int col0 = tn * GN + 32 * c;
-        if (row >= M || col0 >= N) continue;
+        if (row0 >= M || col0 >= N) continue;   // warp-uniform
         epilogue_ops(v, bias, act, col0, N);
-        if constexpr (OUT_BF16) {
-          __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(C) + (int64_t)row * N + col0;
-          if (col0 + 32 <= N && (N % 8) == 0) {
 #pragma unroll
-            for (int i = 0; i < 32; i += 8) {
-              uint4 pk;
-              __nv_bfloat162 h0 = __floats2bfloat162_rn(v[i], v[i + 1]);
-              __nv_bfloat162 h1 = __floats2bfloat162_rn(v[i + 2], v[i + 3]);
-              __nv_bfloat162 h2 = __floats2bfloat162_rn(v[i + 4], v[i + 5]);
-              __nv_bfloat162 h3 = __floats2bfloat162_rn(v[i + 6], v[i + 7]);
-              pk.x = *reinterpret_cast<uint32_t*>(&h0);
-              pk.y = *reinterpret_cast<uint32_t*>(&h1);
-              pk.z = *reinterpret_cast<uint32_t*>(&h2);
-              pk.w = *reinterpret_cast<uint32_t*>(&h3);
-              *reinterpret_cast<uint4*>(out + i) = pk;
+        for (int j = 0; j < 32; ++j) ebuf[lane * 32 + (j ^ lane)] = v[j];
+        __syncwarp();
+        if constexpr (OUT_BF16) {
+          __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(C);
+          const int w = lane & 15, col = col0 + 2 * w;
+#pragma unroll 4
+          for (int r2 = 0; r2 < 16; ++r2) {
+            const int r = 2 * r2 + (lane >> 4);
+            const int grow = row0 + r;
+            const float a = ebuf[r * 32 + ((2 * w) ^ r)], b = ebuf[r * 32 + ((2 * w + 1) ^ r)];
+            if (grow < M) {
+              __nv_bfloat16* o = out + (int64_t)grow * N + col;
+              if (col + 1 < N && (N % 2) == 0) {
+                *reinterpret_cast<__nv_bfloat162*>(o) = __floats2bfloat162_rn(a, b);
+              } else {
+                if (col < N) o[0] = __float2bfloat16_rn(a);
+                if (col + 1 < N) o[1] = __float2bfloat16_rn(b);
+              }
             }
-          } else {
-            for (int i = 0; i < 32 && col0 + i < N; ++i) out[i] = __float2bfloat16_rn(v[i]);
           }
         } else {
-          float* out = reinterpret_cast<float*>(C) + (int64_t)row * N + col0;
-          if (col0 + 32 <= N && (N % 4) == 0) {
-#pragma unroll
-            for (int i = 0; i < 32; i += 4)
-              *reinterpret_cast<float4*>(out + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-          } else {
-            for (int i = 0; i < 32 && col0 + i < N; ++i) out[i] = v[i];
+          float* out = reinterpret_cast<float*>(C);
+          const int col = col0 + lane;
+#pragma unroll 4
+          for (int r = 0; r < 32; ++r) {
+            const float a = ebuf[r * 32 + (lane ^ r)];
+            if (row0 + r < M && col < N) out[(int64_t)(row0 + r) * N + col] = a;
           }
         }
+        __syncwarp();
       }
       // the accumulator is drained: hand it back to the MMA issuer
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
