@@ -375,6 +375,15 @@ int gwx_spectral_features(const float* y, int64_t B, int D, int64_t N, double fs
                           int F_pad, void* features, void* workspace, size_t workspace_bytes, void* stream);
 int gwx_cross_features(const float* y, int64_t B, int D, int64_t N, double fs, double f_lo, int group, int F_pad,
                        int col0, void* features, void* workspace, size_t workspace_bytes, void* stream);
+/* gwx_lag_features: for each detector d and group g the normalised lag-one product
+ *   lam = sum_k Y_k conj(Y_{k+1}) / sqrt(sum_k |Y_k|^2 sum_k |Y_{k+1}|^2) over the group's
+ *   bins k, as bfloat16 Re lam to column col0 + 2 d ng + g and Im lam to col0 + (2 d + 1) ng
+ *   + g.  For a chirp its phase is 2 pi t(f) / T with t(f) the time the signal passes
+ *   frequency f: the time-frequency track that fixes the chirp mass, which log powers
+ *   and cross spectra do not carry.  Needs col0 + 2 D ng <= F_pad.  Workspace as for
+ *   gwx_spectral_features. */
+int gwx_lag_features(const float* y, int64_t B, int D, int64_t N, double fs, double f_lo, int group, int F_pad,
+                     int col0, void* features, void* workspace, size_t workspace_bytes, void* stream);
 int gwx_proposal_targets(const double* theta, int64_t B, const double* mean3, const double* scale3,
                          float* targets, void* stream);
 int gwx_gauss_nll(const float* out, int ldo, const float* targets, int P, int64_t B, float* loss_rows,
@@ -402,8 +411,9 @@ int gwx_sample_proposal(const float* net_out, int ldn, const double* mean3, cons
  * Shape: F feature columns (groups of G bins), embedding width H_e, context width C, K
  * coupling layers (1..64), conditioner width H; F, H_e, C, H multiples of 8 in
  * [8, 65535 * 32].  Features f: the D ng log group powers of gwx_spectral_features,
- * then, when `cross` is 1, the D (D - 1) ng cross-spectral columns of gwx_cross_features
- * from column D ng; F >= D ng (D ng (1 + (D - 1) cross) with the cross columns).
+ * then, when `extra` has GWX_FLOW_CROSS, the D (D - 1) ng cross-spectral columns of
+ * gwx_cross_features, then, when it has GWX_FLOW_LAG, the 2 D ng lag-one columns of
+ * gwx_lag_features; F at least their total.
  * Parameters: one flat FP32 array `params` and its bfloat16 copy `params_bf16` with the
  * same element offsets (gwx_adamw with param_bf16 keeps them in step); weights are read
  * from the bfloat16 copy, biases from the FP32 array.  Tensor t starts at element
@@ -430,8 +440,10 @@ typedef struct gwx_flow_shape {
   int context;       /* C   */
   int layers;        /* K   */
   int hidden;        /* H   */
-  int cross;         /* 1: cross-spectral feature columns after the log powers */
+  int extra;         /* feature columns after the log powers: GWX_FLOW_CROSS | GWX_FLOW_LAG */
 } gwx_flow_shape;
+#define GWX_FLOW_CROSS 1
+#define GWX_FLOW_LAG 2
 int gwx_flow_layout(const gwx_flow_shape* shape, int64_t* n_params, int64_t* offsets);
 
 /* Stages (one kernel each; the calls further down chain them).  Arrays are device

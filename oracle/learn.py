@@ -14,6 +14,11 @@ network of spectral features of the whitened strain.  This module states, in FP6
   imaginary parts): unchanged by a common time shift of all detectors (the shift's phase
   factor cancels in the product), so it carries the inter-detector delay and amplitude
   ratio that localise the source without the arrival time;
+* lag_features -- per detector and group, the normalised lag-one spectral product
+  lam = sum_k Y_k conj(Y_{k+1}) / sqrt(sum_k |Y_k|^2 sum_k |Y_{k+1}|^2) (real and imaginary
+  parts): for a signal its phase is 2 pi t(f) / T, t(f) the time at which the signal
+  passes frequency f (the chirp's time-frequency track, which fixes the chirp mass); a
+  common time shift by s samples adds 2 pi s / N to every phase;
 * targets   -- (Mc, M, D) of each draw, standardised by given means and scales;
 * gauss_nll -- per-row negative log-density of standardised targets t under
   N(mu, exp(s)^2) (without the constant): sum_p [ (t_p - mu_p)^2 e^{-2 s_p} / 2 + s_p ],
@@ -73,6 +78,26 @@ def cross_features(y, k_lo, G):
                                                              np.sum(np.abs(yb) ** 2, axis=-1))
             out[:, 2 * p * ng + g] = rho.real
             out[:, (2 * p + 1) * ng + g] = rho.imag
+    return out
+
+
+def lag_features(y, k_lo, G):
+    """[B][2 D ng] normalised lag-one spectral products of whitened windows y [B][D][N]:
+    for detector d and group g (bins k = k_lo + g G .. k_lo + g G + G - 1, each paired with
+    k + 1), column 2 d ng + g holds Re lam, (2 d + 1) ng + g holds Im lam."""
+    y = np.asarray(y, dtype=np.float64)
+    B, D, N = y.shape
+    Y = np.fft.rfft(y, axis=-1)
+    ng = (N // 2 - k_lo) // G
+    out = np.zeros((B, 2 * D * ng))
+    for d in range(D):
+        for g in range(ng):
+            k = k_lo + g * G
+            a, b = Y[:, d, k:k + G], Y[:, d, k + 1:k + G + 1]
+            lam = np.sum(a * np.conj(b), axis=-1) / np.sqrt(np.sum(np.abs(a) ** 2, axis=-1) *
+                                                           np.sum(np.abs(b) ** 2, axis=-1))
+            out[:, 2 * d * ng + g] = lam.real
+            out[:, (2 * d + 1) * ng + g] = lam.imag
     return out
 
 

@@ -25,7 +25,7 @@ NPARAM = 11
 __all__ = ["GwxError", "version", "init", "detector_geometry", "sample_prior", "generate_waveforms", "project",
            "colored_noise", "welch_psd", "inject", "whiten", "unwhiten", "simulate_batch", "log_likelihood",
            "importance_weights", "gemm_bf16", "dense_bf16", "dense_bf16_backward", "gemm_autotune", "spectral_features",
-           "cross_features", "proposal_targets",
+           "cross_features", "lag_features", "proposal_targets",
            "gauss_nll", "adamw", "sample_proposal", "device_status", "rfft", "irfft",
            "workspace_bytes", "TAYLORF2", "IMRPHENOMD", "DETECTORS"]
 
@@ -362,6 +362,19 @@ def cross_features(y, fs, f_lo, group, F_pad, col0, out):
     return out
 
 
+def lag_features(y, fs, f_lo, group, F_pad, col0, out):
+    """Writes the lag-one spectral columns of whitened windows y [B][D][N] into out
+    (bfloat16 [B][F_pad]) from column col0 (see gwx.h); returns out."""
+    torch = _torch()
+    lib = _lib.load()
+    _dev(y, torch.float32, "y")
+    _dev(out, torch.bfloat16, "out")
+    B, D, N = y.shape
+    ws, nb = _workspace(lib.gwx_spectral_features_workspace(B, D, N), y.device)
+    _check(lib.gwx_lag_features(_ptr(y), B, D, N, fs, f_lo, group, F_pad, col0, _ptr(out), _ptr(ws), nb, _stream()))
+    return out
+
+
 def proposal_targets(theta, mean, scale, out=None):
     """float32 [B][3] standardised (Mc, M, D) of draws theta [11][B]."""
     torch = _torch()
@@ -459,16 +472,19 @@ def irfft(X, N, out=None):
 
 # ---------------------------------------------------------------- conditional coupling flow
 
-def flow_shape(features, group, embed_hidden, context, layers, hidden, cross=0):
+FLOW_CROSS, FLOW_LAG = 1, 2
+
+
+def flow_shape(features, group, embed_hidden, context, layers, hidden, extra=0):
     return _lib.GwxFlowShape(int(features), int(group), int(embed_hidden), int(context), int(layers), int(hidden),
-                             int(cross))
+                             int(extra))
 
 
 def _shape(shape):
     if isinstance(shape, _lib.GwxFlowShape):
         return shape
     return flow_shape(shape["features"], shape["group"], shape["embed_hidden"], shape["context"], shape["layers"],
-                      shape["hidden"], shape.get("cross", 0))
+                      shape["hidden"], shape.get("extra", 0))
 
 
 def _host8(v):

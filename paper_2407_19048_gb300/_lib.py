@@ -28,7 +28,7 @@ class GwxPrior(ctypes.Structure):
 
 class GwxFlowShape(ctypes.Structure):
     _fields_ = [(name, c_int) for name in ("features", "group", "embed_hidden", "context", "layers", "hidden",
-                                              "cross")]
+                                              "extra")]
 
 
 c_shp = ctypes.POINTER(GwxFlowShape)
@@ -77,6 +77,8 @@ SIGNATURES = {
                                       c_vp]),
     "gwx_cross_features": (c_int, [c_vp, c_i64, c_int, c_i64, c_dbl, c_dbl, c_int, c_int, c_int, c_vp, c_vp, c_size,
                                    c_vp]),
+    "gwx_lag_features": (c_int, [c_vp, c_i64, c_int, c_i64, c_dbl, c_dbl, c_int, c_int, c_int, c_vp, c_vp, c_size,
+                                 c_vp]),
     "gwx_proposal_targets": (c_int, [c_vp, c_i64, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl), c_vp, c_vp]),
     "gwx_gauss_nll": (c_int, [c_vp, c_int, c_vp, c_int, c_i64, c_vp, c_vp, c_vp, c_vp]),
     "gwx_adamw": (c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl, c_i64, c_vp, c_vp]),

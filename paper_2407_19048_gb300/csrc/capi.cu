@@ -657,6 +657,28 @@ int gwx_cross_features(const float* y, int64_t B, int D, int64_t N, double fs, d
                   "cross_features");
 }
 
+int gwx_lag_features(const float* y, int64_t B, int D, int64_t N, double fs, double f_lo, int group, int F_pad,
+                     int col0, void* features, void* workspace, size_t workspace_bytes, void* stream) {
+  GWX_TRY(check_window(N));
+  if (D < 1 || D > GWX_MAX_DET) return fail(GWX_ESHAPE, "D=%d", D);
+  if (B < 0 || B * D > 0x7fffffffLL) return fail(GWX_ESHAPE, "B=%lld", (long long)B);
+  if (!(fs > 0.0)) return fail(GWX_EINVAL, "fs must be positive");
+  int k_lo = 0;
+  GWX_TRY(band_start(f_lo, fs / (double)N, N / 2, &k_lo));
+  if (group < 1 || group > N / 2) return fail(GWX_EINVAL, "group %d", group);
+  const int64_t ng = (N / 2 - k_lo) / group;
+  if (col0 < 0 || F_pad % 8 != 0 || col0 + 2 * (int64_t)D * ng > F_pad)
+    return fail(GWX_ESHAPE, "columns col0=%d + %lld exceed F_pad=%d", col0, (long long)(2 * D * ng), F_pad);
+  if (B == 0) return GWX_OK;
+  if (!y || !features) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN8(y);
+  GWX_ALIGN8(features);
+  GWX_TRY(check_ws(workspace, workspace_bytes, gwx_spectral_features_workspace(B, D, N)));
+  GWX_TRY(ensure_init());
+  return launched(launch_lag_features(y, B, D, N, k_lo, group, F_pad, col0, workspace, features, as_stream(stream)),
+                  "lag_features");
+}
+
 int gwx_proposal_targets(const double* theta, int64_t B, const double* mean3, const double* scale3, float* targets,
                          void* stream) {
   if (B < 0) return fail(GWX_ESHAPE, "B=%lld", (long long)B);
@@ -759,7 +781,7 @@ int check_flow_shape(const gwx_flow_shape* sh) {
   if (8 + (int64_t)sh->context > lim) return fail(GWX_ESHAPE, "context width %d", sh->context);
   if (sh->layers < 1 || sh->layers > 64) return fail(GWX_ESHAPE, "layers=%d outside [1, 64]", sh->layers);
   if (sh->group < 1) return fail(GWX_EINVAL, "group=%d", sh->group);
-  if (sh->cross != 0 && sh->cross != 1) return fail(GWX_EINVAL, "cross=%d", sh->cross);
+  if (sh->extra & ~(GWX_FLOW_CROSS | GWX_FLOW_LAG)) return fail(GWX_EINVAL, "extra=%d", sh->extra);
   return GWX_OK;
 }
 
@@ -786,11 +808,12 @@ int check_flow_windows(const gwx_flow_shape* sh, int D, int64_t N, double fs, do
   GWX_TRY(band_start(f_lo, fs / (double)N, N / 2, k_lo));
   if (sh->group > N / 2) return fail(GWX_EINVAL, "group %d", sh->group);
   const int64_t ng = (N / 2 - *k_lo) / sh->group;
-  const int64_t need = (int64_t)D * ng * (1 + (sh->cross ? D - 1 : 0));
+  const int64_t need = (int64_t)D * ng * (1 + ((sh->extra & GWX_FLOW_CROSS) ? D - 1 : 0) +
+                                           ((sh->extra & GWX_FLOW_LAG) ? 2 : 0));
   if (sh->features < need)
-    return fail(GWX_ESHAPE, "F=%d is below the %lld feature columns (D x groups%s)", sh->features, (long long)need,
-                sh->cross ? " x D with the cross spectra" : "");
-  if (sh->cross && D < 2) return fail(GWX_ESHAPE, "cross-spectral features need two detectors or more");
+    return fail(GWX_ESHAPE, "F=%d is below the %lld feature columns (D x groups x %lld)", sh->features,
+                (long long)need, (long long)(need / (D * ng > 0 ? D * ng : 1)));
+  if ((sh->extra & GWX_FLOW_CROSS) && D < 2) return fail(GWX_ESHAPE, "cross-spectral features need two detectors or more");
   return GWX_OK;
 }
 

@@ -101,6 +101,11 @@ cudaError_t launch_cross_from_spectrum(const void* Y, int64_t B, int D, int64_t 
                                        int col0, void* out, cudaStream_t s);
 cudaError_t launch_cross_features(const float* y, int64_t B, int D, int64_t N, int k_lo, int G, int F_pad, int col0,
                                   void* ws, void* out, cudaStream_t s);
+// Lag-one spectral products (k_lag_features), from a spectrum or from y.
+cudaError_t launch_lag_from_spectrum(const void* Y, int64_t B, int D, int64_t N, int k_lo, int G, int F_pad, int col0,
+                                     void* out, cudaStream_t s);
+cudaError_t launch_lag_features(const float* y, int64_t B, int D, int64_t N, int k_lo, int G, int F_pad, int col0,
+                                void* ws, void* out, cudaStream_t s);
 cudaError_t launch_targets(const double* theta, int64_t B, const double* mean, const double* scale, float* t,
                            cudaStream_t s);
 cudaError_t launch_gauss_nll(const float* out, int ldo, const float* t, int P, int B, float* loss, double* mean,

@@ -326,11 +326,11 @@ struct Carve {
 
 struct FlowDims {
   int64_t F, G, He, C, K, H;
-  int cross;
+  int extra;
 };
 
 FlowDims dims_of(const gwx_flow_shape& sh) {
-  return FlowDims{sh.features, sh.group, sh.embed_hidden, sh.context, sh.layers, sh.hidden, sh.cross};
+  return FlowDims{sh.features, sh.group, sh.embed_hidden, sh.context, sh.layers, sh.hidden, sh.extra};
 }
 
 }  // namespace
@@ -444,9 +444,13 @@ cudaError_t embed_forward(const FlowDims& d, const Params& P, const float* y, in
                           void* fws, __nv_bfloat16* feat, __nv_bfloat16* h1, __nv_bfloat16* h2, __nv_bfloat16* ctx,
                           cudaStream_t s) {
   FL_TRY(launch_features(y, R, D, N, k_lo, (int)d.G, (int)d.F, fws, feat, s));
-  if (d.cross)
-    FL_TRY(launch_cross_from_spectrum(fws, R, D, N, k_lo, (int)d.G, (int)d.F, (int)(D * ((N / 2 - k_lo) / d.G)), feat,
-                                      s));
+  const int ng = (int)((N / 2 - k_lo) / d.G);
+  int col = D * ng;
+  if (d.extra & GWX_FLOW_CROSS) {
+    FL_TRY(launch_cross_from_spectrum(fws, R, D, N, k_lo, (int)d.G, (int)d.F, col, feat, s));
+    col += D * (D - 1) * ng;
+  }
+  if (d.extra & GWX_FLOW_LAG) FL_TRY(launch_lag_from_spectrum(fws, R, D, N, k_lo, (int)d.G, (int)d.F, col, feat, s));
   FL_TRY(launch_gemm_bf16(feat, P.W(0), h1, R, d.He, d.F, true, P.b(1), GWX_ACT_RELU, 0, s));
   FL_TRY(launch_gemm_bf16(h1, P.W(2), h2, R, d.He, d.He, true, P.b(3), GWX_ACT_RELU, 0, s));
   return launch_gemm_bf16(h2, P.W(4), ctx, R, d.C, d.He, true, P.b(5), GWX_ACT_NONE, 0, s);

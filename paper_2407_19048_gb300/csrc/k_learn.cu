@@ -71,6 +71,33 @@ __global__ void k_cross_features(const float2* __restrict__ Y, int D, int64_t F,
   row[(2 * p + 1) * ng + g] = __float2bfloat16_rn(im * inv);
 }
 
+// Normalised lag-one spectral product of detector d over group g:
+// lam = sum Y_k conj(Y_{k+1}) / sqrt(sum |Y_k|^2 sum |Y_{k+1}|^2); Re lam to column
+// col0 + 2 d ng + g, Im lam to col0 + (2 d + 1) ng + g.
+__global__ void k_lag_features(const float2* __restrict__ Y, int D, int64_t F, int k_lo, int G, int ng, int F_pad,
+                               int col0, int64_t B, __nv_bfloat16* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B * D * ng) return;
+  const int64_t b = i / (D * ng);
+  const int rem = (int)(i - b * D * ng);
+  const int d = rem / ng, g = rem % ng;
+  const float2* y = Y + (b * D + d) * F + k_lo + (int64_t)g * G;
+  float re = 0.f, im = 0.f, na = 0.f, nb = 0.f;
+  float2 u = y[0];
+  for (int k = 0; k < G; ++k) {
+    const float2 v = y[k + 1];
+    re = fmaf(u.x, v.x, fmaf(u.y, v.y, re));
+    im = fmaf(u.y, v.x, fmaf(-u.x, v.y, im));
+    na = fmaf(u.x, u.x, fmaf(u.y, u.y, na));
+    nb = fmaf(v.x, v.x, fmaf(v.y, v.y, nb));
+    u = v;
+  }
+  const float inv = rsqrtf(na * nb);
+  __nv_bfloat16* row = out + b * F_pad + col0;
+  row[2 * d * ng + g] = __float2bfloat16_rn(re * inv);
+  row[(2 * d + 1) * ng + g] = __float2bfloat16_rn(im * inv);
+}
+
 struct Std3 {
   double mean[3], scale[3];
 };
@@ -233,6 +260,24 @@ cudaError_t launch_cross_from_spectrum(const void* Y, int64_t B, int D, int64_t 
                                                                    k_lo, G, ng, F_pad, col0, B,
                                                                    reinterpret_cast<__nv_bfloat16*>(out));
   return cudaGetLastError();
+}
+
+cudaError_t launch_lag_from_spectrum(const void* Y, int64_t B, int D, int64_t N, int k_lo, int G, int F_pad, int col0,
+                                     void* out, cudaStream_t s) {
+  const int ng = (int)((N / 2 - k_lo) / G);
+  const int64_t total = B * (int64_t)D * ng;
+  if (total == 0) return cudaSuccess;
+  k_lag_features<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(reinterpret_cast<const float2*>(Y), D, N / 2 + 1,
+                                                                 k_lo, G, ng, F_pad, col0, B,
+                                                                 reinterpret_cast<__nv_bfloat16*>(out));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lag_features(const float* y, int64_t B, int D, int64_t N, int k_lo, int G, int F_pad, int col0,
+                                void* ws, void* out, cudaStream_t s) {
+  cudaError_t e = launch_rfft_rows(y, B * D, N, reinterpret_cast<float2*>(ws), s);
+  if (e != cudaSuccess) return e;
+  return launch_lag_from_spectrum(ws, B, D, N, k_lo, G, F_pad, col0, out, s);
 }
 
 cudaError_t launch_cross_features(const float* y, int64_t B, int D, int64_t N, int k_lo, int G, int F_pad, int col0,

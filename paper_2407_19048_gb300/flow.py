@@ -17,7 +17,7 @@ from . import _lib
 
 class FlowPosterior:
     def __init__(self, workload, layers=16, hidden=256, context=64, embed_hidden=512, group=4, seed=0,
-                 device=None, lr=1e-3, weight_decay=2e-3, cross=True):
+                 device=None, lr=1e-3, weight_decay=2e-3, cross=True, lag=True):
         import torch
         import paper_2407_19048_gb300 as gwx
         self.gwx = gwx
@@ -28,10 +28,11 @@ class FlowPosterior:
         k_lo = math.ceil(self.f_lo * self.N / self.fs - 1e-9)
         ng = (self.N // 2 - k_lo) // group
         cross = 1 if (cross and self.D > 1) else 0
-        cols = self.D * ng * (1 + (self.D - 1) * cross)
+        lag = 1 if lag else 0
+        cols = self.D * ng * (1 + (self.D - 1) * cross + 2 * lag)
         F = ((cols + 7) // 8) * 8
         self.shape = {"features": F, "group": group, "embed_hidden": embed_hidden, "context": context,
-                      "layers": layers, "hidden": hidden, "cross": cross}
+                      "layers": layers, "hidden": hidden, "extra": gwx.FLOW_CROSS * cross + gwx.FLOW_LAG * lag}
         self.n_params, self.offsets = gwx.flow_layout(self.shape)
         self.params = torch.zeros(self.n_params, dtype=torch.float32, device=self.dev)
         self.params16 = torch.zeros(self.n_params, dtype=torch.bfloat16, device=self.dev)
@@ -135,7 +136,7 @@ class FlowPosterior:
         with open(path, "wb") as fh:
             fh.write(self._MAGIC)
             np.array([sh["features"], sh["group"], sh["embed_hidden"], sh["context"], sh["layers"], sh["hidden"],
-                      sh["cross"], self.steps, -1 if next_step is None else next_step, self.n_params],
+                      sh["extra"], self.steps, -1 if next_step is None else next_step, self.n_params],
                      dtype="<i8").tofile(fh)
             np.array(self.mean + self.scale, dtype="<f8").tofile(fh)
             for t in (self.params, self.m, self.v):
@@ -152,7 +153,7 @@ class FlowPosterior:
             hdr = [int(v) for v in np.fromfile(fh, dtype="<i8", count=10)]
             sh = self.shape
             want = [sh["features"], sh["group"], sh["embed_hidden"], sh["context"], sh["layers"], sh["hidden"],
-                    sh["cross"]]
+                    sh["extra"]]
             if hdr[:7] != want or hdr[9] != self.n_params:
                 raise ValueError("checkpoint shape %s differs from this flow %s" % (hdr[:7], want))
             ms = np.fromfile(fh, dtype="<f8", count=16)

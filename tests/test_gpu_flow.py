@@ -68,7 +68,7 @@ MEAN, SCALE = _std()
 def model(gwx):
     from paper_2407_19048_gb300.flow import FlowPosterior
     fp = FlowPosterior(WL, layers=4, hidden=64, context=32, embed_hidden=64, group=GROUP, seed=1)
-    assert fp.shape["cross"] == 1
+    assert fp.shape["extra"] == 3          # cross spectra and lag-one products
     shape = workloads.flow_shape(features=fp.shape["features"], group=GROUP, embed_hidden=64, context=32, layers=4,
                                  hidden=64)
     params = workloads.random_flow_params(301, shape, gain=1.0, last_gain=0.5)
@@ -77,16 +77,19 @@ def model(gwx):
     return fp, params
 
 
-def oracle_features(y, F, cross=True):
+def oracle_features(y, F, cross=True, lag=True):
     """bfloat16-rounded features of windows y from the oracle's FP64 spectrum: log group
-    powers, then (cross) the cross-spectral columns from column D ng."""
+    powers, then the cross-spectral columns, then the lag-one columns."""
     y = np.asarray(y, dtype=np.float64)
     k_lo = int(math.ceil(WL["f_lo"] * WL["N"] / WL["fs"] - 1e-9))
     f = learn.features(y, k_lo, GROUP, F)
-    if cross:
-        D, ng = y.shape[1], (WL["N"] // 2 - k_lo) // GROUP
-        c = learn.cross_features(y, k_lo, GROUP)
-        f[:, D * ng:D * ng + c.shape[1]] = c
+    D, ng = y.shape[1], (WL["N"] // 2 - k_lo) // GROUP
+    col = D * ng
+    for on, fn in ((cross, learn.cross_features), (lag, learn.lag_features)):
+        if on:
+            c = fn(y, k_lo, GROUP)
+            f[:, col:col + c.shape[1]] = c
+            col += c.shape[1]
     return fl.round_bf16(f)
 
 

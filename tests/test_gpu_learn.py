@@ -46,7 +46,7 @@ def test_spectral_features(gwx):
     assert np.all(np.abs(got - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-4)
 
 
-def test_cross_features(gwx):
+def test_cross_and_lag_features(gwx):
     wl = workloads.workload("hl3")
     y = workloads.random_strain(206, (8, 3, wl["N"]), 1.0)
     # a common chirp-like tone in all three detectors with different delays and gains
@@ -58,15 +58,17 @@ def test_cross_features(gwx):
     k_lo = int(np.ceil(wl["f_lo"] * wl["N"] / wl["fs"]))
     G = 8
     ng = (wl["N"] // 2 - k_lo) // G
-    F = ((3 * ng + 6 * ng + 7) // 8) * 8
+    F = ((3 * ng + 6 * ng + 6 * ng + 7) // 8) * 8
     out = gwx.spectral_features(cuda(y), wl["fs"], wl["f_lo"], G, F)
     gwx.cross_features(cuda(y), wl["fs"], wl["f_lo"], G, F, 3 * ng, out)
+    gwx.lag_features(cuda(y), wl["fs"], wl["f_lo"], G, F, 9 * ng, out)
     got = host(out.float()).astype(np.float64)
     ref = np.zeros_like(got)
     ref[:, :3 * ng] = learn.features(y.astype(np.float64), k_lo, G, F)[:, :3 * ng]
     ref[:, 3 * ng:9 * ng] = learn.cross_features(y.astype(np.float64), k_lo, G)
+    ref[:, 9 * ng:15 * ng] = learn.lag_features(y.astype(np.float64), k_lo, G)
     assert np.all(np.abs(got - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-4)
-    assert np.all(got[:, 9 * ng:] == 0.0)
+    assert np.all(got[:, 15 * ng:] == 0.0)
 
 
 def test_targets_and_gauss_nll(gwx):

@@ -178,3 +178,37 @@ def test_cross_features_phase_of_a_delayed_tone():
     # Y1 = Y0 e^{-2 pi i k tau / N}, so rho = e^{+2 pi i k0 tau / N}
     assert abs(f[0, g] - np.cos(2 * np.pi * k0 * tau / N)) < 1e-9
     assert abs(f[0, ng + g] - np.sin(2 * np.pi * k0 * tau / N)) < 1e-9
+
+
+def test_lag_features_brute_force_and_track():
+    rng = np.random.default_rng(71)
+    B, D, N, k_lo, G = 2, 2, 64, 3, 4
+    y = rng.normal(size=(B, D, N))
+    got = learn.lag_features(y, k_lo, G)
+    n = np.arange(N)
+    Y = np.array([[[np.sum(y[b, d] * np.exp(-2j * np.pi * k * n / N)) for k in range(N // 2 + 1)]
+                   for d in range(D)] for b in range(B)])
+    ng = (N // 2 - k_lo) // G
+    for d in range(D):
+        for g in range(ng):
+            ks = range(k_lo + g * G, k_lo + (g + 1) * G)
+            num = sum(Y[:, d, k] * np.conj(Y[:, d, k + 1]) for k in ks)
+            den = np.sqrt(sum(abs(Y[:, d, k]) ** 2 for k in ks) * sum(abs(Y[:, d, k + 1]) ** 2 for k in ks))
+            np.testing.assert_allclose(got[:, 2 * d * ng + g], (num / den).real, atol=1e-12)
+            np.testing.assert_allclose(got[:, (2 * d + 1) * ng + g], (num / den).imag, atol=1e-12)
+    re, im = got[:, :ng], got[:, ng:2 * ng]
+    assert np.all(re * re + im * im <= 1.0 + 1e-12)
+    # an impulse at sample tau: Y_k = e^{-2 pi i k tau / N}, so lam = e^{+2 pi i tau / N} in every group
+    tau = 11
+    imp = np.zeros((1, 1, N))
+    imp[0, 0, tau] = 1.0
+    f = learn.lag_features(imp, k_lo, G)
+    np.testing.assert_allclose(f[0, :ng], np.cos(2 * np.pi * tau / N), atol=1e-12)
+    np.testing.assert_allclose(f[0, ng:], np.sin(2 * np.pi * tau / N), atol=1e-12)
+    # a common circular shift by s samples rotates every lam by 2 pi s / N
+    s = 5
+    f0 = learn.lag_features(y, k_lo, G)
+    f1 = learn.lag_features(np.roll(y, s, axis=-1), k_lo, G)
+    l0 = f0[:, :ng] + 1j * f0[:, ng:2 * ng]
+    l1 = f1[:, :ng] + 1j * f1[:, ng:2 * ng]
+    np.testing.assert_allclose(l1, l0 * np.exp(2j * np.pi * s / N), atol=1e-12)
