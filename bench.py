@@ -408,12 +408,13 @@ def learned_leg(gwx, torch, rank, steps=2000, events=32, per_event=4000):
                     "merger time known in both proposals"}
 
 
-def flow_leg(gwx, torch, rank, steps=6000, events=32, per_event=4000, pp_events=200, pp_samples=500, lr=3e-4,
-             cross=True):
+def flow_leg(gwx, torch, rank, steps=8000, events=32, per_event=4000, pp_events=200, pp_samples=500, lr=6e-4,
+             cross=True, batch=4096, layers=16, hidden=256, clip=1.0):
     """The conditional coupling flow (16 affine coupling layers, conditioners 72 -> 256 ->
-    256 -> 8; embedding 984 -> 512 -> 512 -> 64 on log group powers and inter-detector
-    cross spectra; tcgen05 dense layers) trained with AdamW (lr 3e-4, weight decay 2e-3)
-    on 512-draw batches of the two-detector workload (one C-ABI call per step); then
+    256 -> 8; embedding 1968 -> 512 -> 512 -> 64 on log group powers, inter-detector cross
+    spectra and lag-one spectral products; tcgen05 dense layers) trained with AdamW (lr
+    6e-4, weight decay 2e-3, gradient norm clipped at 1) on 4096-draw batches of the
+    two-detector workload, 8000 steps = 32.8 M simulations (one C-ABI call per step); then
     posterior sampling (20,000 draws of one event, the paper's inference size), importance
     sampling of 32 events x 4000 draws against the prior as proposal (spins and merger
     time known to both), and a PP test of the flow's marginals."""
@@ -421,10 +422,10 @@ def flow_leg(gwx, torch, rank, steps=6000, events=32, per_event=4000, pp_events=
     import numpy as np
     import paper_2407_19048_gb300.simulator  # noqa: F401
     from paper_2407_19048_gb300.flow import FlowPosterior
-    wl = workloads.workload("small", B=512)
+    wl = workloads.workload("small", B=batch)
     sim = gwx.simulator.Simulator(wl, pipeline=True, background_every=16)
-    fp = FlowPosterior(wl, layers=16, hidden=256, context=64, embed_hidden=512, group=4, seed=0, lr=lr,
-                       weight_decay=2e-3, cross=cross)
+    fp = FlowPosterior(wl, layers=layers, hidden=hidden, context=64, embed_hidden=512, group=4, seed=0, lr=lr,
+                       weight_decay=2e-3, cross=cross, clip=clip)
     losses = []
     y, th, _ = sim.step(step_counter(rank, 40000))
     fp.train_step(y, th, update=False)          # workspace allocation outside the timing
@@ -441,7 +442,7 @@ def flow_leg(gwx, torch, rank, steps=6000, events=32, per_event=4000, pp_events=
     # training step alone (no simulation) on one resident batch
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     y1, th1 = y.clone(), th.clone()
-    fp_t = FlowPosterior(wl, layers=16, hidden=256, context=64, embed_hidden=512, group=4, seed=1)
+    fp_t = FlowPosterior(wl, layers=layers, hidden=hidden, context=64, embed_hidden=512, group=4, seed=1)
     for _ in range(3):
         fp_t.train_step(y1, th1)
     ev0.record()
@@ -502,8 +503,8 @@ def flow_leg(gwx, torch, rank, steps=6000, events=32, per_event=4000, pp_events=
         n = len(u)
         ks.append(float(max(np.max(np.arange(1, n + 1) / n - u), np.max(u - np.arange(n) / n))))
     del sim, sim_ev, sim_pp
-    return {"shape": fp.shape, "params": fp.n_params, "train_steps": steps, "batch": 512, "train_s": train_s,
-            "simulations_per_s": steps * 512 / train_s, "train_step_ms": step_ms, "loss": losses,
+    return {"shape": fp.shape, "params": fp.n_params, "train_steps": steps, "batch": batch, "train_s": train_s,
+            "simulations_per_s": steps * batch / train_s, "train_step_ms": step_ms, "loss": losses,
             "sample_20000_ms": {"p50": lat[len(lat) // 2] * 1e3, "min": lat[0] * 1e3, "max": lat[-1] * 1e3},
             "events": events, "samples_per_event": per_event, "importance_sampling": res,
             "pp_test": {"events": pp_events, "draws_per_event": pp_samples, "ks_distance": ks,

@@ -390,6 +390,13 @@ int gwx_gauss_nll(const float* out, int ldo, const float* targets, int P, int64_
                   double* loss_mean, float* grad, void* stream);
 int gwx_adamw(float* param, const float* grad, float* m, float* v, int64_t n, double lr, double beta1,
               double beta2, double eps, double weight_decay, int64_t step, void* param_bf16, void* stream);
+/* gwx_adamw_clip: gwx_adamw on the gradients scaled by min(1, clip / |g|), |g| the
+ *   Euclidean norm of all n gradients (summed in FP64); grad itself is not modified.
+ *   Workspace gwx_adamw_clip_workspace() bytes. */
+size_t gwx_adamw_clip_workspace(void);
+int gwx_adamw_clip(float* param, const float* grad, float* m, float* v, int64_t n, double lr, double beta1,
+                   double beta2, double eps, double weight_decay, int64_t step, double clip, void* param_bf16,
+                   void* workspace, size_t workspace_bytes, void* stream);
 int gwx_sample_proposal(const float* net_out, int ldn, const double* mean3, const double* scale3,
                         const gwx_prior* prior, const double* truth, int64_t E, const int64_t* event_offsets,
                         int64_t S, uint64_t seed, uint32_t counter, int flags, double* theta,
@@ -497,13 +504,14 @@ int gwx_flow_proposal(const float* x, const float* z, const float* sum_s, int64_
 /* One training step on a simulated batch: whitened strain y [B][D][N] (FP32) and its
  * parameters theta [GWX_NPARAM][B]: features, embedding, density pass, loss, backward
  * into grads (flat, same layout as params; the whole array is rewritten), then (step >= 1)
- * gwx_adamw over the flat array with step counter `step`; step 0 computes the loss and
+ * gwx_adamw over the flat array with step counter `step` (gwx_adamw_clip when clip > 0:
+ * gradients scaled to a Euclidean norm of at most clip); step 0 computes the loss and
  * gradients only.  *loss_mean (device double) = batch mean of -ln q_x.  B a multiple of 8
  * in [8, 65535 * 32].  Workspace gwx_flow_train_workspace(shape, B, D, N). */
 size_t gwx_flow_train_workspace(const gwx_flow_shape* shape, int64_t B, int D, int64_t N);
 int gwx_flow_train_step(const gwx_flow_shape* shape, float* params, void* params_bf16, float* grads, float* m,
                         float* v, int64_t step, double lr, double beta1, double beta2, double eps,
-                        double weight_decay, const double* mean8, const double* scale8, const float* y,
+                        double weight_decay, double clip, const double* mean8, const double* scale8, const float* y,
                         const double* theta, int64_t B, int D, int64_t N, double fs, double f_lo,
                         double* loss_mean, void* workspace, size_t workspace_bytes, void* stream);
 

@@ -124,9 +124,14 @@ def gauss_nll(out, t):
     return loss, loss.mean(), g
 
 
-def adamw(p, g, m, v, lr, beta1, beta2, eps, wd, step):
-    """One AdamW step (step counts from 1).  Returns (p', m', v')."""
+def adamw(p, g, m, v, lr, beta1, beta2, eps, wd, step, clip=None):
+    """One AdamW step (step counts from 1).  Returns (p', m', v').  With clip, the
+    gradient is first scaled by min(1, clip / |g|) (global Euclidean norm)."""
     p, g, m, v = (np.asarray(a, dtype=np.float64) for a in (p, g, m, v))
+    if clip is not None:
+        norm = math.sqrt(float(np.sum(g * g)))
+        if norm > clip:
+            g = g * (clip / norm)
     m = beta1 * m + (1.0 - beta1) * g
     v = beta2 * v + (1.0 - beta2) * g * g
     mh = m / (1.0 - beta1 ** step)

@@ -26,7 +26,7 @@ __all__ = ["GwxError", "version", "init", "detector_geometry", "sample_prior", "
            "colored_noise", "welch_psd", "inject", "whiten", "unwhiten", "simulate_batch", "log_likelihood",
            "importance_weights", "gemm_bf16", "dense_bf16", "dense_bf16_backward", "gemm_autotune", "spectral_features",
            "cross_features", "lag_features", "proposal_targets",
-           "gauss_nll", "adamw", "sample_proposal", "device_status", "rfft", "irfft",
+           "gauss_nll", "adamw", "adamw_clip", "sample_proposal", "device_status", "rfft", "irfft",
            "workspace_bytes", "TAYLORF2", "IMRPHENOMD", "DETECTORS"]
 
 
@@ -408,6 +408,15 @@ def adamw(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, weight_
                                  weight_decay, step, _ptr(param_bf16), _stream()))
 
 
+def adamw_clip(param, grad, m, v, step, lr, clip, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0,
+               param_bf16=None):
+    """One AdamW step in place with the gradients scaled to a norm of at most clip."""
+    lib = _lib.load()
+    ws, nb = _workspace(lib.gwx_adamw_clip_workspace(), param.device)
+    _check(lib.gwx_adamw_clip(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(), lr, beta1, beta2, eps,
+                              weight_decay, step, clip, _ptr(param_bf16), _ptr(ws), nb, _stream()))
+
+
 def sample_proposal(prior, truth, event_offsets, seed, counter, net_out=None, mean=None, scale=None,
                     fix_angles=False):
     """Importance-sampling draws: returns (theta [11][S] float64, log_ratio [S] float64)."""
@@ -601,7 +610,7 @@ def flow_proposal(x, z, sum_s, mean8, scale8, prior, truth, event_offsets, seed,
 
 
 def flow_train_step(shape, params, params_bf16, grads, m, v, step, lr, mean8, scale8, y, theta, fs, f_lo,
-                    beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, loss_mean=None, workspace=None):
+                    beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, clip=0.0, loss_mean=None, workspace=None):
     """One training step (step 0: loss and gradients only).  Returns loss_mean (device
     float64 [1]).  `workspace` may be a preallocated (tensor, bytes) pair."""
     torch = _torch()
@@ -614,7 +623,8 @@ def flow_train_step(shape, params, params_bf16, grads, m, v, step, lr, mean8, sc
     ws, nb = workspace if workspace is not None else _workspace(
         lib.gwx_flow_train_workspace(ctypes.byref(sh), B, D, N), y.device)
     _check(lib.gwx_flow_train_step(ctypes.byref(sh), _ptr(params), _ptr(params_bf16), _ptr(grads), _ptr(m), _ptr(v),
-                                   step, lr, beta1, beta2, eps, weight_decay, _host8(mean8), _host8(scale8), _ptr(y),
+                                   step, lr, beta1, beta2, eps, weight_decay, clip, _host8(mean8), _host8(scale8),
+                                   _ptr(y),
                                    _ptr(theta), B, D, N, fs, f_lo, _ptr(loss_mean), _ptr(ws), nb, _stream()))
     return loss_mean
 

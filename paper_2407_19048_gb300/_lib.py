@@ -82,6 +82,9 @@ SIGNATURES = {
     "gwx_proposal_targets": (c_int, [c_vp, c_i64, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl), c_vp, c_vp]),
     "gwx_gauss_nll": (c_int, [c_vp, c_int, c_vp, c_int, c_i64, c_vp, c_vp, c_vp, c_vp]),
     "gwx_adamw": (c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl, c_i64, c_vp, c_vp]),
+    "gwx_adamw_clip_workspace": (c_size, []),
+    "gwx_adamw_clip": (c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl, c_i64, c_dbl, c_vp,
+                               c_vp, c_size, c_vp]),
     "gwx_sample_proposal": (c_int, [c_vp, c_int, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl),
                                     ctypes.POINTER(GwxPrior), c_vp, c_i64, c_vp, c_i64, c_u64, c_u32, c_int, c_vp, c_vp,
                                     c_vp]),
@@ -101,7 +104,7 @@ SIGNATURES = {
                                   c_vp, c_vp, c_vp]),
     "gwx_flow_train_workspace": (c_size, [c_shp, c_i64, c_int, c_i64]),
     "gwx_flow_train_step": (c_int, [c_shp, c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl,
-                                    c_d8, c_d8, c_vp, c_vp, c_i64, c_int, c_i64, c_dbl, c_dbl, c_vp, c_vp, c_size,
+                                    c_dbl, c_d8, c_d8, c_vp, c_vp, c_i64, c_int, c_i64, c_dbl, c_dbl, c_vp, c_vp, c_size,
                                     c_vp]),
     "gwx_flow_log_prob_workspace": (c_size, [c_shp, c_i64, c_int, c_i64]),
     "gwx_flow_log_prob": (c_int, [c_shp, c_vp, c_vp, c_d8, c_d8, c_vp, c_vp, c_i64, c_int, c_i64, c_dbl, c_dbl, c_vp,

@@ -715,6 +715,24 @@ int gwx_adamw(float* param, const float* grad, float* m, float* v, int64_t n, do
                   "adamw");
 }
 
+size_t gwx_adamw_clip_workspace(void) { return align_up(adamw_clip_ws()); }
+
+int gwx_adamw_clip(float* param, const float* grad, float* m, float* v, int64_t n, double lr, double beta1,
+                   double beta2, double eps, double weight_decay, int64_t step, double clip, void* param_bf16,
+                   void* workspace, size_t workspace_bytes, void* stream) {
+  if (n < 0) return fail(GWX_ESHAPE, "n=%lld", (long long)n);
+  if (step < 1 || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0) || !(lr >= 0.0))
+    return fail(GWX_EINVAL, "AdamW hyper-parameters (step counts from 1)");
+  if (!(clip > 0.0) || !isfinite(clip)) return fail(GWX_EINVAL, "clip=%g must be positive", clip);
+  if (n == 0) return GWX_OK;
+  if (!param || !grad || !m || !v) return fail(GWX_EINVAL, "NULL array");
+  GWX_TRY(check_ws(workspace, workspace_bytes, gwx_adamw_clip_workspace()));
+  GWX_TRY(ensure_init());
+  return launched(launch_adamw_clip(param, grad, m, v, n, lr, beta1, beta2, eps, weight_decay, step, clip, param_bf16,
+                                    workspace, as_stream(stream)),
+                  "adamw_clip");
+}
+
 int gwx_sample_proposal(const float* net_out, int ldn, const double* mean3, const double* scale3,
                         const gwx_prior* prior, const double* truth, int64_t E, const int64_t* event_offsets,
                         int64_t S, uint64_t seed, uint32_t counter, int flags, double* theta, double* log_ratio,
@@ -956,7 +974,7 @@ size_t gwx_flow_train_workspace(const gwx_flow_shape* shape, int64_t B, int D, i
 
 int gwx_flow_train_step(const gwx_flow_shape* shape, float* params, void* params_bf16, float* grads, float* m,
                         float* v, int64_t step, double lr, double beta1, double beta2, double eps,
-                        double weight_decay, const double* mean8, const double* scale8, const float* y,
+                        double weight_decay, double clip, const double* mean8, const double* scale8, const float* y,
                         const double* theta, int64_t B, int D, int64_t N, double fs, double f_lo,
                         double* loss_mean, void* workspace, size_t workspace_bytes, void* stream) {
   GWX_TRY(check_flow_shape(shape));
@@ -977,8 +995,9 @@ int gwx_flow_train_step(const gwx_flow_shape* shape, float* params, void* params
   GWX_ALIGN8(loss_mean);
   GWX_TRY(check_ws(workspace, workspace_bytes, gwx_flow_train_workspace(shape, B, D, N)));
   GWX_TRY(ensure_init());
+  if (!(clip >= 0.0) || !isfinite(clip)) return fail(GWX_EINVAL, "clip=%g", clip);
   return launched(flow_train_step(*shape, params, params_bf16, grads, m, v, step, lr, beta1, beta2, eps, weight_decay,
-                                  mean8, scale8, y, theta, B, D, N, k_lo, loss_mean, workspace, as_stream(stream)),
+                                  clip, mean8, scale8, y, theta, B, D, N, k_lo, loss_mean, workspace, as_stream(stream)),
                   "flow_train_step");
 }
 

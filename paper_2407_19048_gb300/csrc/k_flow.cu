@@ -475,7 +475,7 @@ size_t dense_bw_max(const FlowDims& d, int64_t B) {
 struct TrainWs {
   __nv_bfloat16 *feat, *h1, *h2, *ctx, *X, *g1, *g2;
   float *xs, *o, *sum_s, *loss, *G, *Gu, *d_o, *dA, *dB, *dctx;
-  void *fws, *dws;
+  void *fws, *dws, *clip;
   size_t bytes;
 };
 
@@ -502,6 +502,7 @@ TrainWs carve_train(const FlowDims& d, int64_t B, int D, int64_t N, void* base) 
   w.dB = c.take<float>(B * maxw);
   w.dctx = c.take<float>(B * d.C);
   w.dws = c.take<char>((int64_t)dense_bw_max(d, B));
+  w.clip = c.take<char>((int64_t)adamw_clip_ws());
   w.bytes = c.used;
   return w;
 }
@@ -532,7 +533,7 @@ size_t flow_train_ws(const gwx_flow_shape& sh, int64_t B, int D, int64_t N) {
 }
 
 cudaError_t flow_train_step(const gwx_flow_shape& sh, float* params, void* params_bf16, float* grads, float* m,
-                            float* v, int64_t step, double lr, double b1, double b2, double eps, double wd,
+                            float* v, int64_t step, double lr, double b1, double b2, double eps, double wd, double clip,
                             const double* mean8, const double* scale8, const float* y, const double* theta, int64_t B,
                             int D, int64_t N, int k_lo, double* loss_mean, void* ws, cudaStream_t s) {
   const FlowDims d = dims_of(sh);
@@ -577,7 +578,12 @@ cudaError_t flow_train_step(const gwx_flow_shape& sh, float* params, void* param
                                grads + P.off[3], w.dws, 0, s));
   FL_TRY(launch_dense_backward(w.feat, P.W(0), P.b(1), w.dB, B, d.He, d.F, GWX_ACT_RELU, nullptr, grads + P.off[0],
                                grads + P.off[1], w.dws, 0, s));
-  if (step >= 1) FL_TRY(launch_adamw(params, grads, m, v, n_params, lr, b1, b2, eps, wd, step, params_bf16, s));
+  if (step >= 1) {
+    if (clip > 0.0)
+      FL_TRY(launch_adamw_clip(params, grads, m, v, n_params, lr, b1, b2, eps, wd, step, clip, params_bf16, w.clip, s));
+    else
+      FL_TRY(launch_adamw(params, grads, m, v, n_params, lr, b1, b2, eps, wd, step, params_bf16, s));
+  }
   return cudaSuccess;
 }
 

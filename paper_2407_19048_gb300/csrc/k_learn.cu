@@ -158,6 +158,56 @@ __global__ void k_adamw(float* __restrict__ p, const float* __restrict__ g, floa
   if (p16) p16[i] = __float2bfloat16_rn(pi);
 }
 
+// Gradient-norm clipping: per-block partial sums of g^2 (FP64), then one block turns
+// them into the factor min(1, clip / |g|) that k_adamw_scaled applies to every gradient.
+constexpr int CLIP_BLOCKS = 256;
+
+__global__ void __launch_bounds__(256) k_sumsq(const float* __restrict__ g, int64_t n, double* __restrict__ part) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += (double)g[i] * (double)g[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void __launch_bounds__(256) k_clip_scale(const double* __restrict__ part, int nparts, double clip,
+                                                    float* __restrict__ scale) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += part[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double norm = sqrt(red[0]);
+    *scale = (float)(norm > clip ? clip / norm : 1.0);
+  }
+}
+
+__global__ void k_adamw_scaled(float* __restrict__ p, const float* __restrict__ g, const float* __restrict__ gscale,
+                               float* __restrict__ m, float* __restrict__ v, int64_t n, float lr, float b1, float b2,
+                               float eps, float wd, float c1, float c2, __nv_bfloat16* __restrict__ p16) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i] * __ldg(gscale);
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  const float pi = p[i] - lr * ((mi / c1) / (sqrtf(vi / c2) + eps) + wd * p[i]);
+  p[i] = pi;
+  if (p16) p16[i] = __float2bfloat16_rn(pi);
+}
+
 __global__ void k_proposal(const float* __restrict__ net, int ldn, Std3 st, gwx_prior pr,
                            const double* __restrict__ truth, int64_t E, const int64_t* __restrict__ off, int64_t S,
                            uint32_t k0, uint32_t k1, uint32_t counter, int fix_angles, double* __restrict__ theta,
@@ -309,6 +359,21 @@ cudaError_t launch_adamw(float* p, const float* g, float* m, float* v, int64_t n
   const float c1 = (float)(1.0 - pow(b1, (double)step)), c2 = (float)(1.0 - pow(b2, (double)step));
   k_adamw<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, g, m, v, n, (float)lr, (float)b1, (float)b2, (float)eps,
                                                       (float)wd, c1, c2, reinterpret_cast<__nv_bfloat16*>(p16));
+  return cudaGetLastError();
+}
+
+size_t adamw_clip_ws() { return CLIP_BLOCKS * sizeof(double) + 256; }
+
+cudaError_t launch_adamw_clip(float* p, const float* g, float* m, float* v, int64_t n, double lr, double b1, double b2,
+                              double eps, double wd, int64_t step, double clip, void* p16, void* ws, cudaStream_t s) {
+  double* part = reinterpret_cast<double*>(ws);
+  float* scale = reinterpret_cast<float*>(reinterpret_cast<char*>(ws) + CLIP_BLOCKS * sizeof(double));
+  k_sumsq<<<CLIP_BLOCKS, 256, 0, s>>>(g, n, part);
+  k_clip_scale<<<1, 256, 0, s>>>(part, CLIP_BLOCKS, clip, scale);
+  const float c1 = (float)(1.0 - pow(b1, (double)step)), c2 = (float)(1.0 - pow(b2, (double)step));
+  k_adamw_scaled<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, g, scale, m, v, n, (float)lr, (float)b1, (float)b2,
+                                                             (float)eps, (float)wd, c1, c2,
+                                                             reinterpret_cast<__nv_bfloat16*>(p16));
   return cudaGetLastError();
 }
 

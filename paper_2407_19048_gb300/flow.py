@@ -17,7 +17,7 @@ from . import _lib
 
 class FlowPosterior:
     def __init__(self, workload, layers=16, hidden=256, context=64, embed_hidden=512, group=4, seed=0,
-                 device=None, lr=1e-3, weight_decay=2e-3, cross=True, lag=True):
+                 device=None, lr=1e-3, weight_decay=2e-3, cross=True, lag=True, clip=1.0):
         import torch
         import paper_2407_19048_gb300 as gwx
         self.gwx = gwx
@@ -39,7 +39,7 @@ class FlowPosterior:
         self.grads = torch.zeros_like(self.params)
         self.m = torch.zeros_like(self.params)
         self.v = torch.zeros_like(self.params)
-        self.lr, self.wd = float(lr), float(weight_decay)
+        self.lr, self.wd, self.clip = float(lr), float(weight_decay), float(clip)
         self.steps = 0
         self._ws = {}
         self._loss = torch.zeros(1, dtype=torch.float64, device=self.dev)
@@ -108,7 +108,7 @@ class FlowPosterior:
         ws = self._workspace(("train", B), nb)
         step = self.steps + 1 if update else 0
         gwx.flow_train_step(self.shape, self.params, self.params16, self.grads, self.m, self.v, step, self.lr,
-                            self.mean, self.scale, y, theta, self.fs, self.f_lo, weight_decay=self.wd,
+                            self.mean, self.scale, y, theta, self.fs, self.f_lo, weight_decay=self.wd, clip=self.clip,
                             loss_mean=self._loss, workspace=ws)
         if update:
             self.steps += 1

@@ -71,6 +71,23 @@ def test_cross_and_lag_features(gwx):
     assert np.all(got[:, 15 * ng:] == 0.0)
 
 
+def test_adamw_clip(gwx):
+    rng = np.random.default_rng(207)
+    n = 100003
+    p = rng.normal(0, 1, n).astype(np.float32)
+    m = np.zeros(n, np.float32)
+    v = np.zeros(n, np.float32)
+    pt, mt, vt = cuda(p), cuda(m), cuda(v)
+    pr, mr, vr = p.astype(np.float64), m.astype(np.float64), v.astype(np.float64)
+    for step, gain in ((1, 3.0), (2, 0.01), (3, 5.0)):          # clipped, not clipped, clipped
+        g = (rng.normal(0, 1, n) * gain / np.sqrt(n)).astype(np.float32)
+        gwx.adamw_clip(pt, cuda(g), mt, vt, step, 1e-3, 0.5, weight_decay=1e-2)
+        pr, mr, vr = learn.adamw(pr, g.astype(np.float64), mr, vr, 1e-3, 0.9, 0.999, 1e-8, 1e-2, step, clip=0.5)
+    np.testing.assert_allclose(host(pt), pr, rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(host(mt), mr, rtol=1e-4, atol=1e-9)
+    np.testing.assert_allclose(host(vt), vr, rtol=1e-4, atol=1e-12)
+
+
 def test_targets_and_gauss_nll(gwx):
     wl = workloads.workload("small")
     th = workloads.random_theta(201, 300, wl["prior"])

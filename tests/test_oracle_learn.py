@@ -212,3 +212,20 @@ def test_lag_features_brute_force_and_track():
     l0 = f0[:, :ng] + 1j * f0[:, ng:2 * ng]
     l1 = f1[:, :ng] + 1j * f1[:, ng:2 * ng]
     np.testing.assert_allclose(l1, l0 * np.exp(2j * np.pi * s / N), atol=1e-12)
+
+
+def test_adamw_clip_invariances():
+    rng = np.random.default_rng(81)
+    p, g = rng.normal(size=50), rng.normal(size=50) * 10.0
+    z = np.zeros(50)
+    # Adam's first step does not see the gradient's scale (eps aside), so clipping leaves it
+    a = learn.adamw(p, g, z, z, 1e-2, 0.9, 0.999, 1e-12, 0.0, 1)
+    b = learn.adamw(p, g, z, z, 1e-2, 0.9, 0.999, 1e-12, 0.0, 1, clip=0.5)
+    np.testing.assert_allclose(a[0], b[0], rtol=1e-9)
+    # a clipped gradient's first moment has norm (1 - beta1) clip
+    assert abs(np.linalg.norm(b[1]) - 0.1 * 0.5) < 1e-12
+    # a clip above the norm changes nothing
+    c = learn.adamw(p, g, z, z, 1e-2, 0.9, 0.999, 1e-8, 0.0, 1, clip=1e9)
+    d = learn.adamw(p, g, z, z, 1e-2, 0.9, 0.999, 1e-8, 0.0, 1)
+    for x, y in zip(c, d):
+        np.testing.assert_array_equal(x, y)
