@@ -601,9 +601,11 @@ int gwx_dense_bf16(const void* X, const void* W, const float* bias, void* Y, int
 
 int gwx_device_status(void) {
   GWX_TRY(ensure_init());
-  int st = 0;
+  int st = 0, st2 = 0;
   GWX_TRY(launched(gemm_status(&st), "device status"));
-  if (st != 0) return fail(GWX_ETIMEOUT, "a kernel gave up waiting for its own copies; its output is incomplete");
+  GWX_TRY(launched(flow_fused_status(&st2), "device status"));
+  if (st != 0 || st2 != 0)
+    return fail(GWX_ETIMEOUT, "a kernel gave up waiting for its own copies; its output is incomplete");
   return GWX_OK;
 }
 

@@ -141,6 +141,14 @@ cudaError_t launch_flow_proposal(const float* x, const float* z, const float* su
                                  int64_t S, const double* mean8, const double* scale8, const gwx_prior& pr,
                                  const double* truth, int64_t E, const int64_t* off, uint64_t seed, uint32_t counter,
                                  double* theta, double* log_q, double* log_ratio, cudaStream_t s);
+// The sampling pass of the coupling flow fused into one persistent tcgen05 kernel
+// (k_flow_fused.cu), for conditioner widths H of 128 or 256 and 8 + C <= 128: draws
+// z [n][8] of global rows row0 .. row0 + n - 1 -> x_out [n][8], ss_out [n].
+bool flow_fused_supported(int C, int H, int K);
+cudaError_t launch_flow_sample_fused(const void* params_bf16, const float* params, const int64_t* off_t, int C, int H,
+                                     int K, const float* z, const void* ctx, const int64_t* ev_off, int64_t E,
+                                     int64_t row0, int64_t n, float* x_out, float* ss_out, cudaStream_t s);
+cudaError_t flow_fused_status(int* status);
 size_t flow_train_ws(const gwx_flow_shape& sh, int64_t B, int D, int64_t N);
 cudaError_t flow_train_step(const gwx_flow_shape& sh, float* params, void* params_bf16, float* grads, float* m,
                             float* v, int64_t step, double lr, double b1, double b2, double eps, double wd, double clip,

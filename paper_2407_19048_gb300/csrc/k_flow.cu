@@ -649,9 +649,17 @@ cudaError_t flow_sample(const gwx_flow_shape& sh, const float* params, const voi
   EmbedWs e = carve_embed(d, E, D, N, c);
   ChainWs w = carve_chain(d, std::min(S, kSampleChunk), c);
   FL_TRY(embed_forward(d, P, y, E, D, N, k_lo, e.fws, e.feat, e.h1, e.h2, e.ctx, s));
+  const bool fused = flow_fused_supported((int)d.C, (int)d.H, (int)d.K);
   for (int64_t row0 = 0; row0 < S; row0 += kSampleChunk) {
     const int64_t n = std::min(kSampleChunk, S - row0);
     FL_TRY(launch_flow_base(seed, counter, row0, n, w.z, s));
+    if (fused) {
+      FL_TRY(launch_flow_sample_fused(params_bf16, params, P.off.data(), (int)d.C, (int)d.H, (int)d.K, w.z, e.ctx,
+                                      off, E, row0, n, w.v, w.sum_s, s));
+      FL_TRY(launch_flow_proposal(w.v, w.z, w.sum_s, n, row0, S, mean8, scale8, pr, truth, E, off, seed, counter,
+                                  theta, log_q, log_ratio, s));
+      continue;
+    }
     const float* vin = w.z;
     for (int l = 0; l < (int)d.K; ++l) {
       FL_TRY(launch_flow_input(l, vin, e.ctx, (int)d.C, off, E, row0, n, w.X, s));

@@ -22,10 +22,13 @@
 #include <cuda_bf16.h>
 
 #include "gwx_internal.h"
+#include "tc05.cuh"
 
 namespace gwx {
 
 namespace {
+
+using namespace tc;
 
 constexpr int GM = 128, GN = 256, GK = 64, STAGES = 4;
 constexpr int EPI_WARPS = 8;                            // two per tensor-memory lane quarter
@@ -38,87 +41,9 @@ constexpr uint32_t WAIT_POLLS = 1u << 22;
 constexpr uint32_t EPI_BUF_BYTES = 32 * 32 * 4;         // per epilogue warp: a 32 x 32 FP32 transpose tile
 constexpr size_t GEMM_SMEM = (size_t)STAGES * STAGE_BYTES + (size_t)EPI_WARPS * EPI_BUF_BYTES + 1024;
 
-// Instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1), A and B
-// bfloat16 (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits
-// 17-22, M >> 4 at bits 24-28.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GN >> 3) << 17) |
-                           ((uint32_t)(GM >> 4) << 24);
+constexpr uint32_t IDESC = idesc_bf16(GM, GN);   // 128 x 256 tiles
 
 __device__ int g_gemm_status;
-
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-// Poll phase `parity` of a barrier at most `limit` times; false on expiry.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t limit) {
-  for (uint32_t i = 0; i < limit; ++i) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor of a K-major bfloat16 tile written by TMA with the
-// 128-byte swizzle: rows of 64 elements (128 B), 8-row groups 1024 B apart (stride byte
-// offset), descriptor version 1 (bits 46-47), swizzle mode 2 = 128 B (bits 61-63).  The
-// leading byte offset is not used by swizzled K-major layouts (set to 16 B).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-// 32 consecutive FP32 columns of this thread's accumulator row.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
 
 // Fused epilogue of a dense layer on 32 accumulator columns starting at col0:
 // z = acc + bias[col], then the activation (0 identity, 1 ReLU, 2 GELU z Phi(z)).
@@ -230,7 +155,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           const uint32_t sa = base + s * STAGE_BYTES, sb = sa + A_BYTES;
 #pragma unroll
           for (int kk = 0; kk < GK / 16; ++kk)   // 16 bfloat16 = 32 bytes along K per instruction
-            mma_bf16(d, sw128_desc(sa + 32u * kk), sw128_desc(sb + 32u * kk), (kb | kk) != 0);
+            mma_bf16(d, sw128_desc(sa + 32u * kk), sw128_desc(sb + 32u * kk), IDESC, (kb | kk) != 0);
           mma_commit(su32(&empty[s]));
         }
         if (!ok) atomicExch(&abort_flag, 1);

@@ -64,17 +64,28 @@ def _std():
 MEAN, SCALE = _std()
 
 
-@pytest.fixture(scope="module")
-def model(gwx):
+def _make_model(hidden, layers=4):
     from paper_2407_19048_gb300.flow import FlowPosterior
-    fp = FlowPosterior(WL, layers=4, hidden=64, context=32, embed_hidden=64, group=GROUP, seed=1)
+    fp = FlowPosterior(WL, layers=layers, hidden=hidden, context=32, embed_hidden=64, group=GROUP, seed=1)
     assert fp.shape["extra"] == 3          # cross spectra and lag-one products
-    shape = workloads.flow_shape(features=fp.shape["features"], group=GROUP, embed_hidden=64, context=32, layers=4,
-                                 hidden=64)
+    shape = workloads.flow_shape(features=fp.shape["features"], group=GROUP, embed_hidden=64, context=32,
+                                 layers=layers, hidden=hidden)
     params = workloads.random_flow_params(301, shape, gain=1.0, last_gain=0.5)
     fp.set_tensors(params)
     fp.mean, fp.scale = list(MEAN), list(SCALE)
     return fp, params
+
+
+@pytest.fixture(scope="module")
+def model(gwx):
+    return _make_model(64)
+
+
+# hidden width 128 or 256 takes the fused sampling kernel (k_flow_fused.cu); 64 the
+# per-layer path
+@pytest.fixture(scope="module", params=[64, 128, 256])
+def sampler(gwx, request):
+    return _make_model(request.param, layers=5)
 
 
 def oracle_features(y, F, cross=True, lag=True):
@@ -244,15 +255,16 @@ def test_train_step_loss_and_gradients(gwx, model):
         assert err <= 0.01 * np.linalg.norm(g_ref[t]) + 1e-6, (t, err, np.linalg.norm(g_ref[t]))
 
 
-def test_sample_posterior(gwx, model):
-    fp, params = model
+def test_sample_posterior(gwx, sampler):
+    fp, params = sampler
+    K = fp.shape["layers"]
     E = 4
     y, truth = _batch(330, E)
     offsets = np.array([0, 150, 150, 400, 700], dtype=np.int64)
     th, lq, lr = fp.sample(cuda(y), cuda(truth), cuda(offsets), 2024, 9)
     th, lq, lr = host(th), host(lq), host(lr)
     feat = oracle_features(y, fp.shape["features"])
-    th_ref, lq_ref, lr_ref = fl.sample_posterior(feat, params, 4, MEAN, SCALE, WL["prior"], truth, offsets, 2024, 9)
+    th_ref, lq_ref, lr_ref = fl.sample_posterior(feat, params, K, MEAN, SCALE, WL["prior"], truth, offsets, 2024, 9)
     both = np.isfinite(lr) & np.isfinite(lr_ref)
     assert both.sum() >= 0.95 * min(np.isfinite(lr).sum(), np.isfinite(lr_ref).sum())
     assert np.mean(np.isfinite(lr) != np.isfinite(lr_ref)) < 0.01
@@ -264,8 +276,8 @@ def test_sample_posterior(gwx, model):
         assert np.array_equal(th[r], th_ref[r])
 
 
-def test_sample_then_density_round_trip(gwx, model):
-    fp, _ = model
+def test_sample_then_density_round_trip(gwx, sampler):
+    fp, _ = sampler
     E = 3
     y, truth = _batch(340, E)
     offsets = np.array([0, 300, 600, 900], dtype=np.int64)
@@ -276,8 +288,9 @@ def test_sample_then_density_round_trip(gwx, model):
     assert np.all(np.abs(lp - host(lq)[ok]) <= 1e-2 + 1e-3 * np.abs(lp))
 
 
-def test_sample_posterior_across_chunks(gwx, model):
-    fp, params = model
+def test_sample_posterior_across_chunks(gwx, sampler):
+    fp, params = sampler
+    K = fp.shape["layers"]
     E = 2
     y, truth = _batch(350, E)
     S = (1 << 17) + 3000
@@ -285,7 +298,7 @@ def test_sample_posterior_across_chunks(gwx, model):
     th, lq, lr = fp.sample(cuda(y), cuda(truth), cuda(offsets), 8, 2)
     pick = np.r_[0:5, 69998:70003, (1 << 17) - 3:(1 << 17) + 3, S - 4:S]
     feat = oracle_features(y, fp.shape["features"])
-    emb, layers = fl.split_params(params, 4)
+    emb, layers = fl.split_params(params, K)
     c, _ = fl.embed(feat, emb)
     ev = fl.event_of(offsets, S)[pick]
     z, coin = fl.base_normals(8, 2, pick)
