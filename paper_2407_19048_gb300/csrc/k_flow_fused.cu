@@ -6,11 +6,12 @@
 //     part: V3 padded to 16 rows by the box's zero fill);
 //   - warp 1 issues tcgen05.mma: acc1 = X V1^T, acc2 = g1 V2^T, acc3 = g2 V3^T (FP32 in
 //     tensor memory, columns 0 and 256; acc3 reuses acc1's columns);
-//   - warps 2-5 own one draw (row) per thread: they keep the draw's eight coordinates and
-//     its log-scale sum in registers, write the conditioner input X (bfloat16; the
-//     context once per tile, the conditioning half once per layer) and the hidden
-//     activations g1, g2 (bias, ReLU, bfloat16) into shared memory in the 128-byte-swizzle
-//     layout the MMA reads, and apply the coupling step from acc3.
+//   - warps 2-9 own one draw (row) per thread, two warps per tensor-memory lane quarter:
+//     the first keeps the draw's eight coordinates and its log-scale sum in registers,
+//     writes the conditioning half of the conditioner input X once per layer and applies
+//     the coupling step from acc3; both write the context into X once per tile and half
+//     of the hidden activations g1, g2 (bias, ReLU, bfloat16) each, into shared memory in
+//     the 128-byte-swizzle layout the MMA reads.
 // The activations never go to global memory: per draw and layer only the weights (shared
 // by all draws, L2-resident) move.  Every mbarrier wait is bounded; on expiry the CTA
 // records a status, stops and frees its tensor memory.
@@ -28,7 +29,7 @@ namespace {
 using namespace tc;
 
 constexpr int FM = 128;                                  // draws per tile
-constexpr int F_THREADS = 192;                           // warp 0 TMA, warp 1 MMA, warps 2-5 rows
+constexpr int F_THREADS = 320;                           // warp 0 TMA, warp 1 MMA, warps 2-9 rows
 constexpr uint32_t KB_BYTES = FM * 128;                  // one 128-row x 64-column bfloat16 K-block: 16 KiB
 constexpr uint32_t X_BYTES = 2 * KB_BYTES;               // conditioner input, 8 + C <= 128 columns
 constexpr uint32_t G_BYTES = 4 * KB_BYTES;               // hidden activations, H <= 256 columns
@@ -120,8 +121,8 @@ __global__ void __launch_bounds__(F_THREADS, 1)
       mbar_init(su32(&full[s]), 1);
       mbar_init(su32(&empty[s]), 1);
     }
-    mbar_init(su32(&xready), 4);
-    mbar_init(su32(&gready), 4);
+    mbar_init(su32(&xready), 8);
+    mbar_init(su32(&gready), 8);
     mbar_init(su32(&acc1f), 1);
     mbar_init(su32(&acc2f), 1);
     mbar_init(su32(&acc3f), 1);
@@ -238,6 +239,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
     }
   } else {
     const int q = warp & 3;
+    const int h = (warp - 2) >> 2;                             // which half of the columns
     const int r = 32 * q + lane;                               // row of the tile = tensor-memory lane
     const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
     uint32_t li = 0;
@@ -253,24 +255,32 @@ __global__ void __launch_bounds__(F_THREADS, 1)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       return __all_sync(0xffffffffu, got) && !*(volatile int*)&abort_flag;
     };
-    // bias + ReLU of one H-column accumulator into the activation tile g
+    // bias + ReLU of this warp's half of an H-column accumulator into the activation tile
+    // g, 64 columns (two loads, one wait) at a time
     auto hidden = [&](uint32_t col0, const float* bias) {
-      for (int c = 0; c < H / 32; ++c) {
-        float v[32];
-        tmem_ld32(lane_addr + col0 + 32u * c, v);
-        const float4* b4 = reinterpret_cast<const float4*>(bias + 32 * c);
-        uint32_t w[16];
+      for (int c = h * (H / 128); c < (h + 1) * (H / 128); ++c) {   // H / 64 chunks, half each
+        uint32_t raw[2][32];
+        tmem_ld32_async(lane_addr + col0 + 64u * c, raw[0]);
+        tmem_ld32_async(lane_addr + col0 + 64u * c + 32u, raw[1]);
+        tmem_wait_ld();
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const float4 b = __ldg(b4 + i);
-          w[2 * i] = pack2(fmaxf(v[4 * i] + b.x, 0.f), fmaxf(v[4 * i + 1] + b.y, 0.f));
-          w[2 * i + 1] = pack2(fmaxf(v[4 * i + 2] + b.z, 0.f), fmaxf(v[4 * i + 3] + b.w, 0.f));
-        }
+        for (int hh = 0; hh < 2; ++hh) {
+          const float4* b4 = reinterpret_cast<const float4*>(bias + 64 * c + 32 * hh);
+          uint32_t w[16];
 #pragma unroll
-        for (int t4 = 0; t4 < 4; ++t4) {
-          const int col = 32 * c + 8 * t4;
-          sts128(sg + KB_BYTES * (col >> 6) + swz(r, (col & 63) >> 3), w[4 * t4], w[4 * t4 + 1], w[4 * t4 + 2],
-                 w[4 * t4 + 3]);
+          for (int i = 0; i < 8; ++i) {
+            const float4 b = __ldg(b4 + i);
+            w[2 * i] = pack2(fmaxf(__uint_as_float(raw[hh][4 * i]) + b.x, 0.f),
+                             fmaxf(__uint_as_float(raw[hh][4 * i + 1]) + b.y, 0.f));
+            w[2 * i + 1] = pack2(fmaxf(__uint_as_float(raw[hh][4 * i + 2]) + b.z, 0.f),
+                                 fmaxf(__uint_as_float(raw[hh][4 * i + 3]) + b.w, 0.f));
+          }
+#pragma unroll
+          for (int t4 = 0; t4 < 4; ++t4) {
+            const int col = 64 * c + 32 * hh + 8 * t4;
+            sts128(sg + KB_BYTES * (col >> 6) + swz(r, (col & 63) >> 3), w[4 * t4], w[4 * t4 + 1], w[4 * t4 + 2],
+                   w[4 * t4 + 3]);
+          }
         }
       }
     };
@@ -278,7 +288,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
       const int64_t row = (int64_t)t * FM + r;
       const bool valid = row < a.n;
       float v[8], ss = 0.f;
-      if (valid) {
+      if (valid && h == 0) {
         const float4 z0 = reinterpret_cast<const float4*>(a.z + row * 8)[0];
         const float4 z1 = reinterpret_cast<const float4*>(a.z + row * 8)[1];
         v[0] = z0.x; v[1] = z0.y; v[2] = z0.z; v[3] = z0.w; v[4] = z1.x; v[5] = z1.y; v[6] = z1.z; v[7] = z1.w;
@@ -297,21 +307,23 @@ __global__ void __launch_bounds__(F_THREADS, 1)
         e = lo;
       }
       const uint4* crow = reinterpret_cast<const uint4*>(a.ctx + e * C);
-      for (int g = 1; g < 16; ++g) {
+      for (int g = h == 0 ? 1 : 8; g < (h == 0 ? 8 : 16); ++g) {
         uint4 d = make_uint4(0u, 0u, 0u, 0u);
         if (valid && g <= C / 8) d = __ldg(crow + (g - 1));
         sts128(sx + KB_BYTES * (g >> 3) + swz(r, g & 7), d.x, d.y, d.z, d.w);
       }
       for (int l = 0; l < K; ++l, ++li) {
         const int p = l & 3;
-        uint32_t w0, w1;
-        switch (p) {
-          case 0: pack_half<0>(v, w0, w1); break;
-          case 1: pack_half<1>(v, w0, w1); break;
-          case 2: pack_half<2>(v, w0, w1); break;
-          default: pack_half<3>(v, w0, w1); break;
+        if (h == 0) {
+          uint32_t w0, w1;
+          switch (p) {
+            case 0: pack_half<0>(v, w0, w1); break;
+            case 1: pack_half<1>(v, w0, w1); break;
+            case 2: pack_half<2>(v, w0, w1); break;
+            default: pack_half<3>(v, w0, w1); break;
+          }
+          sts128(sx + swz(r, 0), w0, w1, 0u, 0u);
         }
-        sts128(sx + swz(r, 0), w0, w1, 0u, 0u);
         arrive(&xready);
         if (!(ok = wait_on(&acc1f, li & 1u))) break;
         hidden(0u, a.e1 + l * a.lstride);
@@ -319,6 +331,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
         if (!(ok = wait_on(&acc2f, li & 1u))) break;
         hidden(256u, a.e2 + l * a.lstride);
         arrive(&gready);
+        if (h != 0) continue;                                  // the coupling step is the first warp's
         if (!(ok = wait_on(&acc3f, li & 1u))) break;
         float o[16];
         tmem_ld16(lane_addr, o);
@@ -331,7 +344,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
         }
       }
       if (!ok) break;
-      if (valid) {
+      if (valid && h == 0) {
         reinterpret_cast<float4*>(a.x_out + row * 8)[0] = make_float4(v[0], v[1], v[2], v[3]);
         reinterpret_cast<float4*>(a.x_out + row * 8)[1] = make_float4(v[4], v[5], v[6], v[7]);
         a.ss_out[row] = ss;
