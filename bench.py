@@ -759,6 +759,9 @@ def main(argv=None):
                     help="run only the log-likelihood leg with U{LO..HI} samples per event; for profiling")
     ap.add_argument("--only-gemm", default=None, metavar="M,N,K",
                     help="run only the bfloat16 product leg at this shape; for profiling")
+    ap.add_argument("--only-flow-sample", default=None, metavar="E,S",
+                    help="run only posterior sampling of the (untrained) default flow, E events x S draws, five "
+                         "times; for profiling")
     ap.add_argument("--only-flow", default=None, metavar="STEPS",
                     help="run only the coupling-flow leg with this many training steps; for profiling")
     args = ap.parse_args(argv)
@@ -775,6 +778,26 @@ def main(argv=None):
         gwx.init()
         shape = tuple(int(v) for v in args.only_gemm.split(","))
         print(json.dumps({"gemm_bf16": gemm_leg(gwx, torch, shape)}), flush=True)
+        return 0
+    if args.only_flow_sample:
+        import torch
+        import paper_2407_19048_gb300 as gwx
+        import paper_2407_19048_gb300.simulator  # noqa: F401
+        from paper_2407_19048_gb300.flow import FlowPosterior
+        gwx.init()
+        E, S = (int(v) for v in args.only_flow_sample.split(","))
+        wl2 = workloads.workload("small", B=E)
+        y, th, _ = gwx.simulator.Simulator(wl2).step(0)
+        fp = FlowPosterior(wl2)
+        offs = torch.arange(E + 1, dtype=torch.int64, device="cuda") * S
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fp.sample(y, th, offs, 1, 0)
+        ev0.record()
+        for rep in range(5):
+            fp.sample(y, th, offs, 1, rep)
+        ev1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"flow_sample": {"events": E, "draws": E * S, "ms": ev0.elapsed_time(ev1) / 5}}), flush=True)
         return 0
     if args.only_flow:
         import torch
