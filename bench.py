@@ -502,7 +502,34 @@ def flow_leg(gwx, torch, rank, steps=8000, events=32, per_event=4000, pp_events=
         u = np.sort(pct)
         n = len(u)
         ks.append(float(max(np.max(np.arange(1, n + 1) / n - u), np.max(u - np.arange(n) / n))))
-    del sim, sim_ev, sim_pp
+    # streaming: 1000 events of U{2000..50000} draws, one at a time, flow vs prior proposal
+    import numpy as np
+    from paper_2407_19048_gb300.scorer import Scorer
+    n_srv = 1000
+    wl_srv = dict(workloads.workload("small", B=n_srv), param_seed=780)
+    sim_srv = gwx.simulator.Simulator(wl_srv)
+    y_srv, th_srv, _ = sim_srv.step(step_counter(rank, 3))
+    counts = workloads.ragged_counts(6 + rank, n_srv, 2000, 50000)
+    serving = {}
+    for name, flow in (("prior", None), ("flow", fp)):
+        sc = Scorer(wl_srv, int(counts.max()), sim_srv.psd, flow=flow)
+        truth = [th_srv[:, e:e + 1].contiguous() for e in range(n_srv)]
+        for e in range(5):
+            sc.score(y_srv[e:e + 1], int(counts[e]), e, truth=truth[e])
+        torch.cuda.synchronize()
+        lat_srv, ess = [], []
+        t0 = time.perf_counter()
+        for e in range(n_srv):
+            a = time.perf_counter()
+            ess.append(sc.score(y_srv[e:e + 1], int(counts[e]), e, truth=truth[e])[0])
+            lat_srv.append(time.perf_counter() - a)
+        wall = time.perf_counter() - t0
+        lat_ms = np.array(lat_srv) * 1e3
+        serving[name] = {"events_per_s": n_srv / wall, "latency_ms_p50": float(np.percentile(lat_ms, 50)),
+                         "latency_ms_p99": float(np.percentile(lat_ms, 99)), "ess_total": float(np.sum(ess)),
+                         "ess_median": float(np.median(ess)), "ess_per_s": float(np.sum(ess)) / wall}
+        del sc
+    del sim, sim_ev, sim_pp, sim_srv
     return {"shape": fp.shape, "params": fp.n_params, "train_steps": steps, "batch": batch, "train_s": train_s,
             "simulations_per_s": steps * batch / train_s, "train_step_ms": step_ms, "loss": losses,
             "sample_20000_ms": {"p50": lat[len(lat) // 2] * 1e3, "min": lat[0] * 1e3, "max": lat[-1] * 1e3},
@@ -510,6 +537,9 @@ def flow_leg(gwx, torch, rank, steps=8000, events=32, per_event=4000, pp_events=
             "pp_test": {"events": pp_events, "draws_per_event": pp_samples, "ks_distance": ks,
                         "ks_95pct_critical": 1.36 / math.sqrt(pp_events),
                         "coords": ["Mc", "q", "D_L", "cos theta_JN", "RA", "sin dec", "psi", "phic"]},
+            "serving": dict(serving, events=n_srv, draws="U{2000..50000} per event",
+                            per_event="draws (prior or flow) + log_likelihood + importance_weights + host read; "
+                                      "spins and merger time from the event"),
             "note": "loss = batch mean of -ln q_x(x) in standardised coordinates; spins and merger time known to "
                     "both proposals in the importance-sampling comparison"}
 

@@ -1,9 +1,9 @@
 """Low-latency scoring of single events (the serving side of the likelihood path).
 
 An event arrives as a whitened window y [D][N]; the scorer draws S samples from a
-proposal (the prior here; `gwx_sample_proposal` can take a learned one), scores them with
-the standard likelihood (Sec. 6) and weighs them, then reads the event's effective
-sample size and evidence back to the host.  Every buffer and workspace is allocated once
+proposal (the prior, or a trained `flow.FlowPosterior` through `gwx_sample_posterior`),
+scores them with the standard likelihood (Sec. 6) and weighs them, then reads the
+event's effective sample size and evidence back to the host.  Every buffer and workspace is allocated once
 for the largest S, the calls go straight to the C ABI on one stream, and the only host
 synchronisation is the final read of two doubles from pinned memory.
 """
@@ -14,7 +14,7 @@ from . import NPARAM, _check, _det_ids, _prior, _ptr, _workspace
 
 
 class Scorer:
-    def __init__(self, workload, max_samples, psd, device=None, seed=55):
+    def __init__(self, workload, max_samples, psd, device=None, seed=55, flow=None):
         import torch
         self.wl = dict(workload)
         wl = self.wl
@@ -38,12 +38,24 @@ class Scorer:
         self.ev_host = torch.empty(2, dtype=torch.int64, pin_memory=True)
         self.ws_ll = _workspace(self.lib.gwx_log_likelihood_workspace(1, self.D, self.N, self.smax), self.dev)
         self.ws_iw = _workspace(self.lib.gwx_importance_weights_workspace(1), self.dev)
+        self.flow = flow
+        if flow is not None:
+            from . import _shape
+            self.shape = _shape(flow.shape)
+            self.ws_fl = _workspace(self.lib.gwx_sample_posterior_workspace(ctypes.byref(self.shape), 1, self.D, self.N,
+                                                                            self.smax), self.dev)
+            self.log_q = torch.empty(self.smax, dtype=f64, device=self.dev)
+            self.log_ratio = torch.empty(self.smax, dtype=f64, device=self.dev)
+            self.mean8 = (ctypes.c_double * 8)(*flow.mean)
+            self.scale8 = (ctypes.c_double * 8)(*flow.scale)
         self.stream = torch.cuda.Stream(device=self.dev)
         self.done = torch.cuda.Event()
 
-    def score(self, y_event, S, step):
+    def score(self, y_event, S, step, truth=None):
         """(ess, efficiency, ln_evidence) of one event y_event [D][N] (device float32)
-        from S prior samples drawn with Philox counter `step`."""
+        from S samples drawn with Philox counter `step`: from the prior, or with a flow
+        from the flow (spins and merger time from truth [11][1], which the flow does not
+        model)."""
         import torch
         if S > self.smax:
             raise ValueError("S exceeds max_samples")
@@ -53,15 +65,26 @@ class Scorer:
         with torch.cuda.stream(self.stream):
             self.ev.copy_(self.ev_host, non_blocking=True)
         theta = ctypes.c_void_p(self.theta.data_ptr())
-        _check(lib.gwx_sample_prior(ctypes.byref(self.prior), self.seed, step & 0xFFFFFFFF, S, self.L, self.N, theta,
-                                    _ptr(self.offsets_draw), s))
+        ratio = None
+        if self.flow is None:
+            _check(lib.gwx_sample_prior(ctypes.byref(self.prior), self.seed, step & 0xFFFFFFFF, S, self.L, self.N,
+                                        theta, _ptr(self.offsets_draw), s))
+        else:
+            ws, nb = self.ws_fl
+            fp = self.flow
+            _check(lib.gwx_sample_posterior(ctypes.byref(self.shape), _ptr(fp.params), _ptr(fp.params16), self.mean8,
+                                            self.scale8, ctypes.byref(self.prior), _ptr(y_event), 1, self.D, self.N,
+                                            self.fs, self.f_lo, _ptr(truth), _ptr(self.ev), S, self.seed,
+                                            step & 0xFFFFFFFF, theta, _ptr(self.log_q), _ptr(self.log_ratio),
+                                            _ptr(ws), nb, s))
+            ratio = _ptr(self.log_ratio)
         ws, nb = self.ws_ll
         _check(lib.gwx_log_likelihood(0, _ptr(y_event), 1, self.D, self.N, _ptr(self.psd), self.M, self.fs,
                                       self.f_lo, self.ids, 0.0, theta, _ptr(self.ev), S, _ptr(self.lnl), _ptr(ws), nb,
                                       s))
         ws, nb = self.ws_iw
         o = self.out.data_ptr()
-        _check(lib.gwx_importance_weights(_ptr(self.lnl), None, _ptr(self.ev), 1, S, _ptr(self.w),
+        _check(lib.gwx_importance_weights(_ptr(self.lnl), ratio, _ptr(self.ev), 1, S, _ptr(self.w),
                                           ctypes.c_void_p(o), ctypes.c_void_p(o + 8), ctypes.c_void_p(o + 16),
                                           _ptr(ws), nb, s))
         with torch.cuda.stream(self.stream):

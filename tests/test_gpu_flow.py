@@ -344,3 +344,24 @@ def test_checkpoint_resume_is_bit_exact(gwx, tmp_path):
         y, theta, _ = sim.step(step)
         b.train_step(y, theta)
     assert torch.equal(a.params, b.params) and torch.equal(a.m, b.m) and b.steps == a.steps
+
+
+def test_scorer_with_the_flow_matches_the_separate_calls(gwx, sampler):
+    from paper_2407_19048_gb300.scorer import Scorer
+    from paper_2407_19048_gb300.simulator import Simulator
+    fp, _ = sampler
+    wl = dict(WL, B=4)
+    sim = Simulator(wl)
+    y, th, _ = sim.step(7)
+    sc = Scorer(wl, 3000, sim.psd, flow=fp)
+    for e, S in ((0, 3000), (2, 1234)):
+        truth = th[:, e:e + 1].contiguous()
+        got = sc.score(y[e:e + 1], S, 11, truth=truth)
+        offs = torch.tensor([0, S], dtype=torch.int64, device="cuda")
+        theta, _, lr = gwx.sample_posterior(fp.shape, fp.params, fp.params16, fp.mean, fp.scale, wl["prior"],
+                                            y[e:e + 1].contiguous(), wl["fs"], wl["f_lo"], truth, offs, 55, 11)
+        lnl = gwx.log_likelihood(y[e:e + 1].contiguous(), sim.psd, wl["seg_len"], wl["fs"], wl["f_lo"], wl["dets"],
+                                 0.0, theta, offs)
+        _, ess, eff, lnz = gwx.importance_weights(lnl, offs, lr)
+        ref = (float(ess[0]), float(eff[0]), float(lnz[0]))
+        assert got == ref or np.allclose(got, ref, rtol=1e-12, atol=0), (got, ref)
