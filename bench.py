@@ -466,6 +466,25 @@ def flow_leg(gwx, torch, rank, steps=8000, events=32, per_event=4000, pp_events=
         if rep >= 3:
             lat.append(time.perf_counter() - a)
     lat.sort()
+    # sky maps: 20,000 draws + likelihood + weights + HEALPix map (the paper: ~0.6 / 1.2 / 2.4 s
+    # for 20k samples and a map at NSIDE 32 / 64 / 128 on an A40)
+    sky = {}
+    y1, t1 = y_ev[:1].contiguous(), th_ev[:, :1].contiguous()
+    for nside in (32, 64, 128):
+        times = []
+        for rep in range(13):
+            torch.cuda.synchronize()
+            a0 = time.perf_counter()
+            theta1, _, lr1 = fp.sample(y1, t1, one, 17, rep)
+            lnl1 = gwx.log_likelihood(y1, sim_ev.psd, wl_ev["seg_len"], wl_ev["fs"], wl_ev["f_lo"], wl_ev["dets"],
+                                      0.0, theta1, one)
+            w1, _, _, _ = gwx.importance_weights(lnl1, one, lr1)
+            gwx.skymap(theta1, nside, weights=w1)
+            torch.cuda.synchronize()
+            if rep >= 3:
+                times.append(time.perf_counter() - a0)
+        times.sort()
+        sky[str(nside)] = times[len(times) // 2] * 1e3
     # importance sampling: flow vs prior, same events and likelihood
     offs = torch.arange(events + 1, dtype=torch.int64, device="cuda") * per_event
     res = {}
@@ -533,6 +552,8 @@ def flow_leg(gwx, torch, rank, steps=8000, events=32, per_event=4000, pp_events=
     return {"shape": fp.shape, "params": fp.n_params, "train_steps": steps, "batch": batch, "train_s": train_s,
             "simulations_per_s": steps * batch / train_s, "train_step_ms": step_ms, "loss": losses,
             "sample_20000_ms": {"p50": lat[len(lat) // 2] * 1e3, "min": lat[0] * 1e3, "max": lat[-1] * 1e3},
+            "skymap_20000_ms": dict(sky, note="sample_posterior 20k + log_likelihood + importance_weights + skymap "
+                                              "(HEALPix nested, importance-weighted), median of 10, host time"),
             "events": events, "samples_per_event": per_event, "importance_sampling": res,
             "pp_test": {"events": pp_events, "draws_per_event": pp_samples, "ks_distance": ks,
                         "ks_95pct_critical": 1.36 / math.sqrt(pp_events),

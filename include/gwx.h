@@ -536,6 +536,19 @@ int gwx_sample_posterior(const gwx_flow_shape* shape, const float* params, const
                          const int64_t* event_offsets, int64_t S, uint64_t seed, uint32_t counter, double* theta,
                          double* log_q, double* log_ratio, void* workspace, size_t workspace_bytes, void* stream);
 
+/* ---- sky maps ---------------------------------------------------------------------
+ * The paper's inference ends in a sky-localisation map in the HEALPix format (Sec. 5).
+ * gwx_skymap: map [12 nside^2] (FP64) = the histogram of samples' sky positions (rows RA
+ * and dec of theta [GWX_NPARAM][S]) over the nested-scheme HEALPix pixels (Gorski et al.
+ * 2005) of resolution nside, each sample counted with its weight (weights [S], e.g. from
+ * gwx_importance_weights; NULL counts every sample once; zero, negative or non-finite
+ * weights are skipped), normalised to unit sum (all zero if no sample counts).  nside a
+ * power of two in [1, 8192]; map overwritten.  Workspace gwx_skymap_workspace() bytes.
+ * Accumulation is by FP64 atomic additions, so the last bits depend on their order. */
+size_t gwx_skymap_workspace(void);
+int gwx_skymap(const double* theta, const double* weights, int64_t S, int nside, double* map, void* workspace,
+               size_t workspace_bytes, void* stream);
+
 /* Autotuner of the product's tile raster (a set-up call, not a hot call: it launches the
  * product several times on the caller's buffers and synchronises `stream`).  For the
  * shape (M, N, K, c_dtype) it times each candidate band height of the persistent tile

@@ -26,7 +26,7 @@ __all__ = ["GwxError", "version", "init", "detector_geometry", "sample_prior", "
            "colored_noise", "welch_psd", "inject", "whiten", "unwhiten", "simulate_batch", "log_likelihood",
            "importance_weights", "gemm_bf16", "dense_bf16", "dense_bf16_backward", "gemm_autotune", "spectral_features",
            "cross_features", "lag_features", "proposal_targets",
-           "gauss_nll", "adamw", "adamw_clip", "sample_proposal", "device_status", "rfft", "irfft",
+           "gauss_nll", "adamw", "adamw_clip", "skymap", "sample_proposal", "device_status", "rfft", "irfft",
            "workspace_bytes", "TAYLORF2", "IMRPHENOMD", "DETECTORS"]
 
 
@@ -415,6 +415,22 @@ def adamw_clip(param, grad, m, v, step, lr, clip, beta1=0.9, beta2=0.999, eps=1e
     ws, nb = _workspace(lib.gwx_adamw_clip_workspace(), param.device)
     _check(lib.gwx_adamw_clip(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(), lr, beta1, beta2, eps,
                               weight_decay, step, clip, _ptr(param_bf16), _ptr(ws), nb, _stream()))
+
+
+def skymap(theta, nside, weights=None, out=None):
+    """Normalised HEALPix (nested) map [12 nside^2] float64 of the samples' sky positions
+    (rows RA, dec of theta [11][S]), each counted with its weight."""
+    torch = _torch()
+    lib = _lib.load()
+    _dev(theta, torch.float64, "theta")
+    if weights is not None:
+        _dev(weights, torch.float64, "weights")
+    S = theta.shape[1]
+    out = torch.empty(12 * nside * nside, dtype=torch.float64, device=theta.device) if out is None else out
+    ws, nb = _workspace(lib.gwx_skymap_workspace(), theta.device)
+    _check(lib.gwx_skymap(_ptr(theta), _ptr(weights) if weights is not None else None, S, nside, _ptr(out), _ptr(ws),
+                          nb, _stream()))
+    return out
 
 
 def sample_proposal(prior, truth, event_offsets, seed, counter, net_out=None, mean=None, scale=None,

@@ -85,6 +85,8 @@ SIGNATURES = {
     "gwx_adamw_clip_workspace": (c_size, []),
     "gwx_adamw_clip": (c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl, c_i64, c_dbl, c_vp,
                                c_vp, c_size, c_vp]),
+    "gwx_skymap_workspace": (c_size, []),
+    "gwx_skymap": (c_int, [c_vp, c_vp, c_i64, c_int, c_vp, c_vp, c_size, c_vp]),
     "gwx_sample_proposal": (c_int, [c_vp, c_int, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl),
                                     ctypes.POINTER(GwxPrior), c_vp, c_i64, c_vp, c_i64, c_u64, c_u32, c_int, c_vp, c_vp,
                                     c_vp]),

@@ -717,6 +717,21 @@ int gwx_adamw(float* param, const float* grad, float* m, float* v, int64_t n, do
                   "adamw");
 }
 
+size_t gwx_skymap_workspace(void) { return kAlign; }
+
+int gwx_skymap(const double* theta, const double* weights, int64_t S, int nside, double* map, void* workspace,
+               size_t workspace_bytes, void* stream) {
+  if (nside < 1 || nside > 8192 || (nside & (nside - 1))) return fail(GWX_EINVAL, "nside=%d must be a power of two", nside);
+  if (S < 0 || S > ((int64_t)1 << 40)) return fail(GWX_ESHAPE, "S=%lld", (long long)S);
+  if (!map || (S > 0 && !theta)) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN8(map);
+  if (theta) GWX_ALIGN8(theta);
+  if (weights) GWX_ALIGN8(weights);
+  GWX_TRY(check_ws(workspace, workspace_bytes, gwx_skymap_workspace()));
+  GWX_TRY(ensure_init());
+  return launched(launch_skymap(theta, weights, S, nside, map, workspace, as_stream(stream)), "skymap");
+}
+
 size_t gwx_adamw_clip_workspace(void) { return align_up(adamw_clip_ws()); }
 
 int gwx_adamw_clip(float* param, const float* grad, float* m, float* v, int64_t n, double lr, double beta1,

@@ -164,6 +164,10 @@ cudaError_t flow_sample(const gwx_flow_shape& sh, const float* params, const voi
                         int k_lo, const double* truth, const int64_t* off, int64_t S, uint64_t seed, uint32_t counter,
                         double* theta, double* log_q, double* log_ratio, void* ws, cudaStream_t s);
 
+// HEALPix sky map of weighted samples (k_skymap.cu); ws holds one double.
+cudaError_t launch_skymap(const double* theta, const double* weights, int64_t S, int nside, double* map, void* ws,
+                          cudaStream_t s);
+
 // Record msg as the calling thread's gwx_last_error() message; returns status.
 int set_last_error(int status, const char* msg);
 
