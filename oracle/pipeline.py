@@ -23,7 +23,7 @@ from .prior import sample_prior
 from .taylorf2 import generate_waveforms
 from .detector import project
 from .noise import colored_noise
-from .spectral import welch_psd, inject, whiten
+from .spectral import crop, welch_psd, inject, whiten
 
 
 def background(wl, step):
@@ -55,4 +55,29 @@ def simulate_batch(wl, step, draws=None, bg=None):
     return {"y": y, "theta": theta, "offsets": offsets, "noise": noise, "psd": psd, "draws": sel}
 
 
-__all__ = ["background", "simulate_batch", "C"]
+def simulate_batch_padded(wl, step, N_pad, draws=None, bg=None):
+    """Definition B (padded grid): the waveform is evaluated on the grid of a padded
+    segment of N_pad >= N samples, f_k = k fs / N_pad, projected with the draw's own tc and
+    delays, inverse-transformed over the whole padded segment, and its first N samples
+    are injected:  d = crop(n, offsets) + irfft_{N_pad}(fs h_det)[:N],  y = whiten(d, S).
+    On the circular padded segment the part of the inspiral before the window start wraps
+    to the segment's far end, outside the window, whenever N_pad / fs >= T + tau - tc
+    (tau the signal's duration from f_lo); N_pad = N is Definition A.  Returns the same
+    dict as simulate_batch."""
+    N = wl["N"]
+    fs = wl["fs"]
+    df = fs / N_pad
+    F = N_pad // 2 + 1
+    noise, psd = bg if bg is not None else background(wl, step)
+    theta, offsets = sample_prior(wl["prior"], wl["param_seed"], step, wl["B"], wl["L"], N)
+    sel = np.arange(wl["B"]) if draws is None else np.asarray(draws, dtype=np.int64)
+    th = theta[:, sel]
+    hp, hc = generate_waveforms(th, wl["f_lo"], df, F)
+    h = project(hp, hc, th, wl["dets"], wl.get("gmst", 0.0), df)
+    sig = np.fft.irfft(fs * h, n=N_pad, axis=-1)[..., :N]
+    d = crop(noise, offsets[sel], N) + sig
+    y = whiten(d, psd, wl["seg_len"], fs, wl["f_lo"])
+    return {"y": y, "theta": theta, "offsets": offsets, "noise": noise, "psd": psd, "draws": sel}
+
+
+__all__ = ["background", "simulate_batch", "simulate_batch_padded", "C"]
