@@ -408,6 +408,40 @@ def learned_leg(gwx, torch, rank, steps=2000, events=32, per_event=4000):
                     "merger time known in both proposals"}
 
 
+def padded_leg(gwx, torch, rank, B=2048, N_pad=8192, reps=20):
+    """Definition B (padded-grid waveforms: generate and project on an N_pad-point grid,
+    inverse-transform the padded segment, inject its first N samples, whiten; five libgwx
+    calls) against the fused Definition A pass, on the two-detector geometry (1024 Hz, 2 s
+    windows) with B draws per step."""
+    wl = workloads.workload("small", B=B)
+    D = len(wl["dets"])
+    n = gwx.colored_noise(wl["noise_seed"], 0, D, wl["L"], wl["fs"], wl["f_lo"])
+    S = gwx.welch_psd(n, wl["fs"], wl["seg_len"], wl["seg_stride"])
+    out = {}
+    for name in ("definition_a_fused", "definition_b"):
+        def run(i):
+            if name == "definition_b":
+                return gwx.simulate_batch_padded(wl["prior"], wl["param_seed"], i, n, S, wl["seg_len"], wl["fs"],
+                                                 wl["f_lo"], wl["dets"], 0.0, B, wl["N"], N_pad)
+            return gwx.simulate_batch(wl["prior"], wl["param_seed"], i, n, S, wl["seg_len"], wl["fs"], wl["f_lo"],
+                                      wl["dets"], 0.0, B, wl["N"])
+        for i in range(3):
+            run(i)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for i in range(reps):
+            run(step_counter(rank, 60000 + i))
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms_per_step": ms, "injections_per_s": B / (ms * 1e-3)}
+    out.update(workload="1024 Hz, 2 s windows (N = 2048), H1+L1, %d draws per step" % B, N_pad=N_pad,
+               note="Definition B pads to %d samples (%.0f s), so inspirals up to ~%.0f s long do not wrap into "
+                    "the window" % (N_pad, N_pad / wl["fs"], N_pad / wl["fs"] - wl["T"] / 2))
+    return out
+
+
 def flow_leg(gwx, torch, rank, steps=8000, events=32, per_event=4000, pp_events=200, pp_samples=500, lr=6e-4,
              cross=True, batch=4096, layers=16, hidden=256, clip=1.0):
     """The conditional coupling flow (16 affine coupling layers, conditioners 72 -> 256 ->
@@ -733,6 +767,7 @@ def run_gpu(args, wl):
     gemm = gemm_leg(gwx, torch)
     learned = learned_leg(gwx, torch, rank)
     flow = flow_leg(gwx, torch, rank)
+    padded = padded_leg(gwx, torch, rank)
 
     sim_avg_s = statistics.mean(sim_ms) * 1e-3
     flops = flops_per_injection(wl) * B
@@ -785,6 +820,7 @@ def run_gpu(args, wl):
             "gemm_bf16": gemm,
             "learned_proposal": learned,
             "flow": flow,
+            "padded_grid": padded,
             "wall_s_timed_region": t_wall,
         }
         print(json.dumps(line), flush=True)

@@ -189,6 +189,17 @@ int gwx_inject(const float* noise, int D, int64_t L, const int64_t* offsets,
  * S~ = psd (grid fs/seg_len) linearly interpolated to f_k.
  *   d in float[B][D][N]; psd in double[D][seg_len/2+1]; y out float[B][D][N]
  *   (y may alias d). */
+/* Definition B injection (the padded-grid waveform): with h_td [B][D][N_pad] the
+ * inverse transforms (gwx_irfft, 1/N_pad normalisation) of waveforms generated and
+ * projected on the grid of a padded segment, f_k = k fs / N_pad (gwx_generate_waveforms,
+ * gwx_project with df = fs / N_pad):
+ *   d[b][dd][i] = noise[dd][offsets[b] + i] + fs h_td[b][dd][i],  i < N.
+ * On the circular padded segment the inspiral before the window start wraps to the far
+ * end, outside the first N samples, when N_pad / fs >= T + tau - tc (tau the signal's
+ * duration from f_lo); N_pad = N reproduces gwx_inject.  N and N_pad powers of two in
+ * [256, 16384], N <= N_pad; offsets in [0, L - N] (not checked: device data). */
+int gwx_inject_padded(const float* noise, int D, int64_t L, const int64_t* offsets, const float* h_td, int64_t B,
+                      int64_t N, int64_t N_pad, double fs, float* d, void* stream);
 size_t gwx_whiten_workspace(int D, int64_t N);
 int gwx_whiten(const float* d, const double* psd, int64_t seg_len, double fs, double f_lo,
                int64_t B, int D, int64_t N, float* y,

@@ -23,7 +23,7 @@ M1, M2, CHI1, CHI2, DIST, TC, PHIC, THETAJN, PSI, RA, DEC = range(11)
 NPARAM = 11
 
 __all__ = ["GwxError", "version", "init", "detector_geometry", "sample_prior", "generate_waveforms", "project",
-           "colored_noise", "welch_psd", "inject", "whiten", "unwhiten", "simulate_batch", "log_likelihood",
+           "colored_noise", "welch_psd", "inject", "inject_padded", "simulate_batch_padded", "whiten", "unwhiten", "simulate_batch", "log_likelihood",
            "importance_weights", "gemm_bf16", "dense_bf16", "dense_bf16_backward", "gemm_autotune", "spectral_features",
            "cross_features", "lag_features", "proposal_targets",
            "gauss_nll", "adamw", "adamw_clip", "skymap", "sample_proposal", "device_status", "rfft", "irfft",
@@ -177,6 +177,34 @@ def inject(noise, offsets, h_det, N, fs, out=None):
     out = torch.empty((B, D, N), dtype=torch.float32, device=noise.device) if out is None else out
     _check(_lib.load().gwx_inject(_ptr(noise), D, L, _ptr(offsets), _ptr(h_det), B, N, fs, _ptr(out), _stream()))
     return out
+
+
+def inject_padded(noise, offsets, h_td, N, fs, out=None):
+    """Definition B injection: d [B][D][N] = noise crops + fs h_td[..., :N] (h_td [B][D][N_pad])."""
+    torch = _torch()
+    _dev(noise, torch.float32, "noise")
+    _dev(offsets, torch.int64, "offsets")
+    _dev(h_td, torch.float32, "h_td")
+    D, L = noise.shape
+    B, _, Np = h_td.shape
+    out = torch.empty((B, D, N), dtype=torch.float32, device=noise.device) if out is None else out
+    _check(_lib.load().gwx_inject_padded(_ptr(noise), D, L, _ptr(offsets), _ptr(h_td), B, N, Np, fs, _ptr(out),
+                                         _stream()))
+    return out
+
+
+def simulate_batch_padded(prior, seed, step, noise, psd, seg_len, fs, f_lo, dets, gmst, B, N, N_pad):
+    """One whitened batch with Definition B waveforms: prior draws, waveforms and projection
+    on the N_pad-point grid, inverse transforms over the padded segment, injection of their
+    first N samples, whitening (each step one libgwx call).  Returns (y, theta, offsets)."""
+    D, L = noise.shape
+    theta, offsets = sample_prior(prior, seed, step, B, L, N)
+    df = fs / N_pad
+    hp, hc = generate_waveforms(theta, f_lo, df, N_pad // 2 + 1)
+    h = project(hp, hc, theta, dets, gmst, df)
+    h_td = irfft(h, N_pad)
+    d = inject_padded(noise, offsets, h_td, N, fs)
+    return whiten(d, psd, seg_len, fs, f_lo), theta, offsets
 
 
 def whiten(d, psd, seg_len, fs, f_lo, out=None):

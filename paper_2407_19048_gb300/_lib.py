@@ -51,6 +51,7 @@ SIGNATURES = {
     "gwx_welch_psd_workspace": (c_size, [c_int, c_i64, c_i64, c_i64]),
     "gwx_welch_psd": (c_int, [c_vp, c_int, c_i64, c_dbl, c_i64, c_i64, c_vp, c_vp, c_size, c_vp]),
     "gwx_inject": (c_int, [c_vp, c_int, c_i64, c_vp, c_vp, c_i64, c_i64, c_dbl, c_vp, c_vp]),
+    "gwx_inject_padded": (c_int, [c_vp, c_int, c_i64, c_vp, c_vp, c_i64, c_i64, c_i64, c_dbl, c_vp, c_vp]),
     "gwx_whiten_workspace": (c_size, [c_int, c_i64]),
     "gwx_whiten": (c_int, [c_vp, c_vp, c_i64, c_dbl, c_dbl, c_i64, c_int, c_i64, c_vp, c_vp, c_size, c_vp]),
     "gwx_unwhiten": (c_int, [c_vp, c_vp, c_i64, c_dbl, c_dbl, c_i64, c_int, c_i64, c_vp, c_vp, c_size, c_vp]),

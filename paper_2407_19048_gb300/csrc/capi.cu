@@ -312,6 +312,23 @@ int gwx_inject(const float* noise, int D, int64_t L, const int64_t* offsets, con
                   "inject");
 }
 
+int gwx_inject_padded(const float* noise, int D, int64_t L, const int64_t* offsets, const float* h_td, int64_t B,
+                      int64_t N, int64_t N_pad, double fs, float* d, void* stream) {
+  GWX_TRY(check_window(N));
+  GWX_TRY(check_window(N_pad));
+  if (N_pad < N) return fail(GWX_ESHAPE, "N_pad=%lld < N=%lld", (long long)N_pad, (long long)N);
+  if (D < 1 || D > GWX_MAX_DET) return fail(GWX_ESHAPE, "D=%d", D);
+  if (L < N) return fail(GWX_ESHAPE, "L < N");
+  if (B < 0 || B * D > 0x7fffffffLL) return fail(GWX_ESHAPE, "B=%lld", (long long)B);
+  if (!(fs > 0.0)) return fail(GWX_EINVAL, "fs must be positive");
+  if (B == 0) return GWX_OK;
+  if (!noise || !offsets || !h_td || !d) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN8(offsets);
+  GWX_TRY(ensure_init());
+  return launched(launch_inject_padded(noise, D, L, offsets, h_td, B, N, N_pad, fs, d, as_stream(stream)),
+                  "inject_padded");
+}
+
 size_t gwx_whiten_workspace(int D, int64_t N) {
   if (D < 1 || N < 2) return 0;
   return whiten_ws_bytes(D, N);

@@ -59,6 +59,8 @@ cudaError_t launch_whiten_rows(const float* d, const float* W, int64_t rows, int
                                cudaStream_t s);
 cudaError_t launch_inject_rows(const float* noise, int D, int64_t L, const int64_t* offsets, const float2* hdet,
                                int64_t B, int64_t N, double fs, float* d, cudaStream_t s);
+cudaError_t launch_inject_padded(const float* noise, int D, int64_t L, const int64_t* offsets, const float* htd,
+                                 int64_t B, int64_t N, int64_t Np, double fs, float* d, cudaStream_t s);
 cudaError_t launch_rfft_rows(const float* x, int64_t R, int64_t N, float2* X, cudaStream_t s);
 cudaError_t launch_irfft_rows(const float2* X, int64_t R, int64_t N, float* x, cudaStream_t s);
 cudaError_t launch_simulate_fused(const DrawCoef* coef, const float* noise, int64_t L, const int64_t* offsets,

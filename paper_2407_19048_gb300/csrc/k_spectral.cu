@@ -339,6 +339,27 @@ cudaError_t launch_inject_rows(const float* noise, int D, int64_t L, const int64
   });
 }
 
+// Definition B injection: d[b][dd][i] = noise[dd][off_b + i] + fs h_td[b][dd][i] for the
+// first N samples of each padded time series h_td (rows of N_pad samples).
+__global__ void k_inject_padded(const float* __restrict__ noise, int D, int64_t L, const int64_t* __restrict__ off,
+                                const float* __restrict__ htd, int64_t B, int64_t N, int64_t Np, float fs,
+                                float* __restrict__ d) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B * D * N) return;
+  const int64_t row = i / N, t = i - row * N;
+  const int64_t b = row / D;
+  const int dd = (int)(row - b * D);
+  d[i] = noise[(int64_t)dd * L + __ldg(&off[b]) + t] + fs * htd[row * Np + t];
+}
+
+cudaError_t launch_inject_padded(const float* noise, int D, int64_t L, const int64_t* offsets, const float* htd,
+                                 int64_t B, int64_t N, int64_t Np, double fs, float* d, cudaStream_t s) {
+  const int64_t total = B * D * N;
+  if (total == 0) return cudaSuccess;
+  k_inject_padded<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(noise, D, L, offsets, htd, B, N, Np, (float)fs, d);
+  return cudaGetLastError();
+}
+
 // ----------------------------------------------------------------- rfft / irfft rows
 template <int LOGN>
 __global__ void __launch_bounds__(RowGeom<LOGN>::THREADS) k_rfft_rows(const float* __restrict__ x, int64_t rows,

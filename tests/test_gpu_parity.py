@@ -291,6 +291,25 @@ def test_simulate_batch_small_matches_oracle(gwx):
     assert np.abs(host(y) - yr).max() <= 1e-4 * rms(yr)
 
 
+@pytest.mark.parametrize("N_pad", [2048, 8192, 16384])
+def test_definition_b_matches_oracle(gwx, N_pad):
+    """Padded-grid waveforms (Definition B): waveforms and projection on the N_pad-point
+    grid, padded inverse transforms, injection of their first N samples, whitening."""
+    wl = workloads.workload("small")
+    step = 0
+    n, S = _gpu_background(gwx, wl, step)
+    y, th, off = gwx.simulate_batch_padded(wl["prior"], wl["param_seed"], step, n, S, wl["seg_len"], wl["fs"],
+                                           wl["f_lo"], wl["dets"], 0.0, wl["B"], wl["N"], N_pad)
+    ref = pipeline.simulate_batch_padded(wl, step, N_pad)
+    np.testing.assert_array_equal(host(off), ref["offsets"])
+    yr = ref["y"]
+    assert np.abs(host(y) - yr).max() <= 1e-4 * rms(yr)
+    if N_pad == wl["N"]:                     # no padding: the fused Definition A pass, to rounding
+        ya, _, _ = gwx.simulate_batch(wl["prior"], wl["param_seed"], step, n, S, wl["seg_len"], wl["fs"], wl["f_lo"],
+                                      wl["dets"], 0.0, wl["B"], wl["N"])
+        assert np.abs(host(ya) - host(y)).max() <= 1e-4 * rms(yr)
+
+
 def test_simulate_batch_unaligned_background(gwx):
     """A background that starts at an odd float (not 8-byte aligned) takes the scalar
     crop-load path; same results."""
