@@ -485,6 +485,17 @@ def flow_leg(gwx, torch, rank, steps=8000, events=32, per_event=4000, pp_events=
     ev1.record()
     torch.cuda.synchronize()
     step_ms = ev0.elapsed_time(ev1) / 50
+    # the same step captured once in a CUDA graph and replayed
+    graph = fp_t.capture_train_step(y1, th1)
+    for _ in range(3):
+        graph.replay()
+    ev0.record()
+    for _ in range(50):
+        graph.replay()
+    ev1.record()
+    torch.cuda.synchronize()
+    step_graph_ms = ev0.elapsed_time(ev1) / 50
+    del graph
     # posterior sampling latency: 20,000 draws for one event
     wl_ev = dict(workloads.workload("small", B=events), param_seed=777)
     sim_ev = gwx.simulator.Simulator(wl_ev)
@@ -584,7 +595,8 @@ def flow_leg(gwx, torch, rank, steps=8000, events=32, per_event=4000, pp_events=
         del sc
     del sim, sim_ev, sim_pp, sim_srv
     return {"shape": fp.shape, "params": fp.n_params, "train_steps": steps, "batch": batch, "train_s": train_s,
-            "simulations_per_s": steps * batch / train_s, "train_step_ms": step_ms, "loss": losses,
+            "simulations_per_s": steps * batch / train_s, "train_step_ms": step_ms,
+            "train_step_graph_ms": step_graph_ms, "loss": losses,
             "sample_20000_ms": {"p50": lat[len(lat) // 2] * 1e3, "min": lat[0] * 1e3, "max": lat[-1] * 1e3},
             "skymap_20000_ms": dict(sky, note="sample_posterior 20k + log_likelihood + importance_weights + skymap "
                                               "(HEALPix nested, importance-weighted), median of 10, host time"),

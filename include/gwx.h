@@ -517,11 +517,14 @@ int gwx_flow_proposal(const float* x, const float* z, const float* sum_s, int64_
  * into grads (flat, same layout as params; the whole array is rewritten), then (step >= 1)
  * gwx_adamw over the flat array with step counter `step` (gwx_adamw_clip when clip > 0:
  * gradients scaled to a Euclidean norm of at most clip); step 0 computes the loss and
- * gradients only.  *loss_mean (device double) = batch mean of -ln q_x.  B a multiple of 8
+ * gradients only.  step_counter (optional, a device int64): the update takes its step
+ * number from *step_counter + 1 on the device and stores it back, so that a captured
+ * CUDA graph of the call replays with the right AdamW bias corrections (step then only
+ * has to be >= 1).  *loss_mean (device double) = batch mean of -ln q_x.  B a multiple of 8
  * in [8, 65535 * 32].  Workspace gwx_flow_train_workspace(shape, B, D, N). */
 size_t gwx_flow_train_workspace(const gwx_flow_shape* shape, int64_t B, int D, int64_t N);
 int gwx_flow_train_step(const gwx_flow_shape* shape, float* params, void* params_bf16, float* grads, float* m,
-                        float* v, int64_t step, double lr, double beta1, double beta2, double eps,
+                        float* v, int64_t step, int64_t* step_counter, double lr, double beta1, double beta2, double eps,
                         double weight_decay, double clip, const double* mean8, const double* scale8, const float* y,
                         const double* theta, int64_t B, int D, int64_t N, double fs, double f_lo,
                         double* loss_mean, void* workspace, size_t workspace_bytes, void* stream);

@@ -654,7 +654,8 @@ def flow_proposal(x, z, sum_s, mean8, scale8, prior, truth, event_offsets, seed,
 
 
 def flow_train_step(shape, params, params_bf16, grads, m, v, step, lr, mean8, scale8, y, theta, fs, f_lo,
-                    beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, clip=0.0, loss_mean=None, workspace=None):
+                    beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, clip=0.0, loss_mean=None, workspace=None,
+                    step_counter=None):
     """One training step (step 0: loss and gradients only).  Returns loss_mean (device
     float64 [1]).  `workspace` may be a preallocated (tensor, bytes) pair."""
     torch = _torch()
@@ -667,7 +668,7 @@ def flow_train_step(shape, params, params_bf16, grads, m, v, step, lr, mean8, sc
     ws, nb = workspace if workspace is not None else _workspace(
         lib.gwx_flow_train_workspace(ctypes.byref(sh), B, D, N), y.device)
     _check(lib.gwx_flow_train_step(ctypes.byref(sh), _ptr(params), _ptr(params_bf16), _ptr(grads), _ptr(m), _ptr(v),
-                                   step, lr, beta1, beta2, eps, weight_decay, clip, _host8(mean8), _host8(scale8),
+                                   step, _ptr(step_counter) if step_counter is not None else None, lr, beta1, beta2, eps, weight_decay, clip, _host8(mean8), _host8(scale8),
                                    _ptr(y),
                                    _ptr(theta), B, D, N, fs, f_lo, _ptr(loss_mean), _ptr(ws), nb, _stream()))
     return loss_mean

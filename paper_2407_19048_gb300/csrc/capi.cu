@@ -1007,7 +1007,7 @@ size_t gwx_flow_train_workspace(const gwx_flow_shape* shape, int64_t B, int D, i
 }
 
 int gwx_flow_train_step(const gwx_flow_shape* shape, float* params, void* params_bf16, float* grads, float* m,
-                        float* v, int64_t step, double lr, double beta1, double beta2, double eps,
+                        float* v, int64_t step, int64_t* step_counter, double lr, double beta1, double beta2, double eps,
                         double weight_decay, double clip, const double* mean8, const double* scale8, const float* y,
                         const double* theta, int64_t B, int D, int64_t N, double fs, double f_lo,
                         double* loss_mean, void* workspace, size_t workspace_bytes, void* stream) {
@@ -1030,8 +1030,9 @@ int gwx_flow_train_step(const gwx_flow_shape* shape, float* params, void* params
   GWX_TRY(check_ws(workspace, workspace_bytes, gwx_flow_train_workspace(shape, B, D, N)));
   GWX_TRY(ensure_init());
   if (!(clip >= 0.0) || !isfinite(clip)) return fail(GWX_EINVAL, "clip=%g", clip);
-  return launched(flow_train_step(*shape, params, params_bf16, grads, m, v, step, lr, beta1, beta2, eps, weight_decay,
-                                  clip, mean8, scale8, y, theta, B, D, N, k_lo, loss_mean, workspace, as_stream(stream)),
+  if (step_counter) GWX_ALIGN8(step_counter);
+  return launched(flow_train_step(*shape, params, params_bf16, grads, m, v, step, step_counter, lr, beta1, beta2, eps,
+                                  weight_decay, clip, mean8, scale8, y, theta, B, D, N, k_lo, loss_mean, workspace, as_stream(stream)),
                   "flow_train_step");
 }
 

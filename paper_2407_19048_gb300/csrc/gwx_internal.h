@@ -117,8 +117,11 @@ cudaError_t launch_adamw(float* p, const float* g, float* m, float* v, int64_t n
 // AdamW on gradients scaled by min(1, clip / |g|) (|g| the FP64 norm of all n gradients);
 // workspace adamw_clip_ws() bytes.
 size_t adamw_clip_ws();
+// With counter (a device int64) the step is *counter + 1, stored back, and clip <= 0
+// means no clipping; without it clip must be positive and `step` is used.
 cudaError_t launch_adamw_clip(float* p, const float* g, float* m, float* v, int64_t n, double lr, double b1, double b2,
-                              double eps, double wd, int64_t step, double clip, void* p16, void* ws, cudaStream_t s);
+                              double eps, double wd, int64_t step, double clip, void* p16, void* ws, cudaStream_t s,
+                              int64_t* counter = nullptr);
 cudaError_t launch_proposal(const float* net, int ldn, const double* mean, const double* scale, const gwx_prior& pr,
                             const double* truth, int64_t E, const int64_t* off, int64_t S, uint64_t seed,
                             uint32_t counter, int fix_angles, double* theta, double* lratio, cudaStream_t s);
@@ -153,7 +156,7 @@ cudaError_t launch_flow_sample_fused(const void* params_bf16, const float* param
 cudaError_t flow_fused_status(int* status);
 size_t flow_train_ws(const gwx_flow_shape& sh, int64_t B, int D, int64_t N);
 cudaError_t flow_train_step(const gwx_flow_shape& sh, float* params, void* params_bf16, float* grads, float* m,
-                            float* v, int64_t step, double lr, double b1, double b2, double eps, double wd, double clip,
+                            float* v, int64_t step, int64_t* step_counter, double lr, double b1, double b2, double eps, double wd, double clip,
                             const double* mean8, const double* scale8, const float* y, const double* theta, int64_t B,
                             int D, int64_t N, int k_lo, double* loss_mean, void* ws, cudaStream_t s);
 size_t flow_log_prob_ws(const gwx_flow_shape& sh, int64_t B, int D, int64_t N);

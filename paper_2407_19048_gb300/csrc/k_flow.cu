@@ -533,7 +533,7 @@ size_t flow_train_ws(const gwx_flow_shape& sh, int64_t B, int D, int64_t N) {
 }
 
 cudaError_t flow_train_step(const gwx_flow_shape& sh, float* params, void* params_bf16, float* grads, float* m,
-                            float* v, int64_t step, double lr, double b1, double b2, double eps, double wd, double clip,
+                            float* v, int64_t step, int64_t* step_counter, double lr, double b1, double b2, double eps, double wd, double clip,
                             const double* mean8, const double* scale8, const float* y, const double* theta, int64_t B,
                             int D, int64_t N, int k_lo, double* loss_mean, void* ws, cudaStream_t s) {
   const FlowDims d = dims_of(sh);
@@ -579,7 +579,10 @@ cudaError_t flow_train_step(const gwx_flow_shape& sh, float* params, void* param
   FL_TRY(launch_dense_backward(w.feat, P.W(0), P.b(1), w.dB, B, d.He, d.F, GWX_ACT_RELU, nullptr, grads + P.off[0],
                                grads + P.off[1], w.dws, 0, s));
   if (step >= 1) {
-    if (clip > 0.0)
+    if (step_counter)
+      FL_TRY(launch_adamw_clip(params, grads, m, v, n_params, lr, b1, b2, eps, wd, step, clip, params_bf16, w.clip, s,
+                               step_counter));
+    else if (clip > 0.0)
       FL_TRY(launch_adamw_clip(params, grads, m, v, n_params, lr, b1, b2, eps, wd, step, clip, params_bf16, w.clip, s));
     else
       FL_TRY(launch_adamw(params, grads, m, v, n_params, lr, b1, b2, eps, wd, step, params_bf16, s));

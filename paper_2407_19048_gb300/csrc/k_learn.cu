@@ -193,11 +193,28 @@ __global__ void __launch_bounds__(256) k_clip_scale(const double* __restrict__ p
   }
 }
 
+// The step counter on the device (CUDA-graph replays): advance it and write the bias
+// corrections 1 - beta^step of the update that follows; with clip <= 0 the gradient
+// scale is 1.
+__global__ void k_adam_step(int64_t* __restrict__ counter, double b1, double b2, float* __restrict__ coef,
+                            float* __restrict__ scale, int set_scale) {
+  const int64_t step = *counter + 1;
+  *counter = step;
+  coef[0] = (float)(1.0 - pow(b1, (double)step));
+  coef[1] = (float)(1.0 - pow(b2, (double)step));
+  if (set_scale) *scale = 1.f;
+}
+
 __global__ void k_adamw_scaled(float* __restrict__ p, const float* __restrict__ g, const float* __restrict__ gscale,
                                float* __restrict__ m, float* __restrict__ v, int64_t n, float lr, float b1, float b2,
-                               float eps, float wd, float c1, float c2, __nv_bfloat16* __restrict__ p16) {
+                               float eps, float wd, float c1, float c2, const float* __restrict__ coef,
+                               __nv_bfloat16* __restrict__ p16) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  if (coef) {
+    c1 = __ldg(coef);
+    c2 = __ldg(coef + 1);
+  }
   const float gi = g[i] * __ldg(gscale);
   const float mi = b1 * m[i] + (1.f - b1) * gi;
   const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
@@ -365,14 +382,20 @@ cudaError_t launch_adamw(float* p, const float* g, float* m, float* v, int64_t n
 size_t adamw_clip_ws() { return CLIP_BLOCKS * sizeof(double) + 256; }
 
 cudaError_t launch_adamw_clip(float* p, const float* g, float* m, float* v, int64_t n, double lr, double b1, double b2,
-                              double eps, double wd, int64_t step, double clip, void* p16, void* ws, cudaStream_t s) {
+                              double eps, double wd, int64_t step, double clip, void* p16, void* ws, cudaStream_t s,
+                              int64_t* counter) {
   double* part = reinterpret_cast<double*>(ws);
   float* scale = reinterpret_cast<float*>(reinterpret_cast<char*>(ws) + CLIP_BLOCKS * sizeof(double));
-  k_sumsq<<<CLIP_BLOCKS, 256, 0, s>>>(g, n, part);
-  k_clip_scale<<<1, 256, 0, s>>>(part, CLIP_BLOCKS, clip, scale);
-  const float c1 = (float)(1.0 - pow(b1, (double)step)), c2 = (float)(1.0 - pow(b2, (double)step));
+  float* coef = scale + 4;   // 16-byte slot after the scale
+  if (clip > 0.0) {
+    k_sumsq<<<CLIP_BLOCKS, 256, 0, s>>>(g, n, part);
+    k_clip_scale<<<1, 256, 0, s>>>(part, CLIP_BLOCKS, clip, scale);
+  }
+  if (counter) k_adam_step<<<1, 1, 0, s>>>(counter, b1, b2, coef, scale, clip > 0.0 ? 0 : 1);
+  const float c1 = counter ? 1.f : (float)(1.0 - pow(b1, (double)step));
+  const float c2 = counter ? 1.f : (float)(1.0 - pow(b2, (double)step));
   k_adamw_scaled<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, g, scale, m, v, n, (float)lr, (float)b1, (float)b2,
-                                                             (float)eps, (float)wd, c1, c2,
+                                                             (float)eps, (float)wd, c1, c2, counter ? coef : nullptr,
                                                              reinterpret_cast<__nv_bfloat16*>(p16));
   return cudaGetLastError();
 }

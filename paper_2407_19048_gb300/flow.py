@@ -114,6 +114,33 @@ class FlowPosterior:
             self.steps += 1
         return self._loss
 
+    def capture_train_step(self, y, theta):
+        """Capture one training step on the batch buffers y [B][D][N], theta [11][B] into a
+        CUDA graph and return it: each replay runs forward, backward and the AdamW update
+        of whatever batch those buffers hold, with the step count kept on the device
+        (call note_replay() after each replay to keep the host count in step)."""
+        import ctypes
+        import torch
+        gwx = self.gwx
+        if getattr(self, "step_dev", None) is None:
+            self.step_dev = torch.tensor([self.steps], dtype=torch.int64, device=self.dev)
+        else:
+            self.step_dev.fill_(self.steps)
+        B = y.shape[0]
+        sh = gwx._shape(self.shape)
+        nb = _lib.load().gwx_flow_train_workspace(ctypes.byref(sh), B, self.D, self.N)
+        ws = self._workspace(("train", B), nb)
+        graph = torch.cuda.CUDAGraph()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph):
+            gwx.flow_train_step(self.shape, self.params, self.params16, self.grads, self.m, self.v, 1, self.lr,
+                                self.mean, self.scale, y, theta, self.fs, self.f_lo, weight_decay=self.wd,
+                                clip=self.clip, loss_mean=self._loss, workspace=ws, step_counter=self.step_dev)
+        return graph
+
+    def note_replay(self):
+        self.steps += 1
+
     def sample(self, y_events, truth, event_offsets, seed, counter):
         """Posterior draws for events y_events [E][D][N] (spins and t_c from truth):
         (theta [11][S], ln q_r [S], ln prior_r - ln q_r [S])."""

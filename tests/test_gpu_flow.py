@@ -365,3 +365,28 @@ def test_scorer_with_the_flow_matches_the_separate_calls(gwx, sampler):
         _, ess, eff, lnz = gwx.importance_weights(lnl, offs, lr)
         ref = (float(ess[0]), float(eff[0]), float(lnz[0]))
         assert got == ref or np.allclose(got, ref, rtol=1e-12, atol=0), (got, ref)
+
+
+def test_captured_training_step_replays_like_eager_steps(gwx):
+    """A CUDA graph of one training step (AdamW step count on the device) replayed on
+    successive batches matches the eager steps on the same batches."""
+    from paper_2407_19048_gb300.flow import FlowPosterior
+    from paper_2407_19048_gb300.simulator import Simulator
+    kw = dict(layers=3, hidden=64, context=16, embed_hidden=32, group=GROUP, clip=0.5)
+    sim = Simulator(WL)
+    a = FlowPosterior(WL, seed=6, **kw)
+    b = FlowPosterior(WL, seed=6, **kw)
+    y0, th0, _ = sim.step(0)
+    yb, thb = y0.clone(), th0.clone()          # the graph's fixed input buffers
+    graph = b.capture_train_step(yb, thb)
+    for step in range(4):
+        y, th, _ = sim.step(step)
+        a.train_step(y, th)
+        yb.copy_(y)
+        thb.copy_(th)
+        graph.replay()
+        b.note_replay()
+    torch.cuda.synchronize()
+    assert int(b.step_dev.item()) == 4 and b.steps == 4
+    assert torch.allclose(a.params, b.params, rtol=1e-5, atol=1e-7)
+    assert torch.allclose(a.m, b.m, rtol=1e-5, atol=1e-9)
