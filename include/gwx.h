@@ -550,6 +550,27 @@ int gwx_sample_posterior(const gwx_flow_shape* shape, const float* params, const
                          const int64_t* event_offsets, int64_t S, uint64_t seed, uint32_t counter, double* theta,
                          double* log_q, double* log_ratio, void* workspace, size_t workspace_bytes, void* stream);
 
+/* ---- self-supervised pre-training of the data summary (Sec. 4.1) ------------------
+ * Two views of each simulated source, identical but for the merger time, are summarised
+ * and expanded (x, x' [B][d]); the summary is trained to make them agree with the VICReg
+ * loss (Bardes, Ponce and LeCun 2022) and the paper's weights (1, 1, 5):
+ *   L = l1 sum (x - x')^2 / (B d) + l2 (v(x) + v(x')) + l3 (c(x) + c(x')),
+ *   v(z) = sum_j max(0, 1 - sqrt(Var_j(z) + 1e-4)) / d,  c(z) = sum_{i != j} C_ij(z)^2 / d,
+ * Var and C the unbiased sample variance and covariance over the batch.
+ * gwx_vicreg: *loss (device double), terms (optional device double[5]: inv, v(x), v(x'),
+ *   c(x), c(x')), grad_x, grad_xp = dL/dx, dL/dx' (FP32 [B][d]).  2 <= B, 1 <= d <= 32.
+ * gwx_retime: theta_out = theta_in ([GWX_NPARAM][B]) with the merger time redrawn
+ *   uniformly in [tc_lo, tc_hi] (uniform52 of Philox4x32-10 words 0, 1 at counter
+ *   (b, 0, 5, counter), key seed): the second view's source.
+ * gwx_prepare_theta: gwx_prepare_batch for given parameters theta [GWX_NPARAM][B] (no
+ *   prior draws), so that gwx_simulate_prepared renders them (with the caller's offsets). */
+int gwx_vicreg(const float* x, const float* xp, int64_t B, int d, double lambda1, double lambda2, double lambda3,
+               double* loss, double* terms, float* grad_x, float* grad_xp, void* stream);
+int gwx_retime(const double* theta_in, double* theta_out, int64_t B, double tc_lo, double tc_hi, uint64_t seed,
+               uint32_t counter, void* stream);
+int gwx_prepare_theta(const double* theta, int64_t L, int64_t N, double fs, double f_lo, const int32_t* det_ids,
+                      int D, double gmst, int64_t B, void* workspace, size_t workspace_bytes, void* stream);
+
 /* ---- sky maps ---------------------------------------------------------------------
  * The paper's inference ends in a sky-localisation map in the HEALPix format (Sec. 5).
  * gwx_skymap: map [12 nside^2] (FP64) = the histogram of samples' sky positions (rows RA

@@ -74,3 +74,20 @@ def grad(x, xp, lam=(1.0, 1.0, 5.0)):
         g = g + lam[2] * 4.0 / (d * (B - 1)) * (zc @ off)
         out.append(g)
     return out[0], out[1]
+
+
+TAG_RETIME = 5
+
+
+def retime(theta, tc_lo, tc_hi, seed, counter):
+    """The second view's parameters: theta [11][B] with tc redrawn uniformly in
+    [tc_lo, tc_hi]; u = uniform52 of Philox4x32-10 words 0, 1 at counter
+    (b, 0, TAG_RETIME, counter), key seed."""
+    from .philox import key_of, philox4x32_10, uniform52
+    th = np.array(theta, dtype=np.float64, copy=True)
+    B = th.shape[1]
+    k0, k1 = key_of(seed)
+    w = philox4x32_10(np.arange(B, dtype=np.uint64).astype(np.uint32), np.uint32(0), np.uint32(TAG_RETIME),
+                      np.uint32(counter & 0xFFFFFFFF), k0, k1)
+    th[5] = tc_lo + (tc_hi - tc_lo) * uniform52(w[0], w[1])
+    return th

@@ -26,7 +26,7 @@ __all__ = ["GwxError", "version", "init", "detector_geometry", "sample_prior", "
            "colored_noise", "welch_psd", "inject", "inject_padded", "simulate_batch_padded", "whiten", "unwhiten", "simulate_batch", "log_likelihood",
            "importance_weights", "gemm_bf16", "dense_bf16", "dense_bf16_backward", "gemm_autotune", "spectral_features",
            "cross_features", "lag_features", "proposal_targets",
-           "gauss_nll", "adamw", "adamw_clip", "skymap", "sample_proposal", "device_status", "rfft", "irfft",
+           "gauss_nll", "adamw", "adamw_clip", "skymap", "vicreg", "retime", "sample_proposal", "device_status", "rfft", "irfft",
            "workspace_bytes", "TAYLORF2", "IMRPHENOMD", "DETECTORS"]
 
 
@@ -443,6 +443,32 @@ def adamw_clip(param, grad, m, v, step, lr, clip, beta1=0.9, beta2=0.999, eps=1e
     ws, nb = _workspace(lib.gwx_adamw_clip_workspace(), param.device)
     _check(lib.gwx_adamw_clip(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(), lr, beta1, beta2, eps,
                               weight_decay, step, clip, _ptr(param_bf16), _ptr(ws), nb, _stream()))
+
+
+def vicreg(x, xp, lam=(1.0, 1.0, 5.0), grad_x=None, grad_xp=None):
+    """VICReg loss of two views' representations x, x' [B][d] (float32): returns
+    (loss [1] float64, terms [5] float64, dL/dx, dL/dx')."""
+    torch = _torch()
+    _dev(x, torch.float32, "x")
+    _dev(xp, torch.float32, "xp")
+    B, d = x.shape
+    dev = x.device
+    loss = torch.empty(1, dtype=torch.float64, device=dev)
+    terms = torch.empty(5, dtype=torch.float64, device=dev)
+    gx = torch.empty_like(x) if grad_x is None else grad_x
+    gxp = torch.empty_like(xp) if grad_xp is None else grad_xp
+    _check(_lib.load().gwx_vicreg(_ptr(x), _ptr(xp), B, d, lam[0], lam[1], lam[2], _ptr(loss), _ptr(terms), _ptr(gx),
+                                  _ptr(gxp), _stream()))
+    return loss, terms, gx, gxp
+
+
+def retime(theta, tc_lo, tc_hi, seed, counter, out=None):
+    """theta [11][B] with the merger time redrawn uniformly in [tc_lo, tc_hi]."""
+    torch = _torch()
+    _dev(theta, torch.float64, "theta")
+    out = torch.empty_like(theta) if out is None else out
+    _check(_lib.load().gwx_retime(_ptr(theta), _ptr(out), theta.shape[1], tc_lo, tc_hi, seed, counter, _stream()))
+    return out
 
 
 def skymap(theta, nside, weights=None, out=None):

@@ -86,6 +86,10 @@ SIGNATURES = {
     "gwx_adamw_clip_workspace": (c_size, []),
     "gwx_adamw_clip": (c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl, c_i64, c_dbl, c_vp,
                                c_vp, c_size, c_vp]),
+    "gwx_vicreg": (c_int, [c_vp, c_vp, c_i64, c_int, c_dbl, c_dbl, c_dbl, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "gwx_retime": (c_int, [c_vp, c_vp, c_i64, c_dbl, c_dbl, c_u64, c_u32, c_vp]),
+    "gwx_prepare_theta": (c_int, [c_vp, c_i64, c_i64, c_dbl, c_dbl, c_i32p, c_int, c_dbl, c_i64, c_vp, c_size,
+                                  c_vp]),
     "gwx_skymap_workspace": (c_size, []),
     "gwx_skymap": (c_int, [c_vp, c_vp, c_i64, c_int, c_vp, c_vp, c_size, c_vp]),
     "gwx_sample_proposal": (c_int, [c_vp, c_int, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl),

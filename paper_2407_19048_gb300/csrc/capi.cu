@@ -393,6 +393,23 @@ int gwx_prepare_batch(const gwx_prior* prior, uint64_t seed, uint32_t step, int6
                   "draw set-up");
 }
 
+int gwx_prepare_theta(const double* theta, int64_t L, int64_t N, double fs, double f_lo, const int32_t* det_ids,
+                      int D, double gmst, int64_t B, void* workspace, size_t workspace_bytes, void* stream) {
+  DetParams dp;
+  GWX_TRY(make_detparams(det_ids, D, dp));
+  int k_lo = 0;
+  GWX_TRY(check_sim_shapes(D, L, B, N, fs, f_lo, &k_lo));
+  if (!isfinite(gmst)) return fail(GWX_EINVAL, "bad gmst");
+  if (B == 0) return GWX_OK;
+  if (!theta) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN8(theta);
+  GWX_TRY(check_ws(workspace, workspace_bytes, gwx_simulate_batch_workspace(D, B, N)));
+  GWX_TRY(ensure_init());
+  return launched(launch_draw_setup(theta, B, k_lo, fs / (double)N, fs, N / 2 + 1, dp, gmst,
+                                    sim_coef(workspace, D, N), as_stream(stream)),
+                  "draw set-up");
+}
+
 int gwx_simulate_prepared(const float* noise, int64_t L, const double* psd, int64_t seg_len, double fs, double f_lo,
                           int D, int64_t B, int64_t N, const int64_t* offsets, float* y, int flags, void* workspace,
                           size_t workspace_bytes, void* stream) {
@@ -732,6 +749,31 @@ int gwx_adamw(float* param, const float* grad, float* m, float* v, int64_t n, do
   return launched(launch_adamw(param, grad, m, v, n, lr, beta1, beta2, eps, weight_decay, step, param_bf16,
                                as_stream(stream)),
                   "adamw");
+}
+
+int gwx_vicreg(const float* x, const float* xp, int64_t B, int d, double lambda1, double lambda2, double lambda3,
+               double* loss, double* terms, float* grad_x, float* grad_xp, void* stream) {
+  if (B < 2 || B > 0x7fffffffLL || !vicreg_supported((int)B, d))
+    return fail(GWX_ESHAPE, "B=%lld d=%d (need B >= 2, 1 <= d <= 32)", (long long)B, d);
+  if (!x || !xp || !loss || !grad_x || !grad_xp) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN8(loss);
+  if (terms) GWX_ALIGN8(terms);
+  GWX_TRY(ensure_init());
+  return launched(launch_vicreg(x, xp, (int)B, d, lambda1, lambda2, lambda3, loss, terms, grad_x, grad_xp,
+                                as_stream(stream)),
+                  "vicreg");
+}
+
+int gwx_retime(const double* theta_in, double* theta_out, int64_t B, double tc_lo, double tc_hi, uint64_t seed,
+               uint32_t counter, void* stream) {
+  if (B < 0) return fail(GWX_ESHAPE, "B=%lld", (long long)B);
+  if (!(tc_hi >= tc_lo) || !isfinite(tc_lo) || !isfinite(tc_hi)) return fail(GWX_EINVAL, "tc range");
+  if (B == 0) return GWX_OK;
+  if (!theta_in || !theta_out) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN8(theta_in);
+  GWX_ALIGN8(theta_out);
+  GWX_TRY(ensure_init());
+  return launched(launch_retime(theta_in, theta_out, B, tc_lo, tc_hi, seed, counter, as_stream(stream)), "retime");
 }
 
 size_t gwx_skymap_workspace(void) { return kAlign; }

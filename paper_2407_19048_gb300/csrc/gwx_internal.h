@@ -173,6 +173,13 @@ cudaError_t flow_sample(const gwx_flow_shape& sh, const float* params, const voi
 cudaError_t launch_skymap(const double* theta, const double* weights, int64_t S, int nside, double* map, void* ws,
                           cudaStream_t s);
 
+// VICReg pre-training (k_vicreg.cu).
+bool vicreg_supported(int B, int d);
+cudaError_t launch_vicreg(const float* x, const float* xp, int B, int d, double l1, double l2, double l3,
+                          double* loss, double* terms, float* gx, float* gxp, cudaStream_t s);
+cudaError_t launch_retime(const double* in, double* out, int64_t B, double tc_lo, double tc_hi, uint64_t seed,
+                          uint32_t counter, cudaStream_t s);
+
 // Record msg as the calling thread's gwx_last_error() message; returns status.
 int set_last_error(int status, const char* msg);
 
