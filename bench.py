@@ -443,12 +443,14 @@ def padded_leg(gwx, torch, rank, B=2048, N_pad=8192, reps=20):
 
 
 def flow_leg(gwx, torch, rank, steps=8000, events=32, per_event=4000, pp_events=200, pp_samples=500, lr=6e-4,
-             cross=True, batch=4096, layers=16, hidden=256, clip=1.0):
+             cross=True, batch=4096, layers=16, hidden=256, clip=1.0, pretrain_steps=2000):
     """The conditional coupling flow (16 affine coupling layers, conditioners 72 -> 256 ->
     256 -> 8; embedding 1968 -> 512 -> 512 -> 64 on log group powers, inter-detector cross
     spectra and lag-one spectral products; tcgen05 dense layers) trained with AdamW (lr
     6e-4, weight decay 2e-3, gradient norm clipped at 1) on 4096-draw batches of the
-    two-detector workload, 8000 steps = 32.8 M simulations (one C-ABI call per step); then
+    two-detector workload, 8000 steps = 32.8 M simulations (one CUDA-graph replay of the
+    C-ABI training call per step), after 2000 steps of VICReg pre-training of the data
+    summary on pairs of views that differ only in merger time; then
     posterior sampling (20,000 draws of one event, the paper's inference size), importance
     sampling of 32 events x 4000 draws against the prior as proposal (spins and merger
     time known to both), and a PP test of the flow's marginals."""
@@ -460,6 +462,21 @@ def flow_leg(gwx, torch, rank, steps=8000, events=32, per_event=4000, pp_events=
     sim = gwx.simulator.Simulator(wl, pipeline=True, background_every=16)
     fp = FlowPosterior(wl, layers=layers, hidden=hidden, context=64, embed_hidden=512, group=4, seed=0, lr=lr,
                        weight_decay=2e-3, cross=cross, clip=clip)
+    pre = None
+    if pretrain_steps:
+        from paper_2407_19048_gb300.pretrain import VICRegPretrainer
+        pt = VICRegPretrainer(fp, batch=1024)
+        torch.cuda.synchronize()
+        a0 = time.perf_counter()
+        vl = []
+        for k in range(pretrain_steps):
+            loss_v, terms_v = pt.step(step_counter(rank, 70000 + k))
+            if k % max(1, pretrain_steps // 4) == 0 or k == pretrain_steps - 1:
+                vl.append((k, loss_v.clone(), terms_v.clone()))
+        torch.cuda.synchronize()
+        pre = {"steps": pretrain_steps, "pairs_per_step": 1024, "seconds": time.perf_counter() - a0,
+               "vicreg": [(k, float(l.item()), [float(t) for t in tt.cpu()]) for k, l, tt in vl]}
+        del pt
     losses = []
     # the training step runs as a CUDA graph per simulator buffer set (the pipelined
     # simulator alternates two), captured once before the timing
@@ -602,7 +619,7 @@ def flow_leg(gwx, torch, rank, steps=8000, events=32, per_event=4000, pp_events=
     del sim, sim_ev, sim_pp, sim_srv
     return {"shape": fp.shape, "params": fp.n_params, "train_steps": steps, "batch": batch, "train_s": train_s,
             "simulations_per_s": steps * batch / train_s, "train_step_ms": step_ms,
-            "train_step_graph_ms": step_graph_ms, "loss": losses,
+            "train_step_graph_ms": step_graph_ms, "loss": losses, "vicreg_pretraining": pre,
             "sample_20000_ms": {"p50": lat[len(lat) // 2] * 1e3, "min": lat[0] * 1e3, "max": lat[-1] * 1e3},
             "skymap_20000_ms": dict(sky, note="sample_posterior 20k + log_likelihood + importance_weights + skymap "
                                               "(HEALPix nested, importance-weighted), median of 10, host time"),
