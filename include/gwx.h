@@ -571,6 +571,40 @@ int gwx_retime(const double* theta_in, double* theta_out, int64_t B, double tc_l
 int gwx_prepare_theta(const double* theta, int64_t L, int64_t N, double fs, double f_lo, const int32_t* det_ids,
                       int D, double gmst, int64_t B, void* workspace, size_t workspace_bytes, void* stream);
 
+/* ---- ResNet-1D data summary (Sec. 4) ------------------------------------------------
+ * 1-D convolutions on channels-last activations x [B][T][C] are im2col rows times the
+ * weights W [C_out][K] on the tensor cores (gwx_dense_bf16, gwx_dense_bf16_backward):
+ *   cols[b, t][j C + c] = x[b][s t + j - p][c] (zero outside 0 .. T - 1; columns k C .. K - 1
+ *   zero), T_out = (T + 2 p - k) / s + 1.
+ * gwx_im2col: bfloat16 x -> bfloat16 cols [B T_out][K]; C, K multiples of 8.
+ * gwx_im2col_cf: the same rows from channels-first FP32 y [B][D][N] (whitened strain).
+ * gwx_col2im: the adjoint: dx [B][T][C] (FP32) = addend (optional) + sum over the rows and
+ *   taps that read x[b][t][c] of dcols (FP32 [B T_out][K]).
+ * gwx_group_norm: per sample and group of C / G channels, over all T and those channels:
+ *   out = act(gamma_c (z - mean) / sqrt(var + 1e-5) + beta_c + residual) (biased variance,
+ *   FP64 sums; residual FP32 or bfloat16 or none; act ReLU when relu != 0); out bfloat16
+ *   (out16) and/or FP32 (out32); mean_rstd [B][G][2] kept for the backward.
+ * gwx_group_norm_backward: dz = rstd (dy gamma - mean(dy gamma) - xhat mean(dy gamma xhat))
+ *   per group, dgamma_c = sum dy xhat, dbeta_c = sum dy; scratch [B][G][2].
+ * gwx_relu_mask: d = dy [out > 0] (out bfloat16).
+ * gwx_maxpool: kernel 3, stride 2, padding 1 over time, the first maximum of a window;
+ *   arg [B][T_out][C] its offset (0..2); gwx_maxpool_backward routes dy there.
+ * gwx_mean_time: m [B][C] (bfloat16) = the mean over time; gwx_mean_time_backward. */
+int gwx_im2col(const void* x, int64_t B, int T, int C, int k, int s, int p, int K, void* cols, void* stream);
+int gwx_im2col_cf(const float* y, int64_t B, int D, int N, int k, int s, int p, int K, void* cols, void* stream);
+int gwx_col2im(const float* dcols, int64_t B, int T, int C, int k, int s, int p, int K, const float* addend, float* dx,
+               void* stream);
+int gwx_group_norm(const float* z, int64_t B, int T, int C, int G, const float* gamma, const float* beta,
+                   const float* residual32, const void* residual16, int relu, void* out16, float* out32,
+                   float* mean_rstd, void* stream);
+int gwx_group_norm_backward(const float* dy, const float* z, int64_t B, int T, int C, int G, const float* mean_rstd,
+                            const float* gamma, float* scratch, float* dz, float* dgamma, float* dbeta, void* stream);
+int gwx_relu_mask(const float* dy, const void* out, int64_t n, float* d, void* stream);
+int gwx_maxpool(const void* x, int64_t B, int T, int C, void* y, uint8_t* arg, void* stream);
+int gwx_maxpool_backward(const float* dy, const uint8_t* arg, int64_t B, int T, int C, float* dx, void* stream);
+int gwx_mean_time(const void* x, int64_t B, int T, int C, void* m, void* stream);
+int gwx_mean_time_backward(const float* dm, int64_t B, int T, int C, float* dx, void* stream);
+
 /* ---- sky maps ---------------------------------------------------------------------
  * The paper's inference ends in a sky-localisation map in the HEALPix format (Sec. 5).
  * gwx_skymap: map [12 nside^2] (FP64) = the histogram of samples' sky positions (rows RA

@@ -90,6 +90,18 @@ SIGNATURES = {
     "gwx_retime": (c_int, [c_vp, c_vp, c_i64, c_dbl, c_dbl, c_u64, c_u32, c_vp]),
     "gwx_prepare_theta": (c_int, [c_vp, c_i64, c_i64, c_dbl, c_dbl, c_i32p, c_int, c_dbl, c_i64, c_vp, c_size,
                                   c_vp]),
+    "gwx_im2col": (c_int, [c_vp, c_i64, c_int, c_int, c_int, c_int, c_int, c_int, c_vp, c_vp]),
+    "gwx_im2col_cf": (c_int, [c_vp, c_i64, c_int, c_int, c_int, c_int, c_int, c_int, c_vp, c_vp]),
+    "gwx_col2im": (c_int, [c_vp, c_i64, c_int, c_int, c_int, c_int, c_int, c_int, c_vp, c_vp, c_vp]),
+    "gwx_group_norm": (c_int, [c_vp, c_i64, c_int, c_int, c_int, c_vp, c_vp, c_vp, c_vp, c_int, c_vp, c_vp, c_vp,
+                               c_vp]),
+    "gwx_group_norm_backward": (c_int, [c_vp, c_vp, c_i64, c_int, c_int, c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
+                                        c_vp]),
+    "gwx_relu_mask": (c_int, [c_vp, c_vp, c_i64, c_vp, c_vp]),
+    "gwx_maxpool": (c_int, [c_vp, c_i64, c_int, c_int, c_vp, c_vp, c_vp]),
+    "gwx_maxpool_backward": (c_int, [c_vp, c_vp, c_i64, c_int, c_int, c_vp, c_vp]),
+    "gwx_mean_time": (c_int, [c_vp, c_i64, c_int, c_int, c_vp, c_vp]),
+    "gwx_mean_time_backward": (c_int, [c_vp, c_i64, c_int, c_int, c_vp, c_vp]),
     "gwx_skymap_workspace": (c_size, []),
     "gwx_skymap": (c_int, [c_vp, c_vp, c_i64, c_int, c_vp, c_vp, c_size, c_vp]),
     "gwx_sample_proposal": (c_int, [c_vp, c_int, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl),

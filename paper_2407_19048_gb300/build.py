@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgwx.so")
-UNITS = ["capi.cu", "k_random.cu", "k_spectral.cu", "k_waveform.cu", "k_fused.cu", "k_weights.cu", "k_gemm.cu", "k_dense.cu", "k_learn.cu", "k_noalloc.cu", "k_flow.cu", "k_flow_fused.cu", "k_skymap.cu", "k_vicreg.cu"]
+UNITS = ["capi.cu", "k_random.cu", "k_spectral.cu", "k_waveform.cu", "k_fused.cu", "k_weights.cu", "k_gemm.cu", "k_dense.cu", "k_learn.cu", "k_noalloc.cu", "k_flow.cu", "k_flow_fused.cu", "k_skymap.cu", "k_vicreg.cu", "k_resnet.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE]

@@ -138,6 +138,11 @@ int check_ws(void* ws, size_t have, size_t need) {
 // Arrays the kernels read or write with 64-bit accesses (complex values, pairs of
 // floats, doubles, int64) must be 8-byte aligned; a misaligned pointer is rejected here
 // instead of faulting on the device.
+#define GWX_ALIGN16(p)                                                                     \
+  do {                                                                                     \
+    if (((uintptr_t)(const void*)(p)) & 15u) return fail(GWX_EINVAL, "%s is not 16-byte aligned", #p); \
+  } while (0)
+
 #define GWX_ALIGN8(p)                                                                     \
   do {                                                                                    \
     if (((uintptr_t)(const void*)(p)) & 7u) return fail(GWX_EINVAL, "%s is not 8-byte aligned", #p); \
@@ -776,6 +781,101 @@ int gwx_retime(const double* theta_in, double* theta_out, int64_t B, double tc_l
   return launched(launch_retime(theta_in, theta_out, B, tc_lo, tc_hi, seed, counter, as_stream(stream)), "retime");
 }
 
+// ---- ResNet-1D pieces
+namespace {
+int check_btc(int64_t B, int T, int C) {
+  if (B < 1 || T < 1 || C < 1 || B * (int64_t)T * C > ((int64_t)1 << 34)) return fail(GWX_ESHAPE, "bad B, T or C");
+  return GWX_OK;
+}
+}  // namespace
+
+int gwx_im2col(const void* x, int64_t B, int T, int C, int k, int s, int p, int K, void* cols, void* stream) {
+  GWX_TRY(check_btc(B, T, C));
+  if (C % 8 || K % 8 || K < k * C || k < 1 || s < 1 || p < 0 || T + 2 * p < k)
+    return fail(GWX_ESHAPE, "im2col C=%d K=%d k=%d s=%d p=%d (C and K multiples of 8, K >= k C)", C, K, k, s, p);
+  if (!x || !cols) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN16(x);
+  GWX_ALIGN16(cols);
+  GWX_TRY(ensure_init());
+  return launched(launch_im2col(x, B, T, C, k, s, p, K, cols, as_stream(stream)), "im2col");
+}
+
+int gwx_im2col_cf(const float* y, int64_t B, int D, int N, int k, int s, int p, int K, void* cols, void* stream) {
+  GWX_TRY(check_btc(B, N, D));
+  if (K < k * D || k < 1 || s < 1 || p < 0 || N + 2 * p < k) return fail(GWX_ESHAPE, "im2col_cf shapes");
+  if (!y || !cols) return fail(GWX_EINVAL, "NULL array");
+  GWX_TRY(ensure_init());
+  return launched(launch_im2col_cf(y, B, D, N, k, s, p, K, cols, as_stream(stream)), "im2col_cf");
+}
+
+int gwx_col2im(const float* dcols, int64_t B, int T, int C, int k, int s, int p, int K, const float* addend, float* dx,
+               void* stream) {
+  GWX_TRY(check_btc(B, T, C));
+  if (K < k * C || k < 1 || s < 1 || p < 0 || T + 2 * p < k) return fail(GWX_ESHAPE, "col2im shapes");
+  if (!dcols || !dx) return fail(GWX_EINVAL, "NULL array");
+  GWX_TRY(ensure_init());
+  return launched(launch_col2im(dcols, B, T, C, k, s, p, K, addend, dx, as_stream(stream)), "col2im");
+}
+
+int gwx_group_norm(const float* z, int64_t B, int T, int C, int G, const float* gamma, const float* beta,
+                   const float* residual32, const void* residual16, int relu, void* out16, float* out32,
+                   float* mean_rstd, void* stream) {
+  GWX_TRY(check_btc(B, T, C));
+  if (G < 1 || C % G) return fail(GWX_ESHAPE, "C=%d not a multiple of G=%d", C, G);
+  if (!z || !gamma || !beta || !mean_rstd || (!out16 && !out32)) return fail(GWX_EINVAL, "NULL array");
+  GWX_TRY(ensure_init());
+  return launched(launch_group_norm(z, B, T, C, G, gamma, beta, residual32, residual16, relu ? 1 : 0, out16, out32,
+                                    mean_rstd, as_stream(stream)),
+                  "group_norm");
+}
+
+int gwx_group_norm_backward(const float* dy, const float* z, int64_t B, int T, int C, int G, const float* mean_rstd,
+                            const float* gamma, float* scratch, float* dz, float* dgamma, float* dbeta, void* stream) {
+  GWX_TRY(check_btc(B, T, C));
+  if (G < 1 || C % G) return fail(GWX_ESHAPE, "C=%d not a multiple of G=%d", C, G);
+  if (!dy || !z || !mean_rstd || !gamma || !scratch || !dz || !dgamma || !dbeta) return fail(GWX_EINVAL, "NULL array");
+  GWX_TRY(ensure_init());
+  return launched(launch_group_norm_backward(dy, z, B, T, C, G, mean_rstd, gamma, scratch, dz, dgamma, dbeta,
+                                             as_stream(stream)),
+                  "group_norm_backward");
+}
+
+int gwx_relu_mask(const float* dy, const void* out, int64_t n, float* d, void* stream) {
+  if (n < 0) return fail(GWX_ESHAPE, "n");
+  if (n == 0) return GWX_OK;
+  if (!dy || !out || !d) return fail(GWX_EINVAL, "NULL array");
+  GWX_TRY(ensure_init());
+  return launched(launch_relu_mask(dy, out, n, d, as_stream(stream)), "relu_mask");
+}
+
+int gwx_maxpool(const void* x, int64_t B, int T, int C, void* y, uint8_t* arg, void* stream) {
+  GWX_TRY(check_btc(B, T, C));
+  if (!x || !y || !arg) return fail(GWX_EINVAL, "NULL array");
+  GWX_TRY(ensure_init());
+  return launched(launch_maxpool(x, B, T, C, y, arg, as_stream(stream)), "maxpool");
+}
+
+int gwx_maxpool_backward(const float* dy, const uint8_t* arg, int64_t B, int T, int C, float* dx, void* stream) {
+  GWX_TRY(check_btc(B, T, C));
+  if (!dy || !arg || !dx) return fail(GWX_EINVAL, "NULL array");
+  GWX_TRY(ensure_init());
+  return launched(launch_maxpool_back(dy, arg, B, T, C, dx, as_stream(stream)), "maxpool_backward");
+}
+
+int gwx_mean_time(const void* x, int64_t B, int T, int C, void* m, void* stream) {
+  GWX_TRY(check_btc(B, T, C));
+  if (!x || !m) return fail(GWX_EINVAL, "NULL array");
+  GWX_TRY(ensure_init());
+  return launched(launch_mean_time(x, B, T, C, m, as_stream(stream)), "mean_time");
+}
+
+int gwx_mean_time_backward(const float* dm, int64_t B, int T, int C, float* dx, void* stream) {
+  GWX_TRY(check_btc(B, T, C));
+  if (!dm || !dx) return fail(GWX_EINVAL, "NULL array");
+  GWX_TRY(ensure_init());
+  return launched(launch_mean_time_back(dm, B, T, C, dx, as_stream(stream)), "mean_time_backward");
+}
+
 size_t gwx_skymap_workspace(void) { return kAlign; }
 
 int gwx_skymap(const double* theta, const double* weights, int64_t S, int nside, double* map, void* workspace,
@@ -859,10 +959,6 @@ int gwx_irfft(const float* X, int64_t R, int64_t N, float* x, void* stream) {
 // ---------------------------------------------------------------- conditional coupling flow
 namespace {
 
-#define GWX_ALIGN16(p)                                                                     \
-  do {                                                                                     \
-    if (((uintptr_t)(const void*)(p)) & 15u) return fail(GWX_EINVAL, "%s is not 16-byte aligned", #p); \
-  } while (0)
 
 int check_flow_shape(const gwx_flow_shape* sh) {
   if (!sh) return fail(GWX_EINVAL, "flow shape is NULL");

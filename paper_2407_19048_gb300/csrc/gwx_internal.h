@@ -180,6 +180,26 @@ cudaError_t launch_vicreg(const float* x, const float* xp, int B, int d, double 
 cudaError_t launch_retime(const double* in, double* out, int64_t B, double tc_lo, double tc_hi, uint64_t seed,
                           uint32_t counter, cudaStream_t s);
 
+// ResNet-1D pieces (k_resnet.cu).
+cudaError_t launch_im2col(const void* x, int64_t B, int T, int C, int k, int s, int p, int K, void* cols,
+                          cudaStream_t st);
+cudaError_t launch_im2col_cf(const float* y, int64_t B, int D, int N, int k, int s, int p, int K, void* cols,
+                             cudaStream_t st);
+cudaError_t launch_col2im(const float* dcols, int64_t B, int T, int C, int k, int s, int p, int K, const float* addend,
+                          float* dx, cudaStream_t st);
+cudaError_t launch_group_norm(const float* z, int64_t B, int T, int C, int G, const float* gamma, const float* beta,
+                              const float* res32, const void* res16, int relu, void* out16, float* out32, float* ms,
+                              cudaStream_t st);
+cudaError_t launch_group_norm_backward(const float* dy, const float* z, int64_t B, int T, int C, int G,
+                                       const float* ms, const float* gamma, float* mm, float* dz, float* dgamma,
+                                       float* dbeta, cudaStream_t st);
+cudaError_t launch_relu_mask(const float* dy, const void* out, int64_t n, float* d, cudaStream_t st);
+cudaError_t launch_maxpool(const void* x, int64_t B, int T, int C, void* y, uint8_t* arg, cudaStream_t st);
+cudaError_t launch_maxpool_back(const float* dy, const uint8_t* arg, int64_t B, int T, int C, float* dx,
+                                cudaStream_t st);
+cudaError_t launch_mean_time(const void* x, int64_t B, int T, int C, void* m, cudaStream_t st);
+cudaError_t launch_mean_time_back(const float* dm, int64_t B, int T, int C, float* dx, cudaStream_t st);
+
 // Record msg as the calling thread's gwx_last_error() message; returns status.
 int set_last_error(int status, const char* msg);
 
