@@ -517,7 +517,12 @@ int gwx_flow_proposal(const float* x, const float* z, const float* sum_s, int64_
  * into grads (flat, same layout as params; the whole array is rewritten), then (step >= 1)
  * gwx_adamw over the flat array with step counter `step` (gwx_adamw_clip when clip > 0:
  * gradients scaled to a Euclidean norm of at most clip); step 0 computes the loss and
- * gradients only.  step_counter (optional, a device int64): the update takes its step
+ * gradients only.  ctx_in (optional, bfloat16 [B][C]): a context from another data-summary
+ * network (the ResNet-1D of Sec. 4) replaces the built-in summary of the features, whose
+ * tensors then get zero gradients, and d_ctx_out (FP32 [B][C]) receives dL/dcontext for
+ * that network's backward pass; y may then be NULL.  The same ctx_in argument of
+ * gwx_flow_log_prob (one row per parameter vector) and gwx_sample_posterior (one row per
+ * event) skips the built-in summary there.  step_counter (optional, a device int64): the update takes its step
  * number from *step_counter + 1 on the device and stores it back, so that a captured
  * CUDA graph of the call replays with the right AdamW bias corrections (step then only
  * has to be >= 1).  *loss_mean (device double) = batch mean of -ln q_x.  B a multiple of 8
@@ -527,14 +532,15 @@ int gwx_flow_train_step(const gwx_flow_shape* shape, float* params, void* params
                         float* v, int64_t step, int64_t* step_counter, double lr, double beta1, double beta2, double eps,
                         double weight_decay, double clip, const double* mean8, const double* scale8, const float* y,
                         const double* theta, int64_t B, int D, int64_t N, double fs, double f_lo,
-                        double* loss_mean, void* workspace, size_t workspace_bytes, void* stream);
+                        const void* ctx_in, float* d_ctx_out, double* loss_mean, void* workspace,
+                        size_t workspace_bytes, void* stream);
 
 /* Density ln q_r(r(theta_b) | y_b) (FP64 [B]) of B parameter vectors, each with its own
  * whitened window y [B][D][N].  Workspace gwx_flow_log_prob_workspace(shape, B, D, N). */
 size_t gwx_flow_log_prob_workspace(const gwx_flow_shape* shape, int64_t B, int D, int64_t N);
 int gwx_flow_log_prob(const gwx_flow_shape* shape, const float* params, const void* params_bf16,
                       const double* mean8, const double* scale8, const float* y, const double* theta, int64_t B,
-                      int D, int64_t N, double fs, double f_lo, double* log_q, void* workspace,
+                      int D, int64_t N, double fs, double f_lo, const void* ctx_in, double* log_q, void* workspace,
                       size_t workspace_bytes, void* stream);
 
 /* Posterior samples (Sec. 5: draws from q(theta | d) for new data; Sec. 6 judges them):
@@ -546,9 +552,10 @@ int gwx_flow_log_prob(const gwx_flow_shape* shape, const float* params, const vo
 size_t gwx_sample_posterior_workspace(const gwx_flow_shape* shape, int64_t E, int D, int64_t N, int64_t S);
 int gwx_sample_posterior(const gwx_flow_shape* shape, const float* params, const void* params_bf16,
                          const double* mean8, const double* scale8, const gwx_prior* prior, const float* y,
-                         int64_t E, int D, int64_t N, double fs, double f_lo, const double* truth,
-                         const int64_t* event_offsets, int64_t S, uint64_t seed, uint32_t counter, double* theta,
-                         double* log_q, double* log_ratio, void* workspace, size_t workspace_bytes, void* stream);
+                         int64_t E, int D, int64_t N, double fs, double f_lo, const void* ctx_in,
+                         const double* truth, const int64_t* event_offsets, int64_t S, uint64_t seed,
+                         uint32_t counter, double* theta, double* log_q, double* log_ratio, void* workspace,
+                         size_t workspace_bytes, void* stream);
 
 /* ---- self-supervised pre-training of the data summary (Sec. 4.1) ------------------
  * Two views of each simulated source, identical but for the merger time, are summarised

@@ -681,9 +681,11 @@ def flow_proposal(x, z, sum_s, mean8, scale8, prior, truth, event_offsets, seed,
 
 def flow_train_step(shape, params, params_bf16, grads, m, v, step, lr, mean8, scale8, y, theta, fs, f_lo,
                     beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, clip=0.0, loss_mean=None, workspace=None,
-                    step_counter=None):
+                    step_counter=None, ctx=None, d_ctx=None):
     """One training step (step 0: loss and gradients only).  Returns loss_mean (device
-    float64 [1]).  `workspace` may be a preallocated (tensor, bytes) pair."""
+    float64 [1]).  `workspace` may be a preallocated (tensor, bytes) pair.  With ctx
+    (bfloat16 [B][C]) the context comes from the caller's summary network and d_ctx
+    (float32 [B][C]) receives its gradient."""
     torch = _torch()
     sh = _shape(shape)
     _dev(y, torch.float32, "y")
@@ -694,13 +696,15 @@ def flow_train_step(shape, params, params_bf16, grads, m, v, step, lr, mean8, sc
     ws, nb = workspace if workspace is not None else _workspace(
         lib.gwx_flow_train_workspace(ctypes.byref(sh), B, D, N), y.device)
     _check(lib.gwx_flow_train_step(ctypes.byref(sh), _ptr(params), _ptr(params_bf16), _ptr(grads), _ptr(m), _ptr(v),
-                                   step, _ptr(step_counter) if step_counter is not None else None, lr, beta1, beta2, eps, weight_decay, clip, _host8(mean8), _host8(scale8),
-                                   _ptr(y),
-                                   _ptr(theta), B, D, N, fs, f_lo, _ptr(loss_mean), _ptr(ws), nb, _stream()))
+                                   step, _ptr(step_counter) if step_counter is not None else None, lr, beta1, beta2,
+                                   eps, weight_decay, clip, _host8(mean8), _host8(scale8), _ptr(y), _ptr(theta), B, D,
+                                   N, fs, f_lo, _ptr(ctx) if ctx is not None else None,
+                                   _ptr(d_ctx) if d_ctx is not None else None, _ptr(loss_mean), _ptr(ws), nb,
+                                   _stream()))
     return loss_mean
 
 
-def flow_log_prob(shape, params, params_bf16, mean8, scale8, y, theta, fs, f_lo):
+def flow_log_prob(shape, params, params_bf16, mean8, scale8, y, theta, fs, f_lo, ctx=None):
     """float64 [B] ln q_r(r(theta_b) | y_b)."""
     torch = _torch()
     sh = _shape(shape)
@@ -711,12 +715,13 @@ def flow_log_prob(shape, params, params_bf16, mean8, scale8, y, theta, fs, f_lo)
     out = torch.empty(B, dtype=torch.float64, device=y.device)
     ws, nb = _workspace(lib.gwx_flow_log_prob_workspace(ctypes.byref(sh), B, D, N), y.device)
     _check(lib.gwx_flow_log_prob(ctypes.byref(sh), _ptr(params), _ptr(params_bf16), _host8(mean8), _host8(scale8),
-                                 _ptr(y), _ptr(theta), B, D, N, fs, f_lo, _ptr(out), _ptr(ws), nb, _stream()))
+                                 _ptr(y), _ptr(theta), B, D, N, fs, f_lo, _ptr(ctx) if ctx is not None else None,
+                                 _ptr(out), _ptr(ws), nb, _stream()))
     return out
 
 
 def sample_posterior(shape, params, params_bf16, mean8, scale8, prior, y, fs, f_lo, truth, event_offsets, seed,
-                     counter, out=None, workspace=None):
+                     counter, out=None, workspace=None, ctx=None):
     """Posterior draws for events y [E][D][N]: (theta [11][S], log_q [S], log_ratio [S])."""
     torch = _torch()
     sh = _shape(shape)
@@ -735,7 +740,8 @@ def sample_posterior(shape, params, params_bf16, mean8, scale8, prior, y, fs, f_
         lib.gwx_sample_posterior_workspace(ctypes.byref(sh), E, D, N, S), dev)
     p = _prior(prior)
     _check(lib.gwx_sample_posterior(ctypes.byref(sh), _ptr(params), _ptr(params_bf16), _host8(mean8), _host8(scale8),
-                                    ctypes.byref(p), _ptr(y), E, D, N, fs, f_lo, _ptr(truth), _ptr(event_offsets), S,
+                                    ctypes.byref(p), _ptr(y), E, D, N, fs, f_lo,
+                                    _ptr(ctx) if ctx is not None else None, _ptr(truth), _ptr(event_offsets), S,
                                     seed, counter, _ptr(theta), _ptr(log_q), _ptr(lr), _ptr(ws), nb, _stream()))
     return theta, log_q, lr
 

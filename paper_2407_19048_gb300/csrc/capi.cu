@@ -1148,7 +1148,8 @@ int gwx_flow_train_step(const gwx_flow_shape* shape, float* params, void* params
                         float* v, int64_t step, int64_t* step_counter, double lr, double beta1, double beta2, double eps,
                         double weight_decay, double clip, const double* mean8, const double* scale8, const float* y,
                         const double* theta, int64_t B, int D, int64_t N, double fs, double f_lo,
-                        double* loss_mean, void* workspace, size_t workspace_bytes, void* stream) {
+                        const void* ctx_in, float* d_ctx_out, double* loss_mean, void* workspace,
+                        size_t workspace_bytes, void* stream) {
   GWX_TRY(check_flow_shape(shape));
   GWX_TRY(check_std8(mean8, scale8));
   int k_lo = 0;
@@ -1160,9 +1161,11 @@ int gwx_flow_train_step(const gwx_flow_shape* shape, float* params, void* params
   if (step >= 1 && (!(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0) || !(lr >= 0.0)))
     return fail(GWX_EINVAL, "AdamW hyper-parameters");
   GWX_TRY(check_flow_params(shape, params, params_bf16));
-  if (!grads || !y || !theta || !loss_mean || (step >= 1 && (!m || !v))) return fail(GWX_EINVAL, "NULL array");
+  if (!grads || (!y && !ctx_in) || !theta || !loss_mean || (step >= 1 && (!m || !v)) || (ctx_in && !d_ctx_out))
+    return fail(GWX_EINVAL, "NULL array");
   GWX_ALIGN16(grads);
-  GWX_ALIGN8(y);
+  if (y) GWX_ALIGN8(y);
+  if (ctx_in) GWX_ALIGN16(ctx_in);
   GWX_ALIGN8(theta);
   GWX_ALIGN8(loss_mean);
   GWX_TRY(check_ws(workspace, workspace_bytes, gwx_flow_train_workspace(shape, B, D, N)));
@@ -1170,7 +1173,8 @@ int gwx_flow_train_step(const gwx_flow_shape* shape, float* params, void* params
   if (!(clip >= 0.0) || !isfinite(clip)) return fail(GWX_EINVAL, "clip=%g", clip);
   if (step_counter) GWX_ALIGN8(step_counter);
   return launched(flow_train_step(*shape, params, params_bf16, grads, m, v, step, step_counter, lr, beta1, beta2, eps,
-                                  weight_decay, clip, mean8, scale8, y, theta, B, D, N, k_lo, loss_mean, workspace, as_stream(stream)),
+                                  weight_decay, clip, mean8, scale8, y, theta, B, D, N, k_lo, ctx_in, d_ctx_out,
+                                  loss_mean, workspace, as_stream(stream)),
                   "flow_train_step");
 }
 
@@ -1181,7 +1185,7 @@ size_t gwx_flow_log_prob_workspace(const gwx_flow_shape* shape, int64_t B, int D
 
 int gwx_flow_log_prob(const gwx_flow_shape* shape, const float* params, const void* params_bf16,
                       const double* mean8, const double* scale8, const float* y, const double* theta, int64_t B,
-                      int D, int64_t N, double fs, double f_lo, double* log_q, void* workspace,
+                      int D, int64_t N, double fs, double f_lo, const void* ctx_in, double* log_q, void* workspace,
                       size_t workspace_bytes, void* stream) {
   GWX_TRY(check_flow_shape(shape));
   GWX_TRY(check_std8(mean8, scale8));
@@ -1190,13 +1194,15 @@ int gwx_flow_log_prob(const gwx_flow_shape* shape, const float* params, const vo
   if (B < 0 || B > ((int64_t)1 << 23)) return fail(GWX_ESHAPE, "B=%lld", (long long)B);
   if (B == 0) return GWX_OK;
   GWX_TRY(check_flow_params(shape, params, params_bf16));
-  if (!y || !theta || !log_q) return fail(GWX_EINVAL, "NULL array");
-  GWX_ALIGN8(y);
+  if ((!y && !ctx_in) || !theta || !log_q) return fail(GWX_EINVAL, "NULL array");
+  if (y) GWX_ALIGN8(y);
+  if (ctx_in) GWX_ALIGN16(ctx_in);
   GWX_ALIGN8(theta);
   GWX_ALIGN8(log_q);
   GWX_TRY(check_ws(workspace, workspace_bytes, gwx_flow_log_prob_workspace(shape, B, D, N)));
   GWX_TRY(ensure_init());
-  return launched(flow_log_prob(*shape, params, params_bf16, mean8, scale8, y, theta, B, D, N, k_lo, log_q, workspace,
+  return launched(flow_log_prob(*shape, params, params_bf16, mean8, scale8, y, theta, B, D, N, k_lo, ctx_in, log_q,
+                                workspace,
                                 as_stream(stream)),
                   "flow_log_prob");
 }
@@ -1208,9 +1214,10 @@ size_t gwx_sample_posterior_workspace(const gwx_flow_shape* shape, int64_t E, in
 
 int gwx_sample_posterior(const gwx_flow_shape* shape, const float* params, const void* params_bf16,
                          const double* mean8, const double* scale8, const gwx_prior* prior, const float* y,
-                         int64_t E, int D, int64_t N, double fs, double f_lo, const double* truth,
-                         const int64_t* event_offsets, int64_t S, uint64_t seed, uint32_t counter, double* theta,
-                         double* log_q, double* log_ratio, void* workspace, size_t workspace_bytes, void* stream) {
+                         int64_t E, int D, int64_t N, double fs, double f_lo, const void* ctx_in,
+                         const double* truth, const int64_t* event_offsets, int64_t S, uint64_t seed,
+                         uint32_t counter, double* theta, double* log_q, double* log_ratio, void* workspace,
+                         size_t workspace_bytes, void* stream) {
   GWX_TRY(check_flow_shape(shape));
   GWX_TRY(check_std8(mean8, scale8));
   GWX_TRY(check_prior_box(prior));
@@ -1220,8 +1227,10 @@ int gwx_sample_posterior(const gwx_flow_shape* shape, const float* params, const
     return fail(GWX_ESHAPE, "bad E or S");
   if (S == 0) return GWX_OK;
   GWX_TRY(check_flow_params(shape, params, params_bf16));
-  if (!y || !truth || !event_offsets || !theta || !log_q || !log_ratio) return fail(GWX_EINVAL, "NULL array");
-  GWX_ALIGN8(y);
+  if ((!y && !ctx_in) || !truth || !event_offsets || !theta || !log_q || !log_ratio)
+    return fail(GWX_EINVAL, "NULL array");
+  if (y) GWX_ALIGN8(y);
+  if (ctx_in) GWX_ALIGN16(ctx_in);
   GWX_ALIGN8(truth);
   GWX_ALIGN8(event_offsets);
   GWX_ALIGN8(theta);
@@ -1229,7 +1238,7 @@ int gwx_sample_posterior(const gwx_flow_shape* shape, const float* params, const
   GWX_ALIGN8(log_ratio);
   GWX_TRY(check_ws(workspace, workspace_bytes, gwx_sample_posterior_workspace(shape, E, D, N, S)));
   GWX_TRY(ensure_init());
-  return launched(flow_sample(*shape, params, params_bf16, mean8, scale8, *prior, y, E, D, N, k_lo, truth,
+  return launched(flow_sample(*shape, params, params_bf16, mean8, scale8, *prior, y, E, D, N, k_lo, ctx_in, truth,
                               event_offsets, S, seed, counter, theta, log_q, log_ratio, workspace, as_stream(stream)),
                   "sample_posterior");
 }

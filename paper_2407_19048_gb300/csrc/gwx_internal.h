@@ -158,16 +158,18 @@ size_t flow_train_ws(const gwx_flow_shape& sh, int64_t B, int D, int64_t N);
 cudaError_t flow_train_step(const gwx_flow_shape& sh, float* params, void* params_bf16, float* grads, float* m,
                             float* v, int64_t step, int64_t* step_counter, double lr, double b1, double b2, double eps, double wd, double clip,
                             const double* mean8, const double* scale8, const float* y, const double* theta, int64_t B,
-                            int D, int64_t N, int k_lo, double* loss_mean, void* ws, cudaStream_t s);
+                            int D, int64_t N, int k_lo, const void* ctx_in, float* d_ctx_out, double* loss_mean,
+                            void* ws, cudaStream_t s);
 size_t flow_log_prob_ws(const gwx_flow_shape& sh, int64_t B, int D, int64_t N);
 cudaError_t flow_log_prob(const gwx_flow_shape& sh, const float* params, const void* params_bf16, const double* mean8,
                           const double* scale8, const float* y, const double* theta, int64_t B, int D, int64_t N,
-                          int k_lo, double* log_q, void* ws, cudaStream_t s);
+                          int k_lo, const void* ctx_in, double* log_q, void* ws, cudaStream_t s);
 size_t flow_sample_ws(const gwx_flow_shape& sh, int64_t E, int D, int64_t N, int64_t S);
 cudaError_t flow_sample(const gwx_flow_shape& sh, const float* params, const void* params_bf16, const double* mean8,
                         const double* scale8, const gwx_prior& pr, const float* y, int64_t E, int D, int64_t N,
-                        int k_lo, const double* truth, const int64_t* off, int64_t S, uint64_t seed, uint32_t counter,
-                        double* theta, double* log_q, double* log_ratio, void* ws, cudaStream_t s);
+                        int k_lo, const void* ctx_in, const double* truth, const int64_t* off, int64_t S,
+                        uint64_t seed, uint32_t counter, double* theta, double* log_q, double* log_ratio, void* ws,
+                        cudaStream_t s);
 
 // HEALPix sky map of weighted samples (k_skymap.cu); ws holds one double.
 cudaError_t launch_skymap(const double* theta, const double* weights, int64_t S, int nside, double* map, void* ws,

@@ -535,20 +535,24 @@ size_t flow_train_ws(const gwx_flow_shape& sh, int64_t B, int D, int64_t N) {
 cudaError_t flow_train_step(const gwx_flow_shape& sh, float* params, void* params_bf16, float* grads, float* m,
                             float* v, int64_t step, int64_t* step_counter, double lr, double b1, double b2, double eps, double wd, double clip,
                             const double* mean8, const double* scale8, const float* y, const double* theta, int64_t B,
-                            int D, int64_t N, int k_lo, double* loss_mean, void* ws, cudaStream_t s) {
+                            int D, int64_t N, int k_lo, const void* ctx_in, float* d_ctx_out, double* loss_mean,
+                            void* ws, cudaStream_t s) {
   const FlowDims d = dims_of(sh);
   const Params P = make_params(sh, params, params_bf16);
   const int64_t n_params = flow_layout(sh, nullptr);
   TrainWs w = carve_train(d, B, D, N, ws);
   const int64_t rows8 = B * 8;
-  FL_TRY(embed_forward(d, P, y, B, D, N, k_lo, w.fws, w.feat, w.h1, w.h2, w.ctx, s));
+  // the context: the built-in summary of the features, or the caller's (another summary
+  // network, whose backward takes the context gradient from d_ctx_out)
+  const __nv_bfloat16* ctx = ctx_in ? reinterpret_cast<const __nv_bfloat16*>(ctx_in) : w.ctx;
+  if (!ctx_in) FL_TRY(embed_forward(d, P, y, B, D, N, k_lo, w.fws, w.feat, w.h1, w.h2, w.ctx, s));
   FL_TRY(launch_flow_targets(theta, B, mean8, scale8, w.xs + d.K * rows8, s));
   for (int l = (int)d.K - 1; l >= 0; --l) {
     __nv_bfloat16* X = w.X + l * B * (8 + d.C);
     __nv_bfloat16* g1 = w.g1 + l * B * d.H;
     __nv_bfloat16* g2 = w.g2 + l * B * d.H;
     float* o = w.o + l * rows8;
-    FL_TRY(launch_flow_input(l, w.xs + (l + 1) * rows8, w.ctx, (int)d.C, nullptr, B, 0, B, X, s));
+    FL_TRY(launch_flow_input(l, w.xs + (l + 1) * rows8, ctx, (int)d.C, nullptr, B, 0, B, X, s));
     FL_TRY(conditioner_forward(d, P, l, B, X, g1, g2, o, s));
     FL_TRY(launch_flow_coupling(l, -1, w.xs + (l + 1) * rows8, o, B, w.xs + l * rows8, w.sum_s,
                                 l == (int)d.K - 1, s));
@@ -572,12 +576,16 @@ cudaError_t flow_train_step(const gwx_flow_shape& sh, float* params, void* param
     FL_TRY(launch_flow_input_backward(l, w.dA, (int)d.C, B, Gu, w.dctx, l == 0, s));
     std::swap(G, Gu);
   }
-  FL_TRY(launch_dense_backward(w.h2, P.W(4), P.b(5), w.dctx, B, d.C, d.He, GWX_ACT_NONE, w.dA, grads + P.off[4],
-                               grads + P.off[5], w.dws, 0, s));
-  FL_TRY(launch_dense_backward(w.h1, P.W(2), P.b(3), w.dA, B, d.He, d.He, GWX_ACT_RELU, w.dB, grads + P.off[2],
-                               grads + P.off[3], w.dws, 0, s));
-  FL_TRY(launch_dense_backward(w.feat, P.W(0), P.b(1), w.dB, B, d.He, d.F, GWX_ACT_RELU, nullptr, grads + P.off[0],
-                               grads + P.off[1], w.dws, 0, s));
+  if (ctx_in) {
+    FL_TRY(cudaMemcpyAsync(d_ctx_out, w.dctx, (size_t)B * d.C * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  } else {
+    FL_TRY(launch_dense_backward(w.h2, P.W(4), P.b(5), w.dctx, B, d.C, d.He, GWX_ACT_NONE, w.dA, grads + P.off[4],
+                                 grads + P.off[5], w.dws, 0, s));
+    FL_TRY(launch_dense_backward(w.h1, P.W(2), P.b(3), w.dA, B, d.He, d.He, GWX_ACT_RELU, w.dB, grads + P.off[2],
+                                 grads + P.off[3], w.dws, 0, s));
+    FL_TRY(launch_dense_backward(w.feat, P.W(0), P.b(1), w.dB, B, d.He, d.F, GWX_ACT_RELU, nullptr,
+                                 grads + P.off[0], grads + P.off[1], w.dws, 0, s));
+  }
   if (step >= 1) {
     if (step_counter)
       FL_TRY(launch_adamw_clip(params, grads, m, v, n_params, lr, b1, b2, eps, wd, step, clip, params_bf16, w.clip, s,
@@ -616,16 +624,17 @@ size_t flow_log_prob_ws(const gwx_flow_shape& sh, int64_t B, int D, int64_t N) {
 
 cudaError_t flow_log_prob(const gwx_flow_shape& sh, const float* params, const void* params_bf16, const double* mean8,
                           const double* scale8, const float* y, const double* theta, int64_t B, int D, int64_t N,
-                          int k_lo, double* log_q, void* ws, cudaStream_t s) {
+                          int k_lo, const void* ctx_in, double* log_q, void* ws, cudaStream_t s) {
   const FlowDims d = dims_of(sh);
   const Params P = make_params(sh, params, params_bf16);
   Carve c(ws);
   EmbedWs e = carve_embed(d, B, D, N, c);
   ChainWs w = carve_chain(d, B, c);
-  FL_TRY(embed_forward(d, P, y, B, D, N, k_lo, e.fws, e.feat, e.h1, e.h2, e.ctx, s));
+  const __nv_bfloat16* ctx = ctx_in ? reinterpret_cast<const __nv_bfloat16*>(ctx_in) : e.ctx;
+  if (!ctx_in) FL_TRY(embed_forward(d, P, y, B, D, N, k_lo, e.fws, e.feat, e.h1, e.h2, e.ctx, s));
   FL_TRY(launch_flow_targets(theta, B, mean8, scale8, w.v, s));
   for (int l = (int)d.K - 1; l >= 0; --l) {
-    FL_TRY(launch_flow_input(l, w.v, e.ctx, (int)d.C, nullptr, B, 0, B, w.X, s));
+    FL_TRY(launch_flow_input(l, w.v, ctx, (int)d.C, nullptr, B, 0, B, w.X, s));
     FL_TRY(conditioner_forward(d, P, l, B, w.X, w.g1, w.g2, w.o, s));
     FL_TRY(launch_flow_coupling(l, -1, w.v, w.o, B, w.v, w.sum_s, l == (int)d.K - 1, s));
   }
@@ -644,20 +653,22 @@ size_t flow_sample_ws(const gwx_flow_shape& sh, int64_t E, int D, int64_t N, int
 
 cudaError_t flow_sample(const gwx_flow_shape& sh, const float* params, const void* params_bf16, const double* mean8,
                         const double* scale8, const gwx_prior& pr, const float* y, int64_t E, int D, int64_t N,
-                        int k_lo, const double* truth, const int64_t* off, int64_t S, uint64_t seed, uint32_t counter,
-                        double* theta, double* log_q, double* log_ratio, void* ws, cudaStream_t s) {
+                        int k_lo, const void* ctx_in, const double* truth, const int64_t* off, int64_t S,
+                        uint64_t seed, uint32_t counter, double* theta, double* log_q, double* log_ratio, void* ws,
+                        cudaStream_t s) {
   const FlowDims d = dims_of(sh);
   const Params P = make_params(sh, params, params_bf16);
   Carve c(ws);
   EmbedWs e = carve_embed(d, E, D, N, c);
   ChainWs w = carve_chain(d, std::min(S, kSampleChunk), c);
-  FL_TRY(embed_forward(d, P, y, E, D, N, k_lo, e.fws, e.feat, e.h1, e.h2, e.ctx, s));
+  const __nv_bfloat16* ctx = ctx_in ? reinterpret_cast<const __nv_bfloat16*>(ctx_in) : e.ctx;
+  if (!ctx_in) FL_TRY(embed_forward(d, P, y, E, D, N, k_lo, e.fws, e.feat, e.h1, e.h2, e.ctx, s));
   const bool fused = flow_fused_supported((int)d.C, (int)d.H, (int)d.K);
   for (int64_t row0 = 0; row0 < S; row0 += kSampleChunk) {
     const int64_t n = std::min(kSampleChunk, S - row0);
     FL_TRY(launch_flow_base(seed, counter, row0, n, w.z, s));
     if (fused) {
-      FL_TRY(launch_flow_sample_fused(params_bf16, params, P.off.data(), (int)d.C, (int)d.H, (int)d.K, w.z, e.ctx,
+      FL_TRY(launch_flow_sample_fused(params_bf16, params, P.off.data(), (int)d.C, (int)d.H, (int)d.K, w.z, ctx,
                                       off, E, row0, n, w.v, w.sum_s, s));
       FL_TRY(launch_flow_proposal(w.v, w.z, w.sum_s, n, row0, S, mean8, scale8, pr, truth, E, off, seed, counter,
                                   theta, log_q, log_ratio, s));
@@ -665,7 +676,7 @@ cudaError_t flow_sample(const gwx_flow_shape& sh, const float* params, const voi
     }
     const float* vin = w.z;
     for (int l = 0; l < (int)d.K; ++l) {
-      FL_TRY(launch_flow_input(l, vin, e.ctx, (int)d.C, off, E, row0, n, w.X, s));
+      FL_TRY(launch_flow_input(l, vin, ctx, (int)d.C, off, E, row0, n, w.X, s));
       FL_TRY(conditioner_forward(d, P, l, n, w.X, w.g1, w.g2, w.o, s));
       FL_TRY(launch_flow_coupling(l, +1, vin, w.o, n, w.v, w.sum_s, l == 0, s));
       vin = w.v;

@@ -17,7 +17,8 @@ from . import _lib
 
 class FlowPosterior:
     def __init__(self, workload, layers=16, hidden=256, context=64, embed_hidden=512, group=4, seed=0,
-                 device=None, lr=1e-3, weight_decay=2e-3, cross=True, lag=True, clip=1.0):
+                 device=None, lr=1e-3, weight_decay=2e-3, cross=True, lag=True, clip=1.0, embedding="spectral",
+                 resnet_stages=None):
         import torch
         import paper_2407_19048_gb300 as gwx
         self.gwx = gwx
@@ -45,6 +46,16 @@ class FlowPosterior:
         self._loss = torch.zeros(1, dtype=torch.float64, device=self.dev)
         self.init_random(seed)
         # standardisation of the flow's coordinates from prior draws (computed by the library)
+        # the data summary: the built-in dense network on spectral features, or the
+        # ResNet-1D of Sec. 4 on the whitened strain (trained here, its context fed in)
+        self.embedding = embedding
+        self.resnet = None
+        if embedding == "resnet":
+            from .resnet import ResNet1D, STAGES
+            self.resnet = ResNet1D(self.D, context, stages=resnet_stages or STAGES, device=self.dev, seed=seed + 1)
+            self.rmom = {name: (torch.zeros_like(p), torch.zeros_like(p)) for name, p, _ in self.resnet.tensors()}
+        elif embedding != "spectral":
+            raise ValueError("embedding must be 'spectral' or 'resnet'")
         th, _ = gwx.sample_prior(wl["prior"], 12345, 0, 100000, wl["L"], self.N)
         r = gwx.flow_targets(th, [0.0] * 8, [1.0] * 8).double()
         self.mean = [float(x) for x in r.mean(dim=0).cpu()]
@@ -107,12 +118,28 @@ class FlowPosterior:
         nb = _lib.load().gwx_flow_train_workspace(ctypes.byref(sh), B, self.D, self.N)
         ws = self._workspace(("train", B), nb)
         step = self.steps + 1 if update else 0
+        ctx = d_ctx = None
+        if self.resnet is not None:
+            import torch
+            ctx = self.resnet.forward(y, out_dtype=torch.bfloat16)
+            d_ctx = torch.empty(ctx.shape, dtype=torch.float32, device=self.dev)
         gwx.flow_train_step(self.shape, self.params, self.params16, self.grads, self.m, self.v, step, self.lr,
                             self.mean, self.scale, y, theta, self.fs, self.f_lo, weight_decay=self.wd, clip=self.clip,
-                            loss_mean=self._loss, workspace=ws)
+                            loss_mean=self._loss, workspace=ws, ctx=ctx, d_ctx=d_ctx)
         if update:
             self.steps += 1
+            if self.resnet is not None:
+                G = self.resnet.backward(d_ctx)
+                for name, p, p16 in self.resnet.tensors():
+                    mm, vv = self.rmom[name]
+                    gwx.adamw(p, G[name].contiguous(), mm, vv, self.steps, self.lr, weight_decay=self.wd,
+                              param_bf16=p16)
         return self._loss
+
+    def context(self, y):
+        """The ResNet-1D summary of y (bfloat16 [rows][C]), or None for the built-in one."""
+        import torch
+        return None if self.resnet is None else self.resnet.forward(y, out_dtype=torch.bfloat16)
 
     def capture_train_step(self, y, theta):
         """Capture one training step on the batch buffers y [B][D][N], theta [11][B] into a
@@ -122,6 +149,8 @@ class FlowPosterior:
         import ctypes
         import torch
         gwx = self.gwx
+        if self.resnet is not None:
+            raise NotImplementedError("graph capture covers the built-in summary only")
         if getattr(self, "step_dev", None) is None:
             self.step_dev = torch.tensor([self.steps], dtype=torch.int64, device=self.dev)
         else:
@@ -146,17 +175,17 @@ class FlowPosterior:
         (theta [11][S], ln q_r [S], ln prior_r - ln q_r [S])."""
         return self.gwx.sample_posterior(self.shape, self.params, self.params16, self.mean, self.scale,
                                          self.wl["prior"], y_events, self.fs, self.f_lo, truth, event_offsets, seed,
-                                         counter)
+                                         counter, ctx=self.context(y_events))
 
     def log_prob(self, y, theta):
         return self.gwx.flow_log_prob(self.shape, self.params, self.params16, self.mean, self.scale, y, theta,
-                                      self.fs, self.f_lo)
+                                      self.fs, self.f_lo, ctx=self.context(y))
 
     # ------------------------------------------------------------ checkpoints
     _MAGIC = b"GWXFLOW1"
 
     def save(self, path, next_step=None):
-        """Flat binary checkpoint: magic, little-endian int64 header (7 shape fields, steps,
+        """Flat binary checkpoint (built-in summary only): magic, little-endian int64 header (7 shape fields, steps,
         next_step, n_params), 16 float64 (mean, scale), then params, m and v as float32."""
         import numpy as np
         sh = self.shape

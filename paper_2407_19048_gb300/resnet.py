@@ -128,8 +128,9 @@ class ResNet1D:
         return (o32 if out32 else o16), ms
 
     # ------------------------------------------------------------------ forward / backward
-    def forward(self, y):
-        """Representation [B][out_dim] (FP32) of whitened windows y [B][D][N] (FP32)."""
+    def forward(self, y, out_dtype=None):
+        """Representation [B][out_dim] (FP32, or out_dtype) of whitened windows y [B][D][N]
+        (FP32)."""
         import torch
         gwx, lib = self.gwx, _lib.load()
         st = gwx._stream()
@@ -163,7 +164,7 @@ class ResNet1D:
         gwx._check(lib.gwx_mean_time(gwx._ptr(h), B, T, C, gwx._ptr(m), st))
         tape["m"] = m
         self.tape = tape
-        return gwx.dense_bf16(m, self.W16["Wf"], self.P["bf"], act=gwx.ACT_NONE, out_dtype=torch.float32)
+        return gwx.dense_bf16(m, self.W16["Wf"], self.P["bf"], act=gwx.ACT_NONE, out_dtype=out_dtype or torch.float32)
 
     def _gn_back(self, dy, z, ms, g):
         import torch

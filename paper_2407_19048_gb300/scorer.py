@@ -74,7 +74,7 @@ class Scorer:
             fp = self.flow
             _check(lib.gwx_sample_posterior(ctypes.byref(self.shape), _ptr(fp.params), _ptr(fp.params16), self.mean8,
                                             self.scale8, ctypes.byref(self.prior), _ptr(y_event), 1, self.D, self.N,
-                                            self.fs, self.f_lo, _ptr(truth), _ptr(self.ev), S, self.seed,
+                                            self.fs, self.f_lo, None, _ptr(truth), _ptr(self.ev), S, self.seed,
                                             step & 0xFFFFFFFF, theta, _ptr(self.log_q), _ptr(self.log_ratio),
                                             _ptr(ws), nb, s))
             ratio = _ptr(self.log_ratio)

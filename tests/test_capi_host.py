@@ -123,12 +123,12 @@ def test_flow_layout_and_validation(lib):
     # batch not a multiple of 8: rejected before any launch
     st = lib.gwx_flow_train_step(ctypes.byref(sh), None, None, None, None, None, 1, None, 1e-3, 0.9, 0.999, 1e-8, 0.0,
                                  1.0,
-                                 m8, s8, None, None, 12, 2, 2048, 1024.0, 20.0, None, None, 0, None)
+                                 m8, s8, None, None, 12, 2, 2048, 1024.0, 20.0, None, None, None, None, 0, None)
     assert st == -2 and b"multiple of 8" in lib.gwx_last_error()
     # too few feature columns for the band
     sh_small = gwx.flow_shape(64, 16, 64, 32, 3, 48)
     st = lib.gwx_flow_log_prob(ctypes.byref(sh_small), None, None, m8, s8, None, None, 8, 2, 2048, 1024.0, 20.0,
-                               None, None, 0, None)
+                               None, None, None, 0, None)
     assert st == -2 and b"groups" in lib.gwx_last_error()
     bad = (ctypes.c_double * 8)(*([1.0] * 7 + [0.0]))
     st = lib.gwx_flow_targets(None, 4, m8, bad, None, None)

@@ -390,3 +390,38 @@ def test_captured_training_step_replays_like_eager_steps(gwx):
     assert int(b.step_dev.item()) == 4 and b.steps == 4
     assert torch.allclose(a.params, b.params, rtol=1e-5, atol=1e-7)
     assert torch.allclose(a.m, b.m, rtol=1e-5, atol=1e-9)
+
+
+def test_external_context_matches_oracle_and_resnet_summary_trains(gwx, model):
+    """The flow with the caller's context (the ResNet-1D path) against the oracle's flow
+    with that context, and a short training run of flow + ResNet-1D summary."""
+    from oracle.gemm import bf16_to_f64
+    from paper_2407_19048_gb300.flow import FlowPosterior
+    from paper_2407_19048_gb300.simulator import Simulator
+    fp, params = model
+    B = 32
+    y, th = _batch(360, B)
+    bits = workloads.random_bf16_bits(361, (B, 32), exp_lo=-3, exp_hi=0)
+    ctx = torch.from_numpy(bits.view(np.int16)).cuda().view(torch.bfloat16)
+    got = host(fp.gwx.flow_log_prob(fp.shape, fp.params, fp.params16, MEAN, SCALE, cuda(y), cuda(th), WL["fs"],
+                                    WL["f_lo"], ctx=ctx))
+    _, layers = fl.split_params(params, 4)
+    x = fl.standardise(fl.coords(th), MEAN, SCALE)
+    z, ss, _ = fl.density(x, bf16_to_f64(bits), layers)
+    ref = fl.log_normal(z) - ss - np.sum(np.log(SCALE))
+    assert np.all(np.abs(got - ref) <= 5e-3 + 5e-4 * np.abs(ref)), np.max(np.abs(got - ref))
+    # flow + ResNet-1D summary: the loss falls
+    sim = Simulator(dict(WL, B=64))
+    net = FlowPosterior(dict(WL, B=64), layers=2, hidden=64, context=32, group=GROUP, seed=8, lr=1e-3,
+                        embedding="resnet", resnet_stages=((8, 1, 1), (16, 1, 2), (16, 1, 2)))
+    losses = []
+    for step in range(120):
+        yb, tb, _ = sim.step(step)
+        losses.append(float(host(net.train_step(yb, tb))[0]))
+    assert np.mean(losses[-15:]) < np.mean(losses[:15]) - 0.3, (np.mean(losses[:15]), np.mean(losses[-15:]))
+    offs = torch.tensor([0, 100, 250], dtype=torch.int64, device="cuda")
+    theta_s, lq, lr = net.sample(yb[:2].contiguous(), tb[:, :2].contiguous(), offs, 3, 0)
+    ok = torch.isfinite(lr)
+    lp = net.log_prob(yb[torch.tensor([0] * 100 + [1] * 150, device="cuda")][ok].contiguous(),
+                      theta_s[:, ok].contiguous())
+    assert torch.allclose(lp, lq[ok], atol=1e-2, rtol=1e-3)
