@@ -592,7 +592,8 @@ int gwx_prepare_theta(const double* theta, int64_t L, int64_t N, double fs, doub
  *   FP64 sums; residual FP32 or bfloat16 or none; act ReLU when relu != 0); out bfloat16
  *   (out16) and/or FP32 (out32); mean_rstd [B][G][2] kept for the backward.
  * gwx_group_norm_backward: dz = rstd (dy gamma - mean(dy gamma) - xhat mean(dy gamma xhat))
- *   per group, dgamma_c = sum dy xhat, dbeta_c = sum dy; scratch [B][G][2].
+ *   per group, dgamma_c = sum dy xhat, dbeta_c = sum dy (deterministic FP64 sums); scratch
+ *   of gwx_group_norm_backward_scratch(B, C, G) bytes (256-byte aligned).
  * gwx_relu_mask: d = dy [out > 0] (out bfloat16).
  * gwx_maxpool: kernel 3, stride 2, padding 1 over time, the first maximum of a window;
  *   arg [B][T_out][C] its offset (0..2); gwx_maxpool_backward routes dy there.
@@ -604,8 +605,9 @@ int gwx_col2im(const float* dcols, int64_t B, int T, int C, int k, int s, int p,
 int gwx_group_norm(const float* z, int64_t B, int T, int C, int G, const float* gamma, const float* beta,
                    const float* residual32, const void* residual16, int relu, void* out16, float* out32,
                    float* mean_rstd, void* stream);
+size_t gwx_group_norm_backward_scratch(int64_t B, int C, int G);
 int gwx_group_norm_backward(const float* dy, const float* z, int64_t B, int T, int C, int G, const float* mean_rstd,
-                            const float* gamma, float* scratch, float* dz, float* dgamma, float* dbeta, void* stream);
+                            const float* gamma, void* scratch, float* dz, float* dgamma, float* dbeta, void* stream);
 int gwx_relu_mask(const float* dy, const void* out, int64_t n, float* d, void* stream);
 int gwx_maxpool(const void* x, int64_t B, int T, int C, void* y, uint8_t* arg, void* stream);
 int gwx_maxpool_backward(const float* dy, const uint8_t* arg, int64_t B, int T, int C, float* dx, void* stream);

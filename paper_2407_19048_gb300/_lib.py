@@ -97,6 +97,7 @@ SIGNATURES = {
                                c_vp]),
     "gwx_group_norm_backward": (c_int, [c_vp, c_vp, c_i64, c_int, c_int, c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
                                         c_vp]),
+    "gwx_group_norm_backward_scratch": (c_size, [c_i64, c_int, c_int]),
     "gwx_relu_mask": (c_int, [c_vp, c_vp, c_i64, c_vp, c_vp]),
     "gwx_maxpool": (c_int, [c_vp, c_i64, c_int, c_int, c_vp, c_vp, c_vp]),
     "gwx_maxpool_backward": (c_int, [c_vp, c_vp, c_i64, c_int, c_int, c_vp, c_vp]),

@@ -829,8 +829,13 @@ int gwx_group_norm(const float* z, int64_t B, int T, int C, int G, const float* 
                   "group_norm");
 }
 
+size_t gwx_group_norm_backward_scratch(int64_t B, int C, int G) {
+  if (B < 1 || C < 1 || G < 1) return 0;
+  return align_up(group_norm_backward_scratch(B, C, G));
+}
+
 int gwx_group_norm_backward(const float* dy, const float* z, int64_t B, int T, int C, int G, const float* mean_rstd,
-                            const float* gamma, float* scratch, float* dz, float* dgamma, float* dbeta, void* stream) {
+                            const float* gamma, void* scratch, float* dz, float* dgamma, float* dbeta, void* stream) {
   GWX_TRY(check_btc(B, T, C));
   if (G < 1 || C % G) return fail(GWX_ESHAPE, "C=%d not a multiple of G=%d", C, G);
   if (!dy || !z || !mean_rstd || !gamma || !scratch || !dz || !dgamma || !dbeta) return fail(GWX_EINVAL, "NULL array");

@@ -192,8 +192,9 @@ cudaError_t launch_col2im(const float* dcols, int64_t B, int T, int C, int k, in
 cudaError_t launch_group_norm(const float* z, int64_t B, int T, int C, int G, const float* gamma, const float* beta,
                               const float* res32, const void* res16, int relu, void* out16, float* out32, float* ms,
                               cudaStream_t st);
+size_t group_norm_backward_scratch(int64_t B, int C, int G);
 cudaError_t launch_group_norm_backward(const float* dy, const float* z, int64_t B, int T, int C, int G,
-                                       const float* ms, const float* gamma, float* mm, float* dz, float* dgamma,
+                                       const float* ms, const float* gamma, void* scratch, float* dz, float* dgamma,
                                        float* dbeta, cudaStream_t st);
 cudaError_t launch_relu_mask(const float* dy, const void* out, int64_t n, float* d, cudaStream_t st);
 cudaError_t launch_maxpool(const void* x, int64_t B, int T, int C, void* y, uint8_t* arg, cudaStream_t st);

@@ -5,7 +5,7 @@
 // k_im2col_cf for the channels-first input strain), fold row gradients back (k_col2im),
 // normalise per sample and channel group (k_gn_stats, k_gn_apply, with the residual
 // addition and the ReLU fused) and take the gradient of that (k_gn_bwd_stats,
-// k_gn_bwd_apply, k_gn_param_grad, k_relu_mask), and pool (k_maxpool, k_mean_time and
+// k_gn_bwd_apply, k_gn_param_part / k_gn_param_finish, k_relu_mask), and pool (k_maxpool, k_mean_time and
 // their backward).
 #include <cuda_bf16.h>
 
@@ -179,18 +179,22 @@ __global__ void k_gn_bwd_apply(const float* __restrict__ dy, const float* __rest
   dz[i] = rstd * (dy[i] * gamma[c] - mm[2 * bg] - xh * mm[2 * bg + 1]);
 }
 
-// dgamma_c = sum dy xhat, dbeta_c = sum dy over samples and times: block (32 channels x 8
-// row lanes), FP64 sums, one column of results per block.
-__global__ void __launch_bounds__(256) k_gn_param_grad(const float* __restrict__ dy, const float* __restrict__ z,
+// dgamma_c = sum dy xhat, dbeta_c = sum dy over samples and times, in two deterministic
+// passes: block (channel tile of 32, row slice) sums its slice (8 row lanes, FP64) into
+// part[slice][c][2]; k_gn_param_finish adds the slices.
+constexpr int GN_SLICES = 64;
+
+__global__ void __launch_bounds__(256) k_gn_param_part(const float* __restrict__ dy, const float* __restrict__ z,
                                                        int64_t rows, int T, int C, int G,
-                                                       const float* __restrict__ ms, float* __restrict__ dgamma,
-                                                       float* __restrict__ dbeta) {
+                                                       const float* __restrict__ ms, double* __restrict__ part) {
   __shared__ double a[8][33], bb[8][33];
   const int cx = threadIdx.x & 31, ry = threadIdx.x >> 5;
   const int c = blockIdx.x * 32 + cx;
+  const int64_t per = (rows + GN_SLICES - 1) / GN_SLICES;
+  const int64_t r0 = blockIdx.y * per, r1 = min(rows, r0 + per);
   double sg = 0.0, sb = 0.0;
   if (c < C)
-    for (int64_t r = ry; r < rows; r += 8) {
+    for (int64_t r = r0 + ry; r < r1; r += 8) {
       const int64_t i = r * C + c;
       const int64_t bg = (r / T) * G + c / (C / G);
       const double xh = (double)((z[i] - ms[2 * bg]) * ms[2 * bg + 1]);
@@ -206,9 +210,22 @@ __global__ void __launch_bounds__(256) k_gn_param_grad(const float* __restrict__
       tg += a[k][cx];
       tb += bb[k][cx];
     }
-    dgamma[c] = (float)tg;
-    dbeta[c] = (float)tb;
+    part[((int64_t)blockIdx.y * C + c) * 2] = tg;
+    part[((int64_t)blockIdx.y * C + c) * 2 + 1] = tb;
   }
+}
+
+__global__ void k_gn_param_finish(const double* __restrict__ part, int C, float* __restrict__ dgamma,
+                                  float* __restrict__ dbeta) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  double tg = 0.0, tb = 0.0;
+  for (int s = 0; s < GN_SLICES; ++s) {
+    tg += part[((int64_t)s * C + c) * 2];
+    tb += part[((int64_t)s * C + c) * 2 + 1];
+  }
+  dgamma[c] = (float)tg;
+  dbeta[c] = (float)tb;
 }
 
 // k 3, s 2, p 1 max pool over time (first maximum of a window), and its backward.
@@ -306,12 +323,20 @@ cudaError_t launch_group_norm(const float* z, int64_t B, int T, int C, int G, co
   return cudaGetLastError();
 }
 
+size_t group_norm_backward_scratch(int64_t B, int C, int G) {
+  return (size_t)B * G * 2 * sizeof(float) + 256 + (size_t)GN_SLICES * C * 2 * sizeof(double);
+}
+
 cudaError_t launch_group_norm_backward(const float* dy, const float* z, int64_t B, int T, int C, int G,
-                                       const float* ms, const float* gamma, float* mm, float* dz, float* dgamma,
+                                       const float* ms, const float* gamma, void* scratch, float* dz, float* dgamma,
                                        float* dbeta, cudaStream_t st) {
+  float* mm = reinterpret_cast<float*>(scratch);
+  double* part = reinterpret_cast<double*>(reinterpret_cast<char*>(scratch) +
+                                           (((size_t)B * G * 2 * sizeof(float) + 255) & ~(size_t)255));
   k_gn_bwd_stats<<<(unsigned)(B * G), 256, 0, st>>>(dy, z, T, C, G, ms, gamma, mm);
   k_gn_bwd_apply<<<nblk(B * T * C, 256), 256, 0, st>>>(dy, z, B, T, C, G, ms, mm, gamma, dz);
-  k_gn_param_grad<<<nblk(C, 32), 256, 0, st>>>(dy, z, B * T, T, C, G, ms, dgamma, dbeta);
+  k_gn_param_part<<<dim3(nblk(C, 32), GN_SLICES), 256, 0, st>>>(dy, z, B * T, T, C, G, ms, part);
+  k_gn_param_finish<<<nblk(C, 128), 128, 0, st>>>(part, C, dgamma, dbeta);
   return cudaGetLastError();
 }
 

@@ -166,13 +166,23 @@ class ResNet1D:
         self.tape = tape
         return gwx.dense_bf16(m, self.W16["Wf"], self.P["bf"], act=gwx.ACT_NONE, out_dtype=out_dtype or torch.float32)
 
+    def _scratch(self, nbytes):
+        import torch
+        buf = getattr(self, "_scratch_buf", None)
+        if buf is None or buf.numel() < nbytes + 256:
+            self._scratch_buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.dev)
+        buf = self._scratch_buf
+        off = (-buf.data_ptr()) % 256
+        return buf[off:off + nbytes]
+
     def _gn_back(self, dy, z, ms, g):
         import torch
         gwx, lib = self.gwx, _lib.load()
         B, T, C = dy.shape
         dz = torch.empty_like(dy)
         dg, db = torch.empty(C, device=self.dev), torch.empty(C, device=self.dev)
-        scratch = torch.empty((B, GROUPS, 2), dtype=torch.float32, device=self.dev)
+        nb = lib.gwx_group_norm_backward_scratch(B, C, GROUPS)
+        scratch = self._scratch(nb)
         gwx._check(lib.gwx_group_norm_backward(gwx._ptr(dy), gwx._ptr(z), B, T, C, GROUPS, gwx._ptr(ms), gwx._ptr(g),
                                                gwx._ptr(scratch), gwx._ptr(dz), gwx._ptr(dg), gwx._ptr(db),
                                                gwx._stream()))
