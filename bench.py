@@ -475,6 +475,34 @@ def padded_leg(gwx, torch, rank, B=2048, N_pad=8192, reps=20):
     return out
 
 
+def sweep_leg(gwx, torch, rank, steps=40, warmup=3):
+    """Throughput at the long-window geometry (H1+L1+V1, 2048 Hz, 8 s windows, N = 16384,
+    8192 draws per step: 1.61 GB of whitened strain per step, larger than L2, so no flush
+    is needed): the same pipelined simulator step as the headline, background every 16
+    steps, with the fused call's share timed on its own for the roofline."""
+    wl = workloads.workload("sweep")
+    sim = gwx.simulator.Simulator(wl, pipeline=True, background_every=16)
+    for i in range(warmup):
+        sim.step(step_counter(rank, 70000 + i))
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        ev[i][0].record()
+        sim.step(step_counter(rank, 70000 + warmup + i), mark=ev[i][1])
+        torch.cuda.current_stream().wait_stream(sim.side)
+        ev[i][2].record()
+    torch.cuda.synchronize()
+    step_ms = statistics.mean(e[0].elapsed_time(e[2]) for e in ev)
+    sim_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
+    B, D, N = wl["B"], len(wl["dets"]), wl["N"]
+    peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    tflops = flops_per_injection(wl) * B / (sim_ms * 1e-3) / 1e12
+    del sim
+    return {"workload": describe(wl), "steps": steps, "ms_per_step": step_ms, "injections_per_s": B / (step_ms * 1e-3),
+            "simulate_prepared_ms": sim_ms, "flops_per_injection": flops_per_injection(wl), "tflops": tflops,
+            "frac_of_fp32_peak": tflops / peak, "hbm_gbs_output_only": B * D * N * 4 / (sim_ms * 1e-3) / 1e9}
+
+
 def flow_resnet_leg(gwx, torch, rank, steps=500, batch=512, events=32, per_event=4000):
     """The flow with the paper's ResNet-1D data summary (stem, (5, 3, 3) residual blocks of
     64 / 128 / 256 channels, group norm, kernel 5; convolutions on the tensor cores) in
@@ -885,6 +913,7 @@ def run_gpu(args, wl):
     flow = flow_leg(gwx, torch, rank)
     flow_resnet = flow_resnet_leg(gwx, torch, rank)
     padded = padded_leg(gwx, torch, rank)
+    sweep = sweep_leg(gwx, torch, rank)
 
     sim_avg_s = statistics.mean(sim_ms) * 1e-3
     flops = flops_per_injection(wl) * B
@@ -939,6 +968,7 @@ def run_gpu(args, wl):
             "flow": flow,
             "flow_resnet": flow_resnet,
             "padded_grid": padded,
+            "long_windows": sweep,
             "wall_s_timed_region": t_wall,
         }
         print(json.dumps(line), flush=True)
