@@ -503,7 +503,7 @@ def sweep_leg(gwx, torch, rank, steps=40, warmup=3):
             "frac_of_fp32_peak": tflops / peak, "hbm_gbs_output_only": B * D * N * 4 / (sim_ms * 1e-3) / 1e9}
 
 
-def flow_resnet_leg(gwx, torch, rank, steps=500, batch=512, events=32, per_event=4000):
+def flow_resnet_leg(gwx, torch, rank, steps=1500, batch=512, events=32, per_event=4000):
     """The flow with the paper's ResNet-1D data summary (stem, (5, 3, 3) residual blocks of
     64 / 128 / 256 channels, group norm, kernel 5; convolutions on the tensor cores) in
     place of the spectral-feature network, trained jointly with AdamW on 512-draw batches
@@ -551,13 +551,13 @@ def flow_resnet_leg(gwx, torch, rank, steps=500, batch=512, events=32, per_event
                                     "chain_ms": best * 1e3}}
 
 
-def flow_leg(gwx, torch, rank, steps=8000, events=32, per_event=4000, pp_events=200, pp_samples=500, lr=6e-4,
+def flow_leg(gwx, torch, rank, steps=12000, events=32, per_event=4000, pp_events=200, pp_samples=500, lr=6e-4,
              cross=True, batch=4096, layers=16, hidden=256, clip=1.0, pretrain_steps=2000):
     """The conditional coupling flow (16 affine coupling layers, conditioners 72 -> 256 ->
     256 -> 8; embedding 1968 -> 512 -> 512 -> 64 on log group powers, inter-detector cross
     spectra and lag-one spectral products; tcgen05 dense layers) trained with AdamW (lr
     6e-4, weight decay 2e-3, gradient norm clipped at 1) on 4096-draw batches of the
-    two-detector workload, 8000 steps = 32.8 M simulations (one CUDA-graph replay of the
+    two-detector workload, 12000 steps = 49.2 M simulations (one CUDA-graph replay of the
     C-ABI training call per step), after 2000 steps of VICReg pre-training of the data
     summary on pairs of views that differ only in merger time; then
     posterior sampling (20,000 draws of one event, the paper's inference size), importance
@@ -999,6 +999,8 @@ def main(argv=None):
                          "times; for profiling")
     ap.add_argument("--only-flow", default=None, metavar="STEPS",
                     help="run only the coupling-flow leg with this many training steps; for profiling")
+    ap.add_argument("--only-resnet", default=None, metavar="STEPS",
+                    help="run only the ResNet-1D flow leg with this many training steps; for profiling")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -1040,6 +1042,13 @@ def main(argv=None):
         import paper_2407_19048_gb300.simulator  # noqa: F401
         gwx.init()
         print(json.dumps({"flow": flow_leg(gwx, torch, 0, steps=int(args.only_flow))}), flush=True)
+        return 0
+    if args.only_resnet:
+        import torch
+        import paper_2407_19048_gb300 as gwx
+        import paper_2407_19048_gb300.simulator  # noqa: F401
+        gwx.init()
+        print(json.dumps({"flow_resnet": flow_resnet_leg(gwx, torch, 0, steps=int(args.only_resnet))}), flush=True)
         return 0
     if args.only_loglike:
         import torch

@@ -583,16 +583,20 @@ int gwx_prepare_theta(const double* theta, int64_t L, int64_t N, double fs, doub
  * weights W [C_out][K] on the tensor cores (gwx_dense_bf16, gwx_dense_bf16_backward):
  *   cols[b, t][j C + c] = x[b][s t + j - p][c] (zero outside 0 .. T - 1; columns k C .. K - 1
  *   zero), T_out = (T + 2 p - k) / s + 1.
+ * Shapes for every call below: 1 <= B <= 65535, T C < 2^31 and B T < 2^31 (T_out K < 2^31
+ *   for the row builders); otherwise GWX_ESHAPE.
  * gwx_im2col: bfloat16 x -> bfloat16 cols [B T_out][K]; C, K multiples of 8.
  * gwx_im2col_cf: the same rows from channels-first FP32 y [B][D][N] (whitened strain).
  * gwx_col2im: the adjoint: dx [B][T][C] (FP32) = addend (optional) + sum over the rows and
  *   taps that read x[b][t][c] of dcols (FP32 [B T_out][K]).
  * gwx_group_norm: per sample and group of C / G channels, over all T and those channels:
- *   out = act(gamma_c (z - mean) / sqrt(var + 1e-5) + beta_c + residual) (biased variance,
- *   FP64 sums; residual FP32 or bfloat16 or none; act ReLU when relu != 0); out bfloat16
+ *   out = act(gamma_c (z - mean) / sqrt(var + 1e-5) + beta_c + residual) (biased variance of
+ *   the values shifted by the group's first value: FP32 sums of a few dozen terms per
+ *   thread, FP64 across threads; residual FP32 or bfloat16 or none; act ReLU when relu != 0); out bfloat16
  *   (out16) and/or FP32 (out32); mean_rstd [B][G][2] kept for the backward.
  * gwx_group_norm_backward: dz = rstd (dy gamma - mean(dy gamma) - xhat mean(dy gamma xhat))
- *   per group, dgamma_c = sum dy xhat, dbeta_c = sum dy (deterministic FP64 sums); scratch
+ *   per group, dgamma_c = sum dy xhat, dbeta_c = sum dy (deterministic: FP32 over runs of
+ *   at most 64 terms, FP64 across runs and threads); scratch
  *   of gwx_group_norm_backward_scratch(B, C, G) bytes (256-byte aligned).
  * gwx_relu_mask: d = dy [out > 0] (out bfloat16).
  * gwx_maxpool: kernel 3, stride 2, padding 1 over time, the first maximum of a window;

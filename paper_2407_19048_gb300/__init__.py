@@ -338,21 +338,24 @@ def dense_bf16(X, W, bias=None, act=ACT_NONE, out=None, out_dtype=None):
     return out
 
 
-def dense_bf16_backward(X, W, bias, dY, act=ACT_NONE):
+def dense_bf16_backward(X, W, bias, dY, act=ACT_NONE, want_dx=True, want_db=None):
     """Gradients of Y = act(X W^T + bias) for dL/dY = dY (float32 [M][N]): returns
-    (dX float32 [M][K], dW float32 [N][K], db float32 [N])."""
+    (dX float32 [M][K], dW float32 [N][K], db float32 [N]); dX is None when want_dx is
+    false and db None when want_db is false (default: db only when there is a bias)."""
     torch = _torch()
     _dev(X, torch.bfloat16, "X")
     _dev(W, torch.bfloat16, "W")
     _dev(dY, torch.float32, "dY")
     if bias is not None:
         _dev(bias, torch.float32, "bias")
+    if want_db is None:
+        want_db = bias is not None
     M, K = X.shape
     N = W.shape[0]
     dev = X.device
-    dX = torch.empty((M, K), dtype=torch.float32, device=dev)
+    dX = torch.empty((M, K), dtype=torch.float32, device=dev) if want_dx else None
     dW = torch.empty((N, K), dtype=torch.float32, device=dev)
-    db = torch.empty(N, dtype=torch.float32, device=dev)
+    db = torch.empty(N, dtype=torch.float32, device=dev) if want_db else None
     lib = _lib.load()
     ws, nb = _workspace(lib.gwx_dense_bf16_backward_workspace(M, N, K), dev)
     _check(lib.gwx_dense_bf16_backward(_ptr(X), _ptr(W), _ptr(bias), _ptr(dY), M, N, K, act, _ptr(dX), _ptr(dW),

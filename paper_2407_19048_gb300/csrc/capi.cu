@@ -783,8 +783,17 @@ int gwx_retime(const double* theta_in, double* theta_out, int64_t B, double tc_l
 
 // ---- ResNet-1D pieces
 namespace {
+// The kernels run one grid row per sample with 32-bit index arithmetic within a sample.
 int check_btc(int64_t B, int T, int C) {
-  if (B < 1 || T < 1 || C < 1 || B * (int64_t)T * C > ((int64_t)1 << 34)) return fail(GWX_ESHAPE, "bad B, T or C");
+  if (B < 1 || T < 1 || C < 1 || B > 65535 || (int64_t)T * C >= ((int64_t)1 << 31) ||
+      B * (int64_t)T >= ((int64_t)1 << 31))
+    return fail(GWX_ESHAPE, "B=%lld T=%d C=%d (need 1 <= B <= 65535, T C < 2^31, B T < 2^31)", (long long)B, T, C);
+  return GWX_OK;
+}
+
+int check_rows(int T, int k, int s, int p, int K) {
+  const int64_t To = ((int64_t)T + 2 * p - k) / s + 1;
+  if (To * K >= ((int64_t)1 << 31)) return fail(GWX_ESHAPE, "T_out K = %lld (at most 2^31 - 1)", (long long)(To * K));
   return GWX_OK;
 }
 }  // namespace
@@ -793,6 +802,7 @@ int gwx_im2col(const void* x, int64_t B, int T, int C, int k, int s, int p, int 
   GWX_TRY(check_btc(B, T, C));
   if (C % 8 || K % 8 || K < k * C || k < 1 || s < 1 || p < 0 || T + 2 * p < k)
     return fail(GWX_ESHAPE, "im2col C=%d K=%d k=%d s=%d p=%d (C and K multiples of 8, K >= k C)", C, K, k, s, p);
+  GWX_TRY(check_rows(T, k, s, p, K));
   if (!x || !cols) return fail(GWX_EINVAL, "NULL array");
   GWX_ALIGN16(x);
   GWX_ALIGN16(cols);
@@ -803,6 +813,7 @@ int gwx_im2col(const void* x, int64_t B, int T, int C, int k, int s, int p, int 
 int gwx_im2col_cf(const float* y, int64_t B, int D, int N, int k, int s, int p, int K, void* cols, void* stream) {
   GWX_TRY(check_btc(B, N, D));
   if (K < k * D || k < 1 || s < 1 || p < 0 || N + 2 * p < k) return fail(GWX_ESHAPE, "im2col_cf shapes");
+  GWX_TRY(check_rows(N, k, s, p, K));
   if (!y || !cols) return fail(GWX_EINVAL, "NULL array");
   GWX_TRY(ensure_init());
   return launched(launch_im2col_cf(y, B, D, N, k, s, p, K, cols, as_stream(stream)), "im2col_cf");
@@ -812,6 +823,7 @@ int gwx_col2im(const float* dcols, int64_t B, int T, int C, int k, int s, int p,
                void* stream) {
   GWX_TRY(check_btc(B, T, C));
   if (K < k * C || k < 1 || s < 1 || p < 0 || T + 2 * p < k) return fail(GWX_ESHAPE, "col2im shapes");
+  GWX_TRY(check_rows(T, k, s, p, K));
   if (!dcols || !dx) return fail(GWX_EINVAL, "NULL array");
   GWX_TRY(ensure_init());
   return launched(launch_col2im(dcols, B, T, C, k, s, p, K, addend, dx, as_stream(stream)), "col2im");

@@ -86,6 +86,12 @@ cudaError_t launch_importance_weights(const double* lnl, const double* ratio, co
 // group: tile-rows per raster band (0 = the default).
 cudaError_t launch_gemm_bf16(const void* A, const void* B, void* C, int64_t M, int64_t N, int64_t K, bool out_bf16,
                              const float* bias, int act, int group, cudaStream_t s);
+// Split-K product C [M][N] (FP32) = A B^T for few tiles and a long K: the slices' partial
+// products go to `part` (gemm_splitk_ws bytes), then one kernel sums them in order.
+int gemm_splits(int64_t M, int64_t N, int64_t K);
+size_t gemm_splitk_ws(int64_t M, int64_t N, int64_t K);
+cudaError_t launch_gemm_splitk(const void* A, const void* B, float* C, int64_t M, int64_t N, int64_t K, float* part,
+                               cudaStream_t s);
 cudaError_t gemm_status(int* status);
 
 // Dense-layer backward (k_dense.cu): workspace bytes and the launcher.

@@ -2,11 +2,14 @@
 // (the embedding network of Sec. 4 and the flow of Sec. 5), by the chain rule:
 //   dZ = dY * act'(Z),  dX = dZ W,  dW = dZ^T X,  db = sum over rows of dZ,
 // with both products on the tensor cores (the tcgen05 GEMM, K-major operands): dX takes
-// dZ [M][N] and W^T [K][N], dW takes dZ^T [N][M] and X^T [K][M].  This file holds the
+// dZ [M][N] and W^T [K][N], dW takes dZ^T [N][M] and X^T [K][M] (split along M when its
+// N x K output has few tiles: M is the batch and can be long).  This file holds the
 // elementwise and layout kernels around them: the activation derivative with the
 // bfloat16 dZ, its transpose and per-tile column sums in one pass, bfloat16 transposes,
 // and the final column-sum reduction.
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "gwx_internal.h"
 
@@ -77,13 +80,37 @@ __global__ void __launch_bounds__(256) k_transpose_bf16(const __nv_bfloat16* __r
   }
 }
 
-// db[n] = sum_p part[p][n] (FP64 accumulation of the FP32 tile sums).
-__global__ void k_colsum(const float* __restrict__ part, int P, int N, float* __restrict__ db) {
+// db[n] = sum_p part[p][n] (FP64 accumulation of the FP32 tile sums), in two
+// deterministic passes: block (32 columns, slice y of the partials) has row lane ty sum
+// partials ty, ty + 32, ... of its slice, the 32 lanes in order into part2[y][n]; then
+// k_colsum_finish adds the slices in order.
+constexpr int CS_MAX_SLICES = 64;
+
+int colsum_slices(int64_t P) { return (int)std::min<int64_t>(CS_MAX_SLICES, std::max<int64_t>(1, (P + 255) / 256)); }
+
+__global__ void __launch_bounds__(1024) k_colsum(const float* __restrict__ part, int P, int N,
+                                                 double* __restrict__ part2) {
+  __shared__ double red[TT][TT + 1];
+  const int n = blockIdx.x * TT + threadIdx.x;
+  const int per = (P + gridDim.y - 1) / gridDim.y, p0 = blockIdx.y * per, p1 = min(P, p0 + per);
+  double s = 0.0;
+  if (n < N)
+    for (int p = p0 + threadIdx.y; p < p1; p += TT) s += (double)__ldg(&part[(int64_t)p * N + n]);
+  red[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && n < N) {
+    double t = 0.0;
+    for (int y = 0; y < TT; ++y) t += red[y][threadIdx.x];
+    part2[(int64_t)blockIdx.y * N + n] = t;
+  }
+}
+
+__global__ void k_colsum_finish(const double* __restrict__ part2, int slices, int N, float* __restrict__ db) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
-  double s = 0.0;
-  for (int p = 0; p < P; ++p) s += (double)part[(int64_t)p * N + n];
-  db[n] = (float)s;
+  double t = 0.0;
+  for (int y = 0; y < slices; ++y) t += part2[(int64_t)y * N + n];
+  db[n] = (float)t;
 }
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -96,7 +123,9 @@ size_t dense_backward_ws(int64_t M, int64_t N, int64_t K) {
          + align256((size_t)M * N * 2) * 2      // dZ, dZ^T
          + align256((size_t)K * M * 2)          // X^T
          + align256((size_t)K * N * 2)          // W^T
-         + align256((size_t)P * N * 4);         // column-sum partials
+         + align256((size_t)P * N * 4)          // column-sum partials
+         + align256((size_t)CS_MAX_SLICES * N * 8)   // their slice sums
+         + align256(gemm_splitk_ws(N, K, M));   // split-K slices of dW
 }
 
 cudaError_t launch_dense_backward(const void* X, const void* W, const float* bias, const float* dY, int64_t M,
@@ -115,6 +144,10 @@ cudaError_t launch_dense_backward(const void* X, const void* W, const float* bia
   w += align256((size_t)K * N * 2);
   float* part = reinterpret_cast<float*>(w);
   const int64_t P = (M + TT - 1) / TT;
+  w += align256((size_t)P * N * 4);
+  double* part2 = reinterpret_cast<double*>(w);
+  w += align256((size_t)CS_MAX_SLICES * N * 8);
+  float* kpart = reinterpret_cast<float*>(w);
   cudaError_t e = cudaSuccess;
   // pre-activation Z = X W^T + b (only the activation derivative needs it)
   if (act != GWX_ACT_NONE) {
@@ -133,9 +166,12 @@ cudaError_t launch_dense_backward(const void* X, const void* W, const float* bia
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // dX [M][K] = dZ [M][N] . (W^T [K][N])^T ;  dW [N][K] = dZ^T [N][M] . (X^T [K][M])^T
   if (dX && (e = launch_gemm_bf16(dZ, Wt, dX, M, K, N, false, nullptr, GWX_ACT_NONE, 0, s)) != cudaSuccess) return e;
-  if (dW && (e = launch_gemm_bf16(dZt, Xt, dW, N, K, M, false, nullptr, GWX_ACT_NONE, 0, s)) != cudaSuccess) return e;
+  if (dW && (e = launch_gemm_splitk(dZt, Xt, dW, N, K, M, kpart, s)) != cudaSuccess) return e;
   if (db) {
-    k_colsum<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(part, (int)P, (int)N, db);
+    const int slices = colsum_slices(P);
+    k_colsum<<<dim3((unsigned)((N + TT - 1) / TT), (unsigned)slices), dim3(TT, TT), 0, s>>>(part, (int)P, (int)N,
+                                                                                            part2);
+    k_colsum_finish<<<(unsigned)((N + 127) / 128), 128, 0, s>>>(part2, slices, (int)N, db);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -17,6 +17,11 @@
 //   with a short K, where it, not the MMA, sets the time per tile.
 // Every mbarrier wait is bounded: on expiry the CTA records a status, stops storing,
 // frees its tensor memory and returns.
+//
+// Split K: a product with few tiles and a long K (the weight gradients dW = dZ^T X, whose
+// K is the batch) would run on a handful of SMs.  There the work list is (tile, K slice)
+// pairs: slice s covers K blocks [s kbs, (s + 1) kbs) and stores its FP32 partial product
+// at C + s M N; a second kernel sums the slices in a fixed order (deterministic).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -80,7 +85,7 @@ __device__ __forceinline__ void tile_coords(int t, int TM, int TN, int group, in
 template <bool OUT_BF16>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, void* __restrict__ C,
-                const float* __restrict__ bias, int act, int group, int M, int N, int K) {
+                const float* __restrict__ bias, int act, int group, int M, int N, int K, int kbs, int splits) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2];
   __shared__ uint32_t tmem_slot;
@@ -90,6 +95,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   const int KB = (K + GK - 1) / GK;
   const int TM = (M + GM - 1) / GM, TN = (N + GN - 1) / GN;
   const int tiles = TM * TN;
+  const int work = tiles * splits;   // (tile, K slice) pairs, tile fastest
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -117,10 +123,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   if (warp == 0) {
     if (lane == 0) {
       uint32_t it = 0;
-      for (int t = blockIdx.x; t < tiles && !*(volatile int*)&abort_flag; t += gridDim.x) {
+      for (int w = blockIdx.x; w < work && !*(volatile int*)&abort_flag; w += gridDim.x) {
         int tm, tn;
-        tile_coords(t, TM, TN, group, tm, tn);
-        for (int kb = 0; kb < KB; ++kb, ++it) {
+        tile_coords(w % tiles, TM, TN, group, tm, tn);
+        const int kb0 = (w / tiles) * kbs, kb1 = min(KB, kb0 + kbs);
+        for (int kb = kb0; kb < kb1; ++kb, ++it) {
           const uint32_t s = it % STAGES;
           if (it >= STAGES && !mbar_wait(su32(&empty[s]), ((it / STAGES) - 1) & 1u, WAIT_POLLS)) {
             atomicExch(&abort_flag, 1);
@@ -136,8 +143,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       uint32_t it = 0, tl = 0;
-      for (int t = blockIdx.x; t < tiles && !*(volatile int*)&abort_flag; t += gridDim.x, ++tl) {
+      for (int w = blockIdx.x; w < work && !*(volatile int*)&abort_flag; w += gridDim.x, ++tl) {
         const uint32_t acc = tl & 1u;
+        const int kb0 = (w / tiles) * kbs, kb1 = min(KB, kb0 + kbs);
         if (tl >= 2 && !mbar_wait(su32(&tempty[acc]), ((tl >> 1) - 1) & 1u, WAIT_POLLS)) {
           atomicExch(&abort_flag, 1);
           break;
@@ -145,7 +153,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t d = tmem + acc * TMEM_COLS;
         bool ok = true;
-        for (int kb = 0; kb < KB; ++kb, ++it) {
+        for (int kb = kb0; kb < kb1; ++kb, ++it) {
           const uint32_t s = it % STAGES;
           if (!mbar_wait(su32(&full[s]), (it / STAGES) & 1u, WAIT_POLLS)) {
             ok = false;
@@ -155,7 +163,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           const uint32_t sa = base + s * STAGE_BYTES, sb = sa + A_BYTES;
 #pragma unroll
           for (int kk = 0; kk < GK / 16; ++kk)   // 16 bfloat16 = 32 bytes along K per instruction
-            mma_bf16(d, sw128_desc(sa + 32u * kk), sw128_desc(sb + 32u * kk), IDESC, (kb | kk) != 0);
+            mma_bf16(d, sw128_desc(sa + 32u * kk), sw128_desc(sb + 32u * kk), IDESC, kb != kb0 || kk != 0);
           mma_commit(su32(&empty[s]));
         }
         if (!ok) atomicExch(&abort_flag, 1);
@@ -171,9 +179,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     float* ebuf = reinterpret_cast<float*>(smem_raw + (base - su32(smem_raw)) + STAGES * STAGE_BYTES +
                                            (warp - 2) * EPI_BUF_BYTES);
     uint32_t tl = 0;
-    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++tl) {
+    for (int w = blockIdx.x; w < work; w += gridDim.x, ++tl) {
       int tm, tn;
-      tile_coords(t, TM, TN, group, tm, tn);
+      tile_coords(w % tiles, TM, TN, group, tm, tn);
+      const size_t slice = (size_t)(w / tiles) * (size_t)M * (size_t)N;   // 0 unless split
       const uint32_t acc = tl & 1u;
       const bool have = mbar_wait(su32(&tfull[acc]), (tl >> 1) & 1u, WAIT_POLLS);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -196,7 +205,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         for (int j = 0; j < 32; ++j) ebuf[lane * 32 + (j ^ lane)] = v[j];
         __syncwarp();
         if constexpr (OUT_BF16) {
-          __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(C);
+          __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(C) + slice;
           const int w = lane & 15, col = col0 + 2 * w;
 #pragma unroll 4
           for (int r2 = 0; r2 < 16; ++r2) {
@@ -214,7 +223,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             }
           }
         } else {
-          float* out = reinterpret_cast<float*>(C);
+          float* out = reinterpret_cast<float*>(C) + slice;
           const int col = col0 + lane;
 #pragma unroll 4
           for (int r = 0; r < 32; ++r) {
@@ -263,10 +272,17 @@ bool make_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t K, uint32
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-}  // namespace
+// out[i] = sum over s of part[s][i] for i < n (slices in order: deterministic).
+__global__ void k_split_reduce(const float* __restrict__ part, int splits, int64_t n, float* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float acc = 0.f;
+  for (int s = 0; s < splits; ++s) acc += __ldg(&part[(int64_t)s * n + i]);
+  out[i] = acc;
+}
 
-cudaError_t launch_gemm_bf16(const void* A, const void* B, void* C, int64_t M, int64_t N, int64_t K, bool out_bf16,
-                             const float* bias, int act, int group, cudaStream_t s) {
+cudaError_t launch_gemm(const void* A, const void* B, void* C, int64_t M, int64_t N, int64_t K, bool out_bf16,
+                        const float* bias, int act, int group, int splits, cudaStream_t s) {
   if (group < 1) group = DEFAULT_GROUP;
   CUtensorMap ta, tb;
   if (!make_map(&ta, A, M, K, GM) || !make_map(&tb, B, N, K, GN)) return cudaErrorInvalidValue;
@@ -274,17 +290,55 @@ cudaError_t launch_gemm_bf16(const void* A, const void* B, void* C, int64_t M, i
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  const int64_t tiles = ((M + GM - 1) / GM) * ((N + GN - 1) / GN);
-  const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);   // persistent: one CTA per SM
+  const int KB = (int)((K + GK - 1) / GK);
+  const int kbs = (KB + splits - 1) / splits;   // every slice has at least one K block
+  splits = (KB + kbs - 1) / kbs;
+  const int64_t work = ((M + GM - 1) / GM) * ((N + GN - 1) / GN) * splits;
+  const unsigned grid = (unsigned)(work < sms ? work : sms);   // persistent: one CTA per SM
   if (out_bf16) {
     e = cudaFuncSetAttribute(k_gemm_bf16<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
     if (e != cudaSuccess) return e;
-    k_gemm_bf16<true><<<grid, GEMM_THREADS, GEMM_SMEM, s>>>(ta, tb, C, bias, act, group, (int)M, (int)N, (int)K);
+    k_gemm_bf16<true><<<grid, GEMM_THREADS, GEMM_SMEM, s>>>(ta, tb, C, bias, act, group, (int)M, (int)N, (int)K, kbs,
+                                                            splits);
   } else {
     e = cudaFuncSetAttribute(k_gemm_bf16<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
     if (e != cudaSuccess) return e;
-    k_gemm_bf16<false><<<grid, GEMM_THREADS, GEMM_SMEM, s>>>(ta, tb, C, bias, act, group, (int)M, (int)N, (int)K);
+    k_gemm_bf16<false><<<grid, GEMM_THREADS, GEMM_SMEM, s>>>(ta, tb, C, bias, act, group, (int)M, (int)N, (int)K, kbs,
+                                                             splits);
   }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_gemm_bf16(const void* A, const void* B, void* C, int64_t M, int64_t N, int64_t K, bool out_bf16,
+                             const float* bias, int act, int group, cudaStream_t s) {
+  return launch_gemm(A, B, C, M, N, K, out_bf16, bias, act, group, 1, s);
+}
+
+int gemm_splits(int64_t M, int64_t N, int64_t K) {
+  const int64_t tiles = ((M + GM - 1) / GM) * ((N + GN - 1) / GN);
+  const int64_t KB = (K + GK - 1) / GK;
+  if (tiles >= 64) return 1;
+  int64_t sp = std::min<int64_t>(128 / tiles, KB / 4);   // ~128 work items, >= 4 K blocks per slice
+  if (sp <= 1) return 1;
+  const int64_t kbs = (KB + sp - 1) / sp;
+  return (int)((KB + kbs - 1) / kbs);
+}
+
+size_t gemm_splitk_ws(int64_t M, int64_t N, int64_t K) {
+  const int sp = gemm_splits(M, N, K);
+  return sp > 1 ? (size_t)sp * (size_t)M * (size_t)N * 4 : 0;
+}
+
+cudaError_t launch_gemm_splitk(const void* A, const void* B, float* C, int64_t M, int64_t N, int64_t K, float* part,
+                               cudaStream_t s) {
+  const int sp = gemm_splits(M, N, K);
+  if (sp <= 1) return launch_gemm(A, B, C, M, N, K, false, nullptr, GWX_ACT_NONE, 0, 1, s);
+  cudaError_t e = launch_gemm(A, B, part, M, N, K, false, nullptr, GWX_ACT_NONE, 0, sp, s);
+  if (e != cudaSuccess) return e;
+  const int64_t n = M * N;
+  k_split_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, sp, n, C);
   return cudaGetLastError();
 }
 

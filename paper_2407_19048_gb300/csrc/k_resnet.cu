@@ -7,6 +7,10 @@
 // addition and the ReLU fused) and take the gradient of that (k_gn_bwd_stats,
 // k_gn_bwd_apply, k_gn_param_part / k_gn_param_finish, k_relu_mask), and pool (k_maxpool, k_mean_time and
 // their backward).
+#include <stdint.h>
+
+#include <algorithm>
+
 #include <cuda_bf16.h>
 
 #include "gwx_internal.h"
@@ -19,110 +23,205 @@ constexpr float GN_EPS = 1e-5f;
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Index arithmetic: every kernel runs on a grid whose y coordinate is the sample b and
+// whose x threads cover one sample's elements, so the divisions below are 32-bit (the
+// C-ABI keeps T C below 2^31 and B below 65536); sums are FP32 per thread over a few
+// dozen terms and FP64 across threads (GB300's FP64 rate is a small fraction of FP32).
+
 // cols[(b To + t) K + j C + c] = x[b][s t + j - p][c] (zero outside the series and for
 // columns >= k C); one thread per 8 columns (C % 8 == 0, so a chunk stays in one tap).
-__global__ void k_im2col(const __nv_bfloat16* __restrict__ x, int64_t B, int T, int C, int k, int s, int p, int To,
-                         int K, __nv_bfloat16* __restrict__ cols) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_im2col(const __nv_bfloat16* __restrict__ x, int T, int C, int k, int s, int p, int To, int K,
+                         __nv_bfloat16* __restrict__ cols) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int ch = K / 8;
-  if (i >= B * To * ch) return;
-  const int64_t row = i / ch;
-  const int q = (int)(i - row * ch);
-  const int64_t b = row / To;
-  const int t = (int)(row - b * To);
+  if (i >= To * ch) return;
+  const int64_t b = blockIdx.y;
+  const int t = i / ch, q = i - t * ch;
   const int col = 8 * q, j = col / C, c0 = col - j * C;
   uint4 v = make_uint4(0u, 0u, 0u, 0u);
   const int src = s * t + j - p;
   if (j < k && src >= 0 && src < T) v = *reinterpret_cast<const uint4*>(x + ((b * T + src) * C + c0));
-  reinterpret_cast<uint4*>(cols + row * K)[q] = v;
+  reinterpret_cast<uint4*>(cols + (b * To + t) * K)[q] = v;
 }
 
 // The same rows from channels-first FP32 input y [B][D][N] (the whitened strain).
-__global__ void k_im2col_cf(const float* __restrict__ y, int64_t B, int D, int N, int k, int s, int p, int To, int K,
+__global__ void k_im2col_cf(const float* __restrict__ y, int D, int N, int k, int s, int p, int To, int K,
                             __nv_bfloat16* __restrict__ cols) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= B * To * K) return;
-  const int64_t row = i / K;
-  const int col = (int)(i - row * K);
-  const int64_t b = row / To;
-  const int t = (int)(row - b * To);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= To * K) return;
+  const int64_t b = blockIdx.y;
+  const int t = i / K, col = i - t * K;
   float v = 0.f;
   if (col < k * D) {
     const int j = col / D, c = col - j * D, src = s * t + j - p;
     if (src >= 0 && src < N) v = y[(b * D + c) * N + src];
   }
-  cols[i] = __float2bfloat16_rn(v);
+  cols[(b * To + t) * K + col] = __float2bfloat16_rn(v);
 }
 
 // dx[b][t][c] = (addend) + sum over taps j with s t_out = t + p - j of dcols[b, t_out][j C + c]
-__global__ void k_col2im(const float* __restrict__ dcols, int64_t B, int T, int C, int k, int s, int p, int To, int K,
+__global__ void k_col2im(const float* __restrict__ dcols, int T, int C, int k, int s, int p, int To, int K,
                          const float* __restrict__ addend, float* __restrict__ dx) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= B * T * C) return;
-  const int64_t bt = i / C;
-  const int c = (int)(i - bt * C);
-  const int64_t b = bt / T;
-  const int t = (int)(bt - b * T);
-  float acc = addend ? addend[i] : 0.f;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= T * C) return;
+  const int64_t b = blockIdx.y;
+  const int t = i / C, c = i - t * C;
+  const int64_t o = b * T * C + i;
+  float acc = addend ? addend[o] : 0.f;
   for (int j = 0; j < k; ++j) {
     const int num = t + p - j;
     if (num < 0 || num % s) continue;
     const int to = num / s;
     if (to < To) acc += dcols[(b * To + to) * K + j * C + c];
   }
-  dx[i] = acc;
+  dx[o] = acc;
 }
 
-// Per (sample, group): mean and 1 / sqrt(var + eps) over T x C/G values (FP64 sums).
+// The same with KT taps known at compile time and four channels per thread: all taps'
+// float4 loads are issued before the sums (in tap order, as above).
+template <int KT>
+__global__ void k_col2im4(const float* __restrict__ dcols, int T, int C, int s, int p, int To, int K,
+                          const float* __restrict__ addend, float* __restrict__ dx) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= T * C / 4) return;
+  const int64_t b = blockIdx.y;
+  const int t = (4 * i) / C, c = 4 * i - t * C;
+  float4 v[KT];
+#pragma unroll
+  for (int j = 0; j < KT; ++j) {
+    const int num = t + p - j;
+    const int to = num / s;
+    v[j] = (num >= 0 && num - to * s == 0 && to < To)
+               ? __ldg(reinterpret_cast<const float4*>(dcols + (b * To + to) * K + j * C + c))
+               : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  const int64_t o = b * T * C + 4 * (int64_t)i;
+  float4 acc = addend ? *reinterpret_cast<const float4*>(addend + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < KT; ++j) {
+    acc.x += v[j].x;
+    acc.y += v[j].y;
+    acc.z += v[j].z;
+    acc.w += v[j].w;
+  }
+  *reinterpret_cast<float4*>(dx + o) = acc;
+}
+
+// Block sums of two FP32 per-thread partials in FP64 (warp shuffles, then the warps in
+// order); the totals land in thread 0.
+__device__ __forceinline__ void block_sum2(double& a, double& b2) {
+  __shared__ double r[2][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b2 += __shfl_down_sync(0xffffffffu, b2, o);
+  }
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    r[0][w] = a;
+    r[1][w] = b2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a = 0.0;
+    b2 = 0.0;
+    for (int k = 0; k < nw; ++k) {
+      a += r[0][k];
+      b2 += r[1][k];
+    }
+  }
+}
+
+// Per (sample, group): mean and 1 / sqrt(var + eps) over T x C/G values.  The values are
+// shifted by the group's first value before squaring, so the FP32 partial sums do not
+// cancel when the mean is large against the spread.  VEC values per load (4 when C/G is a
+// multiple of 4).
+template <int VEC>
 __global__ void __launch_bounds__(256) k_gn_stats(const float* __restrict__ z, int T, int C, int G,
                                                   float* __restrict__ ms) {
-  __shared__ double r1[256], r2[256];
-  const int64_t b = blockIdx.x / G;
-  const int g = blockIdx.x % G, cg = C / G;
-  const int n = T * cg;
-  double s1 = 0.0, s2 = 0.0;
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    const int t = e / cg, c = g * cg + e % cg;
-    const double v = z[(b * T + t) * C + c];
-    s1 += v;
-    s2 += v * v;
-  }
-  r1[threadIdx.x] = s1;
-  r2[threadIdx.x] = s2;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) {
-      r1[threadIdx.x] += r1[threadIdx.x + o];
-      r2[threadIdx.x] += r2[threadIdx.x + o];
+  const int b = blockIdx.x / G, g = blockIdx.x - (blockIdx.x / G) * G, cg = C / G, cv = cg / VEC;
+  const float* zb = z + (int64_t)b * T * C + g * cg;
+  const float k0 = __ldg(zb);
+  float s1 = 0.f, s2 = 0.f;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < T * cv; e += blockDim.x) {
+    const int t = e / cv, c = (e - t * cv) * VEC;
+    if constexpr (VEC == 4) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(zb + (int64_t)t * C + c));
+      const float d0 = v.x - k0, d1 = v.y - k0, d2 = v.z - k0, d3 = v.w - k0;
+      s1 += (d0 + d1) + (d2 + d3);
+      s2 += (d0 * d0 + d1 * d1) + (d2 * d2 + d3 * d3);
+    } else {
+      const float d = __ldg(zb + (int64_t)t * C + c) - k0;
+      s1 += d;
+      s2 += d * d;
     }
-    __syncthreads();
   }
+  double a = s1, q = s2;
+  block_sum2(a, q);
   if (threadIdx.x == 0) {
-    const double mean = r1[0] / n, var = fmax(r2[0] / n - mean * mean, 0.0);
-    ms[2 * blockIdx.x] = (float)mean;
+    const double n = (double)T * cg, m = a / n, var = fmax(q / n - m * m, 0.0);
+    ms[2 * blockIdx.x] = (float)((double)k0 + m);
     ms[2 * blockIdx.x + 1] = (float)(1.0 / sqrt(var + (double)GN_EPS));
   }
 }
 
 // out = act(gamma_c (z - mean) rstd + beta_c + residual), bfloat16 or FP32 out; residual
-// FP32 (res32) or bfloat16 (res16) or none.
-__global__ void k_gn_apply(const float* __restrict__ z, int64_t B, int T, int C, int G, const float* __restrict__ ms,
+// FP32 (res32) or bfloat16 (res16) or none.  VEC consecutive channels per thread.
+template <int VEC>
+__global__ void k_gn_apply(const float* __restrict__ z, int T, int C, int G, const float* __restrict__ ms,
                            const float* __restrict__ gamma, const float* __restrict__ beta,
                            const float* __restrict__ res32, const __nv_bfloat16* __restrict__ res16, int relu,
                            __nv_bfloat16* __restrict__ out16, float* __restrict__ out32) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= B * T * C) return;
-  const int64_t bt = i / C;
-  const int c = (int)(i - bt * C);
-  const int64_t b = bt / T;
-  const int g = c / (C / G);
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= T * C / VEC) return;
+  const int b = blockIdx.y;
+  const int c = (j * VEC) % C, g = c / (C / G);
+  const int64_t i = (int64_t)b * T * C + (int64_t)j * VEC;
   const float mean = ms[2 * (b * G + g)], rstd = ms[2 * (b * G + g) + 1];
-  float v = fmaf((z[i] - mean) * rstd, gamma[c], beta[c]);
-  if (res32) v += res32[i];
-  if (res16) v += __bfloat162float(res16[i]);
-  if (relu) v = fmaxf(v, 0.f);
-  if (out16) out16[i] = __float2bfloat16_rn(v);
-  if (out32) out32[i] = v;
+  float v[VEC];
+  if constexpr (VEC == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(z + i);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  } else {
+    v[0] = z[i];
+  }
+#pragma unroll
+  for (int u = 0; u < VEC; ++u) v[u] = fmaf((v[u] - mean) * rstd, __ldg(&gamma[c + u]), __ldg(&beta[c + u]));
+  if (res32) {
+    if constexpr (VEC == 4) {
+      const float4 q = *reinterpret_cast<const float4*>(res32 + i);
+      v[0] += q.x; v[1] += q.y; v[2] += q.z; v[3] += q.w;
+    } else {
+      v[0] += res32[i];
+    }
+  }
+  if (res16) {
+    if constexpr (VEC == 4) {
+      const uint2 q = *reinterpret_cast<const uint2*>(res16 + i);
+      const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.x));
+      const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.y));
+      v[0] += lo.x; v[1] += lo.y; v[2] += hi.x; v[3] += hi.y;
+    } else {
+      v[0] += __bfloat162float(res16[i]);
+    }
+  }
+  if (relu) {
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) v[u] = fmaxf(v[u], 0.f);
+  }
+  if constexpr (VEC == 4) {
+    if (out16) {
+      __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]), hi = __floats2bfloat162_rn(v[2], v[3]);
+      uint2 q;
+      q.x = *reinterpret_cast<uint32_t*>(&lo);
+      q.y = *reinterpret_cast<uint32_t*>(&hi);
+      *reinterpret_cast<uint2*>(out16 + i) = q;
+    }
+    if (out32) *reinterpret_cast<float4*>(out32 + i) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+    if (out16) out16[i] = __float2bfloat16_rn(v[0]);
+    if (out32) out32[i] = v[0];
+  }
 }
 
 // dsum = dy [out > 0]
@@ -132,75 +231,119 @@ __global__ void k_relu_mask(const float* __restrict__ dy, const __nv_bfloat16* _
   if (i < n) d[i] = __bfloat162float(out[i]) > 0.f ? dy[i] : 0.f;
 }
 
-// Per (sample, group): the means of dxh = dy gamma and dxh xhat (FP64 sums).
+// The same, four elements per thread (n4 = n / 4 groups).
+__global__ void k_relu_mask4(const float* __restrict__ dy, const __nv_bfloat16* __restrict__ out, int64_t n4,
+                             float* __restrict__ d) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n4) return;
+  const float4 g = __ldg(reinterpret_cast<const float4*>(dy) + i);
+  const uint2 q = __ldg(reinterpret_cast<const uint2*>(out) + i);
+  const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.x));
+  const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.y));
+  reinterpret_cast<float4*>(d)[i] = make_float4(lo.x > 0.f ? g.x : 0.f, lo.y > 0.f ? g.y : 0.f,
+                                                hi.x > 0.f ? g.z : 0.f, hi.y > 0.f ? g.w : 0.f);
+}
+
+// Per (sample, group): the means of dxh = dy gamma and dxh xhat.
+template <int VEC>
 __global__ void __launch_bounds__(256) k_gn_bwd_stats(const float* __restrict__ dy, const float* __restrict__ z,
                                                       int T, int C, int G, const float* __restrict__ ms,
                                                       const float* __restrict__ gamma, float* __restrict__ mm) {
-  __shared__ double r1[256], r2[256];
-  const int64_t b = blockIdx.x / G;
-  const int g = blockIdx.x % G, cg = C / G;
-  const int n = T * cg;
+  const int b = blockIdx.x / G, g = blockIdx.x - (blockIdx.x / G) * G, cg = C / G, cv = cg / VEC;
+  const int64_t base = (int64_t)b * T * C + g * cg;
   const float mean = ms[2 * blockIdx.x], rstd = ms[2 * blockIdx.x + 1];
-  double s1 = 0.0, s2 = 0.0;
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    const int t = e / cg, c = g * cg + e % cg;
-    const int64_t i = (b * T + t) * C + c;
-    const double dxh = (double)dy[i] * gamma[c];
-    s1 += dxh;
-    s2 += dxh * (double)((z[i] - mean) * rstd);
-  }
-  r1[threadIdx.x] = s1;
-  r2[threadIdx.x] = s2;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) {
-      r1[threadIdx.x] += r1[threadIdx.x + o];
-      r2[threadIdx.x] += r2[threadIdx.x + o];
+  float s1 = 0.f, s2 = 0.f;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < T * cv; e += blockDim.x) {
+    const int t = e / cv, c = (e - t * cv) * VEC;
+    const int64_t i = base + (int64_t)t * C + c;
+    if constexpr (VEC == 4) {
+      const float4 d = __ldg(reinterpret_cast<const float4*>(dy + i));
+      const float4 x = __ldg(reinterpret_cast<const float4*>(z + i));
+      const float4 gm = make_float4(__ldg(&gamma[g * cg + c]), __ldg(&gamma[g * cg + c + 1]),
+                                    __ldg(&gamma[g * cg + c + 2]), __ldg(&gamma[g * cg + c + 3]));
+      const float a0 = d.x * gm.x, a1 = d.y * gm.y, a2 = d.z * gm.z, a3 = d.w * gm.w;
+      s1 += (a0 + a1) + (a2 + a3);
+      s2 += (a0 * ((x.x - mean) * rstd) + a1 * ((x.y - mean) * rstd)) +
+            (a2 * ((x.z - mean) * rstd) + a3 * ((x.w - mean) * rstd));
+    } else {
+      const float a = __ldg(dy + i) * __ldg(&gamma[g * cg + c]);
+      s1 += a;
+      s2 += a * ((__ldg(z + i) - mean) * rstd);
     }
-    __syncthreads();
   }
+  double a = s1, q = s2;
+  block_sum2(a, q);
   if (threadIdx.x == 0) {
-    mm[2 * blockIdx.x] = (float)(r1[0] / n);
-    mm[2 * blockIdx.x + 1] = (float)(r2[0] / n);
+    const double n = (double)T * cg;
+    mm[2 * blockIdx.x] = (float)(a / n);
+    mm[2 * blockIdx.x + 1] = (float)(q / n);
   }
 }
 
 // dz = rstd (dy gamma - m1 - xhat m2)
-__global__ void k_gn_bwd_apply(const float* __restrict__ dy, const float* __restrict__ z, int64_t B, int T, int C,
-                               int G, const float* __restrict__ ms, const float* __restrict__ mm,
+template <int VEC>
+__global__ void k_gn_bwd_apply(const float* __restrict__ dy, const float* __restrict__ z, int T, int C, int G,
+                               const float* __restrict__ ms, const float* __restrict__ mm,
                                const float* __restrict__ gamma, float* __restrict__ dz) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= B * T * C) return;
-  const int64_t bt = i / C;
-  const int c = (int)(i - bt * C);
-  const int64_t bg = (bt / T) * G + c / (C / G);
-  const float mean = ms[2 * bg], rstd = ms[2 * bg + 1];
-  const float xh = (z[i] - mean) * rstd;
-  dz[i] = rstd * (dy[i] * gamma[c] - mm[2 * bg] - xh * mm[2 * bg + 1]);
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= T * C / VEC) return;
+  const int b = blockIdx.y;
+  const int c = (j * VEC) % C, bg = b * G + c / (C / G);
+  const int64_t i = (int64_t)b * T * C + (int64_t)j * VEC;
+  const float mean = ms[2 * bg], rstd = ms[2 * bg + 1], m1 = mm[2 * bg], m2 = mm[2 * bg + 1];
+  if constexpr (VEC == 4) {
+    const float4 d = *reinterpret_cast<const float4*>(dy + i);
+    const float4 x = *reinterpret_cast<const float4*>(z + i);
+    float4 o;
+    o.x = rstd * (d.x * __ldg(&gamma[c]) - m1 - (x.x - mean) * rstd * m2);
+    o.y = rstd * (d.y * __ldg(&gamma[c + 1]) - m1 - (x.y - mean) * rstd * m2);
+    o.z = rstd * (d.z * __ldg(&gamma[c + 2]) - m1 - (x.z - mean) * rstd * m2);
+    o.w = rstd * (d.w * __ldg(&gamma[c + 3]) - m1 - (x.w - mean) * rstd * m2);
+    *reinterpret_cast<float4*>(dz + i) = o;
+  } else {
+    dz[i] = rstd * (dy[i] * gamma[c] - m1 - (z[i] - mean) * rstd * m2);
+  }
 }
 
 // dgamma_c = sum dy xhat, dbeta_c = sum dy over samples and times, in two deterministic
-// passes: block (channel tile of 32, row slice) sums its slice (8 row lanes, FP64) into
-// part[slice][c][2]; k_gn_param_finish adds the slices.
-constexpr int GN_SLICES = 64;
+// passes: block (channel tile of 32, row slice of about 256 rows) sums its slice (8 row
+// lanes; FP32 over runs of 64 rows, FP64 across runs) into part[slice][c][2];
+// k_gn_param_finish adds the slices in order.
+constexpr int GN_MAX_SLICES = 1024;
+
+int gn_slices(int64_t rows) { return (int)std::min<int64_t>(GN_MAX_SLICES, std::max<int64_t>(1, (rows + 255) / 256)); }
 
 __global__ void __launch_bounds__(256) k_gn_param_part(const float* __restrict__ dy, const float* __restrict__ z,
-                                                       int64_t rows, int T, int C, int G,
+                                                       int rows, int T, int C, int G,
                                                        const float* __restrict__ ms, double* __restrict__ part) {
   __shared__ double a[8][33], bb[8][33];
   const int cx = threadIdx.x & 31, ry = threadIdx.x >> 5;
   const int c = blockIdx.x * 32 + cx;
-  const int64_t per = (rows + GN_SLICES - 1) / GN_SLICES;
-  const int64_t r0 = blockIdx.y * per, r1 = min(rows, r0 + per);
+  const int per = (rows + gridDim.y - 1) / gridDim.y;
+  const int r0 = blockIdx.y * per, r1 = min(rows, r0 + per);
   double sg = 0.0, sb = 0.0;
-  if (c < C)
-    for (int64_t r = r0 + ry; r < r1; r += 8) {
-      const int64_t i = r * C + c;
-      const int64_t bg = (r / T) * G + c / (C / G);
-      const double xh = (double)((z[i] - ms[2 * bg]) * ms[2 * bg + 1]);
-      sg += (double)dy[i] * xh;
-      sb += (double)dy[i];
+  if (c < C) {
+    const int g = c / (C / G);
+    int r = r0 + ry, b = r / T, t = r - b * T;
+    while (r < r1) {
+      float fg = 0.f, fb = 0.f;
+      for (int n = 0; n < 64 && r < r1; ++n) {
+        const int64_t i = (int64_t)r * C + c;
+        const float d = __ldg(dy + i);
+        fg += d * ((__ldg(z + i) - ms[2 * (b * G + g)]) * ms[2 * (b * G + g) + 1]);
+        fb += d;
+        r += 8;
+        t += 8;
+        while (t >= T) {
+          t -= T;
+          ++b;
+        }
+      }
+      sg += fg;
+      sb += fb;
     }
+  }
   a[ry][cx] = sg;
   bb[ry][cx] = sb;
   __syncthreads();
@@ -215,28 +358,39 @@ __global__ void __launch_bounds__(256) k_gn_param_part(const float* __restrict__
   }
 }
 
-__global__ void k_gn_param_finish(const double* __restrict__ part, int C, float* __restrict__ dgamma,
-                                  float* __restrict__ dbeta) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= C) return;
+// Slices in order: block (32 channels) x (32 lanes), lane y summing slices y, y + 32, ...,
+// then the 32 lanes in order.
+__global__ void __launch_bounds__(1024) k_gn_param_finish(const double* __restrict__ part, int slices, int C,
+                                                          float* __restrict__ dgamma, float* __restrict__ dbeta) {
+  __shared__ double rg[32][33], rb[32][33];
+  const int c = blockIdx.x * 32 + threadIdx.x;
   double tg = 0.0, tb = 0.0;
-  for (int s = 0; s < GN_SLICES; ++s) {
-    tg += part[((int64_t)s * C + c) * 2];
-    tb += part[((int64_t)s * C + c) * 2 + 1];
+  if (c < C)
+    for (int s = threadIdx.y; s < slices; s += 32) {
+      tg += part[((int64_t)s * C + c) * 2];
+      tb += part[((int64_t)s * C + c) * 2 + 1];
+    }
+  rg[threadIdx.y][threadIdx.x] = tg;
+  rb[threadIdx.y][threadIdx.x] = tb;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < C) {
+    double g = 0.0, bsum = 0.0;
+    for (int y = 0; y < 32; ++y) {
+      g += rg[y][threadIdx.x];
+      bsum += rb[y][threadIdx.x];
+    }
+    dgamma[c] = (float)g;
+    dbeta[c] = (float)bsum;
   }
-  dgamma[c] = (float)tg;
-  dbeta[c] = (float)tb;
 }
 
 // k 3, s 2, p 1 max pool over time (first maximum of a window), and its backward.
-__global__ void k_maxpool(const __nv_bfloat16* __restrict__ x, int64_t B, int T, int C, int To,
-                          __nv_bfloat16* __restrict__ y, uint8_t* __restrict__ arg) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= B * To * C) return;
-  const int64_t bt = i / C;
-  const int c = (int)(i - bt * C);
-  const int64_t b = bt / To;
-  const int t = (int)(bt - b * To);
+__global__ void k_maxpool(const __nv_bfloat16* __restrict__ x, int T, int C, int To, __nv_bfloat16* __restrict__ y,
+                          uint8_t* __restrict__ arg) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= To * C) return;
+  const int64_t b = blockIdx.y;
+  const int t = i / C, c = i - t * C;
   float best = -INFINITY;
   int a = 0;
   for (int j = 0; j < 3; ++j) {
@@ -248,25 +402,23 @@ __global__ void k_maxpool(const __nv_bfloat16* __restrict__ x, int64_t B, int T,
       a = j;
     }
   }
-  y[i] = __float2bfloat16_rn(best);
-  arg[i] = (uint8_t)a;
+  y[b * To * C + i] = __float2bfloat16_rn(best);
+  arg[b * To * C + i] = (uint8_t)a;
 }
 
-__global__ void k_maxpool_back(const float* __restrict__ dy, const uint8_t* __restrict__ arg, int64_t B, int T, int C,
-                               int To, float* __restrict__ dx) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= B * T * C) return;
-  const int64_t bt = i / C;
-  const int c = (int)(i - bt * C);
-  const int64_t b = bt / T;
-  const int t = (int)(bt - b * T);
+__global__ void k_maxpool_back(const float* __restrict__ dy, const uint8_t* __restrict__ arg, int T, int C, int To,
+                               float* __restrict__ dx) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= T * C) return;
+  const int64_t b = blockIdx.y;
+  const int t = i / C, c = i - t * C;
   float acc = 0.f;
   for (int to = t / 2; to <= (t + 1) / 2; ++to) {
     if (to >= To) continue;
     const int64_t o = (b * To + to) * C + c;
     if (2 * to - 1 + (int)arg[o] == t) acc += dy[o];
   }
-  dx[i] = acc;
+  dx[b * T * C + i] = acc;
 }
 
 __global__ void k_mean_time(const __nv_bfloat16* __restrict__ x, int64_t B, int T, int C,
@@ -280,51 +432,72 @@ __global__ void k_mean_time(const __nv_bfloat16* __restrict__ x, int64_t B, int 
   m[i] = __float2bfloat16_rn(acc / T);
 }
 
-__global__ void k_mean_time_back(const float* __restrict__ dm, int64_t B, int T, int C, float* __restrict__ dx) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= B * T * C) return;
-  const int64_t b = i / ((int64_t)T * C);
-  const int c = (int)(i % C);
-  dx[i] = dm[b * C + c] / T;
+__global__ void k_mean_time_back(const float* __restrict__ dm, int T, int C, float* __restrict__ dx) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= T * C) return;
+  const int64_t b = blockIdx.y;
+  dx[b * T * C + i] = dm[b * C + i % C] / T;
 }
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+bool aligned8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
 
 }  // namespace
 
 cudaError_t launch_im2col(const void* x, int64_t B, int T, int C, int k, int s, int p, int K, void* cols,
                           cudaStream_t st) {
   const int To = (T + 2 * p - k) / s + 1;
-  k_im2col<<<nblk(B * To * (K / 8), 256), 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(x), B, T, C, k, s, p,
-                                                        To, K, reinterpret_cast<__nv_bfloat16*>(cols));
+  k_im2col<<<dim3(nblk((int64_t)To * (K / 8), 256), (unsigned)B), 256, 0, st>>>(
+      reinterpret_cast<const __nv_bfloat16*>(x), T, C, k, s, p, To, K, reinterpret_cast<__nv_bfloat16*>(cols));
   return cudaGetLastError();
 }
 
 cudaError_t launch_im2col_cf(const float* y, int64_t B, int D, int N, int k, int s, int p, int K, void* cols,
                              cudaStream_t st) {
   const int To = (N + 2 * p - k) / s + 1;
-  k_im2col_cf<<<nblk(B * To * K, 256), 256, 0, st>>>(y, B, D, N, k, s, p, To, K,
-                                                     reinterpret_cast<__nv_bfloat16*>(cols));
+  k_im2col_cf<<<dim3(nblk((int64_t)To * K, 256), (unsigned)B), 256, 0, st>>>(y, D, N, k, s, p, To, K,
+                                                                             reinterpret_cast<__nv_bfloat16*>(cols));
   return cudaGetLastError();
 }
 
 cudaError_t launch_col2im(const float* dcols, int64_t B, int T, int C, int k, int s, int p, int K, const float* addend,
                           float* dx, cudaStream_t st) {
   const int To = (T + 2 * p - k) / s + 1;
-  k_col2im<<<nblk(B * T * C, 256), 256, 0, st>>>(dcols, B, T, C, k, s, p, To, K, addend, dx);
+  const bool v4 = C % 4 == 0 && K % 4 == 0 && aligned16(dcols) && aligned16(addend) && aligned16(dx);
+  const dim3 g4(nblk((int64_t)T * C / 4, 256), (unsigned)B);
+  if (v4 && k == 1) {
+    k_col2im4<1><<<g4, 256, 0, st>>>(dcols, T, C, s, p, To, K, addend, dx);
+  } else if (v4 && k == 5) {
+    k_col2im4<5><<<g4, 256, 0, st>>>(dcols, T, C, s, p, To, K, addend, dx);
+  } else if (v4 && k == 7) {
+    k_col2im4<7><<<g4, 256, 0, st>>>(dcols, T, C, s, p, To, K, addend, dx);
+  } else {
+    k_col2im<<<dim3(nblk((int64_t)T * C, 256), (unsigned)B), 256, 0, st>>>(dcols, T, C, k, s, p, To, K, addend, dx);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_group_norm(const float* z, int64_t B, int T, int C, int G, const float* gamma, const float* beta,
                               const float* res32, const void* res16, int relu, void* out16, float* out32, float* ms,
                               cudaStream_t st) {
-  k_gn_stats<<<(unsigned)(B * G), 256, 0, st>>>(z, T, C, G, ms);
-  k_gn_apply<<<nblk(B * T * C, 256), 256, 0, st>>>(z, B, T, C, G, ms, gamma, beta, res32,
-                                                   reinterpret_cast<const __nv_bfloat16*>(res16), relu,
-                                                   reinterpret_cast<__nv_bfloat16*>(out16), out32);
+  const bool v4 = (C / G) % 4 == 0 && aligned16(z) && aligned16(res32) && aligned8(res16) && aligned8(out16) &&
+                  aligned16(out32);
+  const auto r16 = reinterpret_cast<const __nv_bfloat16*>(res16);
+  const auto o16 = reinterpret_cast<__nv_bfloat16*>(out16);
+  if (v4) {
+    k_gn_stats<4><<<(unsigned)(B * G), 256, 0, st>>>(z, T, C, G, ms);
+    k_gn_apply<4><<<dim3(nblk((int64_t)T * C / 4, 256), (unsigned)B), 256, 0, st>>>(z, T, C, G, ms, gamma, beta, res32,
+                                                                                    r16, relu, o16, out32);
+  } else {
+    k_gn_stats<1><<<(unsigned)(B * G), 256, 0, st>>>(z, T, C, G, ms);
+    k_gn_apply<1><<<dim3(nblk((int64_t)T * C, 256), (unsigned)B), 256, 0, st>>>(z, T, C, G, ms, gamma, beta, res32,
+                                                                                r16, relu, o16, out32);
+  }
   return cudaGetLastError();
 }
 
 size_t group_norm_backward_scratch(int64_t B, int C, int G) {
-  return (size_t)B * G * 2 * sizeof(float) + 256 + (size_t)GN_SLICES * C * 2 * sizeof(double);
+  return (size_t)B * G * 2 * sizeof(float) + 256 + (size_t)GN_MAX_SLICES * C * 2 * sizeof(double);
 }
 
 cudaError_t launch_group_norm_backward(const float* dy, const float* z, int64_t B, int T, int C, int G,
@@ -333,29 +506,40 @@ cudaError_t launch_group_norm_backward(const float* dy, const float* z, int64_t 
   float* mm = reinterpret_cast<float*>(scratch);
   double* part = reinterpret_cast<double*>(reinterpret_cast<char*>(scratch) +
                                            (((size_t)B * G * 2 * sizeof(float) + 255) & ~(size_t)255));
-  k_gn_bwd_stats<<<(unsigned)(B * G), 256, 0, st>>>(dy, z, T, C, G, ms, gamma, mm);
-  k_gn_bwd_apply<<<nblk(B * T * C, 256), 256, 0, st>>>(dy, z, B, T, C, G, ms, mm, gamma, dz);
-  k_gn_param_part<<<dim3(nblk(C, 32), GN_SLICES), 256, 0, st>>>(dy, z, B * T, T, C, G, ms, part);
-  k_gn_param_finish<<<nblk(C, 128), 128, 0, st>>>(part, C, dgamma, dbeta);
+  const bool v4 = (C / G) % 4 == 0 && aligned16(dy) && aligned16(z) && aligned16(dz);
+  if (v4) {
+    k_gn_bwd_stats<4><<<(unsigned)(B * G), 256, 0, st>>>(dy, z, T, C, G, ms, gamma, mm);
+    k_gn_bwd_apply<4><<<dim3(nblk((int64_t)T * C / 4, 256), (unsigned)B), 256, 0, st>>>(dy, z, T, C, G, ms, mm, gamma,
+                                                                                        dz);
+  } else {
+    k_gn_bwd_stats<1><<<(unsigned)(B * G), 256, 0, st>>>(dy, z, T, C, G, ms, gamma, mm);
+    k_gn_bwd_apply<1><<<dim3(nblk((int64_t)T * C, 256), (unsigned)B), 256, 0, st>>>(dy, z, T, C, G, ms, mm, gamma, dz);
+  }
+  const int slices = gn_slices(B * T);
+  k_gn_param_part<<<dim3(nblk(C, 32), slices), 256, 0, st>>>(dy, z, (int)(B * T), T, C, G, ms, part);
+  k_gn_param_finish<<<nblk(C, 32), dim3(32, 32), 0, st>>>(part, slices, C, dgamma, dbeta);
   return cudaGetLastError();
 }
 
 cudaError_t launch_relu_mask(const float* dy, const void* out, int64_t n, float* d, cudaStream_t st) {
-  k_relu_mask<<<nblk(n, 256), 256, 0, st>>>(dy, reinterpret_cast<const __nv_bfloat16*>(out), n, d);
+  if (n % 4 == 0 && aligned16(dy) && aligned8(out) && aligned16(d))
+    k_relu_mask4<<<nblk(n / 4, 256), 256, 0, st>>>(dy, reinterpret_cast<const __nv_bfloat16*>(out), n / 4, d);
+  else
+    k_relu_mask<<<nblk(n, 256), 256, 0, st>>>(dy, reinterpret_cast<const __nv_bfloat16*>(out), n, d);
   return cudaGetLastError();
 }
 
 cudaError_t launch_maxpool(const void* x, int64_t B, int T, int C, void* y, uint8_t* arg, cudaStream_t st) {
   const int To = (T + 2 - 3) / 2 + 1;
-  k_maxpool<<<nblk(B * To * C, 256), 256, 0, st>>>(reinterpret_cast<const __nv_bfloat16*>(x), B, T, C, To,
-                                                   reinterpret_cast<__nv_bfloat16*>(y), arg);
+  k_maxpool<<<dim3(nblk((int64_t)To * C, 256), (unsigned)B), 256, 0, st>>>(
+      reinterpret_cast<const __nv_bfloat16*>(x), T, C, To, reinterpret_cast<__nv_bfloat16*>(y), arg);
   return cudaGetLastError();
 }
 
 cudaError_t launch_maxpool_back(const float* dy, const uint8_t* arg, int64_t B, int T, int C, float* dx,
                                 cudaStream_t st) {
   const int To = (T + 2 - 3) / 2 + 1;
-  k_maxpool_back<<<nblk(B * T * C, 256), 256, 0, st>>>(dy, arg, B, T, C, To, dx);
+  k_maxpool_back<<<dim3(nblk((int64_t)T * C, 256), (unsigned)B), 256, 0, st>>>(dy, arg, T, C, To, dx);
   return cudaGetLastError();
 }
 
@@ -366,7 +550,7 @@ cudaError_t launch_mean_time(const void* x, int64_t B, int T, int C, void* m, cu
 }
 
 cudaError_t launch_mean_time_back(const float* dm, int64_t B, int T, int C, float* dx, cudaStream_t st) {
-  k_mean_time_back<<<nblk(B * T * C, 256), 256, 0, st>>>(dm, B, T, C, dx);
+  k_mean_time_back<<<dim3(nblk((int64_t)T * C, 256), (unsigned)B), 256, 0, st>>>(dm, T, C, dx);
   return cudaGetLastError();
 }
 

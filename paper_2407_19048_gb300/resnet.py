@@ -242,7 +242,7 @@ class ResNet1D:
         gwx._check(lib.gwx_maxpool_backward(gwx._ptr(dh), gwx._ptr(arg), B, T1, C0, gwx._ptr(da0), st))
         da0 = self._relu_mask(da0, a0)
         dz0, G["g0"], G["b0"] = self._gn_back(da0, z0, ms0, self.P["g0"])
-        _, G["W0"], _ = gwx.dense_bf16_backward(cols0, self.W16["W0"], None, dz0.reshape(B * T1, C0),
+        _, G["W0"], _ = gwx.dense_bf16_backward(cols0, self.W16["W0"], None, dz0.reshape(B * T1, C0), want_dx=False,
                                                 act=gwx.ACT_NONE)
         return G
 

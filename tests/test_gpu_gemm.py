@@ -120,13 +120,15 @@ def test_gemm_autotune_keeps_results(gwx):
 
 
 @pytest.mark.parametrize("act", [0, 1, 2])
-@pytest.mark.parametrize("M,N,K", [(256, 512, 128), (200, 136, 72)])
+@pytest.mark.parametrize("M,N,K", [(256, 512, 128), (200, 136, 72), (4000, 64, 328), (8192, 256, 256)])
 def test_dense_backward(gwx, act, M, N, K):
     """dX, dW, db against the FP64 chain rule.  Bounds: dZ enters the products rounded to
     bfloat16 (2^-8 relative) after FP32 evaluation (2^-20), its activation derivative is
     taken at the FP32 pre-activation (|act''| <= 0.4 times that error), and each product
     adds its FP32 summation bound; dY is zeroed where ReLU's kink is within reach of
-    the pre-activation error."""
+    the pre-activation error.  The last two shapes have few dW tiles and a long batch, so
+    dW is computed in K slices (13 ragged slices of 5 and 3 K blocks; 32 slices of 4) and
+    summed afterwards."""
     rng = np.random.default_rng(140 + act)
     x = workloads.random_bf16_bits(150 + act, (M, K), exp_lo=-3, exp_hi=0)
     w = workloads.random_bf16_bits(160 + act, (N, K), exp_lo=-3, exp_hi=0)
