@@ -5,7 +5,11 @@
 //     two-slot ring (part 0: V1; parts 1..H/128: pairs of V2's 64-column K-blocks; last
 //     part: V3 padded to 16 rows by the box's zero fill);
 //   - warp 1 issues tcgen05.mma: acc1 = X V1^T, acc2 = g1 V2^T, acc3 = g2 V3^T (FP32 in
-//     tensor memory, columns 0 and 256; acc3 reuses acc1's columns);
+//     tensor memory, columns 0 and 256; acc3 reuses acc1's columns).  The products are cut
+//     into 128-column parts (N) and 128-column rounds of their input (K) so that the
+//     row warps and the tensor core overlap: the rows drain acc1's first part while the
+//     second is computed, acc2's first K round runs while the rows write the second
+//     quarter-pair of g1, and so on;
 //   - warps 2-9 own one draw (row) per thread, two warps per tensor-memory lane quarter:
 //     the first keeps the draw's eight coordinates and its log-scale sum in registers,
 //     writes the conditioning half of the conditioner input X once per layer and applies
@@ -105,7 +109,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
     k_flow_sample_fused(const __grid_constant__ CUtensorMap mv1, const __grid_constant__ CUtensorMap mv2,
                         const __grid_constant__ CUtensorMap mv3, FusedArgs a) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full[2], empty[2], xready, gready, acc1f, acc2f, acc3f;
+  __shared__ __align__(8) uint64_t full[2], empty[2], xready, gready[2], acc1f[2], acc2f[2], acc3f;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -113,8 +117,9 @@ __global__ void __launch_bounds__(F_THREADS, 1)
   const uint32_t sx = base, sg = base + X_BYTES, sw = base + X_BYTES + G_BYTES;
   const int H = a.H, K = a.K, C = a.C;
   const int NP = 2 + H / 128;                              // weight parts per layer
+  const int NR = H / 128;                                  // 128-column parts and rounds
   const int tiles = (int)((a.n + FM - 1) / FM);
-  const uint32_t id_h = idesc_bf16(FM, (uint32_t)H), id_16 = idesc_bf16(FM, 16);
+  const uint32_t id_128 = idesc_bf16(FM, 128), id_16 = idesc_bf16(FM, 16);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < 2; ++s) {
@@ -122,9 +127,11 @@ __global__ void __launch_bounds__(F_THREADS, 1)
       mbar_init(su32(&empty[s]), 1);
     }
     mbar_init(su32(&xready), 8);
-    mbar_init(su32(&gready), 8);
-    mbar_init(su32(&acc1f), 1);
-    mbar_init(su32(&acc2f), 1);
+    for (int r = 0; r < 2; ++r) {
+      mbar_init(su32(&gready[r]), 8);
+      mbar_init(su32(&acc1f[r]), 1);
+      mbar_init(su32(&acc2f[r]), 1);
+    }
     mbar_init(su32(&acc3f), 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -191,45 +198,55 @@ __global__ void __launch_bounds__(F_THREADS, 1)
       for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x)
         for (int l = 0; l < K && ok; ++l, ++li) {
           uint32_t slot;
-          // acc1 = X V1^T (two K-blocks of the input row)
+          // acc1 = X V1^T (two K-blocks of the input row), one 128-column part at a time
           if (!(ok = wait_on(&xready, li & 1u)) || !(ok = take(slot))) break;
           {
             const uint32_t wb = sw + slot * SLOT_BYTES;
-            for (int kb = 0; kb < 2; ++kb)
+            for (int np = 0; np < NR; ++np) {
+              for (int kb = 0; kb < 2; ++kb)
 #pragma unroll
-              for (int kk = 0; kk < 4; ++kk)
-                mma_bf16(tmem, sw128_desc(sx + KB_BYTES * kb + 32u * kk),
-                         sw128_desc(wb + (uint32_t)H * 128u * kb + 32u * kk), id_h, (kb | kk) != 0);
+                for (int kk = 0; kk < 4; ++kk)
+                  mma_bf16(tmem + 128u * np, sw128_desc(sx + KB_BYTES * kb + 32u * kk),
+                           sw128_desc(wb + (uint32_t)H * 128u * kb + 16384u * np + 32u * kk), id_128,
+                           (kb | kk) != 0);
+              mma_commit(su32(&acc1f[np]));
+            }
             mma_commit(su32(&empty[slot]));
             ++it;
-            mma_commit(su32(&acc1f));
           }
-          // acc2 = g1 V2^T
-          if (!(ok = wait_on(&gready, (2 * li) & 1u))) break;
-          for (int p = 1; p < NP - 1 && ok; ++p) {
-            if (!(ok = take(slot))) break;
+          // acc2 = g1 V2^T: K round pr (g1 columns 128 pr .. + 127, weight part pr) once the
+          // rows have written it, both 128-column output parts per round
+          for (int pr = 0; pr < NR && ok; ++pr) {
+            if (!(ok = wait_on(&gready[pr], 0u)) || !(ok = take(slot))) break;
             const uint32_t wb = sw + slot * SLOT_BYTES;
-            for (int kb = 0; kb < 2; ++kb) {
-              const int kg = 2 * (p - 1) + kb;
+            for (int np = 0; np < NR; ++np) {
+              for (int kb = 0; kb < 2; ++kb) {
+                const int kg = 2 * pr + kb;
 #pragma unroll
-              for (int kk = 0; kk < 4; ++kk)
-                mma_bf16(tmem + 256u, sw128_desc(sg + KB_BYTES * kg + 32u * kk),
-                         sw128_desc(wb + (uint32_t)H * 128u * kb + 32u * kk), id_h, (kg | kk) != 0);
+                for (int kk = 0; kk < 4; ++kk)
+                  mma_bf16(tmem + 256u + 128u * np, sw128_desc(sg + KB_BYTES * kg + 32u * kk),
+                           sw128_desc(wb + (uint32_t)H * 128u * kb + 16384u * np + 32u * kk), id_128,
+                           (kg | kk) != 0);
+              }
+              if (pr == NR - 1) mma_commit(su32(&acc2f[np]));
             }
             mma_commit(su32(&empty[slot]));
             ++it;
           }
           if (!ok) break;
-          mma_commit(su32(&acc2f));
-          // acc3 = g2 V3^T (16 rows, 8 of them the conditioner's outputs)
-          if (!(ok = wait_on(&gready, (2 * li + 1) & 1u)) || !(ok = take(slot))) break;
+          // acc3 = g2 V3^T (16 rows, 8 of them the conditioner's outputs), K round by round
+          if (!(ok = take(slot))) break;
           {
             const uint32_t wb = sw + slot * SLOT_BYTES;
-            for (int kb = 0; kb < H / 64; ++kb)
+            for (int r = 0; r < NR && ok; ++r) {
+              if (!(ok = wait_on(&gready[r], 1u))) break;
+              for (int kb = 2 * r; kb < 2 * r + 2; ++kb)
 #pragma unroll
-              for (int kk = 0; kk < 4; ++kk)
-                mma_bf16(tmem, sw128_desc(sg + KB_BYTES * kb + 32u * kk), sw128_desc(wb + 2048u * kb + 32u * kk),
-                         id_16, (kb | kk) != 0);
+                for (int kk = 0; kk < 4; ++kk)
+                  mma_bf16(tmem, sw128_desc(sg + KB_BYTES * kb + 32u * kk), sw128_desc(wb + 2048u * kb + 32u * kk),
+                           id_16, (kb | kk) != 0);
+            }
+            if (!ok) break;
             mma_commit(su32(&empty[slot]));
             ++it;
             mma_commit(su32(&acc3f));
@@ -255,32 +272,30 @@ __global__ void __launch_bounds__(F_THREADS, 1)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       return __all_sync(0xffffffffu, got) && !*(volatile int*)&abort_flag;
     };
-    // bias + ReLU of this warp's half of an H-column accumulator into the activation tile
-    // g, 64 columns (two loads, one wait) at a time
-    auto hidden = [&](uint32_t col0, const float* bias) {
-      for (int c = h * (H / 128); c < (h + 1) * (H / 128); ++c) {   // H / 64 chunks, half each
-        uint32_t raw[2][32];
-        tmem_ld32_async(lane_addr + col0 + 64u * c, raw[0]);
-        tmem_ld32_async(lane_addr + col0 + 64u * c + 32u, raw[1]);
-        tmem_wait_ld();
+    // bias + ReLU of 64 accumulator columns (chunk c: two loads, one wait) into K-block c
+    // of the activation tile g; round rd of a hidden layer is chunk 2 rd + h
+    auto hidden = [&](uint32_t col0, const float* bias, int c) {
+      uint32_t raw[2][32];
+      tmem_ld32_async(lane_addr + col0 + 64u * c, raw[0]);
+      tmem_ld32_async(lane_addr + col0 + 64u * c + 32u, raw[1]);
+      tmem_wait_ld();
 #pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-          const float4* b4 = reinterpret_cast<const float4*>(bias + 64 * c + 32 * hh);
-          uint32_t w[16];
+      for (int hh = 0; hh < 2; ++hh) {
+        const float4* b4 = reinterpret_cast<const float4*>(bias + 64 * c + 32 * hh);
+        uint32_t w[16];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const float4 b = __ldg(b4 + i);
-            w[2 * i] = pack2(fmaxf(__uint_as_float(raw[hh][4 * i]) + b.x, 0.f),
-                             fmaxf(__uint_as_float(raw[hh][4 * i + 1]) + b.y, 0.f));
-            w[2 * i + 1] = pack2(fmaxf(__uint_as_float(raw[hh][4 * i + 2]) + b.z, 0.f),
-                                 fmaxf(__uint_as_float(raw[hh][4 * i + 3]) + b.w, 0.f));
-          }
+        for (int i = 0; i < 8; ++i) {
+          const float4 b = __ldg(b4 + i);
+          w[2 * i] = pack2(fmaxf(__uint_as_float(raw[hh][4 * i]) + b.x, 0.f),
+                           fmaxf(__uint_as_float(raw[hh][4 * i + 1]) + b.y, 0.f));
+          w[2 * i + 1] = pack2(fmaxf(__uint_as_float(raw[hh][4 * i + 2]) + b.z, 0.f),
+                               fmaxf(__uint_as_float(raw[hh][4 * i + 3]) + b.w, 0.f));
+        }
 #pragma unroll
-          for (int t4 = 0; t4 < 4; ++t4) {
-            const int col = 64 * c + 32 * hh + 8 * t4;
-            sts128(sg + KB_BYTES * (col >> 6) + swz(r, (col & 63) >> 3), w[4 * t4], w[4 * t4 + 1], w[4 * t4 + 2],
-                   w[4 * t4 + 3]);
-          }
+        for (int t4 = 0; t4 < 4; ++t4) {
+          const int col = 64 * c + 32 * hh + 8 * t4;
+          sts128(sg + KB_BYTES * (col >> 6) + swz(r, (col & 63) >> 3), w[4 * t4], w[4 * t4 + 1], w[4 * t4 + 2],
+                 w[4 * t4 + 3]);
         }
       }
     };
@@ -325,12 +340,17 @@ __global__ void __launch_bounds__(F_THREADS, 1)
           sts128(sx + swz(r, 0), w0, w1, 0u, 0u);
         }
         arrive(&xready);
-        if (!(ok = wait_on(&acc1f, li & 1u))) break;
-        hidden(0u, a.e1 + l * a.lstride);
-        arrive(&gready);
-        if (!(ok = wait_on(&acc2f, li & 1u))) break;
-        hidden(256u, a.e2 + l * a.lstride);
-        arrive(&gready);
+        for (int rd = 0; rd < NR && ok; ++rd) {
+          if (!(ok = wait_on(&acc1f[rd], li & 1u))) break;
+          hidden(0u, a.e1 + l * a.lstride, 2 * rd + h);
+          arrive(&gready[rd]);
+        }
+        for (int rd = 0; rd < NR && ok; ++rd) {
+          if (!(ok = wait_on(&acc2f[rd], li & 1u))) break;
+          hidden(256u, a.e2 + l * a.lstride, 2 * rd + h);
+          arrive(&gready[rd]);
+        }
+        if (!ok) break;
         if (h != 0) continue;                                  // the coupling step is the first warp's
         if (!(ok = wait_on(&acc3f, li & 1u))) break;
         float o[16];
