@@ -165,6 +165,100 @@ __global__ void __launch_bounds__(256) k_gn_stats(const float* __restrict__ z, i
   }
 }
 
+// Per-sample variants of the two statistics kernels for C / 4 dividing 256: one block of
+// 256 threads reads sample b's whole [T][C] slab with coalesced float4 loads (thread
+// (row lane l, column quad q) reads rows l, l + 256 / (C / 4), ... of channels 4 q ..
+// 4 q + 3), FP32 sums over runs of 16 rows added into FP64; then the row lanes of each
+// column quad and the column quads of each group are added in order.
+__device__ __forceinline__ void sample_group_sums(double a, double q, int cq, int rl, int cg, int G, double* out) {
+  __shared__ double r1[256], r2[256];
+  const int tid = threadIdx.x;
+  r1[tid] = a;
+  r2[tid] = q;
+  __syncthreads();
+  if (tid < cq) {
+    double x = 0.0, y = 0.0;
+    for (int l = 0; l < rl; ++l) {
+      x += r1[l * cq + tid];
+      y += r2[l * cq + tid];
+    }
+    r1[tid] = x;
+    r2[tid] = y;
+  }
+  __syncthreads();
+  if (tid < G) {
+    double x = 0.0, y = 0.0;
+    for (int k = tid * (cg / 4); k < (tid + 1) * (cg / 4); ++k) {
+      x += r1[k];
+      y += r2[k];
+    }
+    out[2 * tid] = x;
+    out[2 * tid + 1] = y;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_gn_stats_s(const float* __restrict__ z, int T, int C, int G,
+                                                    float* __restrict__ ms) {
+  __shared__ double sums[64];
+  const int cq = C / 4, rl = 256 / cq, cg = C / G;
+  const int q4 = threadIdx.x % cq, l0 = threadIdx.x / cq;
+  const float* zb = z + (int64_t)blockIdx.x * T * C;
+  const float k0 = __ldg(zb + ((4 * q4) / cg) * cg);
+  double a = 0.0, q = 0.0;
+  for (int t0 = l0; t0 < T; t0 += 16 * rl) {
+    float s1 = 0.f, s2 = 0.f;
+#pragma unroll 4
+    for (int t = t0; t < min(T, t0 + 16 * rl); t += rl) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(zb + (int64_t)t * C) + q4);
+      const float d0 = v.x - k0, d1 = v.y - k0, d2 = v.z - k0, d3 = v.w - k0;
+      s1 += (d0 + d1) + (d2 + d3);
+      s2 += (d0 * d0 + d1 * d1) + (d2 * d2 + d3 * d3);
+    }
+    a += s1;
+    q += s2;
+  }
+  sample_group_sums(a, q, cq, rl, cg, G, sums);
+  if ((int)threadIdx.x < G) {
+    const int g = threadIdx.x;
+    const double n = (double)T * cg, m = sums[2 * g] / n, var = fmax(sums[2 * g + 1] / n - m * m, 0.0);
+    ms[2 * ((int64_t)blockIdx.x * G + g)] = (float)((double)__ldg(zb + g * cg) + m);
+    ms[2 * ((int64_t)blockIdx.x * G + g) + 1] = (float)(1.0 / sqrt(var + (double)GN_EPS));
+  }
+}
+
+__global__ void __launch_bounds__(256) k_gn_bwd_stats_s(const float* __restrict__ dy, const float* __restrict__ z,
+                                                        int T, int C, int G, const float* __restrict__ ms,
+                                                        const float* __restrict__ gamma, float* __restrict__ mm) {
+  __shared__ double sums[64];
+  const int cq = C / 4, rl = 256 / cq, cg = C / G;
+  const int q4 = threadIdx.x % cq, l0 = threadIdx.x / cq, g = (4 * q4) / cg;
+  const int64_t off = (int64_t)blockIdx.x * T * C;
+  const float mean = ms[2 * ((int64_t)blockIdx.x * G + g)], rstd = ms[2 * ((int64_t)blockIdx.x * G + g) + 1];
+  const float4 gm = make_float4(__ldg(&gamma[4 * q4]), __ldg(&gamma[4 * q4 + 1]), __ldg(&gamma[4 * q4 + 2]),
+                                __ldg(&gamma[4 * q4 + 3]));
+  double a = 0.0, q = 0.0;
+  for (int t0 = l0; t0 < T; t0 += 16 * rl) {
+    float s1 = 0.f, s2 = 0.f;
+#pragma unroll 4
+    for (int t = t0; t < min(T, t0 + 16 * rl); t += rl) {
+      const float4 d = __ldg(reinterpret_cast<const float4*>(dy + off + (int64_t)t * C) + q4);
+      const float4 x = __ldg(reinterpret_cast<const float4*>(z + off + (int64_t)t * C) + q4);
+      const float a0 = d.x * gm.x, a1 = d.y * gm.y, a2 = d.z * gm.z, a3 = d.w * gm.w;
+      s1 += (a0 + a1) + (a2 + a3);
+      s2 += (a0 * ((x.x - mean) * rstd) + a1 * ((x.y - mean) * rstd)) +
+            (a2 * ((x.z - mean) * rstd) + a3 * ((x.w - mean) * rstd));
+    }
+    a += s1;
+    q += s2;
+  }
+  sample_group_sums(a, q, cq, rl, cg, G, sums);
+  if ((int)threadIdx.x < G) {
+    const double n = (double)T * cg;
+    mm[2 * ((int64_t)blockIdx.x * G + threadIdx.x)] = (float)(sums[2 * threadIdx.x] / n);
+    mm[2 * ((int64_t)blockIdx.x * G + threadIdx.x) + 1] = (float)(sums[2 * threadIdx.x + 1] / n);
+  }
+}
+
 // out = act(gamma_c (z - mean) rstd + beta_c + residual), bfloat16 or FP32 out; residual
 // FP32 (res32) or bfloat16 (res16) or none.  VEC consecutive channels per thread.
 template <int VEC>
@@ -440,6 +534,8 @@ __global__ void k_mean_time_back(const float* __restrict__ dm, int T, int C, flo
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+// the per-sample statistics kernels: C / 4 divides 256, at most 32 groups of whole quads
+bool per_sample_ok(int C, int G) { return C % 4 == 0 && 256 % (C / 4) == 0 && (C / G) % 4 == 0 && G <= 32; }
 bool aligned8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
 
 }  // namespace
@@ -484,7 +580,11 @@ cudaError_t launch_group_norm(const float* z, int64_t B, int T, int C, int G, co
                   aligned16(out32);
   const auto r16 = reinterpret_cast<const __nv_bfloat16*>(res16);
   const auto o16 = reinterpret_cast<__nv_bfloat16*>(out16);
-  if (v4) {
+  if (v4 && per_sample_ok(C, G)) {
+    k_gn_stats_s<<<(unsigned)B, 256, 0, st>>>(z, T, C, G, ms);
+    k_gn_apply<4><<<dim3(nblk((int64_t)T * C / 4, 256), (unsigned)B), 256, 0, st>>>(z, T, C, G, ms, gamma, beta, res32,
+                                                                                    r16, relu, o16, out32);
+  } else if (v4) {
     k_gn_stats<4><<<(unsigned)(B * G), 256, 0, st>>>(z, T, C, G, ms);
     k_gn_apply<4><<<dim3(nblk((int64_t)T * C / 4, 256), (unsigned)B), 256, 0, st>>>(z, T, C, G, ms, gamma, beta, res32,
                                                                                     r16, relu, o16, out32);
@@ -507,7 +607,11 @@ cudaError_t launch_group_norm_backward(const float* dy, const float* z, int64_t 
   double* part = reinterpret_cast<double*>(reinterpret_cast<char*>(scratch) +
                                            (((size_t)B * G * 2 * sizeof(float) + 255) & ~(size_t)255));
   const bool v4 = (C / G) % 4 == 0 && aligned16(dy) && aligned16(z) && aligned16(dz);
-  if (v4) {
+  if (v4 && per_sample_ok(C, G)) {
+    k_gn_bwd_stats_s<<<(unsigned)B, 256, 0, st>>>(dy, z, T, C, G, ms, gamma, mm);
+    k_gn_bwd_apply<4><<<dim3(nblk((int64_t)T * C / 4, 256), (unsigned)B), 256, 0, st>>>(dy, z, T, C, G, ms, mm, gamma,
+                                                                                        dz);
+  } else if (v4) {
     k_gn_bwd_stats<4><<<(unsigned)(B * G), 256, 0, st>>>(dy, z, T, C, G, ms, gamma, mm);
     k_gn_bwd_apply<4><<<dim3(nblk((int64_t)T * C / 4, 256), (unsigned)B), 256, 0, st>>>(dy, z, T, C, G, ms, mm, gamma,
                                                                                         dz);
