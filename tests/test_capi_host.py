@@ -133,3 +133,25 @@ def test_flow_layout_and_validation(lib):
     bad = (ctypes.c_double * 8)(*([1.0] * 7 + [0.0]))
     st = lib.gwx_flow_targets(None, 4, m8, bad, None, None)
     assert st == -1 and b"scale" in lib.gwx_last_error()
+
+
+def test_resnet_and_dense_validation(lib):
+    """The ResNet pieces keep one grid row per sample and 32-bit index arithmetic within a
+    sample, so their shapes are bounded on the host; the dense backward's workspace
+    grows with the split-K slices of dW when the batch is long and the output small."""
+    import ctypes
+    st = lib.gwx_group_norm(None, 65536, 8, 64, 8, None, None, None, None, 1, None, None, None, None)
+    assert st == -2 and b"65535" in lib.gwx_last_error()
+    st = lib.gwx_group_norm(None, 2, 1 << 20, 4096, 8, None, None, None, None, 1, None, None, None, None)
+    assert st == -2                                                  # T C = 2^32
+    st = lib.gwx_group_norm(None, 4, 8, 60, 8, None, None, None, None, 1, None, None, None, None)
+    assert st == -2 and b"multiple of G" in lib.gwx_last_error()
+    st = lib.gwx_im2col(None, 2, 1 << 19, 1024, 5, 1, 2, 5120, None, None)   # T_out K >= 2^31
+    assert st == -2 and b"T_out K" in lib.gwx_last_error()
+    st = lib.gwx_col2im(None, 65536, 16, 8, 5, 1, 2, 40, None, None, None)
+    assert st == -2
+    small = lib.gwx_dense_bf16_backward_workspace(512, 64, 320)
+    long_batch = lib.gwx_dense_bf16_backward_workspace(262144, 64, 320)
+    # the dW slices: at most ~128 work items over 2 tiles, 64 x 320 FP32 each
+    assert long_batch >= 262144 * 64 * 4 + 262144 * 320 * 2 + 64 * 64 * 320 * 4
+    assert small < long_batch
