@@ -644,6 +644,13 @@ int gwx_gemm_autotune(const void* A, const void* B, void* C, int64_t M, int64_t 
  * kernel gave up a bounded wait since the last call, else GWX_OK. */
 int gwx_device_status(void);
 
+/* Self-test of that path: launches one thread that waits on an mbarrier nothing arrives
+ * at and gives up after `polls` polls (1 .. 2^20; each poll returns within a bounded,
+ * hardware-defined time), recording the expiry as a kernel whose copies never landed
+ * would.  The next gwx_device_status returns GWX_ETIMEOUT; the context stays usable.
+ * GWX_EINVAL for polls out of range. */
+int gwx_selftest_bounded_wait(uint32_t polls, void* stream);
+
 /* ---- transforms (the FFT kernels of the steps above, exposed for checking) ----
  * gwx_rfft:  X[r] = rfft(x[r]) for R rows of N real samples (numpy convention,
  *            X_k = sum_n x_n e^{-2 pi i k n/N}); X complex[R][N/2+1].

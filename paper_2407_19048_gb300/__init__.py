@@ -26,7 +26,7 @@ __all__ = ["GwxError", "version", "init", "detector_geometry", "sample_prior", "
            "colored_noise", "welch_psd", "inject", "inject_padded", "simulate_batch_padded", "whiten", "unwhiten", "simulate_batch", "log_likelihood",
            "importance_weights", "gemm_bf16", "dense_bf16", "dense_bf16_backward", "gemm_autotune", "spectral_features",
            "cross_features", "lag_features", "proposal_targets",
-           "gauss_nll", "adamw", "adamw_clip", "skymap", "vicreg", "retime", "sample_proposal", "device_status", "rfft", "irfft",
+           "gauss_nll", "adamw", "adamw_clip", "skymap", "vicreg", "retime", "sample_proposal", "device_status", "selftest_bounded_wait", "rfft", "irfft",
            "workspace_bytes", "TAYLORF2", "IMRPHENOMD", "DETECTORS"]
 
 
@@ -531,6 +531,12 @@ def device_status():
     """Raise GwxError(GWX_ETIMEOUT) if a kernel gave up a bounded wait since the last
     call (synchronises the device)."""
     _check(_lib.load().gwx_device_status())
+
+
+def selftest_bounded_wait(polls=256):
+    """Launch a kernel whose bounded wait expires (nothing arrives at its mbarrier); the
+    next device_status() raises GwxError(GWX_ETIMEOUT)."""
+    _check(_lib.load().gwx_selftest_bounded_wait(int(polls), _stream()))
 
 
 def rfft(x, out=None):

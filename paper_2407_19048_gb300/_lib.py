@@ -110,6 +110,7 @@ SIGNATURES = {
                                     c_vp]),
     "gwx_gemm_autotune": (c_int, [c_vp, c_vp, c_vp, c_i64, c_i64, c_i64, c_int, c_vp, c_vp]),
     "gwx_device_status": (c_int, []),
+    "gwx_selftest_bounded_wait": (c_int, [c_u32, c_vp]),
     "gwx_rfft": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp]),
     "gwx_irfft": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp]),
     "gwx_flow_layout": (c_int, [c_shp, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),

@@ -180,6 +180,11 @@ DrawCoef* sim_coef(void* ws, int D, int64_t N) {
 
 int gwx::set_last_error(int status, const char* msg) { return fail(status, "%s", msg); }
 
+namespace gwx {
+// defined in k_gemm.cu, next to the status flag it sets
+cudaError_t launch_selftest_wait(uint32_t polls, cudaStream_t s);
+}  // namespace gwx
+
 extern "C" {
 
 int gwx_version(void) { return 100; }
@@ -636,6 +641,12 @@ int gwx_gemm_bf16(const void* A, const void* B, void* C, int64_t M, int64_t N, i
 int gwx_dense_bf16(const void* X, const void* W, const float* bias, void* Y, int64_t M, int64_t N, int64_t K,
                    int act, int y_dtype, void* stream) {
   return dense_common(X, W, bias, Y, M, N, K, act, y_dtype, stream);
+}
+
+int gwx_selftest_bounded_wait(uint32_t polls, void* stream) {
+  if (polls < 1 || polls > (1u << 20)) return fail(GWX_EINVAL, "polls=%u (1 .. 2^20)", polls);
+  GWX_TRY(ensure_init());
+  return launched(launch_selftest_wait(polls, as_stream(stream)), "selftest_bounded_wait");
 }
 
 int gwx_device_status(void) {

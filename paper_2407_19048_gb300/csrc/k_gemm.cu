@@ -342,6 +342,24 @@ cudaError_t launch_gemm_splitk(const void* A, const void* B, float* C, int64_t M
   return cudaGetLastError();
 }
 
+// Self-test of the bounded waits: one thread waits on an mbarrier that nothing arrives at,
+// gives up after `polls` polls and records the expiry in the status flag the tensor-core
+// kernels use, as they do when their own copies never land.
+__global__ void k_selftest_wait(uint32_t polls) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(su32(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(su32(&bar), 0u, polls)) atomicExch(&g_gemm_status, 1);
+}
+
+cudaError_t launch_selftest_wait(uint32_t polls, cudaStream_t s) {
+  k_selftest_wait<<<1, 32, 0, s>>>(polls);
+  return cudaGetLastError();
+}
+
 cudaError_t gemm_status(int* status) {
   int zero = 0;
   cudaError_t e = cudaDeviceSynchronize();

@@ -151,3 +151,24 @@ def test_dense_backward(gwx, act, M, N, K):
     for got, ref, tol in ((dX, dX_ref, tol_dX), (dW, dW_ref, tol_dW), (db, db_ref, tol_db)):
         err = np.abs(got.cpu().numpy().astype(np.float64) - ref)
         assert np.all(err <= tol * (1.0 + 1e-6) + 1e-30), (float(err.max()), float((err / (tol + 1e-30)).max()))
+
+
+def test_bounded_wait_expiry_is_reported_and_the_context_survives(gwx):
+    """A kernel waiting on an mbarrier that nothing arrives at gives up after its poll
+    limit (the bounded-wait helper every tensor-core kernel uses), records the expiry,
+    and returns: device_status reports GWX_ETIMEOUT once, then OK, and a product run
+    afterwards is still correct."""
+    gwx.device_status()                                   # start from a clean record
+    gwx.selftest_bounded_wait(256)
+    with pytest.raises(gwx.GwxError) as err:
+        gwx.device_status()
+    assert err.value.status == -5
+    gwx.device_status()                                   # the record was cleared
+    M, N, K = 256, 256, 128
+    a = workloads.random_bf16_bits(170, (M, K))
+    b = workloads.random_bf16_bits(171, (N, K))
+    C = gwx.gemm_bf16(_bf16(a), _bf16(b))
+    gwx.device_status()
+    ref = gemm.gemm_nt(a, b)
+    tol = 2.0 * K * 2.0 ** -24 * gemm.abs_product_sum(a, b)
+    assert np.all(np.abs(C.cpu().numpy().astype(np.float64) - ref) <= tol)
