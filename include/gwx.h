@@ -2,7 +2,7 @@
  * gwx.h -- C ABI of libgwx: on-the-fly simulation and pre-processing of
  * compact-binary gravitational-wave training data on one NVIDIA GB300 (sm_103a).
  *
- * The paper (Sec. 3, "Simulations on Accelerated Hardware") generates every
+ * The paper (Sec. 3, simulation on accelerated hardware) generates every
  * training batch on the GPU: prior draws (Table 1), frequency-domain waveforms
  * (Sec. 3.1), projection onto the detectors, injection into background
  * windows cropped from a device-resident chunk, a power spectrum fitted to the
@@ -110,7 +110,7 @@ int         gwx_init(void);                     /* tables for the current device
 int gwx_detector_geometry(int det, double* tensor9, double* position3);
 
 /* ---- A1: prior draws --------------------------------------------------
- * Sec. 3.2 "We generate N points from our parameter prior"; Table 1 shapes.
+ * Sec. 3.2 (each batch draws its parameters from the prior); Table 1 shapes.
  * Draw b uses Philox4x32-10 (Salmon et al., SC'11) with counter
  * (b, j, 1, step), key (seed low word, seed high word), j = 0..5.  Block j
  * yields uniforms u_{2j}, u_{2j+1} from word pairs (0,1), (2,3) as
@@ -164,7 +164,7 @@ int gwx_colored_noise(uint64_t seed, uint32_t step, int D, int64_t L, double fs,
                       float* noise, void* workspace, size_t workspace_bytes, void* stream);
 
 /* ---- A5: Welch PSD --------------------------------------------------------
- * Sec. 3.2 "The power spectra is fit to this background chunk".  One-sided
+ * Sec. 3.2 (the PSD is estimated from the background chunk).  One-sided
  * density, periodic Hann window, mean of K = (L - seg_len)/stride + 1
  * periodograms, no detrending: P_k = c_k/(fs sum w^2) (1/K) sum_s |rfft(w x_s)_k|^2,
  * c_k = 1 at DC and Nyquist, 2 elsewhere.  FP32 FFTs, FP64 squares and sums.
@@ -184,7 +184,7 @@ int gwx_inject(const float* noise, int D, int64_t L, const int64_t* offsets,
                float* d, void* stream);
 
 /* ---- A7: whitening -----------------------------------------------------------
- * Sec. 3.2 "We whiten the batch using the estimated power spectra".
+ * Sec. 3.2 (the batch is whitened with the estimated PSD).
  * y = irfft(rfft(d) M_k / sqrt(S~_k fs/2)), M_k = 1 for ceil(f_lo/df) <= k < N/2,
  * S~ = psd (grid fs/seg_len) linearly interpolated to f_k.
  *   d in float[B][D][N]; psd in double[D][seg_len/2+1]; y out float[B][D][N]
@@ -267,7 +267,7 @@ int gwx_simulate_prepared(const float* noise, int64_t L, const double* psd, int6
                           float* y, int flags, void* workspace, size_t workspace_bytes, void* stream);
 
 /* ---- A8: log-likelihood -------------------------------------------------------
- * Sec. 6 (Fig. 5 caption): the standard GW likelihood.  For sample s of event e
+ * Sec. 6 (Fig. 5 caption): the usual Gaussian-noise GW likelihood.  For sample s of event e
  * (event_offsets[e] <= s < event_offsets[e+1]):
  *   ln L_s = -(1/N) sum_d sum_{ceil(f_lo/df) <= k < N/2} |Y_e,d,k - fs h_d(theta_s, f_k) W_d,k|^2,
  * Y = rfft(y_data) of the whitened data, W = 1/sqrt(S~ fs/2), h_d the TaylorF2

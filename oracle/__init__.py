@@ -7,13 +7,13 @@ of ``bench.py``.  The product path (the ``paper_2407_19048_gb300`` package and
 its CUDA library) never imports, calls or links anything here, and this package
 imports nothing from the product.
 
-The method (Sec. 3, "Simulations on Accelerated Hardware") generates training
+The method (Sec. 3, simulation on accelerated hardware) generates training
 data on the fly: draw parameters from the prior (Table 1), evaluate
 frequency-domain compact-binary waveforms (Sec. 3.1), project them onto the
 detectors, inject them into background strain, estimate the background power
 spectrum and whiten the batch (Sec. 3.2).  The plain likelihood used by the
-paper's nested-sampling comparison (Sec. 6, Fig. 5 caption: "the standard GW
-likelihood") is the sixth piece, and importance weights built on it the seventh.
+paper's nested-sampling comparison (Sec. 6, Fig. 5 caption: the usual
+Gaussian-noise GW likelihood) is the sixth piece, and importance weights built on it the seventh.
 
 Modules, in pipeline order:
 

@@ -1,8 +1,8 @@
 """Detector geometry, antenna patterns, delays and projection (oracle; test infrastructure).
 
 Sec. 3.2 trains on Hanford and Livingston (HL) strain; the three-detector
-workload adds Virgo.  Sec. 6 notes that "Signal projection ... performs this
-operation on-the-fly on the GPU" for the extrinsic parameters (ra, dec, psi).
+workload adds Virgo.  Sec. 6 notes that the projection onto the detectors is done
+on the fly on the GPU, for the extrinsic parameters (ra, dec, psi).
 The projection implemented here is the textbook long-wavelength response:
 
     h_d(f) = (F+_d h_plus(f) + Fx_d h_cross(f)) exp(-2 pi i f (tc + dt_d))

@@ -1,7 +1,7 @@
 """Noise-weighted inner product, log-likelihood and mismatch (oracle; test infrastructure).
 
-Sec. 6 (Fig. 5 caption) compares with nested sampling using "the standard GW
-likelihood": Gaussian stationary noise with one-sided PSD S gives
+Sec. 6 (Fig. 5 caption) compares with nested sampling under the usual GW
+likelihood: Gaussian stationary noise with one-sided PSD S gives
 
     <a, b> = 4 df Re sum_k a~_k conj(b~_k) / S_k,     ln L = -1/2 <d - h, d - h>
 

@@ -1,11 +1,10 @@
 """Welch PSD, PSD interpolation, injection and whitening (oracle; test infrastructure).
 
-Sec. 3.2: "The power spectra is fit to this background chunk", N background
-crops of the window length are taken from the chunk, the signals are injected
-and the batch is whitened with the estimated spectrum; "all data
-pre-processing, like fourier transforms, power spectra estimation, data
-whitening, are carried out on the GPU".  The paper gives no formulas; these are
-the textbook definitions, with the readings listed per function.
+Sec. 3.2: the PSD is estimated from a background chunk, N crops of the window
+length are taken from that chunk, the signals are injected into them and the batch
+is whitened with the estimated spectrum, with the transforms, the spectral estimate
+and the whitening all run on the accelerator.  The paper gives no formulas; these
+are the textbook definitions, with the readings listed per function.
 
 Welch (P. D. Welch 1967), one-sided density, mean of K periodograms:
     P_k = c_k / (fs sum_n w_n^2) (1/K) sum_s |sum_n w_n x_{s*stride+n} e^{-2 pi i k n/M}|^2

@@ -1,8 +1,8 @@
 """TaylorF2 frequency-domain inspiral waveform (oracle; test infrastructure).
 
-Sec. 3.1: the paper's IMRPhenomD starts from the inspiral phase "up to 3.5
-post-Newtonian order in GW phase (known as TaylorF2; see Buonanno et al. 2009
-for a review)".  This module evaluates that TaylorF2 model directly from its
+Sec. 3.1: the paper's IMRPhenomD builds on the inspiral phase to 3.5
+post-Newtonian order, the TaylorF2 model (reviewed by Buonanno et al. 2009).  This
+module evaluates that TaylorF2 model directly from its
 definition, bin by bin, in float64:
 
     h(f)  = A(f) exp(-i Psi(f))
