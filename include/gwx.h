@@ -221,15 +221,17 @@ int gwx_unwhiten(const float* y, const double* psd, int64_t seg_len, double fs, 
  * point; it exists for those callers only.
  *
  * The whitening filter is kept in a file-scope device array of the library that
- * holds at most GWX_MAX_DET x 8193 floats (128 KiB), so D x (N/2 + 1) must not
- * exceed 4 x 8193; larger requests return GWX_ESHAPE.  Every GPU that loads the
+ * holds at most GWX_MAX_DET x 8193 floats (128 KiB): the largest filter that
+ * gwx_whiten's own limits allow (D <= GWX_MAX_DET, N a power of two <= 16384), so
+ * a request beyond it fails those checks with GWX_ESHAPE.  Every GPU that loads the
  * library holds that array until the process exits.  The call allocates nothing.
  * The first call on a device looks up the array's device address on that device
  * (and prepares the library's tables as gwx_init does), so that first call should
  * happen before any stream capture.  All calls share the one array, and each call
  * overwrites it completely before reading it: calls that overlap in time on the
  * GPU (different streams, or different host threads) race on it and must be
- * serialised by the caller.  Arguments and errors as gwx_whiten. */
+ * serialised by the caller.  Arguments, checks, statuses and messages as gwx_whiten
+ * (without the workspace); the output is bit-identical to gwx_whiten's. */
 int gwx_whiten_static(const float* d, const double* psd, int64_t seg_len, double fs, double f_lo,
                       int64_t B, int D, int64_t N, float* y, void* stream);
 

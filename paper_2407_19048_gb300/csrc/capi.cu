@@ -180,6 +180,30 @@ DrawCoef* sim_coef(void* ws, int D, int64_t N) {
 
 int gwx::set_last_error(int status, const char* msg) { return fail(status, "%s", msg); }
 
+// Argument checks shared by gwx_whiten, gwx_unwhiten and gwx_whiten_static (everything
+// but the workspace); *k_lo receives the first band bin.  B == 0 passes with the
+// arrays unchecked.
+int gwx::whiten_check_args(const float* d, const double* psd, int64_t seg_len, double fs, double f_lo, int64_t B,
+                           int D, int64_t N, const float* y, int* k_lo) {
+  GWX_TRY(check_window(N));
+  GWX_TRY(check_psd_args(seg_len, N));
+  if (D < 1 || D > GWX_MAX_DET) return fail(GWX_ESHAPE, "D=%d", D);
+  if (B < 0 || B * D > 0x7fffffffLL) return fail(GWX_ESHAPE, "B=%lld", (long long)B);
+  if (!(fs > 0.0)) return fail(GWX_EINVAL, "fs must be positive");
+  GWX_TRY(band_start(f_lo, fs / (double)N, N / 2, k_lo));
+  if (B == 0) return GWX_OK;
+  if (!d || !psd || !y) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN8(d);
+  GWX_ALIGN8(psd);
+  GWX_ALIGN8(y);
+  return GWX_OK;
+}
+
+int gwx::init_device() { return ensure_init(); }
+
+int gwx::launch_status(cudaError_t e, const char* what) { return launched(e, what); }
+
+
 namespace gwx {
 // defined in k_gemm.cu, next to the status flag it sets
 cudaError_t launch_selftest_wait(uint32_t polls, cudaStream_t s);
@@ -347,18 +371,9 @@ size_t gwx_whiten_workspace(int D, int64_t N) {
 
 static int whiten_common(bool inverse, const float* d, const double* psd, int64_t seg_len, double fs, double f_lo, int64_t B, int D,
                int64_t N, float* y, void* workspace, size_t workspace_bytes, void* stream) {
-  GWX_TRY(check_window(N));
-  GWX_TRY(check_psd_args(seg_len, N));
-  if (D < 1 || D > GWX_MAX_DET) return fail(GWX_ESHAPE, "D=%d", D);
-  if (B < 0 || B * D > 0x7fffffffLL) return fail(GWX_ESHAPE, "B=%lld", (long long)B);
-  if (!(fs > 0.0)) return fail(GWX_EINVAL, "fs must be positive");
   int k_lo = 0;
-  GWX_TRY(band_start(f_lo, fs / (double)N, N / 2, &k_lo));
+  GWX_TRY(whiten_check_args(d, psd, seg_len, fs, f_lo, B, D, N, y, &k_lo));
   if (B == 0) return GWX_OK;
-  if (!d || !psd || !y) return fail(GWX_EINVAL, "NULL array");
-  GWX_ALIGN8(d);
-  GWX_ALIGN8(psd);
-  GWX_ALIGN8(y);
   GWX_TRY(check_ws(workspace, workspace_bytes, gwx_whiten_workspace(D, N)));
   GWX_TRY(ensure_init());
   float* W = reinterpret_cast<float*>(workspace);

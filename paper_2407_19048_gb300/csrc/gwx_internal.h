@@ -212,6 +212,16 @@ cudaError_t launch_mean_time_back(const float* dm, int64_t B, int T, int C, floa
 // Record msg as the calling thread's gwx_last_error() message; returns status.
 int set_last_error(int status, const char* msg);
 
+// The argument checks of gwx_whiten (sizes, band, NULL and alignment of d, psd, y;
+// everything but the workspace), with gwx_whiten's statuses and messages; *k_lo gets
+// the first band bin.
+int whiten_check_args(const float* d, const double* psd, int64_t seg_len, double fs, double f_lo, int64_t B, int D,
+                      int64_t N, const float* y, int* k_lo);
+// gwx_init's per-device set-up; on failure the message names the failing step.
+int init_device();
+// GWX_OK for cudaSuccess, else GWX_ECUDA with "what: <CUDA error name> (<string>)".
+int launch_status(cudaError_t e, const char* what);
+
 // per-translation-unit table set-up on the current device
 cudaError_t init_tables_random();
 cudaError_t init_tables_spectral();

@@ -155,3 +155,27 @@ def test_resnet_and_dense_validation(lib):
     # the dW slices: at most ~128 work items over 2 tiles, 64 x 320 FP32 each
     assert long_batch >= 262144 * 64 * 4 + 262144 * 320 * 2 + 64 * 64 * 320 * 4
     assert small < long_batch
+
+
+def test_static_whitening_checks_as_gwx_whiten(lib):
+    """gwx_whiten_static runs gwx_whiten's own argument checks (before any device work):
+    the same statuses and messages for a non-finite sample rate, a band start above the
+    last bin, a bad window and too many detectors."""
+    import ctypes
+    ws = ctypes.c_void_p(0x10000)
+    cases = [
+        (4096, float("inf"), 20.0, 1, 3, 8192),      # fs = +inf: df = inf
+        (4096, 2048.0, float("inf"), 1, 3, 8192),    # f_lo = +inf
+        (4096, 2048.0, 2000.0, 1, 3, 8192),          # band starts above the last usable bin
+        (4096, 2048.0, 20.0, 1, 3, 8000),            # window not a power of two
+        (4096, 2048.0, 20.0, 1, 5, 8192),            # more detectors than GWX_MAX_DET
+        (4095, 2048.0, 20.0, 1, 3, 8192),            # Welch segment not a power of two
+    ]
+    for seg_len, fs, f_lo, B, D, N in cases:
+        st_ref = lib.gwx_whiten(None, None, seg_len, fs, f_lo, B, D, N, None, ws, 1 << 20, None)
+        msg_ref = lib.gwx_last_error()
+        st = lib.gwx_whiten_static(None, None, seg_len, fs, f_lo, B, D, N, None, None)
+        assert st == st_ref and st < 0, (seg_len, fs, f_lo, D, N, st, st_ref)
+        assert lib.gwx_last_error() == msg_ref
+    st = lib.gwx_whiten_static(None, None, 4096, float("inf"), 20.0, 1, 3, 8192, None, None)
+    assert st == -1 and b"must be positive" in lib.gwx_last_error()
