@@ -113,3 +113,106 @@ def test_ragged_events_and_empty_events():
     one = likelihood.log_likelihood(y[1:2], psd, wl["seg_len"], wl["fs"], wl["f_lo"], samples[:, :4],
                                     np.array([0, 4]), wl["dets"])
     np.testing.assert_allclose(lnl[:4], one, rtol=1e-14)
+
+
+# ---------------------------------------------------------------- merger-time marginal
+def _noisy_case(E=2, S_per=3, seed=21):
+    wl = workloads.workload("small")
+    th, h, d, psd = _events(wl, E, seed)
+    y = spectral.whiten(d, psd, wl["seg_len"], wl["fs"], wl["f_lo"])
+    samples = workloads.random_theta(seed + 1, E * S_per, wl["prior"])
+    # half of the samples near their event's source, so that the grid sum has a sharp peak
+    for e in range(E):
+        samples[:, e * S_per] = th[:, e]
+        samples[C.DIST, e * S_per] *= 1.1
+    offs = np.arange(E + 1) * S_per
+    return wl, th, y, psd, samples, offs
+
+
+def test_tmarg_is_the_log_mean_exp_of_the_likelihood_on_the_grid():
+    """Brute force: ln L at every grid time from log_likelihood (tc in the parameter
+    vector), then ln of their mean -- no phase-rotation identity involved."""
+    wl, th, y, psd, samples, offs = _noisy_case()
+    fs = wl["fs"]
+    tc_lo, n_tc, u = 1.1, 6, 2
+    got = likelihood.log_likelihood_tmarg(y, psd, wl["seg_len"], fs, wl["f_lo"], samples, offs, wl["dets"],
+                                          tc_lo, n_tc, u)
+    grid = []
+    for j in range(u * n_tc):
+        s = samples.copy()
+        s[C.TC] = tc_lo + j / (u * fs)
+        grid.append(likelihood.log_likelihood(y, psd, wl["seg_len"], fs, wl["f_lo"], s, offs, wl["dets"]))
+    grid = np.array(grid)
+    mx = grid.max(axis=0)
+    ref = mx + np.log(np.mean(np.exp(grid - mx), axis=0))
+    np.testing.assert_allclose(got, ref, rtol=1e-11, atol=1e-9)
+    # the tc row of theta is not used
+    s2 = samples.copy()
+    s2[C.TC] = 123.0
+    np.testing.assert_array_equal(
+        likelihood.log_likelihood_tmarg(y, psd, wl["seg_len"], fs, wl["f_lo"], s2, offs, wl["dets"], tc_lo, n_tc, u),
+        got)
+
+
+def test_tmarg_single_grid_point_and_silent_template():
+    wl, th, y, psd, samples, offs = _noisy_case(seed=31)
+    fs = wl["fs"]
+    one = likelihood.log_likelihood_tmarg(y, psd, wl["seg_len"], fs, wl["f_lo"], samples, offs, wl["dets"],
+                                          1.3, 1, 1)
+    s = samples.copy()
+    s[C.TC] = 1.3
+    ref = likelihood.log_likelihood(y, psd, wl["seg_len"], fs, wl["f_lo"], s, offs, wl["dets"])
+    np.testing.assert_allclose(one, ref, rtol=1e-12)
+    # a template of vanishing amplitude: every grid point gives -|Y|^2 / N
+    far = samples.copy()
+    far[C.DIST] = 1e30
+    got = likelihood.log_likelihood_tmarg(y, psd, wl["seg_len"], fs, wl["f_lo"], far, offs, wl["dets"], 1.0, 512, 16)
+    k_lo = math.ceil(wl["f_lo"] * wl["N"] / fs)
+    Y = np.fft.rfft(y, axis=-1)[..., k_lo:wl["N"] // 2]
+    yy = np.sum(np.abs(Y) ** 2, axis=(1, 2)) / wl["N"]
+    np.testing.assert_allclose(got, -np.repeat(yy, 3), rtol=1e-12)
+
+
+def test_tmarg_invariant_under_a_circular_shift_of_data_and_window():
+    """Shifting the data by s samples (circularly) and the window by s / fs leaves the
+    marginal unchanged: fixes the sign and scale of the time in the phase rotation."""
+    wl, th, y, psd, samples, offs = _noisy_case(seed=41)
+    fs = wl["fs"]
+    a = likelihood.log_likelihood_tmarg(y, psd, wl["seg_len"], fs, wl["f_lo"], samples, offs, wl["dets"],
+                                        1.0, 64, 4)
+    for sh in (37, -200):
+        b = likelihood.log_likelihood_tmarg(np.roll(y, sh, axis=-1), psd, wl["seg_len"], fs, wl["f_lo"], samples,
+                                            offs, wl["dets"], 1.0 + sh / fs, 64, 4)
+        np.testing.assert_allclose(b, a, rtol=1e-11, atol=1e-8)
+
+
+def test_tmarg_laplace_limit_of_a_loud_noise_free_signal():
+    """Noise-free data, template at the truth, merger well inside the window: for a loud
+    signal the grid sum tends to the Gaussian integral of the merger-time peak,
+    ln L_m -> ln( sqrt(2 pi) sigma / (n_tc / fs) ), 1 / sigma^2 = (2 pi)^2 <f h, f h>
+    (second-order expansion of <h(t) - h(t*), h(t) - h(t*)> about the truth)."""
+    wl = workloads.workload("small")
+    N, fs = wl["N"], wl["fs"]
+    df = fs / N
+    dets = wl["dets"]
+    th = np.zeros((C.P, 1))
+    th[C.M1], th[C.M2], th[C.DIST], th[C.TC] = 14.0, 11.0, 100.0, 1.2468
+    th[C.THETAJN], th[C.PSI], th[C.RA], th[C.DEC], th[C.PHIC] = 0.4, 0.3, 1.1, 0.2, 0.7
+    hp, hc = taylorf2.generate_waveforms(th, wl["f_lo"], df, N // 2 + 1)
+    h = detector.project(hp, hc, th, dets, 0.0, df)
+    d = spectral.inject(np.zeros((len(dets), N)), np.array([0]), h, N, fs)
+    f = np.arange(wl["seg_len"] // 2 + 1) * fs / wl["seg_len"]
+    psd = np.tile(noise.noise_psd(f, wl["f_lo"]), (len(dets), 1))
+    y = spectral.whiten(d, psd, wl["seg_len"], fs, wl["f_lo"])
+    S = spectral.interp_psd(psd, wl["seg_len"], N)
+    k_lo = math.ceil(wl["f_lo"] / df)
+    fk = np.arange(N // 2 + 1) * df
+    rho2 = np.sum(likelihood.inner_product(h[0], h[0], S, df, k_lo, N // 2))
+    ff = np.sum(likelihood.inner_product(fk * h[0], fk * h[0], S, df, k_lo, N // 2))
+    assert rho2 > 150.0 ** 2                       # loud: the expansion's error is O(1 / rho^2)
+    sigma = 1.0 / (2.0 * math.pi * math.sqrt(ff))
+    n_tc, u = 64, 128                              # window [1.22, 1.2825) s, grid 7.6 us < sigma
+    ref = math.log(math.sqrt(2.0 * math.pi) * sigma / (n_tc / fs))
+    got = likelihood.log_likelihood_tmarg(y, psd, wl["seg_len"], fs, wl["f_lo"], th, np.array([0, 1]), dets,
+                                          1.22, n_tc, u)[0]
+    assert abs(got - ref) < 1e-4, (got, ref)
