@@ -1,24 +1,26 @@
 #!/usr/bin/env python3
 """Benchmark: whitened injections per second of the on-the-fly simulation path.
 
-One step is one batch of the method's per-batch pass (Sec. 3.2) on the
-three-detector workload: prior draws and the FP64 per-draw set-up (prepared one
-batch ahead on a side stream), and ``simulate_prepared`` (TaylorF2 waveforms,
-projection, crops, injection, whitening) for B draws, through the libgwx C ABI.
-The background (a fresh coloured-noise stretch and its Welch PSD) is regenerated
-inside the timed loop every ``--background-every`` steps (default 16; the paper
-keeps one background chunk for many batches); the line also reports the rate with
-a fresh background every step.  Further legs: end to end through pinned host
-memory, the log-likelihood with importance weights on ragged events, and the FFT
-kernels against cuFFT.
+One step is one batch of the method's per-batch pass (Sec. 3.2) on the long-window
+three-detector workload (H1+L1+V1, 2048 Hz, 8 s windows, N = 16384, 8192 draws per
+step): prior draws and the FP64 per-draw set-up (prepared one batch ahead on a side
+stream), and ``simulate_prepared`` (TaylorF2 waveforms, projection, crops, injection,
+whitening) for B draws, through the libgwx C ABI.  The background (a fresh
+coloured-noise stretch and its Welch PSD) is regenerated inside the timed loop every
+``--background-every`` steps (default 16; the paper keeps one background chunk for
+many batches); the line also reports the rate with a fresh background every step.
+Further legs: end to end through pinned host memory, the same step on the 4 s
+geometry (``hl3``), the log-likelihood with importance weights on ragged events, the
+learned part, and the FFT kernels against cuFFT.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gwx|reference]
 
 Timing: W untimed steps, then K steps, each bracketed by CUDA events on the
-launching stream, with a 256 MiB buffer written between steps (L2 flush, outside
-the events); barrier + synchronize before and after; max over ranks.  Under
-torchrun each rank is an independent replica on its own GPU with its own step
-counters (weak scaling, no data-path collective).  Rank 0 prints one JSON line.
+launching stream, with a 256 MiB buffer written between steps (outside the events;
+the 1.6 GB output of a step exceeds L2 anyway); barrier + synchronize before and
+after; max over ranks.  Under torchrun each rank is an independent replica on its
+own GPU with its own step counters (weak scaling, no data-path collective).  Rank 0
+prints one JSON line.
 """
 import argparse
 import hashlib
@@ -36,15 +38,18 @@ sys.path.insert(0, ROOT)
 
 import workloads  # noqa: E402
 
-WORKLOAD = "hl3"
+WORKLOAD = "sweep"
 STEP_STRIDE = 1 << 20            # per-rank offset of the step counters
-FP32_LANES_PER_SM = 128
-N_SM = 152
-SM_MAX_MHZ = 2070.0
-# ncu DRAM traffic (read + write bytes) of one k_simulate launch on the hl3
-# workload and the hash of the kernel sources it was measured on; see
-# profiles/k_simulate_hl3.md.  None until a capture matches the current sources.
-TRAFFIC = {"bytes_per_launch": 141901824, "sources_sha1": "1b9391f046273340b9eb878050a8e715843fc7c2"}
+FP32_LANES_PER_SM = 128          # FP32 FMA lanes per Blackwell SM
+SM_MAX_MHZ_FALLBACK = 2070.0
+# ncu DRAM traffic (read + write bytes) per k_simulate launch, in steady state (the
+# launch after another, caches not flushed, so the write-back of the previous launch's
+# dirty lines is counted and this launch's own L2-resident tail is not), keyed by
+# workload, with the hash of the kernel sources it was measured on.  A workload whose
+# capture does not match the current sources reports null.
+TRAFFIC = {"sweep": {"bytes_per_launch": 8 * 205540096, "B": 8192, "sources_sha1": "480874119f647970a5ea20b2692205f0c18944c7",
+                    "note": "ncu on 1024 draws of the same geometry (205.54 MB in steady state), scaled by the "
+                            "draws per launch"}}
 
 
 def _measured_peaks():
@@ -77,10 +82,47 @@ def flops_per_injection(wl):
 
 def kernel_sources_sha1():
     h = hashlib.sha1()
-    for f in ("k_fused.cu", "fft16.cuh", "common.cuh", "waveform.cuh", "gwx_internal.h"):
+    for f in ("k_fused.cu", "fft16.cuh", "common.cuh", "waveform.cuh"):
         with open(os.path.join(ROOT, "paper_2407_19048_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
+
+
+def fp32_peak(torch, sm_mhz):
+    """FP32 peak of this GPU in TFLOP/s at the given SM clock: the SM count reported by
+    the device (cudaGetDeviceProperties) x 128 FMA lanes per SM x 2 flops."""
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    n_sm = int(props.multi_processor_count)
+    return n_sm, n_sm * FP32_LANES_PER_SM * 2 * float(sm_mhz) * 1e6 / 1e12
+
+
+def sm_max_mhz(clk):
+    """Maximum SM clock: nvidia-smi's clocks.max.sm sampled during the run, else the
+    measured figure, else the part's nominal maximum."""
+    if clk and clk.get("sm_max_mhz"):
+        return float(clk["sm_max_mhz"]), "nvidia-smi clocks.max.sm"
+    if MEASURED_PEAKS.get("sm_max_mhz"):
+        return float(MEASURED_PEAKS["sm_max_mhz"]), "MEASURED_PEAKS.json sm_max_mhz"
+    return SM_MAX_MHZ_FALLBACK, "nominal maximum"
+
+
+def traffic_per_launch(wl):
+    t = TRAFFIC.get(wl["name"])
+    if t and t["sources_sha1"] == kernel_sources_sha1() and t["B"] == wl["B"]:
+        return t["bytes_per_launch"]
+    return None
+
+
+def bench_config(wl, args, world):
+    """The `config` object of the JSON line; both arms print the same one."""
+    return {"workload": describe(wl), "global_batch": wl["B"] * world, "seq_len": wl["N"],
+            "parallelism": "replicas: one per GPU with disjoint Philox counters, no data-path collective",
+            "l2": "outputs (%.2f GB per step) exceed L2; a 256 MiB buffer is also written between timed steps, "
+                  "outside the events" % (wl["B"] * len(wl["dets"]) * wl["N"] * 4 / 1e9),
+            "step": "prior draws + FP64 per-draw set-up of the next batch, and the fused pass (waveforms, "
+                    "projection, crops, injection, whitening) of this batch; background (coloured noise + Welch "
+                    "PSD) regenerated every %d steps" % args.background_every,
+            "background_every": args.background_every}
 
 
 def step_counter(rank, i):
@@ -199,41 +241,41 @@ def oracle_rate(wl, min_seconds=10.0, draws_per_worker=8, background_every=1, co
 
 
 def run_reference(args, wl):
+    """The oracle arm: each step is a bounded sample of the workload, timed whole.  A
+    step is b = draws_per_core x cores draws of the batch: the oracle's prior for them
+    (on the main process), then waveform, projection, injection and whitening spread
+    over one spawned process per host core, with a fresh background (noise + Welch)
+    in every process every --background-every steps, as in the GPU arm.  value = draws
+    timed / seconds timed; ms_per_step is the measured time of the b-draw step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     cores = os.cpu_count() or 1
-    per = 8
+    per = max(1, args.reference_draws_per_core)
     b = per * cores
     R = max(1, args.background_every)
     from oracle import prior
-    vals, times = [], []
+    times = []
     with _oracle_pool(cores) as ex:
         list(ex.map(_oracle_slice, [(wl, 0, 0, 0, 1)] * cores))          # start-up
         for i in range(args.warmup + args.steps):
             t0 = time.perf_counter()
-            prior.sample_prior(wl["prior"], wl["param_seed"], i, wl["B"], wl["L"], wl["N"])
-            t_prior = time.perf_counter() - t0
-            t1 = time.perf_counter()
+            prior.sample_prior(wl["prior"], wl["param_seed"], i, b, wl["L"], wl["N"])
             list(ex.map(_oracle_slice, [(wl, (i // R) * R, i, (k * per) % (wl["B"] - per + 1), per)
                                         for k in range(cores)]))
-            t_b = time.perf_counter() - t1
+            dt = time.perf_counter() - t0
             if i >= args.warmup:
-                t_step = t_prior + wl["B"] / b * t_b
-                vals.append(wl["B"] / t_step)
-                times.append(t_step)
-    value = len(vals) * wl["B"] / sum(times)
-    sample = ("each step: the oracle prior for %d draws on the main process, then %d of the draws (waveform, "
-              "projection, injection, whitening; a fresh background with its Welch PSD every %d steps, as in the "
-              "GPU arm) spread over %d spawned processes, one per host core; step time extrapolated as "
-              "t_prior + (B/b) t_parallel" % (wl["B"], b, R, cores))
+                times.append(dt)
+    value = len(times) * b / sum(times)
+    sample = ("each step: %d of the %d draws of a batch, all timed: the oracle prior for them on the main process, "
+              "then waveform, projection, injection and whitening in %d spawned processes (one per host core, %d "
+              "draws each), with a fresh background and its Welch PSD in every process every %d steps (those steps "
+              "include it)" % (b, wl["B"], cores, per, R))
     line = {"impl": "reference", "metric": "whitened injections/sec", "value": value, "unit": "injections/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded coloured aLIGO-fit noise)",
-            "config": {"workload": describe(wl), "global_batch": wl["B"], "seq_len": wl["N"],
-                       "parallelism": "host processes on rank 0 (the reference arm runs on rank 0 only)",
-                       "background_every": R},
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded coloured aLIGO-fit noise, Philox prior draws)",
+            "config": bench_config(wl, args, 1),
             "cpu_baseline": {"value": value, "unit": "injections/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "injections/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -475,32 +517,71 @@ def padded_leg(gwx, torch, rank, B=2048, N_pad=8192, reps=20):
     return out
 
 
-def sweep_leg(gwx, torch, rank, steps=40, warmup=3):
-    """Throughput at the long-window geometry (H1+L1+V1, 2048 Hz, 8 s windows, N = 16384,
-    8192 draws per step: 1.61 GB of whitened strain per step, larger than L2, so no flush
-    is needed): the same pipelined simulator step as the headline, background every 16
-    steps, with the fused call's share timed on its own for the roofline."""
-    wl = workloads.workload("sweep")
-    sim = gwx.simulator.Simulator(wl, pipeline=True, background_every=16)
-    for i in range(warmup):
-        sim.step(step_counter(rank, 70000 + i))
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+def timed_steps(torch, sm, flush, rank, first, count, clocks=None, dist=None):
+    """Run `count` simulator steps from counter `first`, each bracketed by CUDA events on
+    the launching stream with the L2 flush before the first event; returns (per-step ms,
+    per-step ms of the fused call from after the wait for the side-stream preparation,
+    wall seconds, kernels launched)."""
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(count)]
     torch.cuda.synchronize()
-    for i in range(steps):
+    if dist is not None:
+        dist.barrier()
+    if clocks is not None:
+        clocks.start()
+    l0 = sm.launches
+    t0 = time.perf_counter()
+    for i in range(count):
+        flush.zero_()
         ev[i][0].record()
-        sim.step(step_counter(rank, 70000 + warmup + i), mark=ev[i][1])
-        torch.cuda.current_stream().wait_stream(sim.side)
+        sm.step(step_counter(rank, first + i), mark=ev[i][1])
+        # the step ends when its fused pass and the next batch's preparation (side
+        # stream) are both done, so no work of the step runs during the L2 flush
+        torch.cuda.current_stream().wait_stream(sm.side)
         ev[i][2].record()
     torch.cuda.synchronize()
-    step_ms = statistics.mean(e[0].elapsed_time(e[2]) for e in ev)
-    sim_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
+    wall = time.perf_counter() - t0
+    if dist is not None:
+        dist.barrier()
+    return ([e[0].elapsed_time(e[2]) for e in ev], [e[1].elapsed_time(e[2]) for e in ev], wall,
+            sm.launches - l0)
+
+
+def roofline_alu(torch, wl, sim_ms_mean, clk):
+    """Roofline object of the fused call: algorithmic FP32 flops per launch / its mean
+    CUDA-event duration, against the FP32 peak of this GPU (SM count from the device,
+    maximum SM clock), with the fraction at the sampled median clock beside it."""
     B, D, N = wl["B"], len(wl["dets"]), wl["N"]
-    peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    tflops = flops_per_injection(wl) * B / (sim_ms * 1e-3) / 1e12
+    mhz, mhz_src = sm_max_mhz(clk)
+    n_sm, peak = fp32_peak(torch, mhz)
+    achieved = flops_per_injection(wl) * B / (sim_ms_mean * 1e-3) / 1e12
+    out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+           "traffic": traffic_per_launch(wl),
+           "kernel": "simulate_prepared call (k_whiten_filter, k_packed_filter, k_simulate), timed from after the "
+                     "wait for the side-stream preparation",
+           "flops_per_injection": flops_per_injection(wl), "injections_per_launch": B,
+           "algorithmic_bytes_per_launch": B * D * N * 4,
+           "peak_basis": "%d SMs (cudaGetDeviceProperties) x %d FP32 lanes x 2 flop x %.0f MHz (%s); derived, not "
+                         "measured" % (n_sm, FP32_LANES_PER_SM, mhz, mhz_src),
+           "sm_count": n_sm, "avg_launch_ms": sim_ms_mean,
+           "hbm_gbs_output_only": B * D * N * 4 / (sim_ms_mean * 1e-3) / 1e9}
+    if clk and clk.get("sm_mhz"):
+        out["frac_at_sampled_sm_clock"] = achieved / fp32_peak(torch, clk["sm_mhz"])[1]
+    return out
+
+
+def hl3_leg(gwx, torch, rank, args, flush, steps=200):
+    """The same pipelined step on the four-second, three-detector geometry (H1+L1+V1,
+    2048 Hz, N = 8192, 2048 draws per step; 201 MB of output, so the 256 MiB flush
+    between steps matters), background every --background-every steps."""
+    wl = workloads.workload("hl3")
+    sim = gwx.simulator.Simulator(wl, pipeline=True, background_every=args.background_every)
+    for i in range(args.warmup):
+        sim.step(step_counter(rank, 80000 + i))
+    step_ms, sim_ms, _, _ = timed_steps(torch, sim, flush, rank, 80000 + args.warmup, steps)
     del sim
-    return {"workload": describe(wl), "steps": steps, "ms_per_step": step_ms, "injections_per_s": B / (step_ms * 1e-3),
-            "simulate_prepared_ms": sim_ms, "flops_per_injection": flops_per_injection(wl), "tflops": tflops,
-            "frac_of_fp32_peak": tflops / peak, "hbm_gbs_output_only": B * D * N * 4 / (sim_ms * 1e-3) / 1e9}
+    ms = statistics.mean(step_ms)
+    return {"workload": describe(wl), "steps": steps, "ms_per_step": ms, "injections_per_s": wl["B"] / (ms * 1e-3),
+            "roofline": roofline_alu(torch, wl, statistics.mean(sim_ms), None)}
 
 
 def flow_resnet_leg(gwx, torch, rank, steps=1500, batch=512, events=32, per_event=4000):
@@ -799,6 +880,7 @@ def run_gpu(args, wl):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dd = dist if world > 1 else None
     import paper_2407_19048_gb300 as gwx
     import paper_2407_19048_gb300.simulator  # noqa: F401
     gwx.init()
@@ -806,38 +888,12 @@ def run_gpu(args, wl):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     B, D, N, L = wl["B"], len(wl["dets"]), wl["N"], wl["L"]
 
-    def timed_steps(sm, first, count, clocks=None):
-        """Run `count` steps from counter `first`; returns (per-step ms, fused-call ms,
-        wall seconds, launches)."""
-        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(count)]
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-        if clocks is not None:
-            clocks.start()
-        l0 = sm.launches
-        t0 = time.perf_counter()
-        for i in range(count):
-            flush.zero_()
-            ev[i][0].record()
-            sm.step(step_counter(rank, first + i), mark=ev[i][1])
-            # the step ends when its fused pass and the next batch's preparation (side
-            # stream) are both done, so no work of the step runs during the L2 flush
-            torch.cuda.current_stream().wait_stream(sm.side)
-            ev[i][2].record()
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        if world > 1:
-            dist.barrier()
-        return ([e[0].elapsed_time(e[2]) for e in ev], [e[1].elapsed_time(e[2]) for e in ev], wall,
-                sm.launches - l0)
-
     for i in range(args.warmup):
         sim.step(step_counter(rank, i))
     clocks = ClockSampler(local)
-    step_ms, sim_ms, t_wall, launches = timed_steps(sim, args.warmup, args.steps, clocks)
+    step_ms, sim_ms, t_wall, launches = timed_steps(torch, sim, flush, rank, args.warmup, args.steps, clocks, dd)
     clk = clocks.stop()
-    total_s = max_over_ranks(sum(step_ms) * 1e-3, dist if world > 1 else None)
+    total_s = max_over_ranks(sum(step_ms) * 1e-3, dd)
     value = world * B * args.steps / total_s
 
     if args.only_step:
@@ -855,19 +911,20 @@ def run_gpu(args, wl):
     n1 = min(args.steps, 500)
     for i in range(args.warmup):
         sim1.step(step_counter(rank, args.warmup + args.steps + i))
-    ms1, _, _, _ = timed_steps(sim1, 2 * args.warmup + args.steps, n1)
-    value_bg1 = world * B * n1 / max_over_ranks(sum(ms1) * 1e-3, dist if world > 1 else None)
+    ms1, _, _, _ = timed_steps(torch, sim1, flush, rank, 2 * args.warmup + args.steps, n1)
+    value_bg1 = world * B * n1 / max_over_ranks(sum(ms1) * 1e-3, dd)
     del sim1
 
     # end to end: background strain from pinned host memory in, products out to pinned
     # host memory.  Batch i's whitened output leaves on a copy stream while batch i + 1
     # is computed (two output buffers in the pipelined simulator); the parameters and
-    # offsets (200 KB) are read back on the launching stream.
+    # offsets are read back on the launching stream.
     host_bg = torch.empty((D, L), dtype=torch.float32, pin_memory=True)
     host_bg.copy_(sim.noise)
     host_y = [torch.empty((B, D, N), dtype=torch.float32, pin_memory=True) for _ in range(2)]
     host_th = torch.empty((11, B), dtype=torch.float64, pin_memory=True)
     host_off = torch.empty(B, dtype=torch.int64, pin_memory=True)
+    del sim
     sim_e2e = gwx.simulator.Simulator(wl, noise_on_device=False, pipeline=True, background_every=1)
     copy_stream = torch.cuda.Stream()
     ev_ready = torch.cuda.Event()
@@ -902,24 +959,26 @@ def run_gpu(args, wl):
     e2e_steps(args.warmup + 100, n_e2e)
     b.record()
     b.synchronize()
-    e2e_s = max_over_ranks(a.elapsed_time(b) * 1e-3, dist if world > 1 else None)
+    e2e_s = max_over_ranks(a.elapsed_time(b) * 1e-3, dd)
     e2e_value = world * B * n_e2e / e2e_s
+    del sim_e2e, host_y
 
-    ll = loglike_leg(gwx, torch, wl, rank)
-    fft_cmp = cufft_leg(gwx, torch, sim, wl, statistics.mean(sim_ms))
+    hl3 = hl3_leg(gwx, torch, rank, args, flush)
+    wl_hl3 = workloads.workload("hl3")
+    sim_h = gwx.simulator.Simulator(wl_hl3, pipeline=True, background_every=args.background_every)
+    for i in range(3):
+        sim_h.step(step_counter(rank, 85000 + i))
+    ll = loglike_leg(gwx, torch, wl_hl3, rank)
+    fft_cmp = cufft_leg(gwx, torch, sim_h, wl_hl3, hl3["roofline"]["avg_launch_ms"])
+    del sim_h
     serve = serving_leg(gwx, torch, rank)
     gemm = gemm_leg(gwx, torch)
     learned = learned_leg(gwx, torch, rank)
     flow = flow_leg(gwx, torch, rank)
     flow_resnet = flow_resnet_leg(gwx, torch, rank)
     padded = padded_leg(gwx, torch, rank)
-    sweep = sweep_leg(gwx, torch, rank)
 
-    sim_avg_s = statistics.mean(sim_ms) * 1e-3
-    flops = flops_per_injection(wl) * B
-    achieved = flops / sim_avg_s / 1e12
-    peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["sources_sha1"] == kernel_sources_sha1() else None
+    roof = roofline_alu(torch, wl, statistics.mean(sim_ms), clk)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -934,22 +993,8 @@ def run_gpu(args, wl):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded coloured aLIGO-fit noise, Philox prior draws)",
-            "config": {"workload": describe(wl), "global_batch": B * world, "seq_len": N,
-                       "parallelism": "%d independent replica(s), one per GPU, disjoint Philox counters" % world,
-                       "l2": "256 MiB buffer written between timed steps (outside the events)",
-                       "step": "prepare_batch of the next batch on a side stream + simulate_prepared; background "
-                               "(colored_noise + welch_psd) regenerated every %d steps inside the timed loop"
-                               % args.background_every,
-                       "background_every": args.background_every},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "simulate_prepared call (k_whiten_filter, k_packed_filter, k_simulate), timed "
-                                   "from after the wait for the side-stream preparation",
-                         "flops_per_injection": flops_per_injection(wl),
-                         "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (recipe unit counts and "
-                                       "maximum SM clock)",
-                         "avg_launch_ms": sim_avg_s * 1e3,
-                         "hbm_gbs_output_only": B * D * N * 4 / sim_avg_s / 1e9},
+            "config": bench_config(wl, args, world),
+            "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "injections/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
@@ -960,6 +1005,7 @@ def run_gpu(args, wl):
             "gpu_launches": launches,
             "value_background_every_step": value_bg1,
             "clocks": clk,
+            "hl3": hl3,
             "log_likelihood": ll,
             "fft_vs_cufft": fft_cmp,
             "serving": serve,
@@ -968,7 +1014,6 @@ def run_gpu(args, wl):
             "flow": flow,
             "flow_resnet": flow_resnet,
             "padded_grid": padded,
-            "long_windows": sweep,
             "wall_s_timed_region": t_wall,
         }
         print(json.dumps(line), flush=True)
@@ -985,6 +1030,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="gwx", choices=["gwx", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workloads.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--reference-draws-per-core", type=int, default=8,
+                    help="draws per host core in each step of the oracle arm")
     ap.add_argument("--background-every", type=int, default=16,
                     help="regenerate the background and its PSD every this many steps")
     ap.add_argument("--batch", type=int, default=None, help="draws per step (default: the workload's)")

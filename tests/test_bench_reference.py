@@ -26,7 +26,11 @@ def _run(argv, env=None):
 
 
 def test_reference_arm_prints_the_contract_line():
-    rc, out = _run(["--impl", "reference", "--steps", "3", "--warmup", "3", "--workload", "small"])
+    import time
+    t0 = time.perf_counter()
+    rc, out = _run(["--impl", "reference", "--steps", "3", "--warmup", "3", "--workload", "small",
+                    "--reference-draws-per-core", "2"])
+    wall = time.perf_counter() - t0
     assert rc == 0
     line = json.loads(out.strip().splitlines()[-1])
     assert line["impl"] == "reference"
@@ -39,6 +43,12 @@ def test_reference_arm_prints_the_contract_line():
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
     assert line["config"]["global_batch"] == 64 and line["config"]["seq_len"] == 2048
+    # every draw the line reports was timed: the steps' time fits in the run's own wall time
+    assert line["steps"] * line["ms_per_step"] * 1e-3 <= wall
+    # the same config object as the GPU arm prints
+    import argparse
+    import workloads
+    assert line["config"] == bench.bench_config(workloads.workload("small"), argparse.Namespace(background_every=16), 1)
 
 
 def test_reference_arm_is_silent_on_other_ranks():
