@@ -413,76 +413,6 @@ def gemm_leg(gwx, torch, shape=(8192, 8192, 8192)):
                          "peak_basis": "measured bf16 burst (MEASURED_PEAKS.json)"}}
 
 
-def learned_leg(gwx, torch, rank, steps=2000, events=32, per_event=4000):
-    """The first learned proposal: a dense network (tcgen05 layers) trained with AdamW on
-    512-draw batches of the two-detector workload, mapping spectral features to a
-    Gaussian over chirp mass, total mass and distance; then importance sampling of 32
-    events with 4000 samples each, against the prior as proposal (spins and merger time
-    known; with and without the angles known)."""
-    import numpy as np
-    import paper_2407_19048_gb300.simulator  # noqa: F401
-    from paper_2407_19048_gb300.proposal import LearnedProposal
-    wl = workloads.workload("small", B=512)
-    sim = gwx.simulator.Simulator(wl, pipeline=True, background_every=16)
-    net = LearnedProposal(wl)
-    losses = []
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for i in range(steps):
-        y, th, _ = sim.step(step_counter(rank, 20000 + i))
-        loss = net.train_step(y, th)
-        if i in (0, steps // 4, steps // 2, steps - 1):
-            losses.append((i, loss))
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
-    losses = [(i, float(l.item())) for i, l in losses]
-    wl_ev = dict(workloads.workload("small", B=events), param_seed=777)
-    sim_ev = gwx.simulator.Simulator(wl_ev)
-    y_ev, th_ev, _ = sim_ev.step(step_counter(rank, 0))
-    y_ev, th_ev = y_ev.clone(), th_ev.clone()
-    offs = torch.arange(events + 1, dtype=torch.int64, device="cuda") * per_event
-    res = {}
-    for fix in (False, True):
-        for learned in (False, True):
-            best = None
-            for rep in range(3):
-                torch.cuda.synchronize()
-                a = time.perf_counter()
-                theta, lrat = net.proposal_samples(y_ev, th_ev, offs, seed=5, counter=rep, learned=learned,
-                                                   fix_angles=fix)
-                lnl = gwx.log_likelihood(y_ev, sim_ev.psd, wl_ev["seg_len"], wl_ev["fs"], wl_ev["f_lo"],
-                                         wl_ev["dets"], 0.0, theta, offs)
-                _, ess, eff, _ = gwx.importance_weights(lnl, offs, lrat)
-                e = float(ess.sum().item())
-                dt = time.perf_counter() - a
-                best = dt if best is None else min(best, dt)
-            key = ("learned" if learned else "prior") + ("_angles_known" if fix else "")
-            res[key] = {"ess_total": e, "ess_median": float(ess.median().item()),
-                        "efficiency_median": float(eff.median().item()), "ess_per_s": e / best}
-    # calibration: the truth's CDF under each event's Gaussian (PP test) on 512 fresh draws
-    wl_pp = dict(workloads.workload("small", B=512), param_seed=778)
-    sim_pp = gwx.simulator.Simulator(wl_pp)
-    y_pp, th_pp, _ = sim_pp.step(step_counter(rank, 1))
-    out = net.net_out(y_pp).cpu().numpy().astype(np.float64)
-    t = gwx.proposal_targets(th_pp, net.mean, net.scale).cpu().numpy().astype(np.float64)
-    z = (t - out[:, :3]) / np.exp(out[:, 3:6])
-    import math
-    cdf = 0.5 * (1.0 + np.vectorize(math.erf)(z / math.sqrt(2.0)))
-    ks = []
-    for p in range(3):
-        u = np.sort(cdf[:, p])
-        n = len(u)
-        ks.append(float(max(np.max(np.arange(1, n + 1) / n - u), np.max(u - np.arange(n) / n))))
-    del sim, sim_ev, sim_pp
-    return {"train_steps": steps, "batch": 512, "train_s": train_s, "loss": losses, "events": events,
-            "samples_per_event": per_event, "importance_sampling": res,
-            "pp_test": {"draws": 512, "z_rms": [float(v) for v in np.sqrt((z ** 2).mean(axis=0))],
-                        "ks_distance": ks, "ks_95pct_critical": 1.36 / math.sqrt(512),
-                        "params": ["chirp mass", "total mass", "distance"]},
-            "note": "Gaussian over (Mc, M, D) from log spectral powers, two GELU layers of 512; spins and "
-                    "merger time known in both proposals"}
-
-
 def padded_leg(gwx, torch, rank, B=2048, N_pad=8192, reps=20):
     """Definition B (padded-grid waveforms: generate and project on an N_pad-point grid,
     inverse-transform the padded segment, inject its first N samples, whiten; five libgwx
@@ -584,14 +514,15 @@ def hl3_leg(gwx, torch, rank, args, flush, steps=200):
             "roofline": roofline_alu(torch, wl, statistics.mean(sim_ms), None)}
 
 
-def flow_resnet_leg(gwx, torch, rank, steps=1500, batch=512, events=32, per_event=4000):
+def flow_resnet_leg(gwx, torch, rank, steps=1500, batch=512, events=64):
     """The flow with the paper's ResNet-1D data summary (stem, (5, 3, 3) residual blocks of
     64 / 128 / 256 channels, group norm, kernel 5; convolutions on the tensor cores) in
     place of the spectral-feature network, trained jointly with AdamW on 512-draw batches
-    of the two-detector workload; importance sampling as in the flow leg."""
+    of the non-spinning two-detector workload; importance sampling of config 4's events
+    as in the flow leg."""
     import paper_2407_19048_gb300.simulator  # noqa: F401
     from paper_2407_19048_gb300.flow import FlowPosterior
-    wl = workloads.workload("small", B=batch)
+    wl = workloads.workload("small_nonspinning", B=batch)
     sim = gwx.simulator.Simulator(wl, pipeline=True, background_every=16)
     fp = FlowPosterior(wl, layers=16, hidden=256, context=64, seed=0, lr=3e-4, weight_decay=2e-3,
                        embedding="resnet")
@@ -607,89 +538,106 @@ def flow_resnet_leg(gwx, torch, rank, steps=1500, batch=512, events=32, per_even
             losses.append((i, loss.clone()))
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
-    wl_ev = dict(workloads.workload("small", B=events), param_seed=777)
+    wl_ev = dict(workloads.workload("small_nonspinning", B=events), param_seed=777)
     sim_ev = gwx.simulator.Simulator(wl_ev)
-    y_ev, th_ev, _ = sim_ev.step(step_counter(rank, 0))
-    y_ev, th_ev = y_ev.clone(), th_ev.clone()
-    offs = torch.arange(events + 1, dtype=torch.int64, device="cuda") * per_event
-    best, e = None, None
-    for rep in range(3):
-        torch.cuda.synchronize()
-        a = time.perf_counter()
-        theta, _, lrat = fp.sample(y_ev, th_ev, offs, 5, rep)
-        lnl = gwx.log_likelihood(y_ev, sim_ev.psd, wl_ev["seg_len"], wl_ev["fs"], wl_ev["f_lo"], wl_ev["dets"], 0.0,
-                                 theta, offs)
-        _, ess, eff, _ = gwx.importance_weights(lnl, offs, lrat)
-        e = float(ess.sum().item())
-        dt = time.perf_counter() - a
-        best = dt if best is None else min(best, dt)
+    y_ev, _, _ = sim_ev.step(step_counter(rank, 0))
+    y_ev = y_ev.clone()
+    isamp = is_compare(gwx, torch, fp, wl_ev, y_ev, sim_ev.psd, workloads.ragged_counts(4, events, 2000, 50000),
+                       workloads.tc_grid(wl_ev))
     del sim, sim_ev
     return {"summary": "ResNet-1D", "resnet_params": sum(p.numel() for _, p, _ in fp.resnet.tensors()),
             "train_steps": steps, "batch": batch, "train_s": train_s, "step_ms": 1e3 * train_s / steps,
-            "loss": [(i, float(l.item())) for i, l in losses],
-            "importance_sampling": {"ess_total": e, "ess_median": float(ess.median().item()),
-                                    "efficiency_median": float(eff.median().item()), "ess_per_s": e / best,
-                                    "chain_ms": best * 1e3}}
+            "loss": [(i, float(l.item())) for i, l in losses], "importance_sampling": isamp}
 
 
-def flow_leg(gwx, torch, rank, steps=12000, events=32, per_event=4000, pp_events=200, pp_samples=500, lr=6e-4,
-             cross=True, batch=4096, layers=16, hidden=256, clip=1.0, pretrain_steps=2000):
-    """The conditional coupling flow (16 affine coupling layers, conditioners 72 -> 256 ->
-    256 -> 8; embedding 1968 -> 512 -> 512 -> 64 on log group powers, inter-detector cross
-    spectra and lag-one spectral products; tcgen05 dense layers) trained with AdamW (lr
-    6e-4, weight decay 2e-3, gradient norm clipped at 1) on 4096-draw batches of the
-    two-detector workload, 12000 steps = 49.2 M simulations (one CUDA-graph replay of the
-    C-ABI training call per step), after 2000 steps of VICReg pre-training of the data
-    summary on pairs of views that differ only in merger time; then
-    posterior sampling (20,000 draws of one event, the paper's inference size), importance
-    sampling of 32 events x 4000 draws against the prior as proposal (spins and merger
-    time known to both), and a PP test of the flow's marginals."""
+def is_compare(gwx, torch, fp, wl, y_ev, psd, counts, grid, seed=5, reps=3):
+    """Importance sampling of events y_ev [E][D][N] with counts[e] draws each, from the
+    prior and from the flow, every draw scored by the likelihood with the merger time
+    integrated out over `grid` and weighted (ln w = ln L + ln prior - ln q).  Device
+    time (CUDA events) of draws + ln L + weights, best of `reps`; per-event ESS and
+    efficiency with their medians."""
+    import numpy as np
+    offs = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    S = int(offs[-1])
+    offs_d = torch.from_numpy(offs).cuda()
+    tc_lo, n_tc, u = grid
+    out = {}
+    for arm in ("prior", "flow"):
+        best, keep = None, None
+        for rep in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            if arm == "flow":
+                theta, _, lrat = fp.sample(y_ev, offs_d, seed, rep, S=S)
+            else:
+                theta, _ = gwx.sample_prior(wl["prior"], seed, rep, S, wl["L"], wl["N"])
+                lrat = None
+            lnl = gwx.log_likelihood_tmarg(y_ev, psd, wl["seg_len"], wl["fs"], wl["f_lo"], wl["dets"], 0.0, tc_lo,
+                                           n_tc, u, theta, offs_d)
+            _, ess, eff, _ = gwx.importance_weights(lnl, offs_d, lrat)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            if best is None or ms < best:
+                best, keep = ms, (ess.cpu().numpy(), eff.cpu().numpy())
+        ess, eff = keep
+        out[arm] = {"ess_total": float(ess.sum()), "ess_median": float(np.median(ess)),
+                    "efficiency_median": float(np.median(eff)), "chain_ms": best,
+                    "ess_per_s": float(ess.sum()) / (best * 1e-3),
+                    "ess_per_event": [round(float(v), 3) for v in ess]}
+    pe, fe = np.array(out["prior"]["ess_per_event"]), np.array(out["flow"]["ess_per_event"])
+    out["per_event_ess_ratio_median"] = float(np.median(fe / np.maximum(pe, 1e-300)))
+    out["events_flow_ahead"] = int(np.sum(fe > pe))
+    out["samples"] = S
+    out["events"] = len(counts)
+    out["likelihood"] = ("gwx_log_likelihood_tmarg: merger time integrated out over [%g, %g) s on a %g us grid"
+                         % (tc_lo, tc_lo + n_tc / wl["fs"], 1e6 / (u * wl["fs"])))
+    return out
+
+
+def flow_leg(gwx, torch, rank, steps=12000, events=64, pp_events=200, pp_samples=500, lr=1e-3, batch=4096,
+             layers=16, hidden=256, clip=1.0):
+    """The learned part (config 3) and its importance-sampling judge (config 4).
+
+    The conditional coupling flow (16 affine coupling layers, conditioners 72 -> 256 ->
+    256 -> 8; embedding 1968 -> 512 -> 512 -> 64 on log group powers, inter-detector
+    cross spectra and lag-one spectral products; tcgen05 dense layers) is trained with
+    AdamW (lr 1e-3, weight decay 2e-3, gradient norm clipped at 1) on batches of the
+    non-spinning two-detector workload, one CUDA-graph replay of the C-ABI training
+    call per step, with the schedule of Sec. 5: epochs of 160,000 simulations, the
+    learning rate divided by 10 after 10 epochs without a better validation loss, stop
+    after 50 (or at the step budget), best epoch restored.  Then: 20,000 posterior draws
+    of one event (the paper's inference size); importance sampling of 64 events with
+    U{2000..50000} draws each from the flow and from the prior, every draw scored by the
+    likelihood with the merger time integrated out (the flow does not model it; spins
+    are zero in the model and the events); a PP test of the flow's marginals; a
+    streaming loop of 1000 events; sky maps."""
     import math
     import numpy as np
     import paper_2407_19048_gb300.simulator  # noqa: F401
     from paper_2407_19048_gb300.flow import FlowPosterior
-    wl = workloads.workload("small", B=batch)
+    wl = workloads.workload("small_nonspinning", B=batch)
+    grid = workloads.tc_grid(wl)
     sim = gwx.simulator.Simulator(wl, pipeline=True, background_every=16)
     fp = FlowPosterior(wl, layers=layers, hidden=hidden, context=64, embed_hidden=512, group=4, seed=0, lr=lr,
-                       weight_decay=2e-3, cross=cross, clip=clip)
-    pre = None
-    if pretrain_steps:
-        from paper_2407_19048_gb300.pretrain import VICRegPretrainer
-        pt = VICRegPretrainer(fp, batch=1024)
-        torch.cuda.synchronize()
-        a0 = time.perf_counter()
-        vl = []
-        for k in range(pretrain_steps):
-            loss_v, terms_v = pt.step(step_counter(rank, 70000 + k))
-            if k % max(1, pretrain_steps // 4) == 0 or k == pretrain_steps - 1:
-                vl.append((k, loss_v.clone(), terms_v.clone()))
-        torch.cuda.synchronize()
-        pre = {"steps": pretrain_steps, "pairs_per_step": 1024, "seconds": time.perf_counter() - a0,
-               "vicreg": [(k, float(l.item()), [float(t) for t in tt.cpu()]) for k, l, tt in vl]}
-        del pt
-    losses = []
-    # the training step runs as a CUDA graph per simulator buffer set (the pipelined
-    # simulator alternates two), captured once before the timing
-    graphs = {}
-    for i in range(2):
-        y, th, _ = sim.step(step_counter(rank, 40000 + i))
-        graphs[y.data_ptr()] = fp.capture_train_step(y, th)
+                       weight_decay=2e-3, clip=clip)
+    # fixed validation set: 4 x 4096 simulations from counters no training batch uses
+    sim_v = gwx.simulator.Simulator(dict(wl, B=16384, param_seed=911))
+    yv, thv, _ = sim_v.step(step_counter(rank, 7))
+    yv, thv = yv.clone(), thv.clone()
+    del sim_v
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for i in range(steps):
-        y, th, _ = sim.step(step_counter(rank, 40002 + i))
-        graphs[y.data_ptr()].replay()
-        fp.note_replay()
-        if i % max(1, steps // 12) == 0 or i == steps - 1:
-            losses.append((i, fp._loss.clone()))
+    hist = fp.fit(sim, steps, step_counter(rank, 40000), (yv, thv))
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
-    del graphs
-    losses = [(i, float(l.item())) for i, l in losses]
-    # training step alone (no simulation) on one resident batch
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    y1, th1 = y.clone(), th.clone()
+    del yv, thv
+    # training step alone (no simulation) on one resident batch, eager and as a graph replay
+    y1, th1, _ = sim.step(step_counter(rank, 39999))
+    y1, th1 = y1.clone(), th1.clone()
     fp_t = FlowPosterior(wl, layers=layers, hidden=hidden, context=64, embed_hidden=512, group=4, seed=1)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(3):
         fp_t.train_step(y1, th1)
     ev0.record()
@@ -698,7 +646,6 @@ def flow_leg(gwx, torch, rank, steps=12000, events=32, per_event=4000, pp_events
     ev1.record()
     torch.cuda.synchronize()
     step_ms = ev0.elapsed_time(ev1) / 50
-    # the same step captured once in a CUDA graph and replayed
     graph = fp_t.capture_train_step(y1, th1)
     for _ in range(3):
         graph.replay()
@@ -708,34 +655,34 @@ def flow_leg(gwx, torch, rank, steps=12000, events=32, per_event=4000, pp_events
     ev1.record()
     torch.cuda.synchronize()
     step_graph_ms = ev0.elapsed_time(ev1) / 50
-    del graph
-    # posterior sampling latency: 20,000 draws for one event
-    wl_ev = dict(workloads.workload("small", B=events), param_seed=777)
+    del graph, fp_t, y1, th1
+    # events: config 4's 64 events of the same generator (other parameter seed)
+    wl_ev = dict(workloads.workload("small_nonspinning", B=events), param_seed=777)
     sim_ev = gwx.simulator.Simulator(wl_ev)
     y_ev, th_ev, _ = sim_ev.step(step_counter(rank, 0))
     y_ev, th_ev = y_ev.clone(), th_ev.clone()
+    # posterior sampling latency: 20,000 draws for one event
     one = torch.tensor([0, 20000], dtype=torch.int64, device="cuda")
     lat = []
+    y1 = y_ev[:1].contiguous()
     for rep in range(23):
         torch.cuda.synchronize()
         a = time.perf_counter()
-        fp.sample(y_ev[:1].contiguous(), th_ev[:, :1].contiguous(), one, 11, rep)
+        fp.sample(y1, one, 11, rep, S=20000)
         torch.cuda.synchronize()
         if rep >= 3:
             lat.append(time.perf_counter() - a)
     lat.sort()
-    # sky maps: 20,000 draws + likelihood + weights + HEALPix map (the paper: ~0.6 / 1.2 / 2.4 s
-    # for 20k samples and a map at NSIDE 32 / 64 / 128 on an A40)
+    # sky maps: 20,000 draws + marginal likelihood + weights + HEALPix map
     sky = {}
-    y1, t1 = y_ev[:1].contiguous(), th_ev[:, :1].contiguous()
     for nside in (32, 64, 128):
         times = []
         for rep in range(13):
             torch.cuda.synchronize()
             a0 = time.perf_counter()
-            theta1, _, lr1 = fp.sample(y1, t1, one, 17, rep)
-            lnl1 = gwx.log_likelihood(y1, sim_ev.psd, wl_ev["seg_len"], wl_ev["fs"], wl_ev["f_lo"], wl_ev["dets"],
-                                      0.0, theta1, one)
+            theta1, _, lr1 = fp.sample(y1, one, 17, rep, S=20000)
+            lnl1 = gwx.log_likelihood_tmarg(y1, sim_ev.psd, wl_ev["seg_len"], wl_ev["fs"], wl_ev["f_lo"],
+                                            wl_ev["dets"], 0.0, *grid, theta1, one)
             w1, _, _, _ = gwx.importance_weights(lnl1, one, lr1)
             gwx.skymap(theta1, nside, weights=w1)
             torch.cuda.synchronize()
@@ -743,62 +690,42 @@ def flow_leg(gwx, torch, rank, steps=12000, events=32, per_event=4000, pp_events
                 times.append(time.perf_counter() - a0)
         times.sort()
         sky[str(nside)] = times[len(times) // 2] * 1e3
-    # importance sampling: flow vs prior, same events and likelihood
-    offs = torch.arange(events + 1, dtype=torch.int64, device="cuda") * per_event
-    res = {}
-    for learned in (False, True):
-        best = None
-        for rep in range(3):
-            torch.cuda.synchronize()
-            a = time.perf_counter()
-            if learned:
-                theta, _, lrat = fp.sample(y_ev, th_ev, offs, 5, rep)
-            else:
-                theta, lrat = gwx.sample_proposal(wl_ev["prior"], th_ev, offs, 5, rep)
-            lnl = gwx.log_likelihood(y_ev, sim_ev.psd, wl_ev["seg_len"], wl_ev["fs"], wl_ev["f_lo"], wl_ev["dets"],
-                                     0.0, theta, offs)
-            _, ess, eff, _ = gwx.importance_weights(lnl, offs, lrat)
-            e = float(ess.sum().item())
-            dt = time.perf_counter() - a
-            best = dt if best is None else min(best, dt)
-        res["flow" if learned else "prior"] = {"ess_total": e, "ess_median": float(ess.median().item()),
-                                               "efficiency_median": float(eff.median().item()),
-                                               "ess_per_s": e / best, "chain_ms": best * 1e3}
+    # config 4: importance sampling, flow vs prior, 64 events x U{2000..50000} draws
+    counts = workloads.ragged_counts(4, events, 2000, 50000)
+    isamp = is_compare(gwx, torch, fp, wl_ev, y_ev, sim_ev.psd, counts, grid)
     # PP test: percentile of each truth among its event's flow draws, per flow coordinate
-    wl_pp = dict(workloads.workload("small", B=pp_events), param_seed=779)
+    wl_pp = dict(workloads.workload("small_nonspinning", B=pp_events), param_seed=779)
     sim_pp = gwx.simulator.Simulator(wl_pp)
     y_pp, th_pp, _ = sim_pp.step(step_counter(rank, 2))
     offs_pp = torch.arange(pp_events + 1, dtype=torch.int64, device="cuda") * pp_samples
-    theta_s, _, lr_s = fp.sample(y_pp, th_pp, offs_pp, 13, 0)
+    theta_s, _, lr_s = fp.sample(y_pp, offs_pp, 13, 0, S=pp_events * pp_samples)
     xs = gwx.flow_targets(theta_s, fp.mean, fp.scale).cpu().numpy().reshape(pp_events, pp_samples, 8)
     ok = np.isfinite(lr_s.cpu().numpy()).reshape(pp_events, pp_samples)
     xt = gwx.flow_targets(th_pp, fp.mean, fp.scale).cpu().numpy()
     ks = []
     for p in range(8):
         pct = np.array([np.mean(xs[e, ok[e], p] < xt[e, p]) if ok[e].any() else 0.5 for e in range(pp_events)])
-        u = np.sort(pct)
-        n = len(u)
-        ks.append(float(max(np.max(np.arange(1, n + 1) / n - u), np.max(u - np.arange(n) / n))))
+        uu = np.sort(pct)
+        n = len(uu)
+        ks.append(float(max(np.max(np.arange(1, n + 1) / n - uu), np.max(uu - np.arange(n) / n))))
     # streaming: 1000 events of U{2000..50000} draws, one at a time, flow vs prior proposal
-    import numpy as np
     from paper_2407_19048_gb300.scorer import Scorer
     n_srv = 1000
-    wl_srv = dict(workloads.workload("small", B=n_srv), param_seed=780)
+    wl_srv = dict(workloads.workload("small_nonspinning", B=n_srv), param_seed=780)
     sim_srv = gwx.simulator.Simulator(wl_srv)
-    y_srv, th_srv, _ = sim_srv.step(step_counter(rank, 3))
-    counts = workloads.ragged_counts(6 + rank, n_srv, 2000, 50000)
+    y_srv, _, _ = sim_srv.step(step_counter(rank, 3))
+    counts_srv = workloads.ragged_counts(6 + rank, n_srv, 2000, 50000)
     serving = {}
     for name, flow in (("prior", None), ("flow", fp)):
-        sc = Scorer(wl_srv, int(counts.max()), sim_srv.psd, flow=flow)
-        truth = [th_srv[:, e:e + 1].contiguous() for e in range(n_srv)]
+        sc = Scorer(wl_srv, int(counts_srv.max()), sim_srv.psd, flow=flow, tmarg=grid)
         for e in range(5):
-            sc.score(y_srv[e:e + 1], int(counts[e]), e, truth=truth[e])
+            sc.score(y_srv[e:e + 1], int(counts_srv[e]), e)
         torch.cuda.synchronize()
         lat_srv, ess = [], []
         t0 = time.perf_counter()
         for e in range(n_srv):
             a = time.perf_counter()
-            ess.append(sc.score(y_srv[e:e + 1], int(counts[e]), e, truth=truth[e])[0])
+            ess.append(sc.score(y_srv[e:e + 1], int(counts_srv[e]), e)[0])
             lat_srv.append(time.perf_counter() - a)
         wall = time.perf_counter() - t0
         lat_ms = np.array(lat_srv) * 1e3
@@ -807,21 +734,21 @@ def flow_leg(gwx, torch, rank, steps=12000, events=32, per_event=4000, pp_events
                          "ess_median": float(np.median(ess)), "ess_per_s": float(np.sum(ess)) / wall}
         del sc
     del sim, sim_ev, sim_pp, sim_srv
-    return {"shape": fp.shape, "params": fp.n_params, "train_steps": steps, "batch": batch, "train_s": train_s,
-            "simulations_per_s": steps * batch / train_s, "train_step_ms": step_ms,
-            "train_step_graph_ms": step_graph_ms, "loss": losses, "vicreg_pretraining": pre,
+    return {"shape": fp.shape, "params": fp.n_params, "batch": batch, "train_s": train_s,
+            "simulations_per_s": hist["steps_run"] * batch / train_s, "schedule": hist,
+            "train_step_ms": step_ms, "train_step_graph_ms": step_graph_ms,
             "sample_20000_ms": {"p50": lat[len(lat) // 2] * 1e3, "min": lat[0] * 1e3, "max": lat[-1] * 1e3},
-            "skymap_20000_ms": dict(sky, note="sample_posterior 20k + log_likelihood + importance_weights + skymap "
-                                              "(HEALPix nested, importance-weighted), median of 10, host time"),
-            "events": events, "samples_per_event": per_event, "importance_sampling": res,
+            "skymap_20000_ms": dict(sky, note="sample_posterior 20k + log_likelihood_tmarg + importance_weights + "
+                                              "skymap (HEALPix nested, importance-weighted), median of 10, host time"),
+            "importance_sampling": isamp,
             "pp_test": {"events": pp_events, "draws_per_event": pp_samples, "ks_distance": ks,
                         "ks_95pct_critical": 1.36 / math.sqrt(pp_events),
                         "coords": ["Mc", "q", "D_L", "cos theta_JN", "RA", "sin dec", "psi", "phic"]},
             "serving": dict(serving, events=n_srv, draws="U{2000..50000} per event",
-                            per_event="draws (prior or flow) + log_likelihood + importance_weights + host read; "
-                                      "spins and merger time from the event"),
-            "note": "loss = batch mean of -ln q_x(x) in standardised coordinates; spins and merger time known to "
-                    "both proposals in the importance-sampling comparison"}
+                            per_event="draws (prior or flow) + log_likelihood_tmarg + importance_weights + host read"),
+            "note": "loss = batch mean of -ln q_x(x) in standardised coordinates; validation loss = mean -ln q_r of "
+                    "16,384 fixed simulations; the merger time is integrated out of the likelihood, spins are zero "
+                    "in the model and the events"}
 
 
 def cufft_leg(gwx, torch, sim, wl, fused_ms):
@@ -973,7 +900,6 @@ def run_gpu(args, wl):
     del sim_h
     serve = serving_leg(gwx, torch, rank)
     gemm = gemm_leg(gwx, torch)
-    learned = learned_leg(gwx, torch, rank)
     flow = flow_leg(gwx, torch, rank)
     flow_resnet = flow_resnet_leg(gwx, torch, rank)
     padded = padded_leg(gwx, torch, rank)
@@ -1010,7 +936,6 @@ def run_gpu(args, wl):
             "fft_vs_cufft": fft_cmp,
             "serving": serve,
             "gemm_bf16": gemm,
-            "learned_proposal": learned,
             "flow": flow,
             "flow_resnet": flow_resnet,
             "padded_grid": padded,
@@ -1070,15 +995,15 @@ def main(argv=None):
         from paper_2407_19048_gb300.flow import FlowPosterior
         gwx.init()
         E, S = (int(v) for v in args.only_flow_sample.split(","))
-        wl2 = workloads.workload("small", B=E)
+        wl2 = workloads.workload("small_nonspinning", B=E)
         y, th, _ = gwx.simulator.Simulator(wl2).step(0)
         fp = FlowPosterior(wl2)
         offs = torch.arange(E + 1, dtype=torch.int64, device="cuda") * S
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        fp.sample(y, th, offs, 1, 0)
+        fp.sample(y, offs, 1, 0, S=E * S)
         ev0.record()
         for rep in range(5):
-            fp.sample(y, th, offs, 1, rep)
+            fp.sample(y, offs, 1, rep, S=E * S)
         ev1.record()
         torch.cuda.synchronize()
         print(json.dumps({"flow_sample": {"events": E, "draws": E * S, "ms": ev0.elapsed_time(ev1) / 5}}), flush=True)

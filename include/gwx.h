@@ -285,6 +285,25 @@ int gwx_log_likelihood(int approximant, const float* y_data, int64_t E, int D, i
                        const double* theta, const int64_t* event_offsets, int64_t S,
                        double* lnl, void* workspace, size_t workspace_bytes, void* stream);
 
+/* ---- A8 with the merger time integrated out ------------------------------------------
+ * Sec. 5 leaves the coalescence time out of the estimated parameters (it is marginalised
+ * over), so the likelihood that judges the estimator's samples is the marginal over a
+ * uniform merger time in the window [tc_lo, tc_lo + n_tc / fs):
+ *   ln L_s = ln( (1/J) sum_{j<J} exp lnL(theta_s with tc = tc_lo + j / (u fs)) ),  J = u n_tc,
+ * lnL as gwx_log_likelihood (its sum over the grid is the rectangle rule for the
+ * normalised integral, on a grid u = oversample times finer than the sampling interval).
+ * The tc row of theta is not read.  Per sample: the template at tc_lo, the band products
+ * c_k = (2/N) sum_d Y_d,k conj(fs h_d,k W_d,k), and u inverse real FFTs of N points of
+ * c_k e^{2 pi i k r/(N u)}, r < u, whose first n_tc outputs are the grid's ln L up to the
+ * data and template norms; FP32 products and transforms, FP64 norms and final sums.
+ *   tc_lo finite; 1 <= n_tc <= N; oversample a power of two in [1, 64]; everything else,
+ *   the layouts and the workspace (gwx_log_likelihood_workspace) as gwx_log_likelihood. */
+int gwx_log_likelihood_tmarg(int approximant, const float* y_data, int64_t E, int D, int64_t N,
+                             const double* psd, int64_t seg_len, double fs, double f_lo,
+                             const int32_t* det_ids, double gmst, double tc_lo, int64_t n_tc, int oversample,
+                             const double* theta, const int64_t* event_offsets, int64_t S,
+                             double* lnl, void* workspace, size_t workspace_bytes, void* stream);
+
 /* ---- importance weights of scored samples ------------------------------------
  * Samples theta_s ~ q of event e, scored by gwx_log_likelihood, become posterior
  * samples by importance sampling with the standard GW likelihood (Sec. 6):
@@ -491,8 +510,11 @@ int gwx_flow_layout(const gwx_flow_shape* shape, int64_t* n_params, int64_t* off
  *   log_q [S] = ln q_r and log_ratio [S] = ln prior_r - ln q_r (-inf outside the prior's
  *   support).  Inside it m_big = Mc (1 + q)^{1/5} q^{-3/5}, m_small = q m_big, swapped
  *   into (m1, m2) when the coin u_8 (block 4 of the draw's counter, words 0 and 1) is
- *   below 1/2; theta_JN = acos, dec = asin of their coordinates; spins and t_c are those
- *   of the owning event in truth [GWX_NPARAM][E].  The prior (uniform in m1, m2, D, cos
+ *   below 1/2; theta_JN = acos, dec = asin of their coordinates.  The flow does not model
+ *   the spins or t_c (Sec. 5: spins ignored, t_c marginalised): they are drawn from the
+ *   prior's ranges, t_c = tc_lo + (tc_hi - tc_lo) u_9 (block 4, words 2 and 3), chi_1 and
+ *   chi_2 = chi_lo + (chi_hi - chi_lo) u_10, u_11 (block 5), so their prior and proposal
+ *   densities cancel in log_ratio.  The prior (uniform in m1, m2, D, cos
  *   theta_JN, RA, sin dec, psi, phic) has ln prior_r = ln 2 + 2 ln m_big - ln Mc
  *   - ln((m_hi - m_lo)^2 (d_hi - d_lo) 8 pi (psi_hi - psi_lo) (phi_hi - phi_lo)).
  *   Outside the support theta holds m_lo, d_lo and clipped angles. */
@@ -510,9 +532,8 @@ int gwx_flow_input_backward(int layer, const float* dX, int C, int64_t B, float*
                             void* stream);
 int gwx_flow_base(uint64_t seed, uint32_t counter, int64_t row0, int64_t n, float* z, void* stream);
 int gwx_flow_proposal(const float* x, const float* z, const float* sum_s, int64_t S, const double* mean8,
-                      const double* scale8, const gwx_prior* prior, const double* truth, int64_t E,
-                      const int64_t* event_offsets, uint64_t seed, uint32_t counter, double* theta, double* log_q,
-                      double* log_ratio, void* stream);
+                      const double* scale8, const gwx_prior* prior, uint64_t seed, uint32_t counter, double* theta,
+                      double* log_q, double* log_ratio, void* stream);
 
 /* One training step on a simulated batch: whitened strain y [B][D][N] (FP32) and its
  * parameters theta [GWX_NPARAM][B]: features, embedding, density pass, loss, backward
@@ -555,7 +576,7 @@ size_t gwx_sample_posterior_workspace(const gwx_flow_shape* shape, int64_t E, in
 int gwx_sample_posterior(const gwx_flow_shape* shape, const float* params, const void* params_bf16,
                          const double* mean8, const double* scale8, const gwx_prior* prior, const float* y,
                          int64_t E, int D, int64_t N, double fs, double f_lo, const void* ctx_in,
-                         const double* truth, const int64_t* event_offsets, int64_t S, uint64_t seed,
+                         const int64_t* event_offsets, int64_t S, uint64_t seed,
                          uint32_t counter, double* theta, double* log_q, double* log_ratio, void* workspace,
                          size_t workspace_bytes, void* stream);
 

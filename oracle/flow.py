@@ -41,8 +41,10 @@ the pins that need a smooth function).
 
 Importance-sampling proposal.  A draw x gives r = mean + scale x; inside the prior's
 support m_big = Mc (1 + q)^{1/5} q^{-3/5} and m_small = q m_big, ordered by a fair coin,
-theta_JN = acos(r_3), delta = asin(r_5); spins and t_c are the event's own (the flow does
-not model them: the paper ignores spins and marginalises t_c).  The prior of the
+theta_JN = acos(r_3), delta = asin(r_5).  The flow does not model the spins or t_c (the
+paper ignores spins and marginalises t_c, Sec. 5): they are drawn from their own prior,
+chi_i = chi_lo + (chi_hi - chi_lo) u, t_c = tc_lo + (tc_hi - tc_lo) u, so their prior
+and proposal densities are equal and cancel in the log ratio below.  The prior of the
 workloads is uniform in (m1, m2) on [m_lo, m_hi]^2 and in D, cos theta_JN, alpha,
 sin delta, psi, phi_c; in r-coordinates its density is
   pi_r = 2 m_big^2 / (Mc (m_hi - m_lo)^2) / ((d_hi - d_lo) 2 (2 pi) 2 (psi_hi - psi_lo)
@@ -53,7 +55,8 @@ The log ratio of a draw is ln pi_r - ln q_r (-inf outside the support).
 Base normals.  Draw s uses Philox4x32-10 counters (s, j, TAG_FLOW, counter), j = 0..4,
 block j giving u_{2j} = uniform52(w0, w1) and u_{2j+1} = uniform52(w2, w3); the normals
 are Box-Muller pairs z_{2i}, z_{2i+1} = sqrt(-2 ln u_{2i}) (cos, sin)(2 pi u_{2i+1}),
-i = 0..3, and u_8 is the ordering coin (masses swapped when u_8 < 1/2).
+i = 0..3, and u_8 is the ordering coin (masses swapped when u_8 < 1/2).  The parameters
+the flow does not model take u_9 (t_c) and block 5's u_10, u_11 (chi_1, chi_2).
 """
 import math
 
@@ -293,17 +296,23 @@ def loss_and_grads(feat, x, params, K, rnd=round_bf16):
 
 # ---------------------------------------------------------------- proposal
 
-def base_normals(seed, counter, idx):
-    """(z [S][8], coin [S]) for global draw indices idx."""
+def base_uniforms(seed, counter, idx):
+    """u [S][12]: u_{2j}, u_{2j+1} from Philox block j = 0..5 of each draw in idx."""
     k0, k1 = key_of(seed)
     idx = np.asarray(idx, dtype=np.uint64)
-    u = np.zeros((len(idx), 10))
-    for j in range(5):
+    u = np.zeros((len(idx), 12))
+    for j in range(6):
         w = philox4x32_10((idx & np.uint64(0xFFFFFFFF)).astype(np.uint32), np.uint32(j), np.uint32(TAG_FLOW),
                           np.uint32(counter & 0xFFFFFFFF), k0, k1)
         u[:, 2 * j] = uniform52(w[0], w[1])
         u[:, 2 * j + 1] = uniform52(w[2], w[3])
-    z = np.zeros((len(idx), 8))
+    return u
+
+
+def base_normals(seed, counter, idx):
+    """(z [S][8], coin [S]) for global draw indices idx."""
+    u = base_uniforms(seed, counter, idx)
+    z = np.zeros((len(u), 8))
     for i in range(4):
         rad = np.sqrt(-2.0 * np.log(u[:, 2 * i]))
         z[:, 2 * i] = rad * np.cos(2.0 * math.pi * u[:, 2 * i + 1])
@@ -311,20 +320,25 @@ def base_normals(seed, counter, idx):
     return z, u[:, 8]
 
 
-def proposal_params(x, z, sum_s, mean, scale, prior, truth, ev, coin):
+def nuisance_uniforms(seed, counter, idx):
+    """[S][3]: the uniforms of t_c, chi_1 and chi_2 (u_9, u_10, u_11) of draws idx."""
+    return base_uniforms(seed, counter, idx)[:, 9:12]
+
+
+def proposal_params(x, z, sum_s, mean, scale, prior, coin, nuis):
     """theta [11][S], ln q_r [S] and ln pi_r - ln q_r [S] of flow draws x (see the module
-    docstring); rows outside the prior's support get -inf and in-range placeholder masses
-    (m_lo), distance (d_lo) and clipped angles."""
+    docstring); nuis [S][3] the uniforms of t_c, chi_1, chi_2.  Rows outside the prior's
+    support get -inf and in-range placeholder masses (m_lo), distance (d_lo) and clipped
+    angles."""
     x = np.asarray(x, dtype=np.float64)
     S = len(x)
     r = np.asarray(mean)[None, :] + np.asarray(scale)[None, :] * x
     log_q = log_normal(z) - np.asarray(sum_s, dtype=np.float64) - np.sum(np.log(np.asarray(scale)))
     lp = log_prior_r(r, prior)
-    truth = np.asarray(truth, dtype=np.float64)
+    nuis = np.asarray(nuis, dtype=np.float64)
     th = np.zeros((11, S))
     for i in range(S):
         Mc, q, D, ct, al, sd, psi, phi = r[i]
-        e = ev[i]
         if np.isfinite(lp[i]):
             big, small = masses(Mc, q)
             m1, m2 = (small, big) if coin[i] < 0.5 else (big, small)
@@ -333,7 +347,9 @@ def proposal_params(x, z, sum_s, mean, scale, prior, truth, ev, coin):
             m1 = m2 = prior["m_lo"]
             dist = prior["d_lo"]
         th[0, i], th[1, i], th[4, i] = m1, m2, dist
-        th[2, i], th[3, i], th[5, i] = truth[2, e], truth[3, e], truth[5, e]
+        th[5, i] = prior["tc_lo"] + (prior["tc_hi"] - prior["tc_lo"]) * nuis[i, 0]
+        th[2, i] = prior["chi_lo"] + (prior["chi_hi"] - prior["chi_lo"]) * nuis[i, 1]
+        th[3, i] = prior["chi_lo"] + (prior["chi_hi"] - prior["chi_lo"]) * nuis[i, 2]
         th[6, i], th[8, i], th[9, i] = phi, psi, al
         th[7, i] = math.acos(min(1.0, max(-1.0, ct)))
         th[10, i] = math.asin(min(1.0, max(-1.0, sd)))
@@ -347,7 +363,7 @@ def event_of(offsets, S):
     return np.minimum(np.maximum(ev, 0), E - 1)
 
 
-def sample_posterior(feat_events, params, K, mean, scale, prior, truth, offsets, seed, counter, rnd=round_bf16):
+def sample_posterior(feat_events, params, K, mean, scale, prior, offsets, seed, counter, rnd=round_bf16):
     """Samples of event e in rows offsets[e] .. offsets[e+1]-1: (theta [11][S], ln q_r [S],
     ln pi_r - ln q_r [S])."""
     emb, layers = split_params(params, K)
@@ -356,7 +372,7 @@ def sample_posterior(feat_events, params, K, mean, scale, prior, truth, offsets,
     ev = event_of(offsets, S)
     z, coin = base_normals(seed, counter, np.arange(S))
     x, ss = sample(z, c[ev], layers, rnd)
-    return proposal_params(x, z, ss, mean, scale, prior, truth, ev, coin)
+    return proposal_params(x, z, ss, mean, scale, prior, coin, nuisance_uniforms(seed, counter, np.arange(S)))
 
 
 def log_prob(feat, theta, params, K, mean, scale, rnd=round_bf16):

@@ -23,7 +23,7 @@ M1, M2, CHI1, CHI2, DIST, TC, PHIC, THETAJN, PSI, RA, DEC = range(11)
 NPARAM = 11
 
 __all__ = ["GwxError", "version", "init", "detector_geometry", "sample_prior", "generate_waveforms", "project",
-           "colored_noise", "welch_psd", "inject", "inject_padded", "simulate_batch_padded", "whiten", "unwhiten", "simulate_batch", "log_likelihood",
+           "colored_noise", "welch_psd", "inject", "inject_padded", "simulate_batch_padded", "whiten", "unwhiten", "simulate_batch", "log_likelihood", "log_likelihood_tmarg",
            "importance_weights", "gemm_bf16", "dense_bf16", "dense_bf16_backward", "gemm_autotune", "spectral_features",
            "cross_features", "lag_features", "proposal_targets",
            "gauss_nll", "adamw", "adamw_clip", "skymap", "vicreg", "retime", "sample_proposal", "device_status", "selftest_bounded_wait", "rfft", "irfft",
@@ -275,6 +275,28 @@ def log_likelihood(y_data, psd, seg_len, fs, f_lo, dets, gmst, theta, event_offs
     ws, nb = _workspace(lib.gwx_log_likelihood_workspace(E, D, N, S), y_data.device)
     _check(lib.gwx_log_likelihood(approximant, _ptr(y_data), E, D, N, _ptr(psd), seg_len, fs, f_lo, ids, gmst,
                                   _ptr(theta), _ptr(event_offsets), S, _ptr(out), _ptr(ws), nb, _stream()))
+    return out
+
+
+def log_likelihood_tmarg(y_data, psd, seg_len, fs, f_lo, dets, gmst, tc_lo, n_tc, oversample, theta, event_offsets,
+                         approximant=TAYLORF2, out=None):
+    """ln L [S] of samples theta [11][S] with the merger time integrated out over
+    [tc_lo, tc_lo + n_tc / fs) on a grid of spacing 1 / (oversample fs) (the tc row of
+    theta is not read)."""
+    torch = _torch()
+    lib = _lib.load()
+    _dev(y_data, torch.float32, "y_data")
+    _dev(psd, torch.float64, "psd")
+    _dev(theta, torch.float64, "theta")
+    _dev(event_offsets, torch.int64, "event_offsets")
+    E, D, N = y_data.shape
+    S = theta.shape[1]
+    ids, nd = _det_ids(dets)
+    out = torch.empty(S, dtype=torch.float64, device=y_data.device) if out is None else out
+    ws, nb = _workspace(lib.gwx_log_likelihood_workspace(E, D, N, S), y_data.device)
+    _check(lib.gwx_log_likelihood_tmarg(approximant, _ptr(y_data), E, D, N, _ptr(psd), seg_len, fs, f_lo, ids, gmst,
+                                        float(tc_lo), int(n_tc), int(oversample), _ptr(theta), _ptr(event_offsets), S,
+                                        _ptr(out), _ptr(ws), nb, _stream()))
     return out
 
 
@@ -668,23 +690,21 @@ def flow_base(seed, counter, row0, n):
     return z
 
 
-def flow_proposal(x, z, sum_s, mean8, scale8, prior, truth, event_offsets, seed, counter):
-    """(theta [11][S], log_q [S], log_ratio [S]) of flow draws x with base z and sum_s."""
+def flow_proposal(x, z, sum_s, mean8, scale8, prior, seed, counter):
+    """(theta [11][S], log_q [S], log_ratio [S]) of flow draws x with base z and sum_s
+    (spins and t_c drawn from the prior)."""
     torch = _torch()
     _dev(x, torch.float32, "x")
     _dev(z, torch.float32, "z")
     _dev(sum_s, torch.float32, "sum_s")
-    _dev(truth, torch.float64, "truth")
-    _dev(event_offsets, torch.int64, "event_offsets")
     S = x.shape[0]
-    E = event_offsets.shape[0] - 1
     dev = x.device
     theta = torch.empty((NPARAM, S), dtype=torch.float64, device=dev)
     log_q, lr = (torch.empty(S, dtype=torch.float64, device=dev) for _ in range(2))
     p = _prior(prior)
     _check(_lib.load().gwx_flow_proposal(_ptr(x), _ptr(z), _ptr(sum_s), S, _host8(mean8), _host8(scale8),
-                                         ctypes.byref(p), _ptr(truth), E, _ptr(event_offsets), seed, counter,
-                                         _ptr(theta), _ptr(log_q), _ptr(lr), _stream()))
+                                         ctypes.byref(p), seed, counter, _ptr(theta), _ptr(log_q), _ptr(lr),
+                                         _stream()))
     return theta, log_q, lr
 
 
@@ -729,16 +749,17 @@ def flow_log_prob(shape, params, params_bf16, mean8, scale8, y, theta, fs, f_lo,
     return out
 
 
-def sample_posterior(shape, params, params_bf16, mean8, scale8, prior, y, fs, f_lo, truth, event_offsets, seed,
-                     counter, out=None, workspace=None, ctx=None):
-    """Posterior draws for events y [E][D][N]: (theta [11][S], log_q [S], log_ratio [S])."""
+def sample_posterior(shape, params, params_bf16, mean8, scale8, prior, y, fs, f_lo, event_offsets, seed,
+                     counter, out=None, workspace=None, ctx=None, S=None):
+    """Posterior draws for events y [E][D][N]: (theta [11][S], log_q [S], log_ratio [S]);
+    spins and t_c (not modelled by the flow) are drawn from the prior.  S (the total
+    number of draws, event_offsets[-1]) is read from the device when not given."""
     torch = _torch()
     sh = _shape(shape)
     _dev(y, torch.float32, "y")
-    _dev(truth, torch.float64, "truth")
     _dev(event_offsets, torch.int64, "event_offsets")
     E, D, N = y.shape
-    S = int(event_offsets[-1].item())
+    S = int(event_offsets[-1].item()) if S is None else int(S)
     dev = y.device
     lib = _lib.load()
     if out is None:
@@ -750,7 +771,7 @@ def sample_posterior(shape, params, params_bf16, mean8, scale8, prior, y, fs, f_
     p = _prior(prior)
     _check(lib.gwx_sample_posterior(ctypes.byref(sh), _ptr(params), _ptr(params_bf16), _host8(mean8), _host8(scale8),
                                     ctypes.byref(p), _ptr(y), E, D, N, fs, f_lo,
-                                    _ptr(ctx) if ctx is not None else None, _ptr(truth), _ptr(event_offsets), S,
+                                    _ptr(ctx) if ctx is not None else None, _ptr(event_offsets), S,
                                     seed, counter, _ptr(theta), _ptr(log_q), _ptr(lr), _ptr(ws), nb, _stream()))
     return theta, log_q, lr
 

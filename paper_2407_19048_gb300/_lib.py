@@ -66,6 +66,8 @@ SIGNATURES = {
     "gwx_log_likelihood_workspace": (c_size, [c_i64, c_int, c_i64, c_i64]),
     "gwx_log_likelihood": (c_int, [c_int, c_vp, c_i64, c_int, c_i64, c_vp, c_i64, c_dbl, c_dbl, c_i32p, c_dbl,
                                    c_vp, c_vp, c_i64, c_vp, c_vp, c_size, c_vp]),
+    "gwx_log_likelihood_tmarg": (c_int, [c_int, c_vp, c_i64, c_int, c_i64, c_vp, c_i64, c_dbl, c_dbl, c_i32p,
+                                         c_dbl, c_dbl, c_i64, c_int, c_vp, c_vp, c_i64, c_vp, c_vp, c_size, c_vp]),
     "gwx_importance_weights_workspace": (c_size, [c_i64]),
     "gwx_importance_weights": (c_int, [c_vp, c_vp, c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_size, c_vp]),
     "gwx_gemm_bf16": (c_int, [c_vp, c_vp, c_vp, c_i64, c_i64, c_i64, c_int, c_vp]),
@@ -121,8 +123,8 @@ SIGNATURES = {
     "gwx_flow_coupling_backward": (c_int, [c_int, c_vp, c_vp, c_vp, c_i64, c_f32, c_vp, c_vp, c_vp]),
     "gwx_flow_input_backward": (c_int, [c_int, c_vp, c_int, c_i64, c_vp, c_vp, c_int, c_vp]),
     "gwx_flow_base": (c_int, [c_u64, c_u32, c_i64, c_i64, c_vp, c_vp]),
-    "gwx_flow_proposal": (c_int, [c_vp, c_vp, c_vp, c_i64, c_d8, c_d8, c_pri, c_vp, c_i64, c_vp, c_u64, c_u32, c_vp,
-                                  c_vp, c_vp, c_vp]),
+    "gwx_flow_proposal": (c_int, [c_vp, c_vp, c_vp, c_i64, c_d8, c_d8, c_pri, c_u64, c_u32, c_vp, c_vp, c_vp,
+                                  c_vp]),
     "gwx_flow_train_workspace": (c_size, [c_shp, c_i64, c_int, c_i64]),
     "gwx_flow_train_step": (c_int, [c_shp, c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, c_vp, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl,
                                     c_dbl, c_d8, c_d8, c_vp, c_vp, c_i64, c_int, c_i64, c_dbl, c_dbl, c_vp, c_vp, c_vp,
@@ -132,7 +134,7 @@ SIGNATURES = {
                                   c_vp, c_vp, c_size, c_vp]),
     "gwx_sample_posterior_workspace": (c_size, [c_shp, c_i64, c_int, c_i64, c_i64]),
     "gwx_sample_posterior": (c_int, [c_shp, c_vp, c_vp, c_d8, c_d8, c_pri, c_vp, c_i64, c_int, c_i64, c_dbl, c_dbl,
-                                     c_vp, c_vp, c_vp, c_i64, c_u64, c_u32, c_vp, c_vp, c_vp, c_vp, c_size, c_vp]),
+                                     c_vp, c_vp, c_i64, c_u64, c_u32, c_vp, c_vp, c_vp, c_vp, c_size, c_vp]),
 }
 
 _lib = None

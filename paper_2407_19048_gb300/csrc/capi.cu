@@ -479,10 +479,13 @@ size_t gwx_log_likelihood_workspace(int64_t E, int D, int64_t N, int64_t S) {
          align_up(loglike_norm_bytes(E));
 }
 
-int gwx_log_likelihood(int approximant, const float* y_data, int64_t E, int D, int64_t N, const double* psd,
-                       int64_t seg_len, double fs, double f_lo, const int32_t* det_ids, double gmst,
-                       const double* theta, const int64_t* event_offsets, int64_t S, double* lnl, void* workspace,
-                       size_t workspace_bytes, void* stream) {
+// Shared by the two likelihood entry points: validation, data spectra, whitening filter
+// and the kernels (tmarg: merger time integrated out over tc_lo + j / (u fs), j < u n_tc).
+static int loglike_common(bool tmarg, int approximant, const float* y_data, int64_t E, int D, int64_t N,
+                          const double* psd, int64_t seg_len, double fs, double f_lo, const int32_t* det_ids,
+                          double gmst, double tc_lo, int64_t n_tc, int oversample, const double* theta,
+                          const int64_t* event_offsets, int64_t S, double* lnl, void* workspace,
+                          size_t workspace_bytes, void* stream) {
   if (approximant == GWX_IMRPHENOMD)
     return fail(GWX_EUNSUPPORTED, "IMRPhenomD is not available: its fitted coefficient tables are not in this build");
   if (approximant != GWX_TAYLORF2) return fail(GWX_EINVAL, "unknown approximant %d", approximant);
@@ -493,6 +496,12 @@ int gwx_log_likelihood(int approximant, const float* y_data, int64_t E, int D, i
   if (E < 0 || S < 0 || S > 0x7fffffffLL * 8 || E * D > 0x7fffffffLL) return fail(GWX_ESHAPE, "bad E or S");
   if (S > 0 && E == 0) return fail(GWX_ESHAPE, "samples without events");
   if (!(fs > 0.0) || !isfinite(gmst)) return fail(GWX_EINVAL, "bad fs or gmst");
+  if (tmarg) {
+    if (!isfinite(tc_lo)) return fail(GWX_EINVAL, "tc_lo must be finite");
+    if (n_tc < 1 || n_tc > N) return fail(GWX_ESHAPE, "n_tc=%lld must be in [1, N=%lld]", (long long)n_tc, (long long)N);
+    if (!is_pow2(oversample) || oversample > 64)
+      return fail(GWX_ESHAPE, "oversample=%d must be a power of two in [1, 64]", oversample);
+  }
   const double df = fs / (double)N;
   int k_lo = 0;
   GWX_TRY(band_start(f_lo, df, N / 2, &k_lo));
@@ -514,9 +523,30 @@ int gwx_log_likelihood(int approximant, const float* y_data, int64_t E, int D, i
   double* yy_part = reinterpret_cast<double*>(w);
   GWX_TRY(launched(launch_rfft_rows(y_data, E * D, N, Y, s), "rfft of the data"));
   GWX_TRY(launched(launch_whiten_filter(psd, D, seg_len, fs, k_lo, N, W, s), "whiten filter"));
+  if (tmarg)
+    return launched(launch_loglike_tmarg(y_data, Y, W, theta, df, fs, dp, gmst, tc_lo, (int)n_tc, oversample,
+                                         event_offsets, yy_part, E, D, N, k_lo, S, lnl, s),
+                    "log_likelihood_tmarg");
   return launched(launch_loglike_full(y_data, Y, W, theta, df, fs, dp, gmst, event_offsets, yy_part, E, D, N, k_lo,
                                       S, lnl, s),
                   "log_likelihood");
+}
+
+int gwx_log_likelihood(int approximant, const float* y_data, int64_t E, int D, int64_t N, const double* psd,
+                       int64_t seg_len, double fs, double f_lo, const int32_t* det_ids, double gmst,
+                       const double* theta, const int64_t* event_offsets, int64_t S, double* lnl, void* workspace,
+                       size_t workspace_bytes, void* stream) {
+  return loglike_common(false, approximant, y_data, E, D, N, psd, seg_len, fs, f_lo, det_ids, gmst, 0.0, 1, 1, theta,
+                        event_offsets, S, lnl, workspace, workspace_bytes, stream);
+}
+
+int gwx_log_likelihood_tmarg(int approximant, const float* y_data, int64_t E, int D, int64_t N, const double* psd,
+                             int64_t seg_len, double fs, double f_lo, const int32_t* det_ids, double gmst,
+                             double tc_lo, int64_t n_tc, int oversample, const double* theta,
+                             const int64_t* event_offsets, int64_t S, double* lnl, void* workspace,
+                             size_t workspace_bytes, void* stream) {
+  return loglike_common(true, approximant, y_data, E, D, N, psd, seg_len, fs, f_lo, det_ids, gmst, tc_lo, n_tc,
+                        oversample, theta, event_offsets, S, lnl, workspace, workspace_bytes, stream);
 }
 
 size_t gwx_importance_weights_workspace(int64_t E) {
@@ -1030,6 +1060,10 @@ int check_prior_box(const gwx_prior* p) {
   if (!p) return fail(GWX_EINVAL, "prior is NULL");
   if (!(p->m_lo > 0.0 && p->m_hi > p->m_lo && p->d_hi > p->d_lo && p->psi_hi > p->psi_lo && p->phi_hi > p->phi_lo))
     return fail(GWX_EINVAL, "prior ranges must be non-empty with m_lo > 0");
+  // spins and merger time are drawn from their ranges (a point range, lo == hi, is allowed)
+  if (!(isfinite(p->chi_lo) && isfinite(p->chi_hi) && p->chi_hi >= p->chi_lo && isfinite(p->tc_lo) &&
+        isfinite(p->tc_hi) && p->tc_hi >= p->tc_lo))
+    return fail(GWX_EINVAL, "spin and merger-time ranges must be finite with lo <= hi");
   return GWX_OK;
 }
 
@@ -1160,25 +1194,21 @@ int gwx_flow_base(uint64_t seed, uint32_t counter, int64_t row0, int64_t n, floa
 }
 
 int gwx_flow_proposal(const float* x, const float* z, const float* sum_s, int64_t S, const double* mean8,
-                      const double* scale8, const gwx_prior* prior, const double* truth, int64_t E,
-                      const int64_t* event_offsets, uint64_t seed, uint32_t counter, double* theta, double* log_q,
-                      double* log_ratio, void* stream) {
+                      const double* scale8, const gwx_prior* prior, uint64_t seed, uint32_t counter, double* theta,
+                      double* log_q, double* log_ratio, void* stream) {
   GWX_TRY(check_std8(mean8, scale8));
   GWX_TRY(check_prior_box(prior));
-  if (S < 0 || S > ((int64_t)1 << 32) || E < 0 || (S > 0 && E == 0)) return fail(GWX_ESHAPE, "bad S or E");
+  if (S < 0 || S > ((int64_t)1 << 32)) return fail(GWX_ESHAPE, "bad S");
   if (S == 0) return GWX_OK;
-  if (!x || !z || !sum_s || !truth || !event_offsets || !theta || !log_q || !log_ratio)
-    return fail(GWX_EINVAL, "NULL array");
+  if (!x || !z || !sum_s || !theta || !log_q || !log_ratio) return fail(GWX_EINVAL, "NULL array");
   GWX_ALIGN16(x);
   GWX_ALIGN16(z);
-  GWX_ALIGN8(truth);
-  GWX_ALIGN8(event_offsets);
   GWX_ALIGN8(theta);
   GWX_ALIGN8(log_q);
   GWX_ALIGN8(log_ratio);
   GWX_TRY(ensure_init());
-  return launched(launch_flow_proposal(x, z, sum_s, S, 0, S, mean8, scale8, *prior, truth, E, event_offsets, seed,
-                                       counter, theta, log_q, log_ratio, as_stream(stream)),
+  return launched(launch_flow_proposal(x, z, sum_s, S, 0, S, mean8, scale8, *prior, seed, counter, theta, log_q,
+                                       log_ratio, as_stream(stream)),
                   "flow_proposal");
 }
 
@@ -1258,7 +1288,7 @@ size_t gwx_sample_posterior_workspace(const gwx_flow_shape* shape, int64_t E, in
 int gwx_sample_posterior(const gwx_flow_shape* shape, const float* params, const void* params_bf16,
                          const double* mean8, const double* scale8, const gwx_prior* prior, const float* y,
                          int64_t E, int D, int64_t N, double fs, double f_lo, const void* ctx_in,
-                         const double* truth, const int64_t* event_offsets, int64_t S, uint64_t seed,
+                         const int64_t* event_offsets, int64_t S, uint64_t seed,
                          uint32_t counter, double* theta, double* log_q, double* log_ratio, void* workspace,
                          size_t workspace_bytes, void* stream) {
   GWX_TRY(check_flow_shape(shape));
@@ -1270,18 +1300,16 @@ int gwx_sample_posterior(const gwx_flow_shape* shape, const float* params, const
     return fail(GWX_ESHAPE, "bad E or S");
   if (S == 0) return GWX_OK;
   GWX_TRY(check_flow_params(shape, params, params_bf16));
-  if ((!y && !ctx_in) || !truth || !event_offsets || !theta || !log_q || !log_ratio)
-    return fail(GWX_EINVAL, "NULL array");
+  if ((!y && !ctx_in) || !event_offsets || !theta || !log_q || !log_ratio) return fail(GWX_EINVAL, "NULL array");
   if (y) GWX_ALIGN8(y);
   if (ctx_in) GWX_ALIGN16(ctx_in);
-  GWX_ALIGN8(truth);
   GWX_ALIGN8(event_offsets);
   GWX_ALIGN8(theta);
   GWX_ALIGN8(log_q);
   GWX_ALIGN8(log_ratio);
   GWX_TRY(check_ws(workspace, workspace_bytes, gwx_sample_posterior_workspace(shape, E, D, N, S)));
   GWX_TRY(ensure_init());
-  return launched(flow_sample(*shape, params, params_bf16, mean8, scale8, *prior, y, E, D, N, k_lo, ctx_in, truth,
+  return launched(flow_sample(*shape, params, params_bf16, mean8, scale8, *prior, y, E, D, N, k_lo, ctx_in,
                               event_offsets, S, seed, counter, theta, log_q, log_ratio, workspace, as_stream(stream)),
                   "sample_posterior");
 }

@@ -74,6 +74,12 @@ cudaError_t launch_loglike_full(const float* ydata, const float2* Ydata, const f
                                 double df, double fs, const DetParams& dp, double gmst, const int64_t* ev_off,
                                 double* yy_part, int64_t E, int D, int64_t N, int k_lo, int64_t S, double* lnl,
                                 cudaStream_t s);
+// ln L with the merger time integrated out over tc_lo + j / (u fs), j < u n_tc (the tc row
+// of theta unused); the same data-norm kernel and workspace as launch_loglike_full.
+cudaError_t launch_loglike_tmarg(const float* ydata, const float2* Ydata, const float* W, const double* theta,
+                                 double df, double fs, const DetParams& dp, double gmst, double tc_lo, int n_tc,
+                                 int u, const int64_t* ev_off, double* yy_part, int64_t E, int D, int64_t N,
+                                 int k_lo, int64_t S, double* lnl, cudaStream_t s);
 
 // Importance weights: E x iw_chunks(E) partials in ws (iw_workspace_bytes(E)).
 size_t iw_workspace_bytes(int64_t E);
@@ -150,8 +156,8 @@ cudaError_t launch_flow_input_backward(int l, const float* dX, int C, int64_t B,
 cudaError_t launch_flow_base(uint64_t seed, uint32_t counter, int64_t row0, int64_t n, float* z, cudaStream_t s);
 cudaError_t launch_flow_proposal(const float* x, const float* z, const float* sum_s, int64_t n, int64_t row0,
                                  int64_t S, const double* mean8, const double* scale8, const gwx_prior& pr,
-                                 const double* truth, int64_t E, const int64_t* off, uint64_t seed, uint32_t counter,
-                                 double* theta, double* log_q, double* log_ratio, cudaStream_t s);
+                                 uint64_t seed, uint32_t counter, double* theta, double* log_q, double* log_ratio,
+                                 cudaStream_t s);
 // The sampling pass of the coupling flow fused into one persistent tcgen05 kernel
 // (k_flow_fused.cu), for conditioner widths H of 128 or 256 and 8 + C <= 128: draws
 // z [n][8] of global rows row0 .. row0 + n - 1 -> x_out [n][8], ss_out [n].
@@ -173,7 +179,7 @@ cudaError_t flow_log_prob(const gwx_flow_shape& sh, const float* params, const v
 size_t flow_sample_ws(const gwx_flow_shape& sh, int64_t E, int D, int64_t N, int64_t S);
 cudaError_t flow_sample(const gwx_flow_shape& sh, const float* params, const void* params_bf16, const double* mean8,
                         const double* scale8, const gwx_prior& pr, const float* y, int64_t E, int D, int64_t N,
-                        int k_lo, const void* ctx_in, const double* truth, const int64_t* off, int64_t S,
+                        int k_lo, const void* ctx_in, const int64_t* off, int64_t S,
                         uint64_t seed, uint32_t counter, double* theta, double* log_q, double* log_ratio, void* ws,
                         cudaStream_t s);
 

@@ -226,14 +226,12 @@ __global__ void k_flow_base(uint32_t k0, uint32_t k1, uint32_t counter, int64_t 
 
 __global__ void k_flow_proposal(const float* __restrict__ x, const float* __restrict__ z,
                                 const float* __restrict__ sum_s, int64_t n, int64_t row0, int64_t S, Std8 st,
-                                gwx_prior pr, const double* __restrict__ truth, int64_t E,
-                                const int64_t* __restrict__ off, uint32_t k0, uint32_t k1, uint32_t counter,
+                                gwx_prior pr, uint32_t k0, uint32_t k1, uint32_t counter,
                                 double* __restrict__ theta, double* __restrict__ log_q,
                                 double* __restrict__ log_ratio) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int64_t s = row0 + i;
-  const int64_t e = event_of(off, E, s);
   float xv[8], zv[8];
   load8(x + i * 8, xv);
   load8(z + i * 8, zv);
@@ -246,6 +244,11 @@ __global__ void k_flow_proposal(const float* __restrict__ x, const float* __rest
   const double lq = -0.5 * zz - 4.0 * LN_2PI - (double)sum_s[i] - st.ln_scale_sum;
   const u32x4 w = philox4x32_10((uint32_t)s, 4u, TAG_FLOW, counter, k0, k1);
   const double coin = uniform52(w.x, w.y);
+  // parameters the flow does not model (t_c, spins): drawn from their prior, so their
+  // prior and proposal densities cancel in the log ratio
+  const double u_tc = uniform52(w.z, w.w);
+  const u32x4 w5 = philox4x32_10((uint32_t)s, 5u, TAG_FLOW, counter, k0, k1);
+  const double u_chi1 = uniform52(w5.x, w5.y), u_chi2 = uniform52(w5.z, w5.w);
   const double Mc = r[0], q = r[1], D = r[2], ct = r[3], al = r[4], sd = r[5], psi = r[6], phi = r[7];
   double m1 = pr.m_lo, m2 = pr.m_lo, dist = pr.d_lo, lr = -INFINITY;
   if (Mc > 0.0 && q > 0.0 && q <= 1.0) {
@@ -265,10 +268,10 @@ __global__ void k_flow_proposal(const float* __restrict__ x, const float* __rest
   }
   theta[s] = m1;
   theta[S + s] = m2;
-  theta[2 * S + s] = truth[2 * E + e];
-  theta[3 * S + s] = truth[3 * E + e];
+  theta[2 * S + s] = pr.chi_lo + (pr.chi_hi - pr.chi_lo) * u_chi1;
+  theta[3 * S + s] = pr.chi_lo + (pr.chi_hi - pr.chi_lo) * u_chi2;
   theta[4 * S + s] = dist;
-  theta[5 * S + s] = truth[5 * E + e];
+  theta[5 * S + s] = pr.tc_lo + (pr.tc_hi - pr.tc_lo) * u_tc;
   theta[6 * S + s] = phi;
   theta[7 * S + s] = acos(fmin(1.0, fmax(-1.0, ct)));
   theta[8 * S + s] = psi;
@@ -407,13 +410,13 @@ cudaError_t launch_flow_base(uint64_t seed, uint32_t counter, int64_t row0, int6
 
 cudaError_t launch_flow_proposal(const float* x, const float* z, const float* sum_s, int64_t n, int64_t row0,
                                  int64_t S, const double* mean8, const double* scale8, const gwx_prior& pr,
-                                 const double* truth, int64_t E, const int64_t* off, uint64_t seed, uint32_t counter,
-                                 double* theta, double* log_q, double* log_ratio, cudaStream_t s) {
+                                 uint64_t seed, uint32_t counter, double* theta, double* log_q, double* log_ratio,
+                                 cudaStream_t s) {
   // ln prior_r = ln 2 + 2 ln m_big - ln Mc - ln((m_hi - m_lo)^2 (d_hi - d_lo) 8 pi (psi range) (phi range))
   Std8 st = make_std(mean8, scale8);
   st.ln_prior0 = log(2.0) - 2.0 * log(pr.m_hi - pr.m_lo) - log(pr.d_hi - pr.d_lo) - log(8.0 * PI_F) -
                  log(pr.psi_hi - pr.psi_lo) - log(pr.phi_hi - pr.phi_lo);
-  k_flow_proposal<<<blocks(n, 128), 128, 0, s>>>(x, z, sum_s, n, row0, S, st, pr, truth, E, off,
+  k_flow_proposal<<<blocks(n, 128), 128, 0, s>>>(x, z, sum_s, n, row0, S, st, pr,
                                                  (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), counter,
                                                  theta, log_q, log_ratio);
   return cudaGetLastError();
@@ -653,7 +656,7 @@ size_t flow_sample_ws(const gwx_flow_shape& sh, int64_t E, int D, int64_t N, int
 
 cudaError_t flow_sample(const gwx_flow_shape& sh, const float* params, const void* params_bf16, const double* mean8,
                         const double* scale8, const gwx_prior& pr, const float* y, int64_t E, int D, int64_t N,
-                        int k_lo, const void* ctx_in, const double* truth, const int64_t* off, int64_t S,
+                        int k_lo, const void* ctx_in, const int64_t* off, int64_t S,
                         uint64_t seed, uint32_t counter, double* theta, double* log_q, double* log_ratio, void* ws,
                         cudaStream_t s) {
   const FlowDims d = dims_of(sh);
@@ -670,8 +673,8 @@ cudaError_t flow_sample(const gwx_flow_shape& sh, const float* params, const voi
     if (fused) {
       FL_TRY(launch_flow_sample_fused(params_bf16, params, P.off.data(), (int)d.C, (int)d.H, (int)d.K, w.z, ctx,
                                       off, E, row0, n, w.v, w.sum_s, s));
-      FL_TRY(launch_flow_proposal(w.v, w.z, w.sum_s, n, row0, S, mean8, scale8, pr, truth, E, off, seed, counter,
-                                  theta, log_q, log_ratio, s));
+      FL_TRY(launch_flow_proposal(w.v, w.z, w.sum_s, n, row0, S, mean8, scale8, pr, seed, counter, theta, log_q,
+                                  log_ratio, s));
       continue;
     }
     const float* vin = w.z;
@@ -681,8 +684,8 @@ cudaError_t flow_sample(const gwx_flow_shape& sh, const float* params, const voi
       FL_TRY(launch_flow_coupling(l, +1, vin, w.o, n, w.v, w.sum_s, l == 0, s));
       vin = w.v;
     }
-    FL_TRY(launch_flow_proposal(w.v, w.z, w.sum_s, n, row0, S, mean8, scale8, pr, truth, E, off, seed, counter, theta,
-                                log_q, log_ratio, s));
+    FL_TRY(launch_flow_proposal(w.v, w.z, w.sum_s, n, row0, S, mean8, scale8, pr, seed, counter, theta, log_q,
+                                log_ratio, s));
   }
   return cudaSuccess;
 }

@@ -273,4 +273,214 @@ cudaError_t launch_loglike_full(const float* ydata, const float2* Ydata, const f
   return cudaGetLastError();
 }
 
+
+// ----------------------------------------------------------------- A8, merger time integrated out
+// ln L_m = ln( (1/J) sum_{j<J} exp ln L(theta, tc = tc_lo + j / (u fs)) ),  J = u n_tc.
+// A merger-time shift only rotates the template's phase, so with the template H built at
+// tc = tc_lo and c_k = (2/N) sum_d Y_d,k conj(H_d,k) (band bins, zero elsewhere)
+//   ln L(tc_lo + (u m + r) / (u fs)) = -(|Y|^2 + |H|^2)/N + Re sum_k c_k e^{2 pi i k r/(N u)} e^{2 pi i k m/N},
+// i.e. for each sub-grid offset r < u an inverse real FFT of N points of
+// c_k e^{2 pi i k r/(N u)}, of which the outputs m < n_tc are used.  A block takes 32
+// consecutive samples: its first warp does their FP64 set-up (one lane per sample), then
+// per sample all threads build c_k in shared memory, and G groups of n/8 threads run the
+// u transforms G at a time (fft_smem_at), folding their outputs into a per-thread running
+// maximum and sum of exponentials; one block reduction per sample gives ln L_m.
+constexpr int TM_SAMPLES = 32;
+
+template <int LOGN>
+struct TmGeom {
+  static constexpr int n = 1 << LOGN;                         // complex points of the packed transform
+  static constexpr int TPR = n / 8;                           // threads per transform
+  static constexpr int G = TPR >= 256 ? 1 : 256 / TPR;        // transforms in flight per block
+  static constexpr int THREADS = TPR * G;
+  static constexpr size_t SMEM = ((size_t)G * n + (size_t)(n + 1)) * sizeof(float2);
+};
+
+// Running log-sum-exp state (max m, sum s of exp(v - m)).
+__device__ __forceinline__ void lse_add(float& m, float& s, float v) {
+  if (v > m) {
+    s = fmaf(s, __expf(m - v), 1.0f);
+    m = v;
+  } else {
+    s += __expf(v - m);
+  }
+}
+__device__ __forceinline__ void lse_merge(float& m, float& s, float m2, float s2) {
+  const float M = fmaxf(m, m2);
+  if (M == -INFINITY) return;
+  s = s * __expf(m - M) + s2 * __expf(m2 - M);
+  m = M;
+}
+
+template <int ND, int LOGN>
+__global__ void __launch_bounds__(TmGeom<LOGN>::THREADS)
+k_loglike_tmarg(const double* __restrict__ theta, SetupConsts kc, double fs, DetParams dp, double gmst, double tc_lo,
+                const float2* __restrict__ Y, const float* __restrict__ W, const int64_t* __restrict__ ev_off,
+                const double* __restrict__ yy_part, int64_t E, int k_lo, int n_tc, int u, int64_t S, double invN,
+                double log_J, double* __restrict__ lnl) {
+  using Gm = TmGeom<LOGN>;
+  constexpr int n = Gm::n;
+  constexpr int F = n + 1;
+  constexpr int NT = Gm::THREADS;
+  constexpr int NW = NT / 32;
+  extern __shared__ float2 tm_smem[];
+  float2* cb = tm_smem + Gm::G * n;                           // c_k, k = 0 .. n
+  __shared__ DrawCoef sc[TM_SAMPLES];
+  __shared__ int se[TM_SAMPLES];
+  __shared__ float red_m[NW], red_s[NW];
+  __shared__ double red_h[NW];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int g = tid / Gm::TPR, t = tid % Gm::TPR;
+  const int64_t base = (int64_t)blockIdx.x * TM_SAMPLES;
+  const int cnt = (int)min((int64_t)TM_SAMPLES, S - base);
+  if (wid == 0 && lane < cnt) {
+    const int64_t s_own = base + lane;
+    int64_t lo = 0, hi = E;                                   // event: largest e with ev_off[e] <= s
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (__ldg(&ev_off[mid]) <= s_own) lo = mid; else hi = mid;
+    }
+    DrawCoef c;
+    double amp = 0.0;
+    draw_waveform_coef(theta, S, s_own, kc, F, c, &amp);
+    draw_detector_coef_at(theta, S, s_own, kc.df, dp, gmst, c.qp, c.qc_im, fs * amp, tc_lo, c);
+    sc[lane] = c;
+    se[lane] = (int)lo;
+  }
+  __syncthreads();
+  const float two_over_N = (float)(2.0 * invN);               // a power of two: exact
+  const uint32_t zaddr = smem_addr(tm_smem + g * n);
+  float2* z = tm_smem + g * n;
+  const uint32_t numask = (uint32_t)(2 * n) * (uint32_t)u - 1u;   // N u - 1 (N u a power of two)
+  const float inv_nu = 1.0f / (float)(numask + 1u);
+  for (int j = 0; j < cnt; ++j) {
+    const int64_t e = se[j];
+    const int kend = min(sc[j].kcut, n - 1);
+    // c_k and this thread's part of sum |H|^2 (Kahan)
+    float hs = 0.f, hcmp = 0.f;
+    for (int k = tid; k <= n; k += NT) {
+      float2 acc = make_float2(0.f, 0.f);
+      if (k >= k_lo && k <= kend) {
+        const DrawCoef& c = sc[j];
+        float k76;
+        const float tt = waveform_turns(c, k, k76);
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+          const float x = k76 * __ldg(&W[(int64_t)d * F + k]);
+          const float4 gg = c.g[d];
+          const float2 ph = expm2pi(tt + lin_turns(c.nu[d], k));
+          const float2 H = cmul(make_float2(df_scale(gg.x, gg.y, x), df_scale(gg.z, gg.w, x)), ph);
+          const float2 yv = __ldg(&Y[(e * ND + d) * F + k]);
+          acc.x = fmaf(yv.x, H.x, fmaf(yv.y, H.y, acc.x));
+          acc.y = fmaf(yv.y, H.x, fmaf(-yv.x, H.y, acc.y));
+          const float yk = fmaf(H.x, H.x, H.y * H.y) - hcmp;
+          const float tk = hs + yk;
+          hcmp = (tk - hs) - yk;
+          hs = tk;
+        }
+      }
+      cb[k] = make_float2(acc.x * two_over_N, acc.y * two_over_N);
+    }
+    __syncthreads();
+    float mx = -INFINITY, sm = 0.f;
+    for (int r0 = 0; r0 < u; r0 += Gm::G) {
+      const uint32_t r = (uint32_t)(r0 + g);
+      // X_k = c_k e^{2 pi i k r/(N u)}, packed into n complex points (c_0 = c_n = 0)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int k = t + i * (n / 8);
+        if (k == 0) {
+          z[0] = make_float2(0.f, 0.f);
+          continue;
+        }
+        const float2 xk = cmul(cb[k], expm2pi(-(float)(((uint32_t)k * r) & numask) * inv_nu));
+        const float2 xnk = cmul(cb[n - k], expm2pi(-(float)(((uint32_t)(n - k) * r) & numask) * inv_nu));
+        float2 zk, znk;
+        pack_pair(xk, xnk, pack_twiddle(k, LOGN + 1), zk, znk);
+        z[sw(k)] = zk;
+        z[sw(n - k)] = znk;
+      }
+      if (t == 0) {
+        const int h = n / 2;
+        const float2 xh = cmul(cb[h], expm2pi(-(float)(((uint32_t)h * r) & numask) * inv_nu));
+        float2 zk, znk;
+        pack_pair(xh, xh, pack_twiddle(h, LOGN + 1), zk, znk);
+        z[sw(h)] = zk;
+      }
+      __syncthreads();
+      fft_smem_at<LOGN, true>(zaddr, t);                      // unscaled inverse: z packs (v_2m, v_2m+1)
+      if ((int)r < u) {
+        for (int mp = t; 2 * mp < n_tc; mp += n / 8) {
+          const float2 v = z[sw(mp)];
+          lse_add(mx, sm, v.x);
+          if (2 * mp + 1 < n_tc) lse_add(mx, sm, v.y);
+        }
+      }
+      __syncthreads();                                        // outputs read before the next pack
+    }
+    // block reductions: (max, sum) and sum |H|^2 (FP64 across threads)
+    double hh = (double)hs - (double)hcmp;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lse_merge(mx, sm, __shfl_xor_sync(0xffffffffu, mx, o), __shfl_xor_sync(0xffffffffu, sm, o));
+      hh += __shfl_xor_sync(0xffffffffu, hh, o);
+    }
+    if (lane == 0) {
+      red_m[wid] = mx;
+      red_s[wid] = sm;
+      red_h[wid] = hh;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float M = red_m[0], Sm = red_s[0];
+      double H2 = red_h[0];
+      for (int w = 1; w < NW; ++w) {
+        lse_merge(M, Sm, red_m[w], red_s[w]);
+        H2 += red_h[w];
+      }
+      double yy = 0.0;
+#pragma unroll
+      for (int c = 0; c < YY_CHUNKS; ++c) yy += yy_part[e * YY_CHUNKS + c];
+      lnl[base + j] = -(yy + H2) * invN + (double)M + log((double)Sm) - log_J;
+    }
+    __syncthreads();                                          // c_k and the reduction slots are reused
+  }
+}
+
+cudaError_t launch_loglike_tmarg(const float* ydata, const float2* Ydata, const float* W, const double* theta,
+                                 double df, double fs, const DetParams& dp, double gmst, double tc_lo, int n_tc,
+                                 int u, const int64_t* ev_off, double* yy_part, int64_t E, int D, int64_t N,
+                                 int k_lo, int64_t S, double* lnl, cudaStream_t s) {
+  const int64_t F = N / 2 + 1;
+  const int n = (int)(N / 2);
+  if (E > 0) {
+    k_event_norm<<<dim3((unsigned)E, YY_CHUNKS), 256, 0, s>>>(ydata, Ydata, D, F, k_lo, n, yy_part);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+  }
+  if (S <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((S + TM_SAMPLES - 1) / TM_SAMPLES);
+  const double invN = 1.0 / (double)N;
+  const double log_J = log((double)u * (double)n_tc);
+  const SetupConsts kc = make_setup_consts(df);
+  return dispatch_log<7, 13>(ilog2_exact(n), [&](auto lg) -> cudaError_t {
+    constexpr int LG = decltype(lg)::value;
+    using Gm = TmGeom<LG>;
+    auto run = [&](auto kern) -> cudaError_t {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SMEM);
+      if (e != cudaSuccess) return e;
+      kern<<<grid, Gm::THREADS, Gm::SMEM, s>>>(theta, kc, fs, dp, gmst, tc_lo, Ydata, W, ev_off, yy_part, E, k_lo,
+                                               n_tc, u, S, invN, log_J, lnl);
+      return cudaGetLastError();
+    };
+    switch (D) {
+      case 1: return run(k_loglike_tmarg<1, LG>);
+      case 2: return run(k_loglike_tmarg<2, LG>);
+      case 3: return run(k_loglike_tmarg<3, LG>);
+      case 4: return run(k_loglike_tmarg<4, LG>);
+      default: return cudaErrorInvalidValue;
+    }
+  });
+}
+
 }  // namespace gwx

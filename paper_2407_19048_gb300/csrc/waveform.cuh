@@ -109,10 +109,11 @@ __device__ inline void draw_waveform_coef(const double* th, int64_t B, int64_t b
 }
 
 // Projection part: scale * (F+ qp - i Fx qc) per detector as a complex double-float,
-// and the per-detector linear phase (tc + dt_d) df modulo one as a 2^-64 fixed point.
-__device__ inline void draw_detector_coef(const double* th, int64_t B, int64_t b, double df, const DetParams& dp,
-                                          double gmst, double qp, double qc, double scale, DrawCoef& c) {
-  const double tc = th_at(th, B, b, GWX_TC), psi = th_at(th, B, b, GWX_PSI);
+// and the per-detector linear phase (tc + dt_d) df modulo one as a 2^-64 fixed point,
+// for a given merger time tc (the sky position and polarisation from theta).
+__device__ inline void draw_detector_coef_at(const double* th, int64_t B, int64_t b, double df, const DetParams& dp,
+                                             double gmst, double qp, double qc, double scale, double tc, DrawCoef& c) {
+  const double psi = th_at(th, B, b, GWX_PSI);
   const double ra = th_at(th, B, b, GWX_RA), dec = th_at(th, B, b, GWX_DEC);
   double sd, cd, sp, cp, spsi, cpsi;
   sincos(dec, &sd, &cd);
@@ -153,6 +154,12 @@ __device__ inline void draw_detector_coef(const double* th, int64_t B, int64_t b
     double fx = ldexp(x, 64);
     c.nu[d] = fx >= 18446744073709551615.0 ? 0ull : (unsigned long long)fx;
   }
+}
+
+// The same with the merger time of theta.
+__device__ inline void draw_detector_coef(const double* th, int64_t B, int64_t b, double df, const DetParams& dp,
+                                          double gmst, double qp, double qc, double scale, DrawCoef& c) {
+  draw_detector_coef_at(th, B, b, df, dp, gmst, qp, qc, scale, th_at(th, B, b, GWX_TC), c);
 }
 
 // Fractional turns of k * nu * 2^-64, in [-1/2, 1/2).

@@ -170,12 +170,79 @@ class FlowPosterior:
     def note_replay(self):
         self.steps += 1
 
-    def sample(self, y_events, truth, event_offsets, seed, counter):
-        """Posterior draws for events y_events [E][D][N] (spins and t_c from truth):
-        (theta [11][S], ln q_r [S], ln prior_r - ln q_r [S])."""
+    def validation_loss(self, y, theta):
+        """Mean of -ln q_r over a fixed validation set (y [B][D][N], theta [11][B]), as a
+        host float (one synchronisation)."""
+        lq = self.log_prob(y, theta)
+        return float(-lq.mean().item())
+
+    def fit(self, sim, steps, counter0, val, epoch_sims=160000, patience=10, stop_patience=50, factor=0.1,
+            threshold=1e-4, min_lr=None, graph=True, log=None):
+        """Train on the simulator's batches (counters counter0, counter0 + 1, ...) for at most
+        `steps` steps with the schedule of Sec. 5: an epoch is `epoch_sims` simulations
+        (the paper: 200 batches of 800); after every epoch the validation loss of `val`
+        (y, theta) is evaluated, the learning rate is divided by 1/factor when it has not
+        improved (by more than `threshold`, relative) for `patience` epochs, and training
+        stops when it has not improved for `stop_patience` epochs or the learning rate
+        falls below `min_lr` (default: initial / 1000).  The parameters of the best epoch
+        are restored at the end.  With graph=True each step is one CUDA-graph replay per
+        simulator buffer set (recaptured when the learning rate changes).  Returns the
+        history: (step, validation loss, learning rate) per epoch and the stop reason."""
+        import torch
+        B = sim.B
+        per_epoch = max(1, round(epoch_sims / B))
+        lr0 = self.lr
+        min_lr = lr0 * 1e-3 if min_lr is None else min_lr
+        best, best_step, bad, bad_stop = float("inf"), 0, 0, 0
+        best_params = self.params.clone()
+        graphs = {}
+        hist, reason = [], "step budget"
+        yv, thv = val
+        for i in range(steps):
+            y, th, _ = sim.step(counter0 + i)
+            if graph:
+                g = graphs.get(y.data_ptr())
+                if g is None:
+                    g = graphs[y.data_ptr()] = self.capture_train_step(y, th)
+                    # the capture itself runs no step; replay it now
+                g.replay()
+                self.note_replay()
+            else:
+                self.train_step(y, th)
+            if (i + 1) % per_epoch == 0 or i == steps - 1:
+                vl = self.validation_loss(yv, thv)
+                hist.append((i + 1, vl, self.lr))
+                if log is not None:
+                    log(i + 1, vl, self.lr)
+                improved = (not math.isfinite(best)) or vl < best - threshold * abs(best)
+                if improved:
+                    best, best_step, bad, bad_stop = vl, i + 1, 0, 0
+                    best_params.copy_(self.params)
+                else:
+                    bad += 1
+                    bad_stop += 1
+                    if bad_stop >= stop_patience:
+                        reason = "validation loss saturated"
+                        break
+                    if bad >= patience:
+                        bad = 0
+                        self.lr *= factor
+                        graphs.clear()
+                        if self.lr < min_lr:
+                            reason = "learning rate below its floor"
+                            break
+        torch.cuda.synchronize()
+        self.params.copy_(best_params)
+        self.params16.copy_(self.params.to(torch.bfloat16))
+        return {"epochs": hist, "best_step": best_step, "best_val_loss": best, "steps_run": hist[-1][0] if hist else 0,
+                "stop": reason, "steps_per_epoch": per_epoch}
+
+    def sample(self, y_events, event_offsets, seed, counter, S=None):
+        """Posterior draws for events y_events [E][D][N] (spins and t_c, which the flow does
+        not model, from the prior): (theta [11][S], ln q_r [S], ln prior_r - ln q_r [S])."""
         return self.gwx.sample_posterior(self.shape, self.params, self.params16, self.mean, self.scale,
-                                         self.wl["prior"], y_events, self.fs, self.f_lo, truth, event_offsets, seed,
-                                         counter, ctx=self.context(y_events))
+                                         self.wl["prior"], y_events, self.fs, self.f_lo, event_offsets, seed,
+                                         counter, ctx=self.context(y_events), S=S)
 
     def log_prob(self, y, theta):
         return self.gwx.flow_log_prob(self.shape, self.params, self.params16, self.mean, self.scale, y, theta,

@@ -2,7 +2,8 @@
 
 An event arrives as a whitened window y [D][N]; the scorer draws S samples from a
 proposal (the prior, or a trained `flow.FlowPosterior` through `gwx_sample_posterior`),
-scores them with the standard likelihood (Sec. 6) and weighs them, then reads the
+scores them with the standard likelihood (Sec. 6; optionally with the merger time
+integrated out, `gwx_log_likelihood_tmarg`) and weighs them, then reads the
 event's effective sample size and evidence back to the host.  Every buffer and workspace is allocated once
 for the largest S, the calls go straight to the C ABI on one stream, and the only host
 synchronisation is the final read of two doubles from pinned memory.
@@ -14,7 +15,7 @@ from . import NPARAM, _check, _det_ids, _prior, _ptr, _workspace
 
 
 class Scorer:
-    def __init__(self, workload, max_samples, psd, device=None, seed=55, flow=None):
+    def __init__(self, workload, max_samples, psd, device=None, seed=55, flow=None, tmarg=None):
         import torch
         self.wl = dict(workload)
         wl = self.wl
@@ -39,6 +40,8 @@ class Scorer:
         self.ws_ll = _workspace(self.lib.gwx_log_likelihood_workspace(1, self.D, self.N, self.smax), self.dev)
         self.ws_iw = _workspace(self.lib.gwx_importance_weights_workspace(1), self.dev)
         self.flow = flow
+        # (tc_lo, n_tc, oversample): score with the merger time integrated out over that grid
+        self.tmarg = None if tmarg is None else (float(tmarg[0]), int(tmarg[1]), int(tmarg[2]))
         if flow is not None:
             from . import _shape
             self.shape = _shape(flow.shape)
@@ -51,11 +54,11 @@ class Scorer:
         self.stream = torch.cuda.Stream(device=self.dev)
         self.done = torch.cuda.Event()
 
-    def score(self, y_event, S, step, truth=None):
+    def score(self, y_event, S, step):
         """(ess, efficiency, ln_evidence) of one event y_event [D][N] (device float32)
-        from S samples drawn with Philox counter `step`: from the prior, or with a flow
-        from the flow (spins and merger time from truth [11][1], which the flow does not
-        model)."""
+        from S samples drawn with Philox counter `step`: from the prior, or from the flow
+        (whose draws take the spins and merger time, which it does not model, from the
+        prior)."""
         import torch
         if S > self.smax:
             raise ValueError("S exceeds max_samples")
@@ -74,14 +77,20 @@ class Scorer:
             fp = self.flow
             _check(lib.gwx_sample_posterior(ctypes.byref(self.shape), _ptr(fp.params), _ptr(fp.params16), self.mean8,
                                             self.scale8, ctypes.byref(self.prior), _ptr(y_event), 1, self.D, self.N,
-                                            self.fs, self.f_lo, None, _ptr(truth), _ptr(self.ev), S, self.seed,
+                                            self.fs, self.f_lo, None, _ptr(self.ev), S, self.seed,
                                             step & 0xFFFFFFFF, theta, _ptr(self.log_q), _ptr(self.log_ratio),
                                             _ptr(ws), nb, s))
             ratio = _ptr(self.log_ratio)
         ws, nb = self.ws_ll
-        _check(lib.gwx_log_likelihood(0, _ptr(y_event), 1, self.D, self.N, _ptr(self.psd), self.M, self.fs,
-                                      self.f_lo, self.ids, 0.0, theta, _ptr(self.ev), S, _ptr(self.lnl), _ptr(ws), nb,
-                                      s))
+        if self.tmarg is None:
+            _check(lib.gwx_log_likelihood(0, _ptr(y_event), 1, self.D, self.N, _ptr(self.psd), self.M, self.fs,
+                                          self.f_lo, self.ids, 0.0, theta, _ptr(self.ev), S, _ptr(self.lnl), _ptr(ws),
+                                          nb, s))
+        else:
+            tc_lo, n_tc, u = self.tmarg
+            _check(lib.gwx_log_likelihood_tmarg(0, _ptr(y_event), 1, self.D, self.N, _ptr(self.psd), self.M, self.fs,
+                                                self.f_lo, self.ids, 0.0, tc_lo, n_tc, u, theta, _ptr(self.ev), S,
+                                                _ptr(self.lnl), _ptr(ws), nb, s))
         ws, nb = self.ws_iw
         o = self.out.data_ptr()
         _check(lib.gwx_importance_weights(_ptr(self.lnl), ratio, _ptr(self.ev), 1, S, _ptr(self.w),

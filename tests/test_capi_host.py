@@ -179,3 +179,19 @@ def test_static_whitening_checks_as_gwx_whiten(lib):
         assert lib.gwx_last_error() == msg_ref
     st = lib.gwx_whiten_static(None, None, 4096, float("inf"), 20.0, 1, 3, 8192, None, None)
     assert st == -1 and b"must be positive" in lib.gwx_last_error()
+
+
+def test_tmarg_likelihood_validation(lib):
+    """The merger-time marginal rejects a bad grid on the host, before any device work."""
+    import ctypes
+    ids = (ctypes.c_int32 * 2)(0, 1)
+    def call(tc_lo, n_tc, u, N=2048):
+        return lib.gwx_log_likelihood_tmarg(0, None, 1, 2, N, None, 1024, 1024.0, 20.0, ids, 0.0, tc_lo, n_tc, u,
+                                            None, None, 4, None, None, 0, None)
+    assert call(1.0, 512, 3) == -2 and b"power of two" in lib.gwx_last_error()
+    assert call(1.0, 512, 128) == -2
+    assert call(1.0, 0, 16) == -2 and b"n_tc" in lib.gwx_last_error()
+    assert call(1.0, 4096, 16) == -2
+    assert call(float("nan"), 512, 16) == -1 and b"tc_lo" in lib.gwx_last_error()
+    assert call(1.0, 512, 16, N=3000) == -2
+    assert call(1.0, 512, 16) == -1 and b"NULL" in lib.gwx_last_error()   # valid grid: the NULL arrays are next

@@ -204,17 +204,14 @@ def test_base_normals(gwx):
 
 def test_proposal_stage(gwx):
     rng = np.random.default_rng(307)
-    S, E = 600, 4
-    offsets = np.array([0, 100, 100, 350, S], dtype=np.int64)
-    truth = workloads.random_theta(308, E, WL["prior"])
+    S = 600
     x = rng.normal(0, 1.2, (S, 8)).astype(np.float32)
     z = rng.normal(0, 1, (S, 8)).astype(np.float32)
     ss = rng.normal(0, 1, S).astype(np.float32)
-    th, lq, lr = gwx.flow_proposal(cuda(x), cuda(z), cuda(ss), MEAN, SCALE, WL["prior"], cuda(truth), cuda(offsets),
-                                   91, 3)
+    th, lq, lr = gwx.flow_proposal(cuda(x), cuda(z), cuda(ss), MEAN, SCALE, WL["prior"], 91, 3)
     _, coin = fl.base_normals(91, 3, np.arange(S))
     th_ref, lq_ref, lr_ref = fl.proposal_params(x.astype(np.float64), z.astype(np.float64), ss.astype(np.float64),
-                                                MEAN, SCALE, WL["prior"], truth, fl.event_of(offsets, S), coin)
+                                                MEAN, SCALE, WL["prior"], coin, fl.nuisance_uniforms(91, 3, np.arange(S)))
     th, lq, lr = host(th), host(lq), host(lr)
     assert np.array_equal(np.isfinite(lr), np.isfinite(lr_ref))
     assert 50 < np.isfinite(lr).sum() < S          # both branches exercised
@@ -259,12 +256,12 @@ def test_sample_posterior(gwx, sampler):
     fp, params = sampler
     K = fp.shape["layers"]
     E = 4
-    y, truth = _batch(330, E)
+    y, _ = _batch(330, E)
     offsets = np.array([0, 150, 150, 400, 700], dtype=np.int64)
-    th, lq, lr = fp.sample(cuda(y), cuda(truth), cuda(offsets), 2024, 9)
+    th, lq, lr = fp.sample(cuda(y), cuda(offsets), 2024, 9)
     th, lq, lr = host(th), host(lq), host(lr)
     feat = oracle_features(y, fp.shape["features"])
-    th_ref, lq_ref, lr_ref = fl.sample_posterior(feat, params, K, MEAN, SCALE, WL["prior"], truth, offsets, 2024, 9)
+    th_ref, lq_ref, lr_ref = fl.sample_posterior(feat, params, K, MEAN, SCALE, WL["prior"], offsets, 2024, 9)
     both = np.isfinite(lr) & np.isfinite(lr_ref)
     assert both.sum() >= 0.95 * min(np.isfinite(lr).sum(), np.isfinite(lr_ref).sum())
     assert np.mean(np.isfinite(lr) != np.isfinite(lr_ref)) < 0.01
@@ -272,16 +269,16 @@ def test_sample_posterior(gwx, sampler):
     x = fl.standardise(fl.coords(th[:, both]), MEAN, SCALE)
     x_ref = fl.standardise(fl.coords(th_ref[:, both]), MEAN, SCALE)
     assert np.max(np.abs(x - x_ref)) < 1e-3
-    for r in (2, 3, 5):
-        assert np.array_equal(th[r], th_ref[r])
+    for r in (2, 3, 5):                     # spins and t_c from the prior: FP64 on both sides
+        np.testing.assert_allclose(th[r], th_ref[r], rtol=0, atol=1e-14 * max(1.0, np.abs(th_ref[r]).max()))
 
 
 def test_sample_then_density_round_trip(gwx, sampler):
     fp, _ = sampler
     E = 3
-    y, truth = _batch(340, E)
+    y, _ = _batch(340, E)
     offsets = np.array([0, 300, 600, 900], dtype=np.int64)
-    th, lq, lr = fp.sample(cuda(y), cuda(truth), cuda(offsets), 5, 1)
+    th, lq, lr = fp.sample(cuda(y), cuda(offsets), 5, 1)
     ev = fl.event_of(offsets, 900)
     ok = np.isfinite(host(lr))
     lp = host(fp.log_prob(cuda(y[ev][ok]), th[:, torch.from_numpy(ok).cuda()].contiguous()))
@@ -292,10 +289,10 @@ def test_sample_posterior_across_chunks(gwx, sampler):
     fp, params = sampler
     K = fp.shape["layers"]
     E = 2
-    y, truth = _batch(350, E)
+    y, _ = _batch(350, E)
     S = (1 << 17) + 3000
     offsets = np.array([0, 70000, S], dtype=np.int64)
-    th, lq, lr = fp.sample(cuda(y), cuda(truth), cuda(offsets), 8, 2)
+    th, lq, lr = fp.sample(cuda(y), cuda(offsets), 8, 2)
     pick = np.r_[0:5, 69998:70003, (1 << 17) - 3:(1 << 17) + 3, S - 4:S]
     feat = oracle_features(y, fp.shape["features"])
     emb, layers = fl.split_params(params, K)
@@ -303,7 +300,7 @@ def test_sample_posterior_across_chunks(gwx, sampler):
     ev = fl.event_of(offsets, S)[pick]
     z, coin = fl.base_normals(8, 2, pick)
     x, ss = fl.sample(z, c[ev], layers)
-    _, lq_ref, _ = fl.proposal_params(x, z, ss, MEAN, SCALE, WL["prior"], truth, ev, coin)
+    _, lq_ref, _ = fl.proposal_params(x, z, ss, MEAN, SCALE, WL["prior"], coin, fl.nuisance_uniforms(8, 2, pick))
     assert np.all(np.abs(host(lq)[pick] - lq_ref) <= 5e-3 + 5e-4 * np.abs(lq_ref))
 
 
@@ -355,11 +352,10 @@ def test_scorer_with_the_flow_matches_the_separate_calls(gwx, sampler):
     y, th, _ = sim.step(7)
     sc = Scorer(wl, 3000, sim.psd, flow=fp)
     for e, S in ((0, 3000), (2, 1234)):
-        truth = th[:, e:e + 1].contiguous()
-        got = sc.score(y[e:e + 1], S, 11, truth=truth)
+        got = sc.score(y[e:e + 1], S, 11)
         offs = torch.tensor([0, S], dtype=torch.int64, device="cuda")
         theta, _, lr = gwx.sample_posterior(fp.shape, fp.params, fp.params16, fp.mean, fp.scale, wl["prior"],
-                                            y[e:e + 1].contiguous(), wl["fs"], wl["f_lo"], truth, offs, 55, 11)
+                                            y[e:e + 1].contiguous(), wl["fs"], wl["f_lo"], offs, 55, 11)
         lnl = gwx.log_likelihood(y[e:e + 1].contiguous(), sim.psd, wl["seg_len"], wl["fs"], wl["f_lo"], wl["dets"],
                                  0.0, theta, offs)
         _, ess, eff, lnz = gwx.importance_weights(lnl, offs, lr)
@@ -420,7 +416,7 @@ def test_external_context_matches_oracle_and_resnet_summary_trains(gwx, model):
         losses.append(float(host(net.train_step(yb, tb))[0]))
     assert np.mean(losses[-15:]) < np.mean(losses[:15]) - 0.3, (np.mean(losses[:15]), np.mean(losses[-15:]))
     offs = torch.tensor([0, 100, 250], dtype=torch.int64, device="cuda")
-    theta_s, lq, lr = net.sample(yb[:2].contiguous(), tb[:, :2].contiguous(), offs, 3, 0)
+    theta_s, lq, lr = net.sample(yb[:2].contiguous(), offs, 3, 0)
     ok = torch.isfinite(lr)
     lp = net.log_prob(yb[torch.tensor([0] * 100 + [1] * 150, device="cuda")][ok].contiguous(),
                       theta_s[:, ok].contiguous())

@@ -165,9 +165,11 @@ def test_coordinates_round_trip_through_the_proposal_map():
     mean, scale = r.mean(axis=0), r.std(axis=0)
     x = fl.standardise(r, mean, scale)
     coin = np.where(th[0] < th[1], 0.25, 0.75)     # the coin that reproduces each draw's order
-    truth = th.copy()
-    out, log_q, lr = fl.proposal_params(x, np.zeros((50, 8)), np.zeros(50), mean, scale, prior, truth,
-                                        np.arange(50), coin)
+    # the uniforms that reproduce each draw's merger time and spins
+    nuis = np.stack([(th[5] - prior["tc_lo"]) / (prior["tc_hi"] - prior["tc_lo"]),
+                     (th[2] - prior["chi_lo"]) / (prior["chi_hi"] - prior["chi_lo"]),
+                     (th[3] - prior["chi_lo"]) / (prior["chi_hi"] - prior["chi_lo"])], axis=1)
+    out, log_q, lr = fl.proposal_params(x, np.zeros((50, 8)), np.zeros(50), mean, scale, prior, coin, nuis)
     assert np.all(np.isfinite(lr))
     assert np.max(np.abs(out - th)) < 1e-9 * np.max(np.abs(th))
     # identity flow at z = 0: ln q_r = -4 ln 2 pi - sum ln scale
@@ -213,15 +215,33 @@ def test_sample_and_density_agree_on_the_proposal_density():
     th = workloads.random_theta(48, 4000, prior)
     r = fl.coords(th)
     mean, scale = r.mean(axis=0), r.std(axis=0)
-    truth = workloads.random_theta(49, E, prior)
     offsets = np.array([0, 5, 5, 40])
-    theta, log_q, lr = fl.sample_posterior(feat, params, K, mean, scale, prior, truth, offsets, 99, 1, fl.exact)
+    theta, log_q, lr = fl.sample_posterior(feat, params, K, mean, scale, prior, offsets, 99, 1, fl.exact)
     ev = fl.event_of(offsets, 40)
     ok = np.isfinite(lr)
     assert ok.sum() > 5
     lp = fl.log_prob(feat[ev], theta, params, K, mean, scale, fl.exact)
     assert np.max(np.abs(lp[ok] - log_q[ok])) < 1e-7
-    assert np.all(theta[2][ok] == truth[2][ev[ok]]) and np.all(theta[5] == truth[5][ev])
+
+
+def test_parameters_the_flow_does_not_model_follow_their_prior():
+    """Spins and t_c of flow draws are uniform over the prior's box, independent of the
+    flow's coordinates (so their prior-to-proposal ratio is one)."""
+    from scipy.stats import kstest
+    prior = dict(workloads.workload("small")["prior"], chi_lo=-0.5, chi_hi=0.5)
+    S = 20000
+    nuis = fl.nuisance_uniforms(5, 3, np.arange(S))
+    x = np.zeros((S, 8))
+    th = workloads.random_theta(6, 1, prior)
+    r = fl.coords(np.repeat(th, S, axis=1))
+    out, _, _ = fl.proposal_params(x, np.zeros((S, 8)), np.zeros(S), r[0], np.ones(8), prior, np.full(S, 0.75), nuis)
+    for row, lo, hi in ((5, prior["tc_lo"], prior["tc_hi"]), (2, prior["chi_lo"], prior["chi_hi"]),
+                        (3, prior["chi_lo"], prior["chi_hi"])):
+        assert kstest((out[row] - lo) / (hi - lo), "uniform").pvalue > 1e-3
+    assert abs(np.corrcoef(out[2], out[3])[0, 1]) < 0.03
+    assert abs(np.corrcoef(out[5], out[2])[0, 1]) < 0.03
+    _, coin = fl.base_normals(5, 3, np.arange(S))
+    assert abs(np.corrcoef(coin, nuis[:, 0])[0, 1]) < 0.03
 
 
 @pytest.mark.parametrize("rnd", ["exact", "bf16"])

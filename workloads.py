@@ -15,6 +15,8 @@ Workloads (synthetic stand-ins for the paper's real O3 HL background, Sec. 3.2):
   spins U[-0.99, 0.99], distance U[100, 3000] Mpc.
 * ``sweep``  -- H1+L1+V1, fs = 2048 Hz, 8 s windows (N = 16384), 8192 draws;
   background 128 s, Welch with 2 s segments, 50 % overlap, ``small``'s priors.
+* ``small_nonspinning`` -- ``small`` with spins fixed at zero, 512 draws: the
+  learned part's training batches and the events its posteriors are judged on.
 
 All: isotropic sky and orientation, phase and polarisation U[0, 2 pi), merger
 time U[T/2, 3T/4] within the window, parameter seed 1, noise seed 2.
@@ -47,7 +49,18 @@ WORKLOADS = {
                      _prior((5.0, 100.0), (-0.99, 0.99), (100.0, 3000.0), 4.0)),
     "sweep": _workload("sweep", 8192, ("H1", "L1", "V1"), 2048, 8.0, 128, 2.0,
                        _prior((10.0, 50.0), (-0.5, 0.5), (200.0, 2000.0), 8.0)),
+    # the learned part's generator and the events it is judged on: ``small`` with
+    # non-spinning sources (the paper's estimator has no spin parameters)
+    "small_nonspinning": _workload("small_nonspinning", 512, ("H1", "L1"), 1024, 2.0, 16, 1.0,
+                                   _prior((10.0, 50.0), (0.0, 0.0), (200.0, 2000.0), 2.0)),
 }
+
+
+def tc_grid(wl, oversample=16):
+    """(tc_lo, n_tc, oversample) of the merger-time marginal over the workload's prior
+    window [tc_lo, tc_hi): n_tc = (tc_hi - tc_lo) fs samples."""
+    p = wl["prior"]
+    return p["tc_lo"], int(round((p["tc_hi"] - p["tc_lo"]) * wl["fs"])), int(oversample)
 
 
 def workload(name, **overrides):
