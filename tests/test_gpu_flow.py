@@ -3,17 +3,14 @@ step, density and posterior sampler) with oracle.flow (needs a GPU).
 
 Tolerances.  Stage kernels: FP32 arithmetic on the same FP32 inputs (1e-5 relative;
 the conditioner input rows are bfloat16 roundings of FP32 values, bit-exact; the
-proposal map works in FP64 from the same FP32 draws, 1e-9).  Whole-flow results: the
-oracle rounds to bfloat16 at the same points as the GPU but accumulates in FP64, so an
-activation that lies within an FP32 accumulation error of a bfloat16 rounding boundary
-can round the other way (one bfloat16 ulp, 2^-8 relative, in a handful of the ~10^5
-activations); through the remaining layers such a flip moves a shift or log-scale by
-~2^-8 / sqrt(H) of its size.  Measured on a GB300 at these shapes: |d ln q| <= 1.2e-3
-(density), <= 6e-5 (draws), draws within 7e-5 in standardised units, gradients within
-2.5e-4 of each tensor's norm.  The bounds below (ln q within 5e-3 + 5e-4 |ln q|, draws
-within 1e-3, gradients within 1 % of each tensor's norm) leave room for other flips and
-stay far below what a wrong term, sign or index gives (a changed split, sign of s or
-dropped sum_s term moves these quantities by O(1)).
+proposal map works in FP64 from the same FP32 draws, 1e-9).  Whole-flow results
+(densities, draws, the loss and every element of every gradient tensor) are compared
+element by element against bounds propagated through the oracle's own chain from the
+FP32 rounding model (tests/rounding_bounds.py): the oracle rounds to bfloat16 at the
+same points as the GPU but accumulates in FP64, and each rounding either absorbs the
+accumulated difference (no rounding boundary within it: the two sides agree exactly)
+or carries it plus one bfloat16 ulp, so an element fails only if it differs by more
+than its own propagated bound.
 """
 import math
 
@@ -23,6 +20,8 @@ import pytest
 import workloads
 from oracle import flow as fl
 from oracle import learn
+
+import rounding_bounds as rb
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -88,9 +87,10 @@ def sampler(gwx, request):
     return _make_model(request.param, layers=5)
 
 
-def oracle_features(y, F, cross=True, lag=True):
-    """bfloat16-rounded features of windows y from the oracle's FP64 spectrum: log group
-    powers, then the cross-spectral columns, then the lag-one columns."""
+def oracle_features(y, F, cross=True, lag=True, rounded=True):
+    """bfloat16-rounded (or, with rounded False, the unrounded FP64) features of windows y
+    from the oracle's FP64 spectrum: log group powers, then the cross-spectral columns,
+    then the lag-one columns."""
     y = np.asarray(y, dtype=np.float64)
     k_lo = int(math.ceil(WL["f_lo"] * WL["N"] / WL["fs"] - 1e-9))
     f = learn.features(y, k_lo, GROUP, F)
@@ -101,7 +101,7 @@ def oracle_features(y, F, cross=True, lag=True):
             c = fn(y, k_lo, GROUP)
             f[:, col:col + c.shape[1]] = c
             col += c.shape[1]
-    return fl.round_bf16(f)
+    return fl.round_bf16(f) if rounded else f
 
 
 # ---------------------------------------------------------------- stage kernels
@@ -235,21 +235,49 @@ def test_log_prob(gwx, model):
     got = host(fp.log_prob(cuda(y), cuda(th)))
     feat = oracle_features(y, fp.shape["features"])
     ref = fl.log_prob(feat, th, params, 4, MEAN, SCALE)
-    assert np.all(np.abs(got - ref) <= 5e-3 + 5e-4 * np.abs(ref)), np.max(np.abs(got - ref))
+    x = fl.standardise(fl.coords(th), MEAN, SCALE)
+    v, bound = rb.log_prob(oracle_features(y, fp.shape["features"], rounded=False), x, params, 4,
+                           np.sum(np.log(SCALE)))
+    assert np.allclose(v, ref, rtol=1e-12, atol=1e-12)        # the bound's chain reproduces the oracle
+    _within(got, ref, bound, "ln q")
+
+
+def _within(got, ref, bound, what):
+    """Every element within its propagated bound (plus FP64 noise of the oracle)."""
+    err = np.abs(np.asarray(got, dtype=np.float64) - ref)
+    tol = bound + 1e-12 * np.abs(ref) + 1e-30
+    bad = err > tol
+    assert not bad.any(), (what, int(bad.sum()), float(err[bad].max()), float(tol[bad].min()),
+                           np.argwhere(bad)[:5].tolist())
+    return float(np.max(err / tol))
+
+
+def _lognormal_bound(z):
+    """|d ln N(z)| for base normals held in FP32 (Box-Muller radius in FP64, angle in FP32:
+    each within 8 x 2^-24 (|z| + 4))."""
+    e = 8.0 * 2.0 ** -24 * (np.abs(z) + 4.0)
+    return np.sum(np.abs(z) * e + 0.5 * e * e, axis=1)
 
 
 def test_train_step_loss_and_gradients(gwx, model):
+    """The training step's loss and every element of every gradient tensor against the
+    oracle's chain rule, each within its own propagated bound; the bounds themselves are
+    a small multiple of the FP32 accumulation error nearly everywhere."""
     fp, params = model
     y, th = _batch(320, 64)
     loss = host(fp.train_step(cuda(y), cuda(th), update=False))[0]
     feat = oracle_features(y, fp.shape["features"])
     x = fl.standardise(fl.coords(th), MEAN, SCALE)
     m_ref, _, g_ref = fl.loss_and_grads(feat, x, params, 4)
-    assert abs(loss - m_ref) <= 1e-3 + 1e-4 * abs(m_ref), (loss, m_ref)
+    m, mb, gv, gb = rb.loss_and_grads(oracle_features(y, fp.shape["features"], rounded=False), x, params, 4)
+    assert abs(m - m_ref) <= 1e-12 * abs(m_ref)
+    _within(loss, m_ref, mb, "loss")
     for t in range(len(params)):
         g = host(fp.grads[fp.offsets[t]:fp.offsets[t] + params[t].size]).reshape(params[t].shape)
-        err = np.linalg.norm(g - g_ref[t])
-        assert err <= 0.01 * np.linalg.norm(g_ref[t]) + 1e-6, (t, err, np.linalg.norm(g_ref[t]))
+        np.testing.assert_allclose(gv[t], g_ref[t], rtol=1e-12, atol=1e-14 * np.abs(g_ref[t]).max())
+        _within(g, g_ref[t], gb[t], "gradient tensor %d" % t)
+        # the bound stays informative: a fraction of the tensor's typical element
+        assert np.median(gb[t]) <= 0.25 * np.median(np.abs(g_ref[t])) + 1e-30, (t, np.median(gb[t]))
 
 
 def test_sample_posterior(gwx, sampler):
@@ -265,10 +293,15 @@ def test_sample_posterior(gwx, sampler):
     both = np.isfinite(lr) & np.isfinite(lr_ref)
     assert both.sum() >= 0.95 * min(np.isfinite(lr).sum(), np.isfinite(lr_ref).sum())
     assert np.mean(np.isfinite(lr) != np.isfinite(lr_ref)) < 0.01
-    assert np.all(np.abs(lq - lq_ref) <= 5e-3 + 5e-4 * np.abs(lq_ref))
+    S = int(offsets[-1])
+    ev = fl.event_of(offsets, S)
+    z, _ = fl.base_normals(2024, 9, np.arange(S))
+    (xb, ssb), (xe, sse) = rb.draws(oracle_features(y, fp.shape["features"], rounded=False), z, ev, params, K)
+    _within(lq, lq_ref, sse + _lognormal_bound(z), "ln q of the draws")
     x = fl.standardise(fl.coords(th[:, both]), MEAN, SCALE)
     x_ref = fl.standardise(fl.coords(th_ref[:, both]), MEAN, SCALE)
-    assert np.max(np.abs(x - x_ref)) < 1e-3
+    np.testing.assert_allclose(xb[both], x_ref, rtol=1e-9, atol=1e-9)
+    _within(x, x_ref, xe[both] + 1e-9 * np.abs(x_ref), "draws")
     for r in (2, 3, 5):                     # spins and t_c from the prior: FP64 on both sides
         np.testing.assert_allclose(th[r], th_ref[r], rtol=0, atol=1e-14 * max(1.0, np.abs(th_ref[r]).max()))
 
@@ -301,7 +334,8 @@ def test_sample_posterior_across_chunks(gwx, sampler):
     z, coin = fl.base_normals(8, 2, pick)
     x, ss = fl.sample(z, c[ev], layers)
     _, lq_ref, _ = fl.proposal_params(x, z, ss, MEAN, SCALE, WL["prior"], coin, fl.nuisance_uniforms(8, 2, pick))
-    assert np.all(np.abs(host(lq)[pick] - lq_ref) <= 5e-3 + 5e-4 * np.abs(lq_ref))
+    _, (_, sse) = rb.draws(oracle_features(y, fp.shape["features"], rounded=False), z, ev, params, K)
+    _within(host(lq)[pick], lq_ref, sse + _lognormal_bound(z), "ln q across chunks")
 
 
 def test_training_lowers_the_loss(gwx):
@@ -405,7 +439,9 @@ def test_external_context_matches_oracle_and_resnet_summary_trains(gwx, model):
     x = fl.standardise(fl.coords(th), MEAN, SCALE)
     z, ss, _ = fl.density(x, bf16_to_f64(bits), layers)
     ref = fl.log_normal(z) - ss - np.sum(np.log(SCALE))
-    assert np.all(np.abs(got - ref) <= 5e-3 + 5e-4 * np.abs(ref)), np.max(np.abs(got - ref))
+    v, bound = rb.log_prob(None, x, params, 4, np.sum(np.log(SCALE)), ctx=bf16_to_f64(bits))
+    assert np.allclose(v, ref, rtol=1e-12, atol=1e-12)
+    _within(got, ref, bound, "ln q with an external context")
     # flow + ResNet-1D summary: the loss falls
     sim = Simulator(dict(WL, B=64))
     net = FlowPosterior(dict(WL, B=64), layers=2, hidden=64, context=32, group=GROUP, seed=8, lr=1e-3,
