@@ -235,6 +235,28 @@ int gwx_unwhiten(const float* y, const double* psd, int64_t seg_len, double fs, 
 int gwx_whiten_static(const float* d, const double* psd, int64_t seg_len, double fs, double f_lo,
                       int64_t B, int D, int64_t N, float* y, void* stream);
 
+/* ---- launch shapes of the fused pass ------------------------------------------------
+ * gwx_simulate_prepared can run its fused kernel in several launch shapes that do the
+ * same arithmetic and give the same output bit for bit: bit 0 of a shape selects
+ * Stockham passes that alternate between two shared-memory window buffers (one block
+ * barrier per pass, twice the shared memory) instead of passes in place in one (two
+ * barriers per pass); bits 1-2 the resident blocks per SM (0: as many as fit, else 1..3,
+ * capped at what fits).  Which is fastest depends on the window length and the number
+ * of detectors (e.g. through how much L1 the larger shared-memory carve-out leaves), so:
+ * gwx_simulate_autotune builds the whitening filter from psd into the workspace, then
+ *   times each candidate shape of the fused pass on the caller's batch (its per-draw
+ *   coefficients already in the workspace from gwx_prepare_batch or gwx_prepare_theta;
+ *   y is overwritten with the batch) and records the fastest for (N, D), process-wide;
+ *   *shape_out (optional) receives it.  It synchronises with the stream.  Arguments as
+ *   gwx_simulate_prepared; B >= 1.
+ * gwx_simulate_shape: shape >= 0 records that shape for (N, D), -1 forgets the record
+ *   (back to the default: two buffers for N >= 16384, else in place), -2 only asks;
+ *   returns the shape gwx_simulate_prepared now uses for (N, D), or a negative status. */
+int gwx_simulate_autotune(const float* noise, int64_t L, const double* psd, int64_t seg_len, double fs,
+                          double f_lo, int D, int64_t B, int64_t N, const int64_t* offsets, float* y,
+                          void* workspace, size_t workspace_bytes, int* shape_out, void* stream);
+int gwx_simulate_shape(int64_t N, int D, int shape);
+
 /* ---- A1-A3, A6, A7 fused: one whitened batch --------------------------------
  * The whole per-batch pass of Sec. 3.2 in one call: prior draws (as
  * gwx_sample_prior with `seed`, `step`), TaylorF2 waveforms, projection and

@@ -23,7 +23,7 @@ M1, M2, CHI1, CHI2, DIST, TC, PHIC, THETAJN, PSI, RA, DEC = range(11)
 NPARAM = 11
 
 __all__ = ["GwxError", "version", "init", "detector_geometry", "sample_prior", "generate_waveforms", "project",
-           "colored_noise", "welch_psd", "inject", "inject_padded", "simulate_batch_padded", "whiten", "unwhiten", "simulate_batch", "log_likelihood", "log_likelihood_tmarg",
+           "colored_noise", "welch_psd", "inject", "inject_padded", "simulate_batch_padded", "whiten", "unwhiten", "simulate_batch", "simulate_shape", "log_likelihood", "log_likelihood_tmarg",
            "importance_weights", "gemm_bf16", "dense_bf16", "dense_bf16_backward", "gemm_autotune", "spectral_features",
            "cross_features", "lag_features", "proposal_targets",
            "gauss_nll", "adamw", "adamw_clip", "skymap", "vicreg", "retime", "sample_proposal", "device_status", "selftest_bounded_wait", "rfft", "irfft",
@@ -276,6 +276,15 @@ def log_likelihood(y_data, psd, seg_len, fs, f_lo, dets, gmst, theta, event_offs
     _check(lib.gwx_log_likelihood(approximant, _ptr(y_data), E, D, N, _ptr(psd), seg_len, fs, f_lo, ids, gmst,
                                   _ptr(theta), _ptr(event_offsets), S, _ptr(out), _ptr(ws), nb, _stream()))
     return out
+
+
+def simulate_shape(N, D, shape=-2):
+    """The fused pass's launch shape for windows of N samples and D detectors: shape >= 0
+    records one, -1 forgets the record, -2 (default) only asks; returns the shape in use."""
+    st = _lib.load().gwx_simulate_shape(int(N), int(D), int(shape))
+    if st < 0:
+        _check(st)
+    return st
 
 
 def log_likelihood_tmarg(y_data, psd, seg_len, fs, f_lo, dets, gmst, tc_lo, n_tc, oversample, theta, event_offsets,

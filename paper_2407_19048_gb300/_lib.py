@@ -66,6 +66,9 @@ SIGNATURES = {
     "gwx_log_likelihood_workspace": (c_size, [c_i64, c_int, c_i64, c_i64]),
     "gwx_log_likelihood": (c_int, [c_int, c_vp, c_i64, c_int, c_i64, c_vp, c_i64, c_dbl, c_dbl, c_i32p, c_dbl,
                                    c_vp, c_vp, c_i64, c_vp, c_vp, c_size, c_vp]),
+    "gwx_simulate_autotune": (c_int, [c_vp, c_i64, c_vp, c_i64, c_dbl, c_dbl, c_int, c_i64, c_i64, c_vp, c_vp, c_vp,
+                                      c_size, ctypes.POINTER(c_int), c_vp]),
+    "gwx_simulate_shape": (c_int, [c_i64, c_int, c_int]),
     "gwx_log_likelihood_tmarg": (c_int, [c_int, c_vp, c_i64, c_int, c_i64, c_vp, c_i64, c_dbl, c_dbl, c_i32p,
                                          c_dbl, c_dbl, c_i64, c_int, c_vp, c_vp, c_i64, c_vp, c_vp, c_size, c_vp]),
     "gwx_importance_weights_workspace": (c_size, [c_i64]),

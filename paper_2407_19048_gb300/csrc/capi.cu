@@ -460,6 +460,67 @@ int gwx_simulate_prepared(const float* noise, int64_t L, const double* psd, int6
                   "simulate");
 }
 
+int gwx_simulate_shape(int64_t N, int D, int shape) {
+  GWX_TRY(check_window(N));
+  if (D < 1 || D > GWX_MAX_DET) return fail(GWX_ESHAPE, "D=%d outside [1, %d]", D, GWX_MAX_DET);
+  if (shape < -2 || shape > 7) return fail(GWX_EINVAL, "shape %d outside [-2, 7]", shape);
+  if (shape >= -1) sim_shape_set(N, D, shape);
+  return sim_shape_for(N, D);
+}
+
+int gwx_simulate_autotune(const float* noise, int64_t L, const double* psd, int64_t seg_len, double fs, double f_lo,
+                          int D, int64_t B, int64_t N, const int64_t* offsets, float* y, void* workspace,
+                          size_t workspace_bytes, int* shape_out, void* stream) {
+  int k_lo = 0;
+  GWX_TRY(check_sim_shapes(D, L, B, N, fs, f_lo, &k_lo));
+  GWX_TRY(check_psd_args(seg_len, N));
+  if (B < 1) return fail(GWX_ESHAPE, "autotune needs at least one draw");
+  if (!noise || !psd || !y || !offsets) return fail(GWX_EINVAL, "NULL array");
+  GWX_ALIGN8(psd);
+  GWX_ALIGN8(y);
+  GWX_ALIGN8(offsets);
+  GWX_TRY(check_ws(workspace, workspace_bytes, gwx_simulate_batch_workspace(D, B, N)));
+  GWX_TRY(ensure_init());
+  cudaStream_t s = as_stream(stream);
+  float* W = reinterpret_cast<float*>(workspace);
+  float2* Wp = sim_packed(workspace, D, N);
+  GWX_TRY(launched(launch_whiten_filter(psd, D, seg_len, fs, k_lo, N, W, s), "whiten filter"));
+  GWX_TRY(launched(launch_packed_filter(W, D, N, Wp, s), "packed filter"));
+  const DrawCoef* coef = sim_coef(workspace, D, N);
+  // two-buffer passes or not x all resident blocks per SM or one
+  const int candidates[] = {0, 1, 2, 3};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(cudaGetLastError(), "autotune event");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(cudaGetLastError(), "autotune event");
+  }
+  int best = -1;
+  float best_ms = 0.f;
+  cudaError_t err = cudaSuccess;
+  for (int c : candidates) {
+    err = launch_simulate_fused(coef, noise, L, offsets, W, Wp, k_lo, D, B, N, fs, y, s, c);   // warm-up
+    if (err == cudaSuccess) err = cudaEventRecord(e0, s);
+    for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep)
+      err = launch_simulate_fused(coef, noise, L, offsets, W, Wp, k_lo, D, B, N, fs, y, s, c);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    if (err != cudaSuccess) break;
+    if (best < 0 || ms < best_ms) {
+      best = c;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return cuda_fail(err, "simulate autotune");
+  sim_shape_set(N, D, best);
+  if (shape_out) *shape_out = best;
+  return GWX_OK;
+}
+
 int gwx_simulate_batch(const gwx_prior* prior, uint64_t seed, uint32_t step, const float* noise, int64_t L,
                        const double* psd, int64_t seg_len, double fs, double f_lo, const int32_t* det_ids, int D,
                        double gmst, int64_t B, int64_t N, float* y, double* theta, int64_t* offsets, void* workspace,

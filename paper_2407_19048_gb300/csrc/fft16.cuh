@@ -107,6 +107,57 @@ __device__ __forceinline__ void pass16(uint32_t x, int t) {
   __syncthreads();
 }
 
+// The same pass out of place: reads src, writes dst, one barrier (the two buffers
+// alternate, so no thread can overwrite an element another has yet to read).
+template <int LOGN, int R, int Ns, bool INV>
+__device__ __forceinline__ void pass16_pp(uint32_t src, uint32_t dst, int t) {
+  constexpr int n = 1 << LOGN;
+  constexpr int NBT = 16 / R;
+  constexpr int nR = n / R;
+  float2 v[NBT][R];
+#pragma unroll
+  for (int i = 0; i < NBT; ++i) {
+    const int j = t + i * (n / 16);
+    load_strided<R, nR>(src, j, v[i]);
+    if constexpr (Ns > 1) {
+      float2 w[R];
+      pass_twiddles<R, Ns, INV>(j & (Ns - 1), w);
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[i][r] = cmul(v[i][r], w[r]);
+    }
+    dftR<R, INV, false>(v[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < NBT; ++i) store_pass<R, Ns>(dst, t + i * (n / 16), v[i]);
+  __syncthreads();
+}
+
+// Middle passes alternating between two buffers; run(a, b) starts from a and returns the
+// buffer that holds the result.
+template <int LOGN, int p, int PMAX>
+struct FwdMiddlePP {
+  static __device__ __forceinline__ uint32_t run(uint32_t a, uint32_t b, int t) {
+    if constexpr (p <= PMAX) {
+      pass16_pp<LOGN, 8, (1 << (3 * p)), false>(a, b, t);
+      return FwdMiddlePP<LOGN, p + 1, PMAX>::run(b, a, t);
+    } else {
+      return a;
+    }
+  }
+};
+
+template <int LOGN, int p, int PMAX, int RL>
+struct InvMiddlePP {
+  static __device__ __forceinline__ uint32_t run(uint32_t a, uint32_t b, int t) {
+    if constexpr (p <= PMAX) {
+      pass16_pp<LOGN, 8, RL * (1 << (3 * (p - 1))), true>(a, b, t);
+      return InvMiddlePP<LOGN, p + 1, PMAX, RL>::run(b, a, t);
+    } else {
+      return a;
+    }
+  }
+};
+
 // Middle passes of the forward transform: radix 8 with Ns = 8^p, p = 1 .. P-2.
 template <int LOGN, int p, int PMAX>
 struct FwdMiddle {

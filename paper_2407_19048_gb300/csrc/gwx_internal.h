@@ -65,7 +65,12 @@ cudaError_t launch_rfft_rows(const float* x, int64_t R, int64_t N, float2* X, cu
 cudaError_t launch_irfft_rows(const float2* X, int64_t R, int64_t N, float* x, cudaStream_t s);
 cudaError_t launch_simulate_fused(const DrawCoef* coef, const float* noise, int64_t L, const int64_t* offsets,
                                   const float* W, const float2* Wp, int k_lo, int D, int64_t B, int64_t N, double fs,
-                                  float* y, cudaStream_t s);
+                                  float* y, cudaStream_t s, int shape = -1);
+// Launch shape of the fused pass for windows of N samples and D detectors (bit 0: two
+// shared buffers, bits 1-2: blocks per SM, 0 = the occupancy limit): the tuned choice, or
+// the default; sim_shape_set records one (a negative shape forgets it).
+int sim_shape_for(int64_t N, int D);
+void sim_shape_set(int64_t N, int D, int shape);
 // yy: E doubles of scratch for the per-event sum of |Y|^2 over the band.
 // Per-event data norms (E x 8 FP64 partials in yy_part, loglike_norm_bytes(E)) and
 // the fused per-sample set-up + likelihood.

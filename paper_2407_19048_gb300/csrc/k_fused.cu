@@ -6,6 +6,10 @@
 // complex points each; the waveform of a bin is evaluated once and projected onto
 // all D detectors, so the frequency-domain stage costs one phase/amplitude
 // evaluation per bin plus one complex exponential per detector.
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "fft16.cuh"
 #include "waveform.cuh"
 
@@ -77,11 +81,14 @@ __device__ __forceinline__ void wave_bin(const DrawCoef& c, int k, int k_lo, flo
 }
 
 // One block per draw (persistent over draws), n/16 threads.  The D windows go
-// through one n-point shared buffer in turn; the waveform values of the bins a
+// through the shared window buffer in turn; the waveform values of the bins a
 // thread owns are computed once per draw and shared by the detectors.
+// PP: the Stockham passes alternate between two n-point buffers (one barrier per pass)
+// instead of running in place in one (two barriers per pass, half the shared memory);
+// both forms do the same arithmetic, so their outputs agree bit for bit.
 // VEC: the background rows are 8-byte aligned (aligned base, even L), so the crop is
 // read as float pairs; otherwise it is read one float at a time.
-template <int LOGN, bool VEC>
+template <int LOGN, bool VEC, bool PP>
 __global__ void __launch_bounds__((1 << LOGN) / 16, LOGN >= 13 ? 1 : 2)
     k_simulate(const DrawCoef* __restrict__ coef, const float* __restrict__ noise, int64_t L,
                const int64_t* __restrict__ offsets, const float* __restrict__ W, const float2* __restrict__ Wp,
@@ -92,11 +99,11 @@ __global__ void __launch_bounds__((1 << LOGN) / 16, LOGN >= 13 ? 1 : 2)
   constexpr int64_t F = n + 1;
   extern __shared__ float2 sm[];
   __shared__ DrawCoef sc;
-  float2 (*wv)[T] = reinterpret_cast<float2 (*)[T]>(sm + n);   // 16 x T waveform values
+  float2 (*wv)[T] = reinterpret_cast<float2 (*)[T]>(sm + (PP ? 2 : 1) * n);   // 16 x T waveform values
 #define WIDX(s, h, r) (((s) * 2 + (h)) * RL + (r))
   const int t = threadIdx.x;
   const int lane = t & 31;
-  const uint32_t x = smem_addr(sm);
+  const uint32_t x = smem_addr(sm), x2 = x + 8u * (uint32_t)n;
   const float inv_n = 1.0f / (float)n;
   for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
     for (int i = t; i < (int)(sizeof(DrawCoef) / 16); i += T)
@@ -159,7 +166,13 @@ __global__ void __launch_bounds__((1 << LOGN) / 16, LOGN >= 13 ? 1 : 2)
         }
       }
       __syncthreads();
-      FwdMiddle<LOGN, 1, P - 2>::run(x, t);
+      uint32_t xf = x;
+      if constexpr (PP) {
+        xf = FwdMiddlePP<LOGN, 1, P - 2>::run(x, x2, t);
+      } else {
+        FwdMiddle<LOGN, 1, P - 2>::run(x, t);
+      }
+      const uint32_t xi = PP ? (xf == x ? x2 : x) : x;
 
       // last forward pass (radix RL, Ns = NB) on butterfly pairs, frequency-domain
       // step and first inverse pass, all in registers
@@ -172,8 +185,8 @@ __global__ void __launch_bounds__((1 << LOGN) / 16, LOGN >= 13 ? 1 : 2)
       for (int s = 0; s < SLOTS; ++s) {
         const int p = t + s * T;
         const int jA = p, jB = p ? NB - p : NB / 2;
-        load_strided<RL, NB>(x, jA, vA[s]);
-        load_strided<RL, NB>(x, jB, vB[s]);
+        load_strided<RL, NB>(xf, jA, vA[s]);
+        load_strided<RL, NB>(xf, jB, vB[s]);
         if constexpr (NB > 1) {
           float2 w[RL];
           pass_twiddles<RL, NB, false>(jA, w);
@@ -210,15 +223,22 @@ __global__ void __launch_bounds__((1 << LOGN) / 16, LOGN >= 13 ? 1 : 2)
         dftR<RL, true, false>(vA[s]);
         dftR<RL, true, false>(vB[s]);
       }
-      __syncthreads();   // every read of the last forward pass precedes the writes below
+      // in place, every read of the last forward pass must precede the writes below; with
+      // two buffers the first inverse pass writes the other one
+      if constexpr (!PP) __syncthreads();
 #pragma unroll
       for (int s = 0; s < SLOTS; ++s) {
         const int p = t + s * T;
-        store_pass<RL, 1>(x, p, vA[s]);
-        store_pass<RL, 1>(x, p ? NB - p : NB / 2, vB[s]);
+        store_pass<RL, 1>(xi, p, vA[s]);
+        store_pass<RL, 1>(xi, p ? NB - p : NB / 2, vB[s]);
       }
       __syncthreads();
-      InvMiddle<LOGN, 1, P - 2, RL>::run(x, t);
+      uint32_t xl = x;
+      if constexpr (PP) {
+        xl = InvMiddlePP<LOGN, 1, P - 2, RL>::run(xi, xf, t);
+      } else {
+        InvMiddle<LOGN, 1, P - 2, RL>::run(x, t);
+      }
 
       // last inverse pass (radix 8, Ns = n/8), output straight to the whitened batch
       float2* out = reinterpret_cast<float2*>(y + (b * D + d) * N);
@@ -226,7 +246,7 @@ __global__ void __launch_bounds__((1 << LOGN) / 16, LOGN >= 13 ? 1 : 2)
       for (int i = 0; i < 2; ++i) {
         const int j = t + i * T;
         float2 v[8];
-        load_strided<8, n / 8>(x, j, v);
+        load_strided<8, n / 8>(xl, j, v);
         float2 w[8];
         pass_twiddles<8, n / 8, true>(j, w);
 #pragma unroll
@@ -241,36 +261,66 @@ __global__ void __launch_bounds__((1 << LOGN) / 16, LOGN >= 13 ? 1 : 2)
 #undef WIDX
 }
 
-template <int LG, bool VEC>
+// Launch shapes of the fused pass (all give the same output bit for bit): bit 0 selects
+// the two-buffer passes, bits 1-2 the resident blocks per SM (1 .. the occupancy limit,
+// 0 = the limit).  The autotuner times them per (N, D) and records its choice here.
+std::mutex g_sim_tune_mu;
+std::map<std::pair<int64_t, int>, int> g_sim_tune;
+
+int sim_default_shape(int64_t N) { return N >= 16384 ? 1 : 0; }
+
+int sim_shape_for(int64_t N, int D) {
+  std::lock_guard<std::mutex> lk(g_sim_tune_mu);
+  auto it = g_sim_tune.find({N, D});
+  return it == g_sim_tune.end() ? sim_default_shape(N) : it->second;
+}
+
+void sim_shape_set(int64_t N, int D, int shape) {
+  std::lock_guard<std::mutex> lk(g_sim_tune_mu);
+  if (shape < 0)
+    g_sim_tune.erase({N, D});
+  else
+    g_sim_tune[{N, D}] = shape;
+}
+
+template <int LG, bool VEC, bool PP>
 static cudaError_t launch_simulate_lg(const DrawCoef* coef, const float* noise, int64_t L, const int64_t* offsets,
                                       const float* W, const float2* Wp, int k_lo, int D, int64_t B, float* y,
-                                      cudaStream_t s) {
+                                      int per_sm_want, cudaStream_t s) {
   constexpr int NT = Plan16<LG>::T;
-  // one window at a time plus 16 waveform values per thread
-  const size_t smem = (size_t)(1 << LG) * sizeof(float2) + (size_t)16 * NT * sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(k_simulate<LG, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // one (or two, PP) window buffers plus 16 waveform values per thread
+  const size_t smem = (size_t)(PP ? 2 : 1) * (1 << LG) * sizeof(float2) + (size_t)16 * NT * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(k_simulate<LG, VEC, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_simulate<LG, VEC>, NT, smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_simulate<LG, VEC, PP>, NT, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  if (per_sm_want > 0 && per_sm_want < per_sm) per_sm = per_sm_want;
   int64_t grid = (int64_t)sms * per_sm;
   if (grid > B) grid = B;
-  k_simulate<LG, VEC><<<(unsigned)grid, NT, smem, s>>>(coef, noise, L, offsets, W, Wp, k_lo, D, B, y);
+  k_simulate<LG, VEC, PP><<<(unsigned)grid, NT, smem, s>>>(coef, noise, L, offsets, W, Wp, k_lo, D, B, y);
   return cudaGetLastError();
 }
 
 cudaError_t launch_simulate_fused(const DrawCoef* coef, const float* noise, int64_t L, const int64_t* offsets,
                                   const float* W, const float2* Wp, int k_lo, int D, int64_t B, int64_t N, double fs,
-                                  float* y, cudaStream_t s) {
+                                  float* y, cudaStream_t s, int shape) {
   if (B <= 0) return cudaSuccess;
+  if (shape < 0) shape = sim_shape_for(N, D);
+  const bool pp = (shape & 1) != 0;
+  const int per_sm = (shape >> 1) & 3;
   const bool vec = ((uintptr_t)noise % 8 == 0) && (L % 2 == 0);
   return dispatch_log<7, 13>(ilog2_exact(N / 2), [&](auto cst) {
     constexpr int LG = decltype(cst)::value;
-    return vec ? launch_simulate_lg<LG, true>(coef, noise, L, offsets, W, Wp, k_lo, D, B, y, s)
-               : launch_simulate_lg<LG, false>(coef, noise, L, offsets, W, Wp, k_lo, D, B, y, s);
+    if (pp)
+      return vec ? launch_simulate_lg<LG, true, true>(coef, noise, L, offsets, W, Wp, k_lo, D, B, y, per_sm, s)
+                 : launch_simulate_lg<LG, false, true>(coef, noise, L, offsets, W, Wp, k_lo, D, B, y, per_sm, s);
+    return vec ? launch_simulate_lg<LG, true, false>(coef, noise, L, offsets, W, Wp, k_lo, D, B, y, per_sm, s)
+               : launch_simulate_lg<LG, false, false>(coef, noise, L, offsets, W, Wp, k_lo, D, B, y, per_sm, s);
   });
 }
 

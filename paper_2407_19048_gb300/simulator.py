@@ -141,6 +141,26 @@ class Simulator:
         self._filter_version[self._slot] = self._psd_version
         self.launches += self.LAUNCHES["prepare"] + self.LAUNCHES["simulate"]
 
+    def autotune(self, step=0):
+        """Time the fused pass's launch shapes (bit-identical outputs) on a batch of this
+        simulator's workload and record the fastest for its (N, D); returns the shape.
+        Synchronises; call it before timing or capturing steps."""
+        import torch
+        if self._since_bg is None:
+            self.background(step)
+            self._since_bg = 0
+        slot = self._slot
+        self.prepare(step, slot)
+        ws, nb = self._ws_sim[slot]
+        shape = ctypes.c_int(-1)
+        _check(self.lib.gwx_simulate_autotune(_ptr(self.noise), self.L, _ptr(self.psd), self.M, self.fs, self.f_lo,
+                                              self.D, self.B, self.N, _ptr(self._offsets[slot]), _ptr(self._y[slot]),
+                                              _ptr(ws), nb, ctypes.byref(shape), _stream()))
+        self._filter_version[slot] = self._psd_version
+        self._ready = None
+        torch.cuda.current_stream(self.dev).synchronize()
+        return shape.value
+
     def step(self, step, mark=None):
         """One batch: returns (y [B][D][N], theta [11][B], offsets [B]) (device tensors).
 

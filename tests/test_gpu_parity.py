@@ -527,3 +527,29 @@ def test_simulator_step_captures_in_a_cuda_graph(gwx):
     np.testing.assert_array_equal(host(off), host(off0))
     np.testing.assert_array_equal(host(th), host(th0))
     np.testing.assert_array_equal(host(y), host(y0))
+
+
+@pytest.mark.parametrize("name", ["small", "hl3", "sweep"])
+def test_simulate_launch_shapes_are_bit_identical_and_autotuned(gwx, name):
+    """Every launch shape of the fused pass (two-buffer or in-place passes, all or one
+    resident block per SM) gives the same batch bit for bit; the autotuner picks one of
+    them for the workload's (N, D) and the simulator then uses it."""
+    import paper_2407_19048_gb300.simulator as S
+    wl = workloads.workload(name, B=min(workloads.workload(name)["B"], 1024))
+    D, N = len(wl["dets"]), wl["N"]
+    default = gwx.simulate_shape(N, D, -1)
+    assert default == (1 if N >= 16384 else 0)
+    sim = S.Simulator(wl)
+    outs = []
+    for shape in (0, 1, 2, 3):
+        assert gwx.simulate_shape(N, D, shape) == shape
+        y, th, off = sim.step(5)
+        outs.append(y.clone())
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+    gwx.simulate_shape(N, D, -1)
+    picked = sim.autotune(step=5)
+    assert picked in (0, 1, 2, 3) and gwx.simulate_shape(N, D) == picked
+    y, _, _ = sim.step(5)
+    assert torch.equal(y, outs[0])
+    gwx.simulate_shape(N, D, -1)

@@ -58,3 +58,46 @@ def test_map_normalisation_and_weights():
     # a single sample puts all its mass in its own pixel
     m3 = sk.skymap(ra[:1], dec[:1], None, 16)
     assert m3.max() == 1.0 and np.argmax(m3) == sk.ang2pix_nest(16, math.pi / 2 - dec[0], ra[0])
+
+
+def test_pixel_centres_invert_the_pinned_pixel_index():
+    for nside in (1, 2, 4, 8, 16, 32):
+        for p in range(12 * nside * nside):
+            assert sk.ang2pix_nest(nside, *sk.pix2ang_nest(nside, p)) == p
+
+
+def test_pixel_centres_lie_on_the_rings():
+    """4 nside - 1 iso-latitude rings: 4, 8, .., 4 (nside - 1) pixels in each polar ring,
+    4 nside in each of the 2 nside + 1 rings of the belt; the centres balance (the sum of
+    their unit vectors is zero) and their z take the rings' values."""
+    nside = 8
+    ra, sd = sk.pixel_centres(nside)
+    z, counts = np.unique(np.round(sd, 12), return_counts=True)
+    assert len(z) == 4 * nside - 1
+    cap = [4 * i for i in range(1, nside)]
+    assert list(counts) == cap + [4 * nside] * (2 * nside + 1) + cap[::-1]
+    v = np.stack([np.sqrt(1 - sd ** 2) * np.cos(ra), np.sqrt(1 - sd ** 2) * np.sin(ra), sd])
+    assert np.abs(v.sum(axis=1)).max() < 1e-9
+    # the first north-cap ring sits at z = 1 - 1 / (3 nside^2)
+    assert abs(z.max() - (1 - 1 / (3 * nside ** 2))) < 1e-12
+
+
+def test_density_map_of_a_factorised_density():
+    """A flow with identity layers is the standard normal in standardised coordinates, so
+    its density factorises: the sky map is the product of the two normal factors of
+    (RA, sin dec), whatever the other coordinates are held at."""
+    mean = np.array([20.0, 0.6, 1000.0, 0.0, 2.5, 0.3, 3.0, 3.0])
+    scale = np.array([5.0, 0.2, 400.0, 0.5, 0.7, 0.25, 1.8, 1.8])
+
+    def log_q(r):
+        x = (r - mean) / scale
+        return -0.5 * np.sum(x * x, axis=1)
+
+    nside = 16
+    ra, sd = sk.pixel_centres(nside)
+    want = np.exp(-0.5 * ((ra - mean[4]) / scale[4]) ** 2 - 0.5 * ((sd - mean[5]) / scale[5]) ** 2)
+    want /= want.sum()
+    for other in ([15.0, 0.9, 600.0, 0.2, 0.0, 0.0, 1.0, 5.0], [30.0, 0.3, 1500.0, -0.5, 0.0, 0.0, 4.0, 0.5]):
+        m = sk.density_map(log_q, other, nside)
+        np.testing.assert_allclose(m, want, rtol=1e-12, atol=1e-300)
+    assert abs(m.sum() - 1.0) < 1e-12
