@@ -694,6 +694,21 @@ def flow_leg(gwx, torch, rank, steps=12000, events=64, pp_events=200, pp_samples
                 times.append(time.perf_counter() - a0)
         times.sort()
         sky[str(nside)] = times[len(times) // 2] * 1e3
+    # sky density (the paper's map: 20,000 draws, then the flow's density at every pixel;
+    # ~0.6 / 1.2 / 2.4 s at NSIDE 32 / 64 / 128 on an A40)
+    sky_density = {}
+    for nside in (32, 64, 128):
+        times = []
+        for rep in range(13):
+            torch.cuda.synchronize()
+            a0 = time.perf_counter()
+            theta1, lq1, _ = fp.sample(y1, one, 19, rep, S=20000)
+            fp.skymap(y1, theta1, lq1, nside)
+            torch.cuda.synchronize()
+            if rep >= 3:
+                times.append(time.perf_counter() - a0)
+        times.sort()
+        sky_density[str(nside)] = times[len(times) // 2] * 1e3
     # config 4: importance sampling, flow vs prior, 64 events x U{2000..50000} draws
     counts = workloads.ragged_counts(4, events, 2000, 50000)
     isamp = is_compare(gwx, torch, fp, wl_ev, y_ev, sim_ev.psd, counts, grid)
@@ -742,8 +757,11 @@ def flow_leg(gwx, torch, rank, steps=12000, events=64, pp_events=200, pp_samples
             "simulations_per_s": hist["steps_run"] * batch / train_s, "schedule": hist,
             "train_step_ms": step_ms, "train_step_graph_ms": step_graph_ms,
             "sample_20000_ms": {"p50": lat[len(lat) // 2] * 1e3, "min": lat[0] * 1e3, "max": lat[-1] * 1e3},
+            "skymap_density_20000_ms": dict(sky_density, note="sample_posterior 20k + flow_skymap (the flow's density "
+                                                              "at every HEALPix pixel centre), median of 10, host time"),
             "skymap_20000_ms": dict(sky, note="sample_posterior 20k + log_likelihood_tmarg + importance_weights + "
-                                              "skymap (HEALPix nested, importance-weighted), median of 10, host time"),
+                                              "skymap (HEALPix nested, importance-weighted histogram), median of 10, "
+                                              "host time"),
             "importance_sampling": isamp,
             "pp_test": {"events": pp_events, "draws_per_event": pp_samples, "ks_distance": ks,
                         "ks_95pct_critical": 1.36 / math.sqrt(pp_events),

@@ -602,6 +602,23 @@ int gwx_sample_posterior(const gwx_flow_shape* shape, const float* params, const
                          uint32_t counter, double* theta, double* log_q, double* log_ratio, void* workspace,
                          size_t workspace_bytes, void* stream);
 
+/* The flow's sky density over HEALPix pixels (Sec. 5: the density is evaluated at every
+ * pixel of the sky map): map [12 nside^2] (FP64, nested order, unit sum) holds, at each
+ * pixel centre, q_r of the flow's coordinates with RA and sin dec at the centre and the
+ * other six (Mc, q, D_L, cos theta_JN, psi, phic) at those of the event's draw of largest
+ * log_q among theta [GWX_NPARAM][S] (device; e.g. gwx_sample_posterior's output, first on
+ * ties), normalised over the pixels.  (RA, sin dec) are equal-area coordinates of the
+ * sphere (d Omega = d RA d sin dec), so with HEALPix's equal-area pixels the map is that
+ * density per steradian times the pixel area, up to its normalisation.  One density
+ * pass of the flow over all pixels (the event's context computed once from y [1][D][N],
+ * or ctx_in [1][C]); nside a power of two in [1, 8192].  Workspace
+ * gwx_flow_skymap_workspace(shape, D, N, nside). */
+size_t gwx_flow_skymap_workspace(const gwx_flow_shape* shape, int D, int64_t N, int nside);
+int gwx_flow_skymap(const gwx_flow_shape* shape, const float* params, const void* params_bf16,
+                    const double* mean8, const double* scale8, const float* y, int D, int64_t N, double fs,
+                    double f_lo, const void* ctx_in, const double* theta, const double* log_q, int64_t S,
+                    int nside, double* map, void* workspace, size_t workspace_bytes, void* stream);
+
 /* ---- self-supervised pre-training of the data summary (Sec. 4.1) ------------------
  * Two views of each simulated source, identical but for the merger time, are summarised
  * and expanded (x, x' [B][d]); the summary is trained to make them agree with the VICReg

@@ -785,6 +785,26 @@ def sample_posterior(shape, params, params_bf16, mean8, scale8, prior, y, fs, f_
     return theta, log_q, lr
 
 
+def flow_skymap(shape, params, params_bf16, mean8, scale8, y, fs, f_lo, theta, log_q, nside, ctx=None, out=None):
+    """The flow's sky density (float64 [12 nside^2], nested HEALPix order, unit sum) for
+    one event y [1][D][N]: RA and sin dec at each pixel centre, the other coordinates at
+    the draw of largest log_q among theta [11][S]."""
+    torch = _torch()
+    sh = _shape(shape)
+    _dev(y, torch.float32, "y")
+    _dev(theta, torch.float64, "theta")
+    _dev(log_q, torch.float64, "log_q")
+    _, D, N = y.shape
+    S = theta.shape[1]
+    lib = _lib.load()
+    out = torch.empty(12 * nside * nside, dtype=torch.float64, device=y.device) if out is None else out
+    ws, nb = _workspace(lib.gwx_flow_skymap_workspace(ctypes.byref(sh), D, N, nside), y.device)
+    _check(lib.gwx_flow_skymap(ctypes.byref(sh), _ptr(params), _ptr(params_bf16), _host8(mean8), _host8(scale8),
+                               _ptr(y), D, N, fs, f_lo, _ptr(ctx) if ctx is not None else None, _ptr(theta),
+                               _ptr(log_q), S, int(nside), _ptr(out), _ptr(ws), nb, _stream()))
+    return out
+
+
 __all__ += ["flow_shape", "flow_layout", "flow_targets", "flow_conditioner_input", "flow_coupling", "flow_nll",
             "flow_coupling_backward", "flow_input_backward", "flow_base", "flow_proposal", "flow_train_step",
-            "flow_log_prob", "sample_posterior"]
+            "flow_log_prob", "sample_posterior", "flow_skymap"]

@@ -136,6 +136,9 @@ SIGNATURES = {
     "gwx_flow_log_prob": (c_int, [c_shp, c_vp, c_vp, c_d8, c_d8, c_vp, c_vp, c_i64, c_int, c_i64, c_dbl, c_dbl, c_vp,
                                   c_vp, c_vp, c_size, c_vp]),
     "gwx_sample_posterior_workspace": (c_size, [c_shp, c_i64, c_int, c_i64, c_i64]),
+    "gwx_flow_skymap_workspace": (c_size, [c_shp, c_int, c_i64, c_int]),
+    "gwx_flow_skymap": (c_int, [c_shp, c_vp, c_vp, c_d8, c_d8, c_vp, c_int, c_i64, c_dbl, c_dbl, c_vp, c_vp, c_vp,
+                                c_i64, c_int, c_vp, c_vp, c_size, c_vp]),
     "gwx_sample_posterior": (c_int, [c_shp, c_vp, c_vp, c_d8, c_d8, c_pri, c_vp, c_i64, c_int, c_i64, c_dbl, c_dbl,
                                      c_vp, c_vp, c_i64, c_u64, c_u32, c_vp, c_vp, c_vp, c_vp, c_size, c_vp]),
 }

@@ -1346,6 +1346,36 @@ size_t gwx_sample_posterior_workspace(const gwx_flow_shape* shape, int64_t E, in
   return align_up(flow_sample_ws(*shape, E, D, N, S));
 }
 
+size_t gwx_flow_skymap_workspace(const gwx_flow_shape* shape, int D, int64_t N, int nside) {
+  if (check_flow_shape(shape) != GWX_OK || D < 1 || N < 2 || nside < 1 || nside > 8192) return 0;
+  return align_up(flow_skymap_ws(*shape, D, N, nside));
+}
+
+int gwx_flow_skymap(const gwx_flow_shape* shape, const float* params, const void* params_bf16, const double* mean8,
+                    const double* scale8, const float* y, int D, int64_t N, double fs, double f_lo, const void* ctx_in,
+                    const double* theta, const double* log_q, int64_t S, int nside, double* map, void* workspace,
+                    size_t workspace_bytes, void* stream) {
+  GWX_TRY(check_flow_shape(shape));
+  GWX_TRY(check_std8(mean8, scale8));
+  int k_lo = 0;
+  GWX_TRY(check_flow_windows(shape, D, N, fs, f_lo, &k_lo));
+  if (nside < 1 || nside > 8192 || (nside & (nside - 1)) != 0)
+    return fail(GWX_ESHAPE, "nside=%d must be a power of two in [1, 8192]", nside);
+  if (S < 1 || S > ((int64_t)1 << 32)) return fail(GWX_ESHAPE, "S=%lld draws (need at least one)", (long long)S);
+  GWX_TRY(check_flow_params(shape, params, params_bf16));
+  if ((!y && !ctx_in) || !theta || !log_q || !map) return fail(GWX_EINVAL, "NULL array");
+  if (y) GWX_ALIGN8(y);
+  if (ctx_in) GWX_ALIGN16(ctx_in);
+  GWX_ALIGN8(theta);
+  GWX_ALIGN8(log_q);
+  GWX_ALIGN8(map);
+  GWX_TRY(check_ws(workspace, workspace_bytes, gwx_flow_skymap_workspace(shape, D, N, nside)));
+  GWX_TRY(ensure_init());
+  return launched(flow_skymap(*shape, params, params_bf16, mean8, scale8, y, D, N, k_lo, ctx_in, theta, log_q, S,
+                              nside, map, workspace, as_stream(stream)),
+                  "flow_skymap");
+}
+
 int gwx_sample_posterior(const gwx_flow_shape* shape, const float* params, const void* params_bf16,
                          const double* mean8, const double* scale8, const gwx_prior* prior, const float* y,
                          int64_t E, int D, int64_t N, double fs, double f_lo, const void* ctx_in,

@@ -187,6 +187,13 @@ cudaError_t flow_sample(const gwx_flow_shape& sh, const float* params, const voi
                         int k_lo, const void* ctx_in, const int64_t* off, int64_t S,
                         uint64_t seed, uint32_t counter, double* theta, double* log_q, double* log_ratio, void* ws,
                         cudaStream_t s);
+// The flow's sky density at the HEALPix (nested) pixel centres of nside, the other
+// coordinates at the draw of largest log_q among theta [GWX_NPARAM][S]; map [12 nside^2].
+size_t flow_skymap_ws(const gwx_flow_shape& sh, int D, int64_t N, int nside);
+cudaError_t flow_skymap(const gwx_flow_shape& sh, const float* params, const void* params_bf16, const double* mean8,
+                        const double* scale8, const float* y, int D, int64_t N, int k_lo, const void* ctx_in,
+                        const double* theta, const double* log_q, int64_t S, int nside, double* map, void* ws,
+                        cudaStream_t s);
 
 // HEALPix sky map of weighted samples (k_skymap.cu); ws holds one double.
 cudaError_t launch_skymap(const double* theta, const double* weights, int64_t S, int nside, double* map, void* ws,

@@ -690,4 +690,193 @@ cudaError_t flow_sample(const gwx_flow_shape& sh, const float* params, const voi
   return cudaSuccess;
 }
 
+// ----------------------------------------------------------------- sky density
+// The flow's density over the sky (Sec. 5: evaluated at every pixel of the map): at each
+// HEALPix pixel centre (nested order) the density of the flow's coordinates with (RA,
+// sin dec) at the centre and the other six held at the event's draw of largest ln q,
+// normalised to unit sum over the pixels.  (RA, sin dec) have equal-area measure on the
+// sphere, so with equal-area pixels this is the density per steradian up to a constant.
+namespace {
+
+constexpr int kSkyThreads = 256;
+
+__device__ __forceinline__ uint32_t compact_bits(uint32_t v) {   // bit 2 b of v -> bit b
+  v &= 0x55555555u;
+  v = (v | (v >> 1)) & 0x33333333u;
+  v = (v | (v >> 2)) & 0x0F0F0F0Fu;
+  v = (v | (v >> 4)) & 0x00FF00FFu;
+  v = (v | (v >> 8)) & 0x0000FFFFu;
+  return v;
+}
+
+// Centre (longitude, cos colatitude) of nested pixel p (Gorski et al. 2005).
+__device__ __forceinline__ void pix2ang_nest(int nside, int64_t p, double& phi, double& z) {
+  const int jrll[12] = {2, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4};
+  const int jpll[12] = {1, 3, 5, 7, 0, 2, 4, 6, 1, 3, 5, 7};
+  const int64_t npf = (int64_t)nside * nside;
+  const int f = (int)(p / npf);
+  const uint32_t loc = (uint32_t)(p - f * npf);
+  const int ix = (int)compact_bits(loc), iy = (int)compact_bits(loc >> 1);
+  const int jr = jrll[f] * nside - ix - iy - 1;
+  int nr, shift;
+  if (jr < nside) {
+    nr = jr;
+    z = 1.0 - (double)jr * jr / (3.0 * (double)npf);
+    shift = 0;
+  } else if (jr > 3 * nside) {
+    nr = 4 * nside - jr;
+    z = -(1.0 - (double)nr * nr / (3.0 * (double)npf));
+    shift = 0;
+  } else {
+    nr = nside;
+    z = 4.0 / 3.0 - 2.0 * jr / (3.0 * nside);
+    shift = (jr - nside) & 1;
+  }
+  int jp = (jpll[f] * nr + ix - iy + 1 + shift) / 2;
+  if (jp > 4 * nr) jp -= 4 * nr;
+  if (jp < 1) jp += 4 * nr;
+  phi = (jp - 0.5 * (1 + shift)) * (0.5 * 3.141592653589793238462643383279502884) / nr;
+}
+
+// One block: the draw of largest log_q (first on ties) and its flow coordinates r8.
+__global__ void __launch_bounds__(kSkyThreads) k_sky_pick(const double* __restrict__ theta,
+                                                          const double* __restrict__ log_q, int64_t S,
+                                                          double* __restrict__ r8) {
+  __shared__ double bv[kSkyThreads];
+  __shared__ int64_t bi[kSkyThreads];
+  double v = -INFINITY;
+  int64_t i = S;
+  for (int64_t s = threadIdx.x; s < S; s += blockDim.x) {
+    const double q = log_q[s];
+    if (q > v) {
+      v = q;
+      i = s;
+    }
+  }
+  bv[threadIdx.x] = v;
+  bi[threadIdx.x] = i;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      const double v2 = bv[threadIdx.x + o];
+      const int64_t i2 = bi[threadIdx.x + o];
+      if (v2 > bv[threadIdx.x] || (v2 == bv[threadIdx.x] && i2 < bi[threadIdx.x])) {
+        bv[threadIdx.x] = v2;
+        bi[threadIdx.x] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int64_t b = bi[0] < S ? bi[0] : 0;                  // every log_q -inf / NaN: the first draw
+    const double m1 = theta[b], m2 = theta[S + b];
+    r8[0] = pow(m1 * m2, 0.6) / pow(m1 + m2, 0.2);
+    r8[1] = fmin(m1, m2) / fmax(m1, m2);
+    r8[2] = theta[4 * S + b];
+    r8[3] = cos(theta[7 * S + b]);
+    r8[4] = theta[9 * S + b];
+    r8[5] = sin(theta[10 * S + b]);
+    r8[6] = theta[8 * S + b];
+    r8[7] = theta[6 * S + b];
+  }
+}
+
+// Standardised flow coordinates of pixels row0 .. row0 + n - 1.
+__global__ void k_sky_rows(int nside, int64_t row0, int64_t n, const double* __restrict__ r8, Std8 st,
+                           float* __restrict__ x) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double r[8];
+#pragma unroll
+  for (int p = 0; p < 8; ++p) r[p] = r8[p];
+  pix2ang_nest(nside, row0 + i, r[4], r[5]);                 // RA = phi, sin dec = cos colatitude
+  float v[8];
+#pragma unroll
+  for (int p = 0; p < 8; ++p) v[p] = (float)((r[p] - st.mean[p]) / st.scale[p]);
+  store8(x + i * 8, v);
+}
+
+__global__ void k_sky_fill_offsets(int64_t* off, int64_t n) {
+  if (threadIdx.x == 0) {
+    off[0] = 0;
+    off[1] = n;
+  }
+}
+
+// One block: map = exp(lnq - max) / sum (FP64).
+__global__ void __launch_bounds__(kSkyThreads) k_sky_norm(const double* __restrict__ lnq, int64_t n,
+                                                          double* __restrict__ map) {
+  __shared__ double red[kSkyThreads];
+  double m = -INFINITY;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, lnq[i]);
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  const double M = red[0];
+  __syncthreads();
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc += isfinite(M) ? exp(lnq[i] - M) : 0.0;
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double tot = red[0];
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+    map[i] = (isfinite(M) && tot > 0.0) ? exp(lnq[i] - M) / tot : 0.0;
+}
+
+}  // namespace
+
+size_t flow_skymap_ws(const gwx_flow_shape& sh, int D, int64_t N, int nside) {
+  const FlowDims d = dims_of(sh);
+  const int64_t npix = 12 * (int64_t)nside * nside;
+  Carve c(nullptr);
+  carve_embed(d, 1, D, N, c);
+  carve_chain(d, std::min(npix, kSampleChunk), c);
+  c.take<double>(npix);
+  c.take<double>(8);
+  c.take<int64_t>(2);
+  return c.used;
+}
+
+cudaError_t flow_skymap(const gwx_flow_shape& sh, const float* params, const void* params_bf16, const double* mean8,
+                        const double* scale8, const float* y, int D, int64_t N, int k_lo, const void* ctx_in,
+                        const double* theta, const double* log_q, int64_t S, int nside, double* map, void* ws,
+                        cudaStream_t s) {
+  const FlowDims d = dims_of(sh);
+  const Params P = make_params(sh, params, params_bf16);
+  const int64_t npix = 12 * (int64_t)nside * nside;
+  Carve c(ws);
+  EmbedWs e = carve_embed(d, 1, D, N, c);
+  ChainWs w = carve_chain(d, std::min(npix, kSampleChunk), c);
+  double* lnq = c.take<double>(npix);
+  double* r8 = c.take<double>(8);
+  int64_t* off = c.take<int64_t>(2);
+  const __nv_bfloat16* ctx = ctx_in ? reinterpret_cast<const __nv_bfloat16*>(ctx_in) : e.ctx;
+  if (!ctx_in) FL_TRY(embed_forward(d, P, y, 1, D, N, k_lo, e.fws, e.feat, e.h1, e.h2, e.ctx, s));
+  k_sky_pick<<<1, kSkyThreads, 0, s>>>(theta, log_q, S, r8);
+  k_sky_fill_offsets<<<1, 32, 0, s>>>(off, npix);
+  FL_TRY(cudaGetLastError());
+  const Std8 st = make_std(mean8, scale8);
+  for (int64_t row0 = 0; row0 < npix; row0 += kSampleChunk) {
+    const int64_t n = std::min(kSampleChunk, npix - row0);
+    k_sky_rows<<<blocks(n, 128), 128, 0, s>>>(nside, row0, n, r8, st, w.v);
+    FL_TRY(cudaGetLastError());
+    for (int l = (int)d.K - 1; l >= 0; --l) {
+      FL_TRY(launch_flow_input(l, w.v, ctx, (int)d.C, off, 1, row0, n, w.X, s));
+      FL_TRY(conditioner_forward(d, P, l, n, w.X, w.g1, w.g2, w.o, s));
+      FL_TRY(launch_flow_coupling(l, -1, w.v, w.o, n, w.v, w.sum_s, l == (int)d.K - 1, s));
+    }
+    k_flow_logq<<<blocks(n, 128), 128, 0, s>>>(w.v, w.sum_s, n, -4.0 * LN_2PI - st.ln_scale_sum, lnq + row0);
+    FL_TRY(cudaGetLastError());
+  }
+  k_sky_norm<<<1, kSkyThreads, 0, s>>>(lnq, npix, map);
+  return cudaGetLastError();
+}
+
 }  // namespace gwx

@@ -1,5 +1,6 @@
 // k_waveform.cu -- per-draw set-up, TaylorF2 waveforms (A2), projection (A3) and
 // the whitened log-likelihood (A8).
+#include "fft16.cuh"
 #include "waveform.cuh"
 
 namespace gwx {
@@ -280,20 +281,24 @@ cudaError_t launch_loglike_full(const float* ydata, const float2* Ydata, const f
 // tc = tc_lo and c_k = (2/N) sum_d Y_d,k conj(H_d,k) (band bins, zero elsewhere)
 //   ln L(tc_lo + (u m + r) / (u fs)) = -(|Y|^2 + |H|^2)/N + Re sum_k c_k e^{2 pi i k r/(N u)} e^{2 pi i k m/N},
 // i.e. for each sub-grid offset r < u an inverse real FFT of N points of
-// c_k e^{2 pi i k r/(N u)}, of which the outputs m < n_tc are used.  A block takes 32
+// X_k = c_k e^{2 pi i k r/(N u)}, of which the outputs m < n_tc are used.  A block takes 32
 // consecutive samples: its first warp does their FP64 set-up (one lane per sample), then
-// per sample all threads build c_k in shared memory, and G groups of n/8 threads run the
-// u transforms G at a time (fft_smem_at), folding their outputs into a per-thread running
-// maximum and sum of exponentials; one block reduction per sample gives ln L_m.
+// per sample all threads build c_k in shared memory, and G groups of n/16 threads (16
+// values each) run the u transforms G at a time: the first inverse pass packs X into the
+// half-length complex transform as it loads (Z_m from X_m and X_{n-m}), the middle passes
+// alternate between two shared buffers (one barrier each), and the last pass folds its
+// outputs into a per-thread running maximum and sum of exponentials in registers; one
+// block reduction per sample gives ln L_m.
 constexpr int TM_SAMPLES = 32;
 
 template <int LOGN>
 struct TmGeom {
-  static constexpr int n = 1 << LOGN;                         // complex points of the packed transform
-  static constexpr int TPR = n / 8;                           // threads per transform
-  static constexpr int G = TPR >= 256 ? 1 : 256 / TPR;        // transforms in flight per block
+  using PL = Plan16<LOGN>;
+  static constexpr int n = PL::n;                              // complex points of the packed transform
+  static constexpr int TPR = PL::T;                            // threads per transform (16 values each)
+  static constexpr int G = TPR >= 256 ? 1 : 256 / TPR;         // transforms in flight per block
   static constexpr int THREADS = TPR * G;
-  static constexpr size_t SMEM = ((size_t)G * n + (size_t)(n + 1)) * sizeof(float2);
+  static constexpr size_t SMEM = ((size_t)G * 2 * n + (size_t)(n + 1)) * sizeof(float2);
 };
 
 // Running log-sum-exp state (max m, sum s of exp(v - m)).
@@ -312,25 +317,40 @@ __device__ __forceinline__ void lse_merge(float& m, float& s, float m2, float s2
   m = M;
 }
 
+// Elements m and n - m (0 < m < n) of the packed half-length transform of
+// X_k = c_k e^{2 pi i k r/(N u)}: with X_m and X_{n-m} (whose ramp is e^{i pi r/u} times the
+// conjugate of X_m's, cr = e^{i pi r/u}), pack_pair gives Z_m and Z_{n-m} together.
+template <int LOGN>
+__device__ __forceinline__ void tm_pair(const float2* __restrict__ cb, int m, uint32_t r, uint32_t numask,
+                                        float inv_nu, float2 cr, float2& zm, float2& zn) {
+  constexpr int n = 1 << LOGN;
+  const float2 ph = expm2pi(-(float)(((uint32_t)m * r) & numask) * inv_nu);   // e^{+2 pi i m r/(N u)}
+  const float2 xm = cmul(cb[m], ph);
+  const float2 xn = cmul(cb[n - m], cmul(cr, cconj(ph)));
+  pack_pair(xm, xn, pack_twiddle(m, LOGN + 1), zm, zn);
+}
+
 template <int ND, int LOGN>
-__global__ void __launch_bounds__(TmGeom<LOGN>::THREADS)
+__global__ void __launch_bounds__(TmGeom<LOGN>::THREADS, TmGeom<LOGN>::THREADS <= 256 ? 2 : 1)
 k_loglike_tmarg(const double* __restrict__ theta, SetupConsts kc, double fs, DetParams dp, double gmst, double tc_lo,
                 const float2* __restrict__ Y, const float* __restrict__ W, const int64_t* __restrict__ ev_off,
                 const double* __restrict__ yy_part, int64_t E, int k_lo, int n_tc, int u, int64_t S, double invN,
                 double log_J, double* __restrict__ lnl) {
   using Gm = TmGeom<LOGN>;
+  using PL = typename Gm::PL;
   constexpr int n = Gm::n;
   constexpr int F = n + 1;
   constexpr int NT = Gm::THREADS;
-  constexpr int NW = NT / 32;
+  constexpr int NW = NT / 32 > 0 ? NT / 32 : 1;
+  constexpr int TPR = Gm::TPR, RL = PL::RL, NB = PL::NB, P = PL::P;
   extern __shared__ float2 tm_smem[];
-  float2* cb = tm_smem + Gm::G * n;                           // c_k, k = 0 .. n
+  float2* cb = tm_smem + Gm::G * 2 * n;                        // c_k, k = 0 .. n
   __shared__ DrawCoef sc[TM_SAMPLES];
   __shared__ int se[TM_SAMPLES];
   __shared__ float red_m[NW], red_s[NW];
   __shared__ double red_h[NW];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int g = tid / Gm::TPR, t = tid % Gm::TPR;
+  const int g = tid / TPR, t = tid % TPR;
   const int64_t base = (int64_t)blockIdx.x * TM_SAMPLES;
   const int cnt = (int)min((int64_t)TM_SAMPLES, S - base);
   if (wid == 0 && lane < cnt) {
@@ -349,10 +369,10 @@ k_loglike_tmarg(const double* __restrict__ theta, SetupConsts kc, double fs, Det
   }
   __syncthreads();
   const float two_over_N = (float)(2.0 * invN);               // a power of two: exact
-  const uint32_t zaddr = smem_addr(tm_smem + g * n);
-  float2* z = tm_smem + g * n;
+  const uint32_t bufA = smem_addr(tm_smem + g * 2 * n), bufB = bufA + 8u * (uint32_t)n;
   const uint32_t numask = (uint32_t)(2 * n) * (uint32_t)u - 1u;   // N u - 1 (N u a power of two)
   const float inv_nu = 1.0f / (float)(numask + 1u);
+  const float inv_2u = 0.5f / (float)u;
   for (int j = 0; j < cnt; ++j) {
     const int64_t e = se[j];
     const int kend = min(sc[j].kcut, n - 1);
@@ -385,38 +405,64 @@ k_loglike_tmarg(const double* __restrict__ theta, SetupConsts kc, double fs, Det
     float mx = -INFINITY, sm = 0.f;
     for (int r0 = 0; r0 < u; r0 += Gm::G) {
       const uint32_t r = (uint32_t)(r0 + g);
-      // X_k = c_k e^{2 pi i k r/(N u)}, packed into n complex points (c_0 = c_n = 0)
+      const float2 cr = expm2pi(-(float)r * inv_2u);         // e^{i pi r/u}
+      // first inverse pass (radix RL, Ns = 1), reading the packed transform from c_k: a
+      // thread owns butterflies p and NB - p, which hold both members of every pair
+      // (m, n - m), so each pair's phase ramp and packing are computed once
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int k = t + i * (n / 8);
-        if (k == 0) {
-          z[0] = make_float2(0.f, 0.f);
-          continue;
+      for (int s2 = 0; s2 < PL::SLOTS; ++s2) {
+        const int pp = t + s2 * TPR;
+        const int jA = pp, jB = pp ? NB - pp : NB / 2;
+        float2 vA[RL], vB[RL];
+        if (pp != 0) {
+#pragma unroll
+          for (int q = 0; q < RL; ++q)
+            tm_pair<LOGN>(cb, jA + NB * q, r, numask, inv_nu, cr, vA[q], vB[RL - 1 - q]);
+        } else {
+          // butterfly 0 holds Z_0 (zero: c_0 = c_n = 0), the pairs (NB q, NB (RL - q)) and
+          // Z_{n/2}; butterfly NB/2 holds the pairs (NB/2 + NB q, NB/2 + NB (RL - 1 - q))
+          vA[0] = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int q = 1; q < RL; ++q) {
+            if (q < RL - q) tm_pair<LOGN>(cb, NB * q, r, numask, inv_nu, cr, vA[q], vA[RL - q]);
+          }
+          if (RL > 1) {
+            float2 zh, unused;
+            tm_pair<LOGN>(cb, n / 2, r, numask, inv_nu, cr, zh, unused);
+            vA[RL / 2] = zh;
+          }
+#pragma unroll
+          for (int q = 0; q < RL / 2; ++q)
+            tm_pair<LOGN>(cb, NB / 2 + NB * q, r, numask, inv_nu, cr, vB[q], vB[RL - 1 - q]);
         }
-        const float2 xk = cmul(cb[k], expm2pi(-(float)(((uint32_t)k * r) & numask) * inv_nu));
-        const float2 xnk = cmul(cb[n - k], expm2pi(-(float)(((uint32_t)(n - k) * r) & numask) * inv_nu));
-        float2 zk, znk;
-        pack_pair(xk, xnk, pack_twiddle(k, LOGN + 1), zk, znk);
-        z[sw(k)] = zk;
-        z[sw(n - k)] = znk;
-      }
-      if (t == 0) {
-        const int h = n / 2;
-        const float2 xh = cmul(cb[h], expm2pi(-(float)(((uint32_t)h * r) & numask) * inv_nu));
-        float2 zk, znk;
-        pack_pair(xh, xh, pack_twiddle(h, LOGN + 1), zk, znk);
-        z[sw(h)] = zk;
+        dftR<RL, true, false>(vA);
+        dftR<RL, true, false>(vB);
+        store_pass<RL, 1>(bufA, jA, vA);
+        store_pass<RL, 1>(bufA, jB, vB);
       }
       __syncthreads();
-      fft_smem_at<LOGN, true>(zaddr, t);                      // unscaled inverse: z packs (v_2m, v_2m+1)
-      if ((int)r < u) {
-        for (int mp = t; 2 * mp < n_tc; mp += n / 8) {
-          const float2 v = z[sw(mp)];
-          lse_add(mx, sm, v.x);
-          if (2 * mp + 1 < n_tc) lse_add(mx, sm, v.y);
+      const uint32_t xl = InvMiddlePP<LOGN, 1, P - 2, RL>::run(bufA, bufB, t);
+      // last inverse pass (radix 8, Ns = n/8); its outputs are the grid's Re z values
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int jj = t + i * TPR;
+        float2 v[8];
+        load_strided<8, n / 8>(xl, jj, v);
+        float2 w[8];
+        pass_twiddles<8, n / 8, true>(jj, w);
+#pragma unroll
+        for (int q = 1; q < 8; ++q) v[q] = cmul(v[q], w[q]);
+        dft8<true, false>(v);
+        if ((int)r < u) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int mp = jj + q * (n / 8);
+            if (2 * mp < n_tc) lse_add(mx, sm, v[q].x);
+            if (2 * mp + 1 < n_tc) lse_add(mx, sm, v[q].y);
+          }
         }
       }
-      __syncthreads();                                        // outputs read before the next pack
+      __syncthreads();                                        // the next round's first pass rewrites bufA
     }
     // block reductions: (max, sum) and sum |H|^2 (FP64 across threads)
     double hh = (double)hs - (double)hcmp;

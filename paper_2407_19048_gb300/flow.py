@@ -244,6 +244,13 @@ class FlowPosterior:
                                          self.wl["prior"], y_events, self.fs, self.f_lo, event_offsets, seed,
                                          counter, ctx=self.context(y_events), S=S)
 
+    def skymap(self, y_event, theta, log_q, nside):
+        """The flow's sky density for one event y_event [1][D][N] over the HEALPix pixels
+        of nside (nested order, unit sum): RA and sin dec at each pixel centre, the other
+        coordinates at the event's draw of largest log_q among theta [11][S]."""
+        return self.gwx.flow_skymap(self.shape, self.params, self.params16, self.mean, self.scale, y_event, self.fs,
+                                    self.f_lo, theta, log_q, nside, ctx=self.context(y_event))
+
     def log_prob(self, y, theta):
         return self.gwx.flow_log_prob(self.shape, self.params, self.params16, self.mean, self.scale, y, theta,
                                       self.fs, self.f_lo, ctx=self.context(y))
