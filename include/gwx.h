@@ -344,6 +344,27 @@ int gwx_importance_weights(const double* lnl, const double* log_ratio, const int
                            int64_t E, int64_t S, double* weights, double* ess, double* efficiency,
                            double* ln_evidence, void* workspace, size_t workspace_bytes, void* stream);
 
+/* ---- debugging aids ------------------------------------------------------------------
+ * The debug build of the library (libgwx_debug.so: the same sources compiled with
+ * GWX_DEBUG_CHECKS; build.build(debug=True)) checks the indices of the global loads and
+ * stores of the hot kernels (the fused simulation pass, both likelihood kernels): an
+ * index outside its array is not accessed (a load gives zero) and the first such event
+ * is recorded instead of faulting.  The paper has no counterpart; these are for testing.
+ * gwx_debug_build: 1 in the debug build, 0 otherwise.
+ * gwx_debug_status: *first_bad = (site << 48) | 2^47 | index of the first recorded
+ *   out-of-range access since the last call (then cleared), 0 if none (always 0 in the
+ *   normal build); returns GWX_ESHAPE with the site and index in the message when there
+ *   was one.  Synchronises the device (not allowed inside stream capture).
+ * gwx_debug_guard / gwx_debug_check_guard: write a fixed byte pattern into the
+ *   guard_bytes that follow the first nbytes of a caller allocation (e.g. a workspace
+ *   allocated nbytes + guard_bytes large), and check later that no call wrote into them
+ *   (*intact = 1) or that one did (*intact = 0); the check synchronises the device
+ *   first (not allowed inside stream capture). */
+int gwx_debug_build(void);
+int gwx_debug_status(uint64_t* first_bad);
+int gwx_debug_guard(void* workspace, size_t nbytes, size_t guard_bytes, void* stream);
+int gwx_debug_check_guard(const void* workspace, size_t nbytes, size_t guard_bytes, int* intact, void* stream);
+
 /* ---- learned part: dense products -----------------------------------------------
  * C = A B^T, the contraction of the dense layers of the embedding network (Sec. 4) and
  * the normalizing flow (Sec. 5) that train on the simulated batches:

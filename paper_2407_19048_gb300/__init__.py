@@ -27,7 +27,7 @@ __all__ = ["GwxError", "version", "init", "detector_geometry", "sample_prior", "
            "importance_weights", "gemm_bf16", "dense_bf16", "dense_bf16_backward", "gemm_autotune", "spectral_features",
            "cross_features", "lag_features", "proposal_targets",
            "gauss_nll", "adamw", "adamw_clip", "skymap", "vicreg", "retime", "sample_proposal", "device_status", "selftest_bounded_wait", "rfft", "irfft",
-           "workspace_bytes", "TAYLORF2", "IMRPHENOMD", "DETECTORS"]
+           "workspace_bytes", "debug_check", "TAYLORF2", "IMRPHENOMD", "DETECTORS"]
 
 
 class GwxError(RuntimeError):
@@ -40,6 +40,40 @@ def _check(status):
     if status != 0:
         lib = _lib.load()
         raise GwxError(status, lib.gwx_last_error().decode(errors="replace"))
+    if _lib.DEBUG:
+        debug_check()
+
+
+# Debug build (GWX_DEBUG=1): every workspace the binding allocates is followed by a
+# guard of _GUARD bytes in a fixed pattern, and after every call the guards of the live
+# workspaces and the kernels' index records are checked (synchronising the device; calls
+# made while a stream is being captured are checked at the next call outside capture).
+_GUARD = 256
+_guards = []
+
+
+def debug_check():
+    """Raise GwxError if a kernel of the debug build recorded an out-of-range access or a
+    call wrote into the guard after one of the binding's workspaces (no-op otherwise)."""
+    if not _lib.DEBUG or _torch().cuda.is_current_stream_capturing():
+        return
+    lib = _lib.load()
+    first = ctypes.c_uint64(0)
+    st = lib.gwx_debug_status(ctypes.byref(first))
+    if st != 0:
+        raise GwxError(st, lib.gwx_last_error().decode(errors="replace"))
+    live = []
+    for ref, ptr, nbytes in _guards:
+        if ref() is None:
+            continue
+        live.append((ref, ptr, nbytes))
+        ok = ctypes.c_int(1)
+        st = lib.gwx_debug_check_guard(ctypes.c_void_p(ptr), nbytes, _GUARD, ctypes.byref(ok), _stream())
+        if st != 0:
+            raise GwxError(st, lib.gwx_last_error().decode(errors="replace"))
+        if not ok.value:
+            raise GwxError(-2, "a call wrote past the end of a %d-byte workspace" % nbytes)
+    _guards[:] = live
 
 
 def _torch():
@@ -73,8 +107,16 @@ def _workspace(nbytes, device):
     torch = _torch()
     if nbytes == 0:
         return None, 0
-    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+    guard = _GUARD if _lib.DEBUG else 0
+    ws = torch.empty(nbytes + 256 + guard, dtype=torch.uint8, device=device)
     off = (-ws.data_ptr()) % 256
+    if guard:
+        import weakref
+        ptr = ws.data_ptr() + off
+        st = _lib.load().gwx_debug_guard(ctypes.c_void_p(ptr), nbytes, guard, _stream())
+        if st != 0:
+            raise GwxError(st, _lib.load().gwx_last_error().decode(errors="replace"))
+        _guards.append((weakref.ref(ws), ptr, nbytes))
     return ws[off:off + nbytes], nbytes
 
 

@@ -7,7 +7,10 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libgwx.so")
+# GWX_DEBUG=1 loads the debug build (index checks in the hot kernels, workspace guards in
+# the binding); it must have been built with build(debug=True)
+DEBUG = os.environ.get("GWX_DEBUG", "0") not in ("", "0")
+LIB_PATH = os.path.join(HERE, "libgwx_debug.so" if DEBUG else "libgwx.so")
 
 c_i64 = ctypes.c_int64
 c_u64 = ctypes.c_uint64
@@ -66,6 +69,10 @@ SIGNATURES = {
     "gwx_log_likelihood_workspace": (c_size, [c_i64, c_int, c_i64, c_i64]),
     "gwx_log_likelihood": (c_int, [c_int, c_vp, c_i64, c_int, c_i64, c_vp, c_i64, c_dbl, c_dbl, c_i32p, c_dbl,
                                    c_vp, c_vp, c_i64, c_vp, c_vp, c_size, c_vp]),
+    "gwx_debug_build": (c_int, []),
+    "gwx_debug_status": (c_int, [ctypes.POINTER(c_u64)]),
+    "gwx_debug_guard": (c_int, [c_vp, c_size, c_size, c_vp]),
+    "gwx_debug_check_guard": (c_int, [c_vp, c_size, c_size, ctypes.POINTER(c_int), c_vp]),
     "gwx_simulate_autotune": (c_int, [c_vp, c_i64, c_vp, c_i64, c_dbl, c_dbl, c_int, c_i64, c_i64, c_vp, c_vp, c_vp,
                                       c_size, ctypes.POINTER(c_int), c_vp]),
     "gwx_simulate_shape": (c_int, [c_i64, c_int, c_int]),

@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -203,6 +204,19 @@ int gwx::init_device() { return ensure_init(); }
 
 int gwx::launch_status(cudaError_t e, const char* what) { return launched(e, what); }
 
+
+namespace {
+// Guard bytes after a workspace: byte i holds (0xA5 ^ (i * 131)) & 0xFF.
+__device__ int g_guard_bad;
+__global__ void k_guard_fill(uint8_t* p, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    p[i] = (uint8_t)(0xA5u ^ (unsigned)(i * 131u));
+}
+__global__ void k_guard_check(const uint8_t* p, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    if (p[i] != (uint8_t)(0xA5u ^ (unsigned)(i * 131u))) atomicExch(&g_guard_bad, 1);
+}
+}  // namespace
 
 namespace gwx {
 // defined in k_gemm.cu, next to the status flag it sets
@@ -753,6 +767,58 @@ int gwx_selftest_bounded_wait(uint32_t polls, void* stream) {
   if (polls < 1 || polls > (1u << 20)) return fail(GWX_EINVAL, "polls=%u (1 .. 2^20)", polls);
   GWX_TRY(ensure_init());
   return launched(launch_selftest_wait(polls, as_stream(stream)), "selftest_bounded_wait");
+}
+
+int gwx_debug_guard(void* workspace, size_t nbytes, size_t guard_bytes, void* stream) {
+  if (!workspace || guard_bytes == 0) return fail(GWX_EINVAL, "workspace is NULL or the guard empty");
+  GWX_TRY(ensure_init());
+  uint8_t* p = reinterpret_cast<uint8_t*>(workspace) + nbytes;
+  k_guard_fill<<<(unsigned)std::min<size_t>((guard_bytes + 255) / 256, 1024), 256, 0, as_stream(stream)>>>(p, guard_bytes);
+  return launched(cudaGetLastError(), "guard fill");
+}
+
+int gwx_debug_check_guard(const void* workspace, size_t nbytes, size_t guard_bytes, int* intact, void* stream) {
+  if (!workspace || guard_bytes == 0 || !intact) return fail(GWX_EINVAL, "NULL argument or empty guard");
+  GWX_TRY(ensure_init());
+  cudaStream_t s = as_stream(stream);
+  // every call queued so far, on any stream, is done before the guard is read
+  GWX_TRY(launched(cudaDeviceSynchronize(), "guard check"));
+  const int zero = 0;
+  GWX_TRY(launched(cudaMemcpyToSymbolAsync(g_guard_bad, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s),
+                   "guard reset"));
+  const uint8_t* p = reinterpret_cast<const uint8_t*>(workspace) + nbytes;
+  k_guard_check<<<(unsigned)std::min<size_t>((guard_bytes + 255) / 256, 1024), 256, 0, s>>>(p, guard_bytes);
+  GWX_TRY(launched(cudaGetLastError(), "guard check"));
+  int bad = 0;
+  GWX_TRY(launched(cudaMemcpyFromSymbolAsync(&bad, g_guard_bad, sizeof(int), 0, cudaMemcpyDeviceToHost, s),
+                   "guard read"));
+  GWX_TRY(launched(cudaStreamSynchronize(s), "guard read"));
+  *intact = bad ? 0 : 1;
+  return GWX_OK;
+}
+
+int gwx_debug_build(void) {
+#ifdef GWX_DEBUG_CHECKS
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+int gwx_debug_status(uint64_t* first_bad) {
+  if (!first_bad) return fail(GWX_EINVAL, "first_bad is NULL");
+  GWX_TRY(ensure_init());
+  unsigned long long a = 0, b = 0;
+  GWX_TRY(launched(cudaDeviceSynchronize(), "debug status"));
+  GWX_TRY(launched(debug_take_fused(&a), "debug status"));
+  GWX_TRY(launched(debug_take_waveform(&b), "debug status"));
+  *first_bad = a ? a : b;
+  if (*first_bad) {
+    const unsigned long long v = *first_bad;
+    return fail(GWX_ESHAPE, "out-of-range access skipped at site 0x%llx, index %lld", (v >> 48) & 0xFFFFull,
+                (long long)(v & ((1ull << 47) - 1)));
+  }
+  return GWX_OK;
 }
 
 int gwx_device_status(void) {

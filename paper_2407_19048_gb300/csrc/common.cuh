@@ -20,6 +20,35 @@
 
 namespace gwx {
 
+// ---------------------------------------------------------------- debug index checks
+// In the debug build (GWX_DEBUG_CHECKS) the hot kernels check the indices of their global
+// loads and stores: an index outside its array is not accessed (loads give zero) and the
+// first such event of the translation unit is recorded as (site << 48) | (index & 2^47-1)
+// | 2^47, for gwx_debug_status.  In the normal build the checks compile to nothing.
+#ifdef GWX_DEBUG_CHECKS
+static __device__ unsigned long long g_dbg_first_bad;
+__device__ __forceinline__ bool dbg_in(int64_t i, int64_t n, unsigned site) {
+  if (i >= 0 && i < n) return true;
+  atomicCAS(&g_dbg_first_bad, 0ull,
+            ((unsigned long long)(site & 0xFFFFu) << 48) | (1ull << 47) | ((unsigned long long)i & ((1ull << 47) - 1)));
+  return false;
+}
+#define GWX_IDX_OK(i, n, site) ::gwx::dbg_in((int64_t)(i), (int64_t)(n), (site))
+// This translation unit's record (read and cleared), on the current device.
+static inline cudaError_t dbg_take_this_tu(unsigned long long* v) {
+  cudaError_t e = cudaMemcpyFromSymbol(v, g_dbg_first_bad, sizeof(*v));
+  if (e != cudaSuccess) return e;
+  const unsigned long long zero = 0;
+  return cudaMemcpyToSymbol(g_dbg_first_bad, &zero, sizeof(zero));
+}
+#else
+#define GWX_IDX_OK(i, n, site) true
+static inline cudaError_t dbg_take_this_tu(unsigned long long* v) {
+  *v = 0;
+  return cudaSuccess;
+}
+#endif
+
 // ---------------------------------------------------------------- complex
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }

@@ -240,6 +240,11 @@ int init_device();
 // GWX_OK for cudaSuccess, else GWX_ECUDA with "what: <CUDA error name> (<string>)".
 int launch_status(cudaError_t e, const char* what);
 
+// Debug build: each checked translation unit's first out-of-range access (read and
+// cleared); zero when none, and always zero in the normal build.
+cudaError_t debug_take_fused(unsigned long long* v);
+cudaError_t debug_take_waveform(unsigned long long* v);
+
 // per-translation-unit table set-up on the current device
 cudaError_t init_tables_random();
 cudaError_t init_tables_spectral();

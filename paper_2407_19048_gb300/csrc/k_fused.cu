@@ -16,6 +16,7 @@
 namespace gwx {
 
 cudaError_t init_tables_fused() { return fill_tables_for_this_tu(); }
+cudaError_t debug_take_fused(unsigned long long* v) { return dbg_take_this_tu(v); }
 
 // Frequency-domain step of one real-FFT bin pair (k, nk = n - k), 0 < k < n, k != n/2,
 // done on the half-length transform Z directly.  Whitening (s = W/n) in that domain is
@@ -143,19 +144,22 @@ __global__ void __launch_bounds__((1 << LOGN) / 16, LOGN >= 13 ? 1 : 2)
 #pragma unroll
           for (int r = 0; r < 8; ++r) {
             const int m = j + r * (n / 8);
+            const int64_t at = (int64_t)d * L + a0 + 2 * m;   // index of row[2 m] in the background
             if constexpr (!VEC) {
               const int o = odd ? 1 : 0;
-              v[r] = make_float2(__ldg(&row[o + 2 * m]), __ldg(&row[o + 2 * m + 1]));
+              v[r] = GWX_IDX_OK(at + o + 1, (int64_t)D * L, 0x101)
+                         ? make_float2(__ldg(&row[o + 2 * m]), __ldg(&row[o + 2 * m + 1]))
+                         : make_float2(0.f, 0.f);
             } else {
-              const float2 q = __ldg(&row2[m]);
+              const float2 q = GWX_IDX_OK(at + 1, (int64_t)D * L, 0x102) ? __ldg(&row2[m]) : make_float2(0.f, 0.f);
               v[r] = q;
               if (odd) {   // the window starts at an odd sample: pair (own .y, next pair's .x)
                 float nx;
                 if constexpr (T >= 32) {
                   nx = __shfl_down_sync(0xffffffffu, q.x, 1);
-                  if (lane == 31) nx = __ldg(&row[2 * m + 2]);
+                  if (lane == 31) nx = GWX_IDX_OK(at + 2, (int64_t)D * L, 0x103) ? __ldg(&row[2 * m + 2]) : 0.f;
                 } else {
-                  nx = __ldg(&row[2 * m + 2]);
+                  nx = GWX_IDX_OK(at + 2, (int64_t)D * L, 0x103) ? __ldg(&row[2 * m + 2]) : 0.f;
                 }
                 v[r] = make_float2(q.y, nx);
               }
@@ -253,7 +257,9 @@ __global__ void __launch_bounds__((1 << LOGN) / 16, LOGN >= 13 ? 1 : 2)
         for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], w[r]);
         dft8<true, false>(v);
 #pragma unroll
-        for (int r = 0; r < 8; ++r) __stcs(&out[j + r * (n / 8)], v[r]);
+        for (int r = 0; r < 8; ++r)
+          if (GWX_IDX_OK((b * D + d) * N + 2 * (j + r * (n / 8)) + 1, B * D * N, 0x104))
+            __stcs(&out[j + r * (n / 8)], v[r]);
       }
       __syncthreads();
     }

@@ -6,6 +6,7 @@
 namespace gwx {
 
 cudaError_t init_tables_waveform() { return fill_tables_for_this_tu(); }
+cudaError_t debug_take_waveform(unsigned long long* v) { return dbg_take_this_tu(v); }
 
 // One thread per draw: FP64 set-up of the waveform and projection coefficients.
 // One thread per draw.  The set-up is FP64-throughput bound (GB300 issues a warp's
@@ -207,12 +208,13 @@ k_loglike(const double* __restrict__ theta, SetupConsts kc, double fs, DetParams
       const float t = waveform_turns(c, k, k76);
 #pragma unroll
       for (int d = 0; d < ND; ++d) {
-        const float x = k76 * __ldg(&W[(int64_t)d * F + k]);
+        const float x = GWX_IDX_OK((int64_t)d * F + k, (int64_t)ND * F, 0x201) ? k76 * __ldg(&W[(int64_t)d * F + k]) : 0.f;
         const float4 g = c.g[d];
         const float2 ph = expm2pi(t + lin_turns(c.nu[d], k));
         // per-draw constant applied with one rounding so it carries no systematic error
         const float2 H = cmul(make_float2(df_scale(g.x, g.y, x), df_scale(g.z, g.w, x)), ph);
-        const float2 yv = __ldg(&Y[(e * ND + d) * F + k]);
+        const float2 yv = GWX_IDX_OK((e * ND + d) * F + k, E * ND * F, 0x202) ? __ldg(&Y[(e * ND + d) * F + k])
+                                                                              : make_float2(0.f, 0.f);
         const float term = fmaf(H.x, H.x - 2.f * yv.x, H.y * (H.y - 2.f * yv.y));
         const float yk = term - comp[d];
         const float tk = sum[d] + yk;
@@ -238,7 +240,7 @@ k_loglike(const double* __restrict__ theta, SetupConsts kc, double fs, DetParams
     double yy = 0.0;
 #pragma unroll
     for (int c = 0; c < YY_CHUNKS; ++c) yy += yy_part[(int64_t)e_own * YY_CHUNKS + c];
-    lnl[s_own] = -(yy + ((double)own_hi + (double)own_lo)) * invN;
+    if (GWX_IDX_OK(s_own, S, 0x203)) lnl[s_own] = -(yy + ((double)own_hi + (double)own_lo)) * invN;
   }
 }
 
@@ -386,11 +388,13 @@ k_loglike_tmarg(const double* __restrict__ theta, SetupConsts kc, double fs, Det
         const float tt = waveform_turns(c, k, k76);
 #pragma unroll
         for (int d = 0; d < ND; ++d) {
-          const float x = k76 * __ldg(&W[(int64_t)d * F + k]);
+          const float x =
+              GWX_IDX_OK((int64_t)d * F + k, (int64_t)ND * F, 0x301) ? k76 * __ldg(&W[(int64_t)d * F + k]) : 0.f;
           const float4 gg = c.g[d];
           const float2 ph = expm2pi(tt + lin_turns(c.nu[d], k));
           const float2 H = cmul(make_float2(df_scale(gg.x, gg.y, x), df_scale(gg.z, gg.w, x)), ph);
-          const float2 yv = __ldg(&Y[(e * ND + d) * F + k]);
+          const float2 yv = GWX_IDX_OK((e * ND + d) * F + k, E * ND * F, 0x302) ? __ldg(&Y[(e * ND + d) * F + k])
+                                                                                : make_float2(0.f, 0.f);
           acc.x = fmaf(yv.x, H.x, fmaf(yv.y, H.y, acc.x));
           acc.y = fmaf(yv.y, H.x, fmaf(-yv.x, H.y, acc.y));
           const float yk = fmaf(H.x, H.x, H.y * H.y) - hcmp;
@@ -487,7 +491,7 @@ k_loglike_tmarg(const double* __restrict__ theta, SetupConsts kc, double fs, Det
       double yy = 0.0;
 #pragma unroll
       for (int c = 0; c < YY_CHUNKS; ++c) yy += yy_part[e * YY_CHUNKS + c];
-      lnl[base + j] = -(yy + H2) * invN + (double)M + log((double)Sm) - log_J;
+      if (GWX_IDX_OK(base + j, S, 0x303)) lnl[base + j] = -(yy + H2) * invN + (double)M + log((double)Sm) - log_J;
     }
     __syncthreads();                                          // c_k and the reduction slots are reused
   }
