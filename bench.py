@@ -476,6 +476,13 @@ def timed_steps(torch, sm, flush, rank, first, count, clocks=None, dist=None):
             sm.launches - l0)
 
 
+def launch_shape_record(shape):
+    """What the fused pass's launch shape bits mean (staged shapes run in place)."""
+    staged = bool(shape & 8)
+    return {"autotuned": shape, "staged_crop_and_filter": staged, "two_buffer_passes": bool(shape & 1) and not staged,
+            "blocks_per_sm": (shape >> 1) & 3 or "as many as fit"}
+
+
 def roofline_alu(torch, wl, sim_ms_mean, clk):
     """Roofline object of the fused call: algorithmic FP32 flops per launch / its mean
     CUDA-event duration, against the FP32 peak of this GPU (SM count from the device,
@@ -486,7 +493,7 @@ def roofline_alu(torch, wl, sim_ms_mean, clk):
     achieved = flops_per_injection(wl) * B / (sim_ms_mean * 1e-3) / 1e12
     out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
            "traffic": traffic_per_launch(wl),
-           "kernel": "simulate_prepared call (k_whiten_filter, k_packed_filter, k_simulate), timed from after the "
+           "kernel": "simulate_prepared call (k_whiten_filter, k_simulate), timed from after the "
                      "wait for the side-stream preparation",
            "flops_per_injection": flops_per_injection(wl), "injections_per_launch": B,
            "algorithmic_bytes_per_launch": B * D * N * 4,
@@ -512,8 +519,7 @@ def hl3_leg(gwx, torch, rank, args, flush, steps=200):
     del sim
     ms = statistics.mean(step_ms)
     roof = roofline_alu(torch, wl, statistics.mean(sim_ms), None)
-    roof["launch_shape"] = {"autotuned": shape, "two_buffer_passes": bool(shape & 1),
-                            "blocks_per_sm": (shape >> 1) & 3 or "as many as fit"}
+    roof["launch_shape"] = launch_shape_record(shape)
     return {"workload": describe(wl), "steps": steps, "ms_per_step": ms, "injections_per_s": wl["B"] / (ms * 1e-3),
             "roofline": roof}
 
@@ -931,8 +937,7 @@ def run_gpu(args, wl):
     padded = padded_leg(gwx, torch, rank)
 
     roof = roofline_alu(torch, wl, statistics.mean(sim_ms), clk)
-    roof["launch_shape"] = {"autotuned": shape, "two_buffer_passes": bool(shape & 1),
-                            "blocks_per_sm": (shape >> 1) & 3 or "as many as fit"}
+    roof["launch_shape"] = launch_shape_record(shape)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

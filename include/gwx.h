@@ -241,7 +241,12 @@ int gwx_whiten_static(const float* d, const double* psd, int64_t seg_len, double
  * Stockham passes that alternate between two shared-memory window buffers (one block
  * barrier per pass, twice the shared memory) instead of passes in place in one (two
  * barriers per pass); bits 1-2 the resident blocks per SM (0: as many as fit, else 1..3,
- * capped at what fits).  Which is fastest depends on the window length and the number
+ * capped at what fits); bit 3 passes in place with the next window's background crop and
+ * the next detector's whitening filter copied into shared memory by bulk asynchronous
+ * copies one window ahead (used when noise and the workspace are 16-byte aligned and
+ * L % 4 == 0, else the shape falls back to bits 0-2; overrides bit 0).  A staged copy that
+ * never completes makes the block stop after a bounded wait and is reported by
+ * gwx_device_status.  Which is fastest depends on the window length and the number
  * of detectors (e.g. through how much L1 the larger shared-memory carve-out leaves), so:
  * gwx_simulate_autotune builds the whitening filter from psd into the workspace, then
  *   times each candidate shape of the fused pass on the caller's batch (its per-draw
@@ -250,7 +255,7 @@ int gwx_whiten_static(const float* d, const double* psd, int64_t seg_len, double
  *   *shape_out (optional) receives it.  It synchronises with the stream.  Arguments as
  *   gwx_simulate_prepared; B >= 1.
  * gwx_simulate_shape: shape >= 0 records that shape for (N, D), -1 forgets the record
- *   (back to the default: two buffers for N >= 16384, else in place), -2 only asks;
+ *   (back to the default: staged for N >= 8192, else in place), -2 only asks;
  *   returns the shape gwx_simulate_prepared now uses for (N, D), or a negative status. */
 int gwx_simulate_autotune(const float* noise, int64_t L, const double* psd, int64_t seg_len, double fs,
                           double f_lo, int D, int64_t B, int64_t N, const int64_t* offsets, float* y,

@@ -120,7 +120,6 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 size_t whiten_ws_bytes(int D, int64_t N) { return align_up((size_t)D * (size_t)(N / 2 + 1) * sizeof(float)); }
 size_t coef_bytes(int64_t B) { return align_up((size_t)B * sizeof(DrawCoef)); }
-size_t packed_ws_bytes(int D, int64_t N) { return align_up((size_t)D * (size_t)(N / 2) * sizeof(float2)); }
 
 int check_ws(void* ws, size_t have, size_t need) {
   if (need == 0) return GWX_OK;
@@ -171,11 +170,10 @@ int check_sim_shapes(int D, int64_t L, int64_t B, int64_t N, double fs, double f
 }
 
 // simulate workspace: [W: D x (N/2+1) floats | Wp: D x N/2 float2 | per-draw coefficients]
-float2* sim_packed(void* ws, int D, int64_t N) {
-  return reinterpret_cast<float2*>(reinterpret_cast<char*>(ws) + whiten_ws_bytes(D, N));
-}
+// floats of the filter region at the start of a simulation workspace (a multiple of 64)
+int64_t sim_filter_floats(int D, int64_t N) { return (int64_t)(whiten_ws_bytes(D, N) / sizeof(float)); }
 DrawCoef* sim_coef(void* ws, int D, int64_t N) {
-  return reinterpret_cast<DrawCoef*>(reinterpret_cast<char*>(ws) + whiten_ws_bytes(D, N) + packed_ws_bytes(D, N));
+  return reinterpret_cast<DrawCoef*>(reinterpret_cast<char*>(ws) + whiten_ws_bytes(D, N));
 }
 }  // namespace
 
@@ -408,7 +406,7 @@ int gwx_unwhiten(const float* y, const double* psd, int64_t seg_len, double fs, 
 
 size_t gwx_simulate_batch_workspace(int D, int64_t B, int64_t N) {
   if (D < 1 || B < 0 || N < 2) return 0;
-  return whiten_ws_bytes(D, N) + packed_ws_bytes(D, N) + coef_bytes(B);
+  return whiten_ws_bytes(D, N) + coef_bytes(B);
 }
 
 int gwx_prepare_batch(const gwx_prior* prior, uint64_t seed, uint32_t step, int64_t L, int64_t N, double fs,
@@ -465,19 +463,17 @@ int gwx_simulate_prepared(const float* noise, int64_t L, const double* psd, int6
   GWX_TRY(ensure_init());
   cudaStream_t s = as_stream(stream);
   float* W = reinterpret_cast<float*>(workspace);
-  float2* Wp = sim_packed(workspace, D, N);
-  if (!(flags & GWX_SIM_FILTERS_READY)) {
+  if (!(flags & GWX_SIM_FILTERS_READY))
     GWX_TRY(launched(launch_whiten_filter(psd, D, seg_len, fs, k_lo, N, W, s), "whiten filter"));
-    GWX_TRY(launched(launch_packed_filter(W, D, N, Wp, s), "packed filter"));
-  }
-  return launched(launch_simulate_fused(sim_coef(workspace, D, N), noise, L, offsets, W, Wp, k_lo, D, B, N, fs, y, s),
+  return launched(launch_simulate_fused(sim_coef(workspace, D, N), noise, L, offsets, W, sim_filter_floats(D, N), k_lo,
+                                        D, B, N, fs, y, s),
                   "simulate");
 }
 
 int gwx_simulate_shape(int64_t N, int D, int shape) {
   GWX_TRY(check_window(N));
   if (D < 1 || D > GWX_MAX_DET) return fail(GWX_ESHAPE, "D=%d outside [1, %d]", D, GWX_MAX_DET);
-  if (shape < -2 || shape > 7) return fail(GWX_EINVAL, "shape %d outside [-2, 7]", shape);
+  if (shape < -2 || shape > 15) return fail(GWX_EINVAL, "shape %d outside [-2, 15]", shape);
   if (shape >= -1) sim_shape_set(N, D, shape);
   return sim_shape_for(N, D);
 }
@@ -497,12 +493,13 @@ int gwx_simulate_autotune(const float* noise, int64_t L, const double* psd, int6
   GWX_TRY(ensure_init());
   cudaStream_t s = as_stream(stream);
   float* W = reinterpret_cast<float*>(workspace);
-  float2* Wp = sim_packed(workspace, D, N);
   GWX_TRY(launched(launch_whiten_filter(psd, D, seg_len, fs, k_lo, N, W, s), "whiten filter"));
-  GWX_TRY(launched(launch_packed_filter(W, D, N, Wp, s), "packed filter"));
   const DrawCoef* coef = sim_coef(workspace, D, N);
-  // two-buffer passes or not x all resident blocks per SM or one
-  const int candidates[] = {0, 1, 2, 3};
+  const int64_t Wcap = sim_filter_floats(D, N);
+  // two-buffer passes or not x all resident blocks per SM or one, and the staged form
+  const bool stage = sim_can_stage(noise, L, W, N);
+  const int candidates[] = {0, 1, 2, 3, 8, 10};
+  const int n_cand = stage ? 6 : 4;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(cudaGetLastError(), "autotune event");
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -512,11 +509,12 @@ int gwx_simulate_autotune(const float* noise, int64_t L, const double* psd, int6
   int best = -1;
   float best_ms = 0.f;
   cudaError_t err = cudaSuccess;
-  for (int c : candidates) {
-    err = launch_simulate_fused(coef, noise, L, offsets, W, Wp, k_lo, D, B, N, fs, y, s, c);   // warm-up
+  for (int ci = 0; ci < n_cand; ++ci) {
+    const int c = candidates[ci];
+    err = launch_simulate_fused(coef, noise, L, offsets, W, Wcap, k_lo, D, B, N, fs, y, s, c);   // warm-up
     if (err == cudaSuccess) err = cudaEventRecord(e0, s);
     for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep)
-      err = launch_simulate_fused(coef, noise, L, offsets, W, Wp, k_lo, D, B, N, fs, y, s, c);
+      err = launch_simulate_fused(coef, noise, L, offsets, W, Wcap, k_lo, D, B, N, fs, y, s, c);
     if (err == cudaSuccess) err = cudaEventRecord(e1, s);
     if (err == cudaSuccess) err = cudaEventSynchronize(e1);
     float ms = 0.f;
@@ -823,10 +821,11 @@ int gwx_debug_status(uint64_t* first_bad) {
 
 int gwx_device_status(void) {
   GWX_TRY(ensure_init());
-  int st = 0, st2 = 0;
+  int st = 0, st2 = 0, st3 = 0;
   GWX_TRY(launched(gemm_status(&st), "device status"));
   GWX_TRY(launched(flow_fused_status(&st2), "device status"));
-  if (st != 0 || st2 != 0)
+  GWX_TRY(launched(sim_status(&st3), "device status"));
+  if (st != 0 || st2 != 0 || st3 != 0)
     return fail(GWX_ETIMEOUT, "a kernel gave up waiting for its own copies; its output is incomplete");
   return GWX_OK;
 }

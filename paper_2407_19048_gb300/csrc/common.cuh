@@ -55,6 +55,11 @@ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
+// The same product with one explicit rounding per partial product, so that it is fused
+// the same way wherever it is inlined.
+__device__ __forceinline__ float2 cmul_rn(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -__fmul_rn(a.y, b.y)), fmaf(a.x, b.y, __fmul_rn(a.y, b.x)));
+}
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 // multiply by -i (forward) or +i (inverse)
@@ -73,9 +78,8 @@ constexpr int KMAX = 16384;
 
 // Per-pass twiddles of the Stockham passes, laid out [pass][row][jm] so that the
 // butterflies of consecutive threads (consecutive jm) read consecutive entries.
-// Radix-8 passes keep rows r = 1, 2, 4 (the other powers are formed by products),
-// radix-4 passes rows 1..3, radix-2 passes row 1; one set for every stride
-// Ns = 2, 4, ..., 4096 of each radix.
+// A radix-R pass keeps rows r = 1 .. R-1; one set for every stride Ns = 2, 4, ..., 4096
+// of each radix 8, 4 and 2.
 __host__ __device__ constexpr int twp_rows(int R) { return R - 1; }   // rows r = 1 .. R-1
 constexpr int TWP_NSETS = 12;                                    // Ns = 2 .. 4096
 __host__ __device__ constexpr int twp_ns(int q) { return 2 << q; }

@@ -54,7 +54,6 @@ size_t welch_ws(int D, int64_t L, int64_t M, int64_t stride);
 cudaError_t launch_whiten_filter(const double* psd, int D, int64_t M, double fs, int k_lo, int64_t N, float* W,
                                  cudaStream_t s, bool inverse = false);
 // Packed-domain whitening coefficients (alpha, beta) [D][N/2] from W [D][N/2+1].
-cudaError_t launch_packed_filter(const float* W, int D, int64_t N, float2* Wp, cudaStream_t s);
 cudaError_t launch_whiten_rows(const float* d, const float* W, int64_t rows, int D, int64_t N, float* y,
                                cudaStream_t s);
 cudaError_t launch_inject_rows(const float* noise, int D, int64_t L, const int64_t* offsets, const float2* hdet,
@@ -63,14 +62,20 @@ cudaError_t launch_inject_padded(const float* noise, int D, int64_t L, const int
                                  int64_t B, int64_t N, int64_t Np, double fs, float* d, cudaStream_t s);
 cudaError_t launch_rfft_rows(const float* x, int64_t R, int64_t N, float2* X, cudaStream_t s);
 cudaError_t launch_irfft_rows(const float2* X, int64_t R, int64_t N, float* x, cudaStream_t s);
+// W: the whitening filter [D][N/2 + 1] at the start of an allocation of Wcap floats
+// (Wcap a multiple of 4; the staged shape copies whole 16-byte words up to it).
 cudaError_t launch_simulate_fused(const DrawCoef* coef, const float* noise, int64_t L, const int64_t* offsets,
-                                  const float* W, const float2* Wp, int k_lo, int D, int64_t B, int64_t N, double fs,
+                                  const float* W, int64_t Wcap, int k_lo, int D, int64_t B, int64_t N, double fs,
                                   float* y, cudaStream_t s, int shape = -1);
 // Launch shape of the fused pass for windows of N samples and D detectors (bit 0: two
-// shared buffers, bits 1-2: blocks per SM, 0 = the occupancy limit): the tuned choice, or
-// the default; sim_shape_set records one (a negative shape forgets it).
+// shared buffers, bits 1-2: blocks per SM, 0 = the occupancy limit, bit 3: staged crop and
+// filter): the tuned choice, or the default; sim_shape_set records one (a negative shape
+// forgets it); sim_can_stage: whether the staged shape applies to these arrays.
 int sim_shape_for(int64_t N, int D);
 void sim_shape_set(int64_t N, int D, int shape);
+bool sim_can_stage(const float* noise, int64_t L, const float* W, int64_t N);
+// Reads and clears the record of a fused pass that gave up waiting for its staged copies.
+cudaError_t sim_status(int* status);
 // yy: E doubles of scratch for the per-event sum of |Y|^2 over the band.
 // Per-event data norms (E x 8 FP64 partials in yy_part, loglike_norm_bytes(E)) and
 // the fused per-sample set-up + likelihood.

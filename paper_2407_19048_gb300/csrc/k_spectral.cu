@@ -160,38 +160,6 @@ cudaError_t launch_whiten_filter(const double* psd, int D, int64_t M, double fs,
   return cudaGetLastError();
 }
 
-// Packed-domain form of the whitening filter for transforms that keep the real window
-// as n = N/2 complex points Z (z_m = x_2m + i x_2m+1).  With s = W/n and
-// theta = 2 pi k/N, unpacking X_k, X_{n-k} from Z_k, Z_{n-k}, scaling by s and
-// repacking collapses to
-//   Z'_k = alpha_k Z_k + i beta_k conj(Z_{n-k}),
-//   alpha_k = (s_k (1 - sin theta) + s_{n-k} (1 + sin theta)) / 2,
-//   beta_k  = cos theta (s_k - s_{n-k}) / 2,
-// for 0 < k < n; entry 0 holds ((s_0 + s_n)/2, (s_0 - s_n)/2) for the DC/Nyquist pair.
-__global__ void k_packed_filter(const float* __restrict__ W, int D, int n, float2* __restrict__ Wp) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (int64_t)D * n) return;
-  const int d = (int)(i / n), k = (int)(i % n);
-  const float* Wd = W + (int64_t)d * (n + 1);
-  const float inv_n = 1.0f / (float)n;
-  if (k == 0) {
-    const float s0 = Wd[0] * inv_n, sn = Wd[n] * inv_n;
-    Wp[i] = make_float2(0.5f * (s0 + sn), 0.5f * (s0 - sn));
-    return;
-  }
-  const float sk = Wd[k] * inv_n, snk = Wd[n - k] * inv_n;
-  float sn_, cs_;
-  sincospif((float)k / (float)n, &sn_, &cs_);   // theta = 2 pi k / N = pi k / n
-  Wp[i] = make_float2(0.5f * (sk * (1.0f - sn_) + snk * (1.0f + sn_)), 0.5f * cs_ * (sk - snk));
-}
-
-cudaError_t launch_packed_filter(const float* W, int D, int64_t N, float2* Wp, cudaStream_t s) {
-  const int n = (int)(N / 2);
-  const int64_t total = (int64_t)D * n;
-  k_packed_filter<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(W, D, n, Wp);
-  return cudaGetLastError();
-}
-
 // ----------------------------------------------------------------- row helpers
 template <int LOGN>
 __device__ __forceinline__ void load_real_row(float2* z, const float* row, int t, bool live) {

@@ -29,9 +29,9 @@ from . import DETECTORS, NPARAM, _det_ids, _prior, _ptr, _stream, _workspace, _c
 
 
 class Simulator:
-    # kernels per call: prepare 2, colored noise 2, Welch 2, simulate_prepared 3 (1 when the
+    # kernels per call: prepare 2, colored noise 2, Welch 2, simulate_prepared 2 (1 when the
     # whitening filter of its workspace is still current)
-    LAUNCHES = {"prepare": 2, "colored_noise": 2, "welch": 2, "simulate": 3, "simulate_reuse": 1}
+    LAUNCHES = {"prepare": 2, "colored_noise": 2, "welch": 2, "simulate": 2, "simulate_reuse": 1}
 
     def __init__(self, workload, device=None, noise_on_device=True, pipeline=False, background_every=1):
         import torch
