@@ -859,7 +859,7 @@ def run_gpu(args, wl):
             print(json.dumps({"metric": "whitened injections/sec", "value": value, "unit": "injections/s",
                               "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                               "ms_per_step": 1e3 * total_s / args.steps, "config": {"workload": describe(wl)},
-                              "launch_shape": shape,
+                              "launch_shape": shape, "roofline": roofline_alu(torch, wl, statistics.mean(sim_ms), clk),
                               "note": "--only-step profiling run: no end-to-end, likelihood or CPU legs"}), flush=True)
         if world > 1:
             dist.destroy_process_group()

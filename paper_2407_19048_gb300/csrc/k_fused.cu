@@ -285,12 +285,13 @@ __global__ void __launch_bounds__((1 << LOGN) / 16, LOGN >= 13 ? 1 : 2)
     const DrawCoef& c = sc;
 
     // waveform values (turns, amplitude factor) of the 16 bins this thread owns in the
-    // short-radix pass, kept in shared memory as wv[v][t] for the D detectors
-#pragma unroll
+    // short-radix pass, kept in shared memory as wv[v][t] for the D detectors (a rolled
+    // loop: the evaluation is long, and 32 inlined copies crowd the instruction cache)
+#pragma unroll 1
     for (int s = 0; s < SLOTS; ++s) {
       const int p = t + s * T;
       const int jA = p, jB = p ? NB - p : NB / 2;
-#pragma unroll
+#pragma unroll 1
       for (int r = 0; r < RL; ++r) {
         float tt, aa;
         wave_bin(c, jA + NB * r, k_lo, tt, aa);
