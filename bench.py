@@ -47,9 +47,10 @@ SM_MAX_MHZ_FALLBACK = 2070.0
 # dirty lines is counted and this launch's own L2-resident tail is not), keyed by
 # workload, with the hash of the kernel sources it was measured on.  A workload whose
 # capture does not match the current sources reports null.
-TRAFFIC = {"sweep": {"bytes_per_launch": 8 * 205469696, "B": 8192, "sources_sha1": "8e52b108e6dd2f462699195da6dd0276896914f4",
-                    "note": "ncu on 1024 draws of the same geometry (205.47 MB in steady state), scaled by the "
-                            "draws per launch"}}
+TRAFFIC = {"sweep": {"bytes_per_launch": 8 * 199872512, "B": 8192, "sources_sha1": "9bad0d9afdb3a0abcbe00bfc2f13efdfe41e0c82",
+                    "note": "ncu DRAM read + write of the second of two back-to-back 1024-draw launches of the same "
+                            "geometry (caches not flushed: it pays the first launch's write-back, 199.87 MB), scaled "
+                            "by the draws per launch"}}
 
 
 def _measured_peaks():
@@ -82,7 +83,7 @@ def flops_per_injection(wl):
 
 def kernel_sources_sha1():
     h = hashlib.sha1()
-    for f in ("k_fused.cu", "fft16.cuh", "common.cuh", "waveform.cuh"):
+    for f in ("k_fused.cu", "fft16.cuh", "fft16r.cuh", "common.cuh", "waveform.cuh", "tc05.cuh"):
         with open(os.path.join(ROOT, "paper_2407_19048_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
