@@ -706,6 +706,30 @@ int gwx_maxpool_backward(const float* dy, const uint8_t* arg, int64_t B, int T, 
 int gwx_mean_time(const void* x, int64_t B, int T, int C, void* m, void* stream);
 int gwx_mean_time_backward(const float* dm, int64_t B, int T, int C, float* dx, void* stream);
 
+/* ---- ResNet-1D: stride-1 convolutions as implicit GEMMs (Sec. 4) ---------------------
+ * The summary's stride-1 convolutions with zero "same" padding, p = (k - 1)/2, on the
+ * tensor cores without an im2col matrix: the product's A tiles come straight from the
+ * channels-last activations through a 3-D tensor map, one 128-time x 64-channel box per
+ * tap and channel block, zero-filled outside the series.
+ * gwx_conv1d_bf16: z[b][t][o] = sum_{j < k, c < C} x[b][t + j - p][c] W[o][j C + c]
+ *   (+ addend[b][t][o]); x bfloat16 [B][T][C], W bfloat16 [O][k C] (the row layout of
+ *   gwx_im2col with K = k C), z FP32 [B][T][O], addend FP32 or NULL.
+ * gwx_conv1d_bf16_backward: from dz FP32 [B][T][O], rounded to bfloat16 for the products
+ *   as in gwx_dense_bf16_backward: dx FP32 [B][T][C] = sum_{j, o} dz[b][t - j + p][o]
+ *   W[o][j C + c] (+ addend FP32 [B][T][C] or NULL) and dW FP32 [O][k C] =
+ *   sum_{b, t} dz[b][t][o] x[b][t + j - p][c] (split-K, deterministic); either output may
+ *   be NULL.  Workspace gwx_conv1d_bf16_backward_workspace(B, T, C, O, k) bytes.
+ * Sizes: T % 128 == 0, C % 64 == 0, O % 64 == 0, k odd in [1, 15], B >= 1, B T <= 2^26;
+ * x, W, z, dx, dW 16-byte aligned, dz and addend 4-byte aligned; else GWX_ESHAPE or
+ * GWX_EINVAL; a workspace below the size GWX_ENOMEM.  A bounded wait that expires is
+ * reported by gwx_device_status. */
+int gwx_conv1d_bf16(const void* x, int64_t B, int64_t T, int C, int k, const void* W, int O, const float* addend,
+                    float* z, void* stream);
+size_t gwx_conv1d_bf16_backward_workspace(int64_t B, int64_t T, int C, int O, int k);
+int gwx_conv1d_bf16_backward(const float* dz, const void* x, const void* W, int64_t B, int64_t T, int C, int O, int k,
+                             const float* addend, float* dx, float* dW, void* workspace, size_t workspace_bytes,
+                             void* stream);
+
 /* ---- sky maps ---------------------------------------------------------------------
  * The paper's inference ends in a sky-localisation map in the HEALPix format (Sec. 5).
  * gwx_skymap: map [12 nside^2] (FP64) = the histogram of samples' sky positions (rows RA

@@ -27,7 +27,7 @@ __all__ = ["GwxError", "version", "init", "detector_geometry", "sample_prior", "
            "importance_weights", "gemm_bf16", "dense_bf16", "dense_bf16_backward", "gemm_autotune", "spectral_features",
            "cross_features", "lag_features", "proposal_targets",
            "gauss_nll", "adamw", "adamw_clip", "skymap", "vicreg", "retime", "sample_proposal", "device_status", "selftest_bounded_wait", "rfft", "irfft",
-           "workspace_bytes", "debug_check", "TAYLORF2", "IMRPHENOMD", "DETECTORS"]
+           "workspace_bytes", "debug_check", "conv1d_bf16", "conv1d_bf16_backward", "TAYLORF2", "IMRPHENOMD", "DETECTORS"]
 
 
 class GwxError(RuntimeError):
@@ -434,6 +434,43 @@ def dense_bf16_backward(X, W, bias, dY, act=ACT_NONE, want_dx=True, want_db=None
     _check(lib.gwx_dense_bf16_backward(_ptr(X), _ptr(W), _ptr(bias), _ptr(dY), M, N, K, act, _ptr(dX), _ptr(dW),
                                        _ptr(db), _ptr(ws), nb, _stream()))
     return dX, dW, db
+
+
+def conv1d_bf16(x, W, k, addend=None, out=None):
+    """Stride-1 "same" convolution z [B][T][O] (float32) of bfloat16 x [B][T][C] with
+    bfloat16 W [O][k C] (tap-major rows), plus addend if given, as an implicit GEMM."""
+    torch = _torch()
+    _dev(x, torch.bfloat16, "x")
+    _dev(W, torch.bfloat16, "W")
+    B, T, C = x.shape
+    O = W.shape[0]
+    if addend is not None:
+        _dev(addend, torch.float32, "addend")
+    z = torch.empty((B, T, O), dtype=torch.float32, device=x.device) if out is None else out
+    _check(_lib.load().gwx_conv1d_bf16(_ptr(x), B, T, C, int(k), _ptr(W), O, _ptr(addend), _ptr(z), _stream()))
+    return z
+
+
+def conv1d_bf16_backward(dz, x, W, k, addend=None, want_dx=True, want_dW=True, workspace=None):
+    """(dx float32 [B][T][C] (+ addend), dW float32 [O][k C]) of z = conv1d_bf16(x, W, k)
+    for dL/dz = dz (float32 [B][T][O]); either is None when not wanted."""
+    torch = _torch()
+    _dev(dz, torch.float32, "dz")
+    _dev(x, torch.bfloat16, "x")
+    _dev(W, torch.bfloat16, "W")
+    B, T, C = x.shape
+    O = W.shape[0]
+    if addend is not None:
+        _dev(addend, torch.float32, "addend")
+    dev = x.device
+    dx = torch.empty((B, T, C), dtype=torch.float32, device=dev) if want_dx else None
+    dW = torch.empty((O, int(k) * C), dtype=torch.float32, device=dev) if want_dW else None
+    lib = _lib.load()
+    ws, nb = workspace if workspace is not None else _workspace(
+        lib.gwx_conv1d_bf16_backward_workspace(B, T, C, O, int(k)), dev)
+    _check(lib.gwx_conv1d_bf16_backward(_ptr(dz), _ptr(x), _ptr(W), B, T, C, O, int(k), _ptr(addend), _ptr(dx),
+                                        _ptr(dW), _ptr(ws), nb, _stream()))
+    return dx, dW
 
 
 def _host3(v):

@@ -69,6 +69,10 @@ SIGNATURES = {
     "gwx_log_likelihood_workspace": (c_size, [c_i64, c_int, c_i64, c_i64]),
     "gwx_log_likelihood": (c_int, [c_int, c_vp, c_i64, c_int, c_i64, c_vp, c_i64, c_dbl, c_dbl, c_i32p, c_dbl,
                                    c_vp, c_vp, c_i64, c_vp, c_vp, c_size, c_vp]),
+    "gwx_conv1d_bf16": (c_int, [c_vp, c_i64, c_i64, c_int, c_int, c_vp, c_int, c_vp, c_vp, c_vp]),
+    "gwx_conv1d_bf16_backward_workspace": (c_size, [c_i64, c_i64, c_int, c_int, c_int]),
+    "gwx_conv1d_bf16_backward": (c_int, [c_vp, c_vp, c_vp, c_i64, c_i64, c_int, c_int, c_int, c_vp, c_vp, c_vp, c_vp,
+                                         c_size, c_vp]),
     "gwx_debug_build": (c_int, []),
     "gwx_debug_status": (c_int, [ctypes.POINTER(c_u64)]),
     "gwx_debug_guard": (c_int, [c_vp, c_size, c_size, c_vp]),

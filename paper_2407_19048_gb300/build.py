@@ -23,7 +23,7 @@ LIB = os.path.join(HERE, "libgwx.so")
 # kernels' global accesses, recorded for gwx_debug_status instead of faulting)
 BUILD_DEBUG = os.path.join(HERE, "_build_debug")
 LIB_DEBUG = os.path.join(HERE, "libgwx_debug.so")
-UNITS = ["capi.cu", "k_random.cu", "k_spectral.cu", "k_waveform.cu", "k_fused.cu", "k_weights.cu", "k_gemm.cu", "k_dense.cu", "k_learn.cu", "k_noalloc.cu", "k_flow.cu", "k_flow_fused.cu", "k_skymap.cu", "k_vicreg.cu", "k_resnet.cu"]
+UNITS = ["capi.cu", "k_random.cu", "k_spectral.cu", "k_waveform.cu", "k_fused.cu", "k_weights.cu", "k_gemm.cu", "k_dense.cu", "k_learn.cu", "k_noalloc.cu", "k_flow.cu", "k_flow_fused.cu", "k_skymap.cu", "k_vicreg.cu", "k_resnet.cu", "k_conv.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE]

@@ -1075,6 +1075,43 @@ int gwx_mean_time_backward(const float* dm, int64_t B, int T, int C, float* dx, 
   return launched(launch_mean_time_back(dm, B, T, C, dx, as_stream(stream)), "mean_time_backward");
 }
 
+static int check_conv(int64_t B, int64_t T, int C, int O, int k) {
+  if (B < 1 || T < 128 || T % 128 || C < 64 || C % 64 || O < 64 || O % 64 || k < 1 || k > 15 || k % 2 == 0 ||
+      B * T > ((int64_t)1 << 26) || (int64_t)k * C > ((int64_t)1 << 20) || (int64_t)k * O > ((int64_t)1 << 20))
+    return fail(GWX_ESHAPE, "conv1d sizes B=%lld T=%lld C=%d O=%d k=%d (T %% 128 == 0, C and O multiples of 64, "
+                "k odd <= 15, B T <= 2^26)", (long long)B, (long long)T, C, O, k);
+  return GWX_OK;
+}
+
+int gwx_conv1d_bf16(const void* x, int64_t B, int64_t T, int C, int k, const void* W, int O, const float* addend,
+                    float* z, void* stream) {
+  GWX_TRY(check_conv(B, T, C, O, k));
+  if (!x || !W || !z) return fail(GWX_EINVAL, "NULL array");
+  if ((((uintptr_t)x) | ((uintptr_t)W) | ((uintptr_t)z)) & 15u) return fail(GWX_EINVAL, "x, W and z must be 16-byte aligned");
+  if (((uintptr_t)addend) & 3u) return fail(GWX_EINVAL, "addend must be 4-byte aligned");
+  GWX_TRY(ensure_init());
+  return launched(launch_conv_forward(x, B, T, C, k, W, O, addend, z, as_stream(stream)), "conv1d_bf16");
+}
+
+size_t gwx_conv1d_bf16_backward_workspace(int64_t B, int64_t T, int C, int O, int k) {
+  if (B < 1 || T < 1 || C < 1 || O < 1 || k < 1) return 0;
+  return conv_backward_ws(B, T, C, O, k);
+}
+
+int gwx_conv1d_bf16_backward(const float* dz, const void* x, const void* W, int64_t B, int64_t T, int C, int O, int k,
+                             const float* addend, float* dx, float* dW, void* workspace, size_t workspace_bytes,
+                             void* stream) {
+  GWX_TRY(check_conv(B, T, C, O, k));
+  if (!dz || !x || !W) return fail(GWX_EINVAL, "NULL array");
+  if ((((uintptr_t)x) | ((uintptr_t)W) | ((uintptr_t)dx) | ((uintptr_t)dW)) & 15u)
+    return fail(GWX_EINVAL, "x, W, dx and dW must be 16-byte aligned");
+  if ((((uintptr_t)dz) | ((uintptr_t)addend)) & 3u) return fail(GWX_EINVAL, "dz and addend must be 4-byte aligned");
+  GWX_TRY(check_ws(workspace, workspace_bytes, conv_backward_ws(B, T, C, O, k)));
+  GWX_TRY(ensure_init());
+  return launched(launch_conv_backward(dz, x, W, B, T, C, O, k, addend, dx, dW, workspace, as_stream(stream)),
+                  "conv1d_bf16_backward");
+}
+
 size_t gwx_skymap_workspace(void) { return kAlign; }
 
 int gwx_skymap(const double* theta, const double* weights, int64_t S, int nside, double* map, void* workspace,

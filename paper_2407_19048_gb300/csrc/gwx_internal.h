@@ -104,6 +104,19 @@ cudaError_t launch_gemm_bf16(const void* A, const void* B, void* C, int64_t M, i
                              const float* bias, int act, int group, cudaStream_t s);
 // Split-K product C [M][N] (FP32) = A B^T for few tiles and a long K: the slices' partial
 // products go to `part` (gemm_splitk_ws bytes), then one kernel sums them in order.
+// Implicit-GEMM 1-D convolution (stride 1, zero "same" padding): out [Bn][T][N] FP32 =
+// sum_{j < k, c < C} x[b][t + dir (j - (k-1)/2)][c] W[o][j C + c] (+ addend); x bfloat16
+// channels last, W bfloat16 [N][k C].  T % 128 == 0, C % 64 == 0, 16-byte aligned x, W.
+cudaError_t launch_conv_gemm(const void* x, int64_t Bn, int64_t T, int64_t C, int k, int dir, const void* W, int64_t N,
+                             float* out, const float* addend, cudaStream_t s);
+// The ResNet's stride-1 convolutions (k_conv.cu): forward z [Bn][T][O] = conv(x, W)
+// (+ addend) and its backward (dx (+ addend), dW) through implicit GEMMs; the workspace
+// of the backward is conv_backward_ws bytes.
+size_t conv_backward_ws(int64_t Bn, int64_t T, int C, int O, int k);
+cudaError_t launch_conv_forward(const void* x, int64_t Bn, int64_t T, int C, int k, const void* W, int O,
+                                const float* addend, float* z, cudaStream_t s);
+cudaError_t launch_conv_backward(const float* dz, const void* x, const void* W, int64_t Bn, int64_t T, int C, int O,
+                                 int k, const float* addend, float* dx, float* dW, void* ws, cudaStream_t s);
 int gemm_splits(int64_t M, int64_t N, int64_t K);
 size_t gemm_splitk_ws(int64_t M, int64_t N, int64_t K);
 cudaError_t launch_gemm_splitk(const void* A, const void* B, float* C, int64_t M, int64_t N, int64_t K, float* part,

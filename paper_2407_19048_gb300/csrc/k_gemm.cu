@@ -35,18 +35,34 @@ namespace {
 
 using namespace tc;
 
-constexpr int GM = 128, GN = 256, GK = 64, STAGES = 4;
+constexpr int GM = 128, GN = 256, GK = 64, STAGES = 4;   // GN: the dense products' tile width
 constexpr int EPI_WARPS = 8;                            // two per tensor-memory lane quarter
 constexpr int GEMM_THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t A_BYTES = GM * GK * 2;               // 16 KiB
-constexpr uint32_t B_BYTES = GN * GK * 2;               // 32 KiB
-constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr uint32_t TMEM_COLS = GN;                      // FP32 accumulator columns
 constexpr uint32_t WAIT_POLLS = 1u << 22;
 constexpr uint32_t EPI_BUF_BYTES = 32 * 32 * 4;         // per epilogue warp: a 32 x 32 FP32 transpose tile
-constexpr size_t GEMM_SMEM = (size_t)STAGES * STAGE_BYTES + (size_t)EPI_WARPS * EPI_BUF_BYTES + 1024;
 
-constexpr uint32_t IDESC = idesc_bf16(GM, GN);   // 128 x 256 tiles
+// Per tile width TN_ (64, 128 or 256 columns of C): B tile, stage and accumulator sizes.
+template <int TN_>
+struct Tile {
+  static constexpr uint32_t B_BYTES = TN_ * GK * 2;
+  static constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr uint32_t TMEM_COLS = TN_;              // FP32 accumulator columns
+  static constexpr uint32_t IDESC = idesc_bf16(GM, TN_);
+  static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + (size_t)EPI_WARPS * EPI_BUF_BYTES + 1024;
+};
+constexpr size_t GEMM_SMEM = Tile<GN>::SMEM;
+
+// Implicit-GEMM convolution geometry (conv mode): A is the channels-last activation
+// x [B][T][Cin] as a 3-D tensor map; M tile tm covers times 128 (tm mod T/128) ..
+// + 127 of sample tm div (T/128), and K block kb covers tap kb div KC, channels
+// 64 (kb mod KC) .. + 63, read at time t + dir (tap - pad) (zero outside [0, T)).
+struct ConvGeo {
+  int T;     // time steps per sample (a multiple of 128)
+  int KC;    // Cin / 64
+  int pad;   // (k - 1) / 2
+  int dir;   // +1: convolution; -1: its input gradient (taps mirrored)
+};
 
 __device__ int g_gemm_status;
 
@@ -82,10 +98,17 @@ __device__ __forceinline__ void tile_coords(int t, int TM, int TN, int group, in
 // accumulators alternate between tiles, so a tile's epilogue overlaps the next tile's
 // main loop; "tfull" (MMA commit) and "tempty" (one arrival per epilogue warp) hand them
 // over.
-template <bool OUT_BF16>
+// TN_: tile width; CONV: A is loaded as an implicit im2col tile (ConvGeo).  addend
+// (FP32 output only, optional): C = A B^T + addend.
+template <bool OUT_BF16, int TN_, bool CONV>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, void* __restrict__ C,
-                const float* __restrict__ bias, int act, int group, int M, int N, int K, int kbs, int splits) {
+                const float* __restrict__ bias, int act, int group, int M, int N, int K, int kbs, int splits,
+                const float* __restrict__ addend, ConvGeo geo) {
+  constexpr int GN = TN_;
+  constexpr uint32_t STAGE_BYTES = Tile<TN_>::STAGE_BYTES;
+  constexpr uint32_t TMEM_COLS = Tile<TN_>::TMEM_COLS;
+  constexpr uint32_t IDESC = Tile<TN_>::IDESC;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2];
   __shared__ uint32_t tmem_slot;
@@ -135,7 +158,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           }
           const uint32_t sa = base + s * STAGE_BYTES, sb = sa + A_BYTES;
           mbar_expect_tx(su32(&full[s]), STAGE_BYTES);
-          tma_load_2d(sa, &ta, kb * GK, tm * GM, su32(&full[s]));
+          if constexpr (CONV) {
+            const int tpb = geo.T / GM;   // M tiles per sample
+            const int tap = kb / geo.KC, cb = kb - tap * geo.KC;
+            tma_load_3d(sa, &ta, cb * GK, (tm % tpb) * GM + geo.dir * (tap - geo.pad), tm / tpb, su32(&full[s]));
+          } else {
+            tma_load_2d(sa, &ta, kb * GK, tm * GM, su32(&full[s]));
+          }
           tma_load_2d(sb, &tb, kb * GK, tn * GN, su32(&full[s]));
         }
       }
@@ -227,8 +256,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           const int col = col0 + lane;
 #pragma unroll 4
           for (int r = 0; r < 32; ++r) {
-            const float a = ebuf[r * 32 + (lane ^ r)];
-            if (row0 + r < M && col < N) out[(int64_t)(row0 + r) * N + col] = a;
+            float a = ebuf[r * 32 + (lane ^ r)];
+            if (row0 + r < M && col < N) {
+              const int64_t o = (int64_t)(row0 + r) * N + col;
+              if (addend) a += __ldg(&addend[o]);
+              out[o] = a;
+            }
           }
         }
         __syncwarp();
@@ -295,21 +328,71 @@ cudaError_t launch_gemm(const void* A, const void* B, void* C, int64_t M, int64_
   splits = (KB + kbs - 1) / kbs;
   const int64_t work = ((M + GM - 1) / GM) * ((N + GN - 1) / GN) * splits;
   const unsigned grid = (unsigned)(work < sms ? work : sms);   // persistent: one CTA per SM
+  const ConvGeo none{0, 0, 0, 0};
   if (out_bf16) {
-    e = cudaFuncSetAttribute(k_gemm_bf16<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
+    e = cudaFuncSetAttribute(k_gemm_bf16<true, GN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)GEMM_SMEM);
     if (e != cudaSuccess) return e;
-    k_gemm_bf16<true><<<grid, GEMM_THREADS, GEMM_SMEM, s>>>(ta, tb, C, bias, act, group, (int)M, (int)N, (int)K, kbs,
-                                                            splits);
+    k_gemm_bf16<true, GN, false><<<grid, GEMM_THREADS, GEMM_SMEM, s>>>(ta, tb, C, bias, act, group, (int)M, (int)N,
+                                                                       (int)K, kbs, splits, nullptr, none);
   } else {
-    e = cudaFuncSetAttribute(k_gemm_bf16<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
+    e = cudaFuncSetAttribute(k_gemm_bf16<false, GN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)GEMM_SMEM);
     if (e != cudaSuccess) return e;
-    k_gemm_bf16<false><<<grid, GEMM_THREADS, GEMM_SMEM, s>>>(ta, tb, C, bias, act, group, (int)M, (int)N, (int)K, kbs,
-                                                             splits);
+    k_gemm_bf16<false, GN, false><<<grid, GEMM_THREADS, GEMM_SMEM, s>>>(ta, tb, C, bias, act, group, (int)M, (int)N,
+                                                                        (int)K, kbs, splits, nullptr, none);
   }
   return cudaGetLastError();
 }
 
+// Channels-last bfloat16 x [Bn][T][C] as a 3-D tensor map with boxes of 64 channels x 128 times.
+bool make_map_3d(CUtensorMap* map, const void* ptr, int64_t Bn, int64_t T, int64_t C) {
+  auto enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)T, (cuuint64_t)Bn};
+  cuuint64_t strides[2] = {(cuuint64_t)C * 2, (cuuint64_t)T * C * 2};
+  cuuint32_t box[3] = {(cuuint32_t)GK, (cuuint32_t)GM, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(ptr), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int TN_>
+cudaError_t launch_conv_tn(const CUtensorMap& ta, const CUtensorMap& tb, float* out, const float* addend, int M, int N,
+                           int K, ConvGeo geo, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int KB = K / GK;
+  const int64_t work = (int64_t)(M / GM) * ((N + TN_ - 1) / TN_);
+  const unsigned grid = (unsigned)(work < sms ? work : sms);
+  constexpr size_t smem = Tile<TN_>::SMEM;
+  e = cudaFuncSetAttribute(k_gemm_bf16<false, TN_, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_gemm_bf16<false, TN_, true><<<grid, GEMM_THREADS, smem, s>>>(ta, tb, out, nullptr, GWX_ACT_NONE, DEFAULT_GROUP, M,
+                                                                 N, K, KB, 1, addend, geo);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+// Implicit-GEMM 1-D convolution, stride 1, "same" zero padding: out [Bn][T][N] (FP32) =
+// sum over taps j < k and channels c of x[b][t + dir (j - (k-1)/2)][c] W[o][j C + c], plus
+// addend if given.  Tile width 64 / 128 / 256 by N.  Shapes checked by the caller.
+cudaError_t launch_conv_gemm(const void* x, int64_t Bn, int64_t T, int64_t C, int k, int dir, const void* W, int64_t N,
+                             float* out, const float* addend, cudaStream_t s) {
+  CUtensorMap ta, tb;
+  const int64_t K = (int64_t)k * C;
+  const int tn = N <= 64 ? 64 : (N <= 128 ? 128 : 256);
+  if (!make_map_3d(&ta, x, Bn, T, C) || !make_map(&tb, W, N, K, (uint32_t)tn)) return cudaErrorInvalidValue;
+  const ConvGeo geo{(int)T, (int)(C / GK), (k - 1) / 2, dir};
+  const int M = (int)(Bn * T);
+  if (tn == 64) return launch_conv_tn<64>(ta, tb, out, addend, M, (int)N, (int)K, geo, s);
+  if (tn == 128) return launch_conv_tn<128>(ta, tb, out, addend, M, (int)N, (int)K, geo, s);
+  return launch_conv_tn<256>(ta, tb, out, addend, M, (int)N, (int)K, geo, s);
+}
 
 cudaError_t launch_gemm_bf16(const void* A, const void* B, void* C, int64_t M, int64_t N, int64_t K, bool out_bf16,
                              const float* bias, int act, int group, cudaStream_t s) {

@@ -157,6 +157,27 @@ def test_resnet_and_dense_validation(lib):
     assert small < long_batch
 
 
+def test_conv1d_validation(lib):
+    """The implicit-GEMM convolutions take whole 128-time tiles and 64-channel blocks; other
+    shapes, even kernels, missing arrays and short workspaces fail before any launch."""
+    import ctypes
+    good = dict(B=2, T=256, C=64, O=64, k=5)
+    for bad, word in ((dict(T=200), b"T %"), (dict(C=96), b"C and O"), (dict(O=32), b"C and O"), (dict(k=4), b"k odd"),
+                      (dict(k=17), b"k odd"), (dict(B=1 << 19, T=256), b"2^26")):
+        a = dict(good, **bad)
+        st = lib.gwx_conv1d_bf16(None, a["B"], a["T"], a["C"], a["k"], None, a["O"], None, None, None)
+        assert st == -2 and word in lib.gwx_last_error(), (bad, lib.gwx_last_error())
+    st = lib.gwx_conv1d_bf16(None, 2, 256, 64, 5, None, 64, None, None, None)
+    assert st == -1 and b"NULL" in lib.gwx_last_error()
+    ws = lib.gwx_conv1d_bf16_backward_workspace(2, 256, 64, 64, 5)
+    # dZ and dZ^T (bfloat16), the transposed weights and the transposed rows 5 C x B T
+    assert ws >= 2 * 512 * 64 * 2 + 64 * 5 * 64 * 2 + 5 * 64 * 512 * 2
+    buf = ctypes.create_string_buffer(64)
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    st = lib.gwx_conv1d_bf16_backward(p, p, p, 2, 256, 64, 64, 5, None, None, None, p, 64, None)
+    assert st == -4 and b"workspace" in lib.gwx_last_error()
+
+
 def test_static_whitening_checks_as_gwx_whiten(lib):
     """gwx_whiten_static runs gwx_whiten's own argument checks (before any device work):
     the same statuses and messages for a non-finite sample rate, a band start above the
