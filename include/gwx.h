@@ -720,7 +720,7 @@ int gwx_mean_time_backward(const float* dm, int64_t B, int T, int C, float* dx, 
  *   sum_{b, t} dz[b][t][o] x[b][t + j - p][c] (split-K, deterministic); either output may
  *   be NULL.  Workspace gwx_conv1d_bf16_backward_workspace(B, T, C, O, k) bytes.
  * Sizes: T % 128 == 0, C % 64 == 0, O % 64 == 0, k odd in [1, 15], B >= 1, B T <= 2^26;
- * x, W, z, dx, dW 16-byte aligned, dz and addend 4-byte aligned; else GWX_ESHAPE or
+ * x, W, z, dx, dW and addend 16-byte aligned, dz 4-byte aligned; else GWX_ESHAPE or
  * GWX_EINVAL; a workspace below the size GWX_ENOMEM.  A bounded wait that expires is
  * reported by gwx_device_status. */
 int gwx_conv1d_bf16(const void* x, int64_t B, int64_t T, int C, int k, const void* W, int O, const float* addend,

@@ -1087,8 +1087,8 @@ int gwx_conv1d_bf16(const void* x, int64_t B, int64_t T, int C, int k, const voi
                     float* z, void* stream) {
   GWX_TRY(check_conv(B, T, C, O, k));
   if (!x || !W || !z) return fail(GWX_EINVAL, "NULL array");
-  if ((((uintptr_t)x) | ((uintptr_t)W) | ((uintptr_t)z)) & 15u) return fail(GWX_EINVAL, "x, W and z must be 16-byte aligned");
-  if (((uintptr_t)addend) & 3u) return fail(GWX_EINVAL, "addend must be 4-byte aligned");
+  if ((((uintptr_t)x) | ((uintptr_t)W) | ((uintptr_t)z) | ((uintptr_t)addend)) & 15u)
+    return fail(GWX_EINVAL, "x, W, z and addend must be 16-byte aligned");
   GWX_TRY(ensure_init());
   return launched(launch_conv_forward(x, B, T, C, k, W, O, addend, z, as_stream(stream)), "conv1d_bf16");
 }
@@ -1103,9 +1103,9 @@ int gwx_conv1d_bf16_backward(const float* dz, const void* x, const void* W, int6
                              void* stream) {
   GWX_TRY(check_conv(B, T, C, O, k));
   if (!dz || !x || !W) return fail(GWX_EINVAL, "NULL array");
-  if ((((uintptr_t)x) | ((uintptr_t)W) | ((uintptr_t)dx) | ((uintptr_t)dW)) & 15u)
-    return fail(GWX_EINVAL, "x, W, dx and dW must be 16-byte aligned");
-  if ((((uintptr_t)dz) | ((uintptr_t)addend)) & 3u) return fail(GWX_EINVAL, "dz and addend must be 4-byte aligned");
+  if ((((uintptr_t)x) | ((uintptr_t)W) | ((uintptr_t)dx) | ((uintptr_t)dW) | ((uintptr_t)addend)) & 15u)
+    return fail(GWX_EINVAL, "x, W, dx, dW and addend must be 16-byte aligned");
+  if (((uintptr_t)dz) & 3u) return fail(GWX_EINVAL, "dz must be 4-byte aligned");
   GWX_TRY(check_ws(workspace, workspace_bytes, conv_backward_ws(B, T, C, O, k)));
   GWX_TRY(ensure_init());
   return launched(launch_conv_backward(dz, x, W, B, T, C, O, k, addend, dx, dW, workspace, as_stream(stream)),

@@ -52,30 +52,53 @@ __global__ void k_conv_wt(const __nv_bfloat16* __restrict__ W, int O, int C, int
   Wt[i] = W[(int64_t)o * k * C + (int64_t)j * C + c];
 }
 
-// colsT[j C + c][b T + t] = x[b][t + j - p][c] (zero outside [0, T)): one 32-channel x
-// 32-time tile of one tap per block, read along channels, written along time.
-__global__ void k_im2col_t(const __nv_bfloat16* __restrict__ x, int64_t Bn, int T, int C, int k,
-                           __nv_bfloat16* __restrict__ colsT) {
-  __shared__ __nv_bfloat16 tile[CT][CT + 2];
+// colsT[j C + c][b T + t] = x[b][t + j - p][c] (zero outside [0, T)).  One block per
+// 64-time x 64-channel tile, all k taps: the 63 + k input rows it needs are loaded once as
+// 16-byte vectors into a shared tile of 33-word rows (conflict-free both ways), then every
+// tap's 64 output rows are written as 16-byte vectors of 8 consecutive times.
+constexpr int IT = 64;   // tile edge (times and channels)
+constexpr int IW = 33;   // shared row stride in 32-bit words (32 data + 1 pad)
+
+__global__ void __launch_bounds__(256) k_im2col_t(const __nv_bfloat16* __restrict__ x, int64_t Bn, int T, int C, int k,
+                                                  __nv_bfloat16* __restrict__ colsT) {
+  __shared__ uint32_t tile[(IT + 14) * IW];
   const int64_t M = Bn * T;
-  const int64_t q0 = (int64_t)blockIdx.x * CT;   // first (b, t) row of the tile (T % 32 == 0)
-  const int c0 = blockIdx.y * CT;
-  const int j = blockIdx.z;
+  const int64_t q0 = (int64_t)blockIdx.x * IT;   // first (b, t) row (T % 64 == 0)
+  const int c0 = blockIdx.y * IT;
   const int p = (k - 1) / 2;
   const int64_t b = q0 / T;
   const int t0 = (int)(q0 - b * T);
-  for (int i = threadIdx.y; i < CT; i += blockDim.y) {
-    const int ts = t0 + i + j - p;
-    const int c = c0 + threadIdx.x;
-    __nv_bfloat16 v = __float2bfloat16_rn(0.f);
-    if (ts >= 0 && ts < T && c < C) v = x[(b * T + ts) * C + c];
-    tile[i][threadIdx.x] = v;
+  const int rows = IT + k - 1;
+  const int tid = threadIdx.x;
+  // load: row r = source time t0 - p + r, 8 vectors of 8 channels
+  for (int e = tid; e < rows * 8; e += 256) {
+    const int r = e >> 3, v = e & 7;
+    const int ts = t0 - p + r;
+    uint4 val = make_uint4(0u, 0u, 0u, 0u);
+    if (ts >= 0 && ts < T) val = __ldg(reinterpret_cast<const uint4*>(x + (b * T + ts) * C + c0) + v);
+    uint32_t* d = tile + r * IW + 4 * v;
+    d[0] = val.x;
+    d[1] = val.y;
+    d[2] = val.z;
+    d[3] = val.w;
   }
   __syncthreads();
-  for (int i = threadIdx.y; i < CT; i += blockDim.y) {
-    const int c = c0 + i;
-    const int64_t q = q0 + threadIdx.x;
-    if (c < C && q < M) colsT[((int64_t)j * C + c) * M + q] = tile[threadIdx.x][i];
+  const unsigned short* ts16 = reinterpret_cast<const unsigned short*>(tile);
+  for (int j = 0; j < k; ++j) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      // output row c, times 8 u .. 8 u + 7; a warp covers 8 channels x 4 vectors, whose
+      // shared rows 8 u + const land in distinct banks
+      const int c = tid >> 2, u = (tid & 3) + 4 * h;
+      uint32_t w[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int r0 = 8 * u + 2 * i + j;
+        const uint32_t lo = ts16[2 * (r0 * IW) + c], hi = ts16[2 * ((r0 + 1) * IW) + c];
+        w[i] = lo | (hi << 16);
+      }
+      *reinterpret_cast<uint4*>(colsT + ((int64_t)j * C + c0 + c) * M + q0 + 8 * u) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
   }
 }
 
@@ -123,7 +146,7 @@ cudaError_t launch_conv_backward(const float* dz, const void* x, const void* W, 
     if ((e = launch_conv_gemm(dZ, Bn, T, O, k, -1, Wt, C, dx, addend, s)) != cudaSuccess) return e;
   }
   if (dW) {
-    k_im2col_t<<<dim3((unsigned)(M / CT), (unsigned)((C + CT - 1) / CT), (unsigned)k), tb, 0, s>>>(
+    k_im2col_t<<<dim3((unsigned)(M / IT), (unsigned)(C / IT)), 256, 0, s>>>(
         reinterpret_cast<const __nv_bfloat16*>(x), Bn, (int)T, C, k, colsT);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_gemm_splitk(dZt, colsT, dW, O, (int64_t)k * C, M, part, s)) != cudaSuccess) return e;

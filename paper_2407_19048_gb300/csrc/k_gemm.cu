@@ -99,7 +99,7 @@ __device__ __forceinline__ void tile_coords(int t, int TM, int TN, int group, in
 // main loop; "tfull" (MMA commit) and "tempty" (one arrival per epilogue warp) hand them
 // over.
 // TN_: tile width; CONV: A is loaded as an implicit im2col tile (ConvGeo).  addend
-// (FP32 output only, optional): C = A B^T + addend.
+// (optional; N % 32 == 0, 16-byte aligned): C = (A B^T + addend), then bias and activation.
 template <bool OUT_BF16, int TN_, bool CONV>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, void* __restrict__ C,
@@ -226,9 +226,28 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 #pragma unroll 1
       for (int c = c_lo; c < c_hi; ++c) {
         float v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + acc * TMEM_COLS + (uint32_t)(32 * c), v);
         const int col0 = tn * GN + 32 * c;
+        // addend row segment of this lane's row (columns col0 .. col0 + 31; N % 32 == 0 and a
+        // 16-byte aligned addend when one is given), fetched before the accumulator so that
+        // its latency overlaps the tensor-memory load
+        float4 ad[8];
+        if (addend != nullptr) {
+          const bool in = row0 + lane < M && col0 < N;
+          const float4* ap = reinterpret_cast<const float4*>(addend + (int64_t)(row0 + lane) * N + col0);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) ad[j] = in ? __ldg(ap + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + acc * TMEM_COLS + (uint32_t)(32 * c), v);
         if (row0 >= M || col0 >= N) continue;   // warp-uniform
+        if (addend != nullptr) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            v[4 * j] += ad[j].x;
+            v[4 * j + 1] += ad[j].y;
+            v[4 * j + 2] += ad[j].z;
+            v[4 * j + 3] += ad[j].w;
+          }
+        }
         epilogue_ops(v, bias, act, col0, N);
 #pragma unroll
         for (int j = 0; j < 32; ++j) ebuf[lane * 32 + (j ^ lane)] = v[j];
@@ -256,12 +275,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           const int col = col0 + lane;
 #pragma unroll 4
           for (int r = 0; r < 32; ++r) {
-            float a = ebuf[r * 32 + (lane ^ r)];
-            if (row0 + r < M && col < N) {
-              const int64_t o = (int64_t)(row0 + r) * N + col;
-              if (addend) a += __ldg(&addend[o]);
-              out[o] = a;
-            }
+            const float a = ebuf[r * 32 + (lane ^ r)];
+            if (row0 + r < M && col < N) out[(int64_t)(row0 + r) * N + col] = a;
           }
         }
         __syncwarp();

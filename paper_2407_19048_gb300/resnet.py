@@ -24,10 +24,15 @@ def stem_k(D):
 
 
 class ResNet1D:
-    def __init__(self, D, out_dim, stages=STAGES, device=None, seed=0, params=None):
+    def __init__(self, D, out_dim, stages=STAGES, device=None, seed=0, params=None, implicit=True):
+        """implicit: run the stride-1 kernel-5 convolutions whose channel counts are
+        multiples of 64 and whose series are multiples of 128 steps as implicit GEMMs
+        (gwx_conv1d_bf16: no im2col rows, the input gradient without col2im); the others
+        (stem, strided entries, 1 x 1 shortcuts) always use im2col rows."""
         import torch
         import paper_2407_19048_gb300 as gwx
         self.gwx = gwx
+        self.implicit = bool(implicit)
         self.dev = device or torch.device("cuda", torch.cuda.current_device())
         self.D, self.out_dim, self.stages = D, out_dim, tuple(stages)
         if params is None:
@@ -94,10 +99,19 @@ class ResNet1D:
         return out
 
     # ------------------------------------------------------------------ pieces
+    def _implicit_ok(self, x, W16, k, s, cf):
+        if not self.implicit or cf or s != 1 or k != 5:
+            return False
+        _, T, C = x.shape
+        return T % 128 == 0 and C % 64 == 0 and W16.shape[0] % 64 == 0
+
     def _conv(self, x, W16, k, s, p, cf=False):
-        """(z [B][T_out][C_out] FP32, cols) of bfloat16 x [B][T][C] (cf: FP32 [B][D][N])."""
+        """(z [B][T_out][C_out] FP32, cols) of bfloat16 x [B][T][C] (cf: FP32 [B][D][N]);
+        cols is None when the convolution ran as an implicit GEMM."""
         import torch
         gwx, lib = self.gwx, _lib.load()
+        if self._implicit_ok(x, W16, k, s, cf):
+            return gwx.conv1d_bf16(x, W16, k), None
         st = gwx._stream()
         K = W16.shape[1]
         if cf:
@@ -195,10 +209,16 @@ class ResNet1D:
         gwx._check(_lib.load().gwx_relu_mask(gwx._ptr(dy), gwx._ptr(out), dy.numel(), gwx._ptr(d), gwx._stream()))
         return d
 
-    def _conv_back(self, dz, cols, W16, T, C, k, s, p, addend=None):
-        """(dx [B][T][C] FP32, dW) of a convolution given dz [B][T_out][C_out]."""
+    def _conv_back(self, dz, cols, W16, T, C, k, s, p, addend=None, x_in=None):
+        """(dx [B][T][C] FP32, dW) of a convolution given dz [B][T_out][C_out]; x_in is the
+        convolution's input when it ran as an implicit GEMM (cols None)."""
         import torch
         gwx = self.gwx
+        if cols is None:
+            B = x_in.shape[0]
+            nb = _lib.load().gwx_conv1d_bf16_backward_workspace(B, T, C, W16.shape[0], k)
+            return gwx.conv1d_bf16_backward(dz, x_in, W16, k, addend=addend,
+                                            workspace=(self._scratch(nb), nb))
         B, To, Co = dz.shape
         dcols, dW, _ = gwx.dense_bf16_backward(cols, W16, None, dz.reshape(B * To, Co), act=gwx.ACT_NONE)
         dx = torch.empty((B, T, C), dtype=torch.float32, device=self.dev)
@@ -227,7 +247,7 @@ class ResNet1D:
             s = blk["s"]
             dsum = self._relu_mask(dh, out)
             dz2, G["%d.g2" % i], G["%d.b2" % i] = self._gn_back(dsum, z2, ms2, blk["g2"])
-            dh1, G["%d.W2" % i] = self._conv_back(dz2, c2, blk["W216"], h1.shape[1], h1.shape[2], 5, 1, 2)
+            dh1, G["%d.W2" % i] = self._conv_back(dz2, c2, blk["W216"], h1.shape[1], h1.shape[2], 5, 1, 2, x_in=h1)
             dh1 = self._relu_mask(dh1, h1)
             dz1, G["%d.g1" % i], G["%d.b1" % i] = self._gn_back(dh1, z1, ms1, blk["g1"])
             if "Wd" in blk:
@@ -235,7 +255,8 @@ class ResNet1D:
                 dxs, G["%d.Wd" % i] = self._conv_back(dzd, cd, blk["Wd16"], h.shape[1], h.shape[2], 1, s, 0)
             else:
                 dxs = dsum
-            dh, G["%d.W1" % i] = self._conv_back(dz1, c1, blk["W116"], h.shape[1], h.shape[2], 5, s, 2, addend=dxs)
+            dh, G["%d.W1" % i] = self._conv_back(dz1, c1, blk["W116"], h.shape[1], h.shape[2], 5, s, 2, addend=dxs,
+                                                 x_in=h)
         cols0, z0, ms0, a0, arg = tape["stem"]
         B, T1, C0 = a0.shape
         da0 = torch.empty((B, T1, C0), dtype=torch.float32, device=self.dev)

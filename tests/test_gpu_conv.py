@@ -171,3 +171,33 @@ def test_conv_matches_the_im2col_path_bit_for_bit_in_the_forward(gwx):
     z2 = gwx.dense_bf16(cols, Wd, None, act=gwx.ACT_NONE, out_dtype=torch.float32)
     torch.cuda.synchronize()
     assert torch.equal(z.reshape(B * T, O), z2)
+
+
+def test_resnet_with_implicit_convolutions_matches_the_im2col_network(gwx):
+    """The whole summary (stem, (5, 3, 3) blocks of 64 / 128 / 256 channels) on 16 windows
+    of 2 x 2048 samples with its stride-1 convolutions as implicit GEMMs, against the same
+    network and parameters on im2col rows.  Both paths are checked against the oracle
+    operation by operation above and in test_gpu_resnet.py; here the plumbing (tape,
+    inputs, addends) is compared: the representation and every gradient tensor agree to
+    1e-2 of their norm (the two differ only in FP32 summation order, which moves a few
+    bfloat16 activations by one unit)."""
+    from paper_2407_19048_gb300.resnet import ResNet1D
+    rng = np.random.default_rng(21)
+    y = torch.from_numpy(rng.standard_normal((16, 2, 2048)).astype(np.float32)).cuda()
+    a = ResNet1D(2, 64, seed=4, implicit=True)
+    b = ResNet1D(2, 64, seed=4, implicit=False)
+    ca = a.forward(y)
+    cb = b.forward(y)
+    dc = torch.from_numpy(rng.standard_normal((16, 64)).astype(np.float32)).cuda()
+    ga = a.backward(dc)
+    gb = b.backward(dc)
+    torch.cuda.synchronize()
+    used = [t for t in a.tape["blocks"] if t[1] is None]
+    # blocks whose first convolution ran implicitly: the five of stage 1 and the two
+    # non-entry blocks of stages 2 and 3 (every block's second convolution does too)
+    assert len(used) == 9
+    assert all(t[5] is None for t in a.tape["blocks"])
+    assert torch.linalg.norm(ca - cb) <= 1e-2 * torch.linalg.norm(cb)
+    for name in gb:
+        assert torch.linalg.norm(ga[name] - gb[name]) <= 1e-2 * torch.linalg.norm(gb[name]) + 1e-30, name
+    assert gwx._lib.load().gwx_device_status() == 0
