@@ -329,35 +329,56 @@ __global__ void k_split_reduce(const float* __restrict__ part, int splits, int64
   out[i] = acc;
 }
 
+template <int TN_>
+cudaError_t launch_gemm_tn(const CUtensorMap& ta, const CUtensorMap& tb, void* C, int64_t M, int64_t N, int64_t K,
+                           bool out_bf16, const float* bias, int act, int group, int splits, int sms,
+                           cudaStream_t s) {
+  const int KB = (int)((K + GK - 1) / GK);
+  const int kbs = (KB + splits - 1) / splits;   // every slice has at least one K block
+  splits = (KB + kbs - 1) / kbs;
+  const int64_t work = ((M + GM - 1) / GM) * ((N + TN_ - 1) / TN_) * splits;
+  const unsigned grid = (unsigned)(work < sms ? work : sms);   // persistent: one CTA per SM
+  constexpr size_t smem = Tile<TN_>::SMEM;
+  const ConvGeo none{0, 0, 0, 0};
+  cudaError_t e;
+  if (out_bf16) {
+    e = cudaFuncSetAttribute(k_gemm_bf16<true, TN_, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gemm_bf16<true, TN_, false><<<grid, GEMM_THREADS, smem, s>>>(ta, tb, C, bias, act, group, (int)M, (int)N,
+                                                                   (int)K, kbs, splits, nullptr, none);
+  } else {
+    e = cudaFuncSetAttribute(k_gemm_bf16<false, TN_, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gemm_bf16<false, TN_, false><<<grid, GEMM_THREADS, smem, s>>>(ta, tb, C, bias, act, group, (int)M, (int)N,
+                                                                    (int)K, kbs, splits, nullptr, none);
+  }
+  return cudaGetLastError();
+}
+
+// Tile width of a product: 256 columns unless the 128 x 256 tiles would leave more than half
+// of the SMs idle (the flow's conditioner products on a few hundred to a few thousand rows),
+// then 128 or 64, so that more CTAs share the work.  Split-K products keep 256.
+int gemm_tile_width(int64_t M, int64_t N, int splits, int sms) {
+  if (splits > 1) return GN;
+  const int64_t tm = (M + GM - 1) / GM;
+  for (int tn : {256, 128})
+    if (tm * ((N + tn - 1) / tn) * 2 >= sms) return tn;
+  return 64;
+}
+
 cudaError_t launch_gemm(const void* A, const void* B, void* C, int64_t M, int64_t N, int64_t K, bool out_bf16,
                         const float* bias, int act, int group, int splits, cudaStream_t s) {
   if (group < 1) group = DEFAULT_GROUP;
-  CUtensorMap ta, tb;
-  if (!make_map(&ta, A, M, K, GM) || !make_map(&tb, B, N, K, GN)) return cudaErrorInvalidValue;
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  const int KB = (int)((K + GK - 1) / GK);
-  const int kbs = (KB + splits - 1) / splits;   // every slice has at least one K block
-  splits = (KB + kbs - 1) / kbs;
-  const int64_t work = ((M + GM - 1) / GM) * ((N + GN - 1) / GN) * splits;
-  const unsigned grid = (unsigned)(work < sms ? work : sms);   // persistent: one CTA per SM
-  const ConvGeo none{0, 0, 0, 0};
-  if (out_bf16) {
-    e = cudaFuncSetAttribute(k_gemm_bf16<true, GN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)GEMM_SMEM);
-    if (e != cudaSuccess) return e;
-    k_gemm_bf16<true, GN, false><<<grid, GEMM_THREADS, GEMM_SMEM, s>>>(ta, tb, C, bias, act, group, (int)M, (int)N,
-                                                                       (int)K, kbs, splits, nullptr, none);
-  } else {
-    e = cudaFuncSetAttribute(k_gemm_bf16<false, GN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)GEMM_SMEM);
-    if (e != cudaSuccess) return e;
-    k_gemm_bf16<false, GN, false><<<grid, GEMM_THREADS, GEMM_SMEM, s>>>(ta, tb, C, bias, act, group, (int)M, (int)N,
-                                                                        (int)K, kbs, splits, nullptr, none);
-  }
-  return cudaGetLastError();
+  const int tn = gemm_tile_width(M, N, splits, sms);
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, A, M, K, GM) || !make_map(&tb, B, N, K, (uint32_t)tn)) return cudaErrorInvalidValue;
+  if (tn == 64) return launch_gemm_tn<64>(ta, tb, C, M, N, K, out_bf16, bias, act, group, splits, sms, s);
+  if (tn == 128) return launch_gemm_tn<128>(ta, tb, C, M, N, K, out_bf16, bias, act, group, splits, sms, s);
+  return launch_gemm_tn<256>(ta, tb, C, M, N, K, out_bf16, bias, act, group, splits, sms, s);
 }
 
 // Channels-last bfloat16 x [Bn][T][C] as a 3-D tensor map with boxes of 64 channels x 128 times.
