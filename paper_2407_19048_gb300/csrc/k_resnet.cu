@@ -226,10 +226,15 @@ __global__ void __launch_bounds__(256) k_gn_stats_s(const float* __restrict__ z,
   }
 }
 
+// part (optional, [B][C][2] doubles): this sample's sums of dy xhat and dy per channel (FP32
+// over runs of at most 16 rows, FP64 across runs and, in a fixed order, across the threads
+// that share the channels), the partials of dgamma and dbeta that k_gn_param_finish adds.
 __global__ void __launch_bounds__(256) k_gn_bwd_stats_s(const float* __restrict__ dy, const float* __restrict__ z,
                                                         int T, int C, int G, const float* __restrict__ ms,
-                                                        const float* __restrict__ gamma, float* __restrict__ mm) {
+                                                        const float* __restrict__ gamma, float* __restrict__ mm,
+                                                        double* __restrict__ part) {
   __shared__ double sums[64];
+  __shared__ double pr[256 * 8];
   const int cq = C / 4, rl = 256 / cq, cg = C / G;
   const int q4 = threadIdx.x % cq, l0 = threadIdx.x / cq, g = (4 * q4) / cg;
   const int64_t off = (int64_t)blockIdx.x * T * C;
@@ -237,25 +242,62 @@ __global__ void __launch_bounds__(256) k_gn_bwd_stats_s(const float* __restrict_
   const float4 gm = make_float4(__ldg(&gamma[4 * q4]), __ldg(&gamma[4 * q4 + 1]), __ldg(&gamma[4 * q4 + 2]),
                                 __ldg(&gamma[4 * q4 + 3]));
   double a = 0.0, q = 0.0;
+  double pg[4] = {0.0, 0.0, 0.0, 0.0}, pb[4] = {0.0, 0.0, 0.0, 0.0};
   for (int t0 = l0; t0 < T; t0 += 16 * rl) {
     float s1 = 0.f, s2 = 0.f;
+    float fg[4] = {0.f, 0.f, 0.f, 0.f}, fb[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 4
     for (int t = t0; t < min(T, t0 + 16 * rl); t += rl) {
       const float4 d = __ldg(reinterpret_cast<const float4*>(dy + off + (int64_t)t * C) + q4);
       const float4 x = __ldg(reinterpret_cast<const float4*>(z + off + (int64_t)t * C) + q4);
       const float a0 = d.x * gm.x, a1 = d.y * gm.y, a2 = d.z * gm.z, a3 = d.w * gm.w;
+      const float h0 = (x.x - mean) * rstd, h1 = (x.y - mean) * rstd, h2 = (x.z - mean) * rstd,
+                  h3 = (x.w - mean) * rstd;
       s1 += (a0 + a1) + (a2 + a3);
-      s2 += (a0 * ((x.x - mean) * rstd) + a1 * ((x.y - mean) * rstd)) +
-            (a2 * ((x.z - mean) * rstd) + a3 * ((x.w - mean) * rstd));
+      s2 += (a0 * h0 + a1 * h1) + (a2 * h2 + a3 * h3);
+      if (part) {
+        fg[0] += d.x * h0;
+        fg[1] += d.y * h1;
+        fg[2] += d.z * h2;
+        fg[3] += d.w * h3;
+        fb[0] += d.x;
+        fb[1] += d.y;
+        fb[2] += d.z;
+        fb[3] += d.w;
+      }
     }
     a += s1;
     q += s2;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      pg[m] += fg[m];
+      pb[m] += fb[m];
+    }
   }
   sample_group_sums(a, q, cq, rl, cg, G, sums);
   if ((int)threadIdx.x < G) {
     const double n = (double)T * cg;
     mm[2 * ((int64_t)blockIdx.x * G + threadIdx.x)] = (float)(sums[2 * threadIdx.x] / n);
     mm[2 * ((int64_t)blockIdx.x * G + threadIdx.x) + 1] = (float)(sums[2 * threadIdx.x + 1] / n);
+  }
+  if (part) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      pr[threadIdx.x * 8 + m] = pg[m];
+      pr[threadIdx.x * 8 + 4 + m] = pb[m];
+    }
+    __syncthreads();
+    // thread tid < C: channel tid, summed over the rl threads l = 0 .. rl-1 in order
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+      const int qq = c / 4, m = c % 4;
+      double sg = 0.0, sb = 0.0;
+      for (int l = 0; l < rl; ++l) {
+        sg += pr[(l * cq + qq) * 8 + m];
+        sb += pr[(l * cq + qq) * 8 + 4 + m];
+      }
+      part[((int64_t)blockIdx.x * C + c) * 2] = sg;
+      part[((int64_t)blockIdx.x * C + c) * 2 + 1] = sb;
+    }
   }
 }
 
@@ -608,9 +650,15 @@ cudaError_t launch_group_norm_backward(const float* dy, const float* z, int64_t 
                                            (((size_t)B * G * 2 * sizeof(float) + 255) & ~(size_t)255));
   const bool v4 = (C / G) % 4 == 0 && aligned16(dy) && aligned16(z) && aligned16(dz);
   if (v4 && per_sample_ok(C, G)) {
-    k_gn_bwd_stats_s<<<(unsigned)B, 256, 0, st>>>(dy, z, T, C, G, ms, gamma, mm);
+    // the per-channel parameter sums come out of the statistics pass, one slice per sample
+    const bool fused = B <= GN_MAX_SLICES;
+    k_gn_bwd_stats_s<<<(unsigned)B, 256, 0, st>>>(dy, z, T, C, G, ms, gamma, mm, fused ? part : nullptr);
     k_gn_bwd_apply<4><<<dim3(nblk((int64_t)T * C / 4, 256), (unsigned)B), 256, 0, st>>>(dy, z, T, C, G, ms, mm, gamma,
                                                                                         dz);
+    if (fused) {
+      k_gn_param_finish<<<nblk(C, 32), dim3(32, 32), 0, st>>>(part, (int)B, C, dgamma, dbeta);
+      return cudaGetLastError();
+    }
   } else if (v4) {
     k_gn_bwd_stats<4><<<(unsigned)(B * G), 256, 0, st>>>(dy, z, T, C, G, ms, gamma, mm);
     k_gn_bwd_apply<4><<<dim3(nblk((int64_t)T * C / 4, 256), (unsigned)B), 256, 0, st>>>(dy, z, T, C, G, ms, mm, gamma,
