@@ -525,6 +525,65 @@ def hl3_leg(gwx, torch, rank, args, flush, steps=200):
             "roofline": roof}
 
 
+def conv_leg(gwx, torch, reps=20):
+    """The ResNet's stage-1 convolution at its training shape (512 windows x 512 steps,
+    64 -> 64 channels, kernel 5, bfloat16 operands, FP32 outputs): the implicit GEMM
+    (gwx_conv1d_bf16 and its backward with the residual-gradient addend) against the
+    im2col rows + dense product route, CUDA events over `reps` calls each."""
+    B, T, C, O, k = 512, 512, 64, 64, 5
+    g = torch.Generator(device="cuda").manual_seed(7)
+    x = torch.randn((B, T, C), device="cuda", generator=g).to(torch.bfloat16)
+    W = (torch.randn((O, k * C), device="cuda", generator=g) * (2.0 / (k * C)) ** 0.5).to(torch.bfloat16)
+    dz = torch.randn((B, T, O), device="cuda", generator=g)
+    add = torch.randn((B, T, C), device="cuda", generator=g)
+    lib = gwx._lib.load()
+    nb = lib.gwx_conv1d_bf16_backward_workspace(B, T, C, O, k)
+    ws = gwx._workspace(nb, x.device)
+    cols = torch.empty((B * T, k * C), dtype=torch.bfloat16, device="cuda")
+    dxe = torch.empty((B, T, C), dtype=torch.float32, device="cuda")
+
+    def implicit_fwd():
+        gwx.conv1d_bf16(x, W, k)
+
+    def implicit_bwd():
+        gwx.conv1d_bf16_backward(dz, x, W, k, addend=add, workspace=ws)
+
+    def explicit_fwd():
+        gwx._check(lib.gwx_im2col(gwx._ptr(x), B, T, C, k, 1, 2, k * C, gwx._ptr(cols), gwx._stream()))
+        gwx.dense_bf16(cols, W, None, act=gwx.ACT_NONE, out_dtype=torch.float32)
+
+    def explicit_bwd():
+        gwx._check(lib.gwx_im2col(gwx._ptr(x), B, T, C, k, 1, 2, k * C, gwx._ptr(cols), gwx._stream()))
+        dcols, _, _ = gwx.dense_bf16_backward(cols, W, None, dz.reshape(B * T, O), act=gwx.ACT_NONE)
+        gwx._check(lib.gwx_col2im(gwx._ptr(dcols), B, T, C, k, 1, 2, k * C, gwx._ptr(add), gwx._ptr(dxe),
+                                  gwx._stream()))
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t = {"implicit_forward_ms": timed(implicit_fwd), "implicit_backward_ms": timed(implicit_bwd),
+         "im2col_forward_ms": timed(explicit_fwd), "im2col_backward_ms": timed(explicit_bwd)}
+    peaks = _measured_peaks()
+    hbm = float(peaks.get("hbm_gbs") or 6800.0)
+    fwd_bytes = B * T * C * 2 + O * k * C * 2 + B * T * O * 4      # x read, W read, z written
+    gbs = fwd_bytes / (t["implicit_forward_ms"] * 1e-3) / 1e9
+    t["shape"] = {"B": B, "T": T, "C": C, "O": O, "k": k}
+    t["forward_flop"] = 2 * B * T * O * k * C
+    t["roofline_forward"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                             "algorithmic_bytes": fwd_bytes,
+                             "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json)" if peaks.get("hbm_gbs")
+                             else "fallback 6800 GB/s"}
+    return t
+
+
 def flow_resnet_leg(gwx, torch, rank, steps=1500, batch=512, events=64):
     """The flow with the paper's ResNet-1D data summary (stem, (5, 3, 3) residual blocks of
     64 / 128 / 256 channels, group norm, kernel 5; convolutions on the tensor cores) in
@@ -935,6 +994,7 @@ def run_gpu(args, wl):
     gemm = gemm_leg(gwx, torch)
     flow = flow_leg(gwx, torch, rank)
     flow_resnet = flow_resnet_leg(gwx, torch, rank)
+    conv1d = conv_leg(gwx, torch)
     padded = padded_leg(gwx, torch, rank)
 
     roof = roofline_alu(torch, wl, statistics.mean(sim_ms), clk)
@@ -971,7 +1031,7 @@ def run_gpu(args, wl):
             "serving": serve,
             "gemm_bf16": gemm,
             "flow": flow,
-            "flow_resnet": flow_resnet,
+            "flow_resnet": flow_resnet, "conv1d_stage1": conv1d,
             "padded_grid": padded,
             "wall_s_timed_region": t_wall,
         }
@@ -1005,6 +1065,8 @@ def main(argv=None):
                          "times; for profiling")
     ap.add_argument("--only-flow", default=None, metavar="STEPS",
                     help="run only the coupling-flow leg with this many training steps; for profiling")
+    ap.add_argument("--only-conv", default=None, metavar="REPS",
+                    help="run only the ResNet stage-1 convolution leg (implicit GEMM vs im2col rows); for profiling")
     ap.add_argument("--only-resnet", default=None, metavar="STEPS",
                     help="run only the ResNet-1D flow leg with this many training steps; for profiling")
     args = ap.parse_args(argv)
@@ -1048,6 +1110,12 @@ def main(argv=None):
         import paper_2407_19048_gb300.simulator  # noqa: F401
         gwx.init()
         print(json.dumps({"flow": flow_leg(gwx, torch, 0, steps=int(args.only_flow))}), flush=True)
+        return 0
+    if args.only_conv:
+        import torch
+        import paper_2407_19048_gb300 as gwx
+        gwx.init()
+        print(json.dumps({"conv1d_stage1": conv_leg(gwx, torch, reps=int(args.only_conv))}), flush=True)
         return 0
     if args.only_resnet:
         import torch

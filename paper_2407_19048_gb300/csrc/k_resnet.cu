@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(256) k_gn_stats_s(const float* __restrict__ z,
 // part (optional, [B][C][2] doubles): this sample's sums of dy xhat and dy per channel (FP32
 // over runs of at most 16 rows, FP64 across runs and, in a fixed order, across the threads
 // that share the channels), the partials of dgamma and dbeta that k_gn_param_finish adds.
-__global__ void __launch_bounds__(256) k_gn_bwd_stats_s(const float* __restrict__ dy, const float* __restrict__ z,
+__global__ void __launch_bounds__(256, 4) k_gn_bwd_stats_s(const float* __restrict__ dy, const float* __restrict__ z,
                                                         int T, int C, int G, const float* __restrict__ ms,
                                                         const float* __restrict__ gamma, float* __restrict__ mm,
                                                         double* __restrict__ part) {
