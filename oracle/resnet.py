@@ -6,9 +6,11 @@ stacks of basic residual blocks with 64, 128 and 256 channels ((5, 3, 3) blocks,
 size 5 in the best configuration), and a final fully connected layer to the
 representation.  This module states that network in FP64, channels-last:
 
-* conv(x, W, k, s, p): y[b][t][o] = sum_{j, c} W[o][j C + c] x[b][s t + j - p][c] (zero
-  outside 0 <= index < T), i.e. im2col rows (all taps j of all channels c, tap-major)
-  times W^T; T_out = (T + 2 p - k) // s + 1;
+* conv_direct(x, W, k, s, p): y[b][t][o] = sum_{j, c} W[o][j C + c] x[b][s t + j - p][c]
+  (zero outside 0 <= index < T), summed tap by tap as written; T_out = (T + 2 p - k) // s
+  + 1; its backward conv_backward_direct is the same sums transposed.  (im2col / col2im,
+  the same product as rows of all taps times W^T and its adjoint, are kept as helpers for
+  tests and are checked against the direct form);
 * gn(z, gamma, beta, G): per sample and group of C / G consecutive channels, over all
   times and those channels: (z - mean) / sqrt(var + 1e-5) (biased variance), then
   gamma_c z + beta_c;
@@ -67,6 +69,40 @@ def col2im(dcols, T, C, k, s, p):
 def conv(x, W, k, s, p):
     cols = im2col(x, k, s, p, W.shape[1])
     return cols @ W.T, cols
+
+
+def conv_direct(x, W, k, s, p):
+    """The convolution as its definition, tap by tap: y[b][t][o] = sum over j < k and c of
+    W[o][j C + c] x[b][s t + j - p][c] (zero outside 0 <= index < T); columns of W past
+    k C (the stem's padding) do not enter."""
+    x = np.asarray(x, dtype=np.float64)
+    B, T, C = x.shape
+    To = (T + 2 * p - k) // s + 1
+    y = np.zeros((B, To, W.shape[0]))
+    for j in range(k):
+        src = s * np.arange(To) + j - p
+        ok = (src >= 0) & (src < T)
+        y[:, ok, :] += np.einsum("btc,oc->bto", x[:, src[ok], :], W[:, j * C:(j + 1) * C])
+    return y
+
+
+def conv_backward_direct(dz, x, W, k, s, p):
+    """(dx [B][T][C], dW with the shape of W) of y = conv_direct(x, W, k, s, p) for
+    dL/dy = dz, tap by tap: dx[b][s t + j - p][c] += sum_o dz[b][t][o] W[o][j C + c] and
+    dW[o][j C + c] = sum_{b, t} dz[b][t][o] x[b][s t + j - p][c]; padded columns of W get
+    zero."""
+    x = np.asarray(x, dtype=np.float64)
+    B, T, C = x.shape
+    To = dz.shape[1]
+    dx = np.zeros_like(x)
+    dW = np.zeros(W.shape)
+    for j in range(k):
+        src = s * np.arange(To) + j - p
+        ok = (src >= 0) & (src < T)
+        Wj = W[:, j * C:(j + 1) * C]
+        np.add.at(dx, (slice(None), src[ok], slice(None)), np.einsum("bto,oc->btc", dz[:, ok, :], Wj))
+        dW[:, j * C:(j + 1) * C] = np.einsum("bto,btc->oc", dz[:, ok, :], x[:, src[ok], :])
+    return dx, dW
 
 
 def gn(z, gamma, beta, G=GROUPS):
@@ -147,26 +183,26 @@ def forward(y, P, rnd=round_bf16):
     """Summary c [B][C_out] of whitened windows y [B][D][N]; returns (c, tape)."""
     x = rnd(np.transpose(np.asarray(y, dtype=np.float64), (0, 2, 1)))      # [B][N][D]
     tape = {"x": x}
-    z0, cols0 = conv(x, P["W0"], 7, 2, 3)
+    z0 = conv_direct(x, P["W0"], 7, 2, 3)
     a0p, xh0, r0 = gn(z0, P["g0"], P["b0"])
     a0 = rnd(np.maximum(a0p, 0.0))
     h, arg = maxpool(a0)
-    tape["stem"] = (cols0, xh0, r0, a0, arg)
+    tape["stem"] = (x, xh0, r0, a0, arg)
     tb = []
     for blk in P["blocks"]:
         s = blk["s"]
-        z1, c1 = conv(h, blk["W1"], 5, s, 2)
+        z1 = conv_direct(h, blk["W1"], 5, s, 2)
         h1p, xh1, r1 = gn(z1, blk["g1"], blk["b1"])
         h1 = rnd(np.maximum(h1p, 0.0))
-        z2, c2 = conv(h1, blk["W2"], 5, 1, 2)
+        z2 = conv_direct(h1, blk["W2"], 5, 1, 2)
         o, xh2, r2 = gn(z2, blk["g2"], blk["b2"])
         if "Wd" in blk:
-            zd, cd = conv(h, blk["Wd"], 1, s, 0)
+            zd = conv_direct(h, blk["Wd"], 1, s, 0)
             sc, xhd, rd = gn(zd, blk["gd"], blk["bd"])
         else:
-            sc, cd, xhd, rd = h, None, None, None
+            sc, xhd, rd = h, None, None
         out = rnd(np.maximum(o + sc, 0.0))
-        tb.append((h, c1, xh1, r1, h1, c2, xh2, r2, cd, xhd, rd, out))
+        tb.append((h, xh1, r1, h1, xh2, r2, xhd, rd, out))
         h = out
     tape["blocks"] = tb
     m = rnd(h.mean(axis=1))
@@ -186,35 +222,26 @@ def backward(dc, P, tape, rnd=round_bf16):
     gblocks = [None] * len(P["blocks"])
     for i in reversed(range(len(P["blocks"]))):
         blk = P["blocks"][i]
-        h, c1, xh1, r1, h1, c2, xh2, r2, cd, xhd, rd, out = tape["blocks"][i]
+        h, xh1, r1, h1, xh2, r2, xhd, rd, out = tape["blocks"][i]
         s = blk["s"]
         dsum = dh * (out > 0)
         g = {}
         dz2, g["g2"], g["b2"] = gn_back(dsum, xh2, r2, blk["g2"])
-        B, T2, C2 = dz2.shape
-        dzr = rnd(dz2).reshape(B * T2, C2)
-        g["W2"] = dzr.T @ c2.reshape(B * T2, -1)
-        dh1 = col2im((dzr @ blk["W2"]).reshape(B, T2, -1), h1.shape[1], h1.shape[2], 5, 1, 2)
+        dh1, g["W2"] = conv_backward_direct(rnd(dz2), h1, blk["W2"], 5, 1, 2)
         dh1 = dh1 * (h1 > 0)
         dz1, g["g1"], g["b1"] = gn_back(dh1, xh1, r1, blk["g1"])
-        B, T1, C1 = dz1.shape
-        dzr = rnd(dz1).reshape(B * T1, C1)
-        g["W1"] = dzr.T @ c1.reshape(B * T1, -1)
-        dx = col2im((dzr @ blk["W1"]).reshape(B, T1, -1), h.shape[1], h.shape[2], 5, s, 2)
+        dx, g["W1"] = conv_backward_direct(rnd(dz1), h, blk["W1"], 5, s, 2)
         if "Wd" in blk:
             dzd, g["gd"], g["bd"] = gn_back(dsum, xhd, rd, blk["gd"])
-            B, Td, Cd = dzd.shape
-            dzr = rnd(dzd).reshape(B * Td, Cd)
-            g["Wd"] = dzr.T @ cd.reshape(B * Td, -1)
-            dx = dx + col2im((dzr @ blk["Wd"]).reshape(B, Td, -1), h.shape[1], h.shape[2], 1, s, 0)
+            dxd, g["Wd"] = conv_backward_direct(rnd(dzd), h, blk["Wd"], 1, s, 0)
+            dx = dx + dxd
         else:
             dx = dx + dsum
         gblocks[i] = g
         dh = dx
     G["blocks"] = gblocks
-    cols0, xh0, r0, a0, arg = tape["stem"]
+    x0, xh0, r0, a0, arg = tape["stem"]
     da0 = maxpool_back(dh, arg, a0.shape[1]) * (a0 > 0)
     dz0, G["g0"], G["b0"] = gn_back(da0, xh0, r0, P["g0"])
-    B, T0, C0 = dz0.shape
-    G["W0"] = rnd(dz0).reshape(B * T0, C0).T @ cols0.reshape(B * T0, -1)
+    _, G["W0"] = conv_backward_direct(rnd(dz0), x0, P["W0"], 7, 2, 3)
     return G

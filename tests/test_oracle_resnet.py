@@ -1,5 +1,6 @@
-"""Pins of the ResNet-1D oracle (oracle/resnet.py): convolution against brute force, the
-im2col/col2im adjoint pair, group normalisation's statistics and gradient, max pooling,
+"""Pins of the ResNet-1D oracle (oracle/resnet.py): convolution against brute force (the
+network's direct tap-by-tap form and the im2col helper), the backward by the adjoint
+identities, the im2col/col2im adjoint pair, group normalisation's statistics and gradient, max pooling,
 and the whole network's gradient against central differences."""
 import numpy as np
 import pytest
@@ -28,6 +29,39 @@ def test_conv_matches_brute_force(k, s, p):
                     if 0 <= src < T:
                         ref[b, t, o] += sum(W[o, j * C + c] * x[b, src, c] for c in range(C))
     np.testing.assert_allclose(y, ref, atol=1e-12)
+
+
+@pytest.mark.parametrize("k,s,p", [(7, 2, 3), (5, 1, 2), (5, 2, 2), (1, 2, 0), (3, 1, 1)])
+def test_direct_convolution_and_its_backward(k, s, p):
+    """The network's convolution (conv_direct, tap by tap) equals a brute-force sum and the
+    im2col product; its backward equals the adjoint identity <dy, conv(x)> = <dx, x> and
+    <dy, conv(x, W)> = <dW, W> (linearity in x and in W), and the im2col route; padded
+    columns of W (the stem's) neither enter nor get a gradient."""
+    rng = np.random.default_rng(100 * k + 10 * s + p)
+    B, T, C, O = 2, 21, 3, 4
+    K = k * C + 5                      # extra zero-weight columns, as the stem's padding
+    x = rng.normal(size=(B, T, C))
+    W = rng.normal(size=(O, K))
+    W[:, k * C:] = 0.0
+    y = rn.conv_direct(x, W, k, s, p)
+    To = (T + 2 * p - k) // s + 1
+    ref = np.zeros((B, To, O))
+    for b in range(B):
+        for t in range(To):
+            for j in range(k):
+                src = s * t + j - p
+                if 0 <= src < T:
+                    ref[b, t] += W[:, j * C:(j + 1) * C] @ x[b, src]
+    np.testing.assert_allclose(y, ref, atol=1e-12)
+    np.testing.assert_allclose(y, rn.conv(x, W, k, s, p)[0], atol=1e-12)
+    dy = rng.normal(size=(B, To, O))
+    dx, dW = rn.conv_backward_direct(dy, x, W, k, s, p)
+    assert dW.shape == W.shape and np.all(dW[:, k * C:] == 0.0)
+    np.testing.assert_allclose(np.sum(dy * y), np.sum(dx * x), rtol=1e-12)
+    np.testing.assert_allclose(np.sum(dy * y), np.sum(dW * W), rtol=1e-12)
+    cols = rn.im2col(x, k, s, p, K)
+    np.testing.assert_allclose(dx, rn.col2im((dy.reshape(-1, O) @ W).reshape(B, To, K), T, C, k, s, p), atol=1e-12)
+    np.testing.assert_allclose(dW, dy.reshape(-1, O).T @ cols.reshape(-1, K), atol=1e-12)
 
 
 def test_col2im_is_the_adjoint_of_im2col():
