@@ -547,9 +547,9 @@ int gwx_simulate_batch(const gwx_prior* prior, uint64_t seed, uint32_t step, con
 
 size_t gwx_log_likelihood_workspace(int64_t E, int D, int64_t N, int64_t S) {
   if (E < 0 || D < 1 || N < 2 || S < 0) return 0;
-  // per-event spectra, whitening filter, per-event norm partials
+  // per-event spectra, whitening filter, per-event norm partials, merger-time grid constants
   return align_up((size_t)E * D * (size_t)(N / 2 + 1) * sizeof(float2)) + whiten_ws_bytes(D, N) +
-         align_up(loglike_norm_bytes(E));
+         align_up(loglike_norm_bytes(E)) + align_up(tm_rows_bytes());
 }
 
 // Shared by the two likelihood entry points: validation, data spectra, whitening filter
@@ -594,11 +594,13 @@ static int loglike_common(bool tmarg, int approximant, const float* y_data, int6
   float* W = reinterpret_cast<float*>(w);
   w += whiten_ws_bytes(D, N);
   double* yy_part = reinterpret_cast<double*>(w);
+  w += align_up(loglike_norm_bytes(E));
+  float2* tm_rows = reinterpret_cast<float2*>(w);
   GWX_TRY(launched(launch_rfft_rows(y_data, E * D, N, Y, s), "rfft of the data"));
   GWX_TRY(launched(launch_whiten_filter(psd, D, seg_len, fs, k_lo, N, W, s), "whiten filter"));
   if (tmarg)
     return launched(launch_loglike_tmarg(y_data, Y, W, theta, df, fs, dp, gmst, tc_lo, (int)n_tc, oversample,
-                                         event_offsets, yy_part, E, D, N, k_lo, S, lnl, s),
+                                         event_offsets, yy_part, tm_rows, E, D, N, k_lo, S, lnl, s),
                     "log_likelihood_tmarg");
   return launched(launch_loglike_full(y_data, Y, W, theta, df, fs, dp, gmst, event_offsets, yy_part, E, D, N, k_lo,
                                       S, lnl, s),

@@ -51,13 +51,9 @@ __device__ __forceinline__ float2 csquare(float2 a) {
   return make_float2(fmaf(a.x, a.x, -__fmul_rn(a.y, a.y)), __fmul_rn(2.f * a.x, a.y));
 }
 
-// w[r] = e^{-+2 pi i jm r/(16 Ns)}, r = 1 .. 15 (w[0] unused).  The products are written
-// with explicit roundings, so every kernel that inlines this rounds them alike.
-template <int Ns, bool INV>
-__device__ __forceinline__ void tw16(int jm, float2* w) {
-  static_assert(Ns >= 2 && Ns <= 512, "no radix-16 twiddle set for this stride");
-  w[1] = __ldg(g_tw16 + tw16_offset(Ns) + jm);
-  if constexpr (INV) w[1] = cconj(w[1]);
+// w[r] = w[1]^r for r = 2 .. 15 from w[1].  The products are written with explicit
+// roundings, so every kernel that inlines this rounds them alike.
+__device__ __forceinline__ void tw16_powers(float2* w) {
   w[2] = csquare(w[1]);
   w[4] = csquare(w[2]);
   w[8] = csquare(w[4]);
@@ -66,6 +62,15 @@ __device__ __forceinline__ void tw16(int jm, float2* w) {
   for (int l = 1; l < 4; ++l) w[4 + l] = cmul_rn(w[4], w[l]);
 #pragma unroll
   for (int l = 1; l < 8; ++l) w[8 + l] = cmul_rn(w[8], w[l]);
+}
+
+// w[r] = e^{-+2 pi i jm r/(16 Ns)}, r = 1 .. 15 (w[0] unused).
+template <int Ns, bool INV>
+__device__ __forceinline__ void tw16(int jm, float2* w) {
+  static_assert(Ns >= 2 && Ns <= 512, "no radix-16 twiddle set for this stride");
+  w[1] = __ldg(g_tw16 + tw16_offset(Ns) + jm);
+  if constexpr (INV) w[1] = cconj(w[1]);
+  tw16_powers(w);
 }
 
 // ---------------------------------------------------------------- butterfly

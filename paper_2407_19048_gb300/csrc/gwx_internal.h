@@ -85,11 +85,13 @@ cudaError_t launch_loglike_full(const float* ydata, const float2* Ydata, const f
                                 double* yy_part, int64_t E, int D, int64_t N, int k_lo, int64_t S, double* lnl,
                                 cudaStream_t s);
 // ln L with the merger time integrated out over tc_lo + j / (u fs), j < u n_tc (the tc row
-// of theta unused); the same data-norm kernel and workspace as launch_loglike_full.
+// of theta unused); the same data-norm kernel and workspace as launch_loglike_full, plus
+// tm_rows_bytes() of per-offset constants in rows.
+size_t tm_rows_bytes();
 cudaError_t launch_loglike_tmarg(const float* ydata, const float2* Ydata, const float* W, const double* theta,
                                  double df, double fs, const DetParams& dp, double gmst, double tc_lo, int n_tc,
-                                 int u, const int64_t* ev_off, double* yy_part, int64_t E, int D, int64_t N,
-                                 int k_lo, int64_t S, double* lnl, cudaStream_t s);
+                                 int u, const int64_t* ev_off, double* yy_part, float2* rows, int64_t E, int D,
+                                 int64_t N, int k_lo, int64_t S, double* lnl, cudaStream_t s);
 
 // Importance weights: E x iw_chunks(E) partials in ws (iw_workspace_bytes(E)).
 size_t iw_workspace_bytes(int64_t E);

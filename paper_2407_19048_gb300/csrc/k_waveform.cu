@@ -1,11 +1,15 @@
 // k_waveform.cu -- per-draw set-up, TaylorF2 waveforms (A2), projection (A3) and
 // the whitened log-likelihood (A8).
-#include "fft16.cuh"
+#include "fft16r.cuh"
 #include "waveform.cuh"
 
 namespace gwx {
 
-cudaError_t init_tables_waveform() { return fill_tables_for_this_tu(); }
+static cudaError_t fill_tmtw_for_this_tu();
+cudaError_t init_tables_waveform() {
+  const cudaError_t e = fill_tables_for_this_tu();
+  return e == cudaSuccess ? fill_tmtw_for_this_tu() : e;
+}
 cudaError_t debug_take_waveform(unsigned long long* v) { return dbg_take_this_tu(v); }
 
 // One thread per draw: FP64 set-up of the waveform and projection coefficients.
@@ -281,26 +285,121 @@ cudaError_t launch_loglike_full(const float* ydata, const float2* Ydata, const f
 // ln L_m = ln( (1/J) sum_{j<J} exp ln L(theta, tc = tc_lo + j / (u fs)) ),  J = u n_tc.
 // A merger-time shift only rotates the template's phase, so with the template H built at
 // tc = tc_lo and c_k = (2/N) sum_d Y_d,k conj(H_d,k) (band bins, zero elsewhere)
-//   ln L(tc_lo + (u m + r) / (u fs)) = -(|Y|^2 + |H|^2)/N + Re sum_k c_k e^{2 pi i k r/(N u)} e^{2 pi i k m/N},
-// i.e. for each sub-grid offset r < u an inverse real FFT of N points of
-// X_k = c_k e^{2 pi i k r/(N u)}, of which the outputs m < n_tc are used.  A block takes 32
-// consecutive samples: its first warp does their FP64 set-up (one lane per sample), then
-// per sample all threads build c_k in shared memory, and G groups of n/16 threads (16
-// values each) run the u transforms G at a time: the first inverse pass packs X into the
-// half-length complex transform as it loads (Z_m from X_m and X_{n-m}), the middle passes
-// alternate between two shared buffers (one barrier each), and the last pass folds its
-// outputs into a per-thread running maximum and sum of exponentials in registers; one
-// block reduction per sample gives ln L_m.
+//   ln L(tc_lo + (u m + r) / (u fs)) = -(|Y|^2 + |H|^2)/N + Re sum_k c_k e^{2 pi i k (u m + r)/(N u)},
+// i.e. for each sub-grid offset r < u the real inverse transform of N points of c_k a^k,
+// a = e^{2 pi i r/(N u)}, of which the outputs m < n_tc are used.
+//
+// Each is computed as a complex inverse transform of n = N/2 points of the packed
+// sequence Z_j = a^j (P_j + e^{-i pi r/u} Q_j), j < n, whose output p holds the real
+// outputs 2p and 2p + 1, with the per-sample tables (w = e^{-2 pi i/N})
+//   P_j = c_j (1 + i conj(w^j))/2,   Q_j = conj(c_{n-j}) (1 - i conj(w^j))/2,
+// which do not depend on r: the usual pairing of bins j and n - j of a real inverse
+// transform, with the ramp of bin n - j written as e^{i pi r/u} conj(a^j).  The ramp a^j
+// itself is never applied element by element.  A Stockham pass of radix R and stride Ns
+// consumes the digit of j of weight n/(R Ns), so the ramp enters as the factor
+// a^{n/(R Ns)} on that pass's twiddle base e^{2 pi i (j mod Ns)/(R Ns)} (every twiddle
+// taken at the fractional output shift r/(2u)); the first pass (Ns = 1) multiplies its
+// inputs by (a^{n/16})^q.  Passes: radix 16 (the first, reading the tables), radix-16
+// middle passes, and a last pass of radix RS = 2^(log2 n mod 4) (16 when that is 0).
+// Its output q of butterfly j holds the grid values 2 (j + q n/RS) and that + 1, so only
+// the q with 2 q n/RS < n_tc are needed; when few are, each is evaluated alone by
+// Horner's rule in e^{2 pi i (j + r/(2u))/n} e^{2 pi i q/RS}, otherwise the butterfly runs
+// in full.
+//
+// A block takes 32 consecutive samples: its first warp does their FP64 set-up (one lane
+// per sample); per sample all threads build P and Q in shared memory, then G groups of
+// n/16 threads (16 values each) run the u transforms G at a time, each group on its own
+// barrier; the last pass folds its outputs into a per-thread running maximum and sum of
+// exponentials, and one block reduction per sample gives ln L_m.
 constexpr int TM_SAMPLES = 32;
 
+// Twiddle powers l of a pass are products of two rounded factors at most: the powers
+// l in {1, 2, 3, 4, 8, 12} are (table entry) x (ramp power), each rounded once from FP64,
+// and l = 4a + b (b = 1 .. 3) is w^{4a} w^b.  (Powers formed by repeated squaring from one
+// base carry ~20 ulp at l = 15 and made the grid values of loud templates ~10x less
+// accurate.)
+constexpr int TM_NL = 6;
+__host__ __device__ constexpr int tm_l(int i) { return i < 4 ? i + 1 : 4 * (i - 2); }   // 1 2 3 4 8 12
+// middle-pass twiddles e^{2 pi i l jm/(16 Ns)} for Ns = 16, 256, laid out [Ns][l][jm]
+constexpr int TMTW_TOTAL = TM_NL * (16 + 256);
+__host__ __device__ constexpr int tmtw_offset(int Ns) { return Ns == 16 ? 0 : TM_NL * 16; }
+// last-pass twiddles e^{2 pi i l j/n} for the powers l = tm_l(i) < RS of each n = 2^LOGN,
+// LOGN = 7 .. 13, laid out [LOGN][i][j], j < n/RS
+__host__ __device__ constexpr int tm_rs(int logn) { return (logn % 4) ? (1 << (logn % 4)) : 16; }
+__host__ __device__ constexpr int tm_nl(int rs) { return rs >= 16 ? 6 : (rs >= 8 ? 4 : (rs >= 4 ? 3 : 1)); }
+__host__ __device__ constexpr int tmlast_offset(int logn) {
+  return logn <= 7 ? 0 : tmlast_offset(logn - 1) + tm_nl(tm_rs(logn - 1)) * ((1 << (logn - 1)) / tm_rs(logn - 1));
+}
+constexpr int TMLAST_TOTAL = tmlast_offset(14);
+namespace {
+__device__ float2 g_tmtw[TMTW_TOTAL];
+__device__ float2 g_tmlast[TMLAST_TOTAL];
+}
+static cudaError_t fill_tmtw_for_this_tu() {
+  static float2 tw[TMTW_TOTAL];
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int Ns = 16; Ns <= 256; Ns *= 16)
+    for (int i = 0; i < TM_NL; ++i)
+        for (int jm = 0; jm < Ns; ++jm) {
+          const float2 w = unit_twiddle(two_pi * (double)(tm_l(i) * jm) / (16.0 * Ns));   // e^{-i angle}
+          tw[tmtw_offset(Ns) + i * Ns + jm] = make_float2(w.x, -w.y);
+        }
+  cudaError_t e = cudaMemcpyToSymbol(g_tmtw, tw, sizeof(tw));
+  if (e != cudaSuccess) return e;
+  static float2 tl[TMLAST_TOTAL];
+  for (int lg = 7; lg <= 13; ++lg) {
+    const int n = 1 << lg, nb = n / tm_rs(lg);
+    for (int i = 0; i < tm_nl(tm_rs(lg)); ++i)
+      for (int j = 0; j < nb; ++j) {
+        const float2 w = unit_twiddle(two_pi * (double)(tm_l(i) * j) / (double)n);
+        tl[tmlast_offset(lg) + i * nb + j] = make_float2(w.x, -w.y);
+      }
+  }
+  return cudaMemcpyToSymbol(g_tmlast, tl, sizeof(tl));
+}
+
+// Per offset r (FP64-rounded once per block), entries e^{2 pi i m/(N u)}: [0, 16) the first
+// pass's twiddles (a^{n/16})^q; 16: e^{-i pi r/u}; [17, 23) and [23, 29): (a^W)^l of the
+// middle passes Ns = 16 and 256 (W = n/(16 Ns)), l = tm_l(i); [29, 35): a^l of the last pass.
+constexpr int TM_ROW = 36;
+constexpr int TM_ROW_MID = 17, TM_ROW_LAST = 29;
+constexpr int TM_U_MAX = 64;
+
+size_t tm_rows_bytes() { return (size_t)TM_U_MAX * TM_ROW * sizeof(float2); }
+
+// The u rows (one block, before the likelihood kernel; the blocks of that kernel copy them
+// into shared memory).
+__global__ void k_tm_rows(int n, int u, float2* __restrict__ rows) {
+  const int64_t Nu = 2LL * n * u;
+  for (int i = threadIdx.x; i < u * TM_ROW; i += blockDim.x) {
+    const int r = i / TM_ROW, k = i - r * TM_ROW;
+    int64_t m = 0;                                            // the entry is e^{2 pi i m/(N u)}
+    if (k < 16) m = (int64_t)k * (n / 16) * r;
+    else if (k == 16) m = -(int64_t)n * r;
+    else if (k < TM_ROW_LAST) m = (int64_t)(n >> (4 * ((k - TM_ROW_MID) / TM_NL + 2))) * tm_l((k - TM_ROW_MID) % TM_NL) * r;
+    else if (k < TM_ROW_LAST + TM_NL) m = (int64_t)tm_l(k - TM_ROW_LAST) * r;
+    m %= Nu;
+    if (m < 0) m += Nu;
+    double sn, cs;
+    sincospi(2.0 * (double)m / (double)Nu, &sn, &cs);
+    rows[i] = make_float2((float)cs, (float)sn);
+  }
+}
+
 template <int LOGN>
-struct TmGeom {
-  using PL = Plan16<LOGN>;
-  static constexpr int n = PL::n;                              // complex points of the packed transform
-  static constexpr int TPR = PL::T;                            // threads per transform (16 values each)
-  static constexpr int G = TPR >= 256 ? 1 : 256 / TPR;         // transforms in flight per block
+struct TmPlan {
+  static constexpr int n = 1 << LOGN;
+  static constexpr int TPR = n / 16;                                  // threads per transform
+  static constexpr int G = TPR >= 256 ? 1 : 256 / TPR;               // transforms in flight per block
   static constexpr int THREADS = TPR * G;
-  static constexpr size_t SMEM = ((size_t)G * 2 * n + (size_t)(n + 1)) * sizeof(float2);
+  static constexpr int RS = (LOGN % 4) ? (1 << (LOGN % 4)) : 16;      // radix of the last pass
+  static constexpr int NMID = LOGN / 4 - ((LOGN % 4) ? 1 : 2);       // radix-16 middle passes
+  static constexpr bool PP = LOGN <= 11;     // two buffers per transform; in place above (shared memory)
+  static constexpr int HQ = RS == 4 ? 1 : 0;  // Horner's rule (three steps) for one output of radix 4
+  static constexpr size_t smem(int u) {
+    return (size_t)n * sizeof(float4) + (size_t)G * (PP ? 2 : 1) * n * sizeof(float2) +
+           (size_t)u * TM_ROW * sizeof(float2);
+  }
 };
 
 // Running log-sum-exp state (max m, sum s of exp(v - m)).
@@ -319,40 +418,193 @@ __device__ __forceinline__ void lse_merge(float& m, float& s, float m2, float s2
   m = M;
 }
 
-// Elements m and n - m (0 < m < n) of the packed half-length transform of
-// X_k = c_k e^{2 pi i k r/(N u)}: with X_m and X_{n-m} (whose ramp is e^{i pi r/u} times the
-// conjugate of X_m's, cr = e^{i pi r/u}), pack_pair gives Z_m and Z_{n-m} together.
+// Barrier of the TPR threads of transform group g (named barrier 1 + g; within a warp,
+// the group's lanes).
+template <int TPR>
+__device__ __forceinline__ void tm_group_sync(int g) {
+  if constexpr (TPR > 32) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(TPR) : "memory");
+  } else if constexpr (TPR == 32) {
+    __syncwarp();
+  } else {
+    __syncwarp(((1u << TPR) - 1u) << ((threadIdx.x & 31) & ~(TPR - 1)));
+  }
+}
+
+// e^{2 pi i q/16}, q < 16 constant (nearest floats to the cosines of multiples of pi/8).
+__device__ __forceinline__ float2 unit16(int q) {
+  constexpr float c1 = 0.92387950420379638671875f, s1 = 0.3826834261417388916015625f;
+  constexpr float h = 0.707106769084930419921875f;
+  constexpr float cs[16] = {1.f, c1, h, s1, 0.f, -s1, -h, -c1, -1.f, -c1, -h, -s1, 0.f, s1, h, c1};
+  return make_float2(cs[q & 15], cs[(q + 12) & 15]);   // sin x = cos(x - pi/2)
+}
+
+// w[4a + b] = w[4a] w[b] for b = 1 .. 3 and 4a < R, from the powers tm_l(i) < R.
+template <int R>
+__device__ __forceinline__ void tm_fill_powers(float2* w) {
+#pragma unroll
+  for (int a4 = 4; a4 < R; a4 += 4) {
+#pragma unroll
+    for (int b = 1; b < 4; ++b) w[a4 + b] = cmul_rn(w[a4], w[b]);
+  }
+}
+
+// c_k = (2/N) sum_d Y_d,k conj(H_d,k) of bin k (zero outside [k_lo, kend]); |H_d,k|^2 is
+// added to the Kahan sum (hs, hcmp).
+template <int ND>
+__device__ __forceinline__ float2 tm_band_product(const DrawCoef& c, int k, int k_lo, int kend, int64_t F,
+                                                  const float* __restrict__ W, const float2* __restrict__ Y,
+                                                  int64_t e, int64_t E, float two_over_N, float& hs, float& hcmp) {
+  float2 acc = make_float2(0.f, 0.f);
+  if (k >= k_lo && k <= kend) {
+    float k76;
+    const float tt = waveform_turns(c, k, k76);
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      const float x = GWX_IDX_OK((int64_t)d * F + k, (int64_t)ND * F, 0x301) ? k76 * __ldg(&W[(int64_t)d * F + k]) : 0.f;
+      const float4 gg = c.g[d];
+      const float2 ph = expm2pi(tt + lin_turns(c.nu[d], k));
+      const float2 H = cmul(make_float2(df_scale(gg.x, gg.y, x), df_scale(gg.z, gg.w, x)), ph);
+      const float2 yv = GWX_IDX_OK((e * ND + d) * F + k, E * ND * F, 0x302) ? __ldg(&Y[(e * ND + d) * F + k])
+                                                                            : make_float2(0.f, 0.f);
+      acc.x = fmaf(yv.x, H.x, fmaf(yv.y, H.y, acc.x));
+      acc.y = fmaf(yv.y, H.x, fmaf(-yv.x, H.y, acc.y));
+      const float yk = fmaf(H.x, H.x, H.y * H.y) - hcmp;
+      const float tk = hs + yk;
+      hcmp = (tk - hs) - yk;
+      hs = tk;
+    }
+  }
+  return make_float2(acc.x * two_over_N, acc.y * two_over_N);
+}
+
+// First pass (radix 16, Ns = 1): butterfly t reads Z_{t + q n/16} from the tables (without
+// the factor a^t, which the later passes carry) and writes buffer dst.
 template <int LOGN>
-__device__ __forceinline__ void tm_pair(const float2* __restrict__ cb, int m, uint32_t r, uint32_t numask,
-                                        float inv_nu, float2 cr, float2& zm, float2& zn) {
-  constexpr int n = 1 << LOGN;
-  const float2 ph = expm2pi(-(float)(((uint32_t)m * r) & numask) * inv_nu);   // e^{+2 pi i m r/(N u)}
-  const float2 xm = cmul(cb[m], ph);
-  const float2 xn = cmul(cb[n - m], cmul(cr, cconj(ph)));
-  pack_pair(xm, xn, pack_twiddle(m, LOGN + 1), zm, zn);
+__device__ __forceinline__ void tm_first_pass(uint32_t pq, uint32_t row, uint32_t dst, int t) {
+  constexpr int T = (1 << LOGN) / 16;
+  const float2 crb = lds2(row + 8u * 16u);   // e^{-i pi r/u}
+  float2 v[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const float4 e = lds4(pq + 16u * (uint32_t)(t + q * T));
+    const float2 z = make_float2(fmaf(crb.x, e.z, fmaf(-crb.y, e.w, e.x)), fmaf(crb.x, e.w, fmaf(crb.y, e.z, e.y)));
+    v[q] = q ? cmul(z, lds2(row + 8u * (uint32_t)q)) : z;
+  }
+  dft16<true>(v);
+  store_pass16<16, 1>(dst, t, v);
+}
+
+// Middle pass of radix 16 and stride Ns: twiddles (e^{2 pi i (t mod Ns)/(16 Ns)} a^W)^l,
+// the ramp powers (a^W)^l at shared-memory address arow.
+template <int LOGN, int Ns, bool PP, int TPR>
+__device__ __forceinline__ void tm_mid_pass(uint32_t src, uint32_t dst, int t, int g, uint32_t arow) {
+  constexpr int nR = (1 << LOGN) / 16;
+  float2 v[16];
+  load_strided16<16, nR>(src, t, v);
+  float2 w[16];
+  const float2* tw = g_tmtw + tmtw_offset(Ns) + (t & (Ns - 1));
+#pragma unroll
+  for (int i = 0; i < TM_NL; ++i) w[tm_l(i)] = cmul_rn(__ldg(tw + i * Ns), lds2(arow + 8u * (uint32_t)i));
+  tm_fill_powers<16>(w);
+#pragma unroll
+  for (int l = 1; l < 16; ++l) v[l] = cmul(v[l], w[l]);
+  dft16<true>(v);
+  if constexpr (!PP) tm_group_sync<TPR>(g);
+  store_pass16<16, Ns>(dst, t, v);
+  tm_group_sync<TPR>(g);
+}
+
+// The middle passes p = 0 .. NMID-1 (Ns = 16^(p+1)); returns the buffer holding the result.
+template <int LOGN, int p>
+struct TmMid {
+  static __device__ __forceinline__ uint32_t run(uint32_t a, uint32_t b, uint32_t row, int t, int g) {
+    using PL = TmPlan<LOGN>;
+    if constexpr (p < PL::NMID) {
+      tm_mid_pass<LOGN, (1 << (4 * (p + 1))), PL::PP, PL::TPR>(a, PL::PP ? b : a, t, g,
+                                                                row + 8u * (uint32_t)(TM_ROW_MID + TM_NL * p));
+      return TmMid<LOGN, p + 1>::run(PL::PP ? b : a, PL::PP ? a : b, row, t, g);
+    } else {
+      return a;
+    }
+  }
+};
+
+// Last pass (radix RS, stride n/RS): the needed outputs of the butterflies t + i n/16
+// enter the running log-sum-exp (mx, sm); nq = the number of needed q.
+template <int LOGN>
+__device__ __forceinline__ void tm_last_pass(uint32_t src, int t, uint32_t row, int n_tc, int nq, float& mx, float& sm) {
+  using PL = TmPlan<LOGN>;
+  constexpr int n = 1 << LOGN, RS = PL::RS, NB = n / RS, T = n / 16;
+#pragma unroll
+  for (int i = 0; i < 16 / RS; ++i) {
+    const int j = t + i * T;
+    float2 v[RS];
+    load_strided16<RS, NB>(src, j, v);
+    const uint32_t arow = row + 8u * (uint32_t)TM_ROW_LAST;
+    const float2* tl = g_tmlast + tmlast_offset(LOGN) + j;
+    if (nq <= PL::HQ) {
+      const float2 b = cmul_rn(__ldg(tl), lds2(arow));   // e^{2 pi i (j + r/(2u))/n}
+#pragma unroll
+      for (int q = 0; q < PL::HQ; ++q) {
+        if (q < nq) {
+          const float2 gq = q ? cmul(b, unit16(q * (16 / RS))) : b;
+          float2 acc = v[RS - 1];
+#pragma unroll
+          for (int l = RS - 2; l >= 0; --l)
+            acc = make_float2(fmaf(acc.x, gq.x, fmaf(-acc.y, gq.y, v[l].x)), fmaf(acc.x, gq.y, fmaf(acc.y, gq.x, v[l].y)));
+          const int mp = j + q * NB;
+          if (2 * mp < n_tc) lse_add(mx, sm, acc.x);
+          if (2 * mp + 1 < n_tc) lse_add(mx, sm, acc.y);
+        }
+      }
+    } else {
+      // twiddles (e^{2 pi i j/n} a)^l
+      float2 w[RS];
+#pragma unroll
+      for (int i = 0; i < TM_NL; ++i) {
+        if (tm_l(i) < RS) w[tm_l(i)] = cmul_rn(__ldg(tl + i * NB), lds2(arow + 8u * (uint32_t)i));
+      }
+      tm_fill_powers<RS>(w);
+#pragma unroll
+      for (int l = 1; l < RS; ++l) v[l] = cmul(v[l], w[l]);
+      if constexpr (RS == 16) dft16<true>(v);
+      else dftR<RS, true, false>(v);
+#pragma unroll
+      for (int q = 0; q < RS; ++q) {
+        const int mp = j + q * NB;
+        if (2 * mp < n_tc) lse_add(mx, sm, v[q].x);
+        if (2 * mp + 1 < n_tc) lse_add(mx, sm, v[q].y);
+      }
+    }
+  }
 }
 
 template <int ND, int LOGN>
-__global__ void __launch_bounds__(TmGeom<LOGN>::THREADS, TmGeom<LOGN>::THREADS <= 256 ? 2 : 1)
+__global__ void __launch_bounds__(TmPlan<LOGN>::THREADS, TmPlan<LOGN>::THREADS <= 256 ? 2 : 1)
 k_loglike_tmarg(const double* __restrict__ theta, SetupConsts kc, double fs, DetParams dp, double gmst, double tc_lo,
                 const float2* __restrict__ Y, const float* __restrict__ W, const int64_t* __restrict__ ev_off,
-                const double* __restrict__ yy_part, int64_t E, int k_lo, int n_tc, int u, int64_t S, double invN,
-                double log_J, double* __restrict__ lnl) {
-  using Gm = TmGeom<LOGN>;
-  using PL = typename Gm::PL;
-  constexpr int n = Gm::n;
+                const double* __restrict__ yy_part, const float2* __restrict__ g_rows, int64_t E, int k_lo, int n_tc,
+                int u, int nq, int64_t S, double invN, double log_J, double* __restrict__ lnl) {
+  using PL = TmPlan<LOGN>;
+  constexpr int n = PL::n;
   constexpr int F = n + 1;
-  constexpr int NT = Gm::THREADS;
-  constexpr int NW = NT / 32 > 0 ? NT / 32 : 1;
-  constexpr int TPR = Gm::TPR, RL = PL::RL, NB = PL::NB, P = PL::P;
-  extern __shared__ float2 tm_smem[];
-  float2* cb = tm_smem + Gm::G * 2 * n;                        // c_k, k = 0 .. n
+  constexpr int NT = PL::THREADS;
+  constexpr int NW = NT / 32;
+  constexpr int TPR = PL::TPR;
+  constexpr int NBUF = PL::PP ? 2 : 1;
+  extern __shared__ __align__(16) unsigned char tm_smem[];
   __shared__ DrawCoef sc[TM_SAMPLES];
   __shared__ int se[TM_SAMPLES];
   __shared__ float red_m[NW], red_s[NW];
   __shared__ double red_h[NW];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int g = tid / TPR, t = tid % TPR;
+  // dynamic shared memory: P_j, Q_j as float4 [n]; G x NBUF buffers of n float2; u rows
+  const uint32_t pq = smem_addr(tm_smem);
+  const uint32_t buf0 = pq + 16u * n + 8u * (uint32_t)(g * NBUF * n);
+  const uint32_t buf1 = buf0 + 8u * n;
+  const uint32_t rows = pq + 16u * n + 8u * (uint32_t)(PL::G * NBUF * n);
   const int64_t base = (int64_t)blockIdx.x * TM_SAMPLES;
   const int cnt = (int)min((int64_t)TM_SAMPLES, S - base);
   if (wid == 0 && lane < cnt) {
@@ -369,104 +621,41 @@ k_loglike_tmarg(const double* __restrict__ theta, SetupConsts kc, double fs, Det
     sc[lane] = c;
     se[lane] = (int)lo;
   }
+  for (int i = tid; i < u * TM_ROW; i += NT) sts2(rows + 8u * (uint32_t)i, __ldg(&g_rows[i]));
   __syncthreads();
   const float two_over_N = (float)(2.0 * invN);               // a power of two: exact
-  const uint32_t bufA = smem_addr(tm_smem + g * 2 * n), bufB = bufA + 8u * (uint32_t)n;
-  const uint32_t numask = (uint32_t)(2 * n) * (uint32_t)u - 1u;   // N u - 1 (N u a power of two)
-  const float inv_nu = 1.0f / (float)(numask + 1u);
-  const float inv_2u = 0.5f / (float)u;
   for (int j = 0; j < cnt; ++j) {
     const int64_t e = se[j];
     const int kend = min(sc[j].kcut, n - 1);
-    // c_k and this thread's part of sum |H|^2 (Kahan)
+    // P, Q of the pair (k, n - k) and this thread's part of sum |H|^2 (Kahan)
     float hs = 0.f, hcmp = 0.f;
-    for (int k = tid; k <= n; k += NT) {
-      float2 acc = make_float2(0.f, 0.f);
-      if (k >= k_lo && k <= kend) {
-        const DrawCoef& c = sc[j];
-        float k76;
-        const float tt = waveform_turns(c, k, k76);
-#pragma unroll
-        for (int d = 0; d < ND; ++d) {
-          const float x =
-              GWX_IDX_OK((int64_t)d * F + k, (int64_t)ND * F, 0x301) ? k76 * __ldg(&W[(int64_t)d * F + k]) : 0.f;
-          const float4 gg = c.g[d];
-          const float2 ph = expm2pi(tt + lin_turns(c.nu[d], k));
-          const float2 H = cmul(make_float2(df_scale(gg.x, gg.y, x), df_scale(gg.z, gg.w, x)), ph);
-          const float2 yv = GWX_IDX_OK((e * ND + d) * F + k, E * ND * F, 0x302) ? __ldg(&Y[(e * ND + d) * F + k])
-                                                                                : make_float2(0.f, 0.f);
-          acc.x = fmaf(yv.x, H.x, fmaf(yv.y, H.y, acc.x));
-          acc.y = fmaf(yv.y, H.x, fmaf(-yv.x, H.y, acc.y));
-          const float yk = fmaf(H.x, H.x, H.y * H.y) - hcmp;
-          const float tk = hs + yk;
-          hcmp = (tk - hs) - yk;
-          hs = tk;
-        }
+    for (int k = tid; k <= n / 2; k += NT) {
+      const float2 ck = tm_band_product<ND>(sc[j], k, k_lo, kend, F, W, Y, e, E, two_over_N, hs, hcmp);
+      const float2 cn = k == n / 2 ? ck : tm_band_product<ND>(sc[j], n - k, k_lo, kend, F, W, Y, e, E, two_over_N, hs, hcmp);
+      const float2 w = pack_twiddle(k, LOGN + 1);               // e^{-2 pi i k/N}
+      const float2 h1 = make_float2(0.5f * (1.f + w.y), 0.5f * w.x);   // (1 + i conj w)/2
+      const float2 h2 = make_float2(0.5f * (1.f - w.y), -0.5f * w.x);  // (1 - i conj w)/2
+      const float2 Pk = cmul(ck, h1), Qk = cmul(cconj(cn), h2);
+      sts4(pq + 16u * (uint32_t)k, make_float4(Pk.x, Pk.y, Qk.x, Qk.y));
+      if (k != 0 && k != n / 2) {
+        // P_{n-k} = c_{n-k} (1 - i w)/2, Q_{n-k} = conj(c_k) (1 + i w)/2
+        const float2 Pn = cmul(cn, cconj(h1)), Qn = cmul(cconj(ck), cconj(h2));
+        sts4(pq + 16u * (uint32_t)(n - k), make_float4(Pn.x, Pn.y, Qn.x, Qn.y));
       }
-      cb[k] = make_float2(acc.x * two_over_N, acc.y * two_over_N);
     }
     __syncthreads();
     float mx = -INFINITY, sm = 0.f;
-    for (int r0 = 0; r0 < u; r0 += Gm::G) {
-      const uint32_t r = (uint32_t)(r0 + g);
-      const float2 cr = expm2pi(-(float)r * inv_2u);         // e^{i pi r/u}
-      // first inverse pass (radix RL, Ns = 1), reading the packed transform from c_k: a
-      // thread owns butterflies p and NB - p, which hold both members of every pair
-      // (m, n - m), so each pair's phase ramp and packing are computed once
-#pragma unroll
-      for (int s2 = 0; s2 < PL::SLOTS; ++s2) {
-        const int pp = t + s2 * TPR;
-        const int jA = pp, jB = pp ? NB - pp : NB / 2;
-        float2 vA[RL], vB[RL];
-        if (pp != 0) {
-#pragma unroll
-          for (int q = 0; q < RL; ++q)
-            tm_pair<LOGN>(cb, jA + NB * q, r, numask, inv_nu, cr, vA[q], vB[RL - 1 - q]);
-        } else {
-          // butterfly 0 holds Z_0 (zero: c_0 = c_n = 0), the pairs (NB q, NB (RL - q)) and
-          // Z_{n/2}; butterfly NB/2 holds the pairs (NB/2 + NB q, NB/2 + NB (RL - 1 - q))
-          vA[0] = make_float2(0.f, 0.f);
-#pragma unroll
-          for (int q = 1; q < RL; ++q) {
-            if (q < RL - q) tm_pair<LOGN>(cb, NB * q, r, numask, inv_nu, cr, vA[q], vA[RL - q]);
-          }
-          if (RL > 1) {
-            float2 zh, unused;
-            tm_pair<LOGN>(cb, n / 2, r, numask, inv_nu, cr, zh, unused);
-            vA[RL / 2] = zh;
-          }
-#pragma unroll
-          for (int q = 0; q < RL / 2; ++q)
-            tm_pair<LOGN>(cb, NB / 2 + NB * q, r, numask, inv_nu, cr, vB[q], vB[RL - 1 - q]);
-        }
-        dftR<RL, true, false>(vA);
-        dftR<RL, true, false>(vB);
-        store_pass<RL, 1>(bufA, jA, vA);
-        store_pass<RL, 1>(bufA, jB, vB);
+    for (int r0 = 0; r0 < u; r0 += PL::G) {
+      const int r = r0 + g;
+      if (r < u) {                                            // uniform over the group
+        const uint32_t row = rows + 8u * (uint32_t)(r * TM_ROW);
+        tm_first_pass<LOGN>(pq, row, buf0, t);
+        tm_group_sync<TPR>(g);
+        const uint32_t xl = TmMid<LOGN, 0>::run(buf0, buf1, row, t, g);
+        tm_last_pass<LOGN>(xl, t, row, n_tc, nq, mx, sm);
+        // the next first pass rewrites buf0, which the last pass read in these two cases
+        if constexpr (!PL::PP || PL::NMID % 2 == 0) tm_group_sync<TPR>(g);
       }
-      __syncthreads();
-      const uint32_t xl = InvMiddlePP<LOGN, 1, P - 2, RL>::run(bufA, bufB, t);
-      // last inverse pass (radix 8, Ns = n/8); its outputs are the grid's Re z values
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int jj = t + i * TPR;
-        float2 v[8];
-        load_strided<8, n / 8>(xl, jj, v);
-        float2 w[8];
-        pass_twiddles<8, n / 8, true>(jj, w);
-#pragma unroll
-        for (int q = 1; q < 8; ++q) v[q] = cmul(v[q], w[q]);
-        dft8<true, false>(v);
-        if ((int)r < u) {
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int mp = jj + q * (n / 8);
-            if (2 * mp < n_tc) lse_add(mx, sm, v[q].x);
-            if (2 * mp + 1 < n_tc) lse_add(mx, sm, v[q].y);
-          }
-        }
-      }
-      __syncthreads();                                        // the next round's first pass rewrites bufA
     }
     // block reductions: (max, sum) and sum |H|^2 (FP64 across threads)
     double hh = (double)hs - (double)hcmp;
@@ -493,14 +682,14 @@ k_loglike_tmarg(const double* __restrict__ theta, SetupConsts kc, double fs, Det
       for (int c = 0; c < YY_CHUNKS; ++c) yy += yy_part[e * YY_CHUNKS + c];
       if (GWX_IDX_OK(base + j, S, 0x303)) lnl[base + j] = -(yy + H2) * invN + (double)M + log((double)Sm) - log_J;
     }
-    __syncthreads();                                          // c_k and the reduction slots are reused
+    __syncthreads();                                          // the tables and the reduction slots are reused
   }
 }
 
 cudaError_t launch_loglike_tmarg(const float* ydata, const float2* Ydata, const float* W, const double* theta,
                                  double df, double fs, const DetParams& dp, double gmst, double tc_lo, int n_tc,
-                                 int u, const int64_t* ev_off, double* yy_part, int64_t E, int D, int64_t N,
-                                 int k_lo, int64_t S, double* lnl, cudaStream_t s) {
+                                 int u, const int64_t* ev_off, double* yy_part, float2* rows, int64_t E, int D,
+                                 int64_t N, int k_lo, int64_t S, double* lnl, cudaStream_t s) {
   const int64_t F = N / 2 + 1;
   const int n = (int)(N / 2);
   if (E > 0) {
@@ -509,18 +698,27 @@ cudaError_t launch_loglike_tmarg(const float* ydata, const float2* Ydata, const 
     if (err != cudaSuccess) return err;
   }
   if (S <= 0) return cudaSuccess;
+  if (u < 1 || u > TM_U_MAX || n_tc < 1) return cudaErrorInvalidValue;
+  k_tm_rows<<<1, 256, 0, s>>>(n, u, rows);
+  {
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+  }
   const unsigned grid = (unsigned)((S + TM_SAMPLES - 1) / TM_SAMPLES);
   const double invN = 1.0 / (double)N;
   const double log_J = log((double)u * (double)n_tc);
   const SetupConsts kc = make_setup_consts(df);
   return dispatch_log<7, 13>(ilog2_exact(n), [&](auto lg) -> cudaError_t {
     constexpr int LG = decltype(lg)::value;
-    using Gm = TmGeom<LG>;
+    using PL = TmPlan<LG>;
+    constexpr int NB = PL::n / PL::RS;
+    const int nq = min(PL::RS, (n_tc + 2 * NB - 1) / (2 * NB));   // outputs q of the last pass with 2 q NB < n_tc
+    const size_t smem = PL::smem(u);
     auto run = [&](auto kern) -> cudaError_t {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SMEM);
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::smem(TM_U_MAX));
       if (e != cudaSuccess) return e;
-      kern<<<grid, Gm::THREADS, Gm::SMEM, s>>>(theta, kc, fs, dp, gmst, tc_lo, Ydata, W, ev_off, yy_part, E, k_lo,
-                                               n_tc, u, S, invN, log_J, lnl);
+      kern<<<grid, PL::THREADS, smem, s>>>(theta, kc, fs, dp, gmst, tc_lo, Ydata, W, ev_off, yy_part, rows, E, k_lo,
+                                           n_tc, u, nq, S, invN, log_J, lnl);
       return cudaGetLastError();
     };
     switch (D) {

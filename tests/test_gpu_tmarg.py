@@ -69,18 +69,27 @@ def _samples(th_true, counts, prior, seed):
     return s, offs
 
 
+# The transforms have n = N/2 points: radix-16 passes and a last pass of radix 2^(log2 n
+# mod 4) (16 when that is 0), whose needed outputs (2 q n/RS < n_tc) are evaluated one by
+# one (few) or by the full butterfly; the cases cover every n from 2^7 to 2^13 and both.
 CASES = [
     ("small", 16, 512, 1.0),     # the two-detector workload's prior window [1, 1.5) s, grid 61 us
     ("small", 1, 37, 0.93),      # odd window length, no sub-grid
-    ("small", 4, 2048, 0.0),     # the whole circular window
-    ("hl3", 4, 256, 2.2),        # three detectors, N = 8192
-    ("sweep", 2, 64, 4.5),       # N = 16384 (one transform per block)
+    ("small", 4, 2048, 0.0),     # the whole circular window (full last butterflies)
+    ("hl3", 4, 256, 2.2),        # three detectors, N = 8192 (last radix 16, one output each)
+    ("hl3", 2, 6000, 0.4),       # N = 8192, twelve of sixteen outputs (full last butterflies)
+    ("sweep", 2, 64, 4.5),       # N = 16384 (one transform per block, in place)
+    (("small", 128, 2.0), 8, 64, 1.0),     # N = 256 (last radix 8, two outputs each)
+    (("small", 256, 2.0), 4, 100, 0.97),   # N = 512 (last radix 16, four outputs each)
+    (("small", 512, 2.0), 2, 129, 1.0),    # N = 1024 (last radix 2)
+    (("small", 2048, 2.0), 4, 700, 1.0),   # N = 4096 (last radix 8, full)
+    (("small", 2048, 2.0), 64, 200, 1.1),  # N = 4096, one output each, the largest oversampling
 ]
 
 
 @pytest.mark.parametrize("name,u,n_tc,tc_lo", CASES)
 def test_tmarg_matches_oracle(gwx, name, u, n_tc, tc_lo):
-    wl = workloads.workload(name)
+    wl = workloads.resampled(*name) if isinstance(name, tuple) else workloads.workload(name)
     E = 5
     th_true, y, psd, prior = _events(wl, E, 51)
     counts = workloads.ragged_counts(52, E, 3, 37, zeros=1)

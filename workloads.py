@@ -69,6 +69,16 @@ def workload(name, **overrides):
     return wl
 
 
+def resampled(name, fs, T):
+    """Workload `name` at sampling rate fs and window T (N = fs T), with its detectors,
+    priors (merger time in [T/2, 3T/4)), background and Welch segment lengths in seconds."""
+    base = WORKLOADS[name]
+    p = base["prior"]
+    prior = _prior((p["m_lo"], p["m_hi"]), (p["chi_lo"], p["chi_hi"]), (p["d_lo"], p["d_hi"]), T)
+    return _workload("%s_%g_%g" % (name, fs, T), base["B"], base["dets"], fs, T, base["L"] / base["fs"],
+                     base["seg_len"] / base["fs"], prior)
+
+
 # ---------------------------------------------------------------------------
 # Seeded arbitrary inputs (numpy generator; independent of the method's Philox)
 # ---------------------------------------------------------------------------
