@@ -584,40 +584,73 @@ def conv_leg(gwx, torch, reps=20):
     return t
 
 
-def flow_resnet_leg(gwx, torch, rank, steps=1500, batch=512, events=64):
+def flow_resnet_leg(gwx, torch, rank, steps=1500, batch=512, events=64, pretrain_steps=400, pretrain_batch=256):
     """The flow with the paper's ResNet-1D data summary (stem, (5, 3, 3) residual blocks of
     64 / 128 / 256 channels, group norm, kernel 5; convolutions on the tensor cores) in
     place of the spectral-feature network, trained jointly with AdamW on 512-draw batches
     of the non-spinning two-detector workload; importance sampling of config 4's events
-    as in the flow leg."""
+    as in the flow leg.  A second arm first pre-trains the ResNet with VICReg on the raw
+    whitened strain (Sec. 4.1: two views per source that differ in the merger time,
+    expander 64 -> 128 -> 24, weights 1, 1, 5), then trains the flow the same way."""
     import paper_2407_19048_gb300.simulator  # noqa: F401
     from paper_2407_19048_gb300.flow import FlowPosterior
+    from paper_2407_19048_gb300.pretrain import VICRegPretrainer
     wl = workloads.workload("small_nonspinning", B=batch)
-    sim = gwx.simulator.Simulator(wl, pipeline=True, background_every=16)
-    fp = FlowPosterior(wl, layers=16, hidden=256, context=64, seed=0, lr=3e-4, weight_decay=2e-3,
-                       embedding="resnet")
-    y, th, _ = sim.step(step_counter(rank, 90000))
-    fp.train_step(y, th, update=False)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    losses = []
-    for i in range(steps):
-        y, th, _ = sim.step(step_counter(rank, 90001 + i))
-        loss = fp.train_step(y, th)
-        if i % max(1, steps // 8) == 0 or i == steps - 1:
-            losses.append((i, loss.clone()))
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
     wl_ev = dict(workloads.workload("small_nonspinning", B=events), param_seed=777)
     sim_ev = gwx.simulator.Simulator(wl_ev)
     y_ev, _, _ = sim_ev.step(step_counter(rank, 0))
     y_ev = y_ev.clone()
-    isamp = is_compare(gwx, torch, fp, wl_ev, y_ev, sim_ev.psd, workloads.ragged_counts(4, events, 2000, 50000),
-                       workloads.tc_grid(wl_ev))
-    del sim, sim_ev
-    return {"summary": "ResNet-1D", "resnet_params": sum(p.numel() for _, p, _ in fp.resnet.tensors()),
-            "train_steps": steps, "batch": batch, "train_s": train_s, "step_ms": 1e3 * train_s / steps,
-            "loss": [(i, float(l.item())) for i, l in losses], "importance_sampling": isamp}
+    psd_ev = sim_ev.psd.clone()
+    del sim_ev
+    counts = workloads.ragged_counts(4, events, 2000, 50000)
+
+    def arm(pretrain):
+        sim = gwx.simulator.Simulator(wl, pipeline=True, background_every=16)
+        fp = FlowPosterior(wl, layers=16, hidden=256, context=64, seed=0, lr=3e-4, weight_decay=2e-3,
+                           embedding="resnet")
+        out = {}
+        if pretrain:
+            pt = VICRegPretrainer(fp, batch=pretrain_batch, lr=1e-3, seed=7)
+            pt.step(0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            trace = []
+            for k in range(1, pretrain_steps + 1):
+                loss, terms = pt.step(k)
+                if k % max(1, pretrain_steps // 8) == 0 or k == 1 or k == pretrain_steps:
+                    trace.append((k, loss.clone(), terms.clone()))
+            torch.cuda.synchronize()
+            out["pretraining"] = {
+                "steps": pretrain_steps, "view_pairs_per_step": pretrain_batch,
+                "s": time.perf_counter() - t0,
+                "loss": [(k, float(l.item())) for k, l, _ in trace],
+                "terms_last": [float(v) for v in trace[-1][2].cpu()],
+                "terms_note": "invariance, variance x, variance x', covariance x, covariance x'"}
+            del pt
+        y, th, _ = sim.step(step_counter(rank, 90000))
+        fp.train_step(y, th, update=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        losses = []
+        for i in range(steps):
+            y, th, _ = sim.step(step_counter(rank, 90001 + i))
+            loss = fp.train_step(y, th)
+            if i % max(1, steps // 8) == 0 or i == steps - 1:
+                losses.append((i, loss.clone()))
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        del sim
+        out.update({"train_steps": steps, "batch": batch, "train_s": train_s, "step_ms": 1e3 * train_s / steps,
+                    "loss": [(i, float(l.item())) for i, l in losses],
+                    "importance_sampling": is_compare(gwx, torch, fp, wl_ev, y_ev, psd_ev, counts,
+                                                      workloads.tc_grid(wl_ev))})
+        out["resnet_params"] = sum(p.numel() for _, p, _ in fp.resnet.tensors())
+        return out
+
+    res = dict(summary="ResNet-1D", **arm(False))
+    if pretrain_steps > 0:
+        res["vicreg_pretrained"] = arm(True)
+    return res
 
 
 def is_compare(gwx, torch, fp, wl, y_ev, psd, counts, grid, seed=5, reps=3):
@@ -1122,7 +1155,8 @@ def main(argv=None):
         import paper_2407_19048_gb300 as gwx
         import paper_2407_19048_gb300.simulator  # noqa: F401
         gwx.init()
-        print(json.dumps({"flow_resnet": flow_resnet_leg(gwx, torch, 0, steps=int(args.only_resnet))}), flush=True)
+        print(json.dumps({"flow_resnet": flow_resnet_leg(gwx, torch, 0, steps=int(args.only_resnet), pretrain_steps=0)}),
+              flush=True)
         return 0
     if args.only_loglike:
         import torch

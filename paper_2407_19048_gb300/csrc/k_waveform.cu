@@ -596,8 +596,8 @@ k_loglike_tmarg(const double* __restrict__ theta, SetupConsts kc, double fs, Det
   extern __shared__ __align__(16) unsigned char tm_smem[];
   __shared__ DrawCoef sc[TM_SAMPLES];
   __shared__ int se[TM_SAMPLES];
-  __shared__ float red_m[NW], red_s[NW];
-  __shared__ double red_h[NW];
+  __shared__ float red_m[TM_SAMPLES][NW], red_s[TM_SAMPLES][NW];   // per sample and warp
+  __shared__ double red_h[TM_SAMPLES][NW];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int g = tid / TPR, t = tid % TPR;
   // dynamic shared memory: P_j, Q_j as float4 [n]; G x NBUF buffers of n float2; u rows
@@ -627,20 +627,26 @@ k_loglike_tmarg(const double* __restrict__ theta, SetupConsts kc, double fs, Det
   for (int j = 0; j < cnt; ++j) {
     const int64_t e = se[j];
     const int kend = min(sc[j].kcut, n - 1);
-    // P, Q of the pair (k, n - k) and this thread's part of sum |H|^2 (Kahan)
+    // P, Q of the pair (k, n - k) and this thread's part of sum |H|^2 (Kahan); item 0 also
+    // takes the middle bin n/2 (its own pair), so the n/2 items split evenly
     float hs = 0.f, hcmp = 0.f;
-    for (int k = tid; k <= n / 2; k += NT) {
-      const float2 ck = tm_band_product<ND>(sc[j], k, k_lo, kend, F, W, Y, e, E, two_over_N, hs, hcmp);
-      const float2 cn = k == n / 2 ? ck : tm_band_product<ND>(sc[j], n - k, k_lo, kend, F, W, Y, e, E, two_over_N, hs, hcmp);
-      const float2 w = pack_twiddle(k, LOGN + 1);               // e^{-2 pi i k/N}
-      const float2 h1 = make_float2(0.5f * (1.f + w.y), 0.5f * w.x);   // (1 + i conj w)/2
-      const float2 h2 = make_float2(0.5f * (1.f - w.y), -0.5f * w.x);  // (1 - i conj w)/2
-      const float2 Pk = cmul(ck, h1), Qk = cmul(cconj(cn), h2);
-      sts4(pq + 16u * (uint32_t)k, make_float4(Pk.x, Pk.y, Qk.x, Qk.y));
-      if (k != 0 && k != n / 2) {
-        // P_{n-k} = c_{n-k} (1 - i w)/2, Q_{n-k} = conj(c_k) (1 + i w)/2
-        const float2 Pn = cmul(cn, cconj(h1)), Qn = cmul(cconj(ck), cconj(h2));
-        sts4(pq + 16u * (uint32_t)(n - k), make_float4(Pn.x, Pn.y, Qn.x, Qn.y));
+    for (int k = tid; k < n / 2; k += NT) {
+#pragma unroll 1
+      for (int h = 0; h < (k == 0 ? 2 : 1); ++h) {
+        const int kk = h ? n / 2 : k;
+        const float2 ck = tm_band_product<ND>(sc[j], kk, k_lo, kend, F, W, Y, e, E, two_over_N, hs, hcmp);
+        const float2 cn =
+            h ? ck : tm_band_product<ND>(sc[j], n - kk, k_lo, kend, F, W, Y, e, E, two_over_N, hs, hcmp);
+        const float2 w = pack_twiddle(kk, LOGN + 1);              // e^{-2 pi i kk/N}
+        const float2 h1 = make_float2(0.5f * (1.f + w.y), 0.5f * w.x);   // (1 + i conj w)/2
+        const float2 h2 = make_float2(0.5f * (1.f - w.y), -0.5f * w.x);  // (1 - i conj w)/2
+        const float2 Pk = cmul(ck, h1), Qk = cmul(cconj(cn), h2);
+        sts4(pq + 16u * (uint32_t)kk, make_float4(Pk.x, Pk.y, Qk.x, Qk.y));
+        if (kk != 0 && kk != n / 2) {
+          // P_{n-k} = c_{n-k} (1 - i w)/2, Q_{n-k} = conj(c_k) (1 + i w)/2
+          const float2 Pn = cmul(cn, cconj(h1)), Qn = cmul(cconj(ck), cconj(h2));
+          sts4(pq + 16u * (uint32_t)(n - kk), make_float4(Pn.x, Pn.y, Qn.x, Qn.y));
+        }
       }
     }
     __syncthreads();
@@ -657,7 +663,8 @@ k_loglike_tmarg(const double* __restrict__ theta, SetupConsts kc, double fs, Det
         if constexpr (!PL::PP || PL::NMID % 2 == 0) tm_group_sync<TPR>(g);
       }
     }
-    // block reductions: (max, sum) and sum |H|^2 (FP64 across threads)
+    // per-warp reductions of (max, sum) and sum |H|^2; the warps' partials are merged, and
+    // the norms added, for all samples at once at the end
     double hh = (double)hs - (double)hcmp;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -665,24 +672,25 @@ k_loglike_tmarg(const double* __restrict__ theta, SetupConsts kc, double fs, Det
       hh += __shfl_xor_sync(0xffffffffu, hh, o);
     }
     if (lane == 0) {
-      red_m[wid] = mx;
-      red_s[wid] = sm;
-      red_h[wid] = hh;
+      red_m[j][wid] = mx;
+      red_s[j][wid] = sm;
+      red_h[j][wid] = hh;
     }
-    __syncthreads();
-    if (tid == 0) {
-      float M = red_m[0], Sm = red_s[0];
-      double H2 = red_h[0];
-      for (int w = 1; w < NW; ++w) {
-        lse_merge(M, Sm, red_m[w], red_s[w]);
-        H2 += red_h[w];
-      }
-      double yy = 0.0;
+    __syncthreads();                                          // the tables are rewritten for the next sample
+  }
+  if (wid == 0 && lane < cnt) {
+    const int j = lane;
+    float M = red_m[j][0], Sm = red_s[j][0];
+    double H2 = red_h[j][0];
+    for (int w = 1; w < NW; ++w) {
+      lse_merge(M, Sm, red_m[j][w], red_s[j][w]);
+      H2 += red_h[j][w];
+    }
+    const int64_t e = se[j];
+    double yy = 0.0;
 #pragma unroll
-      for (int c = 0; c < YY_CHUNKS; ++c) yy += yy_part[e * YY_CHUNKS + c];
-      if (GWX_IDX_OK(base + j, S, 0x303)) lnl[base + j] = -(yy + H2) * invN + (double)M + log((double)Sm) - log_J;
-    }
-    __syncthreads();                                          // the tables and the reduction slots are reused
+    for (int c = 0; c < YY_CHUNKS; ++c) yy += yy_part[e * YY_CHUNKS + c];
+    if (GWX_IDX_OK(base + j, S, 0x303)) lnl[base + j] = -(yy + H2) * invN + (double)M + log((double)Sm) - log_J;
   }
 }
 

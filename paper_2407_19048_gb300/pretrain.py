@@ -5,12 +5,14 @@ identical but for the time of arrival, get the same representation: both views a
 summarised, expanded by a small network to 24 dimensions, and the VICReg loss of the two
 expanded batches (weights 1, 1, 5) is minimised; the expander is then dropped and the
 summary keeps training with the flow.  `VICRegPretrainer` does this for a
-`flow.FlowPosterior`'s embedding: per step it draws B sources from the prior, redraws
+`flow.FlowPosterior`'s summary: per step it draws B sources from the prior, redraws
 their merger times for the second view (`retime`), renders both views into one 2B batch
-against the same background crops (`prepare_theta` + `simulate_prepared`), computes the
-features and the embedding and expander forward on the 2B rows (tcgen05 dense layers),
-the loss and its gradient (`vicreg`), the backward pass, and AdamW on the embedding's
-tensors (updated in place in the flow's parameter arrays) and the expander's.
+against the same background crops (`prepare_theta` + `simulate_prepared`), summarises the
+2B rows, runs the expander (tcgen05 dense layers), the loss and its gradient (`vicreg`),
+the backward pass, and AdamW on the summary's tensors (updated in place in the flow's
+parameter arrays) and the expander's.  The summary is the flow's own: the spectral-feature
+network, or the ResNet-1D over the raw whitened strain (the paper's case, where nothing but
+the pre-training makes the representation insensitive to the arrival time).
 """
 import ctypes
 import math
@@ -42,11 +44,15 @@ class VICRegPretrainer:
             self.X.append(w)
             self.X16.append(w.to(torch.bfloat16))
             self.c.append(torch.zeros(o, device=self.dev))
-        # AdamW moments: the embedding's six tensors and the expander's four
-        self.emb = list(range(6))
+        # AdamW moments: the summary's tensors (the embedding's six, or the ResNet's) and
+        # the expander's four
+        self.resnet = flow.resnet
+        if self.resnet is None:
+            summary = [("e%d" % t, flow.tensor(t)) for t in range(6)]
+        else:
+            summary = [("r:" + name, p) for name, p, _ in self.resnet.tensors()]
         self.mom = {}
-        for key, t in [("e%d" % t, flow.tensor(t)) for t in self.emb] + \
-                      [("X%d" % i, self.X[i]) for i in range(2)] + [("c%d" % i, self.c[i]) for i in range(2)]:
+        for key, t in summary + [("X%d" % i, self.X[i]) for i in range(2)] + [("c%d" % i, self.c[i]) for i in range(2)]:
             self.mom[key] = (torch.zeros_like(t), torch.zeros_like(t))
         self.steps = 0
         self.y = torch.empty((2 * self.B, self.D, self.N), dtype=torch.float32, device=self.dev)
@@ -99,13 +105,18 @@ class VICRegPretrainer:
         import torch
         gwx, fp = self.gwx, self.fp
         R, N = gwx.ACT_RELU, gwx.ACT_NONE
-        f = self.features(y)
-        h1 = gwx.dense_bf16(f, fp.tensor(0, True), fp.tensor(1), act=R, out_dtype=torch.bfloat16)
-        h2 = gwx.dense_bf16(h1, fp.tensor(2, True), fp.tensor(3), act=R, out_dtype=torch.bfloat16)
-        ctx = gwx.dense_bf16(h2, fp.tensor(4, True), fp.tensor(5), act=N, out_dtype=torch.bfloat16)
+        if self.resnet is not None:
+            ctx = self.resnet.forward(y, out_dtype=torch.bfloat16)
+            acts = (None, None, None)
+        else:
+            f = self.features(y)
+            h1 = gwx.dense_bf16(f, fp.tensor(0, True), fp.tensor(1), act=R, out_dtype=torch.bfloat16)
+            h2 = gwx.dense_bf16(h1, fp.tensor(2, True), fp.tensor(3), act=R, out_dtype=torch.bfloat16)
+            ctx = gwx.dense_bf16(h2, fp.tensor(4, True), fp.tensor(5), act=N, out_dtype=torch.bfloat16)
+            acts = (f, h1, h2)
         e1 = gwx.dense_bf16(ctx, self.X16[0], self.c[0], act=R, out_dtype=torch.bfloat16)
         x = gwx.dense_bf16(e1, self.X16[1], self.c[1], act=N, out_dtype=torch.float32)
-        return ctx, x, (f, h1, h2, e1)
+        return ctx, x, acts + (e1,)
 
     def step(self, step):
         """One pre-training step; returns (loss [1], terms [5]) as device tensors."""
@@ -117,16 +128,20 @@ class VICRegPretrainer:
         loss, terms, _, _ = gwx.vicreg(x[:B], x[B:], self.lam, grad_x=g[:B], grad_xp=g[B:])
         de1, dX1, dc1 = gwx.dense_bf16_backward(e1, self.X16[1], self.c[1], g, act=gwx.ACT_NONE)
         dctx, dX0, dc0 = gwx.dense_bf16_backward(ctx, self.X16[0], self.c[0], de1, act=gwx.ACT_RELU)
-        dh2, dW3, db3 = gwx.dense_bf16_backward(h2, fp.tensor(4, True), fp.tensor(5), dctx, act=gwx.ACT_NONE)
-        dh1, dW2, db2 = gwx.dense_bf16_backward(h1, fp.tensor(2, True), fp.tensor(3), dh2, act=gwx.ACT_RELU)
-        _, dW1, db1 = gwx.dense_bf16_backward(f, fp.tensor(0, True), fp.tensor(1), dh1, act=gwx.ACT_RELU)
         self.steps += 1
         k = self.steps
-        upd = [("e0", fp.tensor(0), dW1, fp.tensor(0, True)), ("e1", fp.tensor(1), db1, None),
-               ("e2", fp.tensor(2), dW2, fp.tensor(2, True)), ("e3", fp.tensor(3), db2, None),
-               ("e4", fp.tensor(4), dW3, fp.tensor(4, True)), ("e5", fp.tensor(5), db3, None),
-               ("X0", self.X[0], dX0, self.X16[0]), ("X1", self.X[1], dX1, self.X16[1]),
-               ("c0", self.c[0], dc0, None), ("c1", self.c[1], dc1, None)]
+        if self.resnet is not None:
+            G = self.resnet.backward(dctx.float().contiguous())
+            upd = [("r:" + name, p, G[name], p16) for name, p, p16 in self.resnet.tensors()]
+        else:
+            dh2, dW3, db3 = gwx.dense_bf16_backward(h2, fp.tensor(4, True), fp.tensor(5), dctx, act=gwx.ACT_NONE)
+            dh1, dW2, db2 = gwx.dense_bf16_backward(h1, fp.tensor(2, True), fp.tensor(3), dh2, act=gwx.ACT_RELU)
+            _, dW1, db1 = gwx.dense_bf16_backward(f, fp.tensor(0, True), fp.tensor(1), dh1, act=gwx.ACT_RELU)
+            upd = [("e0", fp.tensor(0), dW1, fp.tensor(0, True)), ("e1", fp.tensor(1), db1, None),
+                   ("e2", fp.tensor(2), dW2, fp.tensor(2, True)), ("e3", fp.tensor(3), db2, None),
+                   ("e4", fp.tensor(4), dW3, fp.tensor(4, True)), ("e5", fp.tensor(5), db3, None)]
+        upd += [("X0", self.X[0], dX0, self.X16[0]), ("X1", self.X[1], dX1, self.X16[1]),
+                ("c0", self.c[0], dc0, None), ("c1", self.c[1], dc1, None)]
         for key, p, grad, p16 in upd:
             m, v = self.mom[key]
             gwx.adamw(p, grad.contiguous(), m, v, k, self.lr, weight_decay=self.wd, param_bf16=p16)

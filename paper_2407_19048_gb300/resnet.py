@@ -4,11 +4,14 @@ A stem convolution (kernel 7, stride 2, 64 channels), group normalisation, ReLU 
 max pool, then stacks of basic residual blocks with 64, 128 and 256 channels ((5, 3, 3)
 blocks, kernel 5, the first block of a stack striding by 2 with a 1 x 1 projection on
 the shortcut), the mean over time and a fully connected layer to the representation.
-Every convolution is an im2col row matrix times the weights on the tensor cores
-(`gwx_im2col`, `gwx_dense_bf16`; backward `gwx_dense_bf16_backward`, `gwx_col2im`),
-normalisation, residual addition and ReLU are fused (`gwx_group_norm`), and the backward
-pass mirrors it call by call.  Activations are channels-last bfloat16, convolution
-outputs FP32.
+The stride-1 kernel-5 convolutions are implicit GEMMs on the tensor cores
+(`gwx_conv1d_bf16`: the A tiles come from a 3-D tensor map of the activations; backward
+`gwx_conv1d_bf16_backward`: the input gradient is the same product with mirrored taps, the
+weight gradient a split-K product over transposed rows); the stem, the strided entries and
+the 1 x 1 shortcuts use im2col rows times the weights (`gwx_im2col`, `gwx_dense_bf16`;
+backward `gwx_dense_bf16_backward`, `gwx_col2im`).  Normalisation, residual addition and
+ReLU are fused (`gwx_group_norm`), and the backward pass mirrors the forward call by call.
+Activations are channels-last bfloat16, convolution outputs FP32.
 """
 import ctypes
 import math

@@ -76,3 +76,30 @@ def test_pretraining_lowers_the_loss_and_pulls_views_together(gwx):
         if k >= 110:
             last.append(loss.item())
     assert np.mean(last) < 0.8 * np.mean(first), (np.mean(first), np.mean(last))
+
+
+def test_pretraining_the_resnet_summary_on_raw_strain_lowers_the_loss(gwx):
+    """VICReg on the ResNet-1D over the raw whitened strain (the paper's case): both views
+    run through the ResNet, the expander and the loss; the gradient flows back through the
+    ResNet's implicit-GEMM convolutions and group norms and AdamW updates its tensors in
+    place.  A two-stage ResNet on one fixed batch of 256 view pairs (every call renders the
+    views of step 0): the first update lowers the loss, 25 of them lower it by more than 7 %
+    (measured: 1.95 -> 1.73; the hinged variance terms keep it well above zero this early),
+    and every ResNet tensor moves."""
+    from paper_2407_19048_gb300.flow import FlowPosterior
+    from paper_2407_19048_gb300.pretrain import VICRegPretrainer
+    wl = workloads.workload("small", B=256)
+    fp = FlowPosterior(wl, layers=2, hidden=64, context=32, embedding="resnet",
+                       resnet_stages=((64, 1, 1), (128, 1, 2)))
+    before = {name: p.clone() for name, p, _ in fp.resnet.tensors()}
+    pt = VICRegPretrainer(fp, batch=256, lr=1e-3)
+    losses = []
+    for _ in range(25):
+        loss, terms = pt.step(0)
+        assert torch.isfinite(loss).all() and torch.isfinite(terms).all()
+        losses.append(loss.item())
+    assert losses[1] < losses[0], losses[:3]
+    assert losses[-1] < 0.93 * losses[0], (losses[0], losses[-1])
+    moved = [name for name, p, _ in fp.resnet.tensors() if not torch.equal(p, before[name])]
+    assert len(moved) == len(before)
+    assert gwx._lib.load().gwx_device_status() == 0
