@@ -584,14 +584,17 @@ def conv_leg(gwx, torch, reps=20):
     return t
 
 
-def flow_resnet_leg(gwx, torch, rank, steps=1500, batch=512, events=64, pretrain_steps=400, pretrain_batch=256):
+def flow_resnet_leg(gwx, torch, rank, steps=1500, batch=512, events=64, pretrain_steps=800, pretrain_batch=256,
+                    pretrain_lr=1e-4):
     """The flow with the paper's ResNet-1D data summary (stem, (5, 3, 3) residual blocks of
     64 / 128 / 256 channels, group norm, kernel 5; convolutions on the tensor cores) in
     place of the spectral-feature network, trained jointly with AdamW on 512-draw batches
     of the non-spinning two-detector workload; importance sampling of config 4's events
     as in the flow leg.  A second arm first pre-trains the ResNet with VICReg on the raw
     whitened strain (Sec. 4.1: two views per source that differ in the merger time,
-    expander 64 -> 128 -> 24, weights 1, 1, 5), then trains the flow the same way."""
+    expander 64 -> 128 -> 24, weights 1, 1, 5; 800 steps of 256 view pairs at a learning
+    rate of 1e-4 -- at 1e-3 or 3e-4 the flow trained after it was behind the plain arm),
+    then trains the flow the same way."""
     import paper_2407_19048_gb300.simulator  # noqa: F401
     from paper_2407_19048_gb300.flow import FlowPosterior
     from paper_2407_19048_gb300.pretrain import VICRegPretrainer
@@ -610,7 +613,7 @@ def flow_resnet_leg(gwx, torch, rank, steps=1500, batch=512, events=64, pretrain
                            embedding="resnet")
         out = {}
         if pretrain:
-            pt = VICRegPretrainer(fp, batch=pretrain_batch, lr=1e-3, seed=7)
+            pt = VICRegPretrainer(fp, batch=pretrain_batch, lr=pretrain_lr, seed=7)
             pt.step(0)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -621,7 +624,7 @@ def flow_resnet_leg(gwx, torch, rank, steps=1500, batch=512, events=64, pretrain
                     trace.append((k, loss.clone(), terms.clone()))
             torch.cuda.synchronize()
             out["pretraining"] = {
-                "steps": pretrain_steps, "view_pairs_per_step": pretrain_batch,
+                "steps": pretrain_steps, "view_pairs_per_step": pretrain_batch, "lr": pretrain_lr,
                 "s": time.perf_counter() - t0,
                 "loss": [(k, float(l.item())) for k, l, _ in trace],
                 "terms_last": [float(v) for v in trace[-1][2].cpu()],
