@@ -656,12 +656,61 @@ def flow_resnet_leg(gwx, torch, rank, steps=1500, batch=512, events=64, pretrain
     return res
 
 
+def tmarg_leg(gwx, torch, events=64, lo=2000, hi=50000, reps=3):
+    """The likelihood with the merger time integrated out (`gwx_log_likelihood_tmarg`)
+    alone, on config 4's scale: `events` two-detector events of the non-spinning workload
+    with U{lo..hi} prior samples each, the merger time integrated over the prior's window
+    on a grid 16 times finer than the sampling interval (u = 16 inverse transforms of
+    n = N/2 = 1024 packed points per sample).  CUDA-event time per call, best of `reps`.
+    Roofline: the u transforms' 5 n log2 n flops per sample (the band products and the
+    log-sum-exp not counted) against the FP32 peak."""
+    import numpy as np
+    import paper_2407_19048_gb300.simulator  # noqa: F401
+    wl = dict(workloads.workload("small_nonspinning", B=events), param_seed=777)
+    sim = gwx.simulator.Simulator(wl)
+    y, _, _ = sim.step(step_counter(0, 0))
+    counts = workloads.ragged_counts(4, events, lo, hi)
+    offs = torch.from_numpy(np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)).cuda()
+    S = int(counts.sum())
+    theta, _ = gwx.sample_prior(wl["prior"], 5, 0, S, wl["L"], wl["N"])
+    tc_lo, n_tc, u = workloads.tc_grid(wl)
+    out = torch.empty(S, dtype=torch.float64, device="cuda")
+
+    def call():
+        gwx.log_likelihood_tmarg(y, sim.psd, wl["seg_len"], wl["fs"], wl["f_lo"], wl["dets"], 0.0, tc_lo, n_tc, u,
+                                 theta, offs, out=out)
+
+    call()
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        call()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    n = wl["N"] // 2
+    flops = u * 5 * n * int(math.log2(n))
+    mhz, mhz_src = sm_max_mhz(None)
+    n_sm, peak = fp32_peak(torch, mhz)
+    achieved = flops * S / (best * 1e-3) / 1e12
+    return {"samples": S, "events": events, "grid": {"tc_lo": tc_lo, "n_tc": n_tc, "oversample": u},
+            "ms_per_call": best, "ns_per_sample": best * 1e6 / S, "samples_per_s": S / (best * 1e-3),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "flops_per_sample": flops,
+                         "peak_basis": "%d SMs x %d FP32 lanes x 2 flop x %.0f MHz (%s); derived" %
+                                       (n_sm, FP32_LANES_PER_SM, mhz, mhz_src)}}
+
+
 def is_compare(gwx, torch, fp, wl, y_ev, psd, counts, grid, seed=5, reps=3):
     """Importance sampling of events y_ev [E][D][N] with counts[e] draws each, from the
     prior and from the flow, every draw scored by the likelihood with the merger time
     integrated out over `grid` and weighted (ln w = ln L + ln prior - ln q).  Device
-    time (CUDA events) of draws + ln L + weights, best of `reps`; per-event ESS and
-    efficiency with their medians."""
+    time (CUDA events) of draws + ln L + weights, best of `reps`; every repetition draws
+    the same samples (the same counter), so the per-event ESS and efficiency (with their
+    medians) do not depend on which repetition was fastest."""
     import numpy as np
     offs = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
     S = int(offs[-1])
@@ -675,9 +724,9 @@ def is_compare(gwx, torch, fp, wl, y_ev, psd, counts, grid, seed=5, reps=3):
             torch.cuda.synchronize()
             e0.record()
             if arm == "flow":
-                theta, _, lrat = fp.sample(y_ev, offs_d, seed, rep, S=S)
+                theta, _, lrat = fp.sample(y_ev, offs_d, seed, 0, S=S)
             else:
-                theta, _ = gwx.sample_prior(wl["prior"], seed, rep, S, wl["L"], wl["N"])
+                theta, _ = gwx.sample_prior(wl["prior"], seed, 0, S, wl["L"], wl["N"])
                 lrat = None
             lnl = gwx.log_likelihood_tmarg(y_ev, psd, wl["seg_len"], wl["fs"], wl["f_lo"], wl["dets"], 0.0, tc_lo,
                                            n_tc, u, theta, offs_d)
@@ -1030,6 +1079,7 @@ def run_gpu(args, wl):
     gemm = gemm_leg(gwx, torch)
     flow = flow_leg(gwx, torch, rank)
     flow_resnet = flow_resnet_leg(gwx, torch, rank)
+    tmarg = tmarg_leg(gwx, torch)
     conv1d = conv_leg(gwx, torch)
     padded = padded_leg(gwx, torch, rank)
 
@@ -1067,7 +1117,7 @@ def run_gpu(args, wl):
             "serving": serve,
             "gemm_bf16": gemm,
             "flow": flow,
-            "flow_resnet": flow_resnet, "conv1d_stage1": conv1d,
+            "flow_resnet": flow_resnet, "log_likelihood_tmarg": tmarg, "conv1d_stage1": conv1d,
             "padded_grid": padded,
             "wall_s_timed_region": t_wall,
         }
@@ -1094,6 +1144,8 @@ def main(argv=None):
                     help="time only the device step (no end-to-end or log-likelihood leg); for profiling")
     ap.add_argument("--only-loglike", default=None, metavar="LO,HI",
                     help="run only the log-likelihood leg with U{LO..HI} samples per event; for profiling")
+    ap.add_argument("--only-tmarg", default=None, metavar="E,LO,HI",
+                    help="run only the merger-time-marginalised likelihood on E events of U{LO..HI} samples")
     ap.add_argument("--only-gemm", default=None, metavar="M,N,K",
                     help="run only the bfloat16 product leg at this shape; for profiling")
     ap.add_argument("--only-flow-sample", default=None, metavar="E,S",
@@ -1160,6 +1212,13 @@ def main(argv=None):
         gwx.init()
         print(json.dumps({"flow_resnet": flow_resnet_leg(gwx, torch, 0, steps=int(args.only_resnet), pretrain_steps=0)}),
               flush=True)
+        return 0
+    if args.only_tmarg:
+        import torch
+        import paper_2407_19048_gb300 as gwx
+        E, lo, hi = (int(v) for v in args.only_tmarg.split(","))
+        gwx.init()
+        print(json.dumps({"log_likelihood_tmarg": tmarg_leg(gwx, torch, E, lo, hi)}), flush=True)
         return 0
     if args.only_loglike:
         import torch
