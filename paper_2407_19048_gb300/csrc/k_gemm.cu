@@ -18,6 +18,15 @@
 // Every mbarrier wait is bounded: on expiry the CTA records a status, stops storing,
 // frees its tensor memory and returns.
 //
+// Wide tiles (MW = 2, large products): a CTA computes a 256 x 256 tile of C as two
+// M 128 x N 256 products that share each B tile, from three 64 KiB stages (A 256 x 64 in
+// one TMA box, B 256 x 64).  Per flop this moves a third less operand data from L2 into
+// shared memory than the 128 x 256 tile (the 128 x 256 kernel's operand stream, ~84 B per
+// cycle and SM at full tensor rate, is what holds its tensor pipe near 70 %).  The two
+// accumulators fill the 512 tensor-memory columns, so a tile's epilogue no longer overlaps
+// the next tile's products (~2 % at K = 8192); the eight draining warps take one
+// accumulator half each.
+//
 // Split K: a product with few tiles and a long K (the weight gradients dW = dZ^T X, whose
 // K is the batch) would run on a handful of SMs.  There the work list is (tile, K slice)
 // pairs: slice s covers K blocks [s kbs, (s + 1) kbs) and stores its FP32 partial product
@@ -38,20 +47,25 @@ using namespace tc;
 constexpr int GM = 128, GN = 256, GK = 64, STAGES = 4;   // GN: the dense products' tile width
 constexpr int EPI_WARPS = 8;                            // two per tensor-memory lane quarter
 constexpr int GEMM_THREADS = 64 + 32 * EPI_WARPS;
-constexpr uint32_t A_BYTES = GM * GK * 2;               // 16 KiB
 constexpr uint32_t WAIT_POLLS = 1u << 22;
 constexpr uint32_t EPI_BUF_BYTES = 32 * 32 * 4;         // per epilogue warp: a 32 x 32 FP32 transpose tile
 
-// Per tile width TN_ (64, 128 or 256 columns of C): B tile, stage and accumulator sizes.
-template <int TN_>
+// Per tile width TN_ (64, 128 or 256 columns of C) and M-tiles per CTA MW (1, or 2 with
+// TN_ = 256): B tile, stage and accumulator sizes.  MW = 1: two accumulators of TN_
+// columns alternate between tiles; MW = 2: one pair (rows 0-127, 128-255) per tile.
+template <int TN_, int MW = 1>
 struct Tile {
+  static_assert(MW == 1 || (MW == 2 && TN_ == 256), "wide tiles are 256 x 256");
+  static constexpr int ROWS = GM * MW;                     // rows of C per tile
+  static constexpr uint32_t A_TILE = (uint32_t)ROWS * GK * 2;
   static constexpr uint32_t B_BYTES = TN_ * GK * 2;
-  static constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr uint32_t TMEM_COLS = TN_;              // FP32 accumulator columns
+  static constexpr uint32_t STAGE_BYTES = A_TILE + B_BYTES;
+  static constexpr int NSTAGE = MW == 1 ? STAGES : 3;
+  static constexpr int NACC = MW == 1 ? 2 : 1;             // accumulator sets in tensor memory
+  static constexpr uint32_t TMEM_COLS = TN_;              // FP32 columns of one accumulator
   static constexpr uint32_t IDESC = idesc_bf16(GM, TN_);
-  static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + (size_t)EPI_WARPS * EPI_BUF_BYTES + 1024;
+  static constexpr size_t SMEM = (size_t)NSTAGE * STAGE_BYTES + (size_t)EPI_WARPS * EPI_BUF_BYTES + 1024;
 };
-constexpr size_t GEMM_SMEM = Tile<GN>::SMEM;
 
 // Implicit-GEMM convolution geometry (conv mode): A is the channels-last activation
 // x [B][T][Cin] as a 3-D tensor map; M tile tm covers times 128 (tm mod T/128) ..
@@ -100,15 +114,21 @@ __device__ __forceinline__ void tile_coords(int t, int TM, int TN, int group, in
 // over.
 // TN_: tile width; CONV: A is loaded as an implicit im2col tile (ConvGeo).  addend
 // (optional; N % 32 == 0, 16-byte aligned): C = (A B^T + addend), then bias and activation.
-template <bool OUT_BF16, int TN_, bool CONV>
+template <bool OUT_BF16, int TN_, bool CONV, int MW = 1>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, void* __restrict__ C,
                 const float* __restrict__ bias, int act, int group, int M, int N, int K, int kbs, int splits,
                 const float* __restrict__ addend, ConvGeo geo) {
+  static_assert(MW == 1 || !CONV, "wide tiles are for plain products");
   constexpr int GN = TN_;
-  constexpr uint32_t STAGE_BYTES = Tile<TN_>::STAGE_BYTES;
-  constexpr uint32_t TMEM_COLS = Tile<TN_>::TMEM_COLS;
-  constexpr uint32_t IDESC = Tile<TN_>::IDESC;
+  using TL = Tile<TN_, MW>;
+  constexpr int GMT = TL::ROWS;
+  constexpr int STAGES = TL::NSTAGE;
+  constexpr int NACC = TL::NACC;
+  constexpr uint32_t A_BYTES = TL::A_TILE;
+  constexpr uint32_t STAGE_BYTES = TL::STAGE_BYTES;
+  constexpr uint32_t TMEM_COLS = TL::TMEM_COLS;
+  constexpr uint32_t IDESC = TL::IDESC;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2];
   __shared__ uint32_t tmem_slot;
@@ -116,7 +136,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t base = (su32(smem_raw) + 1023u) & ~1023u;   // 1024-byte aligned stages
   const int KB = (K + GK - 1) / GK;
-  const int TM = (M + GM - 1) / GM, TN = (N + GN - 1) / GN;
+  const int TM = (M + GMT - 1) / GMT, TN = (N + GN - 1) / GN;
   const int tiles = TM * TN;
   const int work = tiles * splits;   // (tile, K slice) pairs, tile fastest
 
@@ -163,7 +183,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             const int tap = kb / geo.KC, cb = kb - tap * geo.KC;
             tma_load_3d(sa, &ta, cb * GK, (tm % tpb) * GM + geo.dir * (tap - geo.pad), tm / tpb, su32(&full[s]));
           } else {
-            tma_load_2d(sa, &ta, kb * GK, tm * GM, su32(&full[s]));
+            tma_load_2d(sa, &ta, kb * GK, tm * GMT, su32(&full[s]));   // one box of GMT rows
           }
           tma_load_2d(sb, &tb, kb * GK, tn * GN, su32(&full[s]));
         }
@@ -173,9 +193,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     if (lane == 0) {
       uint32_t it = 0, tl = 0;
       for (int w = blockIdx.x; w < work && !*(volatile int*)&abort_flag; w += gridDim.x, ++tl) {
-        const uint32_t acc = tl & 1u;
+        const uint32_t acc = tl % NACC;
         const int kb0 = (w / tiles) * kbs, kb1 = min(KB, kb0 + kbs);
-        if (tl >= 2 && !mbar_wait(su32(&tempty[acc]), ((tl >> 1) - 1) & 1u, WAIT_POLLS)) {
+        if (tl >= NACC && !mbar_wait(su32(&tempty[acc]), ((tl / NACC) - 1) & 1u, WAIT_POLLS)) {
           atomicExch(&abort_flag, 1);
           break;
         }
@@ -191,8 +211,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t sa = base + s * STAGE_BYTES, sb = sa + A_BYTES;
 #pragma unroll
-          for (int kk = 0; kk < GK / 16; ++kk)   // 16 bfloat16 = 32 bytes along K per instruction
-            mma_bf16(d, sw128_desc(sa + 32u * kk), sw128_desc(sb + 32u * kk), IDESC, kb != kb0 || kk != 0);
+          for (int kk = 0; kk < GK / 16; ++kk) {   // 16 bfloat16 = 32 bytes along K per instruction
+            // M-tile m: rows 128 m .. of the A box (16 KiB apart), accumulator columns m TN_ ..
+#pragma unroll
+            for (int m = 0; m < MW; ++m)
+              mma_bf16(d + (uint32_t)m * TMEM_COLS, sw128_desc(sa + (uint32_t)m * (GM * GK * 2) + 32u * kk),
+                       sw128_desc(sb + 32u * kk), IDESC, kb != kb0 || kk != 0);
+          }
           mma_commit(su32(&empty[s]));
         }
         if (!ok) atomicExch(&abort_flag, 1);
@@ -201,10 +226,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       }
     }
   } else {
-    // epilogue warps 2-9; tensor-memory lane quarter (warp % 4) = tile rows 32 q .. 32 q + 31,
-    // column half (warp - 2) / 4
+    // epilogue warps 2-9; tensor-memory lane quarter (warp % 4) = tile rows 32 q .. 32 q + 31;
+    // (warp - 2) / 4 picks the column half (MW = 1) or the M-tile (MW = 2, all columns)
     const int q = warp & 3;
-    const int c_lo = ((warp - 2) >> 2) * (GN / 64), c_hi = c_lo + GN / 64;
+    const int hsel = (warp - 2) >> 2;
+    const int c_lo = MW == 1 ? hsel * (GN / 64) : 0, c_hi = MW == 1 ? c_lo + GN / 64 : GN / 32;
+    const int msel = MW == 1 ? 0 : hsel;
     float* ebuf = reinterpret_cast<float*>(smem_raw + (base - su32(smem_raw)) + STAGES * STAGE_BYTES +
                                            (warp - 2) * EPI_BUF_BYTES);
     uint32_t tl = 0;
@@ -212,8 +239,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       int tm, tn;
       tile_coords(w % tiles, TM, TN, group, tm, tn);
       const size_t slice = (size_t)(w / tiles) * (size_t)M * (size_t)N;   // 0 unless split
-      const uint32_t acc = tl & 1u;
-      const bool have = mbar_wait(su32(&tfull[acc]), (tl >> 1) & 1u, WAIT_POLLS);
+      const uint32_t acc = tl % NACC;
+      const bool have = mbar_wait(su32(&tfull[acc]), (tl / NACC) & 1u, WAIT_POLLS);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (__any_sync(0xffffffffu, !have || *(volatile int*)&abort_flag != 0)) {
         if (lane == 0) atomicExch(&abort_flag, 1);
@@ -222,7 +249,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       // Each warp stages its 32 rows x 32 columns through a swizzled shared tile (word j of
       // row r at r * 32 + (j ^ r): conflict-free both ways), then stores whole row segments:
       // FP32 one 128-byte row per instruction, bfloat16 two 64-byte rows per instruction.
-      const int row0 = tm * GM + 32 * q;
+      const int row0 = tm * GMT + GM * msel + 32 * q;
 #pragma unroll 1
       for (int c = c_lo; c < c_hi; ++c) {
         float v[32];
@@ -237,7 +264,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 #pragma unroll
           for (int j = 0; j < 8; ++j) ad[j] = in ? __ldg(ap + j) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + acc * TMEM_COLS + (uint32_t)(32 * c), v);
+        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (acc + (uint32_t)msel) * TMEM_COLS + (uint32_t)(32 * c), v);
         if (row0 >= M || col0 >= N) continue;   // warp-uniform
         if (addend != nullptr) {
 #pragma unroll
@@ -329,28 +356,30 @@ __global__ void k_split_reduce(const float* __restrict__ part, int splits, int64
   out[i] = acc;
 }
 
-template <int TN_>
+template <int TN_, int MW = 1>
 cudaError_t launch_gemm_tn(const CUtensorMap& ta, const CUtensorMap& tb, void* C, int64_t M, int64_t N, int64_t K,
                            bool out_bf16, const float* bias, int act, int group, int splits, int sms,
                            cudaStream_t s) {
   const int KB = (int)((K + GK - 1) / GK);
   const int kbs = (KB + splits - 1) / splits;   // every slice has at least one K block
   splits = (KB + kbs - 1) / kbs;
-  const int64_t work = ((M + GM - 1) / GM) * ((N + TN_ - 1) / TN_) * splits;
+  const int64_t work = ((M + Tile<TN_, MW>::ROWS - 1) / Tile<TN_, MW>::ROWS) * ((N + TN_ - 1) / TN_) * splits;
   const unsigned grid = (unsigned)(work < sms ? work : sms);   // persistent: one CTA per SM
-  constexpr size_t smem = Tile<TN_>::SMEM;
+  constexpr size_t smem = Tile<TN_, MW>::SMEM;
   const ConvGeo none{0, 0, 0, 0};
   cudaError_t e;
   if (out_bf16) {
-    e = cudaFuncSetAttribute(k_gemm_bf16<true, TN_, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_gemm_bf16<true, TN_, false, MW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
     if (e != cudaSuccess) return e;
-    k_gemm_bf16<true, TN_, false><<<grid, GEMM_THREADS, smem, s>>>(ta, tb, C, bias, act, group, (int)M, (int)N,
-                                                                   (int)K, kbs, splits, nullptr, none);
+    k_gemm_bf16<true, TN_, false, MW><<<grid, GEMM_THREADS, smem, s>>>(ta, tb, C, bias, act, group, (int)M, (int)N,
+                                                                       (int)K, kbs, splits, nullptr, none);
   } else {
-    e = cudaFuncSetAttribute(k_gemm_bf16<false, TN_, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_gemm_bf16<false, TN_, false, MW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
     if (e != cudaSuccess) return e;
-    k_gemm_bf16<false, TN_, false><<<grid, GEMM_THREADS, smem, s>>>(ta, tb, C, bias, act, group, (int)M, (int)N,
-                                                                    (int)K, kbs, splits, nullptr, none);
+    k_gemm_bf16<false, TN_, false, MW><<<grid, GEMM_THREADS, smem, s>>>(ta, tb, C, bias, act, group, (int)M, (int)N,
+                                                                        (int)K, kbs, splits, nullptr, none);
   }
   return cudaGetLastError();
 }
@@ -366,6 +395,14 @@ int gemm_tile_width(int64_t M, int64_t N, int splits, int sms) {
   return 64;
 }
 
+// Wide 256 x 256 tiles for large products: no split K, a K long enough that the epilogue
+// (no longer overlapped) is a small part of a tile, at least one full wave of them, and no
+// GELU (its erfc epilogue, unoverlapped, cost more than the wide tiles gained: 0.77 vs
+// 0.73 ms for an 8192^3 dense layer).
+bool gemm_wide(int64_t M, int64_t N, int64_t K, int splits, int act, int sms) {
+  return splits == 1 && K >= 1024 && act != GWX_ACT_GELU && ((M + 255) / 256) * ((N + 255) / 256) >= sms;
+}
+
 cudaError_t launch_gemm(const void* A, const void* B, void* C, int64_t M, int64_t N, int64_t K, bool out_bf16,
                         const float* bias, int act, int group, int splits, cudaStream_t s) {
   if (group < 1) group = DEFAULT_GROUP;
@@ -373,8 +410,12 @@ cudaError_t launch_gemm(const void* A, const void* B, void* C, int64_t M, int64_
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  const int tn = gemm_tile_width(M, N, splits, sms);
   CUtensorMap ta, tb;
+  if (gemm_wide(M, N, K, splits, act, sms)) {
+    if (!make_map(&ta, A, M, K, 2 * GM) || !make_map(&tb, B, N, K, 256)) return cudaErrorInvalidValue;
+    return launch_gemm_tn<256, 2>(ta, tb, C, M, N, K, out_bf16, bias, act, group, splits, sms, s);
+  }
+  const int tn = gemm_tile_width(M, N, splits, sms);
   if (!make_map(&ta, A, M, K, GM) || !make_map(&tb, B, N, K, (uint32_t)tn)) return cudaErrorInvalidValue;
   if (tn == 64) return launch_gemm_tn<64>(ta, tb, C, M, N, K, out_bf16, bias, act, group, splits, sms, s);
   if (tn == 128) return launch_gemm_tn<128>(ta, tb, C, M, N, K, out_bf16, bias, act, group, splits, sms, s);

@@ -73,6 +73,54 @@ def test_gemm_large(gwx):
     assert np.all(np.abs(got - ref) <= tol)
 
 
+def _rows(M, seed, extra=12):
+    """Rows at and next to every 128-row boundary, the last row, and a few at random."""
+    b = [r for t in range(0, M, 128) for r in (t - 1, t, t + 1) if 0 <= r < M] + [M - 1]
+    return np.unique(np.concatenate([b, np.random.default_rng(seed).integers(0, M, extra)]))
+
+
+@pytest.mark.parametrize("out_dtype", [torch.float32, torch.bfloat16])
+def test_gemm_wide_tiles_ragged(gwx, out_dtype):
+    """Large products run on 256 x 256 tiles (two M 128 x N 256 products per CTA sharing
+    each B tile) once a full wave of them exists and K >= 1024; 4000 x 2600 gives 16 x 11
+    = 176 such tiles on a 152-SM GB300, with ragged rows (4000 = 15 x 256 + 160), columns
+    (2600 = 10 x 256 + 40) and K tail (1096 = 17 x 64 + 8).  Sampled rows at every 128-row
+    boundary, all columns."""
+    M, N, K = 4000, 2600, 1096
+    a = workloads.random_bf16_bits(140, (M, K))
+    b = workloads.random_bf16_bits(141, (N, K))
+    C = gwx.gemm_bf16(_bf16(a), _bf16(b), out_dtype=out_dtype)
+    gwx.device_status()
+    rows = _rows(M, 142)
+    got = C[torch.from_numpy(rows).cuda()].float().cpu().numpy().astype(np.float64)
+    ref = gemm.gemm_nt(a[rows], b)
+    tol = 2.0 * K * 2.0 ** -24 * gemm.abs_product_sum(a[rows], b)
+    if out_dtype == torch.bfloat16:
+        tol = tol * (1.0 + 2.0 ** -8) + 2.0 ** -8 * np.abs(ref)
+    err = np.abs(got - ref)
+    assert np.all(err <= tol + 1e-30), (float(err.max()), float((err / (tol + 1e-30)).max()))
+
+
+def test_dense_layer_wide_tiles(gwx):
+    """Y = ReLU(X W^T + b) with a bfloat16 output on the 256 x 256 tiles (4096 x 2560 x 1024:
+    16 x 10 tiles; GELU layers keep the 128 x 256 tiles): the fused epilogue on both
+    accumulator halves of a tile."""
+    M, N, K, act = 4096, 2560, 1024, 1
+    x = workloads.random_bf16_bits(150, (M, K))
+    w = workloads.random_bf16_bits(151, (N, K))
+    bias = np.random.default_rng(152).normal(0.0, 0.5, N).astype(np.float32)
+    Y = gwx.dense_bf16(_bf16(x), _bf16(w), torch.from_numpy(bias).cuda(), act=act, out_dtype=torch.bfloat16)
+    gwx.device_status()
+    rows = _rows(M, 153)
+    got = Y[torch.from_numpy(rows).cuda()].float().cpu().numpy().astype(np.float64)
+    ref = gemm.dense(x[rows], w, bias.astype(np.float64), act)
+    z = gemm.dense(x[rows], w, bias.astype(np.float64), 0)
+    tol_z = 2.0 * K * 2.0 ** -24 * gemm.abs_product_sum(x[rows], w) + 2.0 ** -23 * np.abs(z)
+    tol = tol_z * (1.0 + 2.0 ** -8) + 2.0 ** -8 * np.abs(ref)   # ReLU is 1-Lipschitz
+    err = np.abs(got - ref)
+    assert np.all(err <= tol + 1e-30), (float(err.max()), float((err / (tol + 1e-30)).max()))
+
+
 def test_gemm_rejects_bad_arguments(gwx):
     a = torch.zeros((16, 12), dtype=torch.bfloat16, device="cuda")
     with pytest.raises(gwx.GwxError):
