@@ -394,7 +394,11 @@ struct TmPlan {
   static constexpr int THREADS = TPR * G;
   static constexpr int RS = (LOGN % 4) ? (1 << (LOGN % 4)) : 16;      // radix of the last pass
   static constexpr int NMID = LOGN / 4 - ((LOGN % 4) ? 1 : 2);       // radix-16 middle passes
-  static constexpr bool PP = LOGN <= 11;     // two buffers per transform; in place above (shared memory)
+  // Two buffers per transform (one barrier per pass) only where in-place passes would not
+  // raise the blocks per SM: n <= 1024 in place fits three 256-thread blocks (80 registers,
+  // ~62 KB of shared memory each), n = 2048 two blocks either way, n >= 4096 only in place.
+  static constexpr bool PP = LOGN == 11;
+  static constexpr int MIN_BLOCKS = LOGN <= 10 ? 3 : (THREADS <= 256 ? 2 : 1);
   static constexpr int HQ = RS == 4 ? 1 : 0;  // Horner's rule (three steps) for one output of radix 4
   static constexpr size_t smem(int u) {
     return (size_t)n * sizeof(float4) + (size_t)G * (PP ? 2 : 1) * n * sizeof(float2) +
@@ -581,7 +585,7 @@ __device__ __forceinline__ void tm_last_pass(uint32_t src, int t, uint32_t row, 
 }
 
 template <int ND, int LOGN>
-__global__ void __launch_bounds__(TmPlan<LOGN>::THREADS, TmPlan<LOGN>::THREADS <= 256 ? 2 : 1)
+__global__ void __launch_bounds__(TmPlan<LOGN>::THREADS, TmPlan<LOGN>::MIN_BLOCKS)
 k_loglike_tmarg(const double* __restrict__ theta, SetupConsts kc, double fs, DetParams dp, double gmst, double tc_lo,
                 const float2* __restrict__ Y, const float* __restrict__ W, const int64_t* __restrict__ ev_off,
                 const double* __restrict__ yy_part, const float2* __restrict__ g_rows, int64_t E, int k_lo, int n_tc,
