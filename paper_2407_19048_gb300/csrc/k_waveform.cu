@@ -399,7 +399,7 @@ struct TmPlan {
   // ~62 KB of shared memory each), n = 2048 two blocks either way, n >= 4096 only in place.
   static constexpr bool PP = LOGN == 11;
   static constexpr int MIN_BLOCKS = LOGN <= 10 ? 3 : (THREADS <= 256 ? 2 : 1);
-  static constexpr int HQ = RS == 4 ? 1 : 0;  // Horner's rule (three steps) for one output of radix 4
+  static constexpr int HQ = RS == 4 ? 1 : 0;  // Horner's rule (three steps) when only output 0 of radix 4 is needed
   static constexpr size_t smem(int u) {
     return (size_t)n * sizeof(float4) + (size_t)G * (PP ? 2 : 1) * n * sizeof(float2) +
            (size_t)u * TM_ROW * sizeof(float2);
@@ -534,52 +534,71 @@ struct TmMid {
   }
 };
 
+// Folds a batch of K grid values into the running log-sum-exp (m, s) with one rescale;
+// values outside the window are -inf (they add nothing).
+template <int K>
+__device__ __forceinline__ void lse_add_batch(float& m, float& s, const float* v) {
+  float mb = v[0];
+#pragma unroll
+  for (int i = 1; i < K; ++i) mb = fmaxf(mb, v[i]);
+  const float M = fmaxf(m, mb);
+  if (M == -INFINITY) return;
+  float acc = s * __expf(m - M);
+#pragma unroll
+  for (int i = 0; i < K; ++i) acc += __expf(v[i] - M);
+  s = acc;
+  m = M;
+}
+
 // Last pass (radix RS, stride n/RS): the needed outputs of the butterflies t + i n/16
 // enter the running log-sum-exp (mx, sm); nq = the number of needed q.
 template <int LOGN>
 __device__ __forceinline__ void tm_last_pass(uint32_t src, int t, uint32_t row, int n_tc, int nq, float& mx, float& sm) {
   using PL = TmPlan<LOGN>;
   constexpr int n = 1 << LOGN, RS = PL::RS, NB = n / RS, T = n / 16;
+  const uint32_t arow = row + 8u * (uint32_t)TM_ROW_LAST;
+  if (nq <= PL::HQ) {
+    // one output (q = 0) per butterfly, by Horner's rule; the thread's 2 x 16/RS grid
+    // values enter the log-sum-exp together
+    float vals[2 * (16 / RS)];
+#pragma unroll
+    for (int i = 0; i < 16 / RS; ++i) {
+      const int j = t + i * T;
+      float2 v[RS];
+      load_strided16<RS, NB>(src, j, v);
+      const float2 b = cmul_rn(__ldg(g_tmlast + tmlast_offset(LOGN) + j), lds2(arow));   // e^{2 pi i (j + r/(2u))/n}
+      float2 acc = v[RS - 1];
+#pragma unroll
+      for (int l = RS - 2; l >= 0; --l)
+        acc = make_float2(fmaf(acc.x, b.x, fmaf(-acc.y, b.y, v[l].x)), fmaf(acc.x, b.y, fmaf(acc.y, b.x, v[l].y)));
+      vals[2 * i] = 2 * j < n_tc ? acc.x : -INFINITY;
+      vals[2 * i + 1] = 2 * j + 1 < n_tc ? acc.y : -INFINITY;
+    }
+    lse_add_batch<2 * (16 / RS)>(mx, sm, vals);
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < 16 / RS; ++i) {
     const int j = t + i * T;
     float2 v[RS];
     load_strided16<RS, NB>(src, j, v);
-    const uint32_t arow = row + 8u * (uint32_t)TM_ROW_LAST;
     const float2* tl = g_tmlast + tmlast_offset(LOGN) + j;
-    if (nq <= PL::HQ) {
-      const float2 b = cmul_rn(__ldg(tl), lds2(arow));   // e^{2 pi i (j + r/(2u))/n}
+    // twiddles (e^{2 pi i j/n} a)^l
+    float2 w[RS];
 #pragma unroll
-      for (int q = 0; q < PL::HQ; ++q) {
-        if (q < nq) {
-          const float2 gq = q ? cmul(b, unit16(q * (16 / RS))) : b;
-          float2 acc = v[RS - 1];
+    for (int k = 0; k < TM_NL; ++k) {
+      if (tm_l(k) < RS) w[tm_l(k)] = cmul_rn(__ldg(tl + k * NB), lds2(arow + 8u * (uint32_t)k));
+    }
+    tm_fill_powers<RS>(w);
 #pragma unroll
-          for (int l = RS - 2; l >= 0; --l)
-            acc = make_float2(fmaf(acc.x, gq.x, fmaf(-acc.y, gq.y, v[l].x)), fmaf(acc.x, gq.y, fmaf(acc.y, gq.x, v[l].y)));
-          const int mp = j + q * NB;
-          if (2 * mp < n_tc) lse_add(mx, sm, acc.x);
-          if (2 * mp + 1 < n_tc) lse_add(mx, sm, acc.y);
-        }
-      }
-    } else {
-      // twiddles (e^{2 pi i j/n} a)^l
-      float2 w[RS];
+    for (int l = 1; l < RS; ++l) v[l] = cmul(v[l], w[l]);
+    if constexpr (RS == 16) dft16<true>(v);
+    else dftR<RS, true, false>(v);
 #pragma unroll
-      for (int i = 0; i < TM_NL; ++i) {
-        if (tm_l(i) < RS) w[tm_l(i)] = cmul_rn(__ldg(tl + i * NB), lds2(arow + 8u * (uint32_t)i));
-      }
-      tm_fill_powers<RS>(w);
-#pragma unroll
-      for (int l = 1; l < RS; ++l) v[l] = cmul(v[l], w[l]);
-      if constexpr (RS == 16) dft16<true>(v);
-      else dftR<RS, true, false>(v);
-#pragma unroll
-      for (int q = 0; q < RS; ++q) {
-        const int mp = j + q * NB;
-        if (2 * mp < n_tc) lse_add(mx, sm, v[q].x);
-        if (2 * mp + 1 < n_tc) lse_add(mx, sm, v[q].y);
-      }
+    for (int q = 0; q < RS; ++q) {
+      const int mp = j + q * NB;
+      if (2 * mp < n_tc) lse_add(mx, sm, v[q].x);
+      if (2 * mp + 1 < n_tc) lse_add(mx, sm, v[q].y);
     }
   }
 }
