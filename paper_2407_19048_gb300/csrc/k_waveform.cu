@@ -406,15 +406,7 @@ struct TmPlan {
   }
 };
 
-// Running log-sum-exp state (max m, sum s of exp(v - m)).
-__device__ __forceinline__ void lse_add(float& m, float& s, float v) {
-  if (v > m) {
-    s = fmaf(s, __expf(m - v), 1.0f);
-    m = v;
-  } else {
-    s += __expf(v - m);
-  }
-}
+// Running log-sum-exp state (max m, sum s of exp(v - m)): merge of two states.
 __device__ __forceinline__ void lse_merge(float& m, float& s, float m2, float s2) {
   const float M = fmaxf(m, m2);
   if (M == -INFINITY) return;
@@ -594,12 +586,15 @@ __device__ __forceinline__ void tm_last_pass(uint32_t src, int t, uint32_t row, 
     for (int l = 1; l < RS; ++l) v[l] = cmul(v[l], w[l]);
     if constexpr (RS == 16) dft16<true>(v);
     else dftR<RS, true, false>(v);
+    // the butterfly's 2 RS grid values (those inside the window) in one update
+    float vals[2 * RS];
 #pragma unroll
     for (int q = 0; q < RS; ++q) {
       const int mp = j + q * NB;
-      if (2 * mp < n_tc) lse_add(mx, sm, v[q].x);
-      if (2 * mp + 1 < n_tc) lse_add(mx, sm, v[q].y);
+      vals[2 * q] = 2 * mp < n_tc ? v[q].x : -INFINITY;
+      vals[2 * q + 1] = 2 * mp + 1 < n_tc ? v[q].y : -INFINITY;
     }
+    lse_add_batch<2 * RS>(mx, sm, vals);
   }
 }
 
