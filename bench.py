@@ -656,12 +656,13 @@ def flow_resnet_leg(gwx, torch, rank, steps=1500, batch=512, events=64, pretrain
     return res
 
 
-def tmarg_leg(gwx, torch, events=64, lo=2000, hi=50000, reps=3):
+def tmarg_leg(gwx, torch, events=64, lo=2000, hi=50000, reps=3, oversample=None, n_tc=None):
     """The likelihood with the merger time integrated out (`gwx_log_likelihood_tmarg`)
     alone, on config 4's scale: `events` two-detector events of the non-spinning workload
     with U{lo..hi} prior samples each, the merger time integrated over the prior's window
     on a grid 16 times finer than the sampling interval (u = 16 inverse transforms of
-    n = N/2 = 1024 packed points per sample).  CUDA-event time per call, best of `reps`.
+    n = N/2 = 1024 packed points per sample; `oversample` and `n_tc` override u and the
+    window's length in samples).  CUDA-event time per call, best of `reps`.
     Roofline: the u transforms' 5 n log2 n flops per sample (the band products and the
     log-sum-exp not counted) against the FP32 peak."""
     import numpy as np
@@ -673,7 +674,9 @@ def tmarg_leg(gwx, torch, events=64, lo=2000, hi=50000, reps=3):
     offs = torch.from_numpy(np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)).cuda()
     S = int(counts.sum())
     theta, _ = gwx.sample_prior(wl["prior"], 5, 0, S, wl["L"], wl["N"])
-    tc_lo, n_tc, u = workloads.tc_grid(wl)
+    tc_lo, n_tc0, u0 = workloads.tc_grid(wl)
+    u = u0 if oversample is None else int(oversample)
+    n_tc = n_tc0 if n_tc is None else int(n_tc)
     out = torch.empty(S, dtype=torch.float64, device="cuda")
 
     def call():
@@ -1144,8 +1147,9 @@ def main(argv=None):
                     help="time only the device step (no end-to-end or log-likelihood leg); for profiling")
     ap.add_argument("--only-loglike", default=None, metavar="LO,HI",
                     help="run only the log-likelihood leg with U{LO..HI} samples per event; for profiling")
-    ap.add_argument("--only-tmarg", default=None, metavar="E,LO,HI",
-                    help="run only the merger-time-marginalised likelihood on E events of U{LO..HI} samples")
+    ap.add_argument("--only-tmarg", default=None, metavar="E,LO,HI[,U,NTC]",
+                    help="run only the merger-time-marginalised likelihood on E events of U{LO..HI} samples "
+                         "(optionally oversampling U and a window of NTC samples)")
     ap.add_argument("--only-gemm", default=None, metavar="M,N,K",
                     help="run only the bfloat16 product leg at this shape; for profiling")
     ap.add_argument("--only-flow-sample", default=None, metavar="E,S",
@@ -1216,9 +1220,11 @@ def main(argv=None):
     if args.only_tmarg:
         import torch
         import paper_2407_19048_gb300 as gwx
-        E, lo, hi = (int(v) for v in args.only_tmarg.split(","))
+        f = [int(v) for v in args.only_tmarg.split(",")]
         gwx.init()
-        print(json.dumps({"log_likelihood_tmarg": tmarg_leg(gwx, torch, E, lo, hi)}), flush=True)
+        print(json.dumps({"log_likelihood_tmarg": tmarg_leg(gwx, torch, f[0], f[1], f[2],
+                                                            oversample=f[3] if len(f) > 3 else None,
+                                                            n_tc=f[4] if len(f) > 4 else None)}), flush=True)
         return 0
     if args.only_loglike:
         import torch
