@@ -273,19 +273,25 @@ __global__ void __launch_bounds__(F_THREADS, 1)
       return __all_sync(0xffffffffu, got) && !*(volatile int*)&abort_flag;
     };
     // bias + ReLU of 64 accumulator columns (chunk c: two loads, one wait) into K-block c
-    // of the activation tile g; round rd of a hidden layer is chunk 2 rd + h
-    auto hidden = [&](uint32_t col0, const float* bias, int c) {
+    // of the activation tile g; round rd of a hidden layer is chunk 2 rd + h.  The chunk's
+    // biases bb (loaded by load_bias before the wait for its accumulator, so that their
+    // latency overlaps the products) are read from registers.
+    auto load_bias = [&](const float* bias, int c, float4* bb) {
+      const float4* b4 = reinterpret_cast<const float4*>(bias + 64 * c);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) bb[i] = __ldg(b4 + i);
+    };
+    auto hidden = [&](uint32_t col0, const float4* bb, int c) {
       uint32_t raw[2][32];
       tmem_ld32_async(lane_addr + col0 + 64u * c, raw[0]);
       tmem_ld32_async(lane_addr + col0 + 64u * c + 32u, raw[1]);
       tmem_wait_ld();
 #pragma unroll
       for (int hh = 0; hh < 2; ++hh) {
-        const float4* b4 = reinterpret_cast<const float4*>(bias + 64 * c + 32 * hh);
         uint32_t w[16];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          const float4 b = __ldg(b4 + i);
+          const float4 b = bb[8 * hh + i];
           w[2 * i] = pack2(fmaxf(__uint_as_float(raw[hh][4 * i]) + b.x, 0.f),
                            fmaxf(__uint_as_float(raw[hh][4 * i + 1]) + b.y, 0.f));
           w[2 * i + 1] = pack2(fmaxf(__uint_as_float(raw[hh][4 * i + 2]) + b.z, 0.f),
@@ -341,13 +347,17 @@ __global__ void __launch_bounds__(F_THREADS, 1)
         }
         arrive(&xready);
         for (int rd = 0; rd < NR && ok; ++rd) {
+          float4 bb[16];
+          load_bias(a.e1 + l * a.lstride, 2 * rd + h, bb);
           if (!(ok = wait_on(&acc1f[rd], li & 1u))) break;
-          hidden(0u, a.e1 + l * a.lstride, 2 * rd + h);
+          hidden(0u, bb, 2 * rd + h);
           arrive(&gready[rd]);
         }
         for (int rd = 0; rd < NR && ok; ++rd) {
+          float4 bb[16];
+          load_bias(a.e2 + l * a.lstride, 2 * rd + h, bb);
           if (!(ok = wait_on(&acc2f[rd], li & 1u))) break;
-          hidden(256u, a.e2 + l * a.lstride, 2 * rd + h);
+          hidden(256u, bb, 2 * rd + h);
           arrive(&gready[rd]);
         }
         if (!ok) break;
