@@ -54,7 +54,7 @@ __host__ __device__ constexpr int Bc(int p, int j) {
 template <int P>
 __device__ __forceinline__ void pack_half(const float* v, uint32_t& w0, uint32_t& w1);
 template <int P>
-__device__ __forceinline__ void couple(float* v, const float* o, const float* __restrict__ b3, float& ss);
+__device__ __forceinline__ void couple(float* v, const float* o, const float* b3, float& ss);
 
 __device__ int g_flow_status;
 
@@ -94,13 +94,14 @@ __device__ __forceinline__ void pack_half(const float* v, uint32_t& w0, uint32_t
   w1 = pack2(v[A(P, 2)], v[A(P, 3)]);
 }
 
-// v_b <- v_b e^s + mu with mu_j = o_j + b3_j, s_j = 3 tanh((o_{4+j} + b3_{4+j}) / 3)
+// v_b <- v_b e^s + mu with mu_j = o_j + b3_j, s_j = 3 tanh((o_{4+j} + b3_{4+j}) / 3);
+// b3: the layer's eight output biases, in registers
 template <int P>
-__device__ __forceinline__ void couple(float* v, const float* o, const float* __restrict__ b3, float& ss) {
+__device__ __forceinline__ void couple(float* v, const float* o, const float* b3, float& ss) {
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const float s = S_MAX * tanhf((o[4 + j] + __ldg(&b3[4 + j])) / S_MAX);
-    v[Bc(P, j)] = fmaf(v[Bc(P, j)], expf(s), o[j] + __ldg(&b3[j]));
+    const float s = S_MAX * tanhf((o[4 + j] + b3[4 + j]) / S_MAX);
+    v[Bc(P, j)] = fmaf(v[Bc(P, j)], expf(s), o[j] + b3[j]);
     ss += s;
   }
 }
@@ -362,10 +363,16 @@ __global__ void __launch_bounds__(F_THREADS, 1)
         }
         if (!ok) break;
         if (h != 0) continue;                                  // the coupling step is the first warp's
+        float b3[8];
+        {
+          const float4* b4 = reinterpret_cast<const float4*>(a.e3 + l * a.lstride);
+          const float4 lo4 = __ldg(b4), hi4 = __ldg(b4 + 1);
+          b3[0] = lo4.x; b3[1] = lo4.y; b3[2] = lo4.z; b3[3] = lo4.w;
+          b3[4] = hi4.x; b3[5] = hi4.y; b3[6] = hi4.z; b3[7] = hi4.w;
+        }
         if (!(ok = wait_on(&acc3f, li & 1u))) break;
         float o[16];
         tmem_ld16(lane_addr, o);
-        const float* b3 = a.e3 + l * a.lstride;
         switch (p) {
           case 0: couple<0>(v, o, b3, ss); break;
           case 1: couple<1>(v, o, b3, ss); break;
