@@ -609,8 +609,7 @@ def flow_resnet_leg(gwx, torch, rank, steps=1500, batch=512, events=64, pretrain
 
     def arm(pretrain):
         sim = gwx.simulator.Simulator(wl, pipeline=True, background_every=16)
-        # learning rate 6e-4: after 1500 steps a loss of 7.57 against 7.70 at 3e-4; 1e-3 diverged
-        fp = FlowPosterior(wl, layers=16, hidden=256, context=64, seed=0, lr=6e-4, weight_decay=2e-3,
+        fp = FlowPosterior(wl, layers=16, hidden=256, context=64, seed=0, lr=3e-4, weight_decay=2e-3,
                            embedding="resnet")
         out = {}
         if pretrain:
