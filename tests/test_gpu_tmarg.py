@@ -79,6 +79,7 @@ CASES = [
     ("hl3", 4, 256, 2.2),        # three detectors, N = 8192 (last radix 16, one output each)
     ("hl3", 2, 6000, 0.4),       # N = 8192, twelve of sixteen outputs (full last butterflies)
     ("sweep", 2, 64, 4.5),       # N = 16384 (one transform per block, in place)
+    ("sweep", 64, 40, 4.5),      # N = 16384 at the largest oversampling (the most shared memory)
     (("small", 128, 2.0), 8, 64, 1.0),     # N = 256 (last radix 8, two outputs each)
     (("small", 256, 2.0), 4, 100, 0.97),   # N = 512 (last radix 16, four outputs each)
     (("small", 512, 2.0), 2, 129, 1.0),    # N = 1024 (last radix 2)
