@@ -1147,6 +1147,9 @@ def main(argv=None):
                     help="time only the device step (no end-to-end or log-likelihood leg); for profiling")
     ap.add_argument("--only-loglike", default=None, metavar="LO,HI",
                     help="run only the log-likelihood leg with U{LO..HI} samples per event; for profiling")
+    ap.add_argument("--only-chain", default=None, metavar="E,LO,HI",
+                    help="time config 4's importance-sampling chains alone (prior and an untrained flow) on E "
+                         "events of U{LO..HI} draws")
     ap.add_argument("--only-tmarg", default=None, metavar="E,LO,HI[,U,NTC]",
                     help="run only the merger-time-marginalised likelihood on E events of U{LO..HI} samples "
                          "(optionally oversampling U and a window of NTC samples)")
@@ -1195,6 +1198,25 @@ def main(argv=None):
         ev1.record()
         torch.cuda.synchronize()
         print(json.dumps({"flow_sample": {"events": E, "draws": E * S, "ms": ev0.elapsed_time(ev1) / 5}}), flush=True)
+        return 0
+    if args.only_chain:
+        import torch
+        import paper_2407_19048_gb300 as gwx
+        import paper_2407_19048_gb300.simulator  # noqa: F401
+        from paper_2407_19048_gb300.flow import FlowPosterior
+        gwx.init()
+        E, lo, hi = (int(v) for v in args.only_chain.split(","))
+        # config 4's events and the benchmark flow's shape, untrained: the same kernels and
+        # amounts of work as the trained flow's chain (its ESS figures mean nothing)
+        wl_ev = dict(workloads.workload("small_nonspinning", B=E), param_seed=777)
+        sim_ev = gwx.simulator.Simulator(wl_ev)
+        y_ev, _, _ = sim_ev.step(step_counter(0, 0))
+        fp = FlowPosterior(workloads.workload("small_nonspinning", B=4096), layers=16, hidden=256, context=64,
+                           embed_hidden=512, group=4, seed=0)
+        isamp = is_compare(gwx, torch, fp, wl_ev, y_ev.clone(), sim_ev.psd, workloads.ragged_counts(4, E, lo, hi),
+                           workloads.tc_grid(wl_ev))
+        print(json.dumps({"chain_ms": {a: isamp[a]["chain_ms"] for a in ("prior", "flow")},
+                          "samples": isamp["samples"], "events": E, "flow": "untrained"}), flush=True)
         return 0
     if args.only_flow:
         import torch
