@@ -302,15 +302,18 @@ cudaError_t launch_loglike_full(const float* ydata, const float2* Ydata, const f
 // inputs by (a^{n/16})^q.  Passes: radix 16 (the first, reading the tables), radix-16
 // middle passes, and a last pass of radix RS = 2^(log2 n mod 4) (16 when that is 0).
 // Its output q of butterfly j holds the grid values 2 (j + q n/RS) and that + 1, so only
-// the q with 2 q n/RS < n_tc are needed; when few are, each is evaluated alone by
-// Horner's rule in e^{2 pi i (j + r/(2u))/n} e^{2 pi i q/RS}, otherwise the butterfly runs
-// in full.
+// the q with 2 q n/RS < n_tc are needed; when that is q = 0 alone and RS = 4 (n = 1024
+// with the window at most a quarter of N: the two-detector workload), the output is
+// evaluated by Horner's rule in e^{2 pi i (j + r/(2u))/n}, otherwise the butterfly runs in
+// full.
 //
 // A block takes 32 consecutive samples: its first warp does their FP64 set-up (one lane
 // per sample); per sample all threads build P and Q in shared memory, then G groups of
 // n/16 threads (16 values each) run the u transforms G at a time, each group on its own
-// barrier; the last pass folds its outputs into a per-thread running maximum and sum of
-// exponentials, and one block reduction per sample gives ln L_m.
+// barrier (in-place passes where that fits more blocks on an SM, two buffers otherwise).
+// The last pass folds each thread's grid values of a round into its running maximum and
+// sum of exponentials at once; per sample the warps reduce theirs, and one warp finishes
+// all 32 samples (warp partials merged, norms added) at the end of the block.
 constexpr int TM_SAMPLES = 32;
 
 // Twiddle powers l of a pass are products of two rounded factors at most: the powers
@@ -425,14 +428,6 @@ __device__ __forceinline__ void tm_group_sync(int g) {
   } else {
     __syncwarp(((1u << TPR) - 1u) << ((threadIdx.x & 31) & ~(TPR - 1)));
   }
-}
-
-// e^{2 pi i q/16}, q < 16 constant (nearest floats to the cosines of multiples of pi/8).
-__device__ __forceinline__ float2 unit16(int q) {
-  constexpr float c1 = 0.92387950420379638671875f, s1 = 0.3826834261417388916015625f;
-  constexpr float h = 0.707106769084930419921875f;
-  constexpr float cs[16] = {1.f, c1, h, s1, 0.f, -s1, -h, -c1, -1.f, -c1, -h, -s1, 0.f, s1, h, c1};
-  return make_float2(cs[q & 15], cs[(q + 12) & 15]);   // sin x = cos(x - pi/2)
 }
 
 // w[4a + b] = w[4a] w[b] for b = 1 .. 3 and 4a < R, from the powers tm_l(i) < R.
