@@ -633,17 +633,41 @@ def flow_resnet_leg(gwx, torch, rank, steps=1500, batch=512, events=64, pretrain
         y, th, _ = sim.step(step_counter(rank, 90000))
         fp.train_step(y, th, update=False)
         torch.cuda.synchronize()
+        # the first `eager` steps issued call by call, the rest as CUDA-graph replays (one
+        # graph per simulator buffer set, captured on first use; the replay timing starts
+        # after the captures)
+        eager = min(20, steps)
+        timed = eager + 4
+        graphs, losses = {}, []
         t0 = time.perf_counter()
-        losses = []
         for i in range(steps):
+            if i == eager:
+                torch.cuda.synchronize()
+                t_eager = time.perf_counter() - t0
+            if i == timed:
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
             y, th, _ = sim.step(step_counter(rank, 90001 + i))
-            loss = fp.train_step(y, th)
+            if i < eager:
+                loss = fp.train_step(y, th)
+            else:
+                g = graphs.get(y.data_ptr())
+                if g is None:
+                    g = graphs[y.data_ptr()] = fp.capture_train_step(y, th)
+                g.replay()
+                fp.note_replay()
+                loss = fp._loss
             if i % max(1, steps // 8) == 0 or i == steps - 1:
                 losses.append((i, loss.clone()))
         torch.cuda.synchronize()
-        train_s = time.perf_counter() - t0
-        del sim
-        out.update({"train_steps": steps, "batch": batch, "train_s": train_s, "step_ms": 1e3 * train_s / steps,
+        t2 = time.perf_counter()
+        train_s = t2 - t0
+        step_eager = 1e3 * t_eager / eager if steps > eager else None
+        step_graph = 1e3 * (t2 - t1) / (steps - timed) if steps > timed else None
+        ncap = len(graphs)
+        del sim, graphs
+        out.update({"train_steps": steps, "batch": batch, "train_s": train_s, "step_ms": step_graph,
+                    "step_ms_eager": step_eager, "graph_captures": ncap,
                     "loss": [(i, float(l.item())) for i, l in losses],
                     "importance_sampling": is_compare(gwx, torch, fp, wl_ev, y_ev, psd_ev, counts,
                                                       workloads.tc_grid(wl_ev))})

@@ -470,6 +470,11 @@ int gwx_gauss_nll(const float* out, int ldo, const float* targets, int P, int64_
                   double* loss_mean, float* grad, void* stream);
 int gwx_adamw(float* param, const float* grad, float* m, float* v, int64_t n, double lr, double beta1,
               double beta2, double eps, double weight_decay, int64_t step, void* param_bf16, void* stream);
+/* gwx_adamw_at: gwx_adamw with the step number read on the device from *step (a device
+ *   int64, not modified; counts from 1): a CUDA graph that advances one step counter can
+ *   replay the updates of many tensors.  step 8-byte aligned. */
+int gwx_adamw_at(float* param, const float* grad, float* m, float* v, int64_t n, double lr, double beta1,
+                 double beta2, double eps, double weight_decay, const int64_t* step, void* param_bf16, void* stream);
 /* gwx_adamw_clip: gwx_adamw on the gradients scaled by min(1, clip / |g|), |g| the
  *   Euclidean norm of all n gradients (summed in FP64); grad itself is not modified.
  *   Workspace gwx_adamw_clip_workspace() bytes. */

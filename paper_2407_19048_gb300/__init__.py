@@ -26,7 +26,7 @@ __all__ = ["GwxError", "version", "init", "detector_geometry", "sample_prior", "
            "colored_noise", "welch_psd", "inject", "inject_padded", "simulate_batch_padded", "whiten", "unwhiten", "simulate_batch", "simulate_shape", "log_likelihood", "log_likelihood_tmarg",
            "importance_weights", "gemm_bf16", "dense_bf16", "dense_bf16_backward", "gemm_autotune", "spectral_features",
            "cross_features", "lag_features", "proposal_targets",
-           "gauss_nll", "adamw", "adamw_clip", "skymap", "vicreg", "retime", "sample_proposal", "device_status", "selftest_bounded_wait", "rfft", "irfft",
+           "gauss_nll", "adamw", "adamw_at", "adamw_clip", "skymap", "vicreg", "retime", "sample_proposal", "device_status", "selftest_bounded_wait", "rfft", "irfft",
            "workspace_bytes", "debug_check", "conv1d_bf16", "conv1d_bf16_backward", "TAYLORF2", "IMRPHENOMD", "DETECTORS"]
 
 
@@ -547,6 +547,15 @@ def adamw(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, weight_
     """One AdamW step in place on float32 param, m, v (step counts from 1)."""
     _check(_lib.load().gwx_adamw(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(), lr, beta1, beta2, eps,
                                  weight_decay, step, _ptr(param_bf16), _stream()))
+
+
+def adamw_at(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, param_bf16=None):
+    """adamw with the step number read on the device from step (an int64 device tensor of one
+    element, not modified), so that a CUDA graph can replay it."""
+    torch = _torch()
+    _dev(step, torch.int64, "step")
+    _check(_lib.load().gwx_adamw_at(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(), lr, beta1, beta2, eps,
+                                    weight_decay, _ptr(step), _ptr(param_bf16), _stream()))
 
 
 def adamw_clip(param, grad, m, v, step, lr, clip, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0,

@@ -99,6 +99,7 @@ SIGNATURES = {
     "gwx_proposal_targets": (c_int, [c_vp, c_i64, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl), c_vp, c_vp]),
     "gwx_gauss_nll": (c_int, [c_vp, c_int, c_vp, c_int, c_i64, c_vp, c_vp, c_vp, c_vp]),
     "gwx_adamw": (c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl, c_i64, c_vp, c_vp]),
+    "gwx_adamw_at": (c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl, c_vp, c_vp, c_vp]),
     "gwx_adamw_clip_workspace": (c_size, []),
     "gwx_adamw_clip": (c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl, c_i64, c_dbl, c_vp,
                                c_vp, c_size, c_vp]),

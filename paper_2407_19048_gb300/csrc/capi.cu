@@ -940,6 +940,20 @@ int gwx_adamw(float* param, const float* grad, float* m, float* v, int64_t n, do
                   "adamw");
 }
 
+int gwx_adamw_at(float* param, const float* grad, float* m, float* v, int64_t n, double lr, double beta1, double beta2,
+                 double eps, double weight_decay, const int64_t* step, void* param_bf16, void* stream) {
+  if (n < 0) return fail(GWX_ESHAPE, "n=%lld", (long long)n);
+  if (!(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0) || !(lr >= 0.0))
+    return fail(GWX_EINVAL, "AdamW hyper-parameters");
+  if (n == 0) return GWX_OK;
+  if (!param || !grad || !m || !v || !step) return fail(GWX_EINVAL, "NULL array or step");
+  GWX_ALIGN8(step);
+  GWX_TRY(ensure_init());
+  return launched(launch_adamw_at(param, grad, m, v, n, lr, beta1, beta2, eps, weight_decay, step, param_bf16,
+                                  as_stream(stream)),
+                  "adamw_at");
+}
+
 int gwx_vicreg(const float* x, const float* xp, int64_t B, int d, double lambda1, double lambda2, double lambda3,
                double* loss, double* terms, float* grad_x, float* grad_xp, void* stream) {
   if (B < 2 || B > 0x7fffffffLL || !vicreg_supported((int)B, d))

@@ -151,6 +151,9 @@ cudaError_t launch_gauss_nll(const float* out, int ldo, const float* t, int P, i
                              float* grad, cudaStream_t s);
 cudaError_t launch_adamw(float* p, const float* g, float* m, float* v, int64_t n, double lr, double b1, double b2,
                          double eps, double wd, int64_t step, void* p16, cudaStream_t s);
+// launch_adamw with the step number *step read on the device (a CUDA-graph step counter).
+cudaError_t launch_adamw_at(float* p, const float* g, float* m, float* v, int64_t n, double lr, double b1, double b2,
+                            double eps, double wd, const int64_t* step, void* p16, cudaStream_t s);
 // AdamW on gradients scaled by min(1, clip / |g|) (|g| the FP64 norm of all n gradients);
 // workspace adamw_clip_ws() bytes.
 size_t adamw_clip_ws();

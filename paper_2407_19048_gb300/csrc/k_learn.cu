@@ -158,6 +158,32 @@ __global__ void k_adamw(float* __restrict__ p, const float* __restrict__ g, floa
   if (p16) p16[i] = __float2bfloat16_rn(pi);
 }
 
+// k_adamw with the step number read from the device (the counter a captured training step
+// advances before its updates): each block's first thread forms the bias corrections in
+// FP64, as the host does for k_adamw.
+__global__ void k_adamw_at(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                           float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float wd,
+                           double b1d, double b2d, const int64_t* __restrict__ step, __nv_bfloat16* __restrict__ p16) {
+  __shared__ float cs[2];
+  if (threadIdx.x == 0) {
+    const double k = (double)*step;
+    cs[0] = (float)(1.0 - pow(b1d, k));
+    cs[1] = (float)(1.0 - pow(b2d, k));
+  }
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float c1 = cs[0], c2 = cs[1];
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  const float pi = p[i] - lr * ((mi / c1) / (sqrtf(vi / c2) + eps) + wd * p[i]);
+  p[i] = pi;
+  if (p16) p16[i] = __float2bfloat16_rn(pi);
+}
+
 // Gradient-norm clipping: per-block partial sums of g^2 (FP64), then one block turns
 // them into the factor min(1, clip / |g|) that k_adamw_scaled applies to every gradient.
 constexpr int CLIP_BLOCKS = 256;
@@ -376,6 +402,13 @@ cudaError_t launch_adamw(float* p, const float* g, float* m, float* v, int64_t n
   const float c1 = (float)(1.0 - pow(b1, (double)step)), c2 = (float)(1.0 - pow(b2, (double)step));
   k_adamw<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, g, m, v, n, (float)lr, (float)b1, (float)b2, (float)eps,
                                                       (float)wd, c1, c2, reinterpret_cast<__nv_bfloat16*>(p16));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adamw_at(float* p, const float* g, float* m, float* v, int64_t n, double lr, double b1, double b2,
+                            double eps, double wd, const int64_t* step, void* p16, cudaStream_t s) {
+  k_adamw_at<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, g, m, v, n, (float)lr, (float)b1, (float)b2, (float)eps,
+                                                         (float)wd, b1, b2, step, reinterpret_cast<__nv_bfloat16*>(p16));
   return cudaGetLastError();
 }
 

@@ -149,8 +149,6 @@ class FlowPosterior:
         import ctypes
         import torch
         gwx = self.gwx
-        if self.resnet is not None:
-            raise NotImplementedError("graph capture covers the built-in summary only")
         if getattr(self, "step_dev", None) is None:
             self.step_dev = torch.tensor([self.steps], dtype=torch.int64, device=self.dev)
         else:
@@ -162,9 +160,22 @@ class FlowPosterior:
         graph = torch.cuda.CUDAGraph()
         torch.cuda.synchronize()
         with torch.cuda.graph(graph):
+            ctx = d_ctx = None
+            if self.resnet is not None:
+                # the ResNet-1D summary: forward, the flow's step (which advances the step
+                # counter), backward, and AdamW on every summary tensor at that step
+                ctx = self.resnet.forward(y, out_dtype=torch.bfloat16)
+                d_ctx = torch.empty(ctx.shape, dtype=torch.float32, device=self.dev)
             gwx.flow_train_step(self.shape, self.params, self.params16, self.grads, self.m, self.v, 1, self.lr,
                                 self.mean, self.scale, y, theta, self.fs, self.f_lo, weight_decay=self.wd,
-                                clip=self.clip, loss_mean=self._loss, workspace=ws, step_counter=self.step_dev)
+                                clip=self.clip, loss_mean=self._loss, workspace=ws, step_counter=self.step_dev,
+                                ctx=ctx, d_ctx=d_ctx)
+            if self.resnet is not None:
+                G = self.resnet.backward(d_ctx)
+                for name, p, p16 in self.resnet.tensors():
+                    mm, vv = self.rmom[name]
+                    gwx.adamw_at(p, G[name].contiguous(), mm, vv, self.step_dev, self.lr, weight_decay=self.wd,
+                                 param_bf16=p16)
         return graph
 
     def note_replay(self):

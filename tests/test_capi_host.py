@@ -157,6 +157,19 @@ def test_resnet_and_dense_validation(lib):
     assert small < long_batch
 
 
+def test_adamw_at_validation(lib):
+    """The device-step AdamW rejects a missing step counter and bad hyper-parameters before
+    any launch, and n = 0 is a no-op."""
+    dummy = 16   # never dereferenced: the checks come first
+    st = lib.gwx_adamw_at(dummy, dummy, dummy, dummy, 10, 1e-3, 0.9, 0.999, 1e-8, 0.0, None, None, None)
+    assert st == -1 and b"step" in lib.gwx_last_error()
+    st = lib.gwx_adamw_at(dummy, dummy, dummy, dummy, 10, 1e-3, 1.0, 0.999, 1e-8, 0.0, dummy, None, None)
+    assert st == -1 and b"hyper-parameters" in lib.gwx_last_error()
+    st = lib.gwx_adamw_at(dummy, dummy, dummy, dummy, -1, 1e-3, 0.9, 0.999, 1e-8, 0.0, dummy, None, None)
+    assert st == -2
+    assert lib.gwx_adamw_at(None, None, None, None, 0, 1e-3, 0.9, 0.999, 1e-8, 0.0, None, None, None) == 0
+
+
 def test_conv1d_validation(lib):
     """The implicit-GEMM convolutions take whole 128-time tiles and 64-channel blocks; other
     shapes, even kernels, missing arrays and short workspaces fail before any launch."""

@@ -422,6 +422,38 @@ def test_captured_training_step_replays_like_eager_steps(gwx):
     assert torch.allclose(a.m, b.m, rtol=1e-5, atol=1e-9)
 
 
+def test_captured_resnet_training_step_replays_like_eager_steps(gwx):
+    """The same with the ResNet-1D summary inside the graph: its forward, the flow's step
+    (which advances the device step counter), its backward and AdamW on every summary
+    tensor at that step (gwx_adamw_at).  64-window batches of the two-detector workload;
+    the stride-1 convolutions of the 64-channel stage run as implicit GEMMs."""
+    from paper_2407_19048_gb300.flow import FlowPosterior
+    from paper_2407_19048_gb300.simulator import Simulator
+    wl = dict(WL, B=64)
+    kw = dict(layers=2, hidden=64, context=16, embed_hidden=32, group=GROUP, embedding="resnet",
+              resnet_stages=((64, 1, 1), (128, 1, 2)))
+    sim = Simulator(wl)
+    a = FlowPosterior(wl, seed=7, **kw)
+    b = FlowPosterior(wl, seed=7, **kw)
+    y0, th0, _ = sim.step(0)
+    yb, thb = y0.clone(), th0.clone()
+    graph = b.capture_train_step(yb, thb)
+    for step in range(4):
+        y, th, _ = sim.step(step)
+        a.train_step(y, th)
+        yb.copy_(y)
+        thb.copy_(th)
+        graph.replay()
+        b.note_replay()
+    torch.cuda.synchronize()
+    assert int(b.step_dev.item()) == 4 and b.steps == 4
+    assert torch.allclose(a.params, b.params, rtol=1e-5, atol=1e-7)
+    for (name, pa, _), (_, pb, _) in zip(a.resnet.tensors(), b.resnet.tensors()):
+        assert torch.allclose(pa, pb, rtol=1e-5, atol=1e-7), name
+        assert torch.allclose(a.rmom[name][0], b.rmom[name][0], rtol=1e-5, atol=1e-9), name
+    assert gwx._lib.load().gwx_device_status() == 0
+
+
 def test_external_context_matches_oracle_and_resnet_summary_trains(gwx, model):
     """The flow with the caller's context (the ResNet-1D path) against the oracle's flow
     with that context, and a short training run of flow + ResNet-1D summary."""
