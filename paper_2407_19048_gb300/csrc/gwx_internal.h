@@ -129,7 +129,8 @@ cudaError_t gemm_status(int* status);
 size_t dense_backward_ws(int64_t M, int64_t N, int64_t K);
 cudaError_t launch_dense_backward(const void* X, const void* W, const float* bias, const float* dY, int64_t M,
                                   int64_t N, int64_t K, int act, float* dX, float* dW, float* db, void* ws, int group,
-                                  cudaStream_t s);
+                                  cudaStream_t s,
+                                  const void* Y = nullptr);
 
 // Learned proposal (k_learn.cu).
 cudaError_t launch_features(const float* y, int64_t B, int D, int64_t N, int k_lo, int G, int F_pad, void* ws,

@@ -28,10 +28,13 @@ __device__ __forceinline__ float act_grad(float z, int act) {
 
 // One 32 x 32 tile per block (32 x 8 threads): dz = dY act'(Z) in FP32; dZ and dZ^T in
 // bfloat16 (round to nearest even); the tile's column sums of the FP32 dz into
-// part[blockIdx.y][n].
-__global__ void __launch_bounds__(256) k_act_backward(const float* __restrict__ Z, const float* __restrict__ dY,
-                                                      int act, int M, int N, __nv_bfloat16* __restrict__ dZ,
-                                                      __nv_bfloat16* __restrict__ dZt, float* __restrict__ part) {
+// part[blockIdx.y][n].  With Y (the layer's bfloat16 output, ReLU only) the mask is Y > 0,
+// which is Z > 0 (a positive float never rounds to a bfloat16 zero short of 1e-40), and Z
+// is not read.
+__global__ void __launch_bounds__(256) k_act_backward(const float* __restrict__ Z, const __nv_bfloat16* __restrict__ Y,
+                                                      const float* __restrict__ dY, int act, int M, int N,
+                                                      __nv_bfloat16* __restrict__ dZ, __nv_bfloat16* __restrict__ dZt,
+                                                      float* __restrict__ part) {
   __shared__ float tile[TT][TT + 1];
   const int n0 = blockIdx.x * TT, m0 = blockIdx.y * TT;
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -42,7 +45,8 @@ __global__ void __launch_bounds__(256) k_act_backward(const float* __restrict__ 
     if (m < M && n < N) {
       const int64_t at = (int64_t)m * N + n;
       v = __ldg(&dY[at]);
-      if (act != GWX_ACT_NONE) v *= act_grad(__ldg(&Z[at]), act);
+      if (Y != nullptr) v = __bfloat162float(Y[at]) > 0.f ? v : 0.f;
+      else if (act != GWX_ACT_NONE) v *= act_grad(__ldg(&Z[at]), act);
       dZ[at] = __float2bfloat16_rn(v);
     }
     tile[ty + i][tx] = v;
@@ -130,7 +134,7 @@ size_t dense_backward_ws(int64_t M, int64_t N, int64_t K) {
 
 cudaError_t launch_dense_backward(const void* X, const void* W, const float* bias, const float* dY, int64_t M,
                                   int64_t N, int64_t K, int act, float* dX, float* dW, float* db, void* ws, int group,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, const void* Y) {
   char* w = reinterpret_cast<char*>(ws);
   float* Z = reinterpret_cast<float*>(w);
   w += align256((size_t)M * N * 4);
@@ -149,14 +153,16 @@ cudaError_t launch_dense_backward(const void* X, const void* W, const float* bia
   w += align256((size_t)CS_MAX_SLICES * N * 8);
   float* kpart = reinterpret_cast<float*>(w);
   cudaError_t e = cudaSuccess;
-  // pre-activation Z = X W^T + b (only the activation derivative needs it)
-  if (act != GWX_ACT_NONE) {
+  // pre-activation Z = X W^T + b (only the activation derivative needs it, and a ReLU
+  // layer whose output Y is given takes its mask from Y instead)
+  const __nv_bfloat16* Y16 = act == GWX_ACT_RELU ? reinterpret_cast<const __nv_bfloat16*>(Y) : nullptr;
+  if (act != GWX_ACT_NONE && Y16 == nullptr) {
     e = launch_gemm_bf16(X, W, Z, M, N, K, false, bias, GWX_ACT_NONE, group, s);
     if (e != cudaSuccess) return e;
   }
   const dim3 tb(TT, 8);
-  k_act_backward<<<dim3((unsigned)((N + TT - 1) / TT), (unsigned)P), tb, 0, s>>>(Z, dY, act, (int)M, (int)N, dZ, dZt,
-                                                                                 part);
+  k_act_backward<<<dim3((unsigned)((N + TT - 1) / TT), (unsigned)P), tb, 0, s>>>(Z, Y16, dY, act, (int)M, (int)N, dZ,
+                                                                                 dZt, part);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_transpose_bf16<<<dim3((unsigned)((K + TT - 1) / TT), (unsigned)((M + TT - 1) / TT)), tb, 0, s>>>(
       reinterpret_cast<const __nv_bfloat16*>(X), (int)M, (int)K, Xt);

@@ -572,10 +572,11 @@ cudaError_t flow_train_step(const gwx_flow_shape& sh, float* params, void* param
     FL_TRY(launch_flow_coupling_backward(l, w.xs + l * rows8, w.o + l * rows8, G, B, 1.f / (float)B, w.d_o, Gu, s));
     FL_TRY(launch_dense_backward(g2, P.W(t + 4), P.b(t + 5), w.d_o, B, 8, d.H, GWX_ACT_NONE, w.dA,
                                  grads + P.off[t + 4], grads + P.off[t + 5], w.dws, 0, s));
+    // the ReLU layers' masks from their stored outputs (g2, g1)
     FL_TRY(launch_dense_backward(g1, P.W(t + 2), P.b(t + 3), w.dA, B, d.H, d.H, GWX_ACT_RELU, w.dB,
-                                 grads + P.off[t + 2], grads + P.off[t + 3], w.dws, 0, s));
+                                 grads + P.off[t + 2], grads + P.off[t + 3], w.dws, 0, s, g2));
     FL_TRY(launch_dense_backward(X, P.W(t), P.b(t + 1), w.dB, B, d.H, 8 + d.C, GWX_ACT_RELU, w.dA,
-                                 grads + P.off[t], grads + P.off[t + 1], w.dws, 0, s));
+                                 grads + P.off[t], grads + P.off[t + 1], w.dws, 0, s, g1));
     FL_TRY(launch_flow_input_backward(l, w.dA, (int)d.C, B, Gu, w.dctx, l == 0, s));
     std::swap(G, Gu);
   }
@@ -585,9 +586,9 @@ cudaError_t flow_train_step(const gwx_flow_shape& sh, float* params, void* param
     FL_TRY(launch_dense_backward(w.h2, P.W(4), P.b(5), w.dctx, B, d.C, d.He, GWX_ACT_NONE, w.dA, grads + P.off[4],
                                  grads + P.off[5], w.dws, 0, s));
     FL_TRY(launch_dense_backward(w.h1, P.W(2), P.b(3), w.dA, B, d.He, d.He, GWX_ACT_RELU, w.dB, grads + P.off[2],
-                                 grads + P.off[3], w.dws, 0, s));
+                                 grads + P.off[3], w.dws, 0, s, w.h2));
     FL_TRY(launch_dense_backward(w.feat, P.W(0), P.b(1), w.dB, B, d.He, d.F, GWX_ACT_RELU, nullptr,
-                                 grads + P.off[0], grads + P.off[1], w.dws, 0, s));
+                                 grads + P.off[0], grads + P.off[1], w.dws, 0, s, w.h1));
   }
   if (step >= 1) {
     if (step_counter)
