@@ -65,22 +65,29 @@ __global__ void __launch_bounds__(256) k_act_backward(const float* __restrict__ 
   }
 }
 
-// out[c][r] = in[r][c] for a bfloat16 [R][C] matrix.
-__global__ void __launch_bounds__(256) k_transpose_bf16(const __nv_bfloat16* __restrict__ in, int R, int C,
-                                                        __nv_bfloat16* __restrict__ out) {
-  __shared__ __nv_bfloat16 tile[TT][TT + 2];
+// out[c][r] = in[r][c] for bfloat16 [R][C] matrices, two in one launch (blockIdx.z picks
+// the matrix; a block past its matrix's extent returns at once, before any barrier).
+struct Transpose {
+  const __nv_bfloat16* in;
+  int R, C;
+  __nv_bfloat16* out;
+};
+__global__ void __launch_bounds__(256) k_transpose2_bf16(Transpose a, Transpose b) {
+  const Transpose p = blockIdx.z ? b : a;
   const int c0 = blockIdx.x * TT, r0 = blockIdx.y * TT;
+  if (c0 >= p.C || r0 >= p.R) return;
+  __shared__ __nv_bfloat16 tile[TT][TT + 2];
   const int tx = threadIdx.x, ty = threadIdx.y;
 #pragma unroll
   for (int i = 0; i < TT; i += 8) {
     const int r = r0 + ty + i, c = c0 + tx;
-    if (r < R && c < C) tile[ty + i][tx] = in[(int64_t)r * C + c];
+    if (r < p.R && c < p.C) tile[ty + i][tx] = p.in[(int64_t)r * p.C + c];
   }
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < TT; i += 8) {
     const int c = c0 + ty + i, r = r0 + tx;
-    if (c < C && r < R) out[(int64_t)c * R + r] = tile[tx][ty + i];
+    if (c < p.C && r < p.R) p.out[(int64_t)c * p.R + r] = tile[tx][ty + i];
   }
 }
 
@@ -164,12 +171,19 @@ cudaError_t launch_dense_backward(const void* X, const void* W, const float* bia
   k_act_backward<<<dim3((unsigned)((N + TT - 1) / TT), (unsigned)P), tb, 0, s>>>(Z, Y16, dY, act, (int)M, (int)N, dZ,
                                                                                  dZt, part);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_transpose_bf16<<<dim3((unsigned)((K + TT - 1) / TT), (unsigned)((M + TT - 1) / TT)), tb, 0, s>>>(
-      reinterpret_cast<const __nv_bfloat16*>(X), (int)M, (int)K, Xt);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_transpose_bf16<<<dim3((unsigned)((K + TT - 1) / TT), (unsigned)((N + TT - 1) / TT)), tb, 0, s>>>(
-      reinterpret_cast<const __nv_bfloat16*>(W), (int)N, (int)K, Wt);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // X^T (for dW) and W^T (for dX), only those needed, in one launch
+  {
+    const Transpose tx{reinterpret_cast<const __nv_bfloat16*>(X), (int)M, (int)K, Xt};
+    const Transpose tw{reinterpret_cast<const __nv_bfloat16*>(W), (int)N, (int)K, Wt};
+    const int nz = (dW ? 1 : 0) + (dX ? 1 : 0);
+    if (nz > 0) {
+      const Transpose first = dW ? tx : tw;
+      const int64_t rows = nz == 2 ? std::max(M, N) : first.R;
+      k_transpose2_bf16<<<dim3((unsigned)((K + TT - 1) / TT), (unsigned)((rows + TT - 1) / TT), (unsigned)nz), tb, 0,
+                          s>>>(first, tw);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+  }
   // dX [M][K] = dZ [M][N] . (W^T [K][N])^T ;  dW [N][K] = dZ^T [N][M] . (X^T [K][M])^T
   if (dX && (e = launch_gemm_bf16(dZ, Wt, dX, M, K, N, false, nullptr, GWX_ACT_NONE, 0, s)) != cudaSuccess) return e;
   if (dW && (e = launch_gemm_splitk(dZt, Xt, dW, N, K, M, kpart, s)) != cudaSuccess) return e;
