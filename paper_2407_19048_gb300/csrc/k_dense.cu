@@ -94,13 +94,14 @@ __global__ void __launch_bounds__(256) k_transpose2_bf16(Transpose a, Transpose 
 // db[n] = sum_p part[p][n] (FP64 accumulation of the FP32 tile sums), in two
 // deterministic passes: block (32 columns, slice y of the partials) has row lane ty sum
 // partials ty, ty + 32, ... of its slice, the 32 lanes in order into part2[y][n]; then
-// k_colsum_finish adds the slices in order.
+// k_colsum_finish adds the slices in order.  With one slice the first pass writes db itself
+// (db non-null): the same FP64 sum, rounded once.
 constexpr int CS_MAX_SLICES = 64;
 
 int colsum_slices(int64_t P) { return (int)std::min<int64_t>(CS_MAX_SLICES, std::max<int64_t>(1, (P + 255) / 256)); }
 
 __global__ void __launch_bounds__(1024) k_colsum(const float* __restrict__ part, int P, int N,
-                                                 double* __restrict__ part2) {
+                                                 double* __restrict__ part2, float* __restrict__ db) {
   __shared__ double red[TT][TT + 1];
   const int n = blockIdx.x * TT + threadIdx.x;
   const int per = (P + gridDim.y - 1) / gridDim.y, p0 = blockIdx.y * per, p1 = min(P, p0 + per);
@@ -112,7 +113,8 @@ __global__ void __launch_bounds__(1024) k_colsum(const float* __restrict__ part,
   if (threadIdx.y == 0 && n < N) {
     double t = 0.0;
     for (int y = 0; y < TT; ++y) t += red[y][threadIdx.x];
-    part2[(int64_t)blockIdx.y * N + n] = t;
+    if (db) db[n] = (float)t;
+    else part2[(int64_t)blockIdx.y * N + n] = t;
   }
 }
 
@@ -189,9 +191,9 @@ cudaError_t launch_dense_backward(const void* X, const void* W, const float* bia
   if (dW && (e = launch_gemm_splitk(dZt, Xt, dW, N, K, M, kpart, s)) != cudaSuccess) return e;
   if (db) {
     const int slices = colsum_slices(P);
-    k_colsum<<<dim3((unsigned)((N + TT - 1) / TT), (unsigned)slices), dim3(TT, TT), 0, s>>>(part, (int)P, (int)N,
-                                                                                            part2);
-    k_colsum_finish<<<(unsigned)((N + 127) / 128), 128, 0, s>>>(part2, slices, (int)N, db);
+    k_colsum<<<dim3((unsigned)((N + TT - 1) / TT), (unsigned)slices), dim3(TT, TT), 0, s>>>(
+        part, (int)P, (int)N, part2, slices == 1 ? db : nullptr);
+    if (slices > 1) k_colsum_finish<<<(unsigned)((N + 127) / 128), 128, 0, s>>>(part2, slices, (int)N, db);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
