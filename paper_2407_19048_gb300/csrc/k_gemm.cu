@@ -108,10 +108,11 @@ __device__ __forceinline__ void tile_coords(int t, int TM, int TN, int group, in
 }
 
 // Persistent, warp-specialised: warp 0 lane 0 produces (TMA), warp 1 allocates tensor
-// memory and its lane 0 issues the MMAs, warps 2-9 drain accumulators.  Two 256-column
-// accumulators alternate between tiles, so a tile's epilogue overlaps the next tile's
-// main loop; "tfull" (MMA commit) and "tempty" (one arrival per epilogue warp) hand them
-// over.
+// memory and its lane 0 issues the MMAs, warps 2-9 drain accumulators.  MW = 1: two
+// TN_-column accumulators alternate between tiles, so a tile's epilogue overlaps the next
+// tile's main loop; MW = 2 (256 x 256 tiles): the two accumulators are the tile's two
+// 128-row halves and the next tile waits for both to drain.  "tfull" (MMA commit) and
+// "tempty" (one arrival per epilogue warp) hand them over.
 // TN_: tile width; CONV: A is loaded as an implicit im2col tile (ConvGeo).  addend
 // (optional; N % 32 == 0, 16-byte aligned): C = (A B^T + addend), then bias and activation.
 template <bool OUT_BF16, int TN_, bool CONV, int MW = 1>
