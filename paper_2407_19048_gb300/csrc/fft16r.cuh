@@ -125,42 +125,38 @@ __device__ __forceinline__ void dft16(float2* v) {
 }
 
 // ---------------------------------------------------------------- shared memory
-// Load x[j + r nR], r < R (swizzled sw16).
-template <int R, int nR>
-__device__ __forceinline__ void load_strided16(uint32_t x, int j, float2* v) {
-  if constexpr (nR % 256 == 0) {
-    // r nR leaves bits 0-7 alone, so sw16(j + r nR) = sw16(j) + r nR
-    const uint32_t b = x + 8u * (uint32_t)sw16(j);
-#pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = lds2(b + 8u * (uint32_t)(r * nR));
-  } else {
-#pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = lds2(x + 8u * (uint32_t)sw16(j + r * nR));
-  }
+// The passes address x[a + b] with a per-thread part a and b = r 2^s, r < 16, a constant
+// once the callers' loops over r unroll, whose bits do not overlap a's.  The swizzle mask of
+// such a sum is the XOR of the parts' masks: sw16(a + b) = sw16(a) ^ b ^ ((b >> 4) & 15), one
+// XOR with a constant per access.  When sw16(a) < 2^s as well (a < 2^s, or 2^s >= 16 with a's
+// bits all above the field of b), this is (sw16(a) ^ ((b >> 4) & 15)) + b, b's mask being
+// below 2^s as r < 16: few distinct constants, and b an immediate offset.
+__device__ __forceinline__ uint32_t sw16_add(uint32_t sa8, int b) {   // 8 sw16(a + b) from 8 sw16(a)
+  return (sa8 ^ (8u * (uint32_t)((b >> 4) & 15))) + 8u * (uint32_t)b;
+}
+__device__ __forceinline__ uint32_t sw16_xor(uint32_t sa8, int b) {
+  return sa8 ^ (8u * (uint32_t)(b ^ ((b >> 4) & 15)));
 }
 
-// Store the outputs of butterfly j of a pass (R, Ns) to x[idx + r Ns], idx = (j - jm) R + jm,
-// with closed forms of sw16 for the radix-16 strides.
+// Load x[j + r nR], r < R, j < nR (swizzled sw16).
+template <int R, int nR>
+__device__ __forceinline__ void load_strided16(uint32_t x, int j, float2* v) {
+  const uint32_t sj8 = 8u * (uint32_t)sw16(j);
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = lds2(x + sw16_add(sj8, r * nR));
+}
+
+// Store the outputs of butterfly j < n/R of a pass (R, Ns) to x[idx + r Ns],
+// idx = (j - jm) R + jm: idx has no bits in the field of r Ns (below it, jm < Ns; above
+// it, (j - jm) R); for Ns < 16 sw16(idx)'s mask reaches into that field.
 template <int R, int Ns>
 __device__ __forceinline__ void store_pass16(uint32_t x, int j, const float2* v) {
   const int jm = j & (Ns - 1);
-  const int idx = (j - jm) * R + jm;
-  if constexpr (R == 16 && Ns == 1) {
-    // idx = 16 j: r fills bits 0-3, which bits 4-7 (= j) flip
-    const int lo = j & 15;
+  const uint32_t si8 = 8u * (uint32_t)sw16((j - jm) * R + jm);
 #pragma unroll
-    for (int r = 0; r < R; ++r) sts2(x + 8u * (uint32_t)(idx | (r ^ lo)), v[r]);
-  } else if constexpr (R == 16 && Ns % 256 == 0) {
-    const uint32_t b = x + 8u * (uint32_t)sw16(idx);
-#pragma unroll
-    for (int r = 0; r < R; ++r) sts2(b + 8u * (uint32_t)(r * Ns), v[r]);
-  } else if constexpr (R == 16 && Ns == 16) {
-    // idx has bits 4-7 clear: they hold r, which flips bits 0-3
-#pragma unroll
-    for (int r = 0; r < R; ++r) sts2(x + 8u * (uint32_t)((idx ^ r) + 16 * r), v[r]);
-  } else {
-#pragma unroll
-    for (int r = 0; r < R; ++r) sts2(x + 8u * (uint32_t)sw16(idx + r * Ns), v[r]);
+  for (int r = 0; r < R; ++r) {
+    if constexpr (Ns >= 16) sts2(x + sw16_add(si8, r * Ns), v[r]);
+    else sts2(x + sw16_xor(si8, r * Ns), v[r]);
   }
 }
 
