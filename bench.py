@@ -47,9 +47,9 @@ SM_MAX_MHZ_FALLBACK = 2070.0
 # dirty lines is counted and this launch's own L2-resident tail is not), keyed by
 # workload, with the hash of the kernel sources it was measured on.  A workload whose
 # capture does not match the current sources reports null.
-TRAFFIC = {"sweep": {"bytes_per_launch": 8 * 199959040, "B": 8192, "sources_sha1": "507cadcb6da9c1a5d93c228f2770747b36b65a9e",
+TRAFFIC = {"sweep": {"bytes_per_launch": 8 * 199666944, "B": 8192, "sources_sha1": "f9ebc7abb1a4a9f4ac4043fe683ceee8bbef3a46",
                     "note": "ncu DRAM read + write of the second of two back-to-back 1024-draw launches of the same "
-                            "geometry (caches not flushed: it pays the first launch's write-back, 199.96 MB), scaled "
+                            "geometry (caches not flushed: it pays the first launch's write-back, 199.67 MB), scaled "
                             "by the draws per launch"}}
 
 
