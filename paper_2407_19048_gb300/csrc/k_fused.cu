@@ -33,32 +33,42 @@ cudaError_t debug_take_fused(unsigned long long* v) { return dbg_take_this_tu(v)
 // FT times fs) adds
 //   Z'_k += p s_k H_k + q s_nk conj(H_nk),  p = (1 + i conj w)/2, q = (1 - i conj w)/2,
 // w = e^{-i theta}, and the mirrored terms with w_nk = -conj(w) for Z'_nk.
-// hk, hnk: the injected strain's values at the two bins (the detector's projected waveform,
-// zero outside the support), before the factors s; (cs, sn) = (cos, sin) theta.
-__device__ __forceinline__ void fd_pair(float2& zk, float2& znk, float2 hk, float2 hnk, float sk, float snk, float cs,
-                                        float sn) {
+// (tk, ak), (tnk, ank): waveform phase in turns and amplitude factor k^-7/6 of the two
+// bins (ak = 0 outside the support); (cs, sn) = (cos, sin) theta.
+template <int LOGN>
+__device__ __forceinline__ void fd_pair(float2& zk, float2& znk, int k, float tk, float ak, float tnk, float ank,
+                                        float2 gd, unsigned long long nu, float sk, float snk, float cs, float sn) {
+  constexpr int n = 1 << LOGN;
   const float A = 0.5f * (sk + snk), Dl = 0.5f * (sk - snk);
   const float alk = fmaf(-sn, Dl, A), alnk = fmaf(sn, Dl, A), be = __fmul_rn(cs, Dl);
   const float2 a = zk, b = znk;
   zk = make_float2(fmaf(alk, a.x, be * b.y), fmaf(alk, a.y, be * b.x));
   znk = make_float2(fmaf(alnk, b.x, be * a.y), fmaf(alnk, b.y, be * a.x));
-  hk = cscale(hk, sk);
-  hnk = cscale(hnk, snk);
-  const float pr = 0.5f * (1.0f - sn), qr = 0.5f * (1.0f + sn), wi = 0.5f * cs;
-  // Z'_k += p hk + q conj(hnk), p = (pr, wi), q = (qr, -wi)
-  zk.x += pr * hk.x - wi * hk.y + qr * hnk.x - wi * hnk.y;
-  zk.y += pr * hk.y + wi * hk.x - qr * hnk.y - wi * hnk.x;
-  // Z'_nk += p' hnk + q' conj(hk), p' = (pr, -wi), q' = (qr, wi)
-  znk.x += pr * hnk.x + wi * hnk.y + qr * hk.x + wi * hk.y;
-  znk.y += pr * hnk.y - wi * hnk.x - qr * hk.y + wi * hk.x;
+  if (ak != 0.f || ank != 0.f) {
+    float2 hk = make_float2(0.f, 0.f), hnk = hk;
+    if (ak != 0.f) hk = cscale(cmul(gd, expm2pi(tk + lin_turns(nu, k))), ak * sk);
+    if (ank != 0.f) hnk = cscale(cmul(gd, expm2pi(tnk + lin_turns(nu, n - k))), ank * snk);
+    // hk, hnk now carry s_k and s_nk
+    const float pr = 0.5f * (1.0f - sn), qr = 0.5f * (1.0f + sn), wi = 0.5f * cs;
+    // Z'_k += p hk + q conj(hnk), p = (pr, wi), q = (qr, -wi)
+    zk.x += pr * hk.x - wi * hk.y + qr * hnk.x - wi * hnk.y;
+    zk.y += pr * hk.y + wi * hk.x - qr * hnk.y - wi * hnk.x;
+    // Z'_nk += p' hnk + q' conj(hk), p' = (pr, -wi), q' = (qr, wi)
+    znk.x += pr * hnk.x + wi * hnk.y + qr * hk.x + wi * hk.y;
+    znk.y += pr * hnk.y - wi * hnk.x - qr * hk.y + wi * hk.x;
+  }
 }
 
 // The bin k = n/2, which pairs with itself (theta = pi/2: alpha = s_h, beta = 0, p = 0, q = 1).
-__device__ __forceinline__ void fd_half(float2& z, float2 hh, float sh) {
+template <int LOGN>
+__device__ __forceinline__ void fd_half(float2& z, float t, float a, float2 gd, unsigned long long nu, float sh) {
+  constexpr int h = (1 << LOGN) / 2;
   z = cscale(z, sh);
-  hh = cscale(hh, sh);
-  z.x += hh.x;
-  z.y -= hh.y;
+  if (a != 0.f) {
+    const float2 hh = cscale(cmul(gd, expm2pi(t + lin_turns(nu, h))), a * sh);
+    z.x += hh.x;
+    z.y -= hh.y;
+  }
 }
 
 // DC and Nyquist (carried together in element 0); the waveform is zero there.
@@ -225,12 +235,6 @@ __global__ void __launch_bounds__((1 << LOGN) / 16, LOGN >= 13 ? 1 : 2)
   __shared__ DrawCoef sc;
   __shared__ __align__(8) uint64_t bars[2];   // staging barriers: crop, filter
   __shared__ int s_o[2];                      // offsets within the staged crop and filter
-  // per detector d: g_d e^{-2 pi i nu_d o} for the offsets o = T s + NB r (index [d][0][s RL + r])
-  // and o = n - T s - NB r ([d][1][...]) of this draw; bin t + T s + NB r of thread t then
-  // takes the factor e^{-2 pi i nu_d t} times [d][0], its partner n - that bin the conjugate
-  // times [d][1]
-  __shared__ float2 s_lin[GWX_MAX_DET][2][8];
-  static_assert(SLOTS * RL == 8, "eight bins per side and thread");
   float2 (*wv)[T] = reinterpret_cast<float2 (*)[T]>(sm + (PP ? 2 : 1) * n);   // 16 x T waveform values
   float* crop_s = reinterpret_cast<float*>(sm + 2 * n);                        // ST: N + 4 floats
   float* w_s = crop_s + N + 4;                                                  // ST: n + 4 floats
@@ -279,16 +283,10 @@ __global__ void __launch_bounds__((1 << LOGN) / 16, LOGN >= 13 ? 1 : 2)
     const bool odd = (off & 1) != 0;
     __syncthreads();
     const DrawCoef& c = sc;
-    for (int i = t; i < 16 * D; i += T) {
-      const int d = i >> 4, side = (i >> 3) & 1, sr = i & 7;
-      const int o = T * (sr / RL) + NB * (sr % RL);
-      s_lin[d][side][sr] = cmul(make_float2(c.g[d].x, c.g[d].z), expm2pi(lin_turns(c.nu[d], side ? n - o : o)));
-    }
 
-    // waveform values k^{-7/6} e^{-2 pi i Psi_k/(2 pi)} of the 16 bins this thread owns in
-    // the short-radix pass (0 outside the support), kept in shared memory as wv[v][t] for
-    // the D detectors (a rolled loop: the evaluation is long, and 32 inlined copies crowd
-    // the instruction cache)
+    // waveform values (turns, amplitude factor) of the 16 bins this thread owns in the
+    // short-radix pass, kept in shared memory as wv[v][t] for the D detectors (a rolled
+    // loop: the evaluation is long, and 32 inlined copies crowd the instruction cache)
 #pragma unroll 1
     for (int s = 0; s < SLOTS; ++s) {
       const int p = t + s * T;
@@ -297,9 +295,9 @@ __global__ void __launch_bounds__((1 << LOGN) / 16, LOGN >= 13 ? 1 : 2)
       for (int r = 0; r < RL; ++r) {
         float tt, aa;
         wave_bin(c, jA + NB * r, k_lo, tt, aa);
-        wv[WIDX(s, 0, r)][t] = cscale(expm2pi(tt), aa);
+        wv[WIDX(s, 0, r)][t] = make_float2(tt, aa);
         wave_bin(c, jB + NB * r, k_lo, tt, aa);
-        wv[WIDX(s, 1, r)][t] = cscale(expm2pi(tt), aa);
+        wv[WIDX(s, 1, r)][t] = make_float2(tt, aa);
       }
     }
 
@@ -408,9 +406,6 @@ __global__ void __launch_bounds__((1 << LOGN) / 16, LOGN >= 13 ? 1 : 2)
       // step and first inverse pass, all in registers
       const float2 gd = make_float2(c.g[d].x, c.g[d].z);
       const unsigned long long nu = c.nu[d];
-      const float2 lt = expm2pi(lin_turns(nu, t));   // e^{-2 pi i nu_d t}
-      // g_d e^{-2 pi i nu_d k} of a bin k, straight from the fixed-point nu
-      auto gd_lin = [&](int k) -> float2 { return cmul(gd, expm2pi(lin_turns(nu, k))); };
       const float* Wd = W + (int64_t)d * F;
       int ow = 0;
       if constexpr (ST) {
@@ -471,30 +466,29 @@ __global__ void __launch_bounds__((1 << LOGN) / 16, LOGN >= 13 ? 1 : 2)
 #pragma unroll
           for (int r = 0; r < RL; ++r) {
             const float2 ea = wv[WIDX(s, 0, r)][t], eb = wv[WIDX(s, 1, RL - 1 - r)][t];
-            const int k = jA + NB * r;   // = t + T s + NB r
+            const int k = jA + NB * r;
             const float2 e = rot_pi16(u, r * (16 / RL));   // e^{i pi k/n}
-            const float2 hk = cmul(ea, cmul(lt, s_lin[d][0][s * RL + r]));
-            const float2 hnk = cmul(eb, cmul(cconj(lt), s_lin[d][1][s * RL + r]));
-            fd_pair(vA[s][r], vB[s][RL - 1 - r], hk, hnk, s_of(k), s_of(n - k), e.x, e.y);
+            fd_pair<LOGN>(vA[s][r], vB[s][RL - 1 - r], k, ea.x, ea.y, eb.x, eb.y, gd, nu, s_of(k), s_of(n - k), e.x,
+                          e.y);
           }
         } else {
           fd_dc(vA[s][0], s_of(0), s_of(n));
-          fd_half(vA[s][RL / 2], cmul(wv[WIDX(s, 0, RL / 2)][t], gd_lin(n / 2)), s_of(n / 2));
+          const float2 eh = wv[WIDX(s, 0, RL / 2)][t];
+          fd_half<LOGN>(vA[s][RL / 2], eh.x, eh.y, gd, nu, s_of(n / 2));
 #pragma unroll
           for (int r = 1; r < RL / 2; ++r) {
             const float2 ea = wv[WIDX(s, 0, r)][t], eb = wv[WIDX(s, 0, RL - r)][t];
             const int k = NB * r;
             const float2 e = eipi16(r * (16 / RL));
-            fd_pair(vA[s][r], vA[s][RL - r], cmul(ea, gd_lin(k)), cmul(eb, gd_lin(n - k)), s_of(k), s_of(n - k), e.x,
-                    e.y);
+            fd_pair<LOGN>(vA[s][r], vA[s][RL - r], k, ea.x, ea.y, eb.x, eb.y, gd, nu, s_of(k), s_of(n - k), e.x, e.y);
           }
 #pragma unroll
           for (int r = 0; r < RL / 2; ++r) {
             const float2 ea = wv[WIDX(s, 1, r)][t], eb = wv[WIDX(s, 1, RL - 1 - r)][t];
             const int k = NB / 2 + NB * r;
             const float2 e = eipi16(8 / RL + r * (16 / RL));
-            fd_pair(vB[s][r], vB[s][RL - 1 - r], cmul(ea, gd_lin(k)), cmul(eb, gd_lin(n - k)), s_of(k), s_of(n - k), e.x,
-                    e.y);
+            fd_pair<LOGN>(vB[s][r], vB[s][RL - 1 - r], k, ea.x, ea.y, eb.x, eb.y, gd, nu, s_of(k), s_of(n - k), e.x,
+                          e.y);
           }
         }
         dftR<RL, true, false>(vA[s]);
