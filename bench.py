@@ -1092,7 +1092,21 @@ def run_gpu(args, wl):
     b.synchronize()
     e2e_s = max_over_ranks(a.elapsed_time(b) * 1e-3, dd)
     e2e_value = world * B * n_e2e / e2e_s
-    del sim_e2e, host_y
+    del sim_e2e
+    # the device-to-host link alone: the step's output bytes copied from device memory to
+    # pinned host memory, three times on one stream (splitting the copy over 2, 4 or 8
+    # streams measured the same rate), the bound of the end-to-end loop
+    dev_y = torch.zeros_like(host_y[0], device="cuda")
+    host_y[0].copy_(dev_y, non_blocking=True)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(3):
+        host_y[0].copy_(dev_y, non_blocking=True)
+    b.record()
+    b.synchronize()
+    d2h_link_gbs = 3 * dev_y.numel() * 4 / (a.elapsed_time(b) * 1e-3) / 1e9
+    e2e_d2h_gbs = d2h * n_e2e / e2e_s / 1e9
+    del dev_y, host_y
 
     hl3 = hl3_leg(gwx, torch, rank, args, flush)
     wl_hl3 = workloads.workload("hl3")
@@ -1134,7 +1148,8 @@ def run_gpu(args, wl):
                     "path": "every step: background strain H2D from pinned host memory, welch_psd, prepare_batch "
                             "and simulate_prepared, whitened batch + parameters + offsets D2H to pinned host "
                             "memory; batch i's output copy overlaps batch i + 1's compute",
-                    "steps": n_e2e},
+                    "steps": n_e2e, "d2h_gbs": e2e_d2h_gbs, "d2h_link_gbs": d2h_link_gbs,
+                    "d2h_frac_of_link": e2e_d2h_gbs / d2h_link_gbs},
             "gpu_launches": launches,
             "value_background_every_step": value_bg1,
             "clocks": clk,
