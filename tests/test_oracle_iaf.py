@@ -1,0 +1,159 @@
+"""Pins of the inverse-autoregressive flow oracle (Sec. 5.1), on the CPU: the paper's
+parameter count, the autoregressive structure (exact independence, mask path counts, a
+triangular Jacobian), the change of variables against a numerical Jacobian, an affine
+special case against scipy's multivariate normal, normalisation by quadrature, the
+paper's pass counts (one to sample, D for a density), and a planted self-connection that
+breaks invertibility."""
+import numpy as np
+import pytest
+from scipy.stats import multivariate_normal
+
+from oracle import iaf
+
+
+def _rows(B, D, C, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((B, D)), rng.standard_normal((B, C))
+
+
+def test_parameter_count_is_the_papers():
+    """60 transforms x 6 masked layers of 100 units over D = 8 with the 8-dimensional
+    representation as context: the paper's ~3.2 million."""
+    n = iaf.n_params(8, 8)
+    assert n == 3_228_960
+    assert abs(n / 3.2e6 - 1.0) < 0.02
+    stack = iaf.init(8, 8, seed=0)
+    assert sum(t.size for layer in stack for t in layer) == n
+
+
+@pytest.mark.parametrize("H,n_hidden,wide", [(100, 6, True), (7, 2, False)])
+def test_outputs_ignore_their_own_and_later_coordinates(H, n_hidden, wide):
+    """Exactly unchanged up to the perturbed coordinate at any width; changed after it at
+    the paper's width (with one unit per degree, H = 7, a ReLU that is off for every row
+    can cut the only path)."""
+    D, C = 8, 8
+    layer = iaf.init(D, C, H=H, n_hidden=n_hidden, K=1, seed=3, out_scale=1.0)[0]
+    v, c = _rows(4, D, C, 7)
+    mu0, s0 = iaf.made(layer, v, c)
+    for j in range(D):
+        w = v.copy()
+        w[:, j] += 1.7
+        mu1, s1 = iaf.made(layer, w, c)
+        # exactly unchanged up to coordinate j, changed after it
+        assert np.array_equal(mu1[:, :j + 1], mu0[:, :j + 1]) and np.array_equal(s1[:, :j + 1], s0[:, :j + 1])
+        if wide and j < D - 1:
+            assert np.all(np.abs(mu1[:, j + 1:] - mu0[:, j + 1:]).max(axis=0) > 0)
+
+
+def test_mask_paths_reach_exactly_the_earlier_coordinates():
+    D, C = 8, 8
+    ms = iaf.masks(D, C)
+    P = ms[0][:, :D]
+    for m in ms[1:]:
+        P = m @ P
+    for block in (P[:D], P[D:]):          # shifts, log-scales
+        for i in range(D):
+            assert np.all(block[i, i:] == 0) and np.all(block[i, :i] > 0)
+    assert np.all(ms[0][:, D:] == 1)     # the context reaches every first-layer unit
+
+
+def test_round_trip():
+    D, C = 8, 8
+    stack = iaf.init(D, C, H=32, n_hidden=6, K=12, seed=2, out_scale=0.5)
+    z, c = _rows(16, D, C, 1)
+    x, lq = iaf.sample(stack, z, c)
+    lq2, z2 = iaf.log_prob(stack, x, c)
+    assert np.abs(z2 - z).max() < 1e-11
+    assert np.abs(lq2 - lq).max() < 1e-10
+
+
+def _jacobian(f, z, h=1e-6):
+    D = z.shape[0]
+    J = np.empty((D, D))
+    for j in range(D):
+        e = np.zeros(D)
+        e[j] = h
+        J[:, j] = (f(z + e) - f(z - e)) / (2 * h)
+    return J
+
+
+def test_one_transform_has_a_triangular_jacobian_with_diagonal_e_s():
+    D, C = 8, 8
+    layer = iaf.init(D, C, H=24, n_hidden=3, K=1, seed=4, out_scale=1.0)[0]
+    v, c = _rows(1, D, C, 5)
+    J = _jacobian(lambda u: iaf.forward(layer, u[None, :], c)[0][0], v[0])
+    _, s = iaf.made(layer, v, c)
+    assert np.abs(np.triu(J, 1)).max() == 0.0
+    assert np.allclose(np.diag(J), np.exp(s[0]), rtol=1e-8, atol=0)
+
+
+def test_density_is_the_change_of_variables():
+    """ln q(x) = ln N(z) - ln|det dx/dz|, the determinant from a numerical Jacobian."""
+    D, C = 8, 8
+    stack = iaf.init(D, C, H=24, n_hidden=3, K=5, seed=6, out_scale=0.7)
+    z, c = _rows(3, D, C, 8)
+    for b in range(3):
+        f = lambda u: iaf.sample(stack, u[None, :], c[b:b + 1])[0][0]
+        _, logdet = np.linalg.slogdet(_jacobian(f, z[b]))
+        _, lq = iaf.sample(stack, z[b:b + 1], c[b:b + 1])
+        assert abs((iaf.log_normal(z[b:b + 1])[0] - logdet) - lq[0]) < 1e-6
+
+
+def test_constant_autoencoders_give_scipys_gaussian():
+    """With the output weights zero every transform is affine with constant shift and
+    scale, so x is Gaussian: scipy's multivariate normal gives its density."""
+    D, C, K = 4, 2, 3
+    stack = iaf.init(D, C, H=10, n_hidden=2, K=K, seed=9)
+    rng = np.random.default_rng(10)
+    A, b = np.eye(D), np.zeros(D)
+    R = np.eye(D)[::-1]                     # coordinate reversal
+    for k, layer in enumerate(stack):
+        layer[-2][:] = 0.0
+        layer[-1][:] = rng.uniform(-1.5, 1.5, 2 * D)
+        mu, s = layer[-1][:D], iaf.S_MAX * np.tanh(layer[-1][D:] / iaf.S_MAX)
+        if k:
+            A, b = R @ A, R @ b
+        A, b = np.diag(np.exp(s)) @ A, np.exp(s) * b + mu
+    x, c = _rows(6, D, C, 11)
+    lq, _ = iaf.log_prob(stack, x, c)
+    ref = multivariate_normal(mean=b, cov=A @ A.T).logpdf(x)
+    assert np.abs(lq - ref).max() < 1e-10
+
+
+def test_two_dimensional_density_integrates_to_one():
+    D, C = 2, 1
+    stack = iaf.init(D, C, H=8, n_hidden=2, K=4, seed=12, out_scale=0.6)
+    h = 0.04
+    g = np.arange(-12.0, 12.0, h) + h / 2
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    pts = np.stack([X.ravel(), Y.ravel()], axis=1)
+    c = np.full((len(pts), C), 0.3)
+    lq, _ = iaf.log_prob(stack, pts, c)
+    assert abs(np.exp(lq).sum() * h * h - 1.0) < 2e-3
+
+
+def test_pass_counts_one_to_sample_d_for_a_density():
+    D, C, K = 8, 8, 5
+    stack = iaf.init(D, C, H=16, n_hidden=2, K=K, seed=13)
+    z, c = _rows(2, D, C, 14)
+    st = {}
+    x, _ = iaf.sample(stack, z, c, stats=st)
+    assert st["made"] == K
+    st = {}
+    iaf.log_prob(stack, x, c, stats=st)
+    assert st["made"] == K * D
+
+
+def test_a_self_connection_breaks_the_inverse():
+    """Planted mistake: output masks that keep degree-equal weights (>= instead of >) let
+    mu_i see v_i, and the sequential inverse no longer recovers the input."""
+    D, C = 8, 8
+    layer = iaf.init(D, C, H=24, n_hidden=2, K=1, seed=15, out_scale=1.0)[0]
+    d_in, d_h, d_out = iaf.degrees(D, 24, 2)
+    rng = np.random.default_rng(16)
+    bad = (d_out[:, None] >= d_h[-1][None, :]).astype(np.float64)
+    layer[-2] = rng.standard_normal(bad.shape) / np.sqrt(24) * bad
+    v, c = _rows(4, D, C, 17)
+    y, _ = iaf.forward(layer, v, c)
+    v2, _ = iaf.inverse(layer, y, c)
+    assert np.abs(v2 - v).max() > 1e-3
