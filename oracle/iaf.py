@@ -145,3 +145,123 @@ def log_prob(stack, x, c, rnd=exact, stats=None):
         if k:
             v = v[:, ::-1]
     return log_normal(v) - tot, v
+
+
+# ---------------------------------------------------------------- training gradient
+# The loss of a row is -ln q(x) = |z|^2 / 2 + (D / 2) ln 2 pi + sum over transforms of
+# sum_i s_i, evaluated in the density direction.  Its gradient follows that direction's
+# passes backwards: pass i of a transform read the partial v (entries i .. D-1 still zero),
+# set v_i = (y_i - mu_i) e^{-s_i} and contributed s_i to the log-determinant, so it sends
+#   dy_i = g_i e^{-s_i},  dmu_i = -g_i e^{-s_i},  ds_i = -g_i v_i + (the loss's weight on s)
+# back, its autoencoder turns (dmu_i, ds_i) into gradients of the weights, the context and
+# the partial v, and entry i of g is consumed.  The weights' gradients are masked (a masked
+# weight stays zero under any update); a rounding hook, where given, counts as the identity.
+
+
+def made_tape(layer, v, c, rnd=exact):
+    """(mu, s, tape) with tape = (layer inputs [n], pre-activations [n - 1], s)."""
+    v = np.asarray(v, dtype=np.float64)
+    D = v.shape[1]
+    g = rnd(np.concatenate([v, np.asarray(c, dtype=np.float64)], axis=1))
+    n = len(layer) // 2
+    ins, pre = [g], []
+    for l in range(n - 1):
+        a = g @ layer[2 * l].T + layer[2 * l + 1][None, :]
+        pre.append(a)
+        g = rnd(relu(a))
+        ins.append(g)
+    o = g @ layer[2 * n - 2].T + layer[2 * n - 1][None, :]
+    s = S_MAX * np.tanh(o[:, D:] / S_MAX)
+    return o[:, :D], s, (ins, pre, s)
+
+
+def made_backward(layer, ms, tape, dmu, ds):
+    """Gradients (dW [n], db [n], du) of one autoencoder pass from those of mu and s; du is
+    the gradient of its input row [v, c]."""
+    ins, pre, s = tape
+    n = len(layer) // 2
+    do = np.concatenate([dmu, ds * (1.0 - (s / S_MAX) ** 2)], axis=1)
+    dW, db = [None] * n, [None] * n
+    for l in reversed(range(n)):
+        dW[l] = (do.T @ ins[l]) * ms[l]
+        db[l] = do.sum(axis=0)
+        d_in = do @ layer[2 * l]
+        if l:
+            do = d_in * (pre[l - 1] > 0.0)
+    return dW, db, d_in
+
+
+def inverse_tape(layer, y, c, rnd=exact):
+    """The density direction of one transform with the passes' tapes: (v, sum_s, tape)."""
+    y = np.asarray(y, dtype=np.float64)
+    D = y.shape[1]
+    v = np.zeros_like(y)
+    tot = np.zeros(len(y))
+    passes = []
+    for i in range(D):
+        mu, s, t = made_tape(layer, v, c, rnd)
+        v = v.copy()
+        v[:, i] = (y[:, i] - mu[:, i]) * np.exp(-s[:, i])
+        tot += s[:, i]
+        passes.append((t, s[:, i].copy()))
+    return v, tot, passes
+
+
+def inverse_backward(layer, ms, passes, v, g, ws):
+    """Back through one transform's density direction: g = d loss / d v (its output), ws =
+    the loss's weight on its sum_s per row.  Returns (d loss / d y, dW, db, dc)."""
+    D = v.shape[1]
+    g = np.array(g, dtype=np.float64)
+    dy = np.zeros_like(g)
+    n = len(layer) // 2
+    dW = [np.zeros_like(layer[2 * l]) for l in range(n)]
+    db = [np.zeros_like(layer[2 * l + 1]) for l in range(n)]
+    dc = 0.0
+    for i in reversed(range(D)):
+        t, s_i = passes[i]
+        e = np.exp(-s_i)
+        dy[:, i] = g[:, i] * e
+        dmu = np.zeros_like(g)
+        ds = np.zeros_like(g)
+        dmu[:, i] = -g[:, i] * e
+        ds[:, i] = -g[:, i] * v[:, i] + ws
+        g[:, i] = 0.0                       # entry i was an input zero, overwritten
+        w_l, b_l, du = made_backward(layer, ms, t, dmu, ds)
+        for l in range(n):
+            dW[l] += w_l[l]
+            db[l] += b_l[l]
+        g += du[:, :D]
+        dc = dc + du[:, D:]
+    return dy, dW, db, dc
+
+
+def loss_and_grads(stack, x, c, rnd=exact):
+    """Mean over rows of -ln q(x) and its gradients: (loss, grads per transform as
+    [dW_1, db_1, ...] (masked), dc [B][C], dx [B][D])."""
+    x = np.asarray(x, dtype=np.float64)
+    B, D = x.shape
+    C = np.asarray(c).shape[1]
+    H = stack[0][0].shape[0]
+    ms = masks(D, C, H, len(stack[0]) // 2 - 1)
+    v = x
+    tot = np.zeros(B)
+    tapes = [None] * len(stack)
+    for k in reversed(range(len(stack))):
+        v_out, ss, passes = inverse_tape(stack[k], v, c, rnd)
+        tapes[k] = (passes, v_out)
+        tot += ss
+        v = v_out[:, ::-1] if k else v_out
+    z = v
+    loss = np.mean(0.5 * np.sum(z * z, axis=1) + 0.5 * D * LN_2PI + tot)
+    g = z / B
+    ws = np.full(B, 1.0 / B)
+    grads = [None] * len(stack)
+    dc = np.zeros((B, C))
+    for k in range(len(stack)):
+        if k:
+            g = g[:, ::-1]
+        passes, v_out = tapes[k]
+        g, dW, db, dck = inverse_backward(stack[k], ms, passes, v_out, g, ws)
+        grads[k] = [t for pair in zip(dW, db) for t in pair]
+        dc += dck
+    return loss, grads, dc, g

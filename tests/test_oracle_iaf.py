@@ -2,8 +2,9 @@
 parameter count, the autoregressive structure (exact independence, mask path counts, a
 triangular Jacobian), the change of variables against a numerical Jacobian, an affine
 special case against scipy's multivariate normal, normalisation by quadrature, the
-paper's pass counts (one to sample, D for a density), and a planted self-connection that
-breaks invertibility."""
+paper's pass counts (one to sample, D for a density), a planted self-connection that
+breaks invertibility, and the training gradient against central differences (weights,
+data and context), masked weights without gradient and a planted dropped term."""
 import numpy as np
 import pytest
 from scipy.stats import multivariate_normal
@@ -157,3 +158,66 @@ def test_a_self_connection_breaks_the_inverse():
     y, _ = iaf.forward(layer, v, c)
     v2, _ = iaf.inverse(layer, y, c)
     assert np.abs(v2 - v).max() > 1e-3
+
+
+def _fd_setup():
+    D, C, H, nh, K = 4, 3, 6, 2, 3
+    stack = iaf.init(D, C, H=H, n_hidden=nh, K=K, seed=21, out_scale=0.8)
+    x, c = _rows(5, D, C, 22)
+    return stack, x, c, iaf.masks(D, C, H, nh)
+
+
+def _loss(stack, x, c):
+    return -iaf.log_prob(stack, x, c)[0].mean()
+
+
+def test_loss_is_the_mean_negative_log_density():
+    stack, x, c, _ = _fd_setup()
+    loss, _, _, _ = iaf.loss_and_grads(stack, x, c)
+    assert abs(loss - _loss(stack, x, c)) < 1e-12
+
+
+def test_gradient_against_central_differences():
+    stack, x, c, ms = _fd_setup()
+    _, G, dc, dx = iaf.loss_and_grads(stack, x, c)
+    rng = np.random.default_rng(23)
+    h = 1e-6
+
+    def fd(arr, idx):
+        arr[idx] += h
+        lp = _loss(stack, x, c)
+        arr[idx] -= 2 * h
+        lm = _loss(stack, x, c)
+        arr[idx] += h
+        return (lp - lm) / (2 * h)
+
+    for k in range(len(stack)):
+        for t, arr in enumerate(stack[k]):
+            for _ in range(4):
+                idx = tuple(int(rng.integers(0, n)) for n in arr.shape)
+                if t % 2 == 0 and ms[t // 2][idx] == 0:
+                    continue
+                assert abs(fd(arr, idx) - G[k][t][idx]) <= 1e-6 * max(abs(G[k][t][idx]), 1e-3), (k, t, idx)
+    for i, j in [(0, 0), (2, 1), (4, 3)]:
+        assert abs(fd(x, (i, j)) - dx[i, j]) <= 1e-6 * max(abs(dx[i, j]), 1e-3)
+        if j < c.shape[1]:
+            assert abs(fd(c, (i, j)) - dc[i, j]) <= 1e-6 * max(abs(dc[i, j]), 1e-3)
+
+
+def test_masked_weights_get_no_gradient():
+    stack, x, c, ms = _fd_setup()
+    _, G, _, _ = iaf.loss_and_grads(stack, x, c)
+    for k in range(len(stack)):
+        for l, m in enumerate(ms):
+            assert np.all(G[k][2 * l][m == 0] == 0.0)
+
+
+def test_dropping_the_log_determinant_term_is_caught(monkeypatch):
+    """Planted mistake: the backward pass without the log-determinant's weight on s."""
+    stack, x, c, _ = _fd_setup()
+    _, G_good, _, _ = iaf.loss_and_grads(stack, x, c)
+    orig = iaf.inverse_backward
+    monkeypatch.setattr(iaf, "inverse_backward", lambda layer, ms, passes, v, g, ws: orig(layer, ms, passes, v, g, 0 * ws))
+    _, G_bad, _, _ = iaf.loss_and_grads(stack, x, c)
+    out = len(G_good[0]) - 1                # the output layer's bias
+    assert np.abs(G_bad[0][out] - G_good[0][out]).max() > 1e-3
