@@ -2,8 +2,8 @@
 
 This package is the slow, plain, obviously-correct restatement of what the GPU
 library computes.  It exists only to check the GPU path: the only code allowed
-to import it is ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg
-of ``bench.py``.  The product path (the ``paper_2407_19048_gb300`` package and
+to import it is ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline and
+reference legs of ``bench.py``.  The product path (the ``paper_2407_19048_gb300`` package and
 its CUDA library) never imports, calls or links anything here, and this package
 imports nothing from the product.
 
@@ -29,6 +29,12 @@ Modules, in pipeline order:
 * ``learn``      -- the learned Gaussian proposal: features, loss, AdamW, proposal density.
 * ``flow``       -- the conditional coupling flow: embedding, coupling layers, loss and its
   gradient, base draws, the proposal map to theta and the prior-to-proposal ratio.
+* ``resnet``     -- the ResNet-1D data summary of Sec. 4, forward and backward.
+* ``vicreg``     -- VICReg pre-training of the summary (Sec. 4.1): loss, gradient, view re-timing.
+* ``skymap``     -- HEALPix pixels, sky maps from weighted draws and per-pixel flow densities (Sec. 5).
+* ``iaf``        -- the paper's inverse-autoregressive flow (Sec. 5.1): MADE masks,
+  sampling, the D-pass density and the training gradient (a variant the library's
+  kernels do not build yet).
 * ``pipeline``   -- the whole per-batch pass, step by step, unfused.
 
 Everything is float64 / uint32-uint64 numpy.  ``numpy.fft`` is used as the
