@@ -589,8 +589,8 @@ def flow_resnet_leg(gwx, torch, rank, steps=1500, batch=512, events=64, pretrain
     """The flow with the paper's ResNet-1D data summary (stem, (5, 3, 3) residual blocks of
     64 / 128 / 256 channels, group norm, kernel 5; convolutions on the tensor cores) in
     place of the spectral-feature network, trained jointly with AdamW on 512-draw batches
-    of the non-spinning two-detector workload; importance sampling of config 4's events
-    as in the flow leg.  A second arm first pre-trains the ResNet with VICReg on the raw
+    of the non-spinning two-detector workload; importance sampling of the 64 two-detector
+    events of U{2000..50000} draws as in the flow leg.  A second arm first pre-trains the ResNet with VICReg on the raw
     whitened strain (Sec. 4.1: two views per source that differ in the merger time,
     expander 64 -> 128 -> 24, weights 1, 1, 5; 800 steps of 256 view pairs at a learning
     rate of 1e-4 -- at 1e-3 or 3e-4 the flow trained after it was behind the plain arm),
@@ -682,7 +682,7 @@ def flow_resnet_leg(gwx, torch, rank, steps=1500, batch=512, events=64, pretrain
 
 def tmarg_leg(gwx, torch, events=64, lo=2000, hi=50000, reps=3, oversample=None, n_tc=None):
     """The likelihood with the merger time integrated out (`gwx_log_likelihood_tmarg`)
-    alone, on config 4's scale: `events` two-detector events of the non-spinning workload
+    alone, at the importance-sampling scale: `events` two-detector events of the non-spinning workload
     with U{lo..hi} prior samples each, the merger time integrated over the prior's window
     on a grid 16 times finer than the sampling interval (u = 16 inverse transforms of
     n = N/2 = 1024 packed points per sample; `oversample` and `n_tc` override u and the
@@ -780,7 +780,8 @@ def is_compare(gwx, torch, fp, wl, y_ev, psd, counts, grid, seed=5, reps=3):
 
 def flow_leg(gwx, torch, rank, steps=12000, events=64, pp_events=200, pp_samples=500, lr=1e-3, batch=4096,
              layers=16, hidden=256, clip=1.0):
-    """The learned part (config 3) and its importance-sampling judge (config 4).
+    """The learned part (the flow trained on 4096-draw batches of the two-detector workload)
+    and its importance-sampling judge (64 events of U{2000..50000} draws).
 
     The conditional coupling flow (16 affine coupling layers, conditioners 72 -> 256 ->
     256 -> 8; embedding 1968 -> 512 -> 512 -> 64 on log group powers, inter-detector
@@ -838,7 +839,8 @@ def flow_leg(gwx, torch, rank, steps=12000, events=64, pp_events=200, pp_samples
     torch.cuda.synchronize()
     step_graph_ms = ev0.elapsed_time(ev1) / 50
     del graph, fp_t, y1, th1
-    # events: config 4's 64 events of the same generator (other parameter seed)
+    # events: the importance-sampling workload's 64 events of the same generator (other
+    # parameter seed)
     wl_ev = dict(workloads.workload("small_nonspinning", B=events), param_seed=777)
     sim_ev = gwx.simulator.Simulator(wl_ev)
     y_ev, th_ev, _ = sim_ev.step(step_counter(rank, 0))
@@ -887,7 +889,7 @@ def flow_leg(gwx, torch, rank, steps=12000, events=64, pp_events=200, pp_samples
                 times.append(time.perf_counter() - a0)
         times.sort()
         sky_density[str(nside)] = times[len(times) // 2] * 1e3
-    # config 4: importance sampling, flow vs prior, 64 events x U{2000..50000} draws
+    # importance sampling, flow vs prior, 64 events x U{2000..50000} draws
     counts = workloads.ragged_counts(4, events, 2000, 50000)
     isamp = is_compare(gwx, torch, fp, wl_ev, y_ev, sim_ev.psd, counts, grid)
     # PP test: percentile of each truth among its event's flow draws, per flow coordinate
@@ -1187,7 +1189,7 @@ def main(argv=None):
     ap.add_argument("--only-loglike", default=None, metavar="LO,HI",
                     help="run only the log-likelihood leg with U{LO..HI} samples per event; for profiling")
     ap.add_argument("--only-chain", default=None, metavar="E,LO,HI",
-                    help="time config 4's importance-sampling chains alone (prior and an untrained flow) on E "
+                    help="time the importance-sampling chains alone (prior and an untrained flow) on E "
                          "events of U{LO..HI} draws")
     ap.add_argument("--only-tmarg", default=None, metavar="E,LO,HI[,U,NTC]",
                     help="run only the merger-time-marginalised likelihood on E events of U{LO..HI} samples "
@@ -1245,7 +1247,7 @@ def main(argv=None):
         from paper_2407_19048_gb300.flow import FlowPosterior
         gwx.init()
         E, lo, hi = (int(v) for v in args.only_chain.split(","))
-        # config 4's events and the benchmark flow's shape, untrained: the same kernels and
+        # the importance-sampling events and the benchmark flow's shape, untrained: the same kernels and
         # amounts of work as the trained flow's chain (its ESS figures mean nothing)
         wl_ev = dict(workloads.workload("small_nonspinning", B=E), param_seed=777)
         sim_ev = gwx.simulator.Simulator(wl_ev)
