@@ -9,7 +9,9 @@ The inverse transform runs in four steps (Bailey 1990) with n = n1 n2, k = k1 + 
 and m = n2 m1 + m2: pass A forms G[k1][m2] = e^{2 pi i k1 m2/n} sum_k2 e^{2 pi i k2 m2/n2}
 Z_k, pass B z_m = sum_k1 e^{2 pi i k1 m1/n1} G[k1][m2].  This test restates both steps
 and checks them against numpy, so a wrong index split, twiddle or packing sign fails here
-before any GPU run."""
+before any GPU run.  The forward counterpart (the likelihood's data rows) unpacks
+Z = FFT_n(x_2m + i x_2m+1) into X_k = E + w^k O and X_{n-k} = conj(E - w^k O) with
+E = (Z_k + conj Z_{n-k})/2, O = -i (Z_k - conj Z_{n-k})/2."""
 import numpy as np
 import pytest
 
@@ -76,3 +78,18 @@ def test_a_wrong_twiddle_sign_fails():
     Z = rng.standard_normal(n1 * n2) + 1j * rng.standard_normal(n1 * n2)
     ref = n1 * n2 * np.fft.ifft(Z)
     assert np.abs(_fourstep_inverse(Z, n1, n2, twiddle_sign=-1.0) - ref).max() > 1.0
+
+
+@pytest.mark.parametrize("n", [16, 1024])
+def test_unpacking_gives_the_real_spectrum(n):
+    rng = np.random.default_rng(n + 1)
+    x = rng.standard_normal(2 * n)
+    Z = np.fft.fft(x[0::2] + 1j * x[1::2])
+    X = np.fft.rfft(x)
+    w = np.exp(-2j * np.pi / (2 * n))
+    for k in range(1, n // 2 + 1):
+        Znk = Z[(n - k) % n]
+        E = (Z[k] + np.conj(Znk)) / 2
+        O = -1j * (Z[k] - np.conj(Znk)) / 2
+        assert abs(E + w ** k * O - X[k]) < 1e-11 * np.sqrt(n)
+        assert abs(np.conj(E - w ** k * O) - X[n - k]) < 1e-11 * np.sqrt(n)
