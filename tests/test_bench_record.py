@@ -91,3 +91,16 @@ def test_end_to_end_bytes(rec, wl):
         # bytes per step x steps per second (value / B)
         assert math.isclose(e["d2h_gbs"], e["d2h_bytes_per_step"] * e["value"] / wl["B"] / 1e9, rel_tol=1e-6)
         assert math.isclose(e["d2h_frac_of_link"], e["d2h_gbs"] / e["d2h_link_gbs"], rel_tol=1e-9)
+
+
+def test_marginal_likelihood_leg_arithmetic(rec):
+    """u inverse transforms of n = N/2 points per sample at 5 n log2 n flops each (the
+    two-detector workload: N = 2048, u = 16), and the achieved rate from the call time."""
+    t = rec["log_likelihood_tmarg"]
+    r = t["roofline"]
+    n, u = 1024, t["grid"]["oversample"]
+    assert r["flops_per_sample"] == u * 5 * n * int(math.log2(n))
+    assert math.isclose(t["samples_per_s"], t["samples"] / (t["ms_per_call"] * 1e-3), rel_tol=1e-9)
+    assert math.isclose(r["achieved"], r["flops_per_sample"] * t["samples_per_s"] / 1e12, rel_tol=1e-9)
+    assert math.isclose(r["frac"], r["achieved"] / r["peak"], rel_tol=1e-9)
+    assert math.isclose(r["peak"], rec["roofline"]["peak"], rel_tol=1e-9)
