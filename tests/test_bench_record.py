@@ -104,3 +104,15 @@ def test_marginal_likelihood_leg_arithmetic(rec):
     assert math.isclose(r["achieved"], r["flops_per_sample"] * t["samples_per_s"] / 1e12, rel_tol=1e-9)
     assert math.isclose(r["frac"], r["achieved"] / r["peak"], rel_tol=1e-9)
     assert math.isclose(r["peak"], rec["roofline"]["peak"], rel_tol=1e-9)
+
+
+def test_gemm_leg_arithmetic(rec):
+    """The 8192^3 bf16 product: 2 M N K flops over the measured time, for both arms, and
+    the fraction of the measured bf16 peak."""
+    g = rec["gemm_bf16"]
+    flops = 2.0 * 8192 ** 3
+    assert math.isclose(g["tflops"], flops / (g["ms"] * 1e-3) / 1e12, rel_tol=1e-9)
+    assert math.isclose(g["cublas_tflops"], flops / (g["cublas_ms"] * 1e-3) / 1e12, rel_tol=1e-9)
+    r = g["roofline"]
+    assert r["bound"] == "tensor" and math.isclose(r["achieved"], g["tflops"], rel_tol=1e-12)
+    assert math.isclose(r["frac"], r["achieved"] / r["peak"], rel_tol=1e-9)
