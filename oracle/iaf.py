@@ -37,6 +37,7 @@ import math
 
 import numpy as np
 
+from . import flow
 from .flow import S_MAX, exact, relu
 
 N_HIDDEN = 6      # masked hidden layers per transform (Sec. 5.1)
@@ -265,3 +266,29 @@ def loss_and_grads(stack, x, c, rnd=exact):
         grads[k] = [t for pair in zip(dW, db) for t in pair]
         dc += dck
     return loss, grads, dc, g
+
+
+# ---------------------------------------------------------------- posterior draws
+# The same proposal as the coupling flow's (oracle.flow): base normals z and the ordering
+# coin from Philox (flow.base_normals), x from the stack, r = mean + scale x mapped to
+# theta with the prior-to-proposal log ratio (flow.proposal_params); only the map z -> x
+# and its log-determinant differ.
+
+
+def sample_posterior(stack, c_events, mean, scale, prior, offsets, seed, counter, rnd=exact):
+    """Draws of event e in rows offsets[e] .. offsets[e+1]-1 with context c_events[e]:
+    (theta [11][S], ln q_r [S], ln pi_r - ln q_r [S])."""
+    S = int(np.asarray(offsets)[-1])
+    ev = flow.event_of(offsets, S)
+    z, coin = flow.base_normals(seed, counter, np.arange(S))
+    x, lq = sample(stack, z, np.asarray(c_events, dtype=np.float64)[ev], rnd)
+    return flow.proposal_params(x, z, log_normal(z) - lq, mean, scale, prior, coin,
+                                flow.nuisance_uniforms(seed, counter, np.arange(S)))
+
+
+def log_prob_theta(stack, c, theta, mean, scale, rnd=exact):
+    """ln q_r(r(theta) | c) for each column of theta [11][B] with its context row (the
+    density over the eight modelled coordinates; D passes per transform)."""
+    x = flow.standardise(flow.coords(theta), mean, scale)
+    lq, _ = log_prob(stack, x, c, rnd)
+    return lq - np.sum(np.log(np.asarray(scale)))

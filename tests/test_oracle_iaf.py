@@ -221,3 +221,45 @@ def test_dropping_the_log_determinant_term_is_caught(monkeypatch):
     _, G_bad, _, _ = iaf.loss_and_grads(stack, x, c)
     out = len(G_good[0]) - 1                # the output layer's bias
     assert np.abs(G_bad[0][out] - G_good[0][out]).max() > 1e-3
+
+
+def _proposal_setup():
+    import workloads
+    from oracle import flow as fl
+    prior = workloads.workload("small")["prior"]
+    r = fl.coords(workloads.random_theta(48, 4000, prior))
+    return prior, r.mean(axis=0), r.std(axis=0), fl
+
+
+def test_posterior_draws_and_density_agree():
+    """ln q_r returned with each draw equals the D-pass density of its theta."""
+    prior, mean, scale, fl = _proposal_setup()
+    stack = iaf.init(8, 8, H=16, n_hidden=2, K=3, seed=31, out_scale=0.5)
+    c_events = np.random.default_rng(32).standard_normal((3, 8))
+    offsets = np.array([0, 5, 5, 40])
+    theta, log_q, lr = iaf.sample_posterior(stack, c_events, mean, scale, prior, offsets, 99, 1)
+    ok = np.isfinite(lr)
+    assert ok.sum() > 5
+    lp = iaf.log_prob_theta(stack, c_events[fl.event_of(offsets, 40)], theta, mean, scale)
+    assert np.max(np.abs(lp[ok] - log_q[ok])) < 1e-7
+
+
+@pytest.mark.parametrize("K", [3, 2])
+def test_identity_stack_proposes_its_base_draws(K):
+    """Zero output layers make every transform the identity: the draws are the Philox base
+    normals themselves (reversed once for an even number of transforms), with no
+    log-determinant, through the coupling flow's map to theta."""
+    prior, mean, scale, fl = _proposal_setup()
+    stack = iaf.init(8, 8, H=16, n_hidden=2, K=K, seed=33)
+    for layer in stack:
+        layer[-2][:] = 0.0
+        layer[-1][:] = 0.0
+    offsets = np.array([0, 30])
+    got = iaf.sample_posterior(stack, np.zeros((1, 8)), mean, scale, prior, offsets, 7, 3)
+    z, coin = fl.base_normals(7, 3, np.arange(30))
+    x = z if K % 2 else z[:, ::-1]
+    ref = fl.proposal_params(x, z, np.zeros(30), mean, scale, prior, coin,
+                             fl.nuisance_uniforms(7, 3, np.arange(30)))
+    for a, b in zip(got, ref):
+        assert np.array_equal(np.isfinite(a), np.isfinite(b))
+        assert np.allclose(a[np.isfinite(a)], b[np.isfinite(b)], rtol=0, atol=1e-12)
