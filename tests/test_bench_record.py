@@ -116,3 +116,17 @@ def test_gemm_leg_arithmetic(rec):
     r = g["roofline"]
     assert r["bound"] == "tensor" and math.isclose(r["achieved"], g["tflops"], rel_tol=1e-12)
     assert math.isclose(r["frac"], r["achieved"] / r["peak"], rel_tol=1e-9)
+
+
+def test_four_second_window_leg_arithmetic(rec):
+    """The 4 s-window workload (three detectors, N = 8192, 2048 draws per step): rate from
+    the step time, the flop model of its shapes and the roofline fraction."""
+    h = rec["hl3"]
+    wl = workloads.workload("hl3")
+    r = h["roofline"]
+    assert math.isclose(h["injections_per_s"], wl["B"] / (h["ms_per_step"] * 1e-3), rel_tol=1e-9)
+    assert r["flops_per_injection"] == bench.flops_per_injection(wl) and r["injections_per_launch"] == wl["B"]
+    achieved = r["flops_per_injection"] * wl["B"] / (r["avg_launch_ms"] * 1e-3) / 1e12
+    assert math.isclose(r["achieved"], achieved, rel_tol=1e-9)
+    assert math.isclose(r["frac"], r["achieved"] / r["peak"], rel_tol=1e-9)
+    assert r["algorithmic_bytes_per_launch"] == wl["B"] * len(wl["dets"]) * wl["N"] * 4
